@@ -1,0 +1,143 @@
+/*
+ * C ABI of the GB300 pseudo-spectral Navier-Stokes solver.
+ *
+ * The library advances the Galerkin ODE of Eq. NSfinal (Mortensen &
+ * Langtangen, arXiv 1602.03638, Sec. 2)
+ *
+ *     d u_hat/dt = P[ mask * F(u x omega) ] - nu |k|^2 u_hat,
+ *     P(v) = v - k (k.v)/|k|^2,   omega_hat = i k x u_hat,
+ *
+ * on the triply periodic box [0, 2 pi]^3 with N^3 points (Eq. realmesh),
+ * using the classical RK4 driver of the paper's Appendix and the 2/3-rule
+ * dealiasing of Sec. 3.1. Every step of the path runs in the library's own
+ * CUDA kernels on one GPU; there is no CPU fallback.
+ *
+ * Conventions shared by all entry points
+ * --------------------------------------
+ * - Every function returns an int status: DNS_OK (0) or a negative dns_status.
+ *   No function aborts the process. dns_last_error() gives a message.
+ * - Precision: DNS_F32 (float / complex float) or DNS_F64 (double / complex
+ *   double); all array arguments use the handle's precision.
+ * - Physical arrays: real, shape (3, N, N, N), C order, x slowest
+ *   (u[c][i][j][k] = u_c(2 pi i/N, 2 pi j/N, 2 pi k/N)).
+ * - Spectral arrays: interleaved complex, shape (3, N, N, N/2+1), C order
+ *   [c][kx][ky][kz] as in Sec. 3.1: kx, ky in FFT order (0..N/2-1, -N/2..-1),
+ *   kz = 0..N/2. Transforms are unnormalised forward (e^{-ik.x}) and
+ *   1/N^3-normalised inverse.
+ * - The state never carries Nyquist modes: on input every mode with
+ *   |kx| = N/2, |ky| = N/2 or kz = N/2 is set to zero, and the method keeps
+ *   them zero (they lie outside the dealiasing box).
+ * - Pointers: `on_device` = 1 means a CUDA device pointer (16-byte aligned,
+ *   e.g. a torch tensor's data_ptr()); 0 means host memory (pinned host
+ *   memory gives the fastest copies). The caller owns every buffer it
+ *   passes; the library copies in and out and keeps no reference.
+ * - Streams: work is enqueued on the handle's stream (dns_set_stream);
+ *   dns_step returns after enqueueing, and kernel errors surface at the next
+ *   call that synchronises (dns_get_state*, dns_diagnostics, dns_rhs).
+ * - Supported N: 8, 12, 16, 24, 32, 48, 64, 96, 128, 256, 512, 1024.
+ */
+#ifndef DNS_GB300_H
+#define DNS_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dns_handle dns_handle;
+
+typedef enum { DNS_F32 = 0, DNS_F64 = 1 } dns_dtype;
+
+typedef enum {
+  DNS_OK = 0,
+  DNS_ERR_ARG = -1,         /* invalid argument (N, dtype, pointer, option, ...) */
+  DNS_ERR_OOM = -2,         /* device allocation failed */
+  DNS_ERR_CUDA = -3,        /* a CUDA call or kernel failed */
+  DNS_ERR_NONFINITE = -4,   /* the state holds NaN or Inf */
+  DNS_ERR_TIMEOUT = -5,     /* reserved: a bounded device wait expired */
+  DNS_ERR_UNSUPPORTED = -6  /* no usable sm_103 device, or N not instantiated */
+} dns_status;
+
+/* Diagnostics, all computed in FP64 on the device (Appendix energy; the
+ * workshop quantities named in Sec. 4 "Verification"):
+ *   t           simulated time (number of steps taken times dt)
+ *   energy      E   = 1/2 <|u|^2>            (grid mean, Appendix reduce)
+ *   dissipation eps = nu <|omega|^2>
+ *   max_div     max over the mesh of |div u| = |F^{-1}(i k . u_hat)|
+ *   helicity    H   = <u . omega>
+ *   enstrophy   Z   = 1/2 <|omega|^2>
+ * E, eps, H, Z use the spectral (Parseval) sums over the half spectrum. */
+typedef struct {
+  double t, energy, dissipation, max_div, helicity, enstrophy;
+} dns_diag;
+
+/* Creates a solver for an N^3 grid with viscosity nu and time step dt in the
+ * given precision; allocates 16 complex component-volumes of N^2 (N/2) values
+ * on the current CUDA device (state, RK4 base/accumulator/stage, 6+1 work
+ * fields). Sec. 3.1 (mesh, wavenumbers, arrays) and the Appendix constants.
+ * Errors: DNS_ERR_ARG (N unsupported, nu < 0, dt <= 0, dtype, out NULL),
+ * DNS_ERR_UNSUPPORTED (no compute capability 10.3 device), DNS_ERR_OOM. */
+int dns_create(int N, double nu, double dt, int dtype, dns_handle** out);
+
+/* Frees everything the handle owns. NULL is accepted. */
+int dns_destroy(dns_handle* h);
+
+/* Stream for all subsequent work (a cudaStream_t; NULL = the handle's own
+ * stream, created at dns_create). */
+int dns_set_stream(dns_handle* h, void* stream);
+
+/* Options:
+ *   "dealias_variant"  0: keep |k_i| < N/3 (Sec. 3.1 text, default)
+ *                      1: keep |k_i| < 2/3 (N/2+1) (the Appendix script)
+ *   "use_graph"        1: dns_step replays a captured CUDA graph (default)
+ *   "nu", "dt"         change the viscosity / time step
+ *   "time"             set the simulated time reported by dns_diagnostics
+ * Errors: DNS_ERR_ARG for an unknown key or a value out of range. */
+int dns_set_option(dns_handle* h, const char* key, double value);
+
+/* State from a physical velocity field u (3,N,N,N): u_hat = F(u) with the
+ * Nyquist modes zeroed (Eq. iffteq forward transform; no projection).
+ * Resets the time to 0. */
+int dns_set_state(dns_handle* h, const void* u, int on_device);
+
+/* State from spectral coefficients (3,N,N,N/2+1), complex, paper order;
+ * Nyquist modes are zeroed. Resets the time to 0. */
+int dns_set_state_spectral(dns_handle* h, const void* uhat, int on_device);
+
+/* Enqueues n >= 0 classical RK4 steps (Appendix: a = 1/6,1/3,1/3,1/6,
+ * b = 1/2,1/2,1) of Eq. NSfinal. Asynchronous. */
+int dns_step(dns_handle* h, int n);
+
+/* Physical velocity u = F^{-1}(u_hat), (3,N,N,N). Synchronises the stream. */
+int dns_get_state(dns_handle* h, void* u, int on_device);
+
+/* Spectral state (3,N,N,N/2+1) complex, paper order (kz = N/2 plane = 0).
+ * Synchronises the stream. */
+int dns_get_state_spectral(dns_handle* h, void* uhat, int on_device);
+
+/* One evaluation of the right-hand side of Eq. NSfinal at the current state,
+ * written as (3,N,N,N/2+1) complex in paper order (computeRHS of Sec. 3.1).
+ * Does not change the state. Synchronises the stream. */
+int dns_rhs(dns_handle* h, void* duhat, int on_device);
+
+/* FP64 diagnostics of the current state (see dns_diag). Synchronises.
+ * Returns DNS_ERR_NONFINITE (with *out filled) if any NaN/Inf is present. */
+int dns_diagnostics(dns_handle* h, dns_diag* out);
+
+/* Bytes of device memory the handle owns. */
+size_t dns_device_bytes(const dns_handle* h);
+
+/* Message of the last failed call on this thread (h may be NULL). Never NULL. */
+const char* dns_last_error(const dns_handle* h);
+
+/* Test hook for allocation-failure handling: the n-th device allocation made
+ * by the library from now on (n >= 1) reports DNS_ERR_OOM without touching
+ * the device; n = 0 disables the hook. */
+int dns_debug_fail_alloc_after(int n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DNS_GB300_H */

@@ -1,0 +1,545 @@
+// C ABI of the solver (include/dns.h): handle life cycle, state transfer,
+// RK4 stepping through a captured CUDA graph, diagnostics, and the small
+// non-templated kernels (layout transposes, final diagnostic sum).
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/dns.h"
+#include "dns_internal.h"
+#include "fft_core.cuh"
+#include "instances.h"
+
+namespace dns {
+
+#define DNS_DECL(T, tag, N) const DnsOps* dns_ops_##tag##_##N();
+DNS_INSTANCES(DNS_DECL)
+#undef DNS_DECL
+
+const DnsOps* find_ops(int dtype, int N) {
+#define DNS_FIND(T, tag, NN) \
+  if (N == NN && dtype == (sizeof(T) == 4 ? 0 : 1)) return dns_ops_##tag##_##NN();
+  DNS_INSTANCES(DNS_FIND)
+#undef DNS_FIND
+  return nullptr;
+}
+
+__global__ void k_diag_final(double* partials, int nblocks) {
+  if (threadIdx.x < 4) {
+    double t = 0.0;
+    for (int b = 0; b < nblocks; ++b) t += partials[b * 4 + threadIdx.x];
+    partials[nblocks * 4 + threadIdx.x] = t;
+  }
+}
+
+// Paper order P[c][kx][ky][kz'] (kz' <= N/2)  <->  internal O[c][kz][ky][kx] (kz < N/2).
+// grid = (ceil(N/32), ceil(kzcount/32), 3*N), block = (32, 8)
+template <typename T>
+__global__ void k_paper_to_internal(const cx<T>* __restrict__ P, cx<T>* __restrict__ O, int N) {
+  __shared__ cx<T> tile[32][33];
+  const int M = N / 2;
+  const int c = blockIdx.z / N, ky = blockIdx.z % N;
+  const int kx0 = blockIdx.x * 32, kz0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int kx = kx0 + i, kz = kz0 + threadIdx.x;
+    if (kx < N && kz < M) tile[i][threadIdx.x] = P[(((size_t)c * N + kx) * N + ky) * (M + 1) + kz];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int kz = kz0 + i, kx = kx0 + threadIdx.x;
+    if (kx < N && kz < M) {
+      cx<T> v = tile[threadIdx.x][i];
+      if (kx == N / 2 || ky == N / 2) v = mk((T)0, (T)0);
+      O[(((size_t)c * M + kz) * N + ky) * N + kx] = v;
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_internal_to_paper(const cx<T>* __restrict__ O, cx<T>* __restrict__ P, int N) {
+  __shared__ cx<T> tile[32][33];
+  const int M = N / 2;
+  const int c = blockIdx.z / N, ky = blockIdx.z % N;
+  const int kx0 = blockIdx.x * 32, kz0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int kz = kz0 + i, kx = kx0 + threadIdx.x;
+    if (kx < N && kz < M) tile[i][threadIdx.x] = O[(((size_t)c * M + kz) * N + ky) * N + kx];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int kx = kx0 + i, kz = kz0 + threadIdx.x;
+    if (kx < N && kz <= M) {
+      const cx<T> v = kz < M ? tile[threadIdx.x][i] : mk((T)0, (T)0);
+      P[(((size_t)c * N + kx) * N + ky) * (M + 1) + kz] = v;
+    }
+  }
+}
+
+}  // namespace dns
+
+using namespace dns;
+
+namespace {
+
+thread_local std::string g_err = "no error";
+std::atomic<int> g_fail_after{0};
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  return fail(DNS_ERR_CUDA, "%s: %s (%s)", where, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+#define DNS_CUDA(call, where)                         \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+  } while (0)
+
+// RK4 weights of the Appendix driver.
+const double RK_A[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+const double RK_B[3] = {0.5, 0.5, 1.0};
+
+// exp(-2 pi i t / N) in FP64 with exact quadrant/octant symmetry.
+void twiddle(long t, long N, double* re, double* im) {
+  t %= N;
+  const long q = (4 * t) / N;
+  const long r = 4 * t - q * N;  // angle = q pi/2 + (pi/2) r/N, 0 <= r < N
+  const double pi = 3.14159265358979323846;
+  double c, s;
+  if (2 * r <= N) {
+    const double phi = pi * (double)r / (2.0 * (double)N);
+    c = std::cos(phi);
+    s = std::sin(phi);
+  } else {
+    const double phi = pi * (double)(N - r) / (2.0 * (double)N);
+    c = std::sin(phi);
+    s = std::cos(phi);
+  }
+  double C, S;
+  switch (q & 3) {
+    case 0: C = c; S = s; break;
+    case 1: C = -s; S = c; break;
+    case 2: C = -c; S = -s; break;
+    default: C = s; S = -c; break;
+  }
+  *re = C;
+  *im = -S;
+}
+
+}  // namespace
+
+struct dns_handle {
+  int N = 0;
+  int dtype = 0;
+  int variant = 0;
+  int use_graph = 1;
+  double nu = 0.0, dt = 0.0, t = 0.0;
+  const DnsOps* ops = nullptr;
+  int device = 0;
+  cudaStream_t own_stream = nullptr, stream = nullptr, cap_stream = nullptr;
+  void* U = nullptr;
+  void* U1 = nullptr;
+  void* US = nullptr;
+  void* W = nullptr;
+  void* D = nullptr;
+  void* tw = nullptr;
+  double* diag = nullptr;
+  size_t bytes = 0;
+  size_t fs = 0;  // complex values per field
+  bool w_valid = false;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  bool graph_dirty = true;
+};
+
+namespace {
+
+int dev_alloc(dns_handle* h, void** p, size_t bytes, const char* what) {
+  int n = g_fail_after.load();
+  if (n > 0) {
+    if (n == 1) {
+      g_fail_after.store(0);
+      return fail(DNS_ERR_OOM, "allocation of %s (%zu bytes) failed (injected)", what, bytes);
+    }
+    g_fail_after.store(n - 1);
+  }
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(DNS_ERR_OOM, "cudaMalloc of %s (%zu bytes) failed: %s", what, bytes, cudaGetErrorString(e));
+  }
+  h->bytes += bytes;
+  return DNS_OK;
+}
+
+void release(dns_handle* h) {
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  void* bufs[] = {h->U, h->U1, h->US, h->W, h->D, h->tw, h->diag};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->own_stream) cudaStreamDestroy(h->own_stream);
+}
+
+PassArgs base_args(const dns_handle* h) {
+  PassArgs a;
+  a.U = h->U;
+  a.U1 = h->U1;
+  a.US = h->US;
+  a.W = h->W;
+  a.D = h->D;
+  a.tw = h->tw;
+  a.nu = h->nu;
+  a.kmax3 = h->N + 2 * h->variant;
+  a.partials = h->diag;
+  a.maxbits = reinterpret_cast<unsigned long long*>(h->diag + DIAG_BLOCKS * 4 + 4);
+  return a;
+}
+
+cudaError_t enqueue_step(dns_handle* h, cudaStream_t st) {
+  PassArgs a = base_args(h);
+  for (int s = 0; s < 4; ++s) {
+    a.stage = s;
+    a.cA = RK_A[s] * h->dt;
+    a.cB = s < 3 ? RK_B[s] * h->dt : 0.0;
+    cudaError_t e = h->ops->rk_stage(a, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+int check_handle(const dns_handle* h) {
+  if (!h || !h->ops) return fail(DNS_ERR_ARG, "invalid handle");
+  return DNS_OK;
+}
+
+int use_device(const dns_handle* h) {
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  return DNS_OK;
+}
+
+size_t phys_bytes(const dns_handle* h) { return (size_t)3 * h->N * h->N * h->N * (h->dtype ? 8 : 4); }
+size_t paper_spec_bytes(const dns_handle* h) {
+  return (size_t)3 * h->N * h->N * (h->N / 2 + 1) * h->ops->elem_bytes;
+}
+
+cudaError_t launch_transpose(dns_handle* h, const void* src, void* dst, bool to_internal) {
+  const int N = h->N, M = N / 2;
+  dim3 block(32, 8);
+  dim3 grid((N + 31) / 32, ((to_internal ? M : M + 1) + 31) / 32, 3 * N);
+  if (h->dtype == 0) {
+    if (to_internal)
+      k_paper_to_internal<float><<<grid, block, 0, h->stream>>>((const cx<float>*)src, (cx<float>*)dst, N);
+    else
+      k_internal_to_paper<float><<<grid, block, 0, h->stream>>>((const cx<float>*)src, (cx<float>*)dst, N);
+  } else {
+    if (to_internal)
+      k_paper_to_internal<double><<<grid, block, 0, h->stream>>>((const cx<double>*)src, (cx<double>*)dst, N);
+    else
+      k_internal_to_paper<double><<<grid, block, 0, h->stream>>>((const cx<double>*)src, (cx<double>*)dst, N);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+int dns_create(int N, double nu, double dt, int dtype, dns_handle** out) {
+  if (!out) return fail(DNS_ERR_ARG, "dns_create: out is NULL");
+  *out = nullptr;
+  if (dtype != DNS_F32 && dtype != DNS_F64) return fail(DNS_ERR_ARG, "dns_create: dtype %d is not DNS_F32/DNS_F64", dtype);
+  if (!(nu >= 0.0) || !std::isfinite(nu)) return fail(DNS_ERR_ARG, "dns_create: nu must be finite and >= 0");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(DNS_ERR_ARG, "dns_create: dt must be finite and > 0");
+  const DnsOps* ops = find_ops(dtype, N);
+  if (!ops) return fail(DNS_ERR_ARG, "dns_create: N = %d is not a supported grid size", N);
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(DNS_ERR_UNSUPPORTED, "dns_create: no CUDA device (%s)", cudaGetErrorString(e));
+  }
+  int dev = 0;
+  DNS_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+  cudaDeviceProp prop;
+  DNS_CUDA(cudaGetDeviceProperties(&prop, dev), "cudaGetDeviceProperties");
+  if (!(prop.major == 10 && prop.minor == 3))
+    return fail(DNS_ERR_UNSUPPORTED, "dns_create: device %d is sm_%d%d; this library is built for sm_103a", dev,
+                prop.major, prop.minor);
+
+  dns_handle* h = new dns_handle();
+  h->N = N;
+  h->dtype = dtype;
+  h->nu = nu;
+  h->dt = dt;
+  h->ops = ops;
+  h->device = dev;
+  const int M = N / 2;
+  h->fs = (size_t)M * N * N;
+  const size_t cb = ops->elem_bytes;
+  int rc = DNS_OK;
+  cudaError_t ce = ops->prepare();
+  if (ce != cudaSuccess) rc = cuda_fail(ce, "kernel attribute set-up");
+  if (rc == DNS_OK) {
+    ce = cudaStreamCreate(&h->own_stream);
+    if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+    if (ce != cudaSuccess) rc = cuda_fail(ce, "cudaStreamCreate");
+    h->stream = h->own_stream;
+  }
+  if (rc == DNS_OK) rc = dev_alloc(h, &h->U, 3 * h->fs * cb, "state U");
+  if (rc == DNS_OK) rc = dev_alloc(h, &h->U1, 3 * h->fs * cb, "RK4 accumulator");
+  if (rc == DNS_OK) rc = dev_alloc(h, &h->US, 3 * h->fs * cb, "RK4 stage state");
+  if (rc == DNS_OK) rc = dev_alloc(h, &h->W, (6 * h->fs + (size_t)3 * N * N) * cb, "work fields");
+  if (rc == DNS_OK) rc = dev_alloc(h, &h->D, h->fs * cb, "divergence field");
+  if (rc == DNS_OK) rc = dev_alloc(h, &h->tw, (size_t)N * cb, "twiddles");
+  if (rc == DNS_OK) rc = dev_alloc(h, (void**)&h->diag, (DIAG_BLOCKS * 4 + 8) * sizeof(double), "diagnostics");
+  if (rc == DNS_OK) {
+    std::vector<double> t64(2 * N);
+    for (int t = 0; t < N; ++t) twiddle(t, N, &t64[2 * t], &t64[2 * t + 1]);
+    if (dtype == DNS_F32) {
+      std::vector<float> t32(2 * N);
+      for (int i = 0; i < 2 * N; ++i) t32[i] = (float)t64[i];
+      ce = cudaMemcpy(h->tw, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice);
+    } else {
+      ce = cudaMemcpy(h->tw, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice);
+    }
+    if (ce == cudaSuccess) ce = cudaMemset(h->U, 0, 3 * h->fs * cb);
+    if (ce != cudaSuccess) rc = cuda_fail(ce, "dns_create initialisation");
+  }
+  if (rc != DNS_OK) {
+    std::string msg = g_err;
+    release(h);
+    delete h;
+    g_err = msg;
+    return rc;
+  }
+  *out = h;
+  return DNS_OK;
+}
+
+int dns_destroy(dns_handle* h) {
+  if (!h) return DNS_OK;
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  release(h);
+  delete h;
+  return DNS_OK;
+}
+
+int dns_set_stream(dns_handle* h, void* stream) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  h->stream = stream ? (cudaStream_t)stream : h->own_stream;
+  return DNS_OK;
+}
+
+int dns_set_option(dns_handle* h, const char* key, double value) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!key) return fail(DNS_ERR_ARG, "dns_set_option: key is NULL");
+  if (!strcmp(key, "dealias_variant")) {
+    if (value != 0.0 && value != 1.0) return fail(DNS_ERR_ARG, "dealias_variant must be 0 or 1");
+    h->variant = (int)value;
+  } else if (!strcmp(key, "use_graph")) {
+    if (value != 0.0 && value != 1.0) return fail(DNS_ERR_ARG, "use_graph must be 0 or 1");
+    h->use_graph = (int)value;
+  } else if (!strcmp(key, "nu")) {
+    if (!(value >= 0.0) || !std::isfinite(value)) return fail(DNS_ERR_ARG, "nu must be finite and >= 0");
+    h->nu = value;
+  } else if (!strcmp(key, "dt")) {
+    if (!(value > 0.0) || !std::isfinite(value)) return fail(DNS_ERR_ARG, "dt must be finite and > 0");
+    h->dt = value;
+  } else if (!strcmp(key, "time")) {
+    if (!std::isfinite(value)) return fail(DNS_ERR_ARG, "time must be finite");
+    h->t = value;
+    return DNS_OK;
+  } else {
+    return fail(DNS_ERR_ARG, "dns_set_option: unknown key '%s'", key);
+  }
+  h->graph_dirty = true;
+  h->w_valid = false;  // the x-inverse in W does not depend on these, but keep it simple
+  return DNS_OK;
+}
+
+int dns_set_state(dns_handle* h, const void* u, int on_device) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!u) return fail(DNS_ERR_ARG, "dns_set_state: u is NULL");
+  if ((rc = use_device(h))) return rc;
+  PassArgs a = base_args(h);
+  if (on_device) {
+    if ((uintptr_t)u % 16) return fail(DNS_ERR_ARG, "dns_set_state: device pointer must be 16-byte aligned");
+    a.in = u;
+  } else {
+    DNS_CUDA(cudaMemcpyAsync(h->W, u, phys_bytes(h), cudaMemcpyHostToDevice, h->stream), "dns_set_state copy");
+    a.in = h->W;
+  }
+  DNS_CUDA(h->ops->forward3d(a, h->stream), "dns_set_state transform");
+  h->w_valid = false;
+  h->t = 0.0;
+  return DNS_OK;
+}
+
+int dns_set_state_spectral(dns_handle* h, const void* uhat, int on_device) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!uhat) return fail(DNS_ERR_ARG, "dns_set_state_spectral: uhat is NULL");
+  if ((rc = use_device(h))) return rc;
+  const void* src = uhat;
+  if (on_device) {
+    if ((uintptr_t)uhat % 16) return fail(DNS_ERR_ARG, "dns_set_state_spectral: device pointer must be 16-byte aligned");
+  } else {
+    DNS_CUDA(cudaMemcpyAsync(h->W, uhat, paper_spec_bytes(h), cudaMemcpyHostToDevice, h->stream),
+             "dns_set_state_spectral copy");
+    src = h->W;
+  }
+  DNS_CUDA(launch_transpose(h, src, h->U, true), "dns_set_state_spectral transpose");
+  h->w_valid = false;
+  h->t = 0.0;
+  return DNS_OK;
+}
+
+int dns_step(dns_handle* h, int n) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (n < 0) return fail(DNS_ERR_ARG, "dns_step: n = %d < 0", n);
+  if (n == 0) return DNS_OK;
+  if ((rc = use_device(h))) return rc;
+  if (!h->w_valid) {
+    DNS_CUDA(h->ops->x_inverse_curl(base_args(h), 0, h->stream), "dns_step initial transform");
+    h->w_valid = true;
+  }
+  if (h->use_graph) {
+    if (h->graph_dirty || !h->gexec) {
+      if (h->gexec) cudaGraphExecDestroy(h->gexec);
+      if (h->graph) cudaGraphDestroy(h->graph);
+      h->gexec = nullptr;
+      h->graph = nullptr;
+      DNS_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal), "graph capture begin");
+      cudaError_t e = enqueue_step(h, h->cap_stream);
+      cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &h->graph);
+      if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+      if (e2 != cudaSuccess) return cuda_fail(e2, "graph capture end");
+      DNS_CUDA(cudaGraphInstantiate(&h->gexec, h->graph, 0), "graph instantiate");
+      h->graph_dirty = false;
+    }
+    for (int i = 0; i < n; ++i) DNS_CUDA(cudaGraphLaunch(h->gexec, h->stream), "graph launch");
+  } else {
+    for (int i = 0; i < n; ++i) DNS_CUDA(enqueue_step(h, h->stream), "dns_step");
+  }
+  h->t += n * h->dt;
+  return DNS_OK;
+}
+
+int dns_get_state(dns_handle* h, void* u, int on_device) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!u) return fail(DNS_ERR_ARG, "dns_get_state: u is NULL");
+  if ((rc = use_device(h))) return rc;
+  if (on_device && (uintptr_t)u % 16) return fail(DNS_ERR_ARG, "dns_get_state: device pointer must be 16-byte aligned");
+  PassArgs a = base_args(h);
+  void* dst = on_device ? u : (void*)((char*)h->W + 3 * h->fs * h->ops->elem_bytes);
+  a.out = dst;
+  DNS_CUDA(h->ops->inverse3d(a, h->stream), "dns_get_state transform");
+  if (!on_device)
+    DNS_CUDA(cudaMemcpyAsync(u, dst, phys_bytes(h), cudaMemcpyDeviceToHost, h->stream), "dns_get_state copy");
+  DNS_CUDA(cudaStreamSynchronize(h->stream), "dns_get_state");
+  h->w_valid = false;
+  return DNS_OK;
+}
+
+int dns_get_state_spectral(dns_handle* h, void* uhat, int on_device) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!uhat) return fail(DNS_ERR_ARG, "dns_get_state_spectral: uhat is NULL");
+  if ((rc = use_device(h))) return rc;
+  if (on_device && (uintptr_t)uhat % 16)
+    return fail(DNS_ERR_ARG, "dns_get_state_spectral: device pointer must be 16-byte aligned");
+  void* dst = on_device ? uhat : (void*)((char*)h->W + 3 * h->fs * h->ops->elem_bytes);
+  DNS_CUDA(launch_transpose(h, h->U, dst, false), "dns_get_state_spectral transpose");
+  if (!on_device) {
+    DNS_CUDA(cudaMemcpyAsync(uhat, dst, paper_spec_bytes(h), cudaMemcpyDeviceToHost, h->stream),
+             "dns_get_state_spectral copy");
+    h->w_valid = false;
+  }
+  DNS_CUDA(cudaStreamSynchronize(h->stream), "dns_get_state_spectral");
+  return DNS_OK;
+}
+
+int dns_rhs(dns_handle* h, void* duhat, int on_device) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!duhat) return fail(DNS_ERR_ARG, "dns_rhs: duhat is NULL");
+  if ((rc = use_device(h))) return rc;
+  if (on_device && (uintptr_t)duhat % 16) return fail(DNS_ERR_ARG, "dns_rhs: device pointer must be 16-byte aligned");
+  PassArgs a = base_args(h);
+  a.out = h->W;  // dU overwrites the forward-transformed product in place
+  DNS_CUDA(h->ops->rhs(a, h->stream), "dns_rhs");
+  void* dst = on_device ? duhat : (void*)((char*)h->W + 3 * h->fs * h->ops->elem_bytes);
+  DNS_CUDA(launch_transpose(h, h->W, dst, false), "dns_rhs transpose");
+  if (!on_device)
+    DNS_CUDA(cudaMemcpyAsync(duhat, dst, paper_spec_bytes(h), cudaMemcpyDeviceToHost, h->stream), "dns_rhs copy");
+  DNS_CUDA(cudaStreamSynchronize(h->stream), "dns_rhs");
+  h->w_valid = false;
+  return DNS_OK;
+}
+
+int dns_diagnostics(dns_handle* h, dns_diag* out) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!out) return fail(DNS_ERR_ARG, "dns_diagnostics: out is NULL");
+  if ((rc = use_device(h))) return rc;
+  PassArgs a = base_args(h);
+  DNS_CUDA(h->ops->diag(a, h->stream), "dns_diagnostics");
+  double r[5];
+  DNS_CUDA(cudaMemcpyAsync(r, h->diag + DIAG_BLOCKS * 4, sizeof(r), cudaMemcpyDeviceToHost, h->stream),
+           "dns_diagnostics copy");
+  DNS_CUDA(cudaStreamSynchronize(h->stream), "dns_diagnostics");
+  const double n6 = std::pow((double)h->N, 6.0);
+  unsigned long long bits;
+  memcpy(&bits, &r[4], sizeof(bits));
+  double mdiv;
+  memcpy(&mdiv, &bits, sizeof(mdiv));
+  out->t = h->t;
+  out->energy = 0.5 * r[0] / n6;
+  out->dissipation = h->nu * r[1] / n6;
+  out->max_div = mdiv;
+  out->helicity = r[2] / n6;
+  out->enstrophy = 0.5 * r[1] / n6;
+  if (r[3] != 0.0 || !std::isfinite(out->energy))
+    return fail(DNS_ERR_NONFINITE, "dns_diagnostics: %g non-finite modes in the state", r[3]);
+  return DNS_OK;
+}
+
+size_t dns_device_bytes(const dns_handle* h) { return h ? h->bytes : 0; }
+
+const char* dns_last_error(const dns_handle* h) {
+  (void)h;
+  return g_err.c_str();
+}
+
+int dns_debug_fail_alloc_after(int n) {
+  if (n < 0) return fail(DNS_ERR_ARG, "dns_debug_fail_alloc_after: n < 0");
+  g_fail_after.store(n);
+  return DNS_OK;
+}
+
+}  // extern "C"

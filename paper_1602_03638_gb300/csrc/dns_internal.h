@@ -1,0 +1,58 @@
+// Host-side interface between the C-ABI layer and the per-(dtype, N)
+// kernel instantiations. One DnsOps table exists for every supported grid
+// size and precision; each entry enqueues kernels on the given stream and
+// returns the launch status.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace dns {
+
+// Device buffers and scalars shared by all passes. Complex arrays use the
+// internal spectral layout [component][kz][ky][kx] with kz < N/2 (the
+// Nyquist plane kz = N/2 is identically zero and not stored).
+struct PassArgs {
+  void* U = nullptr;   // state u_hat at the start of the RK4 step (3 fields)
+  void* U1 = nullptr;  // RK4 accumulator (3 fields)
+  void* US = nullptr;  // RK4 stage state (3 fields)
+  void* W = nullptr;   // work: 6 fields, transforms in flight
+  void* D = nullptr;   // work: 1 field, divergence diagnostic
+  const void* tw = nullptr;  // exp(-2 pi i t / N), t < N
+  double nu = 0.0;
+  double cA = 0.0;  // a_s * dt
+  double cB = 0.0;  // b_s * dt
+  int stage = 0;    // RK4 stage 0..3
+  int kmax3 = 0;    // a mode is kept by the 2/3 rule iff 3|k_i| < kmax3
+  const void* in = nullptr;  // physical input (3,N,N,N) for set_state
+  void* out = nullptr;       // physical output (3,N,N,N) / RHS output
+  double* partials = nullptr;          // diagnostics block partials
+  unsigned long long* maxbits = nullptr;  // diagnostics max|div| (bits of a double)
+};
+
+struct DnsOps {
+  int N;
+  int dtype;  // 0 = FP32, 1 = FP64
+  size_t elem_bytes;  // bytes of one complex value
+  cudaError_t (*prepare)();  // one-time kernel attribute set-up
+  // u_hat (state in a.US if from_stage else a.U) -> W[0..5] = x-inverse of (u, omega) / N^3
+  cudaError_t (*x_inverse_curl)(const PassArgs& a, int from_stage, cudaStream_t s);
+  // one RK4 stage on W (holding the x-inverse of the stage state); leaves
+  // W holding the x-inverse of the next stage state
+  cudaError_t (*rk_stage)(const PassArgs& a, cudaStream_t s);
+  // dU = RHS(U) in internal layout, written to a.out (3 fields)
+  cudaError_t (*rhs)(const PassArgs& a, cudaStream_t s);
+  // a.in (physical, device) -> U (spectral, Nyquist zeroed)
+  cudaError_t (*forward3d)(const PassArgs& a, cudaStream_t s);
+  // U -> a.out (physical, device); uses W[0..2] as scratch
+  cudaError_t (*inverse3d)(const PassArgs& a, cudaStream_t s);
+  // FP64 sums over U into a.partials (DIAG_BLOCKS x 4) and max|div u| into a.maxbits
+  cudaError_t (*diag)(const PassArgs& a, cudaStream_t s);
+};
+
+constexpr int DIAG_BLOCKS = 592;  // 4 x 148..152 SMs: one wave of 4 blocks per SM
+
+// Lookup of the instantiation for (dtype, N); nullptr if unsupported.
+const DnsOps* find_ops(int dtype, int N);
+
+}  // namespace dns

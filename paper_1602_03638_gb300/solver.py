@@ -1,0 +1,140 @@
+"""Python handle over the C ABI (argument marshalling only).
+
+Arrays may be numpy arrays (host memory) or torch tensors (host or CUDA).
+Every computation runs in the library's CUDA kernels; this module only
+checks shapes/dtypes and passes pointers.
+"""
+
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+
+try:
+    import torch
+except ImportError:  # pragma: no cover - torch is part of the runtime image
+    torch = None
+
+
+def _ptr(arr, shape, real_dtype_bytes, complex_):
+    """(pointer, on_device) for a C-contiguous numpy array or torch tensor of the expected shape."""
+    if torch is not None and isinstance(arr, torch.Tensor):
+        if not arr.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        if tuple(arr.shape) != tuple(shape):
+            raise ValueError(f"expected shape {tuple(shape)}, got {tuple(arr.shape)}")
+        want = {(4, False): torch.float32, (8, False): torch.float64, (4, True): torch.complex64, (8, True): torch.complex128}
+        if arr.dtype != want[(real_dtype_bytes, complex_)]:
+            raise ValueError(f"expected dtype {want[(real_dtype_bytes, complex_)]}, got {arr.dtype}")
+        return ctypes.c_void_p(arr.data_ptr()), 1 if arr.is_cuda else 0
+    if isinstance(arr, np.ndarray):
+        if not arr.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        if tuple(arr.shape) != tuple(shape):
+            raise ValueError(f"expected shape {tuple(shape)}, got {tuple(arr.shape)}")
+        want = {(4, False): np.float32, (8, False): np.float64, (4, True): np.complex64, (8, True): np.complex128}
+        if arr.dtype != want[(real_dtype_bytes, complex_)]:
+            raise ValueError(f"expected dtype {np.dtype(want[(real_dtype_bytes, complex_)])}, got {arr.dtype}")
+        return ctypes.c_void_p(arr.ctypes.data), 0
+    raise TypeError("expected a numpy array or a torch tensor")
+
+
+class Solver:
+    """One dns_handle: N^3 grid, viscosity nu, time step dt, 'f32' or 'f64'."""
+
+    def __init__(self, N: int, nu: float, dt: float, dtype: str = "f32", dealias_variant: int = 0):
+        self.N = int(N)
+        self.dtype = dtype
+        self._code = {"f32": _lib.DNS_F32, "f64": _lib.DNS_F64}[dtype]
+        self._rb = 4 if dtype == "f32" else 8
+        h = ctypes.c_void_p()
+        _lib.check(_lib.lib().dns_create(self.N, float(nu), float(dt), self._code, ctypes.byref(h)), "dns_create")
+        self._h = h
+        if dealias_variant:
+            self.set_option("dealias_variant", dealias_variant)
+
+    # -- life cycle ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.lib().dns_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- shapes ---------------------------------------------------------------
+    @property
+    def phys_shape(self):
+        return (3, self.N, self.N, self.N)
+
+    @property
+    def spec_shape(self):
+        return (3, self.N, self.N, self.N // 2 + 1)
+
+    # -- calls ----------------------------------------------------------------
+    def set_stream(self, stream=None):
+        s = None
+        if stream is not None:
+            s = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        _lib.check(_lib.lib().dns_set_stream(self._h, s), "dns_set_stream")
+
+    def set_option(self, key: str, value: float):
+        _lib.check(_lib.lib().dns_set_option(self._h, key.encode(), float(value)), "dns_set_option")
+
+    def set_state(self, u):
+        p, dev = _ptr(u, self.phys_shape, self._rb, False)
+        _lib.check(_lib.lib().dns_set_state(self._h, p, dev), "dns_set_state")
+
+    def set_state_spectral(self, uhat):
+        p, dev = _ptr(uhat, self.spec_shape, self._rb, True)
+        _lib.check(_lib.lib().dns_set_state_spectral(self._h, p, dev), "dns_set_state_spectral")
+
+    def step(self, n: int = 1):
+        _lib.check(_lib.lib().dns_step(self._h, int(n)), "dns_step")
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.empty(self.phys_shape, dtype=np.float32 if self._rb == 4 else np.float64)
+        p, dev = _ptr(out, self.phys_shape, self._rb, False)
+        _lib.check(_lib.lib().dns_get_state(self._h, p, dev), "dns_get_state")
+        return out
+
+    def get_state_spectral(self, out=None):
+        if out is None:
+            out = np.empty(self.spec_shape, dtype=np.complex64 if self._rb == 4 else np.complex128)
+        p, dev = _ptr(out, self.spec_shape, self._rb, True)
+        _lib.check(_lib.lib().dns_get_state_spectral(self._h, p, dev), "dns_get_state_spectral")
+        return out
+
+    def rhs(self, out=None):
+        if out is None:
+            out = np.empty(self.spec_shape, dtype=np.complex64 if self._rb == 4 else np.complex128)
+        p, dev = _ptr(out, self.spec_shape, self._rb, True)
+        _lib.check(_lib.lib().dns_rhs(self._h, p, dev), "dns_rhs")
+        return out
+
+    def diagnostics(self, check_finite: bool = True) -> dict:
+        d = _lib.dns_diag()
+        rc = _lib.lib().dns_diagnostics(self._h, ctypes.byref(d))
+        if check_finite or rc != _lib.DNS_ERR_NONFINITE:
+            _lib.check(rc, "dns_diagnostics")
+        return {k: getattr(d, k) for k, _ in d._fields_}
+
+    def device_bytes(self) -> int:
+        return int(_lib.lib().dns_device_bytes(self._h))

@@ -1,0 +1,90 @@
+"""Host-side checks of the C-ABI library (no GPU needed).
+
+The library is compiled here for sm_103a; these tests load it, check that it
+exports every entry point include/dns.h declares, and exercise the argument
+validation and error reporting that run before any device work.
+"""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1602_03638_gb300 import _lib
+from paper_1602_03638_gb300 import build as B
+
+HEADER_DIR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+
+
+@pytest.fixture(scope="module")
+def L():
+    B.build()
+    return _lib.lib()
+
+
+def _declared(header):
+    with open(os.path.join(HEADER_DIR, header)) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(dns_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared("dns.h")
+    for need in ("dns_create", "dns_set_state", "dns_step", "dns_get_state", "dns_diagnostics", "dns_destroy"):
+        assert need in names
+
+
+def test_library_exports_every_declared_symbol(L):
+    for header in sorted(os.listdir(HEADER_DIR)):
+        if header.endswith(".h"):
+            for name in _declared(header):
+                assert hasattr(L, name), f"{name} declared in {header} but not exported"
+
+
+def test_binding_covers_the_header(L):
+    assert set(_declared("dns.h")) <= set(_lib.SIGNATURES)
+
+
+def test_argument_validation_without_device(L):
+    h = ctypes.c_void_p()
+    assert L.dns_create(10, 0.01, 0.01, 0, ctypes.byref(h)) == _lib.DNS_ERR_ARG
+    assert "N = 10" in _lib.last_error()
+    assert L.dns_create(32, -1.0, 0.01, 0, ctypes.byref(h)) == _lib.DNS_ERR_ARG
+    assert L.dns_create(32, 0.01, 0.0, 0, ctypes.byref(h)) == _lib.DNS_ERR_ARG
+    assert L.dns_create(32, 0.01, 0.01, 7, ctypes.byref(h)) == _lib.DNS_ERR_ARG
+    assert L.dns_create(32, 0.01, 0.01, 0, None) == _lib.DNS_ERR_ARG
+    assert L.dns_step(None, 1) == _lib.DNS_ERR_ARG
+    assert L.dns_diagnostics(None, None) == _lib.DNS_ERR_ARG
+    assert L.dns_set_option(None, b"nu", 0.1) == _lib.DNS_ERR_ARG
+    assert L.dns_destroy(None) == _lib.DNS_OK
+    assert L.dns_device_bytes(None) == 0
+    assert L.dns_debug_fail_alloc_after(-1) == _lib.DNS_ERR_ARG
+    assert L.dns_debug_fail_alloc_after(0) == _lib.DNS_OK
+
+
+def test_create_reports_missing_device_instead_of_crashing(L):
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    h = ctypes.c_void_p()
+    rc = L.dns_create(32, 0.01, 0.01, 0, ctypes.byref(h))
+    assert rc == _lib.DNS_ERR_UNSUPPORTED
+    assert h.value is None
+    assert _lib.last_error()
+
+
+def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(B, "library_path", lambda: str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        _lib.lib()
+
+
+def test_supported_sizes_match_the_instances():
+    sizes = sorted({n for _, _, n in B.instances()})
+    assert sizes == [8, 12, 16, 24, 32, 48, 64, 96, 128, 256, 512, 1024]
+    with open(os.path.join(HEADER_DIR, "dns.h")) as f:
+        assert "8, 12, 16, 24, 32, 48, 64, 96, 128, 256, 512, 1024" in f.read()
