@@ -1,0 +1,362 @@
+#!/usr/bin/env python
+"""Throughput of the GB300 pseudo-spectral Navier-Stokes RK4 solver.
+
+Metric: grid points x RK4 steps per second (higher is better), on the
+Taylor-Green vortex at 512^3 in FP32 (nu = 1/1600, dt = 1e-3): the larger
+Taylor-Green configuration that fits one GPU. One bench step is one full RK4
+step (four right-hand-side evaluations with their transforms, projection,
+viscous term and stage updates) of the whole 512^3 state, resident in HBM.
+
+Printed on rank 0 as one JSON line, with
+  value         device-timed throughput (CUDA events on the solver's stream),
+                summed over all ranks (independent replicas, weak scaling)
+  e2e           the same metric through the C ABI with pinned host buffers:
+                state upload, K steps with a diagnostics read-back each, and
+                the state download, all inside the wall-clock region
+  roofline      the dominant kernel's achieved HBM bandwidth (its algorithmic
+                bytes per launch over its mean CUDA-event duration) against
+                the measured copy bandwidth
+  step_roofline the whole step against the 132-component-volume minimum
+  forms         FP64 at 512^3 and FP32 at 1024^3, and the error of each
+                precision against the FP64 CPU oracle at 128^3
+  cpu_baseline  the FP64 CPU oracle timed on this host's cores
+  clocks        nvidia-smi samples taken during the timed region
+
+--impl reference times the CPU oracle instead (the reference arm).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "grid-points x RK4 steps/s (Taylor-Green 512^3 FP32; FP64 and 1024^3 in 'forms'; % HBM roofline in 'step_roofline')"
+UNIT = "points*steps/s"
+N_MAIN, NU, DT = 512, 1.0 / 1600.0, 1e-3
+SPEC_HBM_GBS = 8000.0
+# Bytes each kernel class must move per launch, in component-volumes
+# cv = N^2 (N/2+1) complex values ("Algorithmic bytes").
+KERNEL_CV = {"y_inverse": 12.0, "z_pass": 9.0, "y_forward": 6.0, "x_stage": 21.0}
+STEP_CV = 132.0
+CPU_N, CPU_STEPS = 128, 8
+PAPER_TG512_PTS_STEPS_PER_S = 6.2e7  # Sec. 4 verification run, 2048 Shaheen cores (context)
+
+
+def cv_bytes(N, real_bytes):
+    return N * N * (N // 2 + 1) * 2 * real_bytes
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons of one GPU, sampled every 200 ms."""
+
+    FIELDS = ["index", "uuid", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+    REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, uuid: str, index: int):
+        self.uuid, self.index = uuid, index
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + ",".join(self.FIELDS), "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [[p.strip() for p in line.split(",")] for line in out.strip().splitlines()]
+        rows = [r for r in rows if len(r) == len(self.FIELDS)]
+        mine = [r for r in rows if self.uuid and self.uuid in r[1]] or [r for r in rows if r[0] == str(self.index)]
+        sm, mx, reasons = [], [], set()
+        for r in mine:
+            try:
+                sm.append(float(r[2]))
+                mx.append(float(r[3]))
+            except ValueError:
+                continue
+            for name, v in zip(self.REASONS, r[5:]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_uuid(torch, dev):
+    try:
+        return str(torch.cuda.get_device_properties(dev).uuid).replace("GPU-", "")
+    except Exception:
+        return ""
+
+
+def ncu_traffic(kernel, N, dtype):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current sources."""
+    from paper_1602_03638_gb300 import build
+
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    digest = build._sources_digest()
+    with open(path) as f:
+        for line in f:
+            tok = line.split()
+            if len(tok) >= 6 and tok[0] == "traffic":
+                _, k, n, dt, b, dig = tok[:6]
+                if k == kernel and int(n) == N and dt == dtype and dig == digest:
+                    return float(b)
+    return None
+
+
+def oracle_sample(N, steps, nu, dt):
+    """Times `steps` RK4 steps of the FP64 oracle on Taylor-Green at N^3; returns (seconds, state, cores)."""
+    from oracle import spectral_ns as sn
+    from paper_1602_03638_gb300 import inputs
+
+    uh = sn.to_spectral(inputs.taylor_green(N))
+    g = sn.Grid(N)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        uh = sn.rk4_step(uh, g, nu, dt)
+    return time.perf_counter() - t0, uh, sn.WORKERS
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import spectral_ns as sn
+    from paper_1602_03638_gb300 import inputs
+
+    N = CPU_N
+    uh = sn.to_spectral(inputs.taylor_green(N))
+    g = sn.Grid(N)
+    for _ in range(args.warmup):
+        uh = sn.rk4_step(uh, g, NU, DT)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        uh = sn.rk4_step(uh, g, NU, DT)
+    secs = time.perf_counter() - t0
+    value = N ** 3 * args.steps / secs
+    sample = f"Taylor-Green {N}^3 FP64 oracle, one RK4 step per bench step (nu=1/1600, dt=1e-3), scipy.fft workers={sn.WORKERS}"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (Taylor-Green initial condition)",
+        "config": main_config(world),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": sn.WORKERS, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main_config(world, N=N_MAIN):
+    return {"workload": f"taylor_green_{N}_f32", "model": "pseudo-spectral NS, RK4, 2/3 dealiasing", "N": N,
+            "nu": NU, "dt": DT, "global_batch": world, "seq_len": None, "parallelism": f"replicas{world}",
+            "l2": "no flush needed: every pass streams 1.6-3.2 GB, > 129 MB L2"}
+
+
+def time_steps(torch, s, st, steps):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        s.step(1)
+    e1.record(st)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def run_form(torch, Solver, inputs, N, dtype, warm, steps):
+    td = torch.float32 if dtype == "f32" else torch.float64
+    with Solver(N, NU, DT, dtype) as s:
+        st = torch.cuda.current_stream()
+        s.set_stream(st)
+        u = inputs.taylor_green_torch(N, device="cuda", dtype=td)
+        s.set_state(u)
+        del u
+        for _ in range(warm):
+            s.step(1)
+        torch.cuda.synchronize()
+        ms = time_steps(torch, s, st, steps) / steps
+    rb = 4 if dtype == "f32" else 8
+    model_ms = STEP_CV * cv_bytes(N, rb) / (measured_peaks()[0] * 1e9) * 1e3
+    return {"N": N, "dtype": dtype, "ms_per_step": ms, "value": N ** 3 / (ms * 1e-3), "steps": steps,
+            "hbm_roofline_frac_of_measured": model_ms / ms}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_env()
+    from paper_1602_03638_gb300 import Solver, build, inputs
+
+    build.build()
+    dev = local if torch.cuda.device_count() > local else 0
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", dev))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    N, dtype = args.N, "f32"
+    peak, peak_kind = measured_peaks()
+    s = Solver(N, NU, DT, dtype)
+    st = torch.cuda.current_stream()
+    s.set_stream(st)
+    u = inputs.taylor_green_torch(N, device="cuda", dtype=torch.float32)
+    s.set_state(u)
+    del u
+    for _ in range(args.warmup):
+        s.step(1)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(gpu_uuid(torch, dev), dev)
+    ms = time_steps(torch, s, st, args.steps)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    barrier()
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    ms_step = ms_max / args.steps
+    value = world * N ** 3 * args.steps / (ms_max * 1e-3)
+
+    # per-kernel CUDA-event timing of the same workload (eager launches)
+    prof = s.profile_steps(args.steps)
+    dom = max(prof, key=lambda k: prof[k][0])
+    dom_ms = prof[dom][0] / prof[dom][1]
+    cvb = cv_bytes(N, 4)
+    achieved = KERNEL_CV[dom] * cvb / (dom_ms * 1e-3) / 1e9
+    kernels = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1], "share": v[0] / sum(x[0] for x in prof.values()),
+                   "algorithmic_GBps": KERNEL_CV[k] * cvb / (v[0] / v[1] * 1e-3) / 1e9} for k, v in prof.items()}
+    s.close()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    step_bytes = STEP_CV * cvb
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": value / PAPER_TG512_PTS_STEPS_PER_S, "dtype": "f32",
+        "data": "synthetic (Taylor-Green initial condition on device)", "config": main_config(world, N),
+        "gpu_launches": 16 * args.steps,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind,
+                     "traffic": ncu_traffic(dom, N, dtype),
+                     "algorithmic_bytes_per_launch": KERNEL_CV[dom] * cvb},
+        "step_roofline": {"model_bytes_per_step": step_bytes, "achieved_GBps": step_bytes / (ms_step * 1e-3) / 1e9,
+                          "frac_of_measured": step_bytes / (ms_step * 1e-3) / 1e9 / peak,
+                          "frac_of_spec_8TBps": step_bytes / (ms_step * 1e-3) / 1e9 / SPEC_HBM_GBS},
+        "kernels": kernels,
+        "clocks": clocks,
+    }
+
+    if not args.no_extras:
+        # end to end through the public API with pinned host buffers
+        with Solver(N, NU, DT, dtype) as s2:
+            host_u = torch.from_numpy(inputs.taylor_green(N, dtype=np.float32)).pin_memory()
+            out_u = torch.empty_like(host_u).pin_memory()
+            s2.set_state(host_u)
+            s2.step(1)
+            s2.diagnostics()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s2.set_state(host_u)
+            for _ in range(args.steps):
+                s2.step(1)
+                d = s2.diagnostics()
+            s2.get_state(out_u)
+            e2e_s = time.perf_counter() - t0
+            ph = 3 * N ** 3 * 4
+            line["e2e"] = {"value": N ** 3 * args.steps / e2e_s, "unit": UNIT,
+                           "h2d_bytes_per_step": ph / args.steps,
+                           "d2h_bytes_per_step": (ph + args.steps * 5 * 8) / args.steps,
+                           "final_energy": d["energy"]}
+        # precision forms
+        forms = [run_form(torch, Solver, inputs, 512, "f64", 2, 3), run_form(torch, Solver, inputs, 1024, "f32", 2, 3)]
+        # CPU oracle baseline and error of each GPU precision against it
+        secs, ref, cores = oracle_sample(CPU_N, CPU_STEPS, NU, DT)
+        errs = {}
+        for dt_ in ("f32", "f64"):
+            with Solver(CPU_N, NU, DT, dt_) as s3:
+                s3.set_state(inputs.taylor_green(CPU_N, dtype=np.float32 if dt_ == "f32" else np.float64))
+                s3.step(CPU_STEPS)
+                got = s3.get_state_spectral()
+            errs[dt_] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        line["forms"] = forms
+        line["error_vs_oracle"] = {"case": f"Taylor-Green {CPU_N}^3, {CPU_STEPS} RK4 steps, nu=1/1600, dt=1e-3",
+                                   "rel_l2_f32": errs["f32"], "rel_l2_f64": errs["f64"]}
+        line["cpu_baseline"] = {"value": CPU_N ** 3 * CPU_STEPS / secs, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"Taylor-Green {CPU_N}^3 FP64, {CPU_STEPS} RK4 steps (bounded sample of the "
+                                          f"Taylor-Green workload), scipy.fft workers={cores}"}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-extras", action="store_true", help="skip e2e, forms and the CPU baseline")
+    ap.add_argument("--N", type=int, default=N_MAIN, help="grid size of the timed workload (profiling runs only)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

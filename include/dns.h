@@ -125,6 +125,14 @@ int dns_rhs(dns_handle* h, void* duhat, int on_device);
  * Returns DNS_ERR_NONFINITE (with *out filled) if any NaN/Inf is present. */
 int dns_diagnostics(dns_handle* h, dns_diag* out);
 
+/* Measurement aid: advances n >= 1 RK4 steps exactly like dns_step but
+ * launches the kernels one by one (no graph) with a CUDA event after each,
+ * and returns per kernel class the summed device time in ms[c] and the
+ * launch count in launches[c]: c = 0 y-inverse, 1 z-pass (c2r, u x omega,
+ * r2c), 2 y-forward, 3 x-stage (forward x, mask, projection, viscous term,
+ * RK4 update, next inverse x). nclass must be >= 4. Synchronises. */
+int dns_profile_steps(dns_handle* h, int n, double* ms, int* launches, int nclass);
+
 /* Bytes of device memory the handle owns. */
 size_t dns_device_bytes(const dns_handle* h);
 

@@ -53,6 +53,7 @@ SIGNATURES = {
     "dns_get_state_spectral": (_I, [_P, _P, _I]),
     "dns_rhs": (_I, [_P, _P, _I]),
     "dns_diagnostics": (_I, [_P, ctypes.POINTER(dns_diag)]),
+    "dns_profile_steps": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_I), _I]),
     "dns_device_bytes": (ctypes.c_size_t, [_P]),
     "dns_last_error": (ctypes.c_char_p, [_P]),
     "dns_debug_fail_alloc_after": (_I, [_I]),

@@ -529,6 +529,49 @@ int dns_diagnostics(dns_handle* h, dns_diag* out) {
   return DNS_OK;
 }
 
+int dns_profile_steps(dns_handle* h, int n, double* ms, int* launches, int nclass) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (n < 1 || !ms || !launches || nclass < 4) return fail(DNS_ERR_ARG, "dns_profile_steps: bad arguments");
+  if ((rc = use_device(h))) return rc;
+  if (!h->w_valid) {
+    DNS_CUDA(h->ops->x_inverse_curl(base_args(h), 0, h->stream), "dns_profile_steps initial transform");
+    h->w_valid = true;
+  }
+  const int nk = 16 * n;
+  std::vector<cudaEvent_t> ev(nk + 1);
+  for (auto& e : ev) DNS_CUDA(cudaEventCreate(&e), "cudaEventCreate");
+  PassArgs a = base_args(h);
+  cudaError_t err = cudaEventRecord(ev[0], h->stream);
+  int k = 0;
+  for (int i = 0; i < n && err == cudaSuccess; ++i) {
+    for (int s = 0; s < 4 && err == cudaSuccess; ++s) {
+      a.stage = s;
+      a.cA = RK_A[s] * h->dt;
+      a.cB = s < 3 ? RK_B[s] * h->dt : 0.0;
+      for (int p = 0; p < 4 && err == cudaSuccess; ++p) {
+        err = h->ops->rk_stage_part(a, p, h->stream);
+        if (err == cudaSuccess) err = cudaEventRecord(ev[++k], h->stream);
+      }
+    }
+  }
+  if (err == cudaSuccess) err = cudaEventSynchronize(ev[k]);
+  for (int c = 0; c < nclass; ++c) {
+    ms[c] = 0.0;
+    launches[c] = 0;
+  }
+  for (int j = 1; j <= k && err == cudaSuccess; ++j) {
+    float t = 0.f;
+    err = cudaEventElapsedTime(&t, ev[j - 1], ev[j]);
+    ms[(j - 1) % 4] += t;
+    launches[(j - 1) % 4] += 1;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (err != cudaSuccess) return cuda_fail(err, "dns_profile_steps");
+  h->t += n * h->dt;
+  return DNS_OK;
+}
+
 size_t dns_device_bytes(const dns_handle* h) { return h ? h->bytes : 0; }
 
 const char* dns_last_error(const dns_handle* h) {

@@ -40,6 +40,9 @@ struct DnsOps {
   // one RK4 stage on W (holding the x-inverse of the stage state); leaves
   // W holding the x-inverse of the next stage state
   cudaError_t (*rk_stage)(const PassArgs& a, cudaStream_t s);
+  // the same stage one kernel at a time: part 0 y-inverse, 1 z-pass,
+  // 2 y-forward, 3 x-stage (for per-kernel timing)
+  cudaError_t (*rk_stage_part)(const PassArgs& a, int part, cudaStream_t s);
   // dU = RHS(U) in internal layout, written to a.out (3 fields)
   cudaError_t (*rhs)(const PassArgs& a, cudaStream_t s);
   // a.in (physical, device) -> U (spectral, Nyquist zeroed)

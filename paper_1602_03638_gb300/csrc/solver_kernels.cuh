@@ -502,6 +502,18 @@ struct SolverImpl {
     return cudaGetLastError();
   }
 
+  static cudaError_t rk_stage_part(const PassArgs& a, int part, cudaStream_t st) {
+    cx<T>* W = reinterpret_cast<cx<T>*>(a.W);
+    const cx<T>* tw = reinterpret_cast<const cx<T>*>(a.tw);
+    switch (part) {
+      case 0: k_ypass<T, N, 1, 0><<<dim3(N / G::YTX, M, 6), YP_THREADS, G::YSMEM, st>>>(W, tw, a.kmax3); break;
+      case 1: k_zpass<T, N, ZM_CROSS><<<dim3(N / G::ZTX, N), ZP_THREADS, G::ZSMEM, st>>>(a); break;
+      case 2: k_ypass<T, N, 0, 1><<<dim3(N / G::YTX, kc_of(a.kmax3), 3), YP_THREADS, G::YSMEM, st>>>(W, tw, a.kmax3); break;
+      default: k_xpass<T, N, XM_STAGE><<<M * N / G::XROWS, XP_THREADS, G::XSMEM, st>>>(a); break;
+    }
+    return cudaGetLastError();
+  }
+
   static cudaError_t rhs(const PassArgs& a, cudaStream_t st) {
     cudaError_t e = x_inverse_curl(a, 0, st);
     if (e != cudaSuccess) return e;
@@ -540,8 +552,9 @@ struct SolverImpl {
   }
 
   static const DnsOps* ops() {
-    static const DnsOps o = {N, sizeof(T) == 4 ? 0 : 1, sizeof(cx<T>), &prepare, &x_inverse_curl, &rk_stage,
-                             &rhs, &forward3d, &inverse3d, &diag};
+    static const DnsOps o = {N,        sizeof(T) == 4 ? 0 : 1, sizeof(cx<T>), &prepare,   &x_inverse_curl,
+                             &rk_stage, &rk_stage_part,        &rhs,          &forward3d, &inverse3d,
+                             &diag};
     return &o;
   }
 };

@@ -136,5 +136,14 @@ class Solver:
             _lib.check(rc, "dns_diagnostics")
         return {k: getattr(d, k) for k, _ in d._fields_}
 
+    KERNEL_CLASSES = ("y_inverse", "z_pass", "y_forward", "x_stage")
+
+    def profile_steps(self, n: int) -> dict:
+        """Advance n steps eagerly; per kernel class (total ms, launches)."""
+        ms = (ctypes.c_double * 4)()
+        ln = (ctypes.c_int * 4)()
+        _lib.check(_lib.lib().dns_profile_steps(self._h, int(n), ms, ln, 4), "dns_profile_steps")
+        return {k: (ms[i], ln[i]) for i, k in enumerate(self.KERNEL_CLASSES)}
+
     def device_bytes(self) -> int:
         return int(_lib.lib().dns_device_bytes(self._h))
