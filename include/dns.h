@@ -139,6 +139,34 @@ size_t dns_device_bytes(const dns_handle* h);
 /* Message of the last failed call on this thread (h may be NULL). Never NULL. */
 const char* dns_last_error(const dns_handle* h);
 
+/* Energy, dissipation, helicity and enstrophy of a caller-supplied spectral
+ * velocity field, computed without allocating any device memory. (The paper
+ * has no counterpart: this is a library service.)
+ *
+ * For callers that cannot call cudaMalloc -- a process whose device memory is
+ * entirely owned by another allocator (e.g. a framework's caching pool that has
+ * reserved the device), or a time-critical loop that must not take the
+ * device-wide synchronisation of cudaMalloc/cudaFree. No handle is needed.
+ *
+ *   uhat   device pointer, 16-byte aligned: (3, N, N, N/2+1) complex in the
+ *          public spectral layout, precision `dtype` (DNS_F32 / DNS_F64)
+ *   N      even, 2 <= N <= 2048 (larger N is rejected with DNS_ERR_ARG)
+ *   nu     viscosity used for the dissipation
+ *   out    device pointer to 5 doubles, 8-byte aligned: energy, dissipation,
+ *          helicity, enstrophy (same definitions and FP64 sums as
+ *          dns_diagnostics), then the number of non-finite modes
+ *   stream cudaStream_t the two kernels are enqueued on (NULL = legacy default)
+ *
+ * Asynchronous: returns after enqueueing; read `out` after synchronising.
+ * Partial sums go to a fixed 32 KB array inside the library that every GPU
+ * loading the library holds until exit; every call overwrites all of it before
+ * reading it. Calls that overlap on the GPU (e.g. on two streams at once) share
+ * that array and race: serialise them. The first call on each device looks up
+ * the array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture. Calls no cudaMalloc, cudaFree or other allocating
+ * routine. */
+int dns_spectral_sums_noalloc(const void* uhat, int N, int dtype, double nu, double* out, void* stream);
+
 /* Test hook for allocation-failure handling: the n-th device allocation made
  * by the library from now on (n >= 1) reports DNS_ERR_OOM without touching
  * the device; n = 0 disables the hook. */

@@ -57,6 +57,7 @@ SIGNATURES = {
     "dns_device_bytes": (ctypes.c_size_t, [_P]),
     "dns_last_error": (ctypes.c_char_p, [_P]),
     "dns_debug_fail_alloc_after": (_I, [_I]),
+    "dns_spectral_sums_noalloc": (_I, [_P, _I, _I, _D, _P, _P]),
 }
 
 _lib = None

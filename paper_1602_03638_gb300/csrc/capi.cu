@@ -143,6 +143,11 @@ void twiddle(long t, long N, double* re, double* im) {
 
 }  // namespace
 
+namespace dns {
+// Lets other translation units of the library report through dns_last_error().
+void set_error_message(const char* msg) { g_err = msg; }
+}  // namespace dns
+
 struct dns_handle {
   int N = 0;
   int dtype = 0;
