@@ -3,12 +3,15 @@
 //
 // The 3D transforms of Eqs. fft/ifft (Sec. 2) are compositions of 1D
 // transforms along z (real), y and x (complex). Every 1D transform here is a
-// forward DFT  X_k = sum_j x_j exp(-2 pi i j k / L)  computed by a mixed-radix
-// (16/8/4/2 and 3) Stockham autosort: natural order in and out, one pass per
-// radix, each thread holding one radix-R butterfly in registers per pass.
-// Inverse transforms use conj(DFT(conj(x))), folded into the callers' loads
-// and stores. Twiddles come from a table of exp(-2 pi i t / TWN), t < TWN,
-// generated on the host in FP64 (rounded to T for the FP32 form).
+// forward DFT  X_k = sum_j x_j exp(-2 pi i j k / L)  computed by one warp with
+// a mixed-radix (8, then 16/4/2, then 3) Stockham autosort: natural order in
+// and out, one pass per radix, each lane holding its butterflies in registers
+// and exchanging through a shared-memory line between passes (warp barriers
+// only). The first pass may read and the last pass may write global memory
+// directly. Inverse transforms use conj(DFT(conj(x))), folded into the
+// callers' loads and stores. Twiddles come from a table of
+// exp(-2 pi i t / TWN), t < TWN, generated on the host in FP64 (rounded to T
+// for the FP32 form).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -140,30 +143,60 @@ __device__ __forceinline__ void dft(cx<T>* v) {
   else static_assert(R == 2, "unsupported radix");
 }
 
+// Powers w^1..w^(R-1) of one twiddle w = exp(-2 pi i k / (NS R)) loaded from the
+// FP64-generated table: one table load per butterfly instead of R-1 scattered
+// loads, the rest formed by a multiplication tree at most 4 products deep
+// (FP32 form; the FP64 form loads every power).
+template <int R, typename T>
+__device__ __forceinline__ void twiddle_powers(cx<T> w1, cx<T>* w) {
+  w[1] = w1;
+  if constexpr (R > 2) w[2] = cmul(w1, w1);
+  if constexpr (R > 3) w[3] = cmul(w[2], w1);
+  if constexpr (R > 4) {
+    w[4] = cmul(w[2], w[2]);
+    w[5] = cmul(w[4], w1);
+    w[6] = cmul(w[3], w[3]);
+    w[7] = cmul(w[4], w[3]);
+  }
+  if constexpr (R > 8) {
+    w[8] = cmul(w[4], w[4]);
+#pragma unroll
+    for (int r = 9; r < R; ++r) w[r] = cmul(w[8], w[r - 8]);
+  }
+}
+
 // ---------------------------------------------------------------------------
-// Radix schedule for a length L = 2^a * 3^b (b <= 1): the power-of-two part is
-// split into ceil(a/4) passes of radix <= 16, as evenly as possible (larger
-// radices first); a radix-3 pass comes last.
+// Shared-memory line layout: element p sits at padded position p + p/16. With
+// this padding both the contiguous accesses (j + r*L/R over lanes j) and the
+// stride-R Stockham stores of every pass used here touch each bank pair at
+// most twice per warp (the minimum for 8-byte words).
 // ---------------------------------------------------------------------------
+__host__ __device__ constexpr int padp(int p) { return p + (p >> 4); }
+__host__ __device__ constexpr int padded_len(int L) { return L + L / 16 + 1; }
+
 constexpr int ilog2c(int x) {
   int r = 0;
   while (x > 1) { x >>= 1; ++r; }
   return r;
 }
 
+// Radix schedule of the warp FFT for L = 2^a or 3 * 2^a: radix-8 passes, the
+// remaining factor 2 or 4 as one radix-16 or radix-4 pass, then radix 3.
 template <int L>
-struct FFTPlan {
+struct WarpPlan {
   static constexpr int three = (L % 3 == 0) ? 1 : 0;
   static constexpr int p2 = three ? L / 3 : L;
   static constexpr int a = ilog2c(p2);
-  static constexpr int np2 = (a + 3) / 4;
-  static constexpr int npass = np2 + three;
   static_assert((1 << a) == p2 && (p2 % 3) != 0, "FFT length must be 2^a or 3*2^a");
+  static constexpr int n8 = a / 3, rem = a % 3;
+  // list of power-of-two radices
+  static constexpr int np2 = (rem == 0) ? n8 : (rem == 1 ? (n8 >= 1 ? n8 : 1) : n8 + 1);
+  static constexpr int npass = np2 + three;
   static constexpr int radix(int p) {
     if (p >= np2) return 3;
-    int rem = a;
-    for (int q = 0; q < p; ++q) rem -= (rem + (np2 - q) - 1) / (np2 - q);
-    return 1 << ((rem + (np2 - p) - 1) / (np2 - p));
+    if (rem == 0) return 8;
+    if (rem == 1) return (n8 == 0) ? 2 : (p == np2 - 1 ? 16 : 8);
+    return p == np2 - 1 ? 4 : 8;
   }
   static constexpr int ns(int p) {
     int r = 1;
@@ -172,65 +205,243 @@ struct FFTPlan {
   }
 };
 
-// One Stockham pass over NL lines (runtime count nl <= NL) of length L held in
-// shared memory; element j of line l sits at s[j * LD + l]. Butterflies are
-// assigned line-fastest so that neighbouring threads touch neighbouring words.
-// All reads of a pass finish (barrier) before any thread writes.
-template <typename T, int L, int NL, int THREADS, int LD, int TWN, int P>
-__device__ __forceinline__ void fft_pass(cx<T>* __restrict__ s, int nl, const cx<T>* __restrict__ tw) {
-  using PL = FFTPlan<L>;
+template <int L>
+struct IsPow2 {
+  static constexpr bool value = L > 0 && (L & (L - 1)) == 0;
+};
+
+// Access policies for the warp FFT. at(p) gives the address of position p;
+// for power-of-two plans every pass touches positions base + d with
+// padp(base + d) = padp(base) + padp(d), so off(d) is a compile-time offset.
+template <typename T, int ES>
+struct SLine {  // a line in shared memory at padded positions, element stride ES
+  cx<T>* s;
+  __device__ __forceinline__ cx<T>* at(int p) const { return s + padp(p) * ES; }
+  static constexpr int off(int d) { return padp(d) * ES; }
+  __device__ __forceinline__ cx<T> load(const cx<T>* q) const { return *q; }
+  __device__ __forceinline__ void store(cx<T>* q, int, cx<T> v) const { *q = v; }
+};
+template <typename T, bool CONJ>
+struct GLoad {  // contiguous line in global memory
+  const cx<T>* g;
+  __device__ __forceinline__ const cx<T>* at(int p) const { return g + p; }
+  static constexpr int off(int d) { return d; }
+  __device__ __forceinline__ cx<T> load(const cx<T>* q) const {
+    const cx<T> v = *q;
+    return CONJ ? conjg(v) : v;
+  }
+};
+template <typename T, bool CONJ>
+struct GStore {
+  cx<T>* g;
+  __device__ __forceinline__ cx<T>* at(int p) const { return g + p; }
+  static constexpr int off(int d) { return d; }
+  __device__ __forceinline__ void store(cx<T>* q, int, cx<T> v) const { *q = CONJ ? conjg(v) : v; }
+};
+
+template <typename T, int L, int TWN, int P, class Src, class Work, class Dst>
+__device__ __forceinline__ void warp_fft_pass(const Src& src, const Work& work, const Dst& dst,
+                                              const cx<T>* __restrict__ tw, int lane) {
+  using PL = WarpPlan<L>;
   constexpr int R = PL::radix(P);
   constexpr int NS = PL::ns(P);
-  constexpr int NB = NL * (L / R);
-  constexpr int BPT = (NB + THREADS - 1) / THREADS;
-  cx<T> v[BPT][R];
+  constexpr int NB = L / R;
+  constexpr int BPL = (NB + 31) / 32;
+  constexpr bool FIRST = (P == 0);
+  constexpr bool LAST = (P + 1 == PL::npass);
+  constexpr bool FAST = IsPow2<L>::value;
+  constexpr int TWC = TWN / (NS * R);
+  cx<T> v[BPL][R];
 #pragma unroll
-  for (int i = 0; i < BPT; ++i) {
-    const int b = threadIdx.x + i * THREADS;
-    const int l = b % NL, j = b / NL;
-    if ((NB % THREADS == 0 || b < NB) && l < nl) {
+  for (int b = 0; b < BPL; ++b) {
+    const int j = lane + 32 * b;
+    if (NB % 32 == 0 || j < NB) {
+      if constexpr (FIRST) {
+        if constexpr (FAST) {
+          const auto q = src.at(j);
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[i][r] = s[(j + r * (L / R)) * LD + l];
-      if constexpr (NS > 1) {
-        const int k = j % NS;
+          for (int r = 0; r < R; ++r) v[b][r] = src.load(q + Src::off(r * NB));
+        } else {
 #pragma unroll
-        for (int r = 1; r < R; ++r) v[i][r] = cmul(v[i][r], ldro(tw + k * r * (TWN / (NS * R))));
+          for (int r = 0; r < R; ++r) v[b][r] = src.load(src.at(j + r * NB));
+        }
+      } else {
+        if constexpr (FAST) {
+          const auto q = work.at(j);
+#pragma unroll
+          for (int r = 0; r < R; ++r) v[b][r] = work.load(q + Work::off(r * NB));
+        } else {
+#pragma unroll
+          for (int r = 0; r < R; ++r) v[b][r] = work.load(work.at(j + r * NB));
+        }
       }
-      dft<R>(v[i]);
+      if constexpr (NS > 1) {
+        if constexpr (sizeof(T) == 4) {
+          cx<T> w[R];
+          twiddle_powers<R>(ldro(tw + (j % NS) * TWC), w);
+#pragma unroll
+          for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], w[r]);
+        } else {  // FP64 multiplies are scarcer than loads: read every power
+          const int kc = (j % NS) * TWC;
+#pragma unroll
+          for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], ldro(tw + r * kc));
+        }
+      }
+      dft<R>(v[b]);
     }
   }
-  __syncthreads();
+  __syncwarp();
 #pragma unroll
-  for (int i = 0; i < BPT; ++i) {
-    const int b = threadIdx.x + i * THREADS;
-    const int l = b % NL, j = b / NL;
-    if ((NB % THREADS == 0 || b < NB) && l < nl) {
+  for (int b = 0; b < BPL; ++b) {
+    const int j = lane + 32 * b;
+    if (NB % 32 == 0 || j < NB) {
       const int base = (j / NS) * NS * R + (j % NS);
+      if constexpr (LAST) {
+        if constexpr (FAST) {
+          const auto q = dst.at(base);
 #pragma unroll
-      for (int r = 0; r < R; ++r) s[(base + r * NS) * LD + l] = v[i][r];
+          for (int r = 0; r < R; ++r) dst.store(q + Dst::off(r * NS), base + r * NS, v[b][r]);
+        } else {
+#pragma unroll
+          for (int r = 0; r < R; ++r) dst.store(dst.at(base + r * NS), base + r * NS, v[b][r]);
+        }
+      } else {
+        if constexpr (FAST) {
+          const auto q = work.at(base);
+#pragma unroll
+          for (int r = 0; r < R; ++r) work.store(q + Work::off(r * NS), base + r * NS, v[b][r]);
+        } else {
+#pragma unroll
+          for (int r = 0; r < R; ++r) work.store(work.at(base + r * NS), base + r * NS, v[b][r]);
+        }
+      }
     }
   }
-  __syncthreads();
-  if constexpr (P + 1 < PL::npass) fft_pass<T, L, NL, THREADS, LD, TWN, P + 1>(s, nl, tw);
+  __syncwarp();
+  if constexpr (!LAST) warp_fft_pass<T, L, TWN, P + 1>(src, work, dst, tw, lane);
 }
 
-// Forward DFT of `lines` lines (elements at s[j*LD + l]), processed in chunks
-// of at most CH lines so that each thread holds a bounded number of values.
-// Caller must have synchronised after filling s; returns synchronised.
-template <typename T, int L, int THREADS, int LD, int TWN, int CH>
-__device__ __forceinline__ void fft_lines(cx<T>* __restrict__ s, int lines, const cx<T>* __restrict__ tw) {
-  for (int l0 = 0; l0 < lines; l0 += CH) {
-    const int nl = (lines - l0) < CH ? (lines - l0) : CH;
-    fft_pass<T, L, CH, THREADS, LD, TWN, 0>(s + l0, nl, tw);
+// Forward DFT of one line of length L by one warp: reads through `src`, uses
+// the shared-memory line `work` between passes, writes through `dst` (which may
+// alias `work` or `src`: every pass reads all its values before writing).
+template <typename T, int L, int TWN, class Src, class Work, class Dst>
+__device__ __forceinline__ void warp_fft(const Src& src, const Work& work, const Dst& dst,
+                                         const cx<T>* __restrict__ tw, int lane) {
+  warp_fft_pass<T, L, TWN, 0>(src, work, dst, tw, lane);
+}
+
+// ---------------------------------------------------------------------------
+// Register-resident warp FFT ("canonical" layout): lane l holds positions
+// l + 32 m, m < L/32, in v[m]. Every pass reads its butterfly inputs from the
+// lane's own registers (positions j + r L/R with j = l + 32 b); the Stockham
+// outputs go through the shared-memory line `ln` (padded positions, element
+// stride es) and are read back canonically; the last pass's outputs are
+// already canonical and stay in registers. Needs L/R >= 32 in every pass.
+// ---------------------------------------------------------------------------
+template <int L>
+struct CanonPlan {
+  static constexpr int npass = (L == 128) ? 4 : WarpPlan<L>::npass;
+  static constexpr int radix(int p) { return (L == 128) ? (p < 3 ? 4 : 2) : WarpPlan<L>::radix(p); }
+  static constexpr int ns(int p) {
+    int r = 1;
+    for (int q = 0; q < p; ++q) r *= radix(q);
+    return r;
+  }
+  static constexpr bool valid() {
+    if (L % 32) return false;
+    for (int p = 0; p < npass; ++p)
+      if ((L / radix(p)) % 32) return false;
+    return true;
+  }
+};
+
+// Per-lane twiddle bases of the canonical FFT, loaded once per kernel: for
+// every pass P >= 1 and butterfly slot b, w1 = exp(-2 pi i ((l + 32 b) mod NS) / (NS R)).
+template <typename T, int L, int TWN>
+struct CanonTw {
+  using PL = CanonPlan<L>;
+  static constexpr int off(int P) {
+    int o = 0;
+    for (int q = 1; q < P; ++q) o += (L / PL::radix(q)) / 32;
+    return o;
+  }
+  static constexpr int count() { return off(PL::npass) > 0 ? off(PL::npass) : 1; }
+  cx<T> w[count()];
+  __device__ __forceinline__ void load(const cx<T>* __restrict__ tw, int lane) {
+    load_pass<1>(tw, lane);
+  }
+  template <int P>
+  __device__ __forceinline__ void load_pass(const cx<T>* __restrict__ tw, int lane) {
+    if constexpr (P < PL::npass) {
+      constexpr int R = PL::radix(P), NS = PL::ns(P), BPL = (L / R) / 32, TWC = TWN / (NS * R);
+#pragma unroll
+      for (int b = 0; b < BPL; ++b) w[off(P) + b] = ldro(tw + ((lane + 32 * b) % NS) * TWC);
+      load_pass<P + 1>(tw, lane);
+    }
+  }
+};
+
+template <typename T, int L, int TWN, int ES, int P>
+__device__ __forceinline__ void warp_fft_canon_pass(cx<T> (&v)[L / 32], cx<T>* ln, const CanonTw<T, L, TWN>& ctw,
+                                                    const cx<T>* __restrict__ tw, int lane) {
+  using PL = CanonPlan<L>;
+  constexpr int R = PL::radix(P);
+  constexpr int NS = PL::ns(P);
+  constexpr int NB = L / R;
+  constexpr int BPL = NB / 32;
+  constexpr bool LAST = (P + 1 == PL::npass);
+  constexpr int TWC = TWN / (NS * R);
+  static_assert(NB % 32 == 0, "canonical warp FFT needs L/R >= 32");
+  static_assert(IsPow2<L>::value, "canonical warp FFT needs a power-of-two length");
+  cx<T> u[BPL][R];
+#pragma unroll
+  for (int b = 0; b < BPL; ++b) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) u[b][r] = v[b + r * BPL];
+    if constexpr (NS > 1) {
+      if constexpr (sizeof(T) == 4) {
+        cx<T> w[R];
+        twiddle_powers<R>(ctw.w[CanonTw<T, L, TWN>::off(P) + b], w);
+#pragma unroll
+        for (int r = 1; r < R; ++r) u[b][r] = cmul(u[b][r], w[r]);
+      } else {
+        const int kc = ((lane + 32 * b) % NS) * TWC;
+#pragma unroll
+        for (int r = 1; r < R; ++r) u[b][r] = cmul(u[b][r], ldro(tw + r * kc));
+      }
+    }
+    dft<R>(u[b]);
+  }
+  if constexpr (LAST) {
+    // outputs j + r NS with NS = NB: canonical index b + r BPL
+#pragma unroll
+    for (int b = 0; b < BPL; ++b)
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[b + r * BPL] = u[b][r];
+  } else {
+#pragma unroll
+    for (int b = 0; b < BPL; ++b) {
+      const int j = lane + 32 * b;
+      cx<T>* q = ln + padp((j / NS) * NS * R + (j % NS)) * ES;
+#pragma unroll
+      for (int r = 0; r < R; ++r) q[padp(r * NS) * ES] = u[b][r];
+    }
+    __syncwarp();
+    const cx<T>* rb = ln + padp(lane) * ES;
+#pragma unroll
+    for (int m = 0; m < L / 32; ++m) v[m] = rb[34 * m * ES];
+    __syncwarp();
+    warp_fft_canon_pass<T, L, TWN, ES, P + 1>(v, ln, ctw, tw, lane);
   }
 }
 
-// Lines per chunk so that each thread holds about 16 complex values per pass.
-template <int L, int THREADS, int LINES>
-struct ChunkLines {
-  static constexpr int raw = (16 * THREADS) / L;
-  static constexpr int c1 = raw < 1 ? 1 : raw;
-  static constexpr int value = c1 > LINES ? LINES : c1;
-};
+// Forward DFT of the canonical register array v (length L) by one warp, using
+// the shared-memory line ln (L padded positions, element stride ES) for the
+// exchanges. The caller must have finished reading ln (and __syncwarp'ed).
+template <typename T, int L, int TWN, int ES>
+__device__ __forceinline__ void warp_fft_canon(cx<T> (&v)[L / 32], cx<T>* ln, const CanonTw<T, L, TWN>& ctw,
+                                               const cx<T>* __restrict__ tw, int lane) {
+  warp_fft_canon_pass<T, L, TWN, ES, 0>(v, ln, ctw, tw, lane);
+}
 
 }  // namespace dns

@@ -22,23 +22,17 @@
 
 namespace dns {
 
-constexpr int XP_THREADS = 256;
+constexpr int XP_THREADS = 192;  // 6 warps: one per line of a row (u, omega)
 constexpr int YP_THREADS = 256;
 constexpr int ZP_THREADS = 256;
 constexpr int DG_THREADS = 256;
 
-constexpr int pow2_floor(int x) {
-  int r = 1;
-  while (r * 2 <= x) r *= 2;
-  return r;
-}
 constexpr int pow2_part(int n) {
   int r = 1;
   while (n % (r * 2) == 0) r *= 2;
   return r;
 }
 constexpr int cmin(int a, int b) { return a < b ? a : b; }
-constexpr int cmax(int a, int b) { return a > b ? a : b; }
 constexpr int odd_ld(int lines) { return (lines % 2) ? lines : lines + 1; }
 
 template <typename T, int N>
@@ -46,24 +40,30 @@ struct Geometry {
   static constexpr int M = N / 2;
   static constexpr size_t FS = (size_t)M * N * N;  // complex values per field
   static constexpr int CB = (int)sizeof(cx<T>);
-  // x-pass: XROWS rows (fixed kz, consecutive ky) per block, <= ~64 KB smem.
-  static constexpr int XROWS = cmin(cmin(pow2_floor(cmax(1, (64 * 1024) / (6 * N * CB))), 16), pow2_part(N));
-  static constexpr int XLD = odd_ld(6 * XROWS);
-  static constexpr size_t XSMEM = (size_t)N * XLD * CB;
-  // y-pass: YTX adjacent columns (128-byte rows).
-  static constexpr int YTX = cmin(128 / CB, pow2_part(N));
+  // x-pass: one row (fixed kz, ky) per block, 6 padded line buffers.
+  static constexpr int XLS = padded_len(N);
+  static constexpr size_t XSMEM = (size_t)6 * XLS * CB;
+  // y-pass: YTX adjacent columns (128-byte rows up to N = 512, 64-byte at 1024).
+  static constexpr int YTX = cmin((N <= 512 ? 128 : 64) / CB, pow2_part(N));
   static constexpr int YLD = odd_ld(YTX);
-  static constexpr size_t YSMEM = (size_t)N * YLD * CB;
-  // z-pass: ZTX adjacent x at fixed y, 6 fields of M values each, <= ~112 KB.
-  static constexpr int zfit(int t) { return (size_t)M * odd_ld(6 * t) * CB <= 112 * 1024 ? 1 : 0; }
+  static constexpr size_t YSMEM = (size_t)padded_len(N) * YLD * CB;
+  // z-pass: ZTX adjacent x at fixed y, 6 fields of M values each, <= 112 KB
+  // (two blocks per SM); rows narrower than one 32-byte sector may use up to 200 KB.
+  static constexpr size_t zbytes(int t) { return (size_t)padded_len(M) * odd_ld(6 * t) * CB; }
   static constexpr int ztx() {
     int t = cmin(16, pow2_part(N));
-    while (t > 1 && !zfit(t)) t /= 2;
+    while (t > 1 && zbytes(t) > 112 * 1024 && !(t * CB <= 32 && zbytes(t) <= 200 * 1024)) t /= 2;
     return t;
   }
   static constexpr int ZTX = ztx();
+  // Minimum resident blocks per SM for the register cap: lines longer than 4 KB
+  // hold 32+ registers of data per lane in the warp FFT, so allow more registers.
+  static constexpr int LINE_BYTES = N * CB;
+  static constexpr int XMIN = LINE_BYTES > 4096 ? 2 : 4;
+  static constexpr int YMIN = 2;  // blocks of 32*YTX threads
+  static constexpr int ZMIN = (M * CB > 4096) ? 1 : 2;
   static constexpr int ZLD = odd_ld(6 * ZTX);
-  static constexpr size_t ZSMEM = (size_t)M * ZLD * CB;
+  static constexpr size_t ZSMEM = zbytes(ZTX);
 };
 
 __device__ __forceinline__ int kfreq(int i, int N) { return i < N / 2 ? i : i - N; }
@@ -72,35 +72,48 @@ __device__ __forceinline__ bool kept(int k, int kmax3) { return 3 * (k < 0 ? -k 
 enum XMode { XM_INV_CURL = 0, XM_STAGE = 1, XM_RHS = 2, XM_FWD_STORE = 3, XM_INV_PLAIN = 4, XM_INV_DIV = 5 };
 enum ZMode { ZM_CROSS = 0, ZM_STORE = 1, ZM_LOAD = 2, ZM_MAXABS = 3 };
 
-// Writes conj(u/N^3) and conj(i k x u / N^3) into the 6 lines of one mode
-// (conjugated because the following x transform is an inverse one).
-template <typename T, int R, int LD>
-__device__ __forceinline__ void put_curl_lines(cx<T>* s, int j, int q, cx<T> u0, cx<T> u1, cx<T> u2,
-                                               T kx, T ky, T kz, T sc) {
+// Writes conj(u/N^3) and conj(i k x u / N^3) of one mode into the 6 line
+// buffers (stride LS) at padded position pos (conjugated because the following
+// x transform is an inverse one).
+template <typename T>
+__device__ __forceinline__ void put_curl_lines(cx<T>* s, int pos, int LS, cx<T> u0, cx<T> u1, cx<T> u2, T kx, T ky,
+                                               T kz, T sc) {
   u0 = scal(u0, sc);
   u1 = scal(u1, sc);
   u2 = scal(u2, sc);
   // omega_hat = i k x u_hat
-  cx<T> w0 = mul_pi(mk(ky * u2.x - kz * u1.x, ky * u2.y - kz * u1.y));
-  cx<T> w1 = mul_pi(mk(kz * u0.x - kx * u2.x, kz * u0.y - kx * u2.y));
-  cx<T> w2 = mul_pi(mk(kx * u1.x - ky * u0.x, kx * u1.y - ky * u0.y));
-  cx<T>* p = s + j * LD + q;
-  p[0 * R] = conjg(u0);
-  p[1 * R] = conjg(u1);
-  p[2 * R] = conjg(u2);
-  p[3 * R] = conjg(w0);
-  p[4 * R] = conjg(w1);
-  p[5 * R] = conjg(w2);
+  const cx<T> w0 = mul_pi(mk(ky * u2.x - kz * u1.x, ky * u2.y - kz * u1.y));
+  const cx<T> w1 = mul_pi(mk(kz * u0.x - kx * u2.x, kz * u0.y - kx * u2.y));
+  const cx<T> w2 = mul_pi(mk(kx * u1.x - ky * u0.x, kx * u1.y - ky * u0.y));
+  cx<T>* p = s + pos;
+  p[0 * LS] = conjg(u0);
+  p[1 * LS] = conjg(u1);
+  p[2 * LS] = conjg(u2);
+  p[3 * LS] = conjg(w0);
+  p[4 * LS] = conjg(w1);
+  p[5 * LS] = conjg(w2);
 }
 
+// Global store of a forward-transformed state row with the Nyquist modes zeroed.
+template <typename T>
+struct GStoreNyquistFree {
+  cx<T>* g;
+  int N;
+  bool zero_row;
+  __device__ __forceinline__ cx<T>* at(int p) const { return g + p; }
+  static constexpr int off(int d) { return d; }
+  __device__ __forceinline__ void store(cx<T>* q, int p, cx<T> v) const {
+    *q = (zero_row || p == N / 2) ? mk((T)0, (T)0) : v;
+  }
+};
+
 // ---------------------------------------------------------------------------
-// x-pass: one block owns XROWS rows (kz fixed, consecutive ky) of length N.
+// x-pass: one block owns one row (kz, ky) of length N; warp f transforms line f.
 // ---------------------------------------------------------------------------
 template <typename T, int N, int MODE>
-__global__ void __launch_bounds__(XP_THREADS) k_xpass(PassArgs a) {
+__global__ void __launch_bounds__(XP_THREADS, (Geometry<T, N>::XMIN)) k_xpass(PassArgs a) {
   using G = Geometry<T, N>;
-  constexpr int R = G::XROWS;
-  constexpr int LD = G::XLD;
+  constexpr int LS = G::XLS;
   constexpr size_t FS = G::FS;
   extern __shared__ unsigned char smraw[];
   cx<T>* s = reinterpret_cast<cx<T>*>(smraw);
@@ -109,43 +122,39 @@ __global__ void __launch_bounds__(XP_THREADS) k_xpass(PassArgs a) {
   cx<T>* U1 = reinterpret_cast<cx<T>*>(a.U1);
   cx<T>* US = reinterpret_cast<cx<T>*>(a.US);
   cx<T>* W = reinterpret_cast<cx<T>*>(a.W);
-  const int row0 = blockIdx.x * R;  // row r = kz * N + ky
-  const int kz = row0 / N;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x;  // row = kz * N + ky
+  const int kz = row / N, ky = row % N;
+  const size_t rb = (size_t)row * N;
   const T sc = (T)(1.0 / ((double)N * (double)N * (double)N));
-  const T kzv = (T)kz;
+  const T kzv = (T)kz, kyv = (T)kfreq(ky, N);
 
   if constexpr (MODE == XM_STAGE || MODE == XM_RHS) {
-    const bool kz_kept = 3 * kz < a.kmax3;
-    if (kz_kept) {
-      for (int e = threadIdx.x; e < 3 * R * N; e += XP_THREADS) {
-        const int j = e % N, cq = e / N, q = cq % R, c = cq / R;
-        const int ky = (row0 + q) % N;
-        cx<T> v = mk((T)0, (T)0);
-        if (kept(kfreq(ky, N), a.kmax3)) v = W[c * FS + (size_t)(row0 + q) * N + j];
-        s[j * LD + c * R + q] = v;
-      }
-      __syncthreads();
-      fft_lines<T, N, XP_THREADS, LD, N, ChunkLines<N, XP_THREADS, 3 * R>::value>(s, 3 * R, tw);
+    // rows outside the 2/3 box carry no nonlinear term: skip their transform
+    const bool row_kept = (3 * kz < a.kmax3) && kept(kfreq(ky, N), a.kmax3);
+    if (row_kept && warp < 3) {
+      const SLine<T, 1> line{s + warp * LS};
+      warp_fft<T, N, N>(GLoad<T, false>{W + warp * FS + rb}, line, line, tw, lane);
     }
+    __syncthreads();
     const T nu = (T)a.nu, cA = (T)a.cA, cB = (T)a.cB;
     const int stage = a.stage;
     const cx<T>* Sst = (stage == 0) ? U : US;
-    for (int e = threadIdx.x; e < R * N; e += XP_THREADS) {
-      const int j = e % N, q = e / N;
-      const int r = row0 + q, ky = r % N;
-      const int kxi = kfreq(j, N), kyi = kfreq(ky, N);
-      const T kx = (T)kxi, kyv = (T)kyi;
+    for (int j = threadIdx.x; j < N; j += XP_THREADS) {
+      const int kxi = kfreq(j, N);
+      const T kx = (T)kxi;
+      const int pj = padp(j);
       cx<T> n0 = mk((T)0, (T)0), n1 = n0, n2 = n0;
-      if (kz_kept && kept(kxi, a.kmax3) && kept(kyi, a.kmax3)) {
-        n0 = s[j * LD + 0 * R + q];
-        n1 = s[j * LD + 1 * R + q];
-        n2 = s[j * LD + 2 * R + q];
+      if (row_kept && kept(kxi, a.kmax3)) {
+        n0 = s[0 * LS + pj];
+        n1 = s[1 * LS + pj];
+        n2 = s[2 * LS + pj];
       }
       const T k2 = kx * kx + kyv * kyv + kzv * kzv;
       const T ik2 = k2 > (T)0 ? (T)1 / k2 : (T)0;
       // P = (k . N_hat) / |k|^2   (Eq. mod_pressure without the factor i)
       const cx<T> p = mk((kx * n0.x + kyv * n1.x + kzv * n2.x) * ik2, (kx * n0.y + kyv * n1.y + kzv * n2.y) * ik2);
-      const size_t gi = (size_t)r * N + j;
+      const size_t gi = rb + j;
       const cx<T> u0 = Sst[gi], u1 = Sst[FS + gi], u2 = Sst[2 * FS + gi];
       const T nk2 = nu * k2;
       // dU = N_hat - k P - nu |k|^2 u_hat   (Eq. NSfinal)
@@ -188,86 +197,84 @@ __global__ void __launch_bounds__(XP_THREADS) k_xpass(PassArgs a) {
           U[FS + gi] = v1;
           U[2 * FS + gi] = v2;
         }
-        put_curl_lines<T, R, LD>(s, j, q, v0, v1, v2, kx, kyv, kzv, sc);
+        put_curl_lines<T>(s, pj, LS, v0, v1, v2, kx, kyv, kzv, sc);
       }
     }
     if constexpr (MODE == XM_STAGE) {
       __syncthreads();
-      fft_lines<T, N, XP_THREADS, LD, N, ChunkLines<N, XP_THREADS, 6 * R>::value>(s, 6 * R, tw);
-      for (int e = threadIdx.x; e < 6 * R * N; e += XP_THREADS) {
-        const int j = e % N, fq = e / N, q = fq % R, f = fq / R;
-        W[f * FS + (size_t)(row0 + q) * N + j] = conjg(s[j * LD + f * R + q]);
-      }
+      const SLine<T, 1> line{s + warp * LS};
+      warp_fft<T, N, N>(line, line, GStore<T, true>{W + warp * FS + rb}, tw, lane);
     }
   } else if constexpr (MODE == XM_FWD_STORE) {
-    for (int e = threadIdx.x; e < 3 * R * N; e += XP_THREADS) {
-      const int j = e % N, cq = e / N, q = cq % R, c = cq / R;
-      s[j * LD + c * R + q] = U[c * FS + (size_t)(row0 + q) * N + j];
-    }
-    __syncthreads();
-    fft_lines<T, N, XP_THREADS, LD, N, ChunkLines<N, XP_THREADS, 3 * R>::value>(s, 3 * R, tw);
-    for (int e = threadIdx.x; e < 3 * R * N; e += XP_THREADS) {
-      const int j = e % N, cq = e / N, q = cq % R, c = cq / R;
-      const int ky = (row0 + q) % N;
-      cx<T> v = s[j * LD + c * R + q];
-      if (j == N / 2 || ky == N / 2) v = mk((T)0, (T)0);  // Nyquist modes are not part of the state
-      U[c * FS + (size_t)(row0 + q) * N + j] = v;
+    if (warp < 3) {
+      const SLine<T, 1> line{s + warp * LS};
+      warp_fft<T, N, N>(GLoad<T, false>{U + warp * FS + rb}, line,
+                        GStoreNyquistFree<T>{U + warp * FS + rb, N, ky == N / 2}, tw, lane);
     }
   } else {
     // inverse x transform of u and omega (XM_INV_CURL), of u alone
     // (XM_INV_PLAIN) or of i k . u (XM_INV_DIV), all scaled by 1/N^3
     constexpr int NF = (MODE == XM_INV_CURL) ? 6 : (MODE == XM_INV_PLAIN ? 3 : 1);
-    for (int e = threadIdx.x; e < R * N; e += XP_THREADS) {
-      const int j = e % N, q = e / N;
-      const int r = row0 + q, ky = r % N;
-      const size_t gi = (size_t)r * N + j;
+    for (int j = threadIdx.x; j < N; j += XP_THREADS) {
+      const size_t gi = rb + j;
+      const int pj = padp(j);
       const cx<T> u0 = U[gi], u1 = U[FS + gi], u2 = U[2 * FS + gi];
-      const T kx = (T)kfreq(j, N), kyv = (T)kfreq(ky, N);
+      const T kx = (T)kfreq(j, N);
       if constexpr (MODE == XM_INV_CURL) {
-        put_curl_lines<T, R, LD>(s, j, q, u0, u1, u2, kx, kyv, kzv, sc);
+        put_curl_lines<T>(s, pj, LS, u0, u1, u2, kx, kyv, kzv, sc);
       } else if constexpr (MODE == XM_INV_PLAIN) {
-        s[j * LD + 0 * R + q] = conjg(scal(u0, sc));
-        s[j * LD + 1 * R + q] = conjg(scal(u1, sc));
-        s[j * LD + 2 * R + q] = conjg(scal(u2, sc));
+        s[0 * LS + pj] = conjg(scal(u0, sc));
+        s[1 * LS + pj] = conjg(scal(u1, sc));
+        s[2 * LS + pj] = conjg(scal(u2, sc));
       } else {
         const cx<T> d = mul_pi(mk(kx * u0.x + kyv * u1.x + kzv * u2.x, kx * u0.y + kyv * u1.y + kzv * u2.y));
-        s[j * LD + q] = conjg(scal(d, sc));
+        s[pj] = conjg(scal(d, sc));
       }
     }
     __syncthreads();
-    fft_lines<T, N, XP_THREADS, LD, N, ChunkLines<N, XP_THREADS, NF * R>::value>(s, NF * R, tw);
     cx<T>* dst = (MODE == XM_INV_DIV) ? reinterpret_cast<cx<T>*>(a.D) : W;
-    for (int e = threadIdx.x; e < NF * R * N; e += XP_THREADS) {
-      const int j = e % N, fq = e / N, q = fq % R, f = fq / R;
-      dst[f * FS + (size_t)(row0 + q) * N + j] = conjg(s[j * LD + f * R + q]);
+    if (warp < NF) {
+      const SLine<T, 1> line{s + warp * LS};
+      warp_fft<T, N, N>(line, line, GStore<T, true>{dst + warp * FS + rb}, tw, lane);
     }
   }
 }
 
 // ---------------------------------------------------------------------------
-// y-pass: one block owns YTX adjacent columns (fixed field and kz) of length N.
+// y-pass: one block owns YTX adjacent columns (fixed field and kz) of length N;
+// the tile is loaded with coalesced rows, each warp transforms whole columns.
 // INV: conj-in/conj-out (inverse DFT). PRUNE: store only rows with |ky| < N/3.
 // grid = (N / YTX, number of kz planes, number of fields)
 // ---------------------------------------------------------------------------
 template <typename T, int N, int INV, int PRUNE>
-__global__ void __launch_bounds__(YP_THREADS) k_ypass(cx<T>* __restrict__ F, const cx<T>* __restrict__ tw, int kmax3) {
+__global__ void __launch_bounds__(32 * Geometry<T, N>::YTX, (Geometry<T, N>::YMIN)) k_ypass(cx<T>* __restrict__ F,
+                                                                                         const cx<T>* __restrict__ tw,
+                                                                                         int kmax3) {
   using G = Geometry<T, N>;
   constexpr int TX = G::YTX;
   constexpr int LD = G::YLD;
+  constexpr int NT = 32 * TX;  // one warp per column
   extern __shared__ unsigned char smraw[];
   cx<T>* s = reinterpret_cast<cx<T>*>(smraw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   cx<T>* base = F + blockIdx.z * G::FS + (size_t)blockIdx.y * N * N + blockIdx.x * TX;
-  for (int e = threadIdx.x; e < TX * N; e += YP_THREADS) {
+#pragma unroll 8
+  for (int e = threadIdx.x; e < TX * N; e += NT) {
     const int x = e % TX, y = e / TX;
     const cx<T> v = base[(size_t)y * N + x];
-    s[y * LD + x] = INV ? conjg(v) : v;
+    s[padp(y) * LD + x] = INV ? conjg(v) : v;
   }
   __syncthreads();
-  fft_lines<T, N, YP_THREADS, LD, N, ChunkLines<N, YP_THREADS, TX>::value>(s, TX, tw);
-  for (int e = threadIdx.x; e < TX * N; e += YP_THREADS) {
+  {
+    const SLine<T, LD> line{s + warp};
+    warp_fft<T, N, N>(line, line, line, tw, lane);
+  }
+  __syncthreads();
+#pragma unroll 8
+  for (int e = threadIdx.x; e < TX * N; e += NT) {
     const int x = e % TX, y = e / TX;
     if (PRUNE && !kept(kfreq(y, N), kmax3)) continue;
-    const cx<T> v = s[y * LD + x];
+    const cx<T> v = s[padp(y) * LD + x];
     base[(size_t)y * N + x] = INV ? conjg(v) : v;
   }
 }
@@ -280,7 +287,7 @@ __global__ void __launch_bounds__(YP_THREADS) k_ypass(cx<T>* __restrict__ F, con
 // kz = N/2 coefficient is zero (it is not stored).
 // ---------------------------------------------------------------------------
 template <typename T, int N, int MODE>
-__global__ void __launch_bounds__(ZP_THREADS) k_zpass(PassArgs a) {
+__global__ void __launch_bounds__(ZP_THREADS, (Geometry<T, N>::ZMIN)) k_zpass(PassArgs a) {
   using G = Geometry<T, N>;
   constexpr int M = G::M;
   constexpr int TX = G::ZTX;
@@ -290,6 +297,7 @@ __global__ void __launch_bounds__(ZP_THREADS) k_zpass(PassArgs a) {
   extern __shared__ unsigned char smraw[];
   cx<T>* s = reinterpret_cast<cx<T>*>(smraw);
   const cx<T>* tw = reinterpret_cast<const cx<T>*>(a.tw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int x0 = blockIdx.x * TX;
   const int y = blockIdx.y;
 
@@ -298,14 +306,14 @@ __global__ void __launch_bounds__(ZP_THREADS) k_zpass(PassArgs a) {
     const cx<T>* in = reinterpret_cast<const cx<T>*>(a.in);
     for (int e = threadIdx.x; e < 3 * TX * M; e += ZP_THREADS) {
       const int n = e % M, x = (e / M) % TX, c = e / (M * TX);
-      s[n * LD + c * TX + x] = in[((size_t)(c * N + x0 + x) * N + y) * M + n];
+      s[padp(n) * LD + c * TX + x] = in[((size_t)(c * N + x0 + x) * N + y) * M + n];
     }
     __syncthreads();
   } else {
     const cx<T>* src = reinterpret_cast<const cx<T>*>(MODE == ZM_MAXABS ? a.D : a.W);
     for (int e = threadIdx.x; e < NF * TX * M; e += ZP_THREADS) {
       const int x = e % TX, k = (e / TX) % M, f = e / (TX * M);
-      s[k * LD + f * TX + x] = src[f * FS + ((size_t)k * N + y) * N + x0 + x];
+      s[padp(k) * LD + f * TX + x] = src[f * FS + ((size_t)k * N + y) * N + x0 + x];
     }
     __syncthreads();
     // c2r pre-processing: Z'_k = (X_k + conj X_{M-k}) + i e^{+2 pi i k/N} (X_k - conj X_{M-k}),
@@ -317,28 +325,33 @@ __global__ void __launch_bounds__(ZP_THREADS) k_zpass(PassArgs a) {
         const T r0 = s[l].x;  // Im X_0 ignored, X_M = 0
         s[l] = mk(r0, -r0);
       } else {
-        const cx<T> xk = s[k * LD + l], xm = s[(M - k) * LD + l];
+        cx<T>* pk = s + padp(k) * LD + l;
+        cx<T>* pm = s + padp(M - k) * LD + l;
+        const cx<T> xk = *pk, xm = *pm;
         const cx<T> wk = ldro(tw + k);  // exp(-2 pi i k / N)
         const cx<T> A = xk + conjg(xm), B = xk - conjg(xm);
-        const cx<T> zk = A + mul_pi(cmul(conjg(wk), B));
-        s[k * LD + l] = conjg(zk);
+        *pk = conjg(A + mul_pi(cmul(conjg(wk), B)));
         if (k != M - k) {
           // partner M-k: e^{+2 pi i (M-k)/N} = -wk
           const cx<T> A2 = xm + conjg(xk), B2 = xm - conjg(xk);
-          const cx<T> zm = A2 - mul_pi(cmul(wk, B2));
-          s[(M - k) * LD + l] = conjg(zm);
+          *pm = conjg(A2 - mul_pi(cmul(wk, B2)));
         }
       }
     }
     __syncthreads();
-    fft_lines<T, M, ZP_THREADS, LD, N, ChunkLines<M, ZP_THREADS, NL>::value>(s, NL, tw);
+#pragma unroll 1
+    for (int l = warp; l < NL; l += ZP_THREADS / 32) {
+      const SLine<T, LD> line{s + l};
+      warp_fft<T, M, N>(line, line, line, tw, lane);
+    }
+    __syncthreads();
     // now conj(s) = x_{2n} + i x_{2n+1} (physical values, unnormalised c2r)
   }
 
   if constexpr (MODE == ZM_CROSS) {
     for (int e = threadIdx.x; e < TX * M; e += ZP_THREADS) {
       const int x = e % TX, n = e / TX;
-      cx<T>* p = s + n * LD + x;
+      cx<T>* p = s + padp(n) * LD + x;
       const cx<T> u0 = conjg(p[0 * TX]), u1 = conjg(p[1 * TX]), u2 = conjg(p[2 * TX]);
       const cx<T> w0 = conjg(p[3 * TX]), w1 = conjg(p[4 * TX]), w2 = conjg(p[5 * TX]);
       // u x omega on both packed points (real and imaginary parts)
@@ -350,7 +363,12 @@ __global__ void __launch_bounds__(ZP_THREADS) k_zpass(PassArgs a) {
   }
 
   if constexpr (MODE == ZM_CROSS || MODE == ZM_LOAD) {
-    fft_lines<T, M, ZP_THREADS, LD, N, ChunkLines<M, ZP_THREADS, 3 * TX>::value>(s, 3 * TX, tw);
+#pragma unroll 1
+    for (int l = warp; l < 3 * TX; l += ZP_THREADS / 32) {
+      const SLine<T, LD> line{s + l};
+      warp_fft<T, M, N>(line, line, line, tw, lane);
+    }
+    __syncthreads();
     // r2c post-processing: X_k = 1/2 [(Z_k + conj Z_{M-k}) - i e^{-2 pi i k/N} (Z_k - conj Z_{M-k})]
     cx<T>* dst = reinterpret_cast<cx<T>*>(MODE == ZM_CROSS ? a.W : a.U);
     int kc = M;
@@ -361,36 +379,345 @@ __global__ void __launch_bounds__(ZP_THREADS) k_zpass(PassArgs a) {
     for (int e = threadIdx.x; e < 3 * TX * kc; e += ZP_THREADS) {
       const int x = e % TX, k = (e / TX) % kc, c = e / (TX * kc);
       const int l = c * TX + x;
-      const cx<T> zk = s[k * LD + l], zm = s[((M - k) % M) * LD + l];
+      const cx<T> zk = s[padp(k) * LD + l], zm = s[padp((M - k) % M) * LD + l];
       const cx<T> wk = ldro(tw + k);
       const cx<T> A = zk + conjg(zm), B = zk - conjg(zm);
-      const cx<T> X = scal(A + mul_mi(cmul(wk, B)), (T)0.5);
-      dst[c * FS + ((size_t)k * N + y) * N + x0 + x] = X;
+      dst[c * FS + ((size_t)k * N + y) * N + x0 + x] = scal(A + mul_mi(cmul(wk, B)), (T)0.5);
     }
   } else if constexpr (MODE == ZM_STORE) {
     cx<T>* out = reinterpret_cast<cx<T>*>(a.out);
     for (int e = threadIdx.x; e < 3 * TX * M; e += ZP_THREADS) {
       const int n = e % M, x = (e / M) % TX, c = e / (M * TX);
-      out[((size_t)(c * N + x0 + x) * N + y) * M + n] = conjg(s[n * LD + c * TX + x]);
+      out[((size_t)(c * N + x0 + x) * N + y) * M + n] = conjg(s[padp(n) * LD + c * TX + x]);
     }
   } else if constexpr (MODE == ZM_MAXABS) {
     double m = 0.0;
     for (int e = threadIdx.x; e < TX * M; e += ZP_THREADS) {
       const int x = e % TX, n = e / TX;
-      const cx<T> v = s[n * LD + x];
-      const double ax = fabs((double)v.x), ay = fabs((double)v.y);
-      m = fmax(m, fmax(ax, ay));
+      const cx<T> v = s[padp(n) * LD + x];
+      m = fmax(m, fmax(fabs((double)v.x), fabs((double)v.y)));
     }
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
     __shared__ double red[ZP_THREADS / 32];
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    if (lane == 0) red[warp] = m;
     __syncthreads();
     if (threadIdx.x == 0) {
       for (int w = 1; w < ZP_THREADS / 32; ++w) m = fmax(m, red[w]);
       // non-negative doubles order like their bit patterns
       atomicMax(a.maxbits, (unsigned long long)__double_as_longlong(m));
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// z-pass of the right-hand side with register-resident columns (M = N/2 a
+// multiple of 32, M >= 128): a block owns ZTX adjacent x at fixed y and has one
+// warp per x. After a coalesced load of the 6 fields, each warp on its own
+// column: c2r of u (pre-processing fused into the first pass; physical values
+// parked in the column's own lines), c2r of omega one component at a time
+// with the cross product accumulated incrementally, r2c of each finished
+// component with the post-processing done through lane shuffles. Only the load
+// and the store need block barriers.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ cx<T> pmul(cx<T> a, cx<T> b) { return mk(a.x * b.x, a.y * b.y); }
+
+template <typename T, int N>
+struct ZCross {
+  static constexpr int M = N / 2;
+  static constexpr int V = M / 32;
+  static constexpr bool enabled = (M % 32 == 0) && (M >= 128) && CanonPlan<M>::valid();
+};
+
+// Twiddles the z-cross warps reuse for every line: the canonical-FFT bases
+// and exp(-2 pi i lane / N); exp(-2 pi i k / N) for k = lane + 32 m is then
+// tl * tw[32 m] (a broadcast load).
+template <typename T, int N>
+struct ZTw {
+  CanonTw<T, N / 2, N> fft;
+  cx<T> tl;
+  __device__ __forceinline__ void load(const cx<T>* __restrict__ tw, int lane) {
+    fft.load(tw, lane);
+    tl = ldro(tw + lane);
+  }
+  __device__ __forceinline__ cx<T> wk(const cx<T>* __restrict__ tw, int m) const {
+    if constexpr (sizeof(T) == 4) return m == 0 ? tl : cmul(tl, ldro(tw + 32 * m));
+    else return ldro(tw + (threadIdx.x & 31) + 32 * m);
+  }
+};
+
+// c2r of one column line (element k at ln[padp(k) * LD]) into canonical
+// physical pairs v[m] = x_{2n} + i x_{2n+1}, n = lane + 32 m. The pre-processing
+// Z'_k = (X_k + conj X_{M-k}) + i e^{+2 pi i k/N} (X_k - conj X_{M-k}) is fused
+// into the load (stored conjugated: a forward DFT then gives the inverse one).
+template <typename T, int N>
+__device__ __forceinline__ void zc_c2r(cx<T> (&v)[N / 64], cx<T>* ln, const ZTw<T, N>& zt,
+                                       const cx<T>* __restrict__ tw, int lane) {
+  using G = Geometry<T, N>;
+  constexpr int M = N / 2, V = M / 32, LD = G::ZLD;
+  const cx<T>* pa = ln + padp(lane) * LD;            // X_k, k = lane + 32 m
+  const cx<T>* pb = ln + padp((32 - lane) & 31) * LD;  // X_{M-k} for lane > 0
+#pragma unroll
+  for (int m = 0; m < V; ++m) {
+    const cx<T> xk = pa[34 * m * LD];
+    cx<T> xm;
+    if (lane != 0) xm = pb[34 * (V - 1 - m) * LD];
+    else xm = (m == 0) ? mk((T)0, (T)0) : ln[34 * (V - m) * LD];
+    cx<T> z;
+    if (lane == 0 && m == 0) {
+      z = mk(xk.x, xk.x);  // Im X_0 ignored, X_M = 0
+    } else {
+      const cx<T> wk = zt.wk(tw, m);
+      const cx<T> A = xk + conjg(xm), B = xk - conjg(xm);
+      z = A + mul_pi(cmul(conjg(wk), B));
+    }
+    v[m] = conjg(z);
+  }
+  __syncwarp();
+  warp_fft_canon<T, M, N, LD>(v, ln, zt.fft, tw, lane);
+#pragma unroll
+  for (int m = 0; m < V; ++m) v[m] = conjg(v[m]);
+}
+
+// r2c of canonical physical pairs c, then X_k for k < kc written into line out:
+// X_k = 1/2 [(Z_k + conj Z_{M-k}) - i e^{-2 pi i k/N} (Z_k - conj Z_{M-k})],
+// the partner Z_{M-k} coming from lane 32 - lane (lane 0 holds both).
+template <typename T, int N>
+__device__ __forceinline__ void zc_r2c(cx<T> (&c)[N / 64], cx<T>* scratch, cx<T>* out, int kc, const ZTw<T, N>& zt,
+                                       const cx<T>* __restrict__ tw, int lane) {
+  using G = Geometry<T, N>;
+  constexpr int M = N / 2, V = M / 32, LD = G::ZLD;
+  warp_fft_canon<T, M, N, LD>(c, scratch, zt.fft, tw, lane);
+  const int partner = (32 - lane) & 31;
+  cx<T>* po = out + padp(lane) * LD;
+#pragma unroll
+  for (int m = 0; m < V; ++m) {
+    cx<T> zo;
+    zo.x = __shfl_sync(0xffffffffu, c[V - 1 - m].x, partner);
+    zo.y = __shfl_sync(0xffffffffu, c[V - 1 - m].y, partner);
+    if (lane == 0) zo = c[(V - m) % V];
+    const cx<T> wk = zt.wk(tw, m);
+    const cx<T> A = c[m] + conjg(zo), B = c[m] - conjg(zo);
+    if (lane + 32 * m < kc) po[34 * m * LD] = scal(A + mul_mi(cmul(wk, B)), (T)0.5);
+  }
+}
+
+// Warps per z-cross block: 6 ZTX c2r lines and 3 ZTX r2c lines split evenly
+// (4 and 2 per warp).
+template <typename T, int N>
+struct ZCrossWarps {
+  static constexpr int value = (3 * Geometry<T, N>::ZTX) / 2 >= 1 ? (3 * Geometry<T, N>::ZTX) / 2 : 1;
+};
+
+// Tile element walk for the z-cross block (load, cross product, store): one
+// warp instruction covers kz = 16 g + (ZTX/2) kq + c for kq = lane / ZTX and
+// x = lane % ZTX, which touches every shared-memory bank pair exactly twice
+// with the odd row stride ZLD, while each global access reads whole 32-byte
+// sectors of ZTX contiguous x.
+template <typename T, int N>
+struct ZWalk {
+  static constexpr int TX = Geometry<T, N>::ZTX;
+  static constexpr int S = TX / 2 > 0 ? TX / 2 : 1;  // values of c
+  static constexpr int G16 = (N / 2) / 16;           // values of g
+  static constexpr int ITEMS = G16 * S;              // per field
+};
+
+template <typename T, int N>
+__global__ void __launch_bounds__(32 * ZCrossWarps<T, N>::value, (ZCrossWarps<T, N>::value > 16 ? 1 : 2)) k_zcross(PassArgs a) {
+  using G = Geometry<T, N>;
+  using ZW = ZWalk<T, N>;
+  constexpr int M = G::M, TX = G::ZTX, LD = G::ZLD, V = M / 32;
+  constexpr int NW = ZCrossWarps<T, N>::value;
+  constexpr size_t FS = G::FS;
+  static_assert(32 % TX == 0 && (M % 16) == 0, "z-cross tile walk");
+  extern __shared__ unsigned char smraw[];
+  cx<T>* s = reinterpret_cast<cx<T>*>(smraw);
+  const cx<T>* tw = reinterpret_cast<const cx<T>*>(a.tw);
+  cx<T>* W = reinterpret_cast<cx<T>*>(a.W);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int x0 = blockIdx.x * TX, y = blockIdx.y;
+  int kc = (a.kmax3 + 2) / 3;
+  if (kc > M) kc = M;
+  const int tx = lane % TX, kq = lane / TX;
+  // lane part of the walk: k = 16 g + S kq + c  ->  padp(k) = 17 g + S kq + c
+  const cx<T>* gl = W + ((size_t)(ZW::S * kq) * N + y) * N + x0 + tx;
+  cx<T>* sl = s + (ZW::S * kq) * LD + tx;
+
+  for (int it = w; it < 6 * ZW::ITEMS; it += NW) {
+    const int f = it / ZW::ITEMS, r = it % ZW::ITEMS, g = r / ZW::S, c = r % ZW::S;
+    sl[(17 * g + c) * LD + f * TX] = gl[f * FS + (size_t)(16 * g + c) * N * N];
+  }
+  ZTw<T, N> zt;
+  zt.load(tw, lane);
+  __syncthreads();
+  // c2r of the 6 TX lines (u and omega of each column); physical pairs are
+  // written back into the same line at canonical positions
+  cx<T> v[V];
+#pragma unroll 1
+  for (int l = w; l < 6 * TX; l += NW) {
+    cx<T>* ln = s + l;
+    zc_c2r<T, N>(v, ln, zt, tw, lane);
+    cx<T>* pa = ln + padp(lane) * LD;
+#pragma unroll
+    for (int m = 0; m < V; ++m) pa[34 * m * LD] = v[m];
+  }
+  __syncthreads();
+  // u x omega at every point, into the u lines
+  for (int it = w; it < ZW::ITEMS; it += NW) {
+    const int g = it / ZW::S, c = it % ZW::S;
+    cx<T>* p = sl + (17 * g + c) * LD;
+    const cx<T> u0 = p[0 * TX], u1 = p[1 * TX], u2 = p[2 * TX];
+    const cx<T> w0 = p[3 * TX], w1 = p[4 * TX], w2 = p[5 * TX];
+    p[0 * TX] = mk(u1.x * w2.x - u2.x * w1.x, u1.y * w2.y - u2.y * w1.y);
+    p[1 * TX] = mk(u2.x * w0.x - u0.x * w2.x, u2.y * w0.y - u0.y * w2.y);
+    p[2 * TX] = mk(u0.x * w1.x - u1.x * w0.x, u0.y * w1.y - u1.y * w0.y);
+  }
+  __syncthreads();
+  // r2c of the 3 TX product lines, X_k (k < kc) written back into the line
+#pragma unroll 1
+  for (int l = w; l < 3 * TX; l += NW) {
+    cx<T>* ln = s + l;
+    const cx<T>* pa = ln + padp(lane) * LD;
+#pragma unroll
+    for (int m = 0; m < V; ++m) v[m] = pa[34 * m * LD];
+    __syncwarp();
+    zc_r2c<T, N>(v, ln, ln, kc, zt, tw, lane);
+  }
+  __syncthreads();
+  cx<T>* gd = W + ((size_t)(ZW::S * kq) * N + y) * N + x0 + tx;
+  for (int it = w; it < 3 * ZW::ITEMS; it += NW) {
+    const int f = it / ZW::ITEMS, r = it % ZW::ITEMS, g = r / ZW::S, c = r % ZW::S;
+    if (16 * g + ZW::S * kq + c < kc) gd[f * FS + (size_t)(16 * g + c) * N * N] = sl[(17 * g + c) * LD + f * TX];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// z-pass of the right-hand side for N = 512 (lines of M = 256 values): each
+// line belongs to one half-warp, lane h holding positions h + 16 m (m < 16),
+// and the 256-point DFT is two radix-16 passes with a single shared-memory
+// exchange whose stores (17 h + r) and loads (h + 17 m) are free of bank
+// conflicts. Tile loads, the cross product and the stores walk
+// kz = 32 g + ZTX kq + c (kq = lane / ZTX), conflict-free per half-warp.
+// ---------------------------------------------------------------------------
+template <typename T, int TWN, int ES>
+__device__ __forceinline__ void hw_fft256(cx<T> (&v)[16], cx<T>* ln, cx<T> w1, const cx<T>* __restrict__ tw, int h) {
+  dft16(v);
+  cx<T>* q = ln + 17 * h * ES;
+#pragma unroll
+  for (int r = 0; r < 16; ++r) q[r * ES] = v[r];
+  __syncwarp();
+  const cx<T>* rb = ln + h * ES;
+#pragma unroll
+  for (int m = 0; m < 16; ++m) v[m] = rb[17 * m * ES];
+  __syncwarp();
+  if constexpr (sizeof(T) == 4) {
+    cx<T> w[16];
+    twiddle_powers<16>(w1, w);
+#pragma unroll
+    for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], w[r]);
+  } else {
+    constexpr int C = TWN / 256;
+#pragma unroll
+    for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], ldro(tw + h * r * C));
+  }
+  dft16(v);
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(32 * ZCrossWarps<T, N>::value, (ZCrossWarps<T, N>::value > 16 ? 1 : 2)) k_zcross16(PassArgs a) {
+  using G = Geometry<T, N>;
+  constexpr int M = G::M, TX = G::ZTX, LD = G::ZLD;
+  constexpr int NW = ZCrossWarps<T, N>::value;
+  constexpr int ITEMS = (M / 32) * TX;  // walk items per field
+  constexpr size_t FS = G::FS;
+  static_assert(M == 256, "k_zcross16 is the N = 512 z-pass");
+  static_assert(TX == 4 || TX == 8 || TX == 16, "walk needs ZTX in {4, 8, 16}");
+  extern __shared__ unsigned char smraw[];
+  cx<T>* s = reinterpret_cast<cx<T>*>(smraw);
+  const cx<T>* tw = reinterpret_cast<const cx<T>*>(a.tw);
+  cx<T>* W = reinterpret_cast<cx<T>*>(a.W);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int h = lane & 15, half = lane >> 4;
+  const int x0 = blockIdx.x * TX, y = blockIdx.y;
+  int kc = (a.kmax3 + 2) / 3;
+  if (kc > M) kc = M;
+  const int tx = lane % TX, kq = lane / TX;
+  const cx<T>* gl = W + ((size_t)(TX * kq) * N + y) * N + x0 + tx;
+  cx<T>* sl = s + padp(TX * kq) * LD + tx;
+
+  for (int it = w; it < 6 * ITEMS; it += NW) {
+    const int f = it / ITEMS, r = it % ITEMS, g = r / TX, c = r % TX;
+    sl[(34 * g + c) * LD + f * TX] = gl[f * FS + (size_t)(32 * g + c) * N * N];
+  }
+  const cx<T> w1 = ldro(tw + h * (N / 256));
+  const cx<T> tl = ldro(tw + h);
+  __syncthreads();
+
+  cx<T> v[16];
+  // c2r of the 6 TX lines, two per warp at a time; physical pairs back in place
+#pragma unroll 1
+  for (int l = 2 * w + half; l < 6 * TX; l += 2 * NW) {
+    cx<T>* ln = s + l;
+    const cx<T>* pa = ln + h * LD;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const cx<T> xk = pa[17 * m * LD];
+      const cx<T> xm = (h == 0 && m == 0) ? mk((T)0, (T)0) : ln[padp(M - h - 16 * m) * LD];
+      cx<T> z;
+      if (h == 0 && m == 0) {
+        z = mk(xk.x, xk.x);  // Im X_0 ignored, X_M = 0
+      } else {
+        const cx<T> wk = (sizeof(T) == 4) ? (m == 0 ? tl : cmul(tl, ldro(tw + 16 * m))) : ldro(tw + h + 16 * m);
+        const cx<T> A = xk + conjg(xm), B = xk - conjg(xm);
+        z = A + mul_pi(cmul(conjg(wk), B));
+      }
+      v[m] = conjg(z);
+    }
+    __syncwarp();
+    hw_fft256<T, N, LD>(v, ln, w1, tw, h);
+    cx<T>* pw = ln + h * LD;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) pw[17 * m * LD] = conjg(v[m]);
+  }
+  __syncthreads();
+  // u x omega at every point, into the u lines
+  for (int it = w; it < ITEMS; it += NW) {
+    const int g = it / TX, c = it % TX;
+    cx<T>* p = sl + (34 * g + c) * LD;
+    const cx<T> u0 = p[0 * TX], u1 = p[1 * TX], u2 = p[2 * TX];
+    const cx<T> w0 = p[3 * TX], w1v = p[4 * TX], w2 = p[5 * TX];
+    p[0 * TX] = mk(u1.x * w2.x - u2.x * w1v.x, u1.y * w2.y - u2.y * w1v.y);
+    p[1 * TX] = mk(u2.x * w0.x - u0.x * w2.x, u2.y * w0.y - u0.y * w2.y);
+    p[2 * TX] = mk(u0.x * w1v.x - u1.x * w0.x, u0.y * w1v.y - u1.y * w0.y);
+  }
+  __syncthreads();
+  // r2c of the 3 TX product lines; X_k (k < kc) back into the line
+#pragma unroll 1
+  for (int l = 2 * w + half; l < 3 * TX; l += 2 * NW) {
+    cx<T>* ln = s + l;
+    const cx<T>* pa = ln + h * LD;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) v[m] = pa[17 * m * LD];
+    __syncwarp();
+    hw_fft256<T, N, LD>(v, ln, w1, tw, h);
+    cx<T>* po = ln + h * LD;
+    const int partner = (16 - h) & 15;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      cx<T> zo;
+      zo.x = __shfl_sync(0xffffffffu, v[15 - m].x, partner, 16);
+      zo.y = __shfl_sync(0xffffffffu, v[15 - m].y, partner, 16);
+      if (h == 0) zo = v[(16 - m) & 15];
+      const cx<T> wk = (sizeof(T) == 4) ? (m == 0 ? tl : cmul(tl, ldro(tw + 16 * m))) : ldro(tw + h + 16 * m);
+      const cx<T> A = v[m] + conjg(zo), B = v[m] - conjg(zo);
+      if (h + 16 * m < kc) po[17 * m * LD] = scal(A + mul_mi(cmul(wk, B)), (T)0.5);
+    }
+  }
+  __syncthreads();
+  cx<T>* gd = W + ((size_t)(TX * kq) * N + y) * N + x0 + tx;
+  for (int it = w; it < 3 * ITEMS; it += NW) {
+    const int f = it / ITEMS, r = it % ITEMS, g = r / TX, c = r % TX;
+    if (32 * g + TX * kq + c < kc) gd[f * FS + (size_t)(32 * g + c) * N * N] = sl[(34 * g + c) * LD + f * TX];
   }
 }
 
@@ -469,11 +796,22 @@ struct SolverImpl {
     DNS_ATTR((k_ypass<T, N, 0, 1>), G::YSMEM);
     DNS_ATTR((k_ypass<T, N, 0, 0>), G::YSMEM);
     DNS_ATTR((k_zpass<T, N, ZM_CROSS>), G::ZSMEM);
+    if constexpr (ZCross<T, N>::enabled) DNS_ATTR((k_zcross<T, N>), G::ZSMEM);
+    if constexpr (N == 512) DNS_ATTR((k_zcross16<T, N>), G::ZSMEM);
     DNS_ATTR((k_zpass<T, N, ZM_STORE>), G::ZSMEM);
     DNS_ATTR((k_zpass<T, N, ZM_LOAD>), G::ZSMEM);
     DNS_ATTR((k_zpass<T, N, ZM_MAXABS>), G::ZSMEM);
 #undef DNS_ATTR
     return e;
+  }
+
+  static void z_cross(const PassArgs& a, cudaStream_t st) {
+    if constexpr (N == 512)
+      k_zcross16<T, N><<<dim3(N / G::ZTX, N), 32 * ZCrossWarps<T, N>::value, G::ZSMEM, st>>>(a);
+    else if constexpr (ZCross<T, N>::enabled)
+      k_zcross<T, N><<<dim3(N / G::ZTX, N), 32 * ZCrossWarps<T, N>::value, G::ZSMEM, st>>>(a);
+    else
+      k_zpass<T, N, ZM_CROSS><<<dim3(N / G::ZTX, N), ZP_THREADS, G::ZSMEM, st>>>(a);
   }
 
   static int kc_of(int kmax3) {
@@ -484,21 +822,21 @@ struct SolverImpl {
   static cudaError_t x_inverse_curl(const PassArgs& a0, int from_stage, cudaStream_t st) {
     PassArgs a = a0;
     if (from_stage) a.U = a.US;
-    k_xpass<T, N, XM_INV_CURL><<<M * N / G::XROWS, XP_THREADS, G::XSMEM, st>>>(a);
+    k_xpass<T, N, XM_INV_CURL><<<M * N, XP_THREADS, G::XSMEM, st>>>(a);
     return cudaGetLastError();
   }
 
   static void rhs_front(const PassArgs& a, cudaStream_t st) {
     cx<T>* W = reinterpret_cast<cx<T>*>(a.W);
     const cx<T>* tw = reinterpret_cast<const cx<T>*>(a.tw);
-    k_ypass<T, N, 1, 0><<<dim3(N / G::YTX, M, 6), YP_THREADS, G::YSMEM, st>>>(W, tw, a.kmax3);
-    k_zpass<T, N, ZM_CROSS><<<dim3(N / G::ZTX, N), ZP_THREADS, G::ZSMEM, st>>>(a);
-    k_ypass<T, N, 0, 1><<<dim3(N / G::YTX, kc_of(a.kmax3), 3), YP_THREADS, G::YSMEM, st>>>(W, tw, a.kmax3);
+    k_ypass<T, N, 1, 0><<<dim3(N / G::YTX, M, 6), 32 * G::YTX, G::YSMEM, st>>>(W, tw, a.kmax3);
+    z_cross(a, st);
+    k_ypass<T, N, 0, 1><<<dim3(N / G::YTX, kc_of(a.kmax3), 3), 32 * G::YTX, G::YSMEM, st>>>(W, tw, a.kmax3);
   }
 
   static cudaError_t rk_stage(const PassArgs& a, cudaStream_t st) {
     rhs_front(a, st);
-    k_xpass<T, N, XM_STAGE><<<M * N / G::XROWS, XP_THREADS, G::XSMEM, st>>>(a);
+    k_xpass<T, N, XM_STAGE><<<M * N, XP_THREADS, G::XSMEM, st>>>(a);
     return cudaGetLastError();
   }
 
@@ -506,10 +844,10 @@ struct SolverImpl {
     cx<T>* W = reinterpret_cast<cx<T>*>(a.W);
     const cx<T>* tw = reinterpret_cast<const cx<T>*>(a.tw);
     switch (part) {
-      case 0: k_ypass<T, N, 1, 0><<<dim3(N / G::YTX, M, 6), YP_THREADS, G::YSMEM, st>>>(W, tw, a.kmax3); break;
-      case 1: k_zpass<T, N, ZM_CROSS><<<dim3(N / G::ZTX, N), ZP_THREADS, G::ZSMEM, st>>>(a); break;
-      case 2: k_ypass<T, N, 0, 1><<<dim3(N / G::YTX, kc_of(a.kmax3), 3), YP_THREADS, G::YSMEM, st>>>(W, tw, a.kmax3); break;
-      default: k_xpass<T, N, XM_STAGE><<<M * N / G::XROWS, XP_THREADS, G::XSMEM, st>>>(a); break;
+      case 0: k_ypass<T, N, 1, 0><<<dim3(N / G::YTX, M, 6), 32 * G::YTX, G::YSMEM, st>>>(W, tw, a.kmax3); break;
+      case 1: z_cross(a, st); break;
+      case 2: k_ypass<T, N, 0, 1><<<dim3(N / G::YTX, kc_of(a.kmax3), 3), 32 * G::YTX, G::YSMEM, st>>>(W, tw, a.kmax3); break;
+      default: k_xpass<T, N, XM_STAGE><<<M * N, XP_THREADS, G::XSMEM, st>>>(a); break;
     }
     return cudaGetLastError();
   }
@@ -520,21 +858,21 @@ struct SolverImpl {
     rhs_front(a, st);
     PassArgs b = a;
     b.stage = 0;
-    k_xpass<T, N, XM_RHS><<<M * N / G::XROWS, XP_THREADS, G::XSMEM, st>>>(b);
+    k_xpass<T, N, XM_RHS><<<M * N, XP_THREADS, G::XSMEM, st>>>(b);
     return cudaGetLastError();
   }
 
   static cudaError_t forward3d(const PassArgs& a, cudaStream_t st) {
     k_zpass<T, N, ZM_LOAD><<<dim3(N / G::ZTX, N), ZP_THREADS, G::ZSMEM, st>>>(a);
-    k_ypass<T, N, 0, 0><<<dim3(N / G::YTX, M, 3), YP_THREADS, G::YSMEM, st>>>(
+    k_ypass<T, N, 0, 0><<<dim3(N / G::YTX, M, 3), 32 * G::YTX, G::YSMEM, st>>>(
         reinterpret_cast<cx<T>*>(a.U), reinterpret_cast<const cx<T>*>(a.tw), a.kmax3);
-    k_xpass<T, N, XM_FWD_STORE><<<M * N / G::XROWS, XP_THREADS, G::XSMEM, st>>>(a);
+    k_xpass<T, N, XM_FWD_STORE><<<M * N, XP_THREADS, G::XSMEM, st>>>(a);
     return cudaGetLastError();
   }
 
   static cudaError_t inverse3d(const PassArgs& a, cudaStream_t st) {
-    k_xpass<T, N, XM_INV_PLAIN><<<M * N / G::XROWS, XP_THREADS, G::XSMEM, st>>>(a);
-    k_ypass<T, N, 1, 0><<<dim3(N / G::YTX, M, 3), YP_THREADS, G::YSMEM, st>>>(
+    k_xpass<T, N, XM_INV_PLAIN><<<M * N, XP_THREADS, G::XSMEM, st>>>(a);
+    k_ypass<T, N, 1, 0><<<dim3(N / G::YTX, M, 3), 32 * G::YTX, G::YSMEM, st>>>(
         reinterpret_cast<cx<T>*>(a.W), reinterpret_cast<const cx<T>*>(a.tw), a.kmax3);
     k_zpass<T, N, ZM_STORE><<<dim3(N / G::ZTX, N), ZP_THREADS, G::ZSMEM, st>>>(a);
     return cudaGetLastError();
@@ -543,8 +881,8 @@ struct SolverImpl {
   static cudaError_t diag(const PassArgs& a, cudaStream_t st) {
     k_diag<T, N><<<DIAG_BLOCKS, DG_THREADS, 0, st>>>(a);
     k_diag_final<<<1, 32, 0, st>>>(a.partials, DIAG_BLOCKS);
-    k_xpass<T, N, XM_INV_DIV><<<M * N / G::XROWS, XP_THREADS, G::XSMEM, st>>>(a);
-    k_ypass<T, N, 1, 0><<<dim3(N / G::YTX, M, 1), YP_THREADS, G::YSMEM, st>>>(
+    k_xpass<T, N, XM_INV_DIV><<<M * N, XP_THREADS, G::XSMEM, st>>>(a);
+    k_ypass<T, N, 1, 0><<<dim3(N / G::YTX, M, 1), 32 * G::YTX, G::YSMEM, st>>>(
         reinterpret_cast<cx<T>*>(a.D), reinterpret_cast<const cx<T>*>(a.tw), a.kmax3);
     cudaMemsetAsync(a.maxbits, 0, sizeof(unsigned long long), st);
     k_zpass<T, N, ZM_MAXABS><<<dim3(N / G::ZTX, N), ZP_THREADS, G::ZSMEM, st>>>(a);
