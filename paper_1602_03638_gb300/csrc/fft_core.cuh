@@ -166,6 +166,20 @@ __device__ __forceinline__ void twiddle_powers(cx<T> w1, cx<T>* w) {
 }
 
 // ---------------------------------------------------------------------------
+// Asynchronous global -> shared copies (cp.async, sm_80+): used to prefetch
+// the next tile while the current one is transformed.
+// ---------------------------------------------------------------------------
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem_dst, const void* gmem_src) {
+  static_assert(BYTES == 4 || BYTES == 8 || BYTES == 16, "cp.async size");
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(gmem_src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory"); }
+
+// ---------------------------------------------------------------------------
 // Shared-memory line layout: element p sits at padded position p + p/16. With
 // this padding both the contiguous accesses (j + r*L/R over lanes j) and the
 // stride-R Stockham stores of every pass used here touch each bank pair at

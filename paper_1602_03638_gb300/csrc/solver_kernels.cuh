@@ -599,8 +599,32 @@ __global__ void __launch_bounds__(32 * ZCrossWarps<T, N>::value, (ZCrossWarps<T,
 // conflicts. Tile loads, the cross product and the stores walk
 // kz = 32 g + ZTX kq + c (kq = lane / ZTX), conflict-free per half-warp.
 // ---------------------------------------------------------------------------
+// Per-lane twiddles of the half-warp 256-point FFT and of the real-transform
+// pre/post-processing, computed once per block (FP32 form): p2[r] =
+// exp(-2 pi i h r / 256) for the second radix-16 pass and pre[m] =
+// exp(-2 pi i (h + 16 m) / 512). The FP64 form reads the table where used.
+template <typename T>
+struct HwTw {
+  cx<T> p2[16];
+  cx<T> pre[16];
+  __device__ __forceinline__ void init(const cx<T>* __restrict__ tw, int h) {
+    if constexpr (sizeof(T) == 4) {
+      twiddle_powers<16>(ldro(tw + 2 * h), p2);
+      const cx<T> tl = ldro(tw + h);
+      pre[0] = tl;
+#pragma unroll
+      for (int m = 1; m < 16; ++m) pre[m] = cmul(tl, ldro(tw + 16 * m));
+    }
+  }
+  __device__ __forceinline__ cx<T> wk(const cx<T>* __restrict__ tw, int h, int m) const {
+    if constexpr (sizeof(T) == 4) return pre[m];
+    else return ldro(tw + h + 16 * m);
+  }
+};
+
 template <typename T, int TWN, int ES>
-__device__ __forceinline__ void hw_fft256(cx<T> (&v)[16], cx<T>* ln, cx<T> w1, const cx<T>* __restrict__ tw, int h) {
+__device__ __forceinline__ void hw_fft256(cx<T> (&v)[16], cx<T>* ln, const HwTw<T>& ht, const cx<T>* __restrict__ tw,
+                                          int h) {
   dft16(v);
   cx<T>* q = ln + 17 * h * ES;
 #pragma unroll
@@ -611,10 +635,8 @@ __device__ __forceinline__ void hw_fft256(cx<T> (&v)[16], cx<T>* ln, cx<T> w1, c
   for (int m = 0; m < 16; ++m) v[m] = rb[17 * m * ES];
   __syncwarp();
   if constexpr (sizeof(T) == 4) {
-    cx<T> w[16];
-    twiddle_powers<16>(w1, w);
 #pragma unroll
-    for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], w[r]);
+    for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], ht.p2[r]);
   } else {
     constexpr int C = TWN / 256;
 #pragma unroll
@@ -623,11 +645,18 @@ __device__ __forceinline__ void hw_fft256(cx<T> (&v)[16], cx<T>* ln, cx<T> w1, c
   dft16(v);
 }
 
+// Warps per k_zcross16 block: 6 ZTX c2r and 3 ZTX r2c half-warp lines give
+// 4 and 2 line pairs per warp.
 template <typename T, int N>
-__global__ void __launch_bounds__(32 * ZCrossWarps<T, N>::value, (ZCrossWarps<T, N>::value > 16 ? 1 : 2)) k_zcross16(PassArgs a) {
+struct Z16Warps {
+  static constexpr int value = (3 * Geometry<T, N>::ZTX) / 4;
+};
+
+template <typename T, int N>
+__global__ void __launch_bounds__(32 * Z16Warps<T, N>::value, 2) k_zcross16(PassArgs a) {
   using G = Geometry<T, N>;
   constexpr int M = G::M, TX = G::ZTX, LD = G::ZLD;
-  constexpr int NW = ZCrossWarps<T, N>::value;
+  constexpr int NW = Z16Warps<T, N>::value;
   constexpr int ITEMS = (M / 32) * TX;  // walk items per field
   constexpr size_t FS = G::FS;
   static_assert(M == 256, "k_zcross16 is the N = 512 z-pass");
@@ -645,12 +674,28 @@ __global__ void __launch_bounds__(32 * ZCrossWarps<T, N>::value, (ZCrossWarps<T,
   const cx<T>* gl = W + ((size_t)(TX * kq) * N + y) * N + x0 + tx;
   cx<T>* sl = s + padp(TX * kq) * LD + tx;
 
-  for (int it = w; it < 6 * ITEMS; it += NW) {
-    const int f = it / ITEMS, r = it % ITEMS, g = r / TX, c = r % TX;
-    sl[(34 * g + c) * LD + f * TX] = gl[f * FS + (size_t)(32 * g + c) * N * N];
+  // tile load: loads batched ahead of the shared-memory stores
+  static_assert((6 * ITEMS) % NW == 0, "z tile load split");
+  constexpr int PER_WARP = 6 * ITEMS / NW, BATCH = 8;
+  static_assert(PER_WARP % BATCH == 0, "z tile load batches");
+#pragma unroll 1
+  for (int i0 = 0; i0 < PER_WARP; i0 += BATCH) {
+    cx<T> t[BATCH];
+#pragma unroll
+    for (int u = 0; u < BATCH; ++u) {
+      const int it = w + (i0 + u) * NW;
+      const int f = it / ITEMS, r = it % ITEMS, g = r / TX, c = r % TX;
+      t[u] = gl[f * FS + (size_t)(32 * g + c) * N * N];
+    }
+#pragma unroll
+    for (int u = 0; u < BATCH; ++u) {
+      const int it = w + (i0 + u) * NW;
+      const int f = it / ITEMS, r = it % ITEMS, g = r / TX, c = r % TX;
+      sl[(34 * g + c) * LD + f * TX] = t[u];
+    }
   }
-  const cx<T> w1 = ldro(tw + h * (N / 256));
-  const cx<T> tl = ldro(tw + h);
+  HwTw<T> ht;
+  ht.init(tw, h);
   __syncthreads();
 
   cx<T> v[16];
@@ -667,14 +712,14 @@ __global__ void __launch_bounds__(32 * ZCrossWarps<T, N>::value, (ZCrossWarps<T,
       if (h == 0 && m == 0) {
         z = mk(xk.x, xk.x);  // Im X_0 ignored, X_M = 0
       } else {
-        const cx<T> wk = (sizeof(T) == 4) ? (m == 0 ? tl : cmul(tl, ldro(tw + 16 * m))) : ldro(tw + h + 16 * m);
+        const cx<T> wk = ht.wk(tw, h, m);
         const cx<T> A = xk + conjg(xm), B = xk - conjg(xm);
         z = A + mul_pi(cmul(conjg(wk), B));
       }
       v[m] = conjg(z);
     }
     __syncwarp();
-    hw_fft256<T, N, LD>(v, ln, w1, tw, h);
+    hw_fft256<T, N, LD>(v, ln, ht, tw, h);
     cx<T>* pw = ln + h * LD;
 #pragma unroll
     for (int m = 0; m < 16; ++m) pw[17 * m * LD] = conjg(v[m]);
@@ -699,7 +744,7 @@ __global__ void __launch_bounds__(32 * ZCrossWarps<T, N>::value, (ZCrossWarps<T,
 #pragma unroll
     for (int m = 0; m < 16; ++m) v[m] = pa[17 * m * LD];
     __syncwarp();
-    hw_fft256<T, N, LD>(v, ln, w1, tw, h);
+    hw_fft256<T, N, LD>(v, ln, ht, tw, h);
     cx<T>* po = ln + h * LD;
     const int partner = (16 - h) & 15;
 #pragma unroll
@@ -708,7 +753,7 @@ __global__ void __launch_bounds__(32 * ZCrossWarps<T, N>::value, (ZCrossWarps<T,
       zo.x = __shfl_sync(0xffffffffu, v[15 - m].x, partner, 16);
       zo.y = __shfl_sync(0xffffffffu, v[15 - m].y, partner, 16);
       if (h == 0) zo = v[(16 - m) & 15];
-      const cx<T> wk = (sizeof(T) == 4) ? (m == 0 ? tl : cmul(tl, ldro(tw + 16 * m))) : ldro(tw + h + 16 * m);
+      const cx<T> wk = ht.wk(tw, h, m);
       const cx<T> A = v[m] + conjg(zo), B = v[m] - conjg(zo);
       if (h + 16 * m < kc) po[17 * m * LD] = scal(A + mul_mi(cmul(wk, B)), (T)0.5);
     }
@@ -772,6 +817,19 @@ __global__ void k_diag_final(double* partials, int nblocks);
 // ---------------------------------------------------------------------------
 // Host launchers for one (T, N).
 // ---------------------------------------------------------------------------
+// Number of SMs of the current device (persistent kernels launch one block each).
+inline int num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+      n = v;
+    else
+      n = 148;
+  }
+  return n;
+}
+
 template <typename T, int N>
 struct SolverImpl {
   using G = Geometry<T, N>;
@@ -807,7 +865,7 @@ struct SolverImpl {
 
   static void z_cross(const PassArgs& a, cudaStream_t st) {
     if constexpr (N == 512)
-      k_zcross16<T, N><<<dim3(N / G::ZTX, N), 32 * ZCrossWarps<T, N>::value, G::ZSMEM, st>>>(a);
+      k_zcross16<T, N><<<dim3(N / G::ZTX, N), 32 * Z16Warps<T, N>::value, G::ZSMEM, st>>>(a);
     else if constexpr (ZCross<T, N>::enabled)
       k_zcross<T, N><<<dim3(N / G::ZTX, N), 32 * ZCrossWarps<T, N>::value, G::ZSMEM, st>>>(a);
     else
