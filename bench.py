@@ -19,6 +19,8 @@ Printed on rank 0 as one JSON line, with
   step_roofline the whole step against the 132-component-volume minimum
   forms         FP64 at 512^3 and FP32 at 1024^3, and the error of each
                 precision against the FP64 CPU oracle at 128^3
+  ensemble      128 members of mixed sizes: one graph launch per step versus
+                sequential per-member launches
   cpu_baseline  the FP64 CPU oracle timed on this host's cores
   clocks        nvidia-smi samples taken during the timed region
 
@@ -131,7 +133,7 @@ def ncu_traffic(kernel, N, dtype):
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(path):
         return None
-    digest = build._sources_digest()
+    digest = build.kernel_digest()
     with open(path) as f:
         for line in f:
             tok = line.split()
@@ -218,6 +220,44 @@ def run_form(torch, Solver, inputs, N, dtype, warm, steps):
     model_ms = STEP_CV * cv_bytes(N, rb) / (measured_peaks()[0] * 1e9) * 1e3
     return {"N": N, "dtype": dtype, "ms_per_step": ms, "value": N ** 3 / (ms * 1e-3), "steps": steps,
             "hbm_roofline_frac_of_measured": model_ms / ms}
+
+
+def run_ensemble(torch, np, steps=10):
+    """128 independent members (32 each of 32^3, 48^3, 64^3, 96^3), FP32, isotropic initial
+    fields with k0 drawn from U[2, 6] per member: one graph launch per ensemble step versus
+    one dns_step per member (sequential launches)."""
+    from paper_1602_03638_gb300 import Ensemble, inputs
+
+    sizes = [32, 48, 64, 96]
+    Ns = [sizes[i % 4] for i in range(128)]
+    rng = np.random.default_rng(2024)
+    k0s = rng.uniform(2.0, 6.0, size=len(Ns))
+    nu, dt = 5e-3, 2e-3
+    with Ensemble(Ns, [nu] * len(Ns), [dt] * len(Ns), "f32") as ens:
+        for i, (m, N) in enumerate(zip(ens.members, Ns)):
+            uh = inputs.isotropic_spectral(N, seed=i + 1, k0=float(k0s[i]), device="cuda").to(torch.complex64)
+            m.set_state_spectral(uh)
+        best = ens.tune()
+        ens.step(2)
+        ens.synchronize()
+        t0 = time.perf_counter()
+        ens.step(steps)
+        ens.synchronize()
+        batched = (time.perf_counter() - t0) / steps
+        for m in ens.members:  # warm the per-member graphs
+            m.step(1)
+        ens.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            for m in ens.members:
+                m.step(1)
+        ens.synchronize()
+        sequential = (time.perf_counter() - t0) / steps
+        pts = sum(N ** 3 for N in Ns)
+    return {"members": len(Ns), "sizes": {str(n): Ns.count(n) for n in sizes}, "dtype": "f32", "nu": nu, "dt": dt,
+            "graph_branches": best, "batched_ms_per_step": 1e3 * batched, "sequential_ms_per_step": 1e3 * sequential,
+            "speedup": sequential / batched, "points_steps_per_s_batched": pts / batched,
+            "timing": "host wall clock around K steps + stream synchronize"}
 
 
 def run_ours(args):
@@ -331,6 +371,7 @@ def run_ours(args):
                 got = s3.get_state_spectral()
             errs[dt_] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
         line["forms"] = forms
+        line["ensemble"] = run_ensemble(torch, np)
         line["error_vs_oracle"] = {"case": f"Taylor-Green {CPU_N}^3, {CPU_STEPS} RK4 steps, nu=1/1600, dt=1e-3",
                                    "rel_l2_f32": errs["f32"], "rel_l2_f64": errs["f64"]}
         line["cpu_baseline"] = {"value": CPU_N ** 3 * CPU_STEPS / secs, "unit": UNIT, "cores": cores, "kind": "oracle",

@@ -167,6 +167,28 @@ const char* dns_last_error(const dns_handle* h);
  * routine. */
 int dns_spectral_sums_noalloc(const void* uhat, int N, int dtype, double nu, double* out, void* stream);
 
+/* ---- Ensembles (many independent runs of mixed grid sizes) ------------------
+ * An ensemble owns `count` handles created as by dns_create(N[i], nu[i], dt[i],
+ * dtype). dns_ensemble_step(e, n) advances every member by n RK4 steps; each
+ * step is one launch of a CUDA graph whose member kernel chains are parallel
+ * branches (default: one branch per member), so small members run
+ * concurrently. dns_ensemble_tune times candidate branch counts and keeps the
+ * fastest; it ADVANCES every member by 2 steps per candidate tried (the
+ * count is returned in the members' time, dns_diag.t).
+ * Members are ordinary handles for every other call (set_state, get_state,
+ * diagnostics, ...) and all run on the ensemble's stream; do not destroy them
+ * or change their stream. Results are identical to stepping each member alone. */
+typedef struct dns_ensemble dns_ensemble;
+int dns_ensemble_create(int count, const int* N, const double* nu, const double* dt, int dtype, dns_ensemble** out);
+int dns_ensemble_destroy(dns_ensemble* e);
+int dns_ensemble_size(const dns_ensemble* e);
+int dns_ensemble_member(dns_ensemble* e, int i, dns_handle** member);
+int dns_ensemble_set_streams(dns_ensemble* e, int streams); /* 0 = one branch per member */
+int dns_ensemble_streams(const dns_ensemble* e);            /* branch count (0 = per member) */
+int dns_ensemble_tune(dns_ensemble* e, int* best_streams);  /* advances the members, see above */
+int dns_ensemble_step(dns_ensemble* e, int n);              /* asynchronous */
+int dns_ensemble_synchronize(dns_ensemble* e);
+
 /* Test hook for allocation-failure handling: the n-th device allocation made
  * by the library from now on (n >= 1) reports DNS_ERR_OOM without touching
  * the device; n = 0 disables the hook. */

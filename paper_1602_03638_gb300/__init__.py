@@ -5,6 +5,6 @@ include/dns.h); ``Solver`` is a thin marshalling layer over it. Nothing here
 computes the method on the CPU: without the built library every call raises.
 """
 
-from .solver import Solver  # noqa: F401
+from .solver import Ensemble, Solver  # noqa: F401
 
-__all__ = ["Solver"]
+__all__ = ["Solver", "Ensemble"]

@@ -58,6 +58,15 @@ SIGNATURES = {
     "dns_last_error": (ctypes.c_char_p, [_P]),
     "dns_debug_fail_alloc_after": (_I, [_I]),
     "dns_spectral_sums_noalloc": (_I, [_P, _I, _I, _D, _P, _P]),
+    "dns_ensemble_create": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_D), _I, ctypes.POINTER(_P)]),
+    "dns_ensemble_destroy": (_I, [_P]),
+    "dns_ensemble_size": (_I, [_P]),
+    "dns_ensemble_member": (_I, [_P, _I, ctypes.POINTER(_P)]),
+    "dns_ensemble_set_streams": (_I, [_P, _I]),
+    "dns_ensemble_streams": (_I, [_P]),
+    "dns_ensemble_tune": (_I, [_P, ctypes.POINTER(_I)]),
+    "dns_ensemble_step": (_I, [_P, _I]),
+    "dns_ensemble_synchronize": (_I, [_P]),
 }
 
 _lib = None

@@ -54,6 +54,20 @@ def _sources_digest() -> str:
     return h.hexdigest()
 
 
+KERNEL_SOURCES = ("fft_core.cuh", "solver_kernels.cuh", "dns_internal.h", "solver_inst.cu", "instances.h")
+
+
+def kernel_digest() -> str:
+    """Digest of the files that define the solver kernels (not the C-ABI layer)."""
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(CSRC, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    h.update(" ".join(ARCH + FLAGS).encode())
+    return h.hexdigest()[:16]
+
+
 def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -> str:
     """Compile (if sources changed) and return the path of the shared library."""
     os.makedirs(BUILD, exist_ok=True)

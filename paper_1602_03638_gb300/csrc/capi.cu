@@ -591,3 +591,203 @@ int dns_debug_fail_alloc_after(int n) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Ensembles: many independent handles (any mix of grid sizes) advanced by one
+// CUDA graph per step whose member chains are parallel branches over K streams.
+// ---------------------------------------------------------------------------
+struct dns_ensemble {
+  std::vector<dns_handle*> m;
+  cudaStream_t main = nullptr;
+  std::vector<cudaStream_t> aux;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int streams = 0;  // branches of the step graph; 0 = choose by timing at the first step
+  bool dirty = true;
+};
+
+namespace {
+
+void ens_free_graph(dns_ensemble* e) {
+  if (e->gexec) cudaGraphExecDestroy(e->gexec);
+  if (e->graph) cudaGraphDestroy(e->graph);
+  e->gexec = nullptr;
+  e->graph = nullptr;
+}
+
+int ens_capture(dns_ensemble* e, int K) {
+  ens_free_graph(e);
+  const int n = (int)e->m.size();
+  if (K < 1) K = 1;
+  if (K > n) K = n;
+  while ((int)e->aux.size() < K) {
+    cudaStream_t st;
+    DNS_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "ensemble stream");
+    e->aux.push_back(st);
+    cudaEvent_t ev;
+    DNS_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "ensemble event");
+    e->join.push_back(ev);
+  }
+  DNS_CUDA(cudaStreamBeginCapture(e->main, cudaStreamCaptureModeThreadLocal), "ensemble capture begin");
+  cudaError_t err = cudaEventRecord(e->fork, e->main);
+  for (int k = 0; k < K && err == cudaSuccess; ++k) err = cudaStreamWaitEvent(e->aux[k], e->fork, 0);
+  for (int i = 0; i < n && err == cudaSuccess; ++i) err = enqueue_step(e->m[i], e->aux[i % K]);
+  for (int k = 0; k < K && err == cudaSuccess; ++k) {
+    err = cudaEventRecord(e->join[k], e->aux[k]);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(e->main, e->join[k], 0);
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(e->main, &g);
+  if (err != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(err, "ensemble capture");
+  }
+  if (e2 != cudaSuccess) return cuda_fail(e2, "ensemble capture end");
+  e->graph = g;
+  DNS_CUDA(cudaGraphInstantiate(&e->gexec, e->graph, 0), "ensemble graph instantiate");
+  e->streams = K;
+  e->dirty = false;
+  return DNS_OK;
+}
+
+int ens_prepare_members(dns_ensemble* e) {
+  for (dns_handle* h : e->m) {
+    if (!h->w_valid) {
+      DNS_CUDA(h->ops->x_inverse_curl(base_args(h), 0, e->main), "ensemble initial transform");
+      h->w_valid = true;
+    }
+    if (h->graph_dirty) e->dirty = true;
+  }
+  return DNS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dns_ensemble_create(int count, const int* N, const double* nu, const double* dt, int dtype, dns_ensemble** out) {
+  if (!out) return fail(DNS_ERR_ARG, "dns_ensemble_create: out is NULL");
+  *out = nullptr;
+  if (count < 1 || !N || !nu || !dt) return fail(DNS_ERR_ARG, "dns_ensemble_create: need count >= 1 and N, nu, dt arrays");
+  dns_ensemble* e = new dns_ensemble();
+  int rc = DNS_OK;
+  for (int i = 0; i < count && rc == DNS_OK; ++i) {
+    dns_handle* h = nullptr;
+    rc = dns_create(N[i], nu[i], dt[i], dtype, &h);
+    if (rc == DNS_OK) e->m.push_back(h);
+  }
+  if (rc == DNS_OK) {
+    cudaError_t ce = cudaStreamCreate(&e->main);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&e->fork, cudaEventDisableTiming);
+    if (ce != cudaSuccess) rc = cuda_fail(ce, "dns_ensemble_create");
+  }
+  if (rc != DNS_OK) {
+    std::string msg = g_err;
+    dns_ensemble_destroy(e);
+    g_err = msg;
+    return rc;
+  }
+  for (dns_handle* h : e->m) h->stream = e->main;  // members are ordered on the ensemble's stream
+  *out = e;
+  return DNS_OK;
+}
+
+int dns_ensemble_destroy(dns_ensemble* e) {
+  if (!e) return DNS_OK;
+  if (e->main) cudaStreamSynchronize(e->main);
+  ens_free_graph(e);
+  for (dns_handle* h : e->m) {
+    h->stream = h->own_stream;
+    dns_destroy(h);
+  }
+  for (cudaStream_t st : e->aux) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : e->join) cudaEventDestroy(ev);
+  if (e->fork) cudaEventDestroy(e->fork);
+  if (e->main) cudaStreamDestroy(e->main);
+  delete e;
+  return DNS_OK;
+}
+
+int dns_ensemble_size(const dns_ensemble* e) { return e ? (int)e->m.size() : 0; }
+
+int dns_ensemble_member(dns_ensemble* e, int i, dns_handle** member) {
+  if (!e || !member || i < 0 || i >= (int)e->m.size()) return fail(DNS_ERR_ARG, "dns_ensemble_member: bad index");
+  *member = e->m[i];
+  return DNS_OK;
+}
+
+int dns_ensemble_set_streams(dns_ensemble* e, int streams) {
+  if (!e || streams < 0) return fail(DNS_ERR_ARG, "dns_ensemble_set_streams: bad arguments");
+  e->streams = streams;
+  e->dirty = true;
+  return DNS_OK;
+}
+
+int dns_ensemble_step(dns_ensemble* e, int n) {
+  if (!e) return fail(DNS_ERR_ARG, "dns_ensemble_step: ensemble is NULL");
+  if (n < 0) return fail(DNS_ERR_ARG, "dns_ensemble_step: n = %d < 0", n);
+  if (n == 0) return DNS_OK;
+  int rc = ens_prepare_members(e);
+  if (rc) return rc;
+  if (e->dirty || !e->gexec) {
+    if ((rc = ens_capture(e, e->streams > 0 ? e->streams : (int)e->m.size()))) return rc;
+  }
+  for (int i = 0; i < n; ++i) DNS_CUDA(cudaGraphLaunch(e->gexec, e->main), "ensemble graph launch");
+  for (dns_handle* h : e->m) h->t += n * h->dt;
+  return DNS_OK;
+}
+
+int dns_ensemble_tune(dns_ensemble* e, int* best_streams) {
+  if (!e) return fail(DNS_ERR_ARG, "dns_ensemble_tune: ensemble is NULL");
+  int rc = ens_prepare_members(e);
+  if (rc) return rc;
+  const int n = (int)e->m.size();
+  int cand[] = {1, 2, 4, 8, 16, 32, 64, 128, 256, 512};
+  float best = 1e30f;
+  int best_k = n;
+  cudaEvent_t t0, t1;
+  DNS_CUDA(cudaEventCreate(&t0), "tune event");
+  DNS_CUDA(cudaEventCreate(&t1), "tune event");
+  int taken = 0;
+  for (int K : cand) {
+    const int k = K > n ? n : K;
+    if ((rc = ens_capture(e, k))) break;
+    cudaError_t ce = cudaGraphLaunch(e->gexec, e->main);  // warm-up
+    if (ce == cudaSuccess) ce = cudaEventRecord(t0, e->main);
+    if (ce == cudaSuccess) ce = cudaGraphLaunch(e->gexec, e->main);
+    if (ce == cudaSuccess) ce = cudaEventRecord(t1, e->main);
+    if (ce == cudaSuccess) ce = cudaEventSynchronize(t1);
+    if (ce != cudaSuccess) {
+      rc = cuda_fail(ce, "dns_ensemble_tune");
+      break;
+    }
+    taken += 2;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, t0, t1);
+    if (ms < best) {
+      best = ms;
+      best_k = k;
+    }
+    if (k == n) break;
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  for (dns_handle* h : e->m) h->t += taken * h->dt;
+  if (rc) return rc;
+  e->streams = best_k;
+  e->dirty = true;
+  if (best_streams) *best_streams = best_k;
+  return DNS_OK;
+}
+
+int dns_ensemble_streams(const dns_ensemble* e) { return e ? e->streams : 0; }
+
+int dns_ensemble_synchronize(dns_ensemble* e) {
+  if (!e) return fail(DNS_ERR_ARG, "dns_ensemble_synchronize: ensemble is NULL");
+  DNS_CUDA(cudaStreamSynchronize(e->main), "dns_ensemble_synchronize");
+  return DNS_OK;
+}
+
+}  // extern "C"

@@ -50,16 +50,29 @@ class Solver:
         self.dtype = dtype
         self._code = {"f32": _lib.DNS_F32, "f64": _lib.DNS_F64}[dtype]
         self._rb = 4 if dtype == "f32" else 8
+        self._owned = True
         h = ctypes.c_void_p()
         _lib.check(_lib.lib().dns_create(self.N, float(nu), float(dt), self._code, ctypes.byref(h)), "dns_create")
         self._h = h
         if dealias_variant:
             self.set_option("dealias_variant", dealias_variant)
 
+    @classmethod
+    def _borrow(cls, handle: ctypes.c_void_p, N: int, dtype: str):
+        """Wrap a handle owned elsewhere (an ensemble member); close() does not free it."""
+        obj = cls.__new__(cls)
+        obj.N, obj.dtype = int(N), dtype
+        obj._code = {"f32": _lib.DNS_F32, "f64": _lib.DNS_F64}[dtype]
+        obj._rb = 4 if dtype == "f32" else 8
+        obj._owned = False
+        obj._h = handle
+        return obj
+
     # -- life cycle ---------------------------------------------------------
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
-            _lib.lib().dns_destroy(self._h)
+            if getattr(self, "_owned", True):
+                _lib.lib().dns_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -147,3 +160,65 @@ class Solver:
 
     def device_bytes(self) -> int:
         return int(_lib.lib().dns_device_bytes(self._h))
+
+
+class Ensemble:
+    """dns_ensemble: independent members of mixed grid sizes stepped by one graph per step."""
+
+    def __init__(self, Ns, nus, dts, dtype: str = "f32"):
+        n = len(Ns)
+        if not (len(nus) == len(dts) == n) or n == 0:
+            raise ValueError("Ns, nus and dts must have the same non-zero length")
+        code = {"f32": _lib.DNS_F32, "f64": _lib.DNS_F64}[dtype]
+        e = ctypes.c_void_p()
+        _lib.check(_lib.lib().dns_ensemble_create(n, (ctypes.c_int * n)(*[int(x) for x in Ns]),
+                                                  (ctypes.c_double * n)(*[float(x) for x in nus]),
+                                                  (ctypes.c_double * n)(*[float(x) for x in dts]), code,
+                                                  ctypes.byref(e)), "dns_ensemble_create")
+        self._e = e
+        self.members = []
+        for i, N in enumerate(Ns):
+            h = ctypes.c_void_p()
+            _lib.check(_lib.lib().dns_ensemble_member(e, i, ctypes.byref(h)), "dns_ensemble_member")
+            self.members.append(Solver._borrow(h, N, dtype))
+
+    def __len__(self):
+        return len(self.members)
+
+    def step(self, n: int = 1):
+        _lib.check(_lib.lib().dns_ensemble_step(self._e, int(n)), "dns_ensemble_step")
+
+    def tune(self) -> int:
+        """Pick the graph branch count by timing (advances every member, see include/dns.h)."""
+        k = ctypes.c_int()
+        _lib.check(_lib.lib().dns_ensemble_tune(self._e, ctypes.byref(k)), "dns_ensemble_tune")
+        return k.value
+
+    def set_streams(self, k: int):
+        _lib.check(_lib.lib().dns_ensemble_set_streams(self._e, int(k)), "dns_ensemble_set_streams")
+
+    @property
+    def streams(self) -> int:
+        return int(_lib.lib().dns_ensemble_streams(self._e))
+
+    def synchronize(self):
+        _lib.check(_lib.lib().dns_ensemble_synchronize(self._e), "dns_ensemble_synchronize")
+
+    def close(self):
+        if getattr(self, "_e", None) is not None and self._e.value:
+            for m in self.members:
+                m._h = None
+            _lib.lib().dns_ensemble_destroy(self._e)
+            self._e = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
