@@ -17,10 +17,12 @@ Modules
 spectral_ns  -- the solver: transforms, curl, cross product, dealiasing,
                 projection, viscous term, RK4, diagnostics.
 brute_dft    -- O(N^6) triple-sum DFT used to pin the transform convention.
+sgs_mlp      -- FP64 reference of the learned subgrid-stress closure (filter,
+                gradients, stress, network forward/backward, closure force).
 
 Parity status of each function is stated in its docstring; the one part with
 no independent pin (long-time Taylor-Green Re=1600 statistics, whose workshop
 data the paper cites but does not print) says "parity unpinned".
 """
 
-from . import spectral_ns, brute_dft  # noqa: F401
+from . import spectral_ns, brute_dft, sgs_mlp  # noqa: F401
