@@ -21,6 +21,8 @@ Printed on rank 0 as one JSON line, with
                 precision against the FP64 CPU oracle at 128^3
   ensemble      128 members of mixed sizes: one graph launch per step versus
                 sequential per-member launches
+  closure       learned subgrid closure (512^3 DNS -> 64^3): training cost,
+                coarse-step cost and spectrum/dissipation error with and without it
   cpu_baseline  the FP64 CPU oracle timed on this host's cores
   clocks        nvidia-smi samples taken during the timed region
 
@@ -260,6 +262,20 @@ def run_ensemble(torch, np, steps=10):
             "timing": "host wall clock around K steps + stream synchronize"}
 
 
+def run_closure():
+    """Learned subgrid closure: 512^3 FP32 DNS (this solver) -> box filter width 2 pi/64 -> 64^3,
+    BF16 network trained on the GPU, coarse runs with and without it against the filtered DNS."""
+    from paper_1602_03638_gb300 import sgs
+
+    r = sgs.closure_experiment(Nf=512, Nc=64, nu=2e-3, dt_f=1e-3, dt_c=4e-3, k0=4.0, t_dev=0.3, t_run=1.2,
+                               iters=600, batch=65536)
+    keep = ("Nf", "Nc", "nu", "dt_fine", "dt_coarse", "training_points", "train_s", "coarse_ms_per_step_no_model",
+            "coarse_ms_per_step_model", "dns_ms_per_step", "checkpoints")
+    out = {k: r[k] for k in keep}
+    out["final_train_loss"] = r["train_loss"][-1][1]
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -372,6 +388,7 @@ def run_ours(args):
             errs[dt_] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
         line["forms"] = forms
         line["ensemble"] = run_ensemble(torch, np)
+        line["closure"] = run_closure()
         line["error_vs_oracle"] = {"case": f"Taylor-Green {CPU_N}^3, {CPU_STEPS} RK4 steps, nu=1/1600, dt=1e-3",
                                    "rel_l2_f32": errs["f32"], "rel_l2_f64": errs["f64"]}
         line["cpu_baseline"] = {"value": CPU_N ** 3 * CPU_STEPS / secs, "unit": UNIT, "cores": cores, "kind": "oracle",

@@ -189,6 +189,63 @@ int dns_ensemble_tune(dns_ensemble* e, int* best_streams);  /* advances the memb
 int dns_ensemble_step(dns_ensemble* e, int n);              /* asynchronous */
 int dns_ensemble_synchronize(dns_ensemble* e);
 
+/* ---- Transforms and forcing on a handle ---------------------------------------
+ * dns_transform_r2c: F of 3 physical fields (3,N,N,N) (device) into the public
+ *   spectral layout (3,N,N,N/2+1) (device), Nyquist modes zeroed; does not touch
+ *   the state. dns_transform_c2r: the inverse (1/N^3 included, the c2r reading
+ *   of include/dns.h's header). Both are asynchronous on the handle's stream and
+ *   use the handle's work buffers (Eqs. fft/ifft, Sec. 2).
+ * dns_set_forcing: a spectral force f (3,N,N,N/2+1), public layout, added to
+ *   the nonlinear term before the 2/3 mask and the projection at every stage of
+ *   every following step (used by the learned closure, -i k_j tau_hat_ij); the
+ *   library keeps its own copy; f = NULL removes the force. Host input is copied
+ *   synchronously; device input is read on the handle's stream. */
+int dns_transform_r2c(dns_handle* h, const void* phys3, void* spec3);
+int dns_transform_c2r(dns_handle* h, const void* spec3, void* phys3);
+int dns_set_forcing(dns_handle* h, const void* f3, int on_device);
+
+/* ---- Learned subgrid-stress closure: spectral helpers ------------------------
+ * Standalone kernels on caller-owned device arrays, enqueued on `stream`
+ * (a cudaStream_t, NULL = legacy default); spectral arrays in the public layout.
+ * The paper has no closure model; these serve the closure chosen for the
+ * coarse-grid runs (box filter of width 2 pi/Nc, gradient features, SGS stress
+ * tau_ij = filter(u_i u_j) - ubar_i ubar_j, components 00 11 22 01 02 12).
+ *   dns_spectral_filter:   coarse(3,Nc..) = (Nc/Nf)^3 prod_i sinc(k_i pi/Nc) fine(3,Nf..)
+ *                          for |k_i| < Nc/2, zero elsewhere (Nc <= Nf, both even)
+ *   dns_spectral_gradient: grad9[3 i + j] = i k_j uhat_i        (9 spectral fields)
+ *   dns_stress_force:      force3[i] = -i sum_j k_j tauhat[ij]  (6 -> 3 spectral fields)
+ *   dns_pointwise_products: prod6 = (u0u0, u1u1, u2u2, u0u1, u0u2, u1u2)  (physical)
+ *   dns_subtract_products:  tau6 -= products of ubar3 (same order)        (physical) */
+int dns_spectral_filter(const void* fine, int Nf, void* coarse, int Nc, int dtype, void* stream);
+int dns_spectral_gradient(const void* uhat3, int N, void* grad9, int dtype, void* stream);
+int dns_stress_force(const void* tauhat6, int N, void* force3, int dtype, void* stream);
+int dns_pointwise_products(const void* u3, int N, void* prod6, int dtype, void* stream);
+int dns_subtract_products(void* tau6, const void* ubar3, int N, int dtype, void* stream);
+
+/* ---- Learned subgrid-stress closure: the pointwise network -------------------
+ * 10 inputs (9 resolved velocity gradients + filter width) -> 64 SiLU -> 64 SiLU
+ * -> 6 stress components, BF16 tensor-core products with FP32 accumulation and
+ * FP32 master weights. Parameter vector (dns_mlp_param_count() = 5286 floats):
+ * in_shift[10] in_scale[10] W1[10][64] b1[64] W2[64][64] b2[64] W3[64][6] b3[6]
+ * out_scale[6] out_shift[6]; inputs are standardised as (x - in_shift) *
+ * in_scale and tau = y * out_scale + out_shift. Arrays are planar FP32 device
+ * arrays: X[f * P + p] (10 x P), tau[c * P + p] (6 x P). Training minimises the
+ * mean squared error of the standardised stress with Adam (beta 0.9, 0.999,
+ * eps 1e-8) on W1..b3; the normalisation entries are fixed. */
+typedef struct dns_mlp dns_mlp;
+int dns_mlp_param_count(void);
+int dns_mlp_create(dns_mlp** out);
+int dns_mlp_destroy(dns_mlp* net);
+int dns_mlp_set_params(dns_mlp* net, const float* host_params, int count); /* resets Adam */
+int dns_mlp_get_params(dns_mlp* net, float* host_params, int count);
+int dns_mlp_forward(dns_mlp* net, const float* X, float* tau, int P, void* stream);
+/* loss and the gradient of every parameter (zeros for the normalisation entries), synchronous */
+int dns_mlp_loss_grad(dns_mlp* net, const float* X, const float* T, int P, float* grad_host, float* loss_host,
+                      void* stream);
+/* one Adam step on the full batch; loss_host (may be NULL) receives the loss before the update */
+int dns_mlp_train_step(dns_mlp* net, const float* X, const float* T, int P, double lr, float* loss_host,
+                       void* stream);
+
 /* Test hook for allocation-failure handling: the n-th device allocation made
  * by the library from now on (n >= 1) reports DNS_ERR_OOM without touching
  * the device; n = 0 disables the hook. */

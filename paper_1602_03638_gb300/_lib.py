@@ -65,6 +65,22 @@ SIGNATURES = {
     "dns_ensemble_set_streams": (_I, [_P, _I]),
     "dns_ensemble_streams": (_I, [_P]),
     "dns_ensemble_tune": (_I, [_P, ctypes.POINTER(_I)]),
+    "dns_transform_r2c": (_I, [_P, _P, _P]),
+    "dns_transform_c2r": (_I, [_P, _P, _P]),
+    "dns_set_forcing": (_I, [_P, _P, _I]),
+    "dns_spectral_filter": (_I, [_P, _I, _P, _I, _I, _P]),
+    "dns_spectral_gradient": (_I, [_P, _I, _P, _I, _P]),
+    "dns_stress_force": (_I, [_P, _I, _P, _I, _P]),
+    "dns_pointwise_products": (_I, [_P, _I, _P, _I, _P]),
+    "dns_subtract_products": (_I, [_P, _P, _I, _I, _P]),
+    "dns_mlp_param_count": (_I, []),
+    "dns_mlp_create": (_I, [ctypes.POINTER(_P)]),
+    "dns_mlp_destroy": (_I, [_P]),
+    "dns_mlp_set_params": (_I, [_P, ctypes.POINTER(ctypes.c_float), _I]),
+    "dns_mlp_get_params": (_I, [_P, ctypes.POINTER(ctypes.c_float), _I]),
+    "dns_mlp_forward": (_I, [_P, _P, _P, _I, _P]),
+    "dns_mlp_loss_grad": (_I, [_P, _P, _P, _I, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), _P]),
+    "dns_mlp_train_step": (_I, [_P, _P, _P, _I, _D, ctypes.POINTER(ctypes.c_float), _P]),
     "dns_ensemble_step": (_I, [_P, _I]),
     "dns_ensemble_synchronize": (_I, [_P]),
 }

@@ -86,7 +86,7 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
         cmd = [nvcc, *ARCH, *FLAGS, f"-DDNS_INST_T={ctype}", f"-DDNS_INST_N={n}",
                f"-DDNS_INST_FN=dns_ops_{tag}_{n}", "-c", os.path.join(CSRC, "solver_inst.cu"), "-o", obj]
         jobs_list.append((obj, cmd))
-    extra = ["capi.cu", "noalloc.cu"]
+    extra = ["capi.cu", "noalloc.cu", "sgs.cu", "mlp.cu"]
     for name in extra:
         obj = os.path.join(BUILD, name.replace(".cu", ".o"))
         jobs_list.append((obj, [nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, name), "-o", obj]))

@@ -162,6 +162,8 @@ struct dns_handle {
   void* US = nullptr;
   void* W = nullptr;
   void* D = nullptr;
+  void* F = nullptr;  // optional force, internal layout
+  bool has_force = false;
   void* tw = nullptr;
   double* diag = nullptr;
   size_t bytes = 0;
@@ -196,7 +198,7 @@ int dev_alloc(dns_handle* h, void** p, size_t bytes, const char* what) {
 void release(dns_handle* h) {
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->graph) cudaGraphDestroy(h->graph);
-  void* bufs[] = {h->U, h->U1, h->US, h->W, h->D, h->tw, h->diag};
+  void* bufs[] = {h->U, h->U1, h->US, h->W, h->D, h->F, h->tw, h->diag};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -211,6 +213,7 @@ PassArgs base_args(const dns_handle* h) {
   a.W = h->W;
   a.D = h->D;
   a.tw = h->tw;
+  a.F = h->has_force ? h->F : nullptr;
   a.nu = h->nu;
   a.kmax3 = h->N + 2 * h->variant;
   a.partials = h->diag;
@@ -531,6 +534,61 @@ int dns_diagnostics(dns_handle* h, dns_diag* out) {
   out->enstrophy = 0.5 * r[1] / n6;
   if (r[3] != 0.0 || !std::isfinite(out->energy))
     return fail(DNS_ERR_NONFINITE, "dns_diagnostics: %g non-finite modes in the state", r[3]);
+  return DNS_OK;
+}
+
+int dns_transform_r2c(dns_handle* h, const void* phys3, void* spec3) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!phys3 || !spec3 || (uintptr_t)phys3 % 16 || (uintptr_t)spec3 % 16)
+    return fail(DNS_ERR_ARG, "dns_transform_r2c: device pointers must be non-NULL and 16-byte aligned");
+  if ((rc = use_device(h))) return rc;
+  PassArgs a = base_args(h);
+  a.in = phys3;
+  a.U = h->US;  // scratch: the stage state is rebuilt by every step
+  DNS_CUDA(h->ops->forward3d(a, h->stream), "dns_transform_r2c");
+  DNS_CUDA(launch_transpose(h, h->US, spec3, false), "dns_transform_r2c layout");
+  return DNS_OK;
+}
+
+int dns_transform_c2r(dns_handle* h, const void* spec3, void* phys3) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!phys3 || !spec3 || (uintptr_t)phys3 % 16 || (uintptr_t)spec3 % 16)
+    return fail(DNS_ERR_ARG, "dns_transform_c2r: device pointers must be non-NULL and 16-byte aligned");
+  if ((rc = use_device(h))) return rc;
+  DNS_CUDA(launch_transpose(h, spec3, h->US, true), "dns_transform_c2r layout");
+  PassArgs a = base_args(h);
+  a.U = h->US;
+  a.out = phys3;
+  DNS_CUDA(h->ops->inverse3d(a, h->stream), "dns_transform_c2r");
+  h->w_valid = false;
+  return DNS_OK;
+}
+
+int dns_set_forcing(dns_handle* h, const void* f3, int on_device) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if ((rc = use_device(h))) return rc;
+  if (!f3) {
+    if (h->has_force) h->graph_dirty = true;
+    h->has_force = false;
+    return DNS_OK;
+  }
+  if (!h->F && (rc = dev_alloc(h, &h->F, 3 * h->fs * h->ops->elem_bytes, "force"))) return rc;
+  const void* src = f3;
+  if (on_device) {
+    if ((uintptr_t)f3 % 16) return fail(DNS_ERR_ARG, "dns_set_forcing: device pointer must be 16-byte aligned");
+  } else {
+    void* stage = (char*)h->W + 3 * h->fs * h->ops->elem_bytes;
+    DNS_CUDA(cudaMemcpyAsync(stage, f3, paper_spec_bytes(h), cudaMemcpyHostToDevice, h->stream), "dns_set_forcing copy");
+    DNS_CUDA(cudaStreamSynchronize(h->stream), "dns_set_forcing");
+    src = stage;
+    h->w_valid = false;
+  }
+  DNS_CUDA(launch_transpose(h, src, h->F, true), "dns_set_forcing layout");
+  if (!h->has_force) h->graph_dirty = true;
+  h->has_force = true;
   return DNS_OK;
 }
 

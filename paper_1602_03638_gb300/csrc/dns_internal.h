@@ -19,6 +19,7 @@ struct PassArgs {
   void* W = nullptr;   // work: 6 fields, transforms in flight
   void* D = nullptr;   // work: 1 field, divergence diagnostic
   const void* tw = nullptr;  // exp(-2 pi i t / N), t < N
+  const void* F = nullptr;   // optional force (3 fields, internal layout) added to N_hat
   double nu = 0.0;
   double cA = 0.0;  // a_s * dt
   double cB = 0.0;  // b_s * dt

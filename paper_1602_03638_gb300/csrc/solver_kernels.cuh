@@ -149,6 +149,12 @@ __global__ void __launch_bounds__(XP_THREADS, (Geometry<T, N>::XMIN)) k_xpass(Pa
         n0 = s[0 * LS + pj];
         n1 = s[1 * LS + pj];
         n2 = s[2 * LS + pj];
+        if (a.F) {  // external force (learned closure), masked like the nonlinear term
+          const cx<T>* F = reinterpret_cast<const cx<T>*>(a.F);
+          n0 = n0 + F[rb + j];
+          n1 = n1 + F[FS + rb + j];
+          n2 = n2 + F[2 * FS + rb + j];
+        }
       }
       const T k2 = kx * kx + kyv * kyv + kzv * kzv;
       const T ik2 = k2 > (T)0 ? (T)1 / k2 : (T)0;
