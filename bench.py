@@ -264,12 +264,14 @@ def run_ensemble(torch, np, steps=10):
 
 def run_closure():
     """Learned subgrid closure: 512^3 FP32 DNS (this solver) -> box filter width 2 pi/64 -> 64^3,
-    BF16 network trained on the GPU, coarse runs with and without it against the filtered DNS."""
+    BF16 network trained on the GPU, coarse runs with and without it against the filtered DNS over
+    two large-eddy turnover times."""
     from paper_1602_03638_gb300 import sgs
 
-    r = sgs.closure_experiment(Nf=512, Nc=64, nu=2e-3, dt_f=1e-3, dt_c=4e-3, k0=4.0, t_dev=0.3, t_run=1.2,
+    r = sgs.closure_experiment(Nf=512, Nc=64, nu=2e-3, dt_f=1e-3, dt_c=4e-3, k0=4.0, t_dev=0.3, t_run=None,
                                iters=600, batch=65536)
-    keep = ("Nf", "Nc", "nu", "dt_fine", "dt_coarse", "training_points", "train_s", "coarse_ms_per_step_no_model",
+    keep = ("Nf", "Nc", "nu", "dt_fine", "dt_coarse", "t_dev", "t_run", "eddy", "training_points", "train_s",
+            "coarse_ms_per_step_no_model",
             "coarse_ms_per_step_model", "dns_ms_per_step", "checkpoints")
     out = {k: r[k] for k in keep}
     out["final_train_loss"] = r["train_loss"][-1][1]

@@ -313,8 +313,27 @@ def spectrum_error(uh_model: np.ndarray, uh_ref: np.ndarray, kmax: int) -> float
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
+def eddy_turnover(s: Solver) -> dict:
+    """Large-eddy turnover time T_e = L / u' of a solver state (evaluation helper):
+    u' = sqrt(2E/3), L = pi / (2 u'^2) * sum_k E(k)/k over the shell spectrum, k = round(|k|) >= 1."""
+    N = s.N
+    uh = torch.empty(s.spec_shape, dtype=torch.complex64 if s.dtype == "f32" else torch.complex128, device="cuda")
+    s.get_state_spectral(uh)
+    k = torch.fft.fftfreq(N, 1.0 / N, device="cuda")
+    kz = torch.arange(N // 2 + 1, device="cuda", dtype=k.dtype)
+    kk = torch.sqrt(k[:, None, None] ** 2 + k[None, :, None] ** 2 + kz[None, None, :] ** 2).round().long()
+    w = torch.where((kz == 0) | (kz == N // 2), 1.0, 2.0).to(torch.float64)
+    e = (0.5 / float(N) ** 6) * w * (uh.abs() ** 2).sum(0).to(torch.float64)
+    spec = torch.bincount(kk.reshape(-1), weights=e.reshape(-1)).cpu().numpy()
+    energy = float(spec.sum())
+    up = math.sqrt(2.0 * energy / 3.0)
+    shells = np.arange(1, spec.size)
+    L = math.pi / (2.0 * up * up) * float(np.sum(spec[1:] / shells))
+    return {"energy": energy, "u_rms": up, "integral_scale": L, "T_e": L / up}
+
+
 def closure_experiment(Nf: int = 512, Nc: int = 64, nu: float = 2e-3, dt_f: float = 1e-3, dt_c: float = 4e-3,
-                       k0: float = 4.0, seed: int = 0, t_dev: float = 0.3, t_run: float = 1.2, snaps: int = 3,
+                       k0: float = 4.0, seed: int = 0, t_dev: float = 0.3, t_run: float | None = None, snaps: int = 3,
                        checkpoints: int = 4, iters: int = 600, batch: int = 65536, lr: float = 2e-3) -> dict:
     """Fine DNS -> filtered training data -> GPU training -> coarse runs with and without the closure.
 
@@ -322,7 +341,8 @@ def closure_experiment(Nf: int = 512, Nc: int = 64, nu: float = 2e-3, dt_f: floa
     training snapshots are taken at t_dev * i / snaps (i = 1..snaps). Both coarse runs start from
     the filtered fine state at t_dev and are compared with the filtered DNS at `checkpoints` equally
     spaced times up to t_dev + t_run: relative L2 error of the shell spectrum over 1 <= k < Nc/3 and
-    relative error of the resolved dissipation nu <|curl ubar|^2>.
+    relative error of the resolved dissipation nu <|curl ubar|^2>. t_run = None runs two large-eddy
+    turnover times of the fine field at t_dev.
     """
     import time
 
@@ -350,6 +370,10 @@ def closure_experiment(Nf: int = 512, Nc: int = 64, nu: float = 2e-3, dt_f: floa
     X = torch.cat(Xs, dim=1).contiguous()
     T = torch.cat(Ts, dim=1).contiguous()
     out["training_points"] = int(X.shape[1])
+    out["eddy"] = eddy_turnover(fine)
+    if t_run is None:
+        t_run = 2.0 * out["eddy"]["T_e"]
+    out["t_run"] = t_run
     net = MLP(seed=seed)
     net.set_params(with_normalisation(net.get_params(), X, T))
     t0 = time.perf_counter()
@@ -366,8 +390,8 @@ def closure_experiment(Nf: int = 512, Nc: int = 64, nu: float = 2e-3, dt_f: floa
         return s
 
     plain, model = coarse_from(ub0), coarse_from(ub0)
-    n_f = int(round(t_run / dt_f / checkpoints))
-    n_c = int(round(t_run / dt_c / checkpoints))
+    n_c = max(1, int(round(t_run / dt_c / checkpoints)))
+    n_f = int(round(n_c * dt_c / dt_f))  # the same physical time per checkpoint
     rec = []
     t_plain = t_model = t_dns = 0.0
     for c in range(1, checkpoints + 1):
