@@ -40,9 +40,14 @@ struct Geometry {
   static constexpr int M = N / 2;
   static constexpr size_t FS = (size_t)M * N * N;  // complex values per field
   static constexpr int CB = (int)sizeof(cx<T>);
-  // x-pass: one row (fixed kz, ky) per block, 6 padded line buffers.
+  // x-pass: one row (fixed kz, ky) per block, 6 padded line buffers; where it
+  // fits in 64 KB, 9 more unpadded rows receive the stage's state rows by
+  // cp.async together with the nonlinear-term rows (XPRE).
   static constexpr int XLS = padded_len(N);
+  static constexpr int XST = (6 * XLS + 1) / 2 * 2;  // 16-byte aligned start of the state rows
+  static constexpr bool XPRE = (size_t)(XST + 9 * N) * CB <= 64 * 1024;
   static constexpr size_t XSMEM = (size_t)6 * XLS * CB;
+  static constexpr size_t XSMEM_ST = XPRE ? (size_t)(XST + 9 * N) * CB : XSMEM;  // XM_STAGE, XM_RHS
   // y-pass: YTX adjacent columns (128-byte rows up to N = 512, 64-byte at 1024).
   static constexpr int YTX = cmin((N <= 512 ? 128 : 64) / CB, pow2_part(N));
   static constexpr int YLD = odd_ld(YTX);
@@ -132,14 +137,50 @@ __global__ void __launch_bounds__(XP_THREADS, (Geometry<T, N>::XMIN)) k_xpass(Pa
   if constexpr (MODE == XM_STAGE || MODE == XM_RHS) {
     // rows outside the 2/3 box carry no nonlinear term: skip their transform
     const bool row_kept = (3 * kz < a.kmax3) && kept(kfreq(ky, N), a.kmax3);
-    if (row_kept && warp < 3) {
-      const SLine<T, 1> line{s + warp * LS};
-      warp_fft<T, N, N>(GLoad<T, false>{W + warp * FS + rb}, line, line, tw, lane);
-    }
-    __syncthreads();
     const T nu = (T)a.nu, cA = (T)a.cA, cB = (T)a.cB;
     const int stage = a.stage;
     const cx<T>* Sst = (stage == 0) ? U : US;
+    // state rows read by the update: stage state (all stages), accumulator
+    // (stages 1-3), step-start state (stages 1-2)
+    const bool need1 = MODE == XM_STAGE && stage > 0, need0 = MODE == XM_STAGE && stage > 0 && stage < 3;
+    cx<T>* const st = s + G::XST;  // XPRE: rows [Sst 0..2][U1 0..2][U 0..2], N values each
+    if constexpr (G::XPRE) {
+      if (row_kept) {
+        for (int e = threadIdx.x; e < 3 * N; e += XP_THREADS) {
+          const int f = e / N, j = e % N;
+          cp_async<sizeof(cx<T>)>(s + f * LS + padp(j), W + f * FS + rb + j);
+        }
+      }
+      cp_async_commit();
+      constexpr int PK = 16 / (int)sizeof(cx<T>);  // complex values per 16-byte copy
+      auto fetch_rows = [&](const cx<T>* src, cx<T>* dst) {
+        for (int e = threadIdx.x; e < 3 * N / PK; e += XP_THREADS) {
+          const int f = (e * PK) / N, j = (e * PK) % N;
+          cp_async<16>(dst + f * N + j, src + f * FS + rb + j);
+        }
+      };
+      fetch_rows(Sst, st);
+      if (need1) fetch_rows(U1, st + 3 * N);
+      if (need0) fetch_rows(U, st + 6 * N);
+      cp_async_commit();
+      cp_async_wait<1>();
+      __syncthreads();
+      if (row_kept && warp < 3) {
+        const SLine<T, 1> line{s + warp * LS};
+        warp_fft<T, N, N>(line, line, line, tw, lane);
+      }
+      cp_async_wait<0>();
+    } else {
+      if (row_kept && warp < 3) {
+        const SLine<T, 1> line{s + warp * LS};
+        warp_fft<T, N, N>(GLoad<T, false>{W + warp * FS + rb}, line, line, tw, lane);
+      }
+    }
+    __syncthreads();
+    // state values of component c at column j: staged rows or global memory
+    auto ld_s = [&](int c, int j) -> cx<T> { return G::XPRE ? st[c * N + j] : Sst[c * FS + rb + j]; };
+    auto ld_1 = [&](int c, int j) -> cx<T> { return G::XPRE ? st[(3 + c) * N + j] : U1[c * FS + rb + j]; };
+    auto ld_0 = [&](int c, int j) -> cx<T> { return G::XPRE ? st[(6 + c) * N + j] : U[c * FS + rb + j]; };
     for (int j = threadIdx.x; j < N; j += XP_THREADS) {
       const int kxi = kfreq(j, N);
       const T kx = (T)kxi;
@@ -161,7 +202,7 @@ __global__ void __launch_bounds__(XP_THREADS, (Geometry<T, N>::XMIN)) k_xpass(Pa
       // P = (k . N_hat) / |k|^2   (Eq. mod_pressure without the factor i)
       const cx<T> p = mk((kx * n0.x + kyv * n1.x + kzv * n2.x) * ik2, (kx * n0.y + kyv * n1.y + kzv * n2.y) * ik2);
       const size_t gi = rb + j;
-      const cx<T> u0 = Sst[gi], u1 = Sst[FS + gi], u2 = Sst[2 * FS + gi];
+      const cx<T> u0 = ld_s(0, j), u1 = ld_s(1, j), u2 = ld_s(2, j);
       const T nk2 = nu * k2;
       // dU = N_hat - k P - nu |k|^2 u_hat   (Eq. NSfinal)
       const cx<T> d0 = mk(n0.x - kx * p.x - nk2 * u0.x, n0.y - kx * p.y - nk2 * u0.y);
@@ -185,10 +226,10 @@ __global__ void __launch_bounds__(XP_THREADS, (Geometry<T, N>::XMIN)) k_xpass(Pa
           US[FS + gi] = v1;
           US[2 * FS + gi] = v2;
         } else if (stage < 3) {
-          const cx<T> b0 = U[gi], b1 = U[FS + gi], b2 = U[2 * FS + gi];
-          U1[gi] = U1[gi] + scal(d0, cA);
-          U1[FS + gi] = U1[FS + gi] + scal(d1, cA);
-          U1[2 * FS + gi] = U1[2 * FS + gi] + scal(d2, cA);
+          const cx<T> b0 = ld_0(0, j), b1 = ld_0(1, j), b2 = ld_0(2, j);
+          U1[gi] = ld_1(0, j) + scal(d0, cA);
+          U1[FS + gi] = ld_1(1, j) + scal(d1, cA);
+          U1[2 * FS + gi] = ld_1(2, j) + scal(d2, cA);
           v0 = b0 + scal(d0, cB);
           v1 = b1 + scal(d1, cB);
           v2 = b2 + scal(d2, cB);
@@ -196,9 +237,9 @@ __global__ void __launch_bounds__(XP_THREADS, (Geometry<T, N>::XMIN)) k_xpass(Pa
           US[FS + gi] = v1;
           US[2 * FS + gi] = v2;
         } else {
-          v0 = U1[gi] + scal(d0, cA);
-          v1 = U1[FS + gi] + scal(d1, cA);
-          v2 = U1[2 * FS + gi] + scal(d2, cA);
+          v0 = ld_1(0, j) + scal(d0, cA);
+          v1 = ld_1(1, j) + scal(d1, cA);
+          v2 = ld_1(2, j) + scal(d2, cA);
           U[gi] = v0;
           U[FS + gi] = v1;
           U[2 * FS + gi] = v2;
@@ -773,6 +814,154 @@ __global__ void __launch_bounds__(32 * Z16Warps<T, N>::value, 2) k_zcross16(Pass
 }
 
 // ---------------------------------------------------------------------------
+// Pipelined z-pass for N = 512: one persistent block per SM walks tiles of
+// 128-byte rows (16 adjacent x in FP32, 8 in FP64) at fixed y. The whole tile
+// (6 fields x 256 kz) sits in shared memory and arrives by cp.async straight
+// into the padded layout; the next tile's omega fields are fetched while the
+// products are transformed and stored, its u fields while the omega lines are
+// transformed, so HBM traffic overlaps the shared-memory-bound transforms.
+// Line transforms, cross product and walks are those of k_zcross16. FP32 only:
+// the FP64 form (8 x per row) would spill and keeps k_zcross16.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Z16P {
+  static constexpr int M = 256;
+  static constexpr int TX = 128 / (int)sizeof(cx<T>);  // 128-byte rows
+  static constexpr int LD = odd_ld(6 * TX);
+  static constexpr int NW = 12;                        // warps per block
+  static constexpr int ITEMS = (M / 32) * TX;          // walk items per field
+  static constexpr size_t SMEM = (size_t)padded_len(M) * LD * sizeof(cx<T>);
+};
+
+template <typename T, int N>
+__global__ void __launch_bounds__(32 * Z16P<T>::NW, 1) k_zcross16p(PassArgs a) {
+  using P = Z16P<T>;
+  constexpr int M = P::M, TX = P::TX, LD = P::LD, NW = P::NW, ITEMS = P::ITEMS;
+  constexpr size_t FS = Geometry<T, N>::FS;
+  constexpr int XT = N / TX, NT = XT * N;  // tiles: x-tiles times y
+  static_assert(N == 512 && (TX == 8 || TX == 16), "k_zcross16p is the N = 512 z-pass");
+  static_assert((3 * ITEMS) % NW == 0, "z tile load split");
+  static_assert((3 * TX) % (2 * NW) == 0, "line pairs per warp");
+  extern __shared__ unsigned char smraw[];
+  cx<T>* s = reinterpret_cast<cx<T>*>(smraw);
+  const cx<T>* tw = reinterpret_cast<const cx<T>*>(a.tw);
+  cx<T>* W = reinterpret_cast<cx<T>*>(a.W);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int h = lane & 15, half = lane >> 4;
+  int kc = (a.kmax3 + 2) / 3;
+  if (kc > M) kc = M;
+  const int tx = lane % TX, kq = lane / TX;
+  // lane part of the walk kz = 32 g + TX kq + c: padp(kz) = 34 g + padp(TX kq) + c
+  cx<T>* const sl = s + padp(TX * kq) * LD + tx;
+  const size_t lane_g = ((size_t)(TX * kq) * N) * N + tx;
+
+  // asynchronous fetch of fields f0 .. f0+2 of tile t into their lines
+  auto fetch = [&](int t, int f0) {
+    const cx<T>* gl = W + lane_g + (size_t)(t / XT) * N + (t % XT) * TX;
+#pragma unroll 4
+    for (int it = w; it < 3 * ITEMS; it += NW) {
+      const int f = f0 + it / ITEMS, r = it % ITEMS, g = r / TX, c = r % TX;
+      cp_async<sizeof(cx<T>)>(sl + (34 * g + c) * LD + f * TX, gl + f * FS + (size_t)(32 * g + c) * N * N);
+    }
+  };
+  // c2r of the TX lines of fields f0 .. f0+2, two lines per warp at a time
+  HwTw<T> ht;
+  ht.init(tw, h);
+  auto c2r_lines = [&](int f0) {
+    cx<T> v[16];
+#pragma unroll 1
+    for (int l = f0 * TX + 2 * w + half; l < (f0 + 3) * TX; l += 2 * NW) {
+      cx<T>* ln = s + l;
+      const cx<T>* pa = ln + h * LD;
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        const cx<T> xk = pa[17 * m * LD];
+        const cx<T> xm = (h == 0 && m == 0) ? mk((T)0, (T)0) : ln[padp(M - h - 16 * m) * LD];
+        cx<T> z;
+        if (h == 0 && m == 0) {
+          z = mk(xk.x, xk.x);  // Im X_0 ignored, X_M = 0
+        } else {
+          const cx<T> wk = ht.wk(tw, h, m);
+          const cx<T> A = xk + conjg(xm), B = xk - conjg(xm);
+          z = A + mul_pi(cmul(conjg(wk), B));
+        }
+        v[m] = conjg(z);
+      }
+      __syncwarp();
+      hw_fft256<T, N, LD>(v, ln, ht, tw, h);
+      cx<T>* pw = ln + h * LD;
+#pragma unroll
+      for (int m = 0; m < 16; ++m) pw[17 * m * LD] = conjg(v[m]);
+    }
+  };
+
+  int t = blockIdx.x;
+  if (t < NT) fetch(t, 3);
+  cp_async_commit();
+  if (t < NT) fetch(t, 0);
+  cp_async_commit();
+#pragma unroll 1
+  for (; t < NT; t += gridDim.x) {
+    const int x0 = (t % XT) * TX, y = t / XT, tn = t + gridDim.x;
+    cp_async_wait<1>();  // omega fields of tile t
+    __syncthreads();
+    c2r_lines(3);
+    cp_async_wait<0>();  // u fields of tile t
+    __syncthreads();
+    c2r_lines(0);
+    __syncthreads();
+    // u x omega at every point, into the u lines
+    for (int it = w; it < ITEMS; it += NW) {
+      const int g = it / TX, c = it % TX;
+      cx<T>* p = sl + (34 * g + c) * LD;
+      const cx<T> u0 = p[0 * TX], u1 = p[1 * TX], u2 = p[2 * TX];
+      const cx<T> w0 = p[3 * TX], w1v = p[4 * TX], w2 = p[5 * TX];
+      p[0 * TX] = mk(u1.x * w2.x - u2.x * w1v.x, u1.y * w2.y - u2.y * w1v.y);
+      p[1 * TX] = mk(u2.x * w0.x - u0.x * w2.x, u2.y * w0.y - u0.y * w2.y);
+      p[2 * TX] = mk(u0.x * w1v.x - u1.x * w0.x, u0.y * w1v.y - u1.y * w0.y);
+    }
+    __syncthreads();
+    if (tn < NT) fetch(tn, 3);  // the omega lines are free
+    cp_async_commit();
+    // r2c of the 3 TX product lines; X_k (k < kc) back into the line
+    {
+      cx<T> v[16];
+#pragma unroll 1
+      for (int l = 2 * w + half; l < 3 * TX; l += 2 * NW) {
+        cx<T>* ln = s + l;
+        const cx<T>* pa = ln + h * LD;
+#pragma unroll
+        for (int m = 0; m < 16; ++m) v[m] = pa[17 * m * LD];
+        __syncwarp();
+        hw_fft256<T, N, LD>(v, ln, ht, tw, h);
+        cx<T>* po = ln + h * LD;
+        const int partner = (16 - h) & 15;
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+          cx<T> zo;
+          zo.x = __shfl_sync(0xffffffffu, v[15 - m].x, partner, 16);
+          zo.y = __shfl_sync(0xffffffffu, v[15 - m].y, partner, 16);
+          if (h == 0) zo = v[(16 - m) & 15];
+          const cx<T> wk = ht.wk(tw, h, m);
+          const cx<T> A = v[m] + conjg(zo), B = v[m] - conjg(zo);
+          if (h + 16 * m < kc) po[17 * m * LD] = scal(A + mul_mi(cmul(wk, B)), (T)0.5);
+        }
+      }
+    }
+    __syncthreads();
+    cx<T>* gd = W + lane_g + (size_t)y * N + x0;
+    for (int it = w; it < 3 * ITEMS; it += NW) {
+      const int f = it / ITEMS, r = it % ITEMS, g = r / TX, c = r % TX;
+      if (32 * g + TX * kq + c < kc) gd[f * FS + (size_t)(32 * g + c) * N * N] = sl[(34 * g + c) * LD + f * TX];
+    }
+    __syncthreads();  // the u lines have been read out
+    if (tn < NT) fetch(tn, 0);
+    cp_async_commit();
+  }
+  cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------------------
 // FP64 spectral sums for the diagnostics (Parseval): per block
 //   sum w|u|^2, sum w|omega|^2, sum w Re(conj(u).omega), count of non-finite,
 // w = 1 at kz = 0 and 2 otherwise (half spectrum; kz = N/2 is zero).
@@ -851,8 +1040,8 @@ struct SolverImpl {
 #define DNS_ATTR(kern, bytes) \
   if (e == cudaSuccess) e = smem_attr(kern, bytes)
     DNS_ATTR((k_xpass<T, N, XM_INV_CURL>), G::XSMEM);
-    DNS_ATTR((k_xpass<T, N, XM_STAGE>), G::XSMEM);
-    DNS_ATTR((k_xpass<T, N, XM_RHS>), G::XSMEM);
+    DNS_ATTR((k_xpass<T, N, XM_STAGE>), G::XSMEM_ST);
+    DNS_ATTR((k_xpass<T, N, XM_RHS>), G::XSMEM_ST);
     DNS_ATTR((k_xpass<T, N, XM_FWD_STORE>), G::XSMEM);
     DNS_ATTR((k_xpass<T, N, XM_INV_PLAIN>), G::XSMEM);
     DNS_ATTR((k_xpass<T, N, XM_INV_DIV>), G::XSMEM);
@@ -862,6 +1051,7 @@ struct SolverImpl {
     DNS_ATTR((k_zpass<T, N, ZM_CROSS>), G::ZSMEM);
     if constexpr (ZCross<T, N>::enabled) DNS_ATTR((k_zcross<T, N>), G::ZSMEM);
     if constexpr (N == 512) DNS_ATTR((k_zcross16<T, N>), G::ZSMEM);
+    if constexpr (N == 512 && sizeof(T) == 4) DNS_ATTR((k_zcross16p<T, N>), Z16P<T>::SMEM);
     DNS_ATTR((k_zpass<T, N, ZM_STORE>), G::ZSMEM);
     DNS_ATTR((k_zpass<T, N, ZM_LOAD>), G::ZSMEM);
     DNS_ATTR((k_zpass<T, N, ZM_MAXABS>), G::ZSMEM);
@@ -870,7 +1060,9 @@ struct SolverImpl {
   }
 
   static void z_cross(const PassArgs& a, cudaStream_t st) {
-    if constexpr (N == 512)
+    if constexpr (N == 512 && sizeof(T) == 4)
+      k_zcross16p<T, N><<<num_sms(), 32 * Z16P<T>::NW, Z16P<T>::SMEM, st>>>(a);
+    else if constexpr (N == 512)
       k_zcross16<T, N><<<dim3(N / G::ZTX, N), 32 * Z16Warps<T, N>::value, G::ZSMEM, st>>>(a);
     else if constexpr (ZCross<T, N>::enabled)
       k_zcross<T, N><<<dim3(N / G::ZTX, N), 32 * ZCrossWarps<T, N>::value, G::ZSMEM, st>>>(a);
@@ -900,7 +1092,7 @@ struct SolverImpl {
 
   static cudaError_t rk_stage(const PassArgs& a, cudaStream_t st) {
     rhs_front(a, st);
-    k_xpass<T, N, XM_STAGE><<<M * N, XP_THREADS, G::XSMEM, st>>>(a);
+    k_xpass<T, N, XM_STAGE><<<M * N, XP_THREADS, G::XSMEM_ST, st>>>(a);
     return cudaGetLastError();
   }
 
@@ -911,7 +1103,7 @@ struct SolverImpl {
       case 0: k_ypass<T, N, 1, 0><<<dim3(N / G::YTX, M, 6), 32 * G::YTX, G::YSMEM, st>>>(W, tw, a.kmax3); break;
       case 1: z_cross(a, st); break;
       case 2: k_ypass<T, N, 0, 1><<<dim3(N / G::YTX, kc_of(a.kmax3), 3), 32 * G::YTX, G::YSMEM, st>>>(W, tw, a.kmax3); break;
-      default: k_xpass<T, N, XM_STAGE><<<M * N, XP_THREADS, G::XSMEM, st>>>(a); break;
+      default: k_xpass<T, N, XM_STAGE><<<M * N, XP_THREADS, G::XSMEM_ST, st>>>(a); break;
     }
     return cudaGetLastError();
   }
@@ -922,7 +1114,7 @@ struct SolverImpl {
     rhs_front(a, st);
     PassArgs b = a;
     b.stage = 0;
-    k_xpass<T, N, XM_RHS><<<M * N, XP_THREADS, G::XSMEM, st>>>(b);
+    k_xpass<T, N, XM_RHS><<<M * N, XP_THREADS, G::XSMEM_ST, st>>>(b);
     return cudaGetLastError();
   }
 
