@@ -235,6 +235,13 @@ struct SLine {  // a line in shared memory at padded positions, element stride E
   __device__ __forceinline__ cx<T> load(const cx<T>* q) const { return *q; }
   __device__ __forceinline__ void store(cx<T>* q, int, cx<T> v) const { *q = v; }
 };
+template <typename T, int ES>
+struct SLineConj {  // shared-memory line read conjugated (inverse DFT of staged data)
+  cx<T>* s;
+  __device__ __forceinline__ cx<T>* at(int p) const { return s + padp(p) * ES; }
+  static constexpr int off(int d) { return padp(d) * ES; }
+  __device__ __forceinline__ cx<T> load(const cx<T>* q) const { return conjg(*q); }
+};
 template <typename T, bool CONJ>
 struct GLoad {  // contiguous line in global memory
   const cx<T>* g;

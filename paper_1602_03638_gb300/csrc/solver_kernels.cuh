@@ -305,16 +305,20 @@ __global__ void __launch_bounds__(32 * Geometry<T, N>::YTX, (Geometry<T, N>::YMI
   cx<T>* s = reinterpret_cast<cx<T>*>(smraw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   cx<T>* base = F + blockIdx.z * G::FS + (size_t)blockIdx.y * N * N + blockIdx.x * TX;
+  // the whole tile in flight at once (cp.async, no register staging); the
+  // inverse's conjugation is applied when the first pass reads it
 #pragma unroll 8
   for (int e = threadIdx.x; e < TX * N; e += NT) {
     const int x = e % TX, y = e / TX;
-    const cx<T> v = base[(size_t)y * N + x];
-    s[padp(y) * LD + x] = INV ? conjg(v) : v;
+    cp_async<sizeof(cx<T>)>(s + padp(y) * LD + x, base + (size_t)y * N + x);
   }
+  cp_async_commit();
+  cp_async_wait<0>();
   __syncthreads();
   {
     const SLine<T, LD> line{s + warp};
-    warp_fft<T, N, N>(line, line, line, tw, lane);
+    if constexpr (INV) warp_fft<T, N, N>(SLineConj<T, LD>{s + warp}, line, line, tw, lane);
+    else warp_fft<T, N, N>(line, line, line, tw, lane);
   }
   __syncthreads();
 #pragma unroll 8
