@@ -501,11 +501,10 @@ struct ZTw {
 // physical pairs v[m] = x_{2n} + i x_{2n+1}, n = lane + 32 m. The pre-processing
 // Z'_k = (X_k + conj X_{M-k}) + i e^{+2 pi i k/N} (X_k - conj X_{M-k}) is fused
 // into the load (stored conjugated: a forward DFT then gives the inverse one).
-template <typename T, int N>
+template <typename T, int N, int LD = Geometry<T, N>::ZLD>
 __device__ __forceinline__ void zc_c2r(cx<T> (&v)[N / 64], cx<T>* ln, const ZTw<T, N>& zt,
                                        const cx<T>* __restrict__ tw, int lane) {
-  using G = Geometry<T, N>;
-  constexpr int M = N / 2, V = M / 32, LD = G::ZLD;
+  constexpr int M = N / 2, V = M / 32;
   const cx<T>* pa = ln + padp(lane) * LD;            // X_k, k = lane + 32 m
   const cx<T>* pb = ln + padp((32 - lane) & 31) * LD;  // X_{M-k} for lane > 0
 #pragma unroll
@@ -533,11 +532,10 @@ __device__ __forceinline__ void zc_c2r(cx<T> (&v)[N / 64], cx<T>* ln, const ZTw<
 // r2c of canonical physical pairs c, then X_k for k < kc written into line out:
 // X_k = 1/2 [(Z_k + conj Z_{M-k}) - i e^{-2 pi i k/N} (Z_k - conj Z_{M-k})],
 // the partner Z_{M-k} coming from lane 32 - lane (lane 0 holds both).
-template <typename T, int N>
+template <typename T, int N, int LD = Geometry<T, N>::ZLD>
 __device__ __forceinline__ void zc_r2c(cx<T> (&c)[N / 64], cx<T>* scratch, cx<T>* out, int kc, const ZTw<T, N>& zt,
                                        const cx<T>* __restrict__ tw, int lane) {
-  using G = Geometry<T, N>;
-  constexpr int M = N / 2, V = M / 32, LD = G::ZLD;
+  constexpr int M = N / 2, V = M / 32;
   warp_fft_canon<T, M, N, LD>(c, scratch, zt.fft, tw, lane);
   const int partner = (32 - lane) & 31;
   cx<T>* po = out + padp(lane) * LD;
@@ -966,6 +964,116 @@ __global__ void __launch_bounds__(32 * Z16P<T>::NW, 1) k_zcross16p(PassArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Pipelined z-pass for N = 1024 (lines of M = 512 values, FP32): the schedule
+// of k_zcross16p (persistent block, whole tile in shared memory, next tile's
+// omega fields fetched during the product transforms and its u fields during
+// the omega transforms) with 8 adjacent x per tile (64-byte rows: the widest
+// six 512-value lines fit) and one warp per line (canonical register FFT).
+// ---------------------------------------------------------------------------
+template <typename T>
+struct ZPC {
+  static constexpr int M = 512;
+  static constexpr int TX = 64 / (int)sizeof(cx<T>);
+  static constexpr int LD = odd_ld(6 * TX);
+  static constexpr int NW = 12;
+  static constexpr int ITEMS = (M / 32) * TX;
+  static constexpr size_t SMEM = (size_t)padded_len(M) * LD * sizeof(cx<T>);
+};
+
+template <typename T, int N>
+__global__ void __launch_bounds__(32 * ZPC<T>::NW, 1) k_zcrossp(PassArgs a) {
+  using P = ZPC<T>;
+  constexpr int M = P::M, TX = P::TX, LD = P::LD, NW = P::NW, ITEMS = P::ITEMS, V = M / 32;
+  constexpr size_t FS = Geometry<T, N>::FS;
+  constexpr int XT = N / TX, NT = XT * N;
+  static_assert(N == 1024 && TX == 8, "k_zcrossp is the FP32 N = 1024 z-pass");
+  static_assert((3 * ITEMS) % NW == 0 && (3 * TX) % NW == 0, "z tile split");
+  extern __shared__ unsigned char smraw[];
+  cx<T>* s = reinterpret_cast<cx<T>*>(smraw);
+  const cx<T>* tw = reinterpret_cast<const cx<T>*>(a.tw);
+  cx<T>* W = reinterpret_cast<cx<T>*>(a.W);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int kc = (a.kmax3 + 2) / 3;
+  if (kc > M) kc = M;
+  const int tx = lane % TX, kq = lane / TX;
+  // walk kz = 32 g + TX kq + c: padp(kz) = 34 g + padp(TX kq) + c
+  cx<T>* const sl = s + padp(TX * kq) * LD + tx;
+  const size_t lane_g = ((size_t)(TX * kq) * N) * N + tx;
+  auto fetch = [&](int t, int f0) {
+    const cx<T>* gl = W + lane_g + (size_t)(t / XT) * N + (t % XT) * TX;
+#pragma unroll 4
+    for (int it = w; it < 3 * ITEMS; it += NW) {
+      const int f = f0 + it / ITEMS, r = it % ITEMS, g = r / TX, c = r % TX;
+      cp_async<sizeof(cx<T>)>(sl + (34 * g + c) * LD + f * TX, gl + f * FS + (size_t)(32 * g + c) * N * N);
+    }
+  };
+  ZTw<T, N> zt;
+  zt.load(tw, lane);
+  auto c2r_lines = [&](int f0) {
+    cx<T> v[V];
+#pragma unroll 1
+    for (int l = f0 * TX + w; l < (f0 + 3) * TX; l += NW) {
+      cx<T>* ln = s + l;
+      zc_c2r<T, N, LD>(v, ln, zt, tw, lane);
+      cx<T>* pa = ln + padp(lane) * LD;
+#pragma unroll
+      for (int m = 0; m < V; ++m) pa[34 * m * LD] = v[m];
+    }
+  };
+
+  int t = blockIdx.x;
+  if (t < NT) fetch(t, 3);
+  cp_async_commit();
+  if (t < NT) fetch(t, 0);
+  cp_async_commit();
+#pragma unroll 1
+  for (; t < NT; t += gridDim.x) {
+    const int x0 = (t % XT) * TX, y = t / XT, tn = t + gridDim.x;
+    cp_async_wait<1>();  // omega fields of tile t
+    __syncthreads();
+    c2r_lines(3);
+    cp_async_wait<0>();  // u fields of tile t
+    __syncthreads();
+    c2r_lines(0);
+    __syncthreads();
+    for (int it = w; it < ITEMS; it += NW) {
+      const int g = it / TX, c = it % TX;
+      cx<T>* p = sl + (34 * g + c) * LD;
+      const cx<T> u0 = p[0 * TX], u1 = p[1 * TX], u2 = p[2 * TX];
+      const cx<T> w0 = p[3 * TX], w1v = p[4 * TX], w2 = p[5 * TX];
+      p[0 * TX] = mk(u1.x * w2.x - u2.x * w1v.x, u1.y * w2.y - u2.y * w1v.y);
+      p[1 * TX] = mk(u2.x * w0.x - u0.x * w2.x, u2.y * w0.y - u0.y * w2.y);
+      p[2 * TX] = mk(u0.x * w1v.x - u1.x * w0.x, u0.y * w1v.y - u1.y * w0.y);
+    }
+    __syncthreads();
+    if (tn < NT) fetch(tn, 3);
+    cp_async_commit();
+    {
+      cx<T> v[V];
+#pragma unroll 1
+      for (int l = w; l < 3 * TX; l += NW) {
+        cx<T>* ln = s + l;
+        const cx<T>* pa = ln + padp(lane) * LD;
+#pragma unroll
+        for (int m = 0; m < V; ++m) v[m] = pa[34 * m * LD];
+        __syncwarp();
+        zc_r2c<T, N, LD>(v, ln, ln, kc, zt, tw, lane);
+      }
+    }
+    __syncthreads();
+    cx<T>* gd = W + lane_g + (size_t)y * N + x0;
+    for (int it = w; it < 3 * ITEMS; it += NW) {
+      const int f = it / ITEMS, r = it % ITEMS, g = r / TX, c = r % TX;
+      if (32 * g + TX * kq + c < kc) gd[f * FS + (size_t)(32 * g + c) * N * N] = sl[(34 * g + c) * LD + f * TX];
+    }
+    __syncthreads();
+    if (tn < NT) fetch(tn, 0);
+    cp_async_commit();
+  }
+  cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------------------
 // FP64 spectral sums for the diagnostics (Parseval): per block
 //   sum w|u|^2, sum w|omega|^2, sum w Re(conj(u).omega), count of non-finite,
 // w = 1 at kz = 0 and 2 otherwise (half spectrum; kz = N/2 is zero).
@@ -1056,6 +1164,7 @@ struct SolverImpl {
     if constexpr (ZCross<T, N>::enabled) DNS_ATTR((k_zcross<T, N>), G::ZSMEM);
     if constexpr (N == 512) DNS_ATTR((k_zcross16<T, N>), G::ZSMEM);
     if constexpr (N == 512 && sizeof(T) == 4) DNS_ATTR((k_zcross16p<T, N>), Z16P<T>::SMEM);
+    if constexpr (N == 1024 && sizeof(T) == 4) DNS_ATTR((k_zcrossp<T, N>), ZPC<T>::SMEM);
     DNS_ATTR((k_zpass<T, N, ZM_STORE>), G::ZSMEM);
     DNS_ATTR((k_zpass<T, N, ZM_LOAD>), G::ZSMEM);
     DNS_ATTR((k_zpass<T, N, ZM_MAXABS>), G::ZSMEM);
@@ -1068,6 +1177,8 @@ struct SolverImpl {
       k_zcross16p<T, N><<<num_sms(), 32 * Z16P<T>::NW, Z16P<T>::SMEM, st>>>(a);
     else if constexpr (N == 512)
       k_zcross16<T, N><<<dim3(N / G::ZTX, N), 32 * Z16Warps<T, N>::value, G::ZSMEM, st>>>(a);
+    else if constexpr (N == 1024 && sizeof(T) == 4)
+      k_zcrossp<T, N><<<num_sms(), 32 * ZPC<T>::NW, ZPC<T>::SMEM, st>>>(a);
     else if constexpr (ZCross<T, N>::enabled)
       k_zcross<T, N><<<dim3(N / G::ZTX, N), 32 * ZCrossWarps<T, N>::value, G::ZSMEM, st>>>(a);
     else
