@@ -242,6 +242,13 @@ struct SLineConj {  // shared-memory line read conjugated (inverse DFT of staged
   static constexpr int off(int d) { return padp(d) * ES; }
   __device__ __forceinline__ cx<T> load(const cx<T>* q) const { return conjg(*q); }
 };
+template <typename T>
+struct SRow {  // unpadded contiguous line in shared memory (read only)
+  const cx<T>* s;
+  __device__ __forceinline__ const cx<T>* at(int p) const { return s + p; }
+  static constexpr int off(int d) { return d; }
+  __device__ __forceinline__ cx<T> load(const cx<T>* q) const { return *q; }
+};
 template <typename T, bool CONJ>
 struct GLoad {  // contiguous line in global memory
   const cx<T>* g;

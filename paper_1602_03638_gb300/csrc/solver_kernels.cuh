@@ -40,12 +40,17 @@ struct Geometry {
   static constexpr int M = N / 2;
   static constexpr size_t FS = (size_t)M * N * N;  // complex values per field
   static constexpr int CB = (int)sizeof(cx<T>);
-  // x-pass: one row (fixed kz, ky) per block, 6 padded line buffers; where it
-  // fits in 64 KB, 9 more unpadded rows receive the stage's state rows by
-  // cp.async together with the nonlinear-term rows (XPRE).
+  // x-pass: one row (fixed kz, ky) per block, 6 padded line buffers. The
+  // stage update (XPRE, where it fits in 100 KB) uses 3 padded lines (the
+  // nonlinear term, then u) and 9 unpadded rows that receive the stage's state
+  // rows by cp.async (then omega in rows 0-2 and the padded work lines of the
+  // omega transforms over rows 3-8).
+  // Where 6 padded lines and the 9 rows fit in 64 KB (XWIDE), omega keeps
+  // its own 3 padded lines instead (faster at N = 512 FP32).
   static constexpr int XLS = padded_len(N);
-  static constexpr int XST = (6 * XLS + 1) / 2 * 2;  // 16-byte aligned start of the state rows
-  static constexpr bool XPRE = (size_t)(XST + 9 * N) * CB <= 64 * 1024;
+  static constexpr bool XWIDE = (size_t)((6 * XLS + 1) / 2 * 2 + 9 * N) * CB <= 64 * 1024;
+  static constexpr int XST = ((XWIDE ? 6 : 3) * XLS + 1) / 2 * 2;  // 16-byte aligned start of the state rows
+  static constexpr bool XPRE = (size_t)(XST + 9 * N) * CB <= 100 * 1024;
   static constexpr size_t XSMEM = (size_t)6 * XLS * CB;
   static constexpr size_t XSMEM_ST = XPRE ? (size_t)(XST + 9 * N) * CB : XSMEM;  // XM_STAGE, XM_RHS
   // y-pass: YTX adjacent columns (128-byte rows up to N = 512, 64-byte at 1024).
@@ -244,13 +249,36 @@ __global__ void __launch_bounds__(XP_THREADS, (Geometry<T, N>::XMIN)) k_xpass(Pa
           U[FS + gi] = v1;
           U[2 * FS + gi] = v2;
         }
-        put_curl_lines<T>(s, pj, LS, v0, v1, v2, kx, kyv, kzv, sc);
+        if constexpr (G::XPRE && !G::XWIDE) {
+          // u into lines 0-2 (padded, where this thread read N_hat), omega into
+          // state rows 0-2 (unpadded, where this thread read the stage state)
+          const cx<T> s0 = scal(v0, sc), s1 = scal(v1, sc), s2 = scal(v2, sc);
+          s[0 * LS + pj] = conjg(s0);
+          s[1 * LS + pj] = conjg(s1);
+          s[2 * LS + pj] = conjg(s2);
+          st[0 * N + j] = conjg(mul_pi(mk(kyv * s2.x - kzv * s1.x, kyv * s2.y - kzv * s1.y)));
+          st[1 * N + j] = conjg(mul_pi(mk(kzv * s0.x - kx * s2.x, kzv * s0.y - kx * s2.y)));
+          st[2 * N + j] = conjg(mul_pi(mk(kx * s1.x - kyv * s0.x, kx * s1.y - kyv * s0.y)));
+        } else {
+          put_curl_lines<T>(s, pj, LS, v0, v1, v2, kx, kyv, kzv, sc);
+        }
       }
     }
     if constexpr (MODE == XM_STAGE) {
       __syncthreads();
-      const SLine<T, 1> line{s + warp * LS};
-      warp_fft<T, N, N>(line, line, GStore<T, true>{W + warp * FS + rb}, tw, lane);
+      if constexpr (G::XPRE && !G::XWIDE) {
+        if (warp < 3) {
+          const SLine<T, 1> line{s + warp * LS};
+          warp_fft<T, N, N>(line, line, GStore<T, true>{W + warp * FS + rb}, tw, lane);
+        } else {  // omega: from its unpadded row, through a padded work line over rows 3-8
+          const int c = warp - 3;
+          const SLine<T, 1> work{st + 3 * N + c * LS};
+          warp_fft<T, N, N>(SRow<T>{st + c * N}, work, GStore<T, true>{W + warp * FS + rb}, tw, lane);
+        }
+      } else {
+        const SLine<T, 1> line{s + warp * LS};
+        warp_fft<T, N, N>(line, line, GStore<T, true>{W + warp * FS + rb}, tw, lane);
+      }
     }
   } else if constexpr (MODE == XM_FWD_STORE) {
     if (warp < 3) {
