@@ -169,15 +169,24 @@ int dns_spectral_sums_noalloc(const void* uhat, int N, int dtype, double nu, dou
 
 /* ---- Ensembles (many independent runs of mixed grid sizes) ------------------
  * An ensemble owns `count` handles created as by dns_create(N[i], nu[i], dt[i],
- * dtype). dns_ensemble_step(e, n) advances every member by n RK4 steps; each
- * step is one launch of a CUDA graph whose member kernel chains are parallel
- * branches (default: one branch per member), so small members run
- * concurrently. dns_ensemble_tune times candidate branch counts and keeps the
- * fastest; it ADVANCES every member by 2 steps per candidate tried (the
- * count is returned in the members' time, dns_diag.t).
+ * dtype). dns_ensemble_step(e, n) advances every member by n RK4 steps (Sec. 3,
+ * Appendix driver, per member); each step is one launch of a CUDA graph.
+ * Schedule: with batching on (default), members of equal N (N <= 128),
+ * precision and dealias option are advanced together, one kernel launch per
+ * pass for up to min(max_batch, 32) members (their pointers and RK
+ * coefficients passed as kernel parameters); every batch, and every member that is not batched, is
+ * a parallel branch of the graph. With batching off (max_batch = 0) every
+ * member runs its own kernels and the members are spread over `streams`
+ * branches (0 = one branch per member). dns_ensemble_tune times a set of
+ * schedules (batched, and per-member over 1 .. count branches) on the actual
+ * members and keeps the fastest; it ADVANCES every member by 2 steps per
+ * schedule tried (the count is returned in the members' time, dns_diag.t) and
+ * writes the chosen branch count of the per-member schedule (0 when batched).
  * Members are ordinary handles for every other call (set_state, get_state,
  * diagnostics, ...) and all run on the ensemble's stream; do not destroy them
- * or change their stream. Results are identical to stepping each member alone. */
+ * or change their stream. Results are identical to stepping each member alone
+ * (the batched kernels run the same per-member arithmetic). Errors:
+ * DNS_ERR_ARG for bad arguments, DNS_ERR_CUDA/OOM from capture or launch. */
 typedef struct dns_ensemble dns_ensemble;
 int dns_ensemble_create(int count, const int* N, const double* nu, const double* dt, int dtype, dns_ensemble** out);
 int dns_ensemble_destroy(dns_ensemble* e);
@@ -185,6 +194,8 @@ int dns_ensemble_size(const dns_ensemble* e);
 int dns_ensemble_member(dns_ensemble* e, int i, dns_handle** member);
 int dns_ensemble_set_streams(dns_ensemble* e, int streams); /* 0 = one branch per member */
 int dns_ensemble_streams(const dns_ensemble* e);            /* branch count (0 = per member) */
+int dns_ensemble_set_batching(dns_ensemble* e, int max_batch); /* 0 = off; else members per launch */
+int dns_ensemble_batching(const dns_ensemble* e);              /* current max_batch (0 = off) */
 int dns_ensemble_tune(dns_ensemble* e, int* best_streams);  /* advances the members, see above */
 int dns_ensemble_step(dns_ensemble* e, int n);              /* asynchronous */
 int dns_ensemble_synchronize(dns_ensemble* e);

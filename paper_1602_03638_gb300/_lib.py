@@ -64,6 +64,8 @@ SIGNATURES = {
     "dns_ensemble_member": (_I, [_P, _I, ctypes.POINTER(_P)]),
     "dns_ensemble_set_streams": (_I, [_P, _I]),
     "dns_ensemble_streams": (_I, [_P]),
+    "dns_ensemble_set_batching": (_I, [_P, _I]),
+    "dns_ensemble_batching": (_I, [_P]),
     "dns_ensemble_tune": (_I, [_P, ctypes.POINTER(_I)]),
     "dns_transform_r2c": (_I, [_P, _P, _P]),
     "dns_transform_c2r": (_I, [_P, _P, _P]),

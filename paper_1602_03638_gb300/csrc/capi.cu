@@ -3,6 +3,7 @@
 // non-templated kernels (layout transposes, final diagnostic sum).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -654,6 +655,8 @@ int dns_debug_fail_alloc_after(int n) {
 // Ensembles: many independent handles (any mix of grid sizes) advanced by one
 // CUDA graph per step whose member chains are parallel branches over K streams.
 // ---------------------------------------------------------------------------
+constexpr int kEnsembleWholeGroups = 1 << 30;  // batch size meaning "whole group"
+
 struct dns_ensemble {
   std::vector<dns_handle*> m;
   cudaStream_t main = nullptr;
@@ -662,11 +665,22 @@ struct dns_ensemble {
   cudaEvent_t fork = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
-  int streams = 0;  // branches of the step graph; 0 = choose by timing at the first step
+  int streams = 0;  // per-member schedule: graph branches (0 = one per member)
+  int batch = kEnsembleWholeGroups;  // members per batched launch (0 = per-member schedule)
   bool dirty = true;
 };
 
 namespace {
+
+// A unit of the step graph: one member stepped by its own kernels, or a batch
+// of members of equal (N, precision, dealias rule) stepped by shared launches
+// (their stage arguments at hargs + offset, 4 consecutive arrays of `count`,
+// copied into the kernels' parameters at capture).
+struct EnsUnit {
+  int first = 0;   // single member index, or -1 for a batch
+  std::vector<int> members;
+  size_t offset = 0;
+};
 
 void ens_free_graph(dns_ensemble* e) {
   if (e->gexec) cudaGraphExecDestroy(e->gexec);
@@ -675,11 +689,65 @@ void ens_free_graph(dns_ensemble* e) {
   e->graph = nullptr;
 }
 
+// Work units of the current schedule: batches of at most e->batch members
+// (batch > 0) for every batchable (N, dtype, kmax3) group, singles otherwise.
+std::vector<EnsUnit> ens_units(const dns_ensemble* e) {
+  std::vector<EnsUnit> units;
+  const int n = (int)e->m.size();
+  std::vector<bool> done(n, false);
+  if (e->batch > 0) {
+    for (int i = 0; i < n; ++i) {
+      const dns_handle* h = e->m[i];
+      if (done[i] || !h->ops->rk_stage_batch) continue;
+      std::vector<int> group;
+      for (int j = i; j < n; ++j) {
+        const dns_handle* g = e->m[j];
+        if (!done[j] && g->ops == h->ops && g->variant == h->variant) {
+          group.push_back(j);
+          done[j] = true;
+        }
+      }
+      const size_t per = (size_t)std::min(e->batch, BATCH_MAX_COUNT);
+      for (size_t o = 0; o < group.size(); o += per) {
+        EnsUnit u;
+        u.first = -1;
+        const size_t end = std::min(group.size(), o + per);
+        u.members.assign(group.begin() + o, group.begin() + end);
+        if (u.members.size() == 1) u.first = u.members[0];
+        units.push_back(u);
+      }
+    }
+  }
+  for (int i = 0; i < n; ++i)
+    if (!done[i]) {
+      EnsUnit u;
+      u.first = i;
+      u.members.push_back(i);
+      units.push_back(u);
+    }
+  return units;
+}
+
 int ens_capture(dns_ensemble* e, int K) {
   ens_free_graph(e);
-  const int n = (int)e->m.size();
-  if (K < 1) K = 1;
-  if (K > n) K = n;
+  std::vector<EnsUnit> units = ens_units(e);
+  // stage arguments of the batched units, uploaded once per capture
+  std::vector<PassArgs> hargs;
+  for (EnsUnit& u : units) {
+    if (u.first >= 0) continue;
+    u.offset = hargs.size();
+    for (int s = 0; s < 4; ++s)
+      for (int i : u.members) {
+        const dns_handle* h = e->m[i];
+        PassArgs a = base_args(h);
+        a.stage = s;
+        a.cA = RK_A[s] * h->dt;
+        a.cB = s < 3 ? RK_B[s] * h->dt : 0.0;
+        hargs.push_back(a);
+      }
+  }
+  const int nu = (int)units.size();
+  if (K < 1 || K > nu) K = nu;
   while ((int)e->aux.size() < K) {
     cudaStream_t st;
     DNS_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "ensemble stream");
@@ -691,7 +759,18 @@ int ens_capture(dns_ensemble* e, int K) {
   DNS_CUDA(cudaStreamBeginCapture(e->main, cudaStreamCaptureModeThreadLocal), "ensemble capture begin");
   cudaError_t err = cudaEventRecord(e->fork, e->main);
   for (int k = 0; k < K && err == cudaSuccess; ++k) err = cudaStreamWaitEvent(e->aux[k], e->fork, 0);
-  for (int i = 0; i < n && err == cudaSuccess; ++i) err = enqueue_step(e->m[i], e->aux[i % K]);
+  for (int u = 0; u < nu && err == cudaSuccess; ++u) {
+    const EnsUnit& un = units[u];
+    cudaStream_t st = e->aux[u % K];
+    if (un.first >= 0) {
+      err = enqueue_step(e->m[un.first], st);
+    } else {
+      const dns_handle* h = e->m[un.members[0]];
+      const int cnt = (int)un.members.size();
+      for (int s = 0; s < 4 && err == cudaSuccess; ++s)
+        err = h->ops->rk_stage_batch(hargs.data() + un.offset + (size_t)s * cnt, cnt, h->N + 2 * h->variant, st);
+    }
+  }
   for (int k = 0; k < K && err == cudaSuccess; ++k) {
     err = cudaEventRecord(e->join[k], e->aux[k]);
     if (err == cudaSuccess) err = cudaStreamWaitEvent(e->main, e->join[k], 0);
@@ -705,7 +784,6 @@ int ens_capture(dns_ensemble* e, int K) {
   if (e2 != cudaSuccess) return cuda_fail(e2, "ensemble capture end");
   e->graph = g;
   DNS_CUDA(cudaGraphInstantiate(&e->gexec, e->graph, 0), "ensemble graph instantiate");
-  e->streams = K;
   e->dirty = false;
   return DNS_OK;
 }
@@ -783,6 +861,15 @@ int dns_ensemble_set_streams(dns_ensemble* e, int streams) {
   return DNS_OK;
 }
 
+int dns_ensemble_set_batching(dns_ensemble* e, int max_batch) {
+  if (!e || max_batch < 0) return fail(DNS_ERR_ARG, "dns_ensemble_set_batching: bad arguments");
+  e->batch = max_batch;
+  e->dirty = true;
+  return DNS_OK;
+}
+
+int dns_ensemble_batching(const dns_ensemble* e) { return e ? e->batch : 0; }
+
 int dns_ensemble_step(dns_ensemble* e, int n) {
   if (!e) return fail(DNS_ERR_ARG, "dns_ensemble_step: ensemble is NULL");
   if (n < 0) return fail(DNS_ERR_ARG, "dns_ensemble_step: n = %d < 0", n);
@@ -790,7 +877,7 @@ int dns_ensemble_step(dns_ensemble* e, int n) {
   int rc = ens_prepare_members(e);
   if (rc) return rc;
   if (e->dirty || !e->gexec) {
-    if ((rc = ens_capture(e, e->streams > 0 ? e->streams : (int)e->m.size()))) return rc;
+    if ((rc = ens_capture(e, e->streams))) return rc;
   }
   for (int i = 0; i < n; ++i) DNS_CUDA(cudaGraphLaunch(e->gexec, e->main), "ensemble graph launch");
   for (dns_handle* h : e->m) h->t += n * h->dt;
@@ -802,16 +889,23 @@ int dns_ensemble_tune(dns_ensemble* e, int* best_streams) {
   int rc = ens_prepare_members(e);
   if (rc) return rc;
   const int n = (int)e->m.size();
-  int cand[] = {1, 2, 4, 8, 16, 32, 64, 128, 256, 512};
+  // candidate schedules: batched launches (whole groups, then smaller batches,
+  // one graph branch per unit) and per-member launches over 1 .. n branches
+  struct Cand {
+    int batch, streams;
+  };
+  std::vector<Cand> cand = {{kEnsembleWholeGroups, 0}, {8, 0}};
+  for (int k = 1; k < 2 * n; k *= 4) cand.push_back({0, k < n ? k : n});
   float best = 1e30f;
-  int best_k = n;
+  Cand pick = cand[0];
   cudaEvent_t t0, t1;
   DNS_CUDA(cudaEventCreate(&t0), "tune event");
   DNS_CUDA(cudaEventCreate(&t1), "tune event");
   int taken = 0;
-  for (int K : cand) {
-    const int k = K > n ? n : K;
-    if ((rc = ens_capture(e, k))) break;
+  for (const Cand& c : cand) {
+    e->batch = c.batch;
+    e->streams = c.streams;
+    if ((rc = ens_capture(e, c.streams))) break;
     cudaError_t ce = cudaGraphLaunch(e->gexec, e->main);  // warm-up
     if (ce == cudaSuccess) ce = cudaEventRecord(t0, e->main);
     if (ce == cudaSuccess) ce = cudaGraphLaunch(e->gexec, e->main);
@@ -826,17 +920,17 @@ int dns_ensemble_tune(dns_ensemble* e, int* best_streams) {
     cudaEventElapsedTime(&ms, t0, t1);
     if (ms < best) {
       best = ms;
-      best_k = k;
+      pick = c;
     }
-    if (k == n) break;
   }
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
   for (dns_handle* h : e->m) h->t += taken * h->dt;
   if (rc) return rc;
-  e->streams = best_k;
+  e->batch = pick.batch;
+  e->streams = pick.streams;
   e->dirty = true;
-  if (best_streams) *best_streams = best_k;
+  if (best_streams) *best_streams = pick.streams;
   return DNS_OK;
 }
 

@@ -52,6 +52,17 @@ struct DnsOps {
   cudaError_t (*inverse3d)(const PassArgs& a, cudaStream_t s);
   // FP64 sums over U into a.partials (DIAG_BLOCKS x 4) and max|div u| into a.maxbits
   cudaError_t (*diag)(const PassArgs& a, cudaStream_t s);
+  // rk_stage for `count` <= BATCH_MAX_COUNT independent members at once (same
+  // N, precision and kmax3), their arguments in A[count]: one launch per pass,
+  // the arguments travelling as kernel parameters. nullptr where one member
+  // already fills the GPU (N > BATCH_MAX_N).
+  cudaError_t (*rk_stage_batch)(const PassArgs* A, int count, int kmax3, cudaStream_t s);
+};
+
+constexpr int BATCH_MAX_N = 128;
+constexpr int BATCH_MAX_COUNT = 32;
+struct BatchArgs {  // by-value kernel parameter (constant bank) of the batched passes
+  PassArgs a[BATCH_MAX_COUNT];
 };
 
 constexpr int DIAG_BLOCKS = 592;  // 4 x 148..152 SMs: one wave of 4 blocks per SM

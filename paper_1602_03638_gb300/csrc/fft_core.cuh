@@ -359,6 +359,75 @@ __device__ __forceinline__ void warp_fft(const Src& src, const Work& work, const
 }
 
 // ---------------------------------------------------------------------------
+// Several short lines per warp: G lines at s0 + g (g < G), element p of every
+// line at padded position padp(p) * LD, transformed in place. The butterflies
+// of all G lines of a pass are spread over the lanes (virtual butterfly
+// g * NB + j), so short lines whose passes have fewer butterflies than lanes
+// still keep the warp busy. Same radix plan and twiddles as warp_fft.
+// ---------------------------------------------------------------------------
+template <int L>
+struct LinesPerWarp {  // largest power of two G with G * (butterflies of pass 0) <= 32, at most 16
+  static constexpr int nb0 = L / WarpPlan<L>::radix(0);
+  static constexpr int value = nb0 >= 32 ? 1 : (nb0 >= 16 ? 2 : (nb0 >= 8 ? 4 : (nb0 >= 4 ? 8 : 16)));
+};
+
+template <typename T, int L, int TWN, int G, int LD, int P>
+__device__ __forceinline__ void warp_fft_lines_pass(cx<T>* s0, const cx<T>* __restrict__ tw, int lane) {
+  using PL = WarpPlan<L>;
+  constexpr int R = PL::radix(P);
+  constexpr int NS = PL::ns(P);
+  constexpr int NB = L / R;
+  constexpr int TOT = G * NB;
+  constexpr int BPL = (TOT + 31) / 32;
+  constexpr bool LAST = (P + 1 == PL::npass);
+  constexpr int TWC = TWN / (NS * R);
+  cx<T> v[BPL][R];
+#pragma unroll
+  for (int b = 0; b < BPL; ++b) {
+    const int vj = lane + 32 * b;
+    if (TOT % 32 == 0 || vj < TOT) {
+      const int g = vj / NB, j = vj % NB;
+      const cx<T>* ln = s0 + g;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[b][r] = ln[padp(j + r * NB) * LD];
+      if constexpr (NS > 1) {
+        if constexpr (sizeof(T) == 4) {
+          cx<T> w[R];
+          twiddle_powers<R>(ldro(tw + (j % NS) * TWC), w);
+#pragma unroll
+          for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], w[r]);
+        } else {
+          const int kc = (j % NS) * TWC;
+#pragma unroll
+          for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], ldro(tw + r * kc));
+        }
+      }
+      dft<R>(v[b]);
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int b = 0; b < BPL; ++b) {
+    const int vj = lane + 32 * b;
+    if (TOT % 32 == 0 || vj < TOT) {
+      const int g = vj / NB, j = vj % NB;
+      cx<T>* ln = s0 + g;
+      const int base = (j / NS) * NS * R + (j % NS);
+#pragma unroll
+      for (int r = 0; r < R; ++r) ln[padp(base + r * NS) * LD] = v[b][r];
+    }
+  }
+  __syncwarp();
+  if constexpr (!LAST) warp_fft_lines_pass<T, L, TWN, G, LD, P + 1>(s0, tw, lane);
+}
+
+// Forward DFT, in place, of the G lines s0 + g (see above) by one warp.
+template <typename T, int L, int TWN, int G, int LD>
+__device__ __forceinline__ void warp_fft_lines(cx<T>* s0, const cx<T>* __restrict__ tw, int lane) {
+  warp_fft_lines_pass<T, L, TWN, G, LD, 0>(s0, tw, lane);
+}
+
+// ---------------------------------------------------------------------------
 // Register-resident warp FFT ("canonical" layout): lane l holds positions
 // l + 32 m, m < L/32, in v[m]. Every pass reads its butterfly inputs from the
 // lane's own registers (positions j + r L/R with j = l + 32 b); the Stockham

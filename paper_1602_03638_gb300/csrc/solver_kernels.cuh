@@ -121,7 +121,7 @@ struct GStoreNyquistFree {
 // x-pass: one block owns one row (kz, ky) of length N; warp f transforms line f.
 // ---------------------------------------------------------------------------
 template <typename T, int N, int MODE>
-__global__ void __launch_bounds__(XP_THREADS, (Geometry<T, N>::XMIN)) k_xpass(PassArgs a) {
+__device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
   using G = Geometry<T, N>;
   constexpr int LS = G::XLS;
   constexpr size_t FS = G::FS;
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(XP_THREADS, (Geometry<T, N>::XMIN)) k_xpass(Pa
   cx<T>* US = reinterpret_cast<cx<T>*>(a.US);
   cx<T>* W = reinterpret_cast<cx<T>*>(a.W);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row = blockIdx.x;  // row = kz * N + ky
+  const int row = bx;  // row = kz * N + ky
   const int kz = row / N, ky = row % N;
   const size_t rb = (size_t)row * N;
   const T sc = (T)(1.0 / ((double)N * (double)N * (double)N));
@@ -315,6 +315,17 @@ __global__ void __launch_bounds__(XP_THREADS, (Geometry<T, N>::XMIN)) k_xpass(Pa
   }
 }
 
+template <typename T, int N, int MODE>
+__global__ void __launch_bounds__(XP_THREADS, (Geometry<T, N>::XMIN)) k_xpass(PassArgs a) {
+  xpass_body<T, N, MODE>(a, blockIdx.x);
+}
+
+// Batched form (ensembles): member blockIdx.y, its arguments in B.a[blockIdx.y].
+template <typename T, int N, int MODE>
+__global__ void __launch_bounds__(XP_THREADS, (Geometry<T, N>::XMIN)) k_xpass_b(const __grid_constant__ BatchArgs B) {
+  xpass_body<T, N, MODE>(B.a[blockIdx.y], blockIdx.x);
+}
+
 // ---------------------------------------------------------------------------
 // y-pass: one block owns YTX adjacent columns (fixed field and kz) of length N;
 // the tile is loaded with coalesced rows, each warp transforms whole columns.
@@ -322,9 +333,8 @@ __global__ void __launch_bounds__(XP_THREADS, (Geometry<T, N>::XMIN)) k_xpass(Pa
 // grid = (N / YTX, number of kz planes, number of fields)
 // ---------------------------------------------------------------------------
 template <typename T, int N, int INV, int PRUNE>
-__global__ void __launch_bounds__(32 * Geometry<T, N>::YTX, (Geometry<T, N>::YMIN)) k_ypass(cx<T>* __restrict__ F,
-                                                                                         const cx<T>* __restrict__ tw,
-                                                                                         int kmax3) {
+__device__ __forceinline__ void ypass_body(cx<T>* __restrict__ F, const cx<T>* __restrict__ tw, int kmax3,
+                                           const int bx, const int by, const int bz) {
   using G = Geometry<T, N>;
   constexpr int TX = G::YTX;
   constexpr int LD = G::YLD;
@@ -332,7 +342,7 @@ __global__ void __launch_bounds__(32 * Geometry<T, N>::YTX, (Geometry<T, N>::YMI
   extern __shared__ unsigned char smraw[];
   cx<T>* s = reinterpret_cast<cx<T>*>(smraw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  cx<T>* base = F + blockIdx.z * G::FS + (size_t)blockIdx.y * N * N + blockIdx.x * TX;
+  cx<T>* base = F + bz * G::FS + (size_t)by * N * N + bx * TX;
   // the whole tile in flight at once (cp.async, no register staging); the
   // inverse's conjugation is applied when the first pass reads it
 #pragma unroll 8
@@ -358,6 +368,22 @@ __global__ void __launch_bounds__(32 * Geometry<T, N>::YTX, (Geometry<T, N>::YMI
   }
 }
 
+template <typename T, int N, int INV, int PRUNE>
+__global__ void __launch_bounds__(32 * Geometry<T, N>::YTX, (Geometry<T, N>::YMIN)) k_ypass(cx<T>* __restrict__ F,
+                                                                                         const cx<T>* __restrict__ tw,
+                                                                                         int kmax3) {
+  ypass_body<T, N, INV, PRUNE>(F, tw, kmax3, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Batched form on the members' work arrays: blockIdx.z = member * fields + field.
+template <typename T, int N, int INV, int PRUNE>
+__global__ void __launch_bounds__(32 * Geometry<T, N>::YTX, (Geometry<T, N>::YMIN)) k_ypass_b(const __grid_constant__ BatchArgs B,
+                                                                                           int fields) {
+  const PassArgs& a = B.a[blockIdx.z / fields];
+  ypass_body<T, N, INV, PRUNE>(reinterpret_cast<cx<T>*>(a.W), reinterpret_cast<const cx<T>*>(a.tw), a.kmax3, blockIdx.x,
+                               blockIdx.y, blockIdx.z % fields);
+}
+
 // ---------------------------------------------------------------------------
 // z-pass: one block owns ZTX adjacent x at fixed y; lines run along kz / z.
 // Real transforms of length N use one complex DFT of length M = N/2 on
@@ -366,7 +392,7 @@ __global__ void __launch_bounds__(32 * Geometry<T, N>::YTX, (Geometry<T, N>::YMI
 // kz = N/2 coefficient is zero (it is not stored).
 // ---------------------------------------------------------------------------
 template <typename T, int N, int MODE>
-__global__ void __launch_bounds__(ZP_THREADS, (Geometry<T, N>::ZMIN)) k_zpass(PassArgs a) {
+__device__ __forceinline__ void zpass_body(const PassArgs a, const int bx, const int by) {
   using G = Geometry<T, N>;
   constexpr int M = G::M;
   constexpr int TX = G::ZTX;
@@ -377,8 +403,8 @@ __global__ void __launch_bounds__(ZP_THREADS, (Geometry<T, N>::ZMIN)) k_zpass(Pa
   cx<T>* s = reinterpret_cast<cx<T>*>(smraw);
   const cx<T>* tw = reinterpret_cast<const cx<T>*>(a.tw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int x0 = blockIdx.x * TX;
-  const int y = blockIdx.y;
+  const int x0 = bx * TX;
+  const int y = by;
 
   if constexpr (MODE == ZM_LOAD) {
     // physical lines (x0 + x, y, :) of the 3 components, packed in pairs
@@ -418,11 +444,9 @@ __global__ void __launch_bounds__(ZP_THREADS, (Geometry<T, N>::ZMIN)) k_zpass(Pa
       }
     }
     __syncthreads();
+    constexpr int GL = LinesPerWarp<M>::value <= TX ? LinesPerWarp<M>::value : TX;  // lines per warp
 #pragma unroll 1
-    for (int l = warp; l < NL; l += ZP_THREADS / 32) {
-      const SLine<T, LD> line{s + l};
-      warp_fft<T, M, N>(line, line, line, tw, lane);
-    }
+    for (int l = warp * GL; l < NL; l += (ZP_THREADS / 32) * GL) warp_fft_lines<T, M, N, GL, LD>(s + l, tw, lane);
     __syncthreads();
     // now conj(s) = x_{2n} + i x_{2n+1} (physical values, unnormalised c2r)
   }
@@ -442,11 +466,9 @@ __global__ void __launch_bounds__(ZP_THREADS, (Geometry<T, N>::ZMIN)) k_zpass(Pa
   }
 
   if constexpr (MODE == ZM_CROSS || MODE == ZM_LOAD) {
+    constexpr int GL = LinesPerWarp<M>::value <= TX ? LinesPerWarp<M>::value : TX;
 #pragma unroll 1
-    for (int l = warp; l < 3 * TX; l += ZP_THREADS / 32) {
-      const SLine<T, LD> line{s + l};
-      warp_fft<T, M, N>(line, line, line, tw, lane);
-    }
+    for (int l = warp * GL; l < 3 * TX; l += (ZP_THREADS / 32) * GL) warp_fft_lines<T, M, N, GL, LD>(s + l, tw, lane);
     __syncthreads();
     // r2c post-processing: X_k = 1/2 [(Z_k + conj Z_{M-k}) - i e^{-2 pi i k/N} (Z_k - conj Z_{M-k})]
     cx<T>* dst = reinterpret_cast<cx<T>*>(MODE == ZM_CROSS ? a.W : a.U);
@@ -486,6 +508,17 @@ __global__ void __launch_bounds__(ZP_THREADS, (Geometry<T, N>::ZMIN)) k_zpass(Pa
       atomicMax(a.maxbits, (unsigned long long)__double_as_longlong(m));
     }
   }
+}
+
+template <typename T, int N, int MODE>
+__global__ void __launch_bounds__(ZP_THREADS, (Geometry<T, N>::ZMIN)) k_zpass(PassArgs a) {
+  zpass_body<T, N, MODE>(a, blockIdx.x, blockIdx.y);
+}
+
+// Batched form (ensembles): member blockIdx.z.
+template <typename T, int N, int MODE>
+__global__ void __launch_bounds__(ZP_THREADS, (Geometry<T, N>::ZMIN)) k_zpass_b(const __grid_constant__ BatchArgs B) {
+  zpass_body<T, N, MODE>(B.a[blockIdx.z], blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -1196,6 +1229,12 @@ struct SolverImpl {
     DNS_ATTR((k_zpass<T, N, ZM_STORE>), G::ZSMEM);
     DNS_ATTR((k_zpass<T, N, ZM_LOAD>), G::ZSMEM);
     DNS_ATTR((k_zpass<T, N, ZM_MAXABS>), G::ZSMEM);
+    if constexpr (N <= BATCH_MAX_N && !ZCross<T, N>::enabled) {
+      DNS_ATTR((k_ypass_b<T, N, 1, 0>), G::YSMEM);
+      DNS_ATTR((k_zpass_b<T, N, ZM_CROSS>), G::ZSMEM);
+      DNS_ATTR((k_ypass_b<T, N, 0, 1>), G::YSMEM);
+      DNS_ATTR((k_xpass_b<T, N, XM_STAGE>), G::XSMEM_ST);
+    }
 #undef DNS_ATTR
     return e;
   }
@@ -1251,6 +1290,21 @@ struct SolverImpl {
     return cudaGetLastError();
   }
 
+  static cudaError_t rk_stage_batch(const PassArgs* A, int count, int kmax3, cudaStream_t st) {
+    if constexpr (N <= BATCH_MAX_N && N != 512 && N != 1024 && !ZCross<T, N>::enabled) {
+      if (count < 1 || count > BATCH_MAX_COUNT) return cudaErrorInvalidValue;
+      BatchArgs B;
+      for (int i = 0; i < count; ++i) B.a[i] = A[i];
+      k_ypass_b<T, N, 1, 0><<<dim3(N / G::YTX, M, 6 * count), 32 * G::YTX, G::YSMEM, st>>>(B, 6);
+      k_zpass_b<T, N, ZM_CROSS><<<dim3(N / G::ZTX, N, count), ZP_THREADS, G::ZSMEM, st>>>(B);
+      k_ypass_b<T, N, 0, 1><<<dim3(N / G::YTX, kc_of(kmax3), 3 * count), 32 * G::YTX, G::YSMEM, st>>>(B, 3);
+      k_xpass_b<T, N, XM_STAGE><<<dim3(M * N, count), XP_THREADS, G::XSMEM_ST, st>>>(B);
+      return cudaGetLastError();
+    } else {
+      return cudaErrorNotSupported;
+    }
+  }
+
   static cudaError_t rhs(const PassArgs& a, cudaStream_t st) {
     cudaError_t e = x_inverse_curl(a, 0, st);
     if (e != cudaSuccess) return e;
@@ -1289,9 +1343,10 @@ struct SolverImpl {
   }
 
   static const DnsOps* ops() {
-    static const DnsOps o = {N,        sizeof(T) == 4 ? 0 : 1, sizeof(cx<T>), &prepare,   &x_inverse_curl,
+    constexpr bool batched = N <= BATCH_MAX_N && !ZCross<T, N>::enabled;
+    static const DnsOps o = {N,         sizeof(T) == 4 ? 0 : 1, sizeof(cx<T>), &prepare,   &x_inverse_curl,
                              &rk_stage, &rk_stage_part,        &rhs,          &forward3d, &inverse3d,
-                             &diag};
+                             &diag,     batched ? &rk_stage_batch : nullptr};
     return &o;
   }
 };

@@ -188,11 +188,19 @@ class Ensemble:
     def step(self, n: int = 1):
         _lib.check(_lib.lib().dns_ensemble_step(self._e, int(n)), "dns_ensemble_step")
 
-    def tune(self) -> int:
-        """Pick the graph branch count by timing (advances every member, see include/dns.h)."""
+    def tune(self) -> dict:
+        """Pick the schedule (batching, branch count) by timing; advances every member (see include/dns.h)."""
         k = ctypes.c_int()
         _lib.check(_lib.lib().dns_ensemble_tune(self._e, ctypes.byref(k)), "dns_ensemble_tune")
-        return k.value
+        return {"batching": self.batching, "streams": k.value}
+
+    def set_batching(self, max_batch: int):
+        """0: every member runs its own kernels; n >= 1: up to n equal-size members share each launch."""
+        _lib.check(_lib.lib().dns_ensemble_set_batching(self._e, int(max_batch)), "dns_ensemble_set_batching")
+
+    @property
+    def batching(self) -> int:
+        return int(_lib.lib().dns_ensemble_batching(self._e))
 
     def set_streams(self, k: int):
         _lib.check(_lib.lib().dns_ensemble_set_streams(self._e, int(k)), "dns_ensemble_set_streams")

@@ -39,13 +39,15 @@ def _alone(N, nu, dt, dtype, uh, steps):
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
-@pytest.mark.parametrize("streams", [0, 1, 3])
-def test_ensemble_members_match_solo_runs_bitwise(dtype, streams):
-    Ns = [16, 24, 32, 48, 64, 32, 16]
+@pytest.mark.parametrize("batching,streams", [(0, 0), (0, 1), (0, 3), (1 << 30, 0), (2, 0), (2, 2)])
+def test_ensemble_members_match_solo_runs_bitwise(dtype, batching, streams):
+    # equal sizes with different nu and dt share batched launches (per-member arguments)
+    Ns = [16, 24, 32, 48, 64, 32, 16, 32]
     nus = [5e-3 + 1e-3 * i for i in range(len(Ns))]
     dts = [2e-3 * (1 + i % 2) for i in range(len(Ns))]
     ics = _ics(Ns, dtype)
     with Ensemble(Ns, nus, dts, dtype) as ens:
+        ens.set_batching(batching)
         ens.set_streams(streams)
         for m, uh in zip(ens.members, ics):
             m.set_state_spectral(uh)
@@ -72,14 +74,35 @@ def test_ensemble_member_matches_oracle():
         assert np.linalg.norm(got[i] - ref) / np.linalg.norm(ref) < 1e-12
 
 
-def test_ensemble_tune_advances_and_keeps_identity():
-    Ns = [16, 32, 24]
+def test_batched_groups_split_by_dealias_rule_and_size_limit():
+    # a member with the Appendix dealias rule and a 256^3 member (never batched)
+    # among batchable 32^3 members: every member still matches its solo run
+    Ns = [32, 32, 256, 32]
     ics = _ics(Ns, "f32")
-    with Ensemble(Ns, [0.01] * 3, [0.005] * 3, "f32") as ens:
+    with Ensemble(Ns, [0.01] * 4, [0.004] * 4, "f32") as ens:
+        ens.members[1].set_option("dealias_variant", 1)
         for m, uh in zip(ens.members, ics):
             m.set_state_spectral(uh)
-        k = ens.tune()
-        assert 1 <= k <= len(Ns) and ens.streams == k
+        ens.step(3)
+        got = [m.get_state_spectral() for m in ens.members]
+    for i, N in enumerate(Ns):
+        with Solver(N, 0.01, 0.004, "f32") as s:
+            if i == 1:
+                s.set_option("dealias_variant", 1)
+            s.set_state_spectral(ics[i])
+            s.step(3)
+            assert np.array_equal(got[i], s.get_state_spectral()), f"member {i} (N={N})"
+
+
+def test_ensemble_tune_advances_and_keeps_identity():
+    Ns = [16, 32, 24, 32]
+    ics = _ics(Ns, "f32")
+    with Ensemble(Ns, [0.01] * 4, [0.005] * 4, "f32") as ens:
+        for m, uh in zip(ens.members, ics):
+            m.set_state_spectral(uh)
+        pick = ens.tune()
+        assert pick["batching"] == ens.batching and pick["streams"] == ens.streams
+        assert pick["batching"] > 0 or 1 <= pick["streams"] <= len(Ns)
         taken = int(round(ens.members[0].diagnostics()["t"] / 0.005))
         assert taken >= 2 and taken % 2 == 0
         ens.step(2)
@@ -100,3 +123,5 @@ def test_ensemble_argument_errors():
             ens.step(-1)
         with pytest.raises(_lib.DnsError):
             ens.set_streams(-2)
+        with pytest.raises(_lib.DnsError):
+            ens.set_batching(-1)
