@@ -220,8 +220,16 @@ def run_form(torch, Solver, inputs, N, dtype, warm, steps):
         ms = time_steps(torch, s, st, steps) / steps
     rb = 4 if dtype == "f32" else 8
     model_ms = STEP_CV * cv_bytes(N, rb) / (measured_peaks()[0] * 1e9) * 1e3
-    return {"N": N, "dtype": dtype, "ms_per_step": ms, "value": N ** 3 / (ms * 1e-3), "steps": steps,
-            "hbm_roofline_frac_of_measured": model_ms / ms}
+    out = {"N": N, "dtype": dtype, "ms_per_step": ms, "value": N ** 3 / (ms * 1e-3), "steps": steps,
+           "hbm_roofline_frac_of_measured": model_ms / ms}
+    if dtype == "f64":
+        # FP64 arithmetic bound: ~270 N^3 log2 N flops per RK4 step (36 scalar 3D transforms,
+        # radix-2 count) against 152 SMs x 2 FP64 FMA/clock x 2 flops x 2.07 GHz = 1.26 TFLOP/s
+        flops = 270.0 * N ** 3 * math.log2(N)
+        peak = 152 * 2 * 2 * 2.07e9
+        out["roofline"] = {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": peak / 1e12,
+                           "unit": "TFLOP/s", "frac": flops / (ms * 1e-3) / peak, "flops_per_step": flops}
+    return out
 
 
 def run_ensemble(torch, np, steps=10):

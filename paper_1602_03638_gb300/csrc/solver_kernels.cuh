@@ -333,8 +333,9 @@ __global__ void __launch_bounds__(XP_THREADS, (Geometry<T, N>::XMIN)) k_xpass_b(
 // grid = (N / YTX, number of kz planes, number of fields)
 // ---------------------------------------------------------------------------
 template <typename T, int N, int INV, int PRUNE>
-__device__ __forceinline__ void ypass_body(cx<T>* __restrict__ F, const cx<T>* __restrict__ tw, int kmax3,
-                                           const int bx, const int by, const int bz) {
+__global__ void __launch_bounds__(32 * Geometry<T, N>::YTX, (Geometry<T, N>::YMIN)) k_ypass(cx<T>* __restrict__ F,
+                                                                                         const cx<T>* __restrict__ tw,
+                                                                                         int kmax3) {
   using G = Geometry<T, N>;
   constexpr int TX = G::YTX;
   constexpr int LD = G::YLD;
@@ -342,7 +343,7 @@ __device__ __forceinline__ void ypass_body(cx<T>* __restrict__ F, const cx<T>* _
   extern __shared__ unsigned char smraw[];
   cx<T>* s = reinterpret_cast<cx<T>*>(smraw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  cx<T>* base = F + bz * G::FS + (size_t)by * N * N + bx * TX;
+  cx<T>* base = F + blockIdx.z * G::FS + (size_t)blockIdx.y * N * N + blockIdx.x * TX;
   // the whole tile in flight at once (cp.async, no register staging); the
   // inverse's conjugation is applied when the first pass reads it
 #pragma unroll 8
@@ -368,20 +369,44 @@ __device__ __forceinline__ void ypass_body(cx<T>* __restrict__ F, const cx<T>* _
   }
 }
 
-template <typename T, int N, int INV, int PRUNE>
-__global__ void __launch_bounds__(32 * Geometry<T, N>::YTX, (Geometry<T, N>::YMIN)) k_ypass(cx<T>* __restrict__ F,
-                                                                                         const cx<T>* __restrict__ tw,
-                                                                                         int kmax3) {
-  ypass_body<T, N, INV, PRUNE>(F, tw, kmax3, blockIdx.x, blockIdx.y, blockIdx.z);
-}
-
-// Batched form on the members' work arrays: blockIdx.z = member * fields + field.
+// Batched form on the members' work arrays (ensembles): blockIdx.z = member *
+// fields + field; otherwise the same steps as k_ypass.
 template <typename T, int N, int INV, int PRUNE>
 __global__ void __launch_bounds__(32 * Geometry<T, N>::YTX, (Geometry<T, N>::YMIN)) k_ypass_b(const __grid_constant__ BatchArgs B,
                                                                                            int fields) {
+  using G = Geometry<T, N>;
+  constexpr int TX = G::YTX;
+  constexpr int LD = G::YLD;
+  constexpr int NT = 32 * TX;
+  extern __shared__ unsigned char smraw[];
+  cx<T>* s = reinterpret_cast<cx<T>*>(smraw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const PassArgs& a = B.a[blockIdx.z / fields];
-  ypass_body<T, N, INV, PRUNE>(reinterpret_cast<cx<T>*>(a.W), reinterpret_cast<const cx<T>*>(a.tw), a.kmax3, blockIdx.x,
-                               blockIdx.y, blockIdx.z % fields);
+  const cx<T>* tw = reinterpret_cast<const cx<T>*>(a.tw);
+  const int kmax3 = a.kmax3;
+  cx<T>* base = reinterpret_cast<cx<T>*>(a.W) + (blockIdx.z % fields) * G::FS + (size_t)blockIdx.y * N * N +
+                blockIdx.x * TX;
+#pragma unroll 8
+  for (int e = threadIdx.x; e < TX * N; e += NT) {
+    const int x = e % TX, y = e / TX;
+    cp_async<sizeof(cx<T>)>(s + padp(y) * LD + x, base + (size_t)y * N + x);
+  }
+  cp_async_commit();
+  cp_async_wait<0>();
+  __syncthreads();
+  {
+    const SLine<T, LD> line{s + warp};
+    if constexpr (INV) warp_fft<T, N, N>(SLineConj<T, LD>{s + warp}, line, line, tw, lane);
+    else warp_fft<T, N, N>(line, line, line, tw, lane);
+  }
+  __syncthreads();
+#pragma unroll 8
+  for (int e = threadIdx.x; e < TX * N; e += NT) {
+    const int x = e % TX, y = e / TX;
+    if (PRUNE && !kept(kfreq(y, N), kmax3)) continue;
+    const cx<T> v = s[padp(y) * LD + x];
+    base[(size_t)y * N + x] = INV ? conjg(v) : v;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -930,16 +955,20 @@ __global__ void __launch_bounds__(32 * Z16P<T>::NW, 1) k_zcross16p(PassArgs a) {
   // c2r of the TX lines of fields f0 .. f0+2, two lines per warp at a time
   HwTw<T> ht;
   ht.init(tw, h);
+  // partner X_{M-k} of k = h + 16 m sits at padded row padp(M - k) = pb0 + 17 (15 - m)
+  // with pb0 = 16 - h for h > 0 and 17 for h = 0 (k = 0 has no partner: X_M = 0)
+  const int pb0 = (h == 0) ? 17 : 16 - h;
   auto c2r_lines = [&](int f0) {
     cx<T> v[16];
 #pragma unroll 1
     for (int l = f0 * TX + 2 * w + half; l < (f0 + 3) * TX; l += 2 * NW) {
       cx<T>* ln = s + l;
       const cx<T>* pa = ln + h * LD;
+      const cx<T>* pb = ln + pb0 * LD;
 #pragma unroll
       for (int m = 0; m < 16; ++m) {
         const cx<T> xk = pa[17 * m * LD];
-        const cx<T> xm = (h == 0 && m == 0) ? mk((T)0, (T)0) : ln[padp(M - h - 16 * m) * LD];
+        const cx<T> xm = (h == 0 && m == 0) ? mk((T)0, (T)0) : pb[17 * (15 - m) * LD];
         cx<T> z;
         if (h == 0 && m == 0) {
           z = mk(xk.x, xk.x);  // Im X_0 ignored, X_M = 0
