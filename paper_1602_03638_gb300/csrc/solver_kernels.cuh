@@ -1281,6 +1281,18 @@ struct SolverImpl {
       k_zpass<T, N, ZM_CROSS><<<dim3(N / G::ZTX, N), ZP_THREADS, G::ZSMEM, st>>>(a);
   }
 
+  // shared memory of a stage-update launch: with the wide layout only the rows
+  // the stage reads are allocated (3 in stage 0, 6 in stage 3, 9 in stages 1-2),
+  // so the lighter stages keep more blocks per SM
+  static size_t xsmem_stage(int stage) {
+    if constexpr (G::XPRE && G::XWIDE) {
+      const int rows = stage == 0 ? 3 : (stage == 3 ? 6 : 9);
+      return (size_t)(G::XST + rows * N) * sizeof(cx<T>);
+    } else {
+      return G::XSMEM_ST;
+    }
+  }
+
   static int kc_of(int kmax3) {
     int kc = (kmax3 + 2) / 3;
     return kc > M ? M : kc;
@@ -1303,7 +1315,7 @@ struct SolverImpl {
 
   static cudaError_t rk_stage(const PassArgs& a, cudaStream_t st) {
     rhs_front(a, st);
-    k_xpass<T, N, XM_STAGE><<<M * N, XP_THREADS, G::XSMEM_ST, st>>>(a);
+    k_xpass<T, N, XM_STAGE><<<M * N, XP_THREADS, xsmem_stage(a.stage), st>>>(a);
     return cudaGetLastError();
   }
 
@@ -1314,7 +1326,7 @@ struct SolverImpl {
       case 0: k_ypass<T, N, 1, 0><<<dim3(N / G::YTX, M, 6), 32 * G::YTX, G::YSMEM, st>>>(W, tw, a.kmax3); break;
       case 1: z_cross(a, st); break;
       case 2: k_ypass<T, N, 0, 1><<<dim3(N / G::YTX, kc_of(a.kmax3), 3), 32 * G::YTX, G::YSMEM, st>>>(W, tw, a.kmax3); break;
-      default: k_xpass<T, N, XM_STAGE><<<M * N, XP_THREADS, G::XSMEM_ST, st>>>(a); break;
+      default: k_xpass<T, N, XM_STAGE><<<M * N, XP_THREADS, xsmem_stage(a.stage), st>>>(a); break;
     }
     return cudaGetLastError();
   }
@@ -1327,7 +1339,7 @@ struct SolverImpl {
       k_ypass_b<T, N, 1, 0><<<dim3(N / G::YTX, M, 6 * count), 32 * G::YTX, G::YSMEM, st>>>(B, 6);
       k_zpass_b<T, N, ZM_CROSS><<<dim3(N / G::ZTX, N, count), ZP_THREADS, G::ZSMEM, st>>>(B);
       k_ypass_b<T, N, 0, 1><<<dim3(N / G::YTX, kc_of(kmax3), 3 * count), 32 * G::YTX, G::YSMEM, st>>>(B, 3);
-      k_xpass_b<T, N, XM_STAGE><<<dim3(M * N, count), XP_THREADS, G::XSMEM_ST, st>>>(B);
+      k_xpass_b<T, N, XM_STAGE><<<dim3(M * N, count), XP_THREADS, xsmem_stage(A[0].stage), st>>>(B);
       return cudaGetLastError();
     } else {
       return cudaErrorNotSupported;
@@ -1340,7 +1352,7 @@ struct SolverImpl {
     rhs_front(a, st);
     PassArgs b = a;
     b.stage = 0;
-    k_xpass<T, N, XM_RHS><<<M * N, XP_THREADS, G::XSMEM_ST, st>>>(b);
+    k_xpass<T, N, XM_RHS><<<M * N, XP_THREADS, xsmem_stage(0), st>>>(b);
     return cudaGetLastError();
   }
 
