@@ -53,8 +53,10 @@ struct Geometry {
   static constexpr bool XPRE = (size_t)(XST + 9 * N) * CB <= 100 * 1024;
   static constexpr size_t XSMEM = (size_t)6 * XLS * CB;
   static constexpr size_t XSMEM_ST = XPRE ? (size_t)(XST + 9 * N) * CB : XSMEM;  // XM_STAGE, XM_RHS
-  // y-pass: YTX adjacent columns (128-byte rows up to N = 512, 64-byte at 1024).
-  static constexpr int YTX = cmin((N <= 512 ? 128 : 64) / CB, pow2_part(N));
+  // y-pass: YTX adjacent columns: 64-byte rows in FP32 (measured at 512^3: 64-byte
+  // tiles with 4 blocks per SM beat 128-byte tiles with 2 and 32-byte tiles with 8);
+  // FP64 keeps 128-byte rows up to N = 512.
+  static constexpr int YTX = cmin((CB == 16 && N <= 512 ? 128 : 64) / CB, pow2_part(N));
   static constexpr int YLD = odd_ld(YTX);
   static constexpr size_t YSMEM = (size_t)padded_len(N) * YLD * CB;
   // z-pass: ZTX adjacent x at fixed y, 6 fields of M values each, <= 112 KB
@@ -70,7 +72,7 @@ struct Geometry {
   // hold 32+ registers of data per lane in the warp FFT, so allow more registers.
   static constexpr int LINE_BYTES = N * CB;
   static constexpr int XMIN = LINE_BYTES > 4096 ? 2 : 4;
-  static constexpr int YMIN = 2;  // blocks of 32*YTX threads
+  static constexpr int YMIN = (CB == 8 && 32 * YTX <= 256 && N <= 512) ? 4 : 2;  // blocks of 32*YTX threads
   static constexpr int ZMIN = (M * CB > 4096) ? 1 : 2;
   static constexpr int ZLD = odd_ld(6 * ZTX);
   static constexpr size_t ZSMEM = zbytes(ZTX);
