@@ -759,8 +759,41 @@ struct HwTw {
   }
 };
 
-template <typename T, int TWN, int ES>
-__device__ __forceinline__ void hw_fft256(cx<T> (&v)[16], cx<T>* ln, const HwTw<T>& ht, const cx<T>* __restrict__ tw,
+// Leaner per-lane twiddles for the FP32 pipelined z-pass: the second-pass powers
+// p2[r] as in HwTw, and exp(-2 pi i (h + 16 m) / 512) formed on use as
+// tl * exp(-2 pi i m / 32) with the second factor a compile-time constant.
+struct HwTwL {
+  cx<float> p2[16];
+  cx<float> tl;
+  __device__ __forceinline__ void init(const cx<float>* __restrict__ tw, int h) {
+    twiddle_powers<16>(ldro(tw + 2 * h), p2);
+    tl = ldro(tw + h);
+  }
+  __device__ __forceinline__ cx<float> wk(const cx<float>* __restrict__, int, int m) const {
+    constexpr float c[16][2] = {
+        {1.0f, -0.0f},
+        {0.9807852804032304f, -0.19509032201612825f},
+        {0.9238795325112867f, -0.3826834323650898f},
+        {0.8314696123025452f, -0.5555702330196022f},
+        {0.7071067811865476f, -0.7071067811865475f},
+        {0.5555702330196023f, -0.8314696123025452f},
+        {0.38268343236508984f, -0.9238795325112867f},
+        {0.19509032201612833f, -0.9807852804032304f},
+        {0.0f, -1.0f},
+        {-0.1950903220161282f, -0.9807852804032304f},
+        {-0.3826834323650897f, -0.9238795325112867f},
+        {-0.555570233019602f, -0.8314696123025455f},
+        {-0.7071067811865475f, -0.7071067811865476f},
+        {-0.8314696123025453f, -0.5555702330196022f},
+        {-0.9238795325112867f, -0.3826834323650899f},
+        {-0.9807852804032304f, -0.1950903220161286f}
+    };
+    return m == 0 ? tl : cmul(tl, mk(c[m][0], c[m][1]));
+  }
+};
+
+template <typename T, int TWN, int ES, class HT>
+__device__ __forceinline__ void hw_fft256(cx<T> (&v)[16], cx<T>* ln, const HT& ht, const cx<T>* __restrict__ tw,
                                           int h) {
   dft16(v);
   cx<T>* q = ln + 17 * h * ES;
@@ -918,7 +951,7 @@ struct Z16P {
   static constexpr int M = 256;
   static constexpr int TX = 128 / (int)sizeof(cx<T>);  // 128-byte rows
   static constexpr int LD = odd_ld(6 * TX);
-  static constexpr int NW = 12;                        // warps per block
+  static constexpr int NW = 16;                        // warps per block
   static constexpr int ITEMS = (M / 32) * TX;          // walk items per field
   static constexpr size_t SMEM = (size_t)padded_len(M) * LD * sizeof(cx<T>);
 };
@@ -931,8 +964,7 @@ __global__ void __launch_bounds__(32 * Z16P<T>::NW, 1) k_zcross16p(PassArgs a) {
   constexpr int XT = N / TX, NT = XT * N;  // tiles: x-tiles times y
   static_assert(N == 512 && (TX == 8 || TX == 16), "k_zcross16p is the N = 512 z-pass");
   static_assert((3 * ITEMS) % NW == 0, "z tile load split");
-  static_assert((3 * TX) % (2 * NW) == 0, "line pairs per warp");
-  extern __shared__ unsigned char smraw[];
+    extern __shared__ unsigned char smraw[];
   cx<T>* s = reinterpret_cast<cx<T>*>(smraw);
   const cx<T>* tw = reinterpret_cast<const cx<T>*>(a.tw);
   cx<T>* W = reinterpret_cast<cx<T>*>(a.W);
@@ -955,7 +987,7 @@ __global__ void __launch_bounds__(32 * Z16P<T>::NW, 1) k_zcross16p(PassArgs a) {
     }
   };
   // c2r of the TX lines of fields f0 .. f0+2, two lines per warp at a time
-  HwTw<T> ht;
+  HwTwL ht;
   ht.init(tw, h);
   // partner X_{M-k} of k = h + 16 m sits at padded row padp(M - k) = pb0 + 17 (15 - m)
   // with pb0 = 16 - h for h > 0 and 17 for h = 0 (k = 0 has no partner: X_M = 0)

@@ -47,48 +47,60 @@ def test_rhs_of_random_full_spectrum_field_matches_oracle(N, dtype, tol):
 def _kvecs(N, dev):
     k = torch.fft.fftfreq(N, 1.0 / N, device=dev, dtype=torch.float64)
     kz = torch.arange(N // 2 + 1, device=dev, dtype=torch.float64)
-    return k[:, None, None], k[None, :, None], kz[None, None, :]
+    return k, kz
 
 
-def _inner(a, b, w):
-    """sum_k w_k Re(conj(a_k) . b_k) over the half spectrum, in FP64, one component at a time."""
-    return sum(float((w * (a[c].conj() * b[c]).real.to(torch.float64)).sum()) for c in range(3))
+def _slabs(N, step=64):
+    for a in range(0, N, step):
+        yield slice(a, min(N, a + step))
+
+
+@pytest.fixture(autouse=True)
+def _release_cached_memory():
+    yield
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
 
 
 def test_rhs_invariants_at_1024():
     N, dev = 1024, "cuda"
     uh = inputs.isotropic_spectral(N, seed=17, k0=N / 5.0, energy=1.0, device=dev).to(torch.complex64)
-    kx, ky, kz = _kvecs(N, dev)
-    w = torch.where(kz == 0, 1.0, 2.0).to(torch.float64)
     rhs0 = torch.empty_like(uh)
-    with Solver(N, 0.0, 1e-3, "f32") as s:
-        s.set_state_spectral(uh)
-        s.rhs(rhs0)
-    torch.cuda.synchronize()
-    # omega_hat = i k x u_hat (FP64 only where it is formed)
-    def comp(c):
-        return uh[c].to(torch.complex128)
-    wh = torch.stack([1j * (ky * comp(2) - kz * comp(1)), 1j * (kz * comp(0) - kx * comp(2)),
-                      1j * (kx * comp(1) - ky * comp(0))]).to(torch.complex64)
-    scale_e = sum(float((w * (uh[c].abs() * rhs0[c].abs()).to(torch.float64)).sum()) for c in range(3))
-    scale_h = sum(float((w * (wh[c].abs() * rhs0[c].abs()).to(torch.float64)).sum()) for c in range(3))
-    assert abs(_inner(uh, rhs0, w)) < 1e-5 * scale_e
-    assert abs(_inner(wh, rhs0, w)) < 1e-5 * scale_h
-    del wh
-    div = (kx * rhs0[0].to(torch.complex128) + ky * rhs0[1].to(torch.complex128) + kz * rhs0[2].to(torch.complex128)).abs().max()
-    kmag = torch.sqrt(kx ** 2 + ky ** 2 + kz ** 2)
-    assert float(div) < 1e-5 * float((kmag * rhs0.abs().max(dim=0).values).max())
-    # the term is not trivially zero: it is a sizeable fraction of the state
-    assert float(rhs0.abs().max()) > 1e-3 * float((kmag * uh.abs().max(dim=0).values).max())
-    nu = 0.01
     rhs1 = torch.empty_like(uh)
-    with Solver(N, nu, 1e-3, "f32") as s:
-        s.set_state_spectral(uh)
-        s.rhs(rhs1)
-    torch.cuda.synchronize()
-    k2 = (kx ** 2 + ky ** 2 + kz ** 2)
-    visc = rhs1.to(torch.complex128) - rhs0.to(torch.complex128) + nu * k2 * uh.to(torch.complex128)
-    # both right-hand sides round the same nonlinear term in FP32: the difference is exact
-    # up to one rounding of each
-    bound = 1e-5 * (float(rhs0.abs().max()) + float((nu * k2 * uh.abs().max(dim=0).values).max()))
-    assert float(visc.abs().max()) < bound
+    nu = 0.01
+    for visc, out in ((0.0, rhs0), (nu, rhs1)):
+        with Solver(N, visc, 1e-3, "f32") as s:
+            s.set_state_spectral(uh)
+            s.rhs(out)
+        torch.cuda.synchronize()
+    k, kz = _kvecs(N, dev)
+    w = torch.where(kz == 0, 1.0, 2.0).to(torch.float64)[None, None, :]
+    e_tr = h_tr = e_sc = h_sc = 0.0
+    div_max = div_sc = visc_max = nl_max = visc_sc = 0.0
+    for sl in _slabs(N):  # slabs of kx, everything in FP64
+        kx, ky, kzz = k[sl][:, None, None], k[None, :, None], kz[None, None, :]
+        u = [uh[c, sl].to(torch.complex128) for c in range(3)]
+        r0 = [rhs0[c, sl].to(torch.complex128) for c in range(3)]
+        om = [1j * (ky * u[2] - kzz * u[1]), 1j * (kzz * u[0] - kx * u[2]), 1j * (kx * u[1] - ky * u[0])]
+        e_tr += sum(float((w * (u[c].conj() * r0[c]).real).sum()) for c in range(3))
+        h_tr += sum(float((w * (om[c].conj() * r0[c]).real).sum()) for c in range(3))
+        e_sc += sum(float((w * u[c].abs() * r0[c].abs()).sum()) for c in range(3))
+        h_sc += sum(float((w * om[c].abs() * r0[c].abs()).sum()) for c in range(3))
+        kmag = torch.sqrt(kx ** 2 + ky ** 2 + kzz ** 2)
+        div_max = max(div_max, float((kx * r0[0] + ky * r0[1] + kzz * r0[2]).abs().max()))
+        div_sc = max(div_sc, float((kmag * torch.stack([r.abs() for r in r0]).max(dim=0).values).max()))
+        k2 = kmag ** 2
+        for c in range(3):
+            d = rhs1[c, sl].to(torch.complex128) - r0[c] + nu * k2 * u[c]
+            visc_max = max(visc_max, float(d.abs().max()))
+            visc_sc = max(visc_sc, float((nu * k2 * u[c].abs()).max()))
+            nl_max = max(nl_max, float(r0[c].abs().max()))
+    # no energy or helicity transfer, divergence-free
+    assert abs(e_tr) < 1e-5 * e_sc
+    assert abs(h_tr) < 1e-5 * h_sc
+    assert div_max < 1e-5 * div_sc
+    # the nonlinear term is not trivially small next to the viscous one
+    assert nl_max > 1e-3 * visc_sc
+    # both right-hand sides round the same nonlinear term in FP32: the difference is
+    # -nu |k|^2 u_hat up to one rounding of each
+    assert visc_max < 1e-5 * (nl_max + visc_sc)
