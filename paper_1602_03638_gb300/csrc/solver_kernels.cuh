@@ -334,6 +334,22 @@ __global__ void __launch_bounds__(XP_THREADS, (Geometry<T, N>::XMIN)) k_xpass_b(
 // INV: conj-in/conj-out (inverse DFT). PRUNE: store only rows with |ky| < N/3.
 // grid = (N / YTX, number of kz planes, number of fields)
 // ---------------------------------------------------------------------------
+// Row walked by tile element group r of the y-pass. With 8-byte values in
+// 8-wide rows (row stride 9 in shared memory) a warp covers 4 rows; rows y and
+// y + 1 in one half-warp share banks, rows y and y + 8 do not, so the walk takes
+// rows in the order 0, 8, 1, 9, 2, 10, ... within each block of 16 (a
+// permutation of 0 .. N-1 only when N is a multiple of 16; otherwise the rows
+// are walked in order).
+template <typename T, int TX, int N>
+__device__ __forceinline__ int ywalk_row(int r) {
+  if constexpr (sizeof(cx<T>) == 8 && TX == 8 && N % 16 == 0) {
+    const int t = r & 15, u = t >> 2, q = t & 3;
+    return (r & ~15) | (2 * u + (q >> 1) + (q & 1) * 8);
+  } else {
+    return r;
+  }
+}
+
 template <typename T, int N, int INV, int PRUNE>
 __global__ void __launch_bounds__(32 * Geometry<T, N>::YTX, (Geometry<T, N>::YMIN)) k_ypass(cx<T>* __restrict__ F,
                                                                                          const cx<T>* __restrict__ tw,
@@ -350,7 +366,7 @@ __global__ void __launch_bounds__(32 * Geometry<T, N>::YTX, (Geometry<T, N>::YMI
   // inverse's conjugation is applied when the first pass reads it
 #pragma unroll 8
   for (int e = threadIdx.x; e < TX * N; e += NT) {
-    const int x = e % TX, y = e / TX;
+    const int x = e % TX, y = ywalk_row<T, TX, N>(e / TX);
     cp_async<sizeof(cx<T>)>(s + padp(y) * LD + x, base + (size_t)y * N + x);
   }
   cp_async_commit();
@@ -364,7 +380,7 @@ __global__ void __launch_bounds__(32 * Geometry<T, N>::YTX, (Geometry<T, N>::YMI
   __syncthreads();
 #pragma unroll 8
   for (int e = threadIdx.x; e < TX * N; e += NT) {
-    const int x = e % TX, y = e / TX;
+    const int x = e % TX, y = ywalk_row<T, TX, N>(e / TX);
     if (PRUNE && !kept(kfreq(y, N), kmax3)) continue;
     const cx<T> v = s[padp(y) * LD + x];
     base[(size_t)y * N + x] = INV ? conjg(v) : v;
@@ -390,7 +406,7 @@ __global__ void __launch_bounds__(32 * Geometry<T, N>::YTX, (Geometry<T, N>::YMI
                 blockIdx.x * TX;
 #pragma unroll 8
   for (int e = threadIdx.x; e < TX * N; e += NT) {
-    const int x = e % TX, y = e / TX;
+    const int x = e % TX, y = ywalk_row<T, TX, N>(e / TX);
     cp_async<sizeof(cx<T>)>(s + padp(y) * LD + x, base + (size_t)y * N + x);
   }
   cp_async_commit();
@@ -404,7 +420,7 @@ __global__ void __launch_bounds__(32 * Geometry<T, N>::YTX, (Geometry<T, N>::YMI
   __syncthreads();
 #pragma unroll 8
   for (int e = threadIdx.x; e < TX * N; e += NT) {
-    const int x = e % TX, y = e / TX;
+    const int x = e % TX, y = ywalk_row<T, TX, N>(e / TX);
     if (PRUNE && !kept(kfreq(y, N), kmax3)) continue;
     const cx<T> v = s[padp(y) * LD + x];
     base[(size_t)y * N + x] = INV ? conjg(v) : v;
