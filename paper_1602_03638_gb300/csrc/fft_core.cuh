@@ -219,6 +219,30 @@ struct WarpPlan {
   }
 };
 
+// Radix schedule of the shared-memory warp FFT (warp_fft). For 8-byte values
+// and 512- or 1024-point lines the schedules (16, 16, 2) and (16, 16, 4) replace
+// the radix-8 ones: with the padded line layout (element stride 1 or any odd
+// stride) their reads and Stockham writes hit distinct banks in every pass,
+// while the radix-8 schedules' second-pass writes conflict two-way, and they
+// need slightly fewer operations per point. Other cases use WarpPlan.
+template <int L, int CB>
+struct SmemPlan : WarpPlan<L> {};
+template <int L, int R0, int R1, int R2>
+struct FixedPlan3 {
+  static constexpr int npass = 3;
+  static constexpr int radix(int p) { return p == 0 ? R0 : (p == 1 ? R1 : R2); }
+  static constexpr int ns(int p) {
+    int r = 1;
+    for (int q = 0; q < p; ++q) r *= radix(q);
+    return r;
+  }
+  static_assert(R0 * R1 * R2 == L, "plan covers the line");
+};
+template <>
+struct SmemPlan<512, 8> : FixedPlan3<512, 16, 16, 2> {};
+template <>
+struct SmemPlan<1024, 8> : FixedPlan3<1024, 16, 16, 4> {};
+
 template <int L>
 struct IsPow2 {
   static constexpr bool value = L > 0 && (L & (L - 1)) == 0;
@@ -270,7 +294,7 @@ struct GStore {
 template <typename T, int L, int TWN, int P, class Src, class Work, class Dst>
 __device__ __forceinline__ void warp_fft_pass(const Src& src, const Work& work, const Dst& dst,
                                               const cx<T>* __restrict__ tw, int lane) {
-  using PL = WarpPlan<L>;
+  using PL = SmemPlan<L, (int)sizeof(cx<T>)>;
   constexpr int R = PL::radix(P);
   constexpr int NS = PL::ns(P);
   constexpr int NB = L / R;
