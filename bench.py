@@ -21,6 +21,8 @@ Printed on rank 0 as one JSON line, with
                 precision against the FP64 CPU oracle at 128^3
   ensemble      128 members of mixed sizes: one graph launch per step versus
                 sequential per-member launches
+  cufft_comparison  the same step composed from torch.fft (cuFFT) and torch
+                elementwise calls (a library comparison, not the product path)
   closure       learned subgrid closure (512^3 DNS -> 64^3): training cost,
                 coarse-step cost and spectrum/dissipation error with and without it
   cpu_baseline  the FP64 CPU oracle timed on this host's cores
@@ -271,6 +273,66 @@ def run_ensemble(torch, np, steps=10):
             "timing": "host wall clock around K steps + stream synchronize"}
 
 
+def run_cufft_comparison(torch, N=N_MAIN, steps=3, warm=2):
+    """Library comparison (not the product path): the same RK4 step of the Taylor-Green case
+    written with torch.fft (cuFFT) transforms and torch elementwise operations in FP32 on the
+    GPU, the way the paper's NumPy code composes library calls; CUDA-event time per step."""
+    dev = "cuda"
+    k = torch.fft.fftfreq(N, 1.0 / N, device=dev)
+    kx, ky, kz = k[:, None, None], k[None, :, None], torch.arange(N // 2 + 1, device=dev, dtype=k.dtype)[None, None, :]
+    k2 = kx * kx + ky * ky + kz * kz
+    k2inv = torch.where(k2 == 0, torch.zeros_like(k2), 1.0 / k2)
+    mask = ((3 * kx.abs() < N) & (3 * ky.abs() < N) & (3 * kz.abs() < N)).to(torch.float32)
+
+    def rhs(uh):
+        u = torch.fft.irfftn(uh, s=(N, N, N), dim=(1, 2, 3))
+        wh = torch.stack([1j * (ky * uh[2] - kz * uh[1]), 1j * (kz * uh[0] - kx * uh[2]), 1j * (kx * uh[1] - ky * uh[0])])
+        w = torch.fft.irfftn(wh, s=(N, N, N), dim=(1, 2, 3))
+        del wh
+        c = torch.stack([u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]])
+        del u, w
+        nh = torch.fft.rfftn(c, dim=(1, 2, 3)) * mask
+        del c
+        p = (kx * nh[0] + ky * nh[1] + kz * nh[2]) * k2inv
+        nh[0] -= kx * p
+        nh[1] -= ky * p
+        nh[2] -= kz * p
+        return nh - NU * k2 * uh
+
+    a, b = (1 / 6, 1 / 3, 1 / 3, 1 / 6), (0.5, 0.5, 1.0)
+
+    def step(uh):
+        u0, u1 = uh, uh.clone()
+        for s in range(4):
+            d = rhs(uh)
+            if s < 3:
+                uh = u0 + (b[s] * DT) * d
+            u1 += (a[s] * DT) * d
+        return u1
+
+    from paper_1602_03638_gb300 import inputs
+
+    uh = torch.fft.rfftn(inputs.taylor_green_torch(N, device=dev, dtype=torch.float32), dim=(1, 2, 3))
+    for _ in range(warm):
+        uh = step(uh)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(steps):
+        uh = step(uh)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    energy = float(0.5 * (torch.fft.irfftn(uh, s=(N, N, N), dim=(1, 2, 3)) ** 2).sum(0).mean())
+    out = {"what": "torch.fft (cuFFT) + torch elementwise RK4 step, FP32, same workload", "N": N,
+           "ms_per_step": ms, "value": N ** 3 / (ms * 1e-3), "steps": steps, "energy_after": energy,
+           "steps_taken": warm + steps}
+    del uh
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_closure():
     """Learned subgrid closure: 512^3 FP32 DNS (this solver) -> box filter width 2 pi/64 -> 64^3,
     BF16 network trained on the GPU, coarse runs with and without it against the filtered DNS over
@@ -399,6 +461,7 @@ def run_ours(args):
             errs[dt_] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
         line["forms"] = forms
         line["ensemble"] = run_ensemble(torch, np)
+        line["cufft_comparison"] = run_cufft_comparison(torch)
         line["closure"] = run_closure()
         line["error_vs_oracle"] = {"case": f"Taylor-Green {CPU_N}^3, {CPU_STEPS} RK4 steps, nu=1/1600, dt=1e-3",
                                    "rel_l2_f32": errs["f32"], "rel_l2_f64": errs["f64"]}
