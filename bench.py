@@ -349,6 +349,21 @@ def run_closure():
     return out
 
 
+def combine_replicas(ms_local, steps, points, dist=None, device="cpu"):
+    """Replicas only: every rank steps its own independent copy of the workload. Returns the
+    maximum over ranks of the timed-region duration and the whole-job throughput (all ranks'
+    grid points x steps over that maximum)."""
+    import torch
+
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    world = 1
+    if dist is not None and dist.is_initialized():
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        world = dist.get_world_size()
+    ms_max = float(t.item())
+    return ms_max, world * points * steps / (ms_max * 1e-3)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -387,12 +402,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks = sampler.stop()
     barrier()
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max, value = combine_replicas(ms, args.steps, N ** 3, dist, "cuda")
     ms_step = ms_max / args.steps
-    value = world * N ** 3 * args.steps / (ms_max * 1e-3)
 
     # per-kernel CUDA-event timing of the same workload (eager launches)
     prof = s.profile_steps(args.steps)
