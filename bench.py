@@ -364,6 +364,12 @@ def combine_replicas(ms_local, steps, points, dist=None, device="cpu"):
     return ms_max, world * points * steps / (ms_max * 1e-3)
 
 
+def step_traffic(N, dtype):
+    """DRAM bytes per RK4 step from the per-launch ncu traffic (4 launches of each kernel), or None."""
+    parts = [ncu_traffic(k, N, dtype) for k in KERNEL_CV]
+    return None if any(p is None for p in parts) else 4.0 * sum(parts)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -433,7 +439,12 @@ def run_ours(args):
                      "algorithmic_bytes_per_launch": KERNEL_CV[dom] * cvb},
         "step_roofline": {"model_bytes_per_step": step_bytes, "achieved_GBps": step_bytes / (ms_step * 1e-3) / 1e9,
                           "frac_of_measured": step_bytes / (ms_step * 1e-3) / 1e9 / peak,
-                          "frac_of_spec_8TBps": step_bytes / (ms_step * 1e-3) / 1e9 / SPEC_HBM_GBS},
+                          "frac_of_spec_8TBps": step_bytes / (ms_step * 1e-3) / 1e9 / SPEC_HBM_GBS,
+                          # the 3-pass model (x, y and z transforms each a separate HBM sweep, 204 cv
+                          # per step): what the plane blocking of the 132-cv model would buy
+                          "frac_of_measured_3pass_model": 204.0 * cvb / (ms_step * 1e-3) / 1e9 / peak,
+                          # DRAM bytes this build's four passes move per step (ncu, profiles/)
+                          "dram_bytes_per_step_measured": step_traffic(N, dtype)},
         "kernels": kernels,
         "clocks": clocks,
     }
