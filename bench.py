@@ -50,8 +50,12 @@ METRIC = "grid-points x RK4 steps/s (Taylor-Green 512^3 FP32; FP64 and 1024^3 in
 UNIT = "points*steps/s"
 N_MAIN, NU, DT = 512, 1.0 / 1600.0, 1e-3
 SPEC_HBM_GBS = 8000.0
-# Bytes each kernel class must move per launch, in component-volumes
-# cv = N^2 (N/2+1) complex values ("Algorithmic bytes").
+# Bytes each kernel class must move per launch, in component-volumes cv = N^2 (N/2+1)
+# complex values: y-inverse reads and writes the 6 fields of u and omega (12); the z-pass
+# reads 6 and writes the 3 products (9); the y-forward reads and writes 3 (6); the x-stage
+# reads the 3 products and the stage state (6), writes u and omega (6) and moves 36 cv of
+# RK4 state per step, 9 per stage on average (21). STEP_CV: the fused two-pass model of one
+# RK4 step (x and y transforms in one sweep): 24 cv per stage plus 36 cv of RK4 state.
 KERNEL_CV = {"y_inverse": 12.0, "z_pass": 9.0, "y_forward": 6.0, "x_stage": 21.0}
 STEP_CV = 132.0
 CPU_N, CPU_STEPS = 128, 8
