@@ -967,7 +967,7 @@ struct Z16P {
   static constexpr int M = 256;
   static constexpr int TX = 128 / (int)sizeof(cx<T>);  // 128-byte rows
   static constexpr int LD = odd_ld(6 * TX);
-  static constexpr int NW = 16;                        // warps per block
+  static constexpr int NW = 24;                        // warps per block
   static constexpr int ITEMS = (M / 32) * TX;          // walk items per field
   static constexpr size_t SMEM = (size_t)padded_len(M) * LD * sizeof(cx<T>);
 };
