@@ -53,12 +53,6 @@ struct Geometry {
   static constexpr bool XPRE = (size_t)(XST + 9 * N) * CB <= 100 * 1024;
   static constexpr size_t XSMEM = (size_t)6 * XLS * CB;
   static constexpr size_t XSMEM_ST = XPRE ? (size_t)(XST + 9 * N) * CB : XSMEM;  // XM_STAGE, XM_RHS
-  // y-pass: YTX adjacent columns: 64-byte rows in FP32 (measured at 512^3: 64-byte
-  // tiles with 4 blocks per SM beat 128-byte tiles with 2 and 32-byte tiles with 8);
-  // FP64 keeps 128-byte rows up to N = 512.
-  static constexpr int YTX = cmin((CB == 16 && N <= 512 ? 128 : 64) / CB, pow2_part(N));
-  static constexpr int YLD = odd_ld(YTX);
-  static constexpr size_t YSMEM = (size_t)padded_len(N) * YLD * CB;
   // z-pass: ZTX adjacent x at fixed y, 6 fields of M values each, <= 112 KB
   // (two blocks per SM); rows narrower than one 32-byte sector may use up to 200 KB.
   static constexpr size_t zbytes(int t) { return (size_t)padded_len(M) * odd_ld(6 * t) * CB; }
@@ -72,10 +66,24 @@ struct Geometry {
   // hold 32+ registers of data per lane in the warp FFT, so allow more registers.
   static constexpr int LINE_BYTES = N * CB;
   static constexpr int XMIN = LINE_BYTES > 4096 ? 2 : 4;
-  static constexpr int YMIN = (CB == 8 && 32 * YTX <= 256 && N <= 512) ? 4 : 2;  // blocks of 32*YTX threads
   static constexpr int ZMIN = (M * CB > 4096) ? 1 : 2;
   static constexpr int ZLD = odd_ld(6 * ZTX);
   static constexpr size_t ZSMEM = zbytes(ZTX);
+};
+
+// Tile of the y-pass by direction. The inverse pass (6 full fields) takes 128-byte
+// rows in FP32 up to N = 512 with 8 warps looping over its 16 columns (3 blocks per
+// SM); the forward pass (3 fields, pruned) takes 64-byte rows, one warp per column, 4
+// blocks per SM (both measured at 512^3). FP64 keeps 128-byte rows up to N = 512,
+// 64-byte rows above.
+template <typename T, int N, int INV>
+struct YCfg {
+  static constexpr int CB = (int)sizeof(cx<T>);
+  static constexpr int TX = cmin(((INV || CB == 16) && N <= 512 ? 128 : 64) / CB, pow2_part(N));
+  static constexpr int THREADS = cmin(32 * TX, 256);
+  static constexpr int LD = odd_ld(TX);
+  static constexpr size_t SMEM = (size_t)padded_len(N) * LD * CB;
+  static constexpr int MINB = (CB == 8 && N <= 512) ? (INV ? 3 : 4) : 2;
 };
 
 __device__ __forceinline__ int kfreq(int i, int N) { return i < N / 2 ? i : i - N; }
@@ -329,10 +337,10 @@ __global__ void __launch_bounds__(XP_THREADS, (Geometry<T, N>::XMIN)) k_xpass_b(
 }
 
 // ---------------------------------------------------------------------------
-// y-pass: one block owns YTX adjacent columns (fixed field and kz) of length N;
+// y-pass: one block owns TX adjacent columns (fixed field and kz) of length N;
 // the tile is loaded with coalesced rows, each warp transforms whole columns.
 // INV: conj-in/conj-out (inverse DFT). PRUNE: store only rows with |ky| < N/3.
-// grid = (N / YTX, number of kz planes, number of fields)
+// grid = (N / TX, number of kz planes, number of fields); TX etc. from YCfg
 // ---------------------------------------------------------------------------
 // Row walked by tile element group r of the y-pass. With 8-byte values in
 // 8-wide rows (row stride 9 in shared memory) a warp covers 4 rows; rows y and
@@ -351,13 +359,14 @@ __device__ __forceinline__ int ywalk_row(int r) {
 }
 
 template <typename T, int N, int INV, int PRUNE>
-__global__ void __launch_bounds__(32 * Geometry<T, N>::YTX, (Geometry<T, N>::YMIN)) k_ypass(cx<T>* __restrict__ F,
+__global__ void __launch_bounds__(YCfg<T, N, INV>::THREADS, (YCfg<T, N, INV>::MINB)) k_ypass(cx<T>* __restrict__ F,
                                                                                          const cx<T>* __restrict__ tw,
                                                                                          int kmax3) {
   using G = Geometry<T, N>;
-  constexpr int TX = G::YTX;
-  constexpr int LD = G::YLD;
-  constexpr int NT = 32 * TX;  // one warp per column
+  using Y = YCfg<T, N, INV>;
+  constexpr int TX = Y::TX;
+  constexpr int LD = Y::LD;
+  constexpr int NT = Y::THREADS;  // warps loop over the columns
   extern __shared__ unsigned char smraw[];
   cx<T>* s = reinterpret_cast<cx<T>*>(smraw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -372,9 +381,10 @@ __global__ void __launch_bounds__(32 * Geometry<T, N>::YTX, (Geometry<T, N>::YMI
   cp_async_commit();
   cp_async_wait<0>();
   __syncthreads();
-  {
-    const SLine<T, LD> line{s + warp};
-    if constexpr (INV) warp_fft<T, N, N>(SLineConj<T, LD>{s + warp}, line, line, tw, lane);
+#pragma unroll 1
+  for (int c = warp; c < TX; c += NT / 32) {
+    const SLine<T, LD> line{s + c};
+    if constexpr (INV) warp_fft<T, N, N>(SLineConj<T, LD>{s + c}, line, line, tw, lane);
     else warp_fft<T, N, N>(line, line, line, tw, lane);
   }
   __syncthreads();
@@ -390,12 +400,13 @@ __global__ void __launch_bounds__(32 * Geometry<T, N>::YTX, (Geometry<T, N>::YMI
 // Batched form on the members' work arrays (ensembles): blockIdx.z = member *
 // fields + field; otherwise the same steps as k_ypass.
 template <typename T, int N, int INV, int PRUNE>
-__global__ void __launch_bounds__(32 * Geometry<T, N>::YTX, (Geometry<T, N>::YMIN)) k_ypass_b(const __grid_constant__ BatchArgs B,
+__global__ void __launch_bounds__(YCfg<T, N, INV>::THREADS, (YCfg<T, N, INV>::MINB)) k_ypass_b(const __grid_constant__ BatchArgs B,
                                                                                            int fields) {
   using G = Geometry<T, N>;
-  constexpr int TX = G::YTX;
-  constexpr int LD = G::YLD;
-  constexpr int NT = 32 * TX;
+  using Y = YCfg<T, N, INV>;
+  constexpr int TX = Y::TX;
+  constexpr int LD = Y::LD;
+  constexpr int NT = Y::THREADS;
   extern __shared__ unsigned char smraw[];
   cx<T>* s = reinterpret_cast<cx<T>*>(smraw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -412,9 +423,10 @@ __global__ void __launch_bounds__(32 * Geometry<T, N>::YTX, (Geometry<T, N>::YMI
   cp_async_commit();
   cp_async_wait<0>();
   __syncthreads();
-  {
-    const SLine<T, LD> line{s + warp};
-    if constexpr (INV) warp_fft<T, N, N>(SLineConj<T, LD>{s + warp}, line, line, tw, lane);
+#pragma unroll 1
+  for (int c = warp; c < TX; c += NT / 32) {
+    const SLine<T, LD> line{s + c};
+    if constexpr (INV) warp_fft<T, N, N>(SLineConj<T, LD>{s + c}, line, line, tw, lane);
     else warp_fft<T, N, N>(line, line, line, tw, lane);
   }
   __syncthreads();
@@ -1297,9 +1309,9 @@ struct SolverImpl {
     DNS_ATTR((k_xpass<T, N, XM_FWD_STORE>), G::XSMEM);
     DNS_ATTR((k_xpass<T, N, XM_INV_PLAIN>), G::XSMEM);
     DNS_ATTR((k_xpass<T, N, XM_INV_DIV>), G::XSMEM);
-    DNS_ATTR((k_ypass<T, N, 1, 0>), G::YSMEM);
-    DNS_ATTR((k_ypass<T, N, 0, 1>), G::YSMEM);
-    DNS_ATTR((k_ypass<T, N, 0, 0>), G::YSMEM);
+    DNS_ATTR((k_ypass<T, N, 1, 0>), (YCfg<T, N, 1>::SMEM));
+    DNS_ATTR((k_ypass<T, N, 0, 1>), (YCfg<T, N, 0>::SMEM));
+    DNS_ATTR((k_ypass<T, N, 0, 0>), (YCfg<T, N, 0>::SMEM));
     DNS_ATTR((k_zpass<T, N, ZM_CROSS>), G::ZSMEM);
     if constexpr (ZCross<T, N>::enabled) DNS_ATTR((k_zcross<T, N>), G::ZSMEM);
     if constexpr (N == 512) DNS_ATTR((k_zcross16<T, N>), G::ZSMEM);
@@ -1309,9 +1321,9 @@ struct SolverImpl {
     DNS_ATTR((k_zpass<T, N, ZM_LOAD>), G::ZSMEM);
     DNS_ATTR((k_zpass<T, N, ZM_MAXABS>), G::ZSMEM);
     if constexpr (N <= BATCH_MAX_N && !ZCross<T, N>::enabled) {
-      DNS_ATTR((k_ypass_b<T, N, 1, 0>), G::YSMEM);
+      DNS_ATTR((k_ypass_b<T, N, 1, 0>), (YCfg<T, N, 1>::SMEM));
       DNS_ATTR((k_zpass_b<T, N, ZM_CROSS>), G::ZSMEM);
-      DNS_ATTR((k_ypass_b<T, N, 0, 1>), G::YSMEM);
+      DNS_ATTR((k_ypass_b<T, N, 0, 1>), (YCfg<T, N, 0>::SMEM));
       DNS_ATTR((k_xpass_b<T, N, XM_STAGE>), G::XSMEM_ST);
     }
 #undef DNS_ATTR
@@ -1358,9 +1370,9 @@ struct SolverImpl {
   static void rhs_front(const PassArgs& a, cudaStream_t st) {
     cx<T>* W = reinterpret_cast<cx<T>*>(a.W);
     const cx<T>* tw = reinterpret_cast<const cx<T>*>(a.tw);
-    k_ypass<T, N, 1, 0><<<dim3(N / G::YTX, M, 6), 32 * G::YTX, G::YSMEM, st>>>(W, tw, a.kmax3);
+    k_ypass<T, N, 1, 0><<<dim3(N / YCfg<T, N, 1>::TX, M, 6), YCfg<T, N, 1>::THREADS, YCfg<T, N, 1>::SMEM, st>>>(W, tw, a.kmax3);
     z_cross(a, st);
-    k_ypass<T, N, 0, 1><<<dim3(N / G::YTX, kc_of(a.kmax3), 3), 32 * G::YTX, G::YSMEM, st>>>(W, tw, a.kmax3);
+    k_ypass<T, N, 0, 1><<<dim3(N / YCfg<T, N, 0>::TX, kc_of(a.kmax3), 3), YCfg<T, N, 0>::THREADS, YCfg<T, N, 0>::SMEM, st>>>(W, tw, a.kmax3);
   }
 
   static cudaError_t rk_stage(const PassArgs& a, cudaStream_t st) {
@@ -1373,9 +1385,9 @@ struct SolverImpl {
     cx<T>* W = reinterpret_cast<cx<T>*>(a.W);
     const cx<T>* tw = reinterpret_cast<const cx<T>*>(a.tw);
     switch (part) {
-      case 0: k_ypass<T, N, 1, 0><<<dim3(N / G::YTX, M, 6), 32 * G::YTX, G::YSMEM, st>>>(W, tw, a.kmax3); break;
+      case 0: k_ypass<T, N, 1, 0><<<dim3(N / YCfg<T, N, 1>::TX, M, 6), YCfg<T, N, 1>::THREADS, YCfg<T, N, 1>::SMEM, st>>>(W, tw, a.kmax3); break;
       case 1: z_cross(a, st); break;
-      case 2: k_ypass<T, N, 0, 1><<<dim3(N / G::YTX, kc_of(a.kmax3), 3), 32 * G::YTX, G::YSMEM, st>>>(W, tw, a.kmax3); break;
+      case 2: k_ypass<T, N, 0, 1><<<dim3(N / YCfg<T, N, 0>::TX, kc_of(a.kmax3), 3), YCfg<T, N, 0>::THREADS, YCfg<T, N, 0>::SMEM, st>>>(W, tw, a.kmax3); break;
       default: k_xpass<T, N, XM_STAGE><<<M * N, XP_THREADS, xsmem_stage(a.stage), st>>>(a); break;
     }
     return cudaGetLastError();
@@ -1386,9 +1398,9 @@ struct SolverImpl {
       if (count < 1 || count > BATCH_MAX_COUNT) return cudaErrorInvalidValue;
       BatchArgs B;
       for (int i = 0; i < count; ++i) B.a[i] = A[i];
-      k_ypass_b<T, N, 1, 0><<<dim3(N / G::YTX, M, 6 * count), 32 * G::YTX, G::YSMEM, st>>>(B, 6);
+      k_ypass_b<T, N, 1, 0><<<dim3(N / YCfg<T, N, 1>::TX, M, 6 * count), YCfg<T, N, 1>::THREADS, YCfg<T, N, 1>::SMEM, st>>>(B, 6);
       k_zpass_b<T, N, ZM_CROSS><<<dim3(N / G::ZTX, N, count), ZP_THREADS, G::ZSMEM, st>>>(B);
-      k_ypass_b<T, N, 0, 1><<<dim3(N / G::YTX, kc_of(kmax3), 3 * count), 32 * G::YTX, G::YSMEM, st>>>(B, 3);
+      k_ypass_b<T, N, 0, 1><<<dim3(N / YCfg<T, N, 0>::TX, kc_of(kmax3), 3 * count), YCfg<T, N, 0>::THREADS, YCfg<T, N, 0>::SMEM, st>>>(B, 3);
       k_xpass_b<T, N, XM_STAGE><<<dim3(M * N, count), XP_THREADS, xsmem_stage(A[0].stage), st>>>(B);
       return cudaGetLastError();
     } else {
@@ -1408,7 +1420,7 @@ struct SolverImpl {
 
   static cudaError_t forward3d(const PassArgs& a, cudaStream_t st) {
     k_zpass<T, N, ZM_LOAD><<<dim3(N / G::ZTX, N), ZP_THREADS, G::ZSMEM, st>>>(a);
-    k_ypass<T, N, 0, 0><<<dim3(N / G::YTX, M, 3), 32 * G::YTX, G::YSMEM, st>>>(
+    k_ypass<T, N, 0, 0><<<dim3(N / YCfg<T, N, 0>::TX, M, 3), YCfg<T, N, 0>::THREADS, YCfg<T, N, 0>::SMEM, st>>>(
         reinterpret_cast<cx<T>*>(a.U), reinterpret_cast<const cx<T>*>(a.tw), a.kmax3);
     k_xpass<T, N, XM_FWD_STORE><<<M * N, XP_THREADS, G::XSMEM, st>>>(a);
     return cudaGetLastError();
@@ -1416,7 +1428,7 @@ struct SolverImpl {
 
   static cudaError_t inverse3d(const PassArgs& a, cudaStream_t st) {
     k_xpass<T, N, XM_INV_PLAIN><<<M * N, XP_THREADS, G::XSMEM, st>>>(a);
-    k_ypass<T, N, 1, 0><<<dim3(N / G::YTX, M, 3), 32 * G::YTX, G::YSMEM, st>>>(
+    k_ypass<T, N, 1, 0><<<dim3(N / YCfg<T, N, 1>::TX, M, 3), YCfg<T, N, 1>::THREADS, YCfg<T, N, 1>::SMEM, st>>>(
         reinterpret_cast<cx<T>*>(a.W), reinterpret_cast<const cx<T>*>(a.tw), a.kmax3);
     k_zpass<T, N, ZM_STORE><<<dim3(N / G::ZTX, N), ZP_THREADS, G::ZSMEM, st>>>(a);
     return cudaGetLastError();
@@ -1426,7 +1438,7 @@ struct SolverImpl {
     k_diag<T, N><<<DIAG_BLOCKS, DG_THREADS, 0, st>>>(a);
     k_diag_final<<<1, 32, 0, st>>>(a.partials, DIAG_BLOCKS);
     k_xpass<T, N, XM_INV_DIV><<<M * N, XP_THREADS, G::XSMEM, st>>>(a);
-    k_ypass<T, N, 1, 0><<<dim3(N / G::YTX, M, 1), 32 * G::YTX, G::YSMEM, st>>>(
+    k_ypass<T, N, 1, 0><<<dim3(N / YCfg<T, N, 1>::TX, M, 1), YCfg<T, N, 1>::THREADS, YCfg<T, N, 1>::SMEM, st>>>(
         reinterpret_cast<cx<T>*>(a.D), reinterpret_cast<const cx<T>*>(a.tw), a.kmax3);
     cudaMemsetAsync(a.maxbits, 0, sizeof(unsigned long long), st);
     k_zpass<T, N, ZM_MAXABS><<<dim3(N / G::ZTX, N), ZP_THREADS, G::ZSMEM, st>>>(a);
