@@ -1,0 +1,100 @@
+"""Host checks of the kernels' index maps (restated from solver_kernels.cuh): every tile walk
+touches each element of its tile exactly once and stays inside its shared-memory allocation,
+for every compiled grid size and precision. A walk that leaves its tile faults the GPU, so
+these run on the CPU first."""
+
+import pytest
+
+SIZES = (8, 12, 16, 24, 32, 48, 64, 96, 128, 256, 512, 1024)
+
+
+def padp(p):
+    return p + (p >> 4)
+
+
+def padded_len(L):
+    return L + L // 16 + 1
+
+
+def pow2_part(n):
+    r = 1
+    while n % (r * 2) == 0:
+        r *= 2
+    return r
+
+
+def odd_ld(lines):
+    return lines if lines % 2 else lines + 1
+
+
+def ycfg(N, cb, inv):
+    tx = min(((128 if (inv or cb == 16) and N <= 512 else 64)) // cb, pow2_part(N))
+    return tx, odd_ld(tx), padded_len(N) * odd_ld(tx)
+
+
+def ywalk_row(r, cb, tx, N):
+    if cb == 8 and tx == 8 and N % 16 == 0:
+        t = r & 15
+        u, q = t >> 2, t & 3
+        return (r & ~15) | (2 * u + (q >> 1) + (q & 1) * 8)
+    return r
+
+
+@pytest.mark.parametrize("cb", [8, 16])
+@pytest.mark.parametrize("inv", [0, 1])
+@pytest.mark.parametrize("N", SIZES)
+def test_y_tile_walk_is_a_bijection_inside_the_tile(N, cb, inv):
+    tx, ld, tile = ycfg(N, cb, inv)
+    seen = set()
+    for e in range(tx * N):
+        x, y = e % tx, ywalk_row(e // tx, cb, tx, N)
+        assert 0 <= y < N
+        pos = padp(y) * ld + x
+        assert 0 <= pos < tile
+        seen.add((y, x))
+    assert len(seen) == tx * N
+
+
+def test_z512_tile_walk_covers_the_tile_once():
+    # k_zcross16p: kz = 32 g + TX kq + c (g < 8, c < TX, kq = lane / TX), padp(kz) = 34 g + padp(TX kq) + c
+    M, TX = 256, 16
+    LD = odd_ld(6 * TX)
+    seen = set()
+    for lane in range(32):
+        tx, kq = lane % TX, lane // TX
+        for g in range(M // 32):
+            for c in range(TX):
+                kz = 32 * g + TX * kq + c
+                assert padp(kz) == 34 * g + padp(TX * kq) + c
+                for f in range(6):
+                    pos = padp(kz) * LD + f * TX + tx
+                    assert pos < padded_len(M) * LD
+                    seen.add((kz, f, tx))
+    assert len(seen) == M * 6 * TX
+
+
+def test_z512_c2r_partner_rows():
+    # partner X_{M-k} of k = h + 16 m at padded row pb0 + 17 (15 - m)
+    M = 256
+    for h in range(16):
+        pb0 = 17 if h == 0 else 16 - h
+        for m in range(16):
+            if h == 0 and m == 0:
+                continue  # X_M = 0, not read
+            assert padp(M - h - 16 * m) == pb0 + 17 * (15 - m)
+            assert pb0 + 17 * (15 - m) < padded_len(M)
+
+
+@pytest.mark.parametrize("cb", [8, 16])
+@pytest.mark.parametrize("N", SIZES)
+def test_x_stage_staged_rows_fit(N, cb):
+    xls = padded_len(N)
+    wide = ((6 * xls + 1) // 2 * 2 + 9 * N) * cb <= 64 * 1024
+    xst = ((6 if wide else 3) * xls + 1) // 2 * 2
+    pre = (xst + 9 * N) * cb <= 100 * 1024
+    if not pre:
+        return
+    assert (xst * cb) % 16 == 0  # 16-byte cp.async destinations
+    if not wide:
+        # omega's padded work lines lie over the consumed U1 / U rows 3..8
+        assert 3 * N + 3 * xls <= 9 * N
