@@ -133,6 +133,46 @@ __device__ __forceinline__ void dft16(cx<T>* v) {
   }
 }
 
+// 32-point DFT in place: two 16-point DFTs of the even and odd elements
+// combined with exp(-2 pi i k / 32) (exact constants).
+template <typename T>
+__device__ __forceinline__ void dft32(cx<T>* v) {
+  constexpr double c32[16][2] = {
+      {1.0, 0.0},
+      {0.9807852804032304, -0.19509032201612825},
+      {0.9238795325112867, -0.3826834323650898},
+      {0.8314696123025452, -0.5555702330196022},
+      {0.7071067811865476, -0.7071067811865475},
+      {0.5555702330196023, -0.8314696123025452},
+      {0.38268343236508984, -0.9238795325112867},
+      {0.19509032201612833, -0.9807852804032304},
+      {0.0, -1.0},
+      {-0.1950903220161282, -0.9807852804032304},
+      {-0.3826834323650897, -0.9238795325112867},
+      {-0.555570233019602, -0.8314696123025455},
+      {-0.7071067811865475, -0.7071067811865476},
+      {-0.8314696123025453, -0.5555702330196022},
+      {-0.9238795325112867, -0.3826834323650899},
+      {-0.9807852804032304, -0.1950903220161286}};
+  cx<T> e[16], o[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    e[k] = v[2 * k];
+    o[k] = v[2 * k + 1];
+  }
+  dft16(e);
+  dft16(o);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    cx<T> t;
+    if (k == 0) t = o[0];
+    else if (k == 8) t = mul_mi(o[8]);
+    else t = cmul(o[k], mk((T)c32[k][0], (T)c32[k][1]));
+    v[k] = e[k] + t;
+    v[k + 16] = e[k] - t;
+  }
+}
+
 template <int R, typename T>
 __device__ __forceinline__ void dft(cx<T>* v) {
   if constexpr (R == 2) dft2(v);
@@ -140,6 +180,7 @@ __device__ __forceinline__ void dft(cx<T>* v) {
   else if constexpr (R == 4) dft4(v);
   else if constexpr (R == 8) dft8(v);
   else if constexpr (R == 16) dft16(v);
+  else if constexpr (R == 32) dft32(v);
   else static_assert(R == 2, "unsupported radix");
 }
 

@@ -1116,14 +1116,97 @@ __global__ void __launch_bounds__(32 * Z16P<T>::NW, 1) k_zcross16p(PassArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Pipelined z-pass for N = 1024 (lines of M = 512 values, FP32): the schedule
-// of k_zcross16p (persistent block, whole tile in shared memory, next tile's
-// omega fields fetched during the product transforms and its u fields during
-// the omega transforms) with 8 adjacent x per tile (64-byte rows: the widest
-// six 512-value lines fit) and one warp per line (canonical register FFT).
+// Half-warp 512-point FFT for the N = 1024 z-pass (FP32). Lane h of a half-warp
+// holds v[m] = x[h + 16 m], m < 32. With k = k1 + 32 k2: a 32-point DFT over m in
+// each lane gives Y[h][k1]; after the twiddle exp(-2 pi i h k1 / 512) one
+// shared-memory exchange (stores at 33 h + k1, loads at 33 h + h' and
+// 33 h + h' + 16: conflict-free for any odd element stride) gives lane h' the
+// 16-point columns k1 = h' and h' + 16, whose DFTs over h leave
+// v[j] = X[h' + 16 j] in the lane: the input layout again.
 // ---------------------------------------------------------------------------
+struct HwTw32 {
+  cx<float> p[16];  // w^r, w = exp(-2 pi i h / 512), r < 16
+  cx<float> q[16];  // w^(16 + r)
+  cx<float> tl;     // exp(-2 pi i h / 1024)
+  __device__ __forceinline__ void init(const cx<float>* __restrict__ tw, int h) {
+    twiddle_powers<16>(ldro(tw + 2 * h), p);
+    p[0] = mk(1.f, 0.f);
+    const cx<float> w16 = cmul(p[8], p[8]);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) q[r] = r == 0 ? w16 : cmul(w16, p[r]);
+    tl = ldro(tw + h);
+  }
+  // exp(-2 pi i (h + 16 m) / 1024) = tl * exp(-2 pi i m / 64)
+  __device__ __forceinline__ cx<float> wk(int m) const {
+    constexpr float c[32][2] = {
+      {1.0f, 0.0f},
+      {0.9951847266721969f, -0.0980171403295606f},
+      {0.9807852804032304f, -0.19509032201612825f},
+      {0.9569403357322088f, -0.29028467725446233f},
+      {0.9238795325112867f, -0.3826834323650898f},
+      {0.881921264348355f, -0.47139673682599764f},
+      {0.8314696123025452f, -0.5555702330196022f},
+      {0.773010453362737f, -0.6343932841636455f},
+      {0.7071067811865476f, -0.7071067811865475f},
+      {0.6343932841636455f, -0.773010453362737f},
+      {0.5555702330196023f, -0.8314696123025452f},
+      {0.4713967368259978f, -0.8819212643483549f},
+      {0.38268343236508984f, -0.9238795325112867f},
+      {0.29028467725446233f, -0.9569403357322089f},
+      {0.19509032201612833f, -0.9807852804032304f},
+      {0.09801714032956077f, -0.9951847266721968f},
+      {0.0f, -1.0f},
+      {-0.09801714032956065f, -0.9951847266721969f},
+      {-0.1950903220161282f, -0.9807852804032304f},
+      {-0.29028467725446216f, -0.9569403357322089f},
+      {-0.3826834323650897f, -0.9238795325112867f},
+      {-0.4713967368259977f, -0.881921264348355f},
+      {-0.555570233019602f, -0.8314696123025455f},
+      {-0.6343932841636454f, -0.7730104533627371f},
+      {-0.7071067811865475f, -0.7071067811865476f},
+      {-0.773010453362737f, -0.6343932841636455f},
+      {-0.8314696123025453f, -0.5555702330196022f},
+      {-0.8819212643483549f, -0.47139673682599786f},
+      {-0.9238795325112867f, -0.3826834323650899f},
+      {-0.9569403357322088f, -0.2902846772544624f},
+      {-0.9807852804032304f, -0.1950903220161286f},
+      {-0.9951847266721968f, -0.09801714032956083f}};
+    return m == 0 ? tl : cmul(tl, mk(c[m][0], c[m][1]));
+  }
+};
+
+template <int ES>
+__device__ __forceinline__ void hw_fft512(cx<float> (&v)[32], cx<float>* ln, const HwTw32& ht, int h) {
+  dft32(v);
+#pragma unroll
+  for (int k = 1; k < 32; ++k) v[k] = cmul(v[k], k < 16 ? ht.p[k] : ht.q[k - 16]);
+  cx<float>* q = ln + 33 * h * ES;
+#pragma unroll
+  for (int k = 0; k < 32; ++k) q[k * ES] = v[k];
+  __syncwarp();
+  cx<float> a[16], b[16];
+  const cx<float>* rb = ln + h * ES;
+#pragma unroll
+  for (int g = 0; g < 16; ++g) {
+    a[g] = rb[33 * g * ES];
+    b[g] = rb[(33 * g + 16) * ES];
+  }
+  __syncwarp();
+  dft16(a);
+  dft16(b);
+#pragma unroll
+  for (int k2 = 0; k2 < 16; ++k2) {
+    v[2 * k2] = a[k2];
+    v[2 * k2 + 1] = b[k2];
+  }
+}
+
+// Pipelined z-pass for N = 1024, FP32, with half-warp lines: the schedule of
+// k_zcross16p (persistent block, whole tile in shared memory, next tile's omega
+// fields fetched during the product transforms, its u fields during the omega
+// transforms) on tiles of 8 adjacent x (64-byte rows) and 512-value lines.
 template <typename T>
-struct ZPC {
+struct Z32P {
   static constexpr int M = 512;
   static constexpr int TX = 64 / (int)sizeof(cx<T>);
   static constexpr int LD = odd_ld(6 * TX);
@@ -1133,18 +1216,20 @@ struct ZPC {
 };
 
 template <typename T, int N>
-__global__ void __launch_bounds__(32 * ZPC<T>::NW, 1) k_zcrossp(PassArgs a) {
-  using P = ZPC<T>;
-  constexpr int M = P::M, TX = P::TX, LD = P::LD, NW = P::NW, ITEMS = P::ITEMS, V = M / 32;
-  constexpr size_t FS = Geometry<T, N>::FS;
+__global__ void __launch_bounds__(32 * Z32P<T>::NW, 1) k_zcross32p(PassArgs a) {
+  using P = Z32P<T>;
+  using G = Geometry<T, N>;
+  constexpr int M = P::M, TX = P::TX, LD = P::LD, NW = P::NW, ITEMS = P::ITEMS;
+  constexpr size_t FS = G::FS;
   constexpr int XT = N / TX, NT = XT * N;
-  static_assert(N == 1024 && TX == 8, "k_zcrossp is the FP32 N = 1024 z-pass");
-  static_assert((3 * ITEMS) % NW == 0 && (3 * TX) % NW == 0, "z tile split");
+  static_assert(N == 1024 && sizeof(T) == 4 && TX == 8, "k_zcross32p is the FP32 N = 1024 z-pass");
+  static_assert((3 * ITEMS) % NW == 0 && (3 * TX) % (2 * NW) == 0, "z tile split");
   extern __shared__ unsigned char smraw[];
   cx<T>* s = reinterpret_cast<cx<T>*>(smraw);
   const cx<T>* tw = reinterpret_cast<const cx<T>*>(a.tw);
   cx<T>* W = reinterpret_cast<cx<T>*>(a.W);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int h = lane & 15, half = lane >> 4;
   int kc = (a.kmax3 + 2) / 3;
   if (kc > M) kc = M;
   const int tx = lane % TX, kq = lane / TX;
@@ -1159,17 +1244,36 @@ __global__ void __launch_bounds__(32 * ZPC<T>::NW, 1) k_zcrossp(PassArgs a) {
       cp_async<sizeof(cx<T>)>(sl + (34 * g + c) * LD + f * TX, gl + f * FS + (size_t)(32 * g + c) * N * N);
     }
   };
-  ZTw<T, N> zt;
-  zt.load(tw, lane);
+  HwTw32 ht;
+  ht.init(tw, h);
+  // partner X_{M-k} of k = h + 16 m at padded row pb0 + 17 (31 - m), pb0 = 16 - h (h > 0), 17 (h = 0)
+  const int pb0 = (h == 0) ? 17 : 16 - h;
   auto c2r_lines = [&](int f0) {
-    cx<T> v[V];
+    cx<T> v[32];
 #pragma unroll 1
-    for (int l = f0 * TX + w; l < (f0 + 3) * TX; l += NW) {
+    for (int l = f0 * TX + 2 * w + half; l < (f0 + 3) * TX; l += 2 * NW) {
       cx<T>* ln = s + l;
-      zc_c2r<T, N, LD>(v, ln, zt, tw, lane);
-      cx<T>* pa = ln + padp(lane) * LD;
+      const cx<T>* pa = ln + h * LD;
+      const cx<T>* pb = ln + pb0 * LD;
 #pragma unroll
-      for (int m = 0; m < V; ++m) pa[34 * m * LD] = v[m];
+      for (int m = 0; m < 32; ++m) {
+        const cx<T> xk = pa[17 * m * LD];
+        cx<T> z;
+        if (h == 0 && m == 0) {
+          z = mk(xk.x, xk.x);  // Im X_0 ignored, X_M = 0
+        } else {
+          const cx<T> xm = pb[17 * (31 - m) * LD];
+          const cx<T> wk = ht.wk(m);
+          const cx<T> A = xk + conjg(xm), B = xk - conjg(xm);
+          z = A + mul_pi(cmul(conjg(wk), B));
+        }
+        v[m] = conjg(z);
+      }
+      __syncwarp();
+      hw_fft512<LD>(v, ln, ht, h);
+      cx<T>* pw = ln + h * LD;
+#pragma unroll
+      for (int m = 0; m < 32; ++m) pw[17 * m * LD] = conjg(v[m]);
     }
   };
 
@@ -1198,18 +1302,30 @@ __global__ void __launch_bounds__(32 * ZPC<T>::NW, 1) k_zcrossp(PassArgs a) {
       p[2 * TX] = mk(u0.x * w1v.x - u1.x * w0.x, u0.y * w1v.y - u1.y * w0.y);
     }
     __syncthreads();
-    if (tn < NT) fetch(tn, 3);
+    if (tn < NT) fetch(tn, 3);  // the omega lines are free
     cp_async_commit();
     {
-      cx<T> v[V];
+      cx<T> v[32];
 #pragma unroll 1
-      for (int l = w; l < 3 * TX; l += NW) {
+      for (int l = 2 * w + half; l < 3 * TX; l += 2 * NW) {
         cx<T>* ln = s + l;
-        const cx<T>* pa = ln + padp(lane) * LD;
+        const cx<T>* pa = ln + h * LD;
 #pragma unroll
-        for (int m = 0; m < V; ++m) v[m] = pa[34 * m * LD];
+        for (int m = 0; m < 32; ++m) v[m] = pa[17 * m * LD];
         __syncwarp();
-        zc_r2c<T, N, LD>(v, ln, ln, kc, zt, tw, lane);
+        hw_fft512<LD>(v, ln, ht, h);
+        cx<T>* po = ln + h * LD;
+        const int partner = (16 - h) & 15;
+#pragma unroll
+        for (int m = 0; m < 32; ++m) {
+          cx<T> zo;
+          zo.x = __shfl_sync(0xffffffffu, v[31 - m].x, partner, 16);
+          zo.y = __shfl_sync(0xffffffffu, v[31 - m].y, partner, 16);
+          if (h == 0) zo = v[(32 - m) & 31];
+          const cx<T> wk = ht.wk(m);
+          const cx<T> A = v[m] + conjg(zo), B = v[m] - conjg(zo);
+          if (h + 16 * m < kc) po[17 * m * LD] = scal(A + mul_mi(cmul(wk, B)), (T)0.5);
+        }
       }
     }
     __syncthreads();
@@ -1218,7 +1334,7 @@ __global__ void __launch_bounds__(32 * ZPC<T>::NW, 1) k_zcrossp(PassArgs a) {
       const int f = it / ITEMS, r = it % ITEMS, g = r / TX, c = r % TX;
       if (32 * g + TX * kq + c < kc) gd[f * FS + (size_t)(32 * g + c) * N * N] = sl[(34 * g + c) * LD + f * TX];
     }
-    __syncthreads();
+    __syncthreads();  // the u lines have been read out
     if (tn < NT) fetch(tn, 0);
     cp_async_commit();
   }
@@ -1316,7 +1432,7 @@ struct SolverImpl {
     if constexpr (ZCross<T, N>::enabled) DNS_ATTR((k_zcross<T, N>), G::ZSMEM);
     if constexpr (N == 512) DNS_ATTR((k_zcross16<T, N>), G::ZSMEM);
     if constexpr (N == 512 && sizeof(T) == 4) DNS_ATTR((k_zcross16p<T, N>), Z16P<T>::SMEM);
-    if constexpr (N == 1024 && sizeof(T) == 4) DNS_ATTR((k_zcrossp<T, N>), ZPC<T>::SMEM);
+    if constexpr (N == 1024 && sizeof(T) == 4) DNS_ATTR((k_zcross32p<T, N>), Z32P<T>::SMEM);
     DNS_ATTR((k_zpass<T, N, ZM_STORE>), G::ZSMEM);
     DNS_ATTR((k_zpass<T, N, ZM_LOAD>), G::ZSMEM);
     DNS_ATTR((k_zpass<T, N, ZM_MAXABS>), G::ZSMEM);
@@ -1336,7 +1452,7 @@ struct SolverImpl {
     else if constexpr (N == 512)
       k_zcross16<T, N><<<dim3(N / G::ZTX, N), 32 * Z16Warps<T, N>::value, G::ZSMEM, st>>>(a);
     else if constexpr (N == 1024 && sizeof(T) == 4)
-      k_zcrossp<T, N><<<num_sms(), 32 * ZPC<T>::NW, ZPC<T>::SMEM, st>>>(a);
+      k_zcross32p<T, N><<<num_sms(), 32 * Z32P<T>::NW, Z32P<T>::SMEM, st>>>(a);
     else if constexpr (ZCross<T, N>::enabled)
       k_zcross<T, N><<<dim3(N / G::ZTX, N), 32 * ZCrossWarps<T, N>::value, G::ZSMEM, st>>>(a);
     else
