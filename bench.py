@@ -17,7 +17,7 @@ Printed on rank 0 as one JSON line, with
                 bytes per launch over its mean CUDA-event duration) against
                 the measured copy bandwidth
   step_roofline the whole step against the 132-component-volume minimum
-  forms         FP64 at 512^3 and FP32 at 1024^3, and the error of each
+  forms         FP64 at 512^3, FP32 at 1024^3, both at 256^3, and the error of each
                 precision against the FP64 CPU oracle at 128^3
   ensemble      128 members of mixed sizes: one graph launch per step versus
                 sequential per-member launches
@@ -475,7 +475,8 @@ def run_ours(args):
                            "d2h_bytes_per_step": (ph + args.steps * 5 * 8) / args.steps,
                            "final_energy": d["energy"]}
         # precision forms
-        forms = [run_form(torch, Solver, inputs, 512, "f64", 2, 3), run_form(torch, Solver, inputs, 1024, "f32", 2, 3)]
+        forms = [run_form(torch, Solver, inputs, 512, "f64", 2, 3), run_form(torch, Solver, inputs, 1024, "f32", 2, 3),
+                 run_form(torch, Solver, inputs, 256, "f32", 3, 20), run_form(torch, Solver, inputs, 256, "f64", 2, 5)]
         # CPU oracle baseline and error of each GPU precision against it
         secs, ref, cores = oracle_sample(CPU_N, CPU_STEPS, NU, DT)
         errs = {}

@@ -670,8 +670,9 @@ __device__ __forceinline__ void zc_r2c(cx<T> (&c)[N / 64], cx<T>* scratch, cx<T>
 // Warps per z-cross block: 6 ZTX c2r lines and 3 ZTX r2c lines split evenly
 // (4 and 2 per warp).
 template <typename T, int N>
-struct ZCrossWarps {
-  static constexpr int value = (3 * Geometry<T, N>::ZTX) / 2 >= 1 ? (3 * Geometry<T, N>::ZTX) / 2 : 1;
+struct ZCrossWarps {  // at most 12, so that two blocks share an SM and overlap load and transform
+  static constexpr int full = (3 * Geometry<T, N>::ZTX) / 2 >= 1 ? (3 * Geometry<T, N>::ZTX) / 2 : 1;
+  static constexpr int value = full > 12 ? 12 : full;
 };
 
 // Tile element walk for the z-cross block (load, cross product, store): one
