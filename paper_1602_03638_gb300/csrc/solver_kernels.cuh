@@ -1343,6 +1343,153 @@ __global__ void __launch_bounds__(32 * Z32P<T>::NW, 1) k_zcross32p(PassArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Quarter-warp 128-point FFT for the N = 256 z-pass (FP32): lane h < 8 of a
+// quarter-warp holds v[m] = x[h + 8 m], m < 16; a 16-point DFT in each lane, the
+// twiddle exp(-2 pi i h k1 / 128), one exchange through positions 17 h + k1 and two
+// 8-point DFTs per lane leave v[j] = X[h + 8 j] in the lane. The two quarter-warps of
+// a half-warp work on lines l and l + 8, whose banks are disjoint. The twiddles are
+// those of the 256-point half-warp transform (HwTwL) on the N = 256 table.
+// ---------------------------------------------------------------------------
+template <int ES>
+__device__ __forceinline__ void qw_fft128(cx<float> (&v)[16], cx<float>* ln, const HwTwL& qt, int h) {
+  dft16(v);
+#pragma unroll
+  for (int k = 1; k < 16; ++k) v[k] = cmul(v[k], qt.p2[k]);
+  cx<float>* q = ln + 17 * h * ES;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) q[k * ES] = v[k];
+  __syncwarp();
+  cx<float> a[8], b[8];
+  const cx<float>* rb = ln + h * ES;
+#pragma unroll
+  for (int g = 0; g < 8; ++g) {
+    a[g] = rb[17 * g * ES];
+    b[g] = rb[(17 * g + 8) * ES];
+  }
+  __syncwarp();
+  dft8(a);
+  dft8(b);
+#pragma unroll
+  for (int k2 = 0; k2 < 8; ++k2) {
+    v[2 * k2] = a[k2];
+    v[2 * k2 + 1] = b[k2];
+  }
+}
+
+template <typename T>
+struct Z8Q {
+  static constexpr int M = 128;
+  static constexpr int TX = 128 / (int)sizeof(cx<T>);  // 128-byte rows
+  static constexpr int LD = odd_ld(6 * TX);
+  static constexpr int NW = 12;
+  static constexpr int ITEMS = (M / 32) * TX;
+  static constexpr size_t SMEM = (size_t)padded_len(M) * LD * sizeof(cx<T>);
+};
+
+// z-pass for N = 256, FP32: one tile (16 adjacent x at fixed y, 6 fields of 128
+// values) per block, fetched whole by cp.async, two blocks per SM; each warp
+// transforms four lines at once as quarter-warps (lines b, b + 8, b + 1, b + 9).
+template <typename T, int N>
+__global__ void __launch_bounds__(32 * Z8Q<T>::NW, 2) k_zcross8q(PassArgs a) {
+  using P = Z8Q<T>;
+  using G = Geometry<T, N>;
+  constexpr int M = P::M, TX = P::TX, LD = P::LD, NW = P::NW, ITEMS = P::ITEMS;
+  constexpr size_t FS = G::FS;
+  static_assert(N == 256 && sizeof(T) == 4 && TX == 16, "k_zcross8q is the FP32 N = 256 z-pass");
+  static_assert((6 * ITEMS) % NW == 0, "z tile split");
+  extern __shared__ unsigned char smraw[];
+  cx<T>* s = reinterpret_cast<cx<T>*>(smraw);
+  const cx<T>* tw = reinterpret_cast<const cx<T>*>(a.tw);
+  cx<T>* W = reinterpret_cast<cx<T>*>(a.W);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int h = lane & 7, qw = lane >> 3;
+  const int x0 = blockIdx.x * TX, y = blockIdx.y;
+  int kc = (a.kmax3 + 2) / 3;
+  if (kc > M) kc = M;
+  const int tx = lane % TX, kq = lane / TX;
+  // walk kz = 32 g + TX kq + c: padp(kz) = 34 g + padp(TX kq) + c
+  cx<T>* const sl = s + padp(TX * kq) * LD + tx;
+  const cx<T>* gl = W + ((size_t)(TX * kq) * N + y) * N + x0 + tx;
+#pragma unroll 4
+  for (int it = w; it < 6 * ITEMS; it += NW) {
+    const int f = it / ITEMS, r = it % ITEMS, g = r / TX, c = r % TX;
+    cp_async<sizeof(cx<T>)>(sl + (34 * g + c) * LD + f * TX, gl + f * FS + (size_t)(32 * g + c) * N * N);
+  }
+  cp_async_commit();
+  HwTwL qt;  // w = exp(-2 pi i h / 128), tl = exp(-2 pi i h / 256)
+  qt.init(tw, h);
+  // quarter-warp line of group gi (groups of 4 lines b, b + 8, b + 1, b + 9 with b = 16 f + 2 i)
+  auto line_of = [&](int gi) { return 16 * (gi >> 2) + 2 * (gi & 3) + (qw & 1) * 8 + (qw >> 1); };
+  cp_async_wait<0>();
+  __syncthreads();
+  {
+    cx<T> v[16];
+#pragma unroll 1
+    for (int gi = w; gi < 6 * 4; gi += NW) {  // c2r of the 96 lines
+      cx<T>* ln = s + line_of(gi);
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        const int k = h + 8 * m;
+        const cx<T> xk = ln[padp(k) * LD];
+        cx<T> z;
+        if (h == 0 && m == 0) {
+          z = mk(xk.x, xk.x);  // Im X_0 ignored, X_M = 0
+        } else {
+          const cx<T> xm = ln[padp(M - k) * LD];
+          const cx<T> wk = qt.wk(tw, h, m);
+          const cx<T> A = xk + conjg(xm), B = xk - conjg(xm);
+          z = A + mul_pi(cmul(conjg(wk), B));
+        }
+        v[m] = conjg(z);
+      }
+      __syncwarp();
+      qw_fft128<LD>(v, ln, qt, h);
+#pragma unroll
+      for (int m = 0; m < 16; ++m) ln[padp(h + 8 * m) * LD] = conjg(v[m]);
+    }
+  }
+  __syncthreads();
+  for (int it = w; it < ITEMS; it += NW) {
+    const int g = it / TX, c = it % TX;
+    cx<T>* p = sl + (34 * g + c) * LD;
+    const cx<T> u0 = p[0 * TX], u1 = p[1 * TX], u2 = p[2 * TX];
+    const cx<T> w0 = p[3 * TX], w1v = p[4 * TX], w2 = p[5 * TX];
+    p[0 * TX] = mk(u1.x * w2.x - u2.x * w1v.x, u1.y * w2.y - u2.y * w1v.y);
+    p[1 * TX] = mk(u2.x * w0.x - u0.x * w2.x, u2.y * w0.y - u0.y * w2.y);
+    p[2 * TX] = mk(u0.x * w1v.x - u1.x * w0.x, u0.y * w1v.y - u1.y * w0.y);
+  }
+  __syncthreads();
+  {
+    cx<T> v[16];
+    const int partner = (8 - h) & 7;
+#pragma unroll 1
+    for (int gi = w; gi < 3 * 4; gi += NW) {  // r2c of the 48 product lines
+      cx<T>* ln = s + line_of(gi);
+#pragma unroll
+      for (int m = 0; m < 16; ++m) v[m] = ln[padp(h + 8 * m) * LD];
+      __syncwarp();
+      qw_fft128<LD>(v, ln, qt, h);
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        cx<T> zo;
+        zo.x = __shfl_sync(0xffffffffu, v[15 - m].x, partner, 8);
+        zo.y = __shfl_sync(0xffffffffu, v[15 - m].y, partner, 8);
+        if (h == 0) zo = v[(16 - m) & 15];
+        const cx<T> wk = qt.wk(tw, h, m);
+        const cx<T> A = v[m] + conjg(zo), B = v[m] - conjg(zo);
+        if (h + 8 * m < kc) ln[padp(h + 8 * m) * LD] = scal(A + mul_mi(cmul(wk, B)), (T)0.5);
+      }
+    }
+  }
+  __syncthreads();
+  cx<T>* gd = W + ((size_t)(TX * kq) * N + y) * N + x0 + tx;
+  for (int it = w; it < 3 * ITEMS; it += NW) {
+    const int f = it / ITEMS, r = it % ITEMS, g = r / TX, c = r % TX;
+    if (32 * g + TX * kq + c < kc) gd[f * FS + (size_t)(32 * g + c) * N * N] = sl[(34 * g + c) * LD + f * TX];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // FP64 spectral sums for the diagnostics (Parseval): per block
 //   sum w|u|^2, sum w|omega|^2, sum w Re(conj(u).omega), count of non-finite,
 // w = 1 at kz = 0 and 2 otherwise (half spectrum; kz = N/2 is zero).
@@ -1434,6 +1581,7 @@ struct SolverImpl {
     if constexpr (N == 512) DNS_ATTR((k_zcross16<T, N>), G::ZSMEM);
     if constexpr (N == 512 && sizeof(T) == 4) DNS_ATTR((k_zcross16p<T, N>), Z16P<T>::SMEM);
     if constexpr (N == 1024 && sizeof(T) == 4) DNS_ATTR((k_zcross32p<T, N>), Z32P<T>::SMEM);
+    if constexpr (N == 256 && sizeof(T) == 4) DNS_ATTR((k_zcross8q<T, N>), Z8Q<T>::SMEM);
     DNS_ATTR((k_zpass<T, N, ZM_STORE>), G::ZSMEM);
     DNS_ATTR((k_zpass<T, N, ZM_LOAD>), G::ZSMEM);
     DNS_ATTR((k_zpass<T, N, ZM_MAXABS>), G::ZSMEM);
@@ -1454,6 +1602,8 @@ struct SolverImpl {
       k_zcross16<T, N><<<dim3(N / G::ZTX, N), 32 * Z16Warps<T, N>::value, G::ZSMEM, st>>>(a);
     else if constexpr (N == 1024 && sizeof(T) == 4)
       k_zcross32p<T, N><<<num_sms(), 32 * Z32P<T>::NW, Z32P<T>::SMEM, st>>>(a);
+    else if constexpr (N == 256 && sizeof(T) == 4)
+      k_zcross8q<T, N><<<dim3(N / Z8Q<T>::TX, N), 32 * Z8Q<T>::NW, Z8Q<T>::SMEM, st>>>(a);
     else if constexpr (ZCross<T, N>::enabled)
       k_zcross<T, N><<<dim3(N / G::ZTX, N), 32 * ZCrossWarps<T, N>::value, G::ZSMEM, st>>>(a);
     else

@@ -98,3 +98,37 @@ def test_x_stage_staged_rows_fit(N, cb):
     if not wide:
         # omega's padded work lines lie over the consumed U1 / U rows 3..8
         assert 3 * N + 3 * xls <= 9 * N
+
+
+def test_z256_quarter_warp_maps():
+    # k_zcross8q: tile walk kz = 32 g + TX kq + c (g < 4) over 16 x and 6 fields; quarter-warp qw of
+    # warp group gi takes line 16 (gi >> 2) + 2 (gi & 3) + 8 (qw & 1) + (qw >> 1); lane h < 8 holds
+    # k = h + 8 m; exchange at 17 h + k1 inside the padded line
+    M, TX, NW = 128, 16, 12
+    LD = odd_ld(6 * TX)
+    tile = padded_len(M) * LD
+    seen = set()
+    for lane in range(32):
+        tx, kq = lane % TX, lane // TX
+        for g in range(M // 32):
+            for c in range(TX):
+                kz = 32 * g + TX * kq + c
+                assert padp(kz) == 34 * g + padp(TX * kq) + c
+                for f in range(6):
+                    assert padp(kz) * LD + f * TX + tx < tile
+                    seen.add((kz, f, tx))
+    assert len(seen) == M * 6 * TX
+    assert (6 * (M // 32) * TX) % NW == 0
+    lines = [16 * (gi >> 2) + 2 * (gi & 3) + 8 * (qw & 1) + (qw >> 1) for gi in range(24) for qw in range(4)]
+    assert sorted(lines) == list(range(6 * TX))
+    assert sorted(lines[: 12 * 4]) == list(range(3 * TX))
+    for h in range(8):
+        for k1 in range(16):
+            assert 17 * h + k1 < padded_len(M)
+        for m in range(16):
+            k = h + 8 * m
+            if k:
+                assert 0 < M - k < M
+            # r2c partner Z_{M-k}: lane (8 - h) & 7, slot 15 - m (lane 0: slot (16 - m) & 15)
+            src_h, src_m = ((8 - h) & 7, 15 - m) if h else (0, (16 - m) & 15)
+            assert (src_h + 8 * src_m) % M == (M - k) % M
