@@ -1021,6 +1021,12 @@ __global__ void __launch_bounds__(32 * Z16P<T>::NW, 1) k_zcross16p(PassArgs a) {
   // partner X_{M-k} of k = h + 16 m sits at padded row padp(M - k) = pb0 + 17 (15 - m)
   // with pb0 = 16 - h for h > 0 and 17 for h = 0 (k = 0 has no partner: X_M = 0)
   const int pb0 = (h == 0) ? 17 : 16 - h;
+  // The inputs of modes k and M - k come from one pair (X_k, X_{M-k}): with
+  // A = X_k + conj X_{M-k}, B = X_k - conj X_{M-k} and P = i conj(w_k) B,
+  // z_k = A + P and z_{M-k} = conj(A - P). Lane h forms the pairs of its slots
+  // m < 8 (k = h + 16 m); the mirror M - k = (16 - h) + 16 (15 - m) is slot
+  // 15 - m of lane 16 - h, which receives it by a shuffle. Lane 0 pairs its slots
+  // m and 16 - m, takes the self-paired k = M/2 at m = 0 and forms k = 0 apart.
   auto c2r_lines = [&](int f0) {
     cx<T> v[16];
 #pragma unroll 1
@@ -1028,19 +1034,37 @@ __global__ void __launch_bounds__(32 * Z16P<T>::NW, 1) k_zcross16p(PassArgs a) {
       cx<T>* ln = s + l;
       const cx<T>* pa = ln + h * LD;
       const cx<T>* pb = ln + pb0 * LD;
+      const cx<T> x0 = ln[0];
+      cx<T> zq[8];
 #pragma unroll
-      for (int m = 0; m < 16; ++m) {
-        const cx<T> xk = pa[17 * m * LD];
-        const cx<T> xm = (h == 0 && m == 0) ? mk((T)0, (T)0) : pb[17 * (15 - m) * LD];
-        cx<T> z;
-        if (h == 0 && m == 0) {
-          z = mk(xk.x, xk.x);  // Im X_0 ignored, X_M = 0
+      for (int m = 0; m < 8; ++m) {
+        cx<T> xk, xm, wk;
+        if (m == 0) {
+          const cx<T>* ph = ln + padp(M / 2) * LD;
+          xk = (h == 0) ? *ph : pa[0];
+          xm = (h == 0) ? xk : pb[17 * 15 * LD];
+          wk = (h == 0) ? mk((T)0, (T)-1) : ht.wk(tw, h, 0);  // w_{M/2} = -i
         } else {
-          const cx<T> wk = ht.wk(tw, h, m);
-          const cx<T> A = xk + conjg(xm), B = xk - conjg(xm);
-          z = A + mul_pi(cmul(conjg(wk), B));
+          xk = pa[17 * m * LD];
+          xm = pb[17 * (15 - m) * LD];
+          wk = ht.wk(tw, h, m);
         }
-        v[m] = conjg(z);
+        const cx<T> A = xk + conjg(xm), B = xk - conjg(xm);
+        const cx<T> P = mul_pi(cmul(conjg(wk), B));
+        v[m] = conjg(A + P);
+        zq[m] = A - P;  // conj of z_{M-k}
+      }
+      const int src = (16 - h) & 15;
+#pragma unroll
+      for (int q = 8; q < 16; ++q) {
+        v[q].x = __shfl_sync(0xffffffffu, zq[15 - q].x, src, 16);
+        v[q].y = __shfl_sync(0xffffffffu, zq[15 - q].y, src, 16);
+      }
+      if (h == 0) {
+        v[8] = v[0];
+#pragma unroll
+        for (int q = 9; q < 16; ++q) v[q] = zq[16 - q];
+        v[0] = mk(x0.x, -x0.x);  // z_0 = (1 + i) Re X_0: Im X_0 ignored, X_M = 0
       }
       __syncwarp();
       hw_fft256<T, N, LD>(v, ln, ht, tw, h);
@@ -1093,6 +1117,7 @@ __global__ void __launch_bounds__(32 * Z16P<T>::NW, 1) k_zcross16p(PassArgs a) {
         const int partner = (16 - h) & 15;
 #pragma unroll
         for (int m = 0; m < 16; ++m) {
+          if (16 * m >= kc) break;  // slots m and above hold modes past the 2/3 cut
           cx<T> zo;
           zo.x = __shfl_sync(0xffffffffu, v[15 - m].x, partner, 16);
           zo.y = __shfl_sync(0xffffffffu, v[15 - m].y, partner, 16);
