@@ -1281,19 +1281,40 @@ __global__ void __launch_bounds__(32 * Z32P<T>::NW, 1) k_zcross32p(PassArgs a) {
       cx<T>* ln = s + l;
       const cx<T>* pa = ln + h * LD;
       const cx<T>* pb = ln + pb0 * LD;
+      const cx<T> x0 = ln[0];
+      // modes k = h + 16 m (m < 16) and M - k = (16 - h) + 16 (31 - m) from one pair:
+      // z_k = A + P, z_{M-k} = conj(A - P), the mirror going to slot 31 - m of lane
+      // 16 - h; lane 0 pairs its slots m and 32 - m and takes k = M/2 at m = 0
+      cx<T> zq[16];
 #pragma unroll
-      for (int m = 0; m < 32; ++m) {
-        const cx<T> xk = pa[17 * m * LD];
-        cx<T> z;
-        if (h == 0 && m == 0) {
-          z = mk(xk.x, xk.x);  // Im X_0 ignored, X_M = 0
+      for (int m = 0; m < 16; ++m) {
+        cx<T> xk, xm, wk;
+        if (m == 0) {
+          const cx<T>* ph = ln + padp(M / 2) * LD;
+          xk = (h == 0) ? *ph : pa[0];
+          xm = (h == 0) ? xk : pb[17 * 31 * LD];
+          wk = (h == 0) ? mk((T)0, (T)-1) : ht.wk(0);  // w_{M/2} = -i
         } else {
-          const cx<T> xm = pb[17 * (31 - m) * LD];
-          const cx<T> wk = ht.wk(m);
-          const cx<T> A = xk + conjg(xm), B = xk - conjg(xm);
-          z = A + mul_pi(cmul(conjg(wk), B));
+          xk = pa[17 * m * LD];
+          xm = pb[17 * (31 - m) * LD];
+          wk = ht.wk(m);
         }
-        v[m] = conjg(z);
+        const cx<T> A = xk + conjg(xm), B = xk - conjg(xm);
+        const cx<T> P = mul_pi(cmul(conjg(wk), B));
+        v[m] = conjg(A + P);
+        zq[m] = A - P;  // conj of z_{M-k}
+      }
+      const int src = (16 - h) & 15;
+#pragma unroll
+      for (int q = 16; q < 32; ++q) {
+        v[q].x = __shfl_sync(0xffffffffu, zq[31 - q].x, src, 16);
+        v[q].y = __shfl_sync(0xffffffffu, zq[31 - q].y, src, 16);
+      }
+      if (h == 0) {
+        v[16] = v[0];
+#pragma unroll
+        for (int q = 17; q < 32; ++q) v[q] = zq[32 - q];
+        v[0] = mk(x0.x, -x0.x);  // z_0 = (1 + i) Re X_0: Im X_0 ignored, X_M = 0
       }
       __syncwarp();
       hw_fft512<LD>(v, ln, ht, h);
@@ -1344,6 +1365,7 @@ __global__ void __launch_bounds__(32 * Z32P<T>::NW, 1) k_zcross32p(PassArgs a) {
         const int partner = (16 - h) & 15;
 #pragma unroll
         for (int m = 0; m < 32; ++m) {
+          if (16 * m >= kc) break;  // slots m and above hold modes past the 2/3 cut
           cx<T> zo;
           zo.x = __shfl_sync(0xffffffffu, v[31 - m].x, partner, 16);
           zo.y = __shfl_sync(0xffffffffu, v[31 - m].y, partner, 16);
@@ -1452,20 +1474,33 @@ __global__ void __launch_bounds__(32 * Z8Q<T>::NW, 2) k_zcross8q(PassArgs a) {
 #pragma unroll 1
     for (int gi = w; gi < 6 * 4; gi += NW) {  // c2r of the 96 lines
       cx<T>* ln = s + line_of(gi);
+      const cx<T> x0 = ln[0];
+      // modes k = h + 8 m (m < 8) and M - k = (8 - h) + 8 (15 - m) from one pair:
+      // z_k = A + P, z_{M-k} = conj(A - P), the mirror going to slot 15 - m of lane
+      // 8 - h; lane 0 pairs its slots m and 16 - m and takes k = M/2 at m = 0
+      cx<T> zq[8];
 #pragma unroll
-      for (int m = 0; m < 16; ++m) {
-        const int k = h + 8 * m;
+      for (int m = 0; m < 8; ++m) {
+        const int k = (m == 0 && h == 0) ? M / 2 : h + 8 * m;
         const cx<T> xk = ln[padp(k) * LD];
-        cx<T> z;
-        if (h == 0 && m == 0) {
-          z = mk(xk.x, xk.x);  // Im X_0 ignored, X_M = 0
-        } else {
-          const cx<T> xm = ln[padp(M - k) * LD];
-          const cx<T> wk = qt.wk(tw, h, m);
-          const cx<T> A = xk + conjg(xm), B = xk - conjg(xm);
-          z = A + mul_pi(cmul(conjg(wk), B));
-        }
-        v[m] = conjg(z);
+        const cx<T> xm = (m == 0 && h == 0) ? xk : ln[padp(M - k) * LD];
+        const cx<T> wk = (m == 0 && h == 0) ? mk((T)0, (T)-1) : qt.wk(tw, h, m);  // w_{M/2} = -i
+        const cx<T> A = xk + conjg(xm), B = xk - conjg(xm);
+        const cx<T> P = mul_pi(cmul(conjg(wk), B));
+        v[m] = conjg(A + P);
+        zq[m] = A - P;  // conj of z_{M-k}
+      }
+      const int src = (8 - h) & 7;
+#pragma unroll
+      for (int q = 8; q < 16; ++q) {
+        v[q].x = __shfl_sync(0xffffffffu, zq[15 - q].x, src, 8);
+        v[q].y = __shfl_sync(0xffffffffu, zq[15 - q].y, src, 8);
+      }
+      if (h == 0) {
+        v[8] = v[0];
+#pragma unroll
+        for (int q = 9; q < 16; ++q) v[q] = zq[16 - q];
+        v[0] = mk(x0.x, -x0.x);  // z_0 = (1 + i) Re X_0: Im X_0 ignored, X_M = 0
       }
       __syncwarp();
       qw_fft128<LD>(v, ln, qt, h);
@@ -1496,6 +1531,7 @@ __global__ void __launch_bounds__(32 * Z8Q<T>::NW, 2) k_zcross8q(PassArgs a) {
       qw_fft128<LD>(v, ln, qt, h);
 #pragma unroll
       for (int m = 0; m < 16; ++m) {
+        if (8 * m >= kc) break;  // slots m and above hold modes past the 2/3 cut
         cx<T> zo;
         zo.x = __shfl_sync(0xffffffffu, v[15 - m].x, partner, 8);
         zo.y = __shfl_sync(0xffffffffu, v[15 - m].y, partner, 8);
