@@ -90,6 +90,15 @@ int dns_set_stream(dns_handle* h, void* stream);
 /* Options:
  *   "dealias_variant"  0: keep |k_i| < N/3 (Sec. 3.1 text, default)
  *                      1: keep |k_i| < 2/3 (N/2+1) (the Appendix script)
+ *   "integrator"       explicit Runge-Kutta scheme of dns_step, each in the
+ *                      two-register form of the Appendix driver (stage s + 1
+ *                      starts from u0 + b_s dt dU_s, the new state is
+ *                      u0 + sum_s a_s dt dU_s):
+ *                      0: classical RK4, a = 1/6,1/3,1/3,1/6, b = 1/2,1/2,1
+ *                         (Appendix, default)
+ *                      1: forward Euler, a = 1 (the integrator loop of Sec. 3.1)
+ *                      2: Heun, a = 1/2,1/2, b = 1
+ *                      3: midpoint, a = 0,1, b = 1/2
  *   "use_graph"        1: dns_step replays a captured CUDA graph (default)
  *   "nu", "dt"         change the viscosity / time step
  *   "time"             set the simulated time reported by dns_diagnostics
@@ -105,8 +114,9 @@ int dns_set_state(dns_handle* h, const void* u, int on_device);
  * Nyquist modes are zeroed. Resets the time to 0. */
 int dns_set_state_spectral(dns_handle* h, const void* uhat, int on_device);
 
-/* Enqueues n >= 0 classical RK4 steps (Appendix: a = 1/6,1/3,1/3,1/6,
- * b = 1/2,1/2,1) of Eq. NSfinal. Asynchronous. */
+/* Enqueues n >= 0 steps of Eq. NSfinal with the handle's integrator (default
+ * the classical RK4 of the Appendix: a = 1/6,1/3,1/3,1/6, b = 1/2,1/2,1).
+ * Asynchronous. */
 int dns_step(dns_handle* h, int n);
 
 /* Physical velocity u = F^{-1}(u_hat), (3,N,N,N). Synchronises the stream. */
@@ -125,12 +135,12 @@ int dns_rhs(dns_handle* h, void* duhat, int on_device);
  * Returns DNS_ERR_NONFINITE (with *out filled) if any NaN/Inf is present. */
 int dns_diagnostics(dns_handle* h, dns_diag* out);
 
-/* Measurement aid: advances n >= 1 RK4 steps exactly like dns_step but
+/* Measurement aid: advances n >= 1 steps exactly like dns_step but
  * launches the kernels one by one (no graph) with a CUDA event after each,
  * and returns per kernel class the summed device time in ms[c] and the
  * launch count in launches[c]: c = 0 y-inverse, 1 z-pass (c2r, u x omega,
  * r2c), 2 y-forward, 3 x-stage (forward x, mask, projection, viscous term,
- * RK4 update, next inverse x). nclass must be >= 4. Synchronises. */
+ * stage update, next inverse x). nclass must be >= 4. Synchronises. */
 int dns_profile_steps(dns_handle* h, int n, double* ms, int* launches, int nclass);
 
 /* Bytes of device memory the handle owns. */
@@ -169,10 +179,11 @@ int dns_spectral_sums_noalloc(const void* uhat, int N, int dtype, double nu, dou
 
 /* ---- Ensembles (many independent runs of mixed grid sizes) ------------------
  * An ensemble owns `count` handles created as by dns_create(N[i], nu[i], dt[i],
- * dtype). dns_ensemble_step(e, n) advances every member by n RK4 steps (Sec. 3,
- * Appendix driver, per member); each step is one launch of a CUDA graph.
+ * dtype). dns_ensemble_step(e, n) advances every member by n steps of its
+ * integrator (RK4 unless set on the member's handle; Sec. 3, Appendix driver);
+ * each step is one launch of a CUDA graph.
  * Schedule: with batching on (default), members of equal N (N <= 128),
- * precision and dealias option are advanced together, one kernel launch per
+ * precision, dealias option and integrator are advanced together, one kernel launch per
  * pass for up to min(max_batch, 32) members (their pointers and RK
  * coefficients passed as kernel parameters); every batch, and every member that is not batched, is
  * a parallel branch of the graph. With batching off (max_batch = 0) every

@@ -41,6 +41,17 @@ WORKERS = max(1, len(os.sched_getaffinity(0))) if hasattr(os, "sched_getaffinity
 RK4_A = (1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0)
 RK4_B = (0.5, 0.5, 1.0)
 
+# Explicit Runge-Kutta schemes in the same two-register form (stage s + 1 starts
+# from u0 + b_s dt dU_s, the new state is u0 + sum_s a_s dt dU_s): the Appendix's
+# RK4, the forward Euler loop of Sec. 3.1, and the two-stage Heun and midpoint
+# rules (textbook Butcher tableaux with c = (0, 1) and (0, 1/2)).
+RK_SCHEMES = {
+    "rk4": (RK4_A, RK4_B),
+    "euler": ((1.0,), ()),
+    "heun": ((0.5, 0.5), (1.0,)),
+    "midpoint": ((0.0, 1.0), (0.5,)),
+}
+
 
 def set_workers(n: int) -> None:
     """Thread count for the library FFT (the CPU baseline reports it)."""
@@ -204,15 +215,38 @@ def euler_step(uh: np.ndarray, g: Grid, nu: float, dt: float) -> np.ndarray:
     return uh + dt * rhs(uh, g, nu)
 
 
+def rk_step(uh: np.ndarray, g: Grid, nu: float, dt: float, scheme: str = "rk4") -> np.ndarray:
+    """One step of an explicit RK scheme of RK_SCHEMES, stage by stage as the
+    Appendix driver orders RK4: dU_s = RHS(stage state); stage s + 1 starts from
+    u0 + b_s dt dU_s; the new state is u0 + sum_s a_s dt dU_s."""
+    a, b = RK_SCHEMES[scheme]
+    u0 = uh.copy()
+    u1 = uh.copy()
+    cur = uh
+    for s in range(len(a)):
+        dU = rhs(cur, g, nu)
+        if s < len(b):
+            cur = u0 + b[s] * dt * dU
+        u1 = u1 + a[s] * dt * dU
+    return u1
+
+
 def run(uh: np.ndarray, N: int, nu: float, dt: float, nsteps: int, variant: int = 0,
-        paper_reuse_u: bool = False, u0_phys: np.ndarray | None = None) -> np.ndarray:
-    """Advance ``nsteps`` RK4 steps (the step count is round(T/dt), reading of the while loop).
+        paper_reuse_u: bool = False, u0_phys: np.ndarray | None = None, scheme: str = "rk4") -> np.ndarray:
+    """Advance ``nsteps`` steps (the step count is round(T/dt), reading of the while loop)
+    of the Appendix's RK4, or of another scheme of RK_SCHEMES.
 
     paper_reuse_u=True mimics the Appendix: the physical U used at stage 0 is
     the one computed at the end of the previous step (the initial physical
-    field ``u0_phys`` at step one) instead of F^{-1}(u_hat).
+    field ``u0_phys`` at step one) instead of F^{-1}(u_hat); RK4 only.
     """
     g = Grid(N, variant)
+    if scheme != "rk4":
+        if paper_reuse_u:
+            raise ValueError("paper_reuse_u applies to the Appendix RK4 driver only")
+        for _ in range(nsteps):
+            uh = rk_step(uh, g, nu, dt, scheme)
+        return uh
     u_phys = u0_phys if paper_reuse_u else None
     for _ in range(nsteps):
         uh = rk4_step(uh, g, nu, dt, u_phys)

@@ -111,9 +111,22 @@ int cuda_fail(cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail(e_, where); \
   } while (0)
 
-// RK4 weights of the Appendix driver.
-const double RK_A[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
-const double RK_B[3] = {0.5, 0.5, 1.0};
+// Explicit Runge-Kutta schemes in the two-register form of the Appendix driver:
+// stage s evaluates dU_s on its stage state, stage s + 1 starts from
+// u0 + b_s dt dU_s, and the new state is u0 + sum_s a_s dt dU_s. Index 0 is the
+// classical RK4 of the Appendix (the default), 1 forward Euler (the integrator
+// loop of Sec. 3.1), 2 and 3 the two-stage Heun and midpoint rules.
+struct RkScheme {
+  int stages;
+  double a[4];
+  double b[3];
+};
+const RkScheme RK_SCHEMES[4] = {
+    {4, {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0}, {0.5, 0.5, 1.0}},
+    {1, {1.0, 0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}},
+    {2, {0.5, 0.5, 0.0, 0.0}, {1.0, 0.0, 0.0}},
+    {2, {0.0, 1.0, 0.0, 0.0}, {0.5, 0.0, 0.0}},
+};
 
 // exp(-2 pi i t / N) in FP64 with exact quadrant/octant symmetry.
 void twiddle(long t, long N, double* re, double* im) {
@@ -153,6 +166,7 @@ struct dns_handle {
   int N = 0;
   int dtype = 0;
   int variant = 0;
+  int integrator = 0;  // index into RK_SCHEMES
   int use_graph = 1;
   double nu = 0.0, dt = 0.0, t = 0.0;
   const DnsOps* ops = nullptr;
@@ -173,6 +187,7 @@ struct dns_handle {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   bool graph_dirty = true;
+  unsigned epoch = 0;  // bumped whenever a captured step of this handle goes stale
 };
 
 namespace {
@@ -222,12 +237,21 @@ PassArgs base_args(const dns_handle* h) {
   return a;
 }
 
+int rk_stages(const dns_handle* h) { return RK_SCHEMES[h->integrator].stages; }
+
+// stage s of the handle's scheme: its coefficients times dt and the index of the last stage
+void set_stage(const dns_handle* h, int s, PassArgs& a) {
+  const RkScheme& r = RK_SCHEMES[h->integrator];
+  a.stage = s;
+  a.last = r.stages - 1;
+  a.cA = r.a[s] * h->dt;
+  a.cB = s < r.stages - 1 ? r.b[s] * h->dt : 0.0;
+}
+
 cudaError_t enqueue_step(dns_handle* h, cudaStream_t st) {
   PassArgs a = base_args(h);
-  for (int s = 0; s < 4; ++s) {
-    a.stage = s;
-    a.cA = RK_A[s] * h->dt;
-    a.cB = s < 3 ? RK_B[s] * h->dt : 0.0;
+  for (int s = 0; s < rk_stages(h); ++s) {
+    set_stage(h, s, a);
     cudaError_t e = h->ops->rk_stage(a, st);
     if (e != cudaSuccess) return e;
   }
@@ -367,6 +391,10 @@ int dns_set_option(dns_handle* h, const char* key, double value) {
   if (!strcmp(key, "dealias_variant")) {
     if (value != 0.0 && value != 1.0) return fail(DNS_ERR_ARG, "dealias_variant must be 0 or 1");
     h->variant = (int)value;
+  } else if (!strcmp(key, "integrator")) {
+    if (value != 0.0 && value != 1.0 && value != 2.0 && value != 3.0)
+      return fail(DNS_ERR_ARG, "integrator must be 0 (RK4), 1 (Euler), 2 (Heun) or 3 (midpoint)");
+    h->integrator = (int)value;
   } else if (!strcmp(key, "use_graph")) {
     if (value != 0.0 && value != 1.0) return fail(DNS_ERR_ARG, "use_graph must be 0 or 1");
     h->use_graph = (int)value;
@@ -384,6 +412,7 @@ int dns_set_option(dns_handle* h, const char* key, double value) {
     return fail(DNS_ERR_ARG, "dns_set_option: unknown key '%s'", key);
   }
   h->graph_dirty = true;
+  ++h->epoch;
   h->w_valid = false;  // the x-inverse in W does not depend on these, but keep it simple
   return DNS_OK;
 }
@@ -572,7 +601,10 @@ int dns_set_forcing(dns_handle* h, const void* f3, int on_device) {
   if (rc) return rc;
   if ((rc = use_device(h))) return rc;
   if (!f3) {
-    if (h->has_force) h->graph_dirty = true;
+    if (h->has_force) {
+      h->graph_dirty = true;
+      ++h->epoch;
+    }
     h->has_force = false;
     return DNS_OK;
   }
@@ -588,7 +620,10 @@ int dns_set_forcing(dns_handle* h, const void* f3, int on_device) {
     h->w_valid = false;
   }
   DNS_CUDA(launch_transpose(h, src, h->F, true), "dns_set_forcing layout");
-  if (!h->has_force) h->graph_dirty = true;
+  if (!h->has_force) {
+    h->graph_dirty = true;
+    ++h->epoch;
+  }
   h->has_force = true;
   return DNS_OK;
 }
@@ -602,17 +637,15 @@ int dns_profile_steps(dns_handle* h, int n, double* ms, int* launches, int nclas
     DNS_CUDA(h->ops->x_inverse_curl(base_args(h), 0, h->stream), "dns_profile_steps initial transform");
     h->w_valid = true;
   }
-  const int nk = 16 * n;
+  const int nk = 4 * rk_stages(h) * n;
   std::vector<cudaEvent_t> ev(nk + 1);
   for (auto& e : ev) DNS_CUDA(cudaEventCreate(&e), "cudaEventCreate");
   PassArgs a = base_args(h);
   cudaError_t err = cudaEventRecord(ev[0], h->stream);
   int k = 0;
   for (int i = 0; i < n && err == cudaSuccess; ++i) {
-    for (int s = 0; s < 4 && err == cudaSuccess; ++s) {
-      a.stage = s;
-      a.cA = RK_A[s] * h->dt;
-      a.cB = s < 3 ? RK_B[s] * h->dt : 0.0;
+    for (int s = 0; s < rk_stages(h) && err == cudaSuccess; ++s) {
+      set_stage(h, s, a);
       for (int p = 0; p < 4 && err == cudaSuccess; ++p) {
         err = h->ops->rk_stage_part(a, p, h->stream);
         if (err == cudaSuccess) err = cudaEventRecord(ev[++k], h->stream);
@@ -668,14 +701,15 @@ struct dns_ensemble {
   int streams = 0;  // per-member schedule: graph branches (0 = one per member)
   int batch = kEnsembleWholeGroups;  // members per batched launch (0 = per-member schedule)
   bool dirty = true;
+  std::vector<unsigned> epochs;  // the members' epochs at the last capture
 };
 
 namespace {
 
 // A unit of the step graph: one member stepped by its own kernels, or a batch
-// of members of equal (N, precision, dealias rule) stepped by shared launches
-// (their stage arguments at hargs + offset, 4 consecutive arrays of `count`,
-// copied into the kernels' parameters at capture).
+// of members of equal (N, precision, dealias rule, integrator) stepped by shared
+// launches (their stage arguments at hargs + offset, one array of `count` per
+// stage, copied into the kernels' parameters at capture).
 struct EnsUnit {
   int first = 0;   // single member index, or -1 for a batch
   std::vector<int> members;
@@ -702,7 +736,7 @@ std::vector<EnsUnit> ens_units(const dns_ensemble* e) {
       std::vector<int> group;
       for (int j = i; j < n; ++j) {
         const dns_handle* g = e->m[j];
-        if (!done[j] && g->ops == h->ops && g->variant == h->variant) {
+        if (!done[j] && g->ops == h->ops && g->variant == h->variant && g->integrator == h->integrator) {
           group.push_back(j);
           done[j] = true;
         }
@@ -736,13 +770,11 @@ int ens_capture(dns_ensemble* e, int K) {
   for (EnsUnit& u : units) {
     if (u.first >= 0) continue;
     u.offset = hargs.size();
-    for (int s = 0; s < 4; ++s)
+    for (int s = 0; s < rk_stages(e->m[u.members[0]]); ++s)
       for (int i : u.members) {
         const dns_handle* h = e->m[i];
         PassArgs a = base_args(h);
-        a.stage = s;
-        a.cA = RK_A[s] * h->dt;
-        a.cB = s < 3 ? RK_B[s] * h->dt : 0.0;
+        set_stage(h, s, a);
         hargs.push_back(a);
       }
   }
@@ -767,7 +799,7 @@ int ens_capture(dns_ensemble* e, int K) {
     } else {
       const dns_handle* h = e->m[un.members[0]];
       const int cnt = (int)un.members.size();
-      for (int s = 0; s < 4 && err == cudaSuccess; ++s)
+      for (int s = 0; s < rk_stages(h) && err == cudaSuccess; ++s)
         err = h->ops->rk_stage_batch(hargs.data() + un.offset + (size_t)s * cnt, cnt, h->N + 2 * h->variant, st);
     }
   }
@@ -785,6 +817,8 @@ int ens_capture(dns_ensemble* e, int K) {
   e->graph = g;
   DNS_CUDA(cudaGraphInstantiate(&e->gexec, e->graph, 0), "ensemble graph instantiate");
   e->dirty = false;
+  e->epochs.clear();
+  for (const dns_handle* h : e->m) e->epochs.push_back(h->epoch);
   return DNS_OK;
 }
 
@@ -794,8 +828,11 @@ int ens_prepare_members(dns_ensemble* e) {
       DNS_CUDA(h->ops->x_inverse_curl(base_args(h), 0, e->main), "ensemble initial transform");
       h->w_valid = true;
     }
-    if (h->graph_dirty) e->dirty = true;
   }
+  // re-capture only when a member's options or forcing changed since the last capture
+  if (e->epochs.size() != e->m.size()) e->dirty = true;
+  for (size_t i = 0; i < e->m.size() && !e->dirty; ++i)
+    if (e->epochs[i] != e->m[i]->epoch) e->dirty = true;
   return DNS_OK;
 }
 

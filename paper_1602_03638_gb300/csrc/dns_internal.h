@@ -23,7 +23,8 @@ struct PassArgs {
   double nu = 0.0;
   double cA = 0.0;  // a_s * dt
   double cB = 0.0;  // b_s * dt
-  int stage = 0;    // RK4 stage 0..3
+  int stage = 0;    // stage of the step, 0..last
+  int last = 3;     // the step's final stage (it writes the new state); 3 for RK4
   int kmax3 = 0;    // a mode is kept by the 2/3 rule iff 3|k_i| < kmax3
   const void* in = nullptr;  // physical input (3,N,N,N) for set_state
   void* out = nullptr;       // physical output (3,N,N,N) / RHS output

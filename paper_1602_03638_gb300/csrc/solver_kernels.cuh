@@ -153,11 +153,11 @@ __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
     // rows outside the 2/3 box carry no nonlinear term: skip their transform
     const bool row_kept = (3 * kz < a.kmax3) && kept(kfreq(ky, N), a.kmax3);
     const T nu = (T)a.nu, cA = (T)a.cA, cB = (T)a.cB;
-    const int stage = a.stage;
+    const int stage = a.stage, last = a.last;
     const cx<T>* Sst = (stage == 0) ? U : US;
     // state rows read by the update: stage state (all stages), accumulator
-    // (stages 1-3), step-start state (stages 1-2)
-    const bool need1 = MODE == XM_STAGE && stage > 0, need0 = MODE == XM_STAGE && stage > 0 && stage < 3;
+    // (stages after the first), step-start state (the stages between first and last)
+    const bool need1 = MODE == XM_STAGE && stage > 0, need0 = MODE == XM_STAGE && stage > 0 && stage < last;
     cx<T>* const st = s + G::XST;  // XPRE: rows [Sst 0..2][U1 0..2][U 0..2], N values each
     if constexpr (G::XPRE) {
       if (row_kept) {
@@ -230,7 +230,14 @@ __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
         out[2 * FS + gi] = d2;
       } else {
         cx<T> v0, v1, v2;
-        if (stage == 0) {
+        if (stage == 0 && last == 0) {  // one-stage step (forward Euler): u += a_0 dt dU
+          v0 = u0 + scal(d0, cA);
+          v1 = u1 + scal(d1, cA);
+          v2 = u2 + scal(d2, cA);
+          U[gi] = v0;
+          U[FS + gi] = v1;
+          U[2 * FS + gi] = v2;
+        } else if (stage == 0) {
           U1[gi] = u0 + scal(d0, cA);
           U1[FS + gi] = u1 + scal(d1, cA);
           U1[2 * FS + gi] = u2 + scal(d2, cA);
@@ -240,7 +247,7 @@ __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
           US[gi] = v0;
           US[FS + gi] = v1;
           US[2 * FS + gi] = v2;
-        } else if (stage < 3) {
+        } else if (stage < last) {
           const cx<T> b0 = ld_0(0, j), b1 = ld_0(1, j), b2 = ld_0(2, j);
           U1[gi] = ld_1(0, j) + scal(d0, cA);
           U1[FS + gi] = ld_1(1, j) + scal(d1, cA);
@@ -1672,11 +1679,11 @@ struct SolverImpl {
   }
 
   // shared memory of a stage-update launch: with the wide layout only the rows
-  // the stage reads are allocated (3 in stage 0, 6 in stage 3, 9 in stages 1-2),
-  // so the lighter stages keep more blocks per SM
-  static size_t xsmem_stage(int stage) {
+  // the stage reads are allocated (3 in the first stage, 6 in the last, 9 in the
+  // stages between), so the lighter stages keep more blocks per SM
+  static size_t xsmem_stage(int stage, int last) {
     if constexpr (G::XPRE && G::XWIDE) {
-      const int rows = stage == 0 ? 3 : (stage == 3 ? 6 : 9);
+      const int rows = stage == 0 ? 3 : (stage == last ? 6 : 9);
       return (size_t)(G::XST + rows * N) * sizeof(cx<T>);
     } else {
       return G::XSMEM_ST;
@@ -1705,7 +1712,7 @@ struct SolverImpl {
 
   static cudaError_t rk_stage(const PassArgs& a, cudaStream_t st) {
     rhs_front(a, st);
-    k_xpass<T, N, XM_STAGE><<<M * N, XP_THREADS, xsmem_stage(a.stage), st>>>(a);
+    k_xpass<T, N, XM_STAGE><<<M * N, XP_THREADS, xsmem_stage(a.stage, a.last), st>>>(a);
     return cudaGetLastError();
   }
 
@@ -1716,7 +1723,7 @@ struct SolverImpl {
       case 0: k_ypass<T, N, 1, 0><<<dim3(N / YCfg<T, N, 1>::TX, M, 6), YCfg<T, N, 1>::THREADS, YCfg<T, N, 1>::SMEM, st>>>(W, tw, a.kmax3); break;
       case 1: z_cross(a, st); break;
       case 2: k_ypass<T, N, 0, 1><<<dim3(N / YCfg<T, N, 0>::TX, kc_of(a.kmax3), 3), YCfg<T, N, 0>::THREADS, YCfg<T, N, 0>::SMEM, st>>>(W, tw, a.kmax3); break;
-      default: k_xpass<T, N, XM_STAGE><<<M * N, XP_THREADS, xsmem_stage(a.stage), st>>>(a); break;
+      default: k_xpass<T, N, XM_STAGE><<<M * N, XP_THREADS, xsmem_stage(a.stage, a.last), st>>>(a); break;
     }
     return cudaGetLastError();
   }
@@ -1729,7 +1736,7 @@ struct SolverImpl {
       k_ypass_b<T, N, 1, 0><<<dim3(N / YCfg<T, N, 1>::TX, M, 6 * count), YCfg<T, N, 1>::THREADS, YCfg<T, N, 1>::SMEM, st>>>(B, 6);
       k_zpass_b<T, N, ZM_CROSS><<<dim3(N / G::ZTX, N, count), ZP_THREADS, G::ZSMEM, st>>>(B);
       k_ypass_b<T, N, 0, 1><<<dim3(N / YCfg<T, N, 0>::TX, kc_of(kmax3), 3 * count), YCfg<T, N, 0>::THREADS, YCfg<T, N, 0>::SMEM, st>>>(B, 3);
-      k_xpass_b<T, N, XM_STAGE><<<dim3(M * N, count), XP_THREADS, xsmem_stage(A[0].stage), st>>>(B);
+      k_xpass_b<T, N, XM_STAGE><<<dim3(M * N, count), XP_THREADS, xsmem_stage(A[0].stage, A[0].last), st>>>(B);
       return cudaGetLastError();
     } else {
       return cudaErrorNotSupported;
@@ -1742,7 +1749,7 @@ struct SolverImpl {
     rhs_front(a, st);
     PassArgs b = a;
     b.stage = 0;
-    k_xpass<T, N, XM_RHS><<<M * N, XP_THREADS, xsmem_stage(0), st>>>(b);
+    k_xpass<T, N, XM_RHS><<<M * N, XP_THREADS, xsmem_stage(0, 3), st>>>(b);
     return cudaGetLastError();
   }
 

@@ -42,10 +42,18 @@ def _ptr(arr, shape, real_dtype_bytes, complex_):
     raise TypeError("expected a numpy array or a torch tensor")
 
 
-class Solver:
-    """One dns_handle: N^3 grid, viscosity nu, time step dt, 'f32' or 'f64'."""
+# explicit Runge-Kutta schemes of dns_step ("integrator" option of the C ABI)
+INTEGRATORS = {"rk4": 0, "euler": 1, "heun": 2, "midpoint": 3}
 
-    def __init__(self, N: int, nu: float, dt: float, dtype: str = "f32", dealias_variant: int = 0):
+
+class Solver:
+    """One dns_handle: N^3 grid, viscosity nu, time step dt, 'f32' or 'f64'; integrator
+    'rk4' (the Appendix driver, default), 'euler', 'heun' or 'midpoint'."""
+
+    def __init__(self, N: int, nu: float, dt: float, dtype: str = "f32", dealias_variant: int = 0,
+                 integrator: str = "rk4"):
+        if integrator not in INTEGRATORS:
+            raise ValueError(f"integrator must be one of {sorted(INTEGRATORS)}, got {integrator!r}")
         self.N = int(N)
         self.dtype = dtype
         self._code = {"f32": _lib.DNS_F32, "f64": _lib.DNS_F64}[dtype]
@@ -56,6 +64,8 @@ class Solver:
         self._h = h
         if dealias_variant:
             self.set_option("dealias_variant", dealias_variant)
+        if integrator != "rk4":
+            self.set_option("integrator", INTEGRATORS[integrator])
 
     @classmethod
     def _borrow(cls, handle: ctypes.c_void_p, N: int, dtype: str):
