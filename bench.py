@@ -238,6 +238,26 @@ def run_form(torch, Solver, inputs, N, dtype, warm, steps):
     return out
 
 
+def run_integrators(torch, Solver, inputs, N=512, warm=3, steps=10):
+    """Taylor-Green N^3 FP32 step time of each explicit RK scheme of the integrator option;
+    a stage costs the same four passes in every scheme, so ms per stage is the comparison."""
+    stages = {"euler": 1, "heun": 2, "midpoint": 2, "rk4": 4}
+    out = {}
+    for scheme, ns in stages.items():
+        with Solver(N, NU, DT, "f32", integrator=scheme) as s:
+            st = torch.cuda.current_stream()
+            s.set_stream(st)
+            u = inputs.taylor_green_torch(N, device="cuda", dtype=torch.float32)
+            s.set_state(u)
+            del u
+            for _ in range(warm):
+                s.step(1)
+            torch.cuda.synchronize()
+            ms = time_steps(torch, s, st, steps) / steps
+        out[scheme] = {"stages": ns, "ms_per_step": ms, "ms_per_stage": ms / ns}
+    return {"N": N, "dtype": "f32", "steps": steps, "schemes": out}
+
+
 def run_ensemble(torch, np, steps=10):
     """128 independent members (32 each of 32^3, 48^3, 64^3, 96^3), FP32, isotropic initial
     fields with k0 drawn from U[2, 6] per member: one graph launch per ensemble step (schedule
@@ -487,6 +507,7 @@ def run_ours(args):
                 got = s3.get_state_spectral()
             errs[dt_] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
         line["forms"] = forms
+        line["integrators"] = run_integrators(torch, Solver, inputs)
         line["ensemble"] = run_ensemble(torch, np)
         line["cufft_comparison"] = run_cufft_comparison(torch)
         line["closure"] = run_closure()
