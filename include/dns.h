@@ -99,6 +99,10 @@ int dns_set_stream(dns_handle* h, void* stream);
  *                      1: forward Euler, a = 1 (the integrator loop of Sec. 3.1)
  *                      2: Heun, a = 1/2,1/2, b = 1
  *                      3: midpoint, a = 0,1, b = 1/2
+ *   "Lx", "Ly", "Lz"   box lengths (default 2 pi each): the mesh spacing along x is
+ *                      Lx / N and the wavenumber of index l is 2 pi l / Lx (Sec. 2
+ *                      footnote, Sec. 3.1: other box sizes by scaling). The 2/3
+ *                      rule acts on the indices; the SGS helpers assume 2 pi.
  *   "use_graph"        1: dns_step replays a captured CUDA graph (default)
  *   "nu", "dt"         change the viscosity / time step
  *   "time"             set the simulated time reported by dns_diagnostics

@@ -63,10 +63,12 @@ def set_workers(n: int) -> None:
 # Mesh and wavenumbers (Eq. realmesh, Eq. kmesh, Sec. 3.1)
 # --------------------------------------------------------------------------
 
-def mesh(N: int) -> np.ndarray:
-    """Physical mesh x_i = 2*pi*i/N in each direction (Eq. realmesh); shape (3,N,N,N)."""
-    x = 2.0 * np.pi * np.arange(N, dtype=np.float64) / N
-    return np.array(np.meshgrid(x, x, x, indexing="ij"))
+def mesh(N: int, lengths=None) -> np.ndarray:
+    """Physical mesh x_i = 2*pi*i/N in each direction (Eq. realmesh); shape (3,N,N,N).
+    With box lengths (Lx, Ly, Lz) (Sec. 2 footnote) x_i = Lx*i/N, and so on."""
+    L = (2.0 * np.pi,) * 3 if lengths is None else tuple(float(v) for v in lengths)
+    xs = [L[d] * np.arange(N, dtype=np.float64) / N for d in range(3)]
+    return np.array(np.meshgrid(*xs, indexing="ij"))
 
 
 def wavenumbers(N: int) -> np.ndarray:
@@ -96,13 +98,22 @@ def dealias_mask(N: int, variant: int = 0) -> np.ndarray:
 
 @dataclass
 class Grid:
-    """Precomputed K, |K|^2, K/|K|^2 and the dealias mask (Sec. 3.1)."""
+    """Precomputed K, |K|^2, K/|K|^2 and the dealias mask (Sec. 3.1).
+
+    With box lengths (Lx, Ly, Lz) the wavenumber of index l along x is 2*pi*l/Lx
+    (Sec. 2 footnote; Sec. 3.1: other box sizes by scaling); the 2/3 mask stays on
+    the integer indices.
+    """
 
     N: int
     variant: int = 0
+    lengths: tuple | None = None
 
     def __post_init__(self):
         self.K = wavenumbers(self.N)
+        if self.lengths is not None:
+            scale = np.array([2.0 * np.pi / float(v) for v in self.lengths]).reshape(3, 1, 1, 1)
+            self.K = self.K * scale
         self.K2 = np.sum(self.K * self.K, axis=0)
         # K/|K|^2 with the k=0 entry set to 0 (Sec. 3.1: where(K2 == 0, 1, K2)).
         self.K_over_K2 = self.K.astype(np.float64) / np.where(self.K2 == 0, 1, self.K2).astype(np.float64)
@@ -232,15 +243,17 @@ def rk_step(uh: np.ndarray, g: Grid, nu: float, dt: float, scheme: str = "rk4") 
 
 
 def run(uh: np.ndarray, N: int, nu: float, dt: float, nsteps: int, variant: int = 0,
-        paper_reuse_u: bool = False, u0_phys: np.ndarray | None = None, scheme: str = "rk4") -> np.ndarray:
+        paper_reuse_u: bool = False, u0_phys: np.ndarray | None = None, scheme: str = "rk4",
+        lengths=None) -> np.ndarray:
     """Advance ``nsteps`` steps (the step count is round(T/dt), reading of the while loop)
     of the Appendix's RK4, or of another scheme of RK_SCHEMES.
 
     paper_reuse_u=True mimics the Appendix: the physical U used at stage 0 is
     the one computed at the end of the previous step (the initial physical
-    field ``u0_phys`` at step one) instead of F^{-1}(u_hat); RK4 only.
+    field ``u0_phys`` at step one) instead of F^{-1}(u_hat); RK4 only. ``lengths``:
+    box lengths (Lx, Ly, Lz), default 2 pi each.
     """
-    g = Grid(N, variant)
+    g = Grid(N, variant, lengths)
     if scheme != "rk4":
         if paper_reuse_u:
             raise ValueError("paper_reuse_u applies to the Appendix RK4 driver only")
@@ -266,7 +279,7 @@ def energy(uh: np.ndarray) -> float:
     return float(0.5 * np.sum(u * u) / N**3)
 
 
-def diagnostics(uh: np.ndarray, nu: float) -> dict:
+def diagnostics(uh: np.ndarray, nu: float, lengths=None) -> dict:
     """Energy, dissipation, max|div u|, helicity and enstrophy as grid means.
 
     E = 1/2 <|u|^2>, eps = nu <|omega|^2> (the paper names "energy dissipation"
@@ -274,7 +287,7 @@ def diagnostics(uh: np.ndarray, nu: float) -> dict:
     flow), H = <u . omega>, Z = 1/2 <|omega|^2>, div = max_x |F^{-1}(i k . u_hat)|.
     """
     N = uh.shape[-3]
-    g = Grid(N)
+    g = Grid(N, 0, lengths)
     u = inverse(uh)
     w = inverse(curl_hat(uh, g))
     n3 = float(N) ** 3

@@ -116,6 +116,8 @@ int cuda_fail(cudaError_t e, const char* where) {
 // u0 + b_s dt dU_s, and the new state is u0 + sum_s a_s dt dU_s. Index 0 is the
 // classical RK4 of the Appendix (the default), 1 forward Euler (the integrator
 // loop of Sec. 3.1), 2 and 3 the two-stage Heun and midpoint rules.
+const double kTwoPi = 6.283185307179586476925286766559;
+
 struct RkScheme {
   int stages;
   double a[4];
@@ -167,6 +169,7 @@ struct dns_handle {
   int dtype = 0;
   int variant = 0;
   int integrator = 0;  // index into RK_SCHEMES
+  double L[3] = {kTwoPi, kTwoPi, kTwoPi};  // box lengths along x, y, z
   int use_graph = 1;
   double nu = 0.0, dt = 0.0, t = 0.0;
   const DnsOps* ops = nullptr;
@@ -232,6 +235,7 @@ PassArgs base_args(const dns_handle* h) {
   a.F = h->has_force ? h->F : nullptr;
   a.nu = h->nu;
   a.kmax3 = h->N + 2 * h->variant;
+  for (int i = 0; i < 3; ++i) a.ks[i] = kTwoPi / h->L[i];  // exactly 1 on the 2 pi box
   a.partials = h->diag;
   a.maxbits = reinterpret_cast<unsigned long long*>(h->diag + DIAG_BLOCKS * 4 + 4);
   return a;
@@ -395,6 +399,9 @@ int dns_set_option(dns_handle* h, const char* key, double value) {
     if (value != 0.0 && value != 1.0 && value != 2.0 && value != 3.0)
       return fail(DNS_ERR_ARG, "integrator must be 0 (RK4), 1 (Euler), 2 (Heun) or 3 (midpoint)");
     h->integrator = (int)value;
+  } else if (!strcmp(key, "Lx") || !strcmp(key, "Ly") || !strcmp(key, "Lz")) {
+    if (!(value > 0.0) || !std::isfinite(value)) return fail(DNS_ERR_ARG, "%s must be finite and > 0", key);
+    h->L[key[1] - 'x'] = value;
   } else if (!strcmp(key, "use_graph")) {
     if (value != 0.0 && value != 1.0) return fail(DNS_ERR_ARG, "use_graph must be 0 or 1");
     h->use_graph = (int)value;

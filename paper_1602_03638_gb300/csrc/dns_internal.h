@@ -26,6 +26,11 @@ struct PassArgs {
   int stage = 0;    // stage of the step, 0..last
   int last = 3;     // the step's final stage (it writes the new state); 3 for RK4
   int kmax3 = 0;    // a mode is kept by the 2/3 rule iff 3|k_i| < kmax3
+  double ks[3] = {1.0, 1.0, 1.0};  // 2 pi / L along x, y, z: the wavenumber of index 1
+  // FP32 copies of nu, cA, cB and ks for the FP32 kernels (filled when a kernel is
+  // launched), so that they need no double-to-float conversion per thread
+  float f_nu = 0.f, f_cA = 0.f, f_cB = 0.f;
+  float f_ks[3] = {1.f, 1.f, 1.f};
   const void* in = nullptr;  // physical input (3,N,N,N) for set_state
   void* out = nullptr;       // physical output (3,N,N,N) / RHS output
   double* partials = nullptr;          // diagnostics block partials

@@ -17,6 +17,8 @@
 // [component][kz][ky][kx], kz < N/2, kx and ky in FFT order.
 #pragma once
 
+#include <type_traits>
+
 #include "dns_internal.h"
 #include "fft_core.cuh"
 
@@ -87,6 +89,21 @@ struct YCfg {
 };
 
 __device__ __forceinline__ int kfreq(int i, int N) { return i < N / 2 ? i : i - N; }
+
+// the launch parameters with their FP32 copies filled in
+inline PassArgs f32args(PassArgs a) {
+  a.f_nu = (float)a.nu;
+  a.f_cA = (float)a.cA;
+  a.f_cB = (float)a.cB;
+  for (int i = 0; i < 3; ++i) a.f_ks[i] = (float)a.ks[i];
+  return a;
+}
+// a launch parameter in the kernel's precision: the FP32 copy or the FP64 value
+template <typename T>
+__device__ __forceinline__ T par(double d, float f) {
+  if constexpr (sizeof(T) == 4) return f;
+  else return d;
+}
 __device__ __forceinline__ bool kept(int k, int kmax3) { return 3 * (k < 0 ? -k : k) < kmax3; }
 
 enum XMode { XM_INV_CURL = 0, XM_STAGE = 1, XM_RHS = 2, XM_FWD_STORE = 3, XM_INV_PLAIN = 4, XM_INV_DIV = 5 };
@@ -147,12 +164,14 @@ __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
   const int kz = row / N, ky = row % N;
   const size_t rb = (size_t)row * N;
   const T sc = (T)(1.0 / ((double)N * (double)N * (double)N));
-  const T kzv = (T)kz, kyv = (T)kfreq(ky, N);
+  // wavenumbers of the row and of column j: integer index times 2 pi / L (1 on the 2 pi box)
+  const T ksx = par<T>(a.ks[0], a.f_ks[0]);
+  const T kzv = (T)kz * par<T>(a.ks[2], a.f_ks[2]), kyv = (T)kfreq(ky, N) * par<T>(a.ks[1], a.f_ks[1]);
 
   if constexpr (MODE == XM_STAGE || MODE == XM_RHS) {
     // rows outside the 2/3 box carry no nonlinear term: skip their transform
     const bool row_kept = (3 * kz < a.kmax3) && kept(kfreq(ky, N), a.kmax3);
-    const T nu = (T)a.nu, cA = (T)a.cA, cB = (T)a.cB;
+    const T nu = par<T>(a.nu, a.f_nu), cA = par<T>(a.cA, a.f_cA), cB = par<T>(a.cB, a.f_cB);
     const int stage = a.stage, last = a.last;
     const cx<T>* Sst = (stage == 0) ? U : US;
     // state rows read by the update: stage state (all stages), accumulator
@@ -196,91 +215,100 @@ __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
     auto ld_s = [&](int c, int j) -> cx<T> { return G::XPRE ? st[c * N + j] : Sst[c * FS + rb + j]; };
     auto ld_1 = [&](int c, int j) -> cx<T> { return G::XPRE ? st[(3 + c) * N + j] : U1[c * FS + rb + j]; };
     auto ld_0 = [&](int c, int j) -> cx<T> { return G::XPRE ? st[(6 + c) * N + j] : U[c * FS + rb + j]; };
-    for (int j = threadIdx.x; j < N; j += XP_THREADS) {
-      const int kxi = kfreq(j, N);
-      const T kx = (T)kxi;
-      const int pj = padp(j);
-      cx<T> n0 = mk((T)0, (T)0), n1 = n0, n2 = n0;
-      if (row_kept && kept(kxi, a.kmax3)) {
-        n0 = s[0 * LS + pj];
-        n1 = s[1 * LS + pj];
-        n2 = s[2 * LS + pj];
-        if (a.F) {  // external force (learned closure), masked like the nonlinear term
-          const cx<T>* F = reinterpret_cast<const cx<T>*>(a.F);
-          n0 = n0 + F[rb + j];
-          n1 = n1 + F[FS + rb + j];
-          n2 = n2 + F[2 * FS + rb + j];
+    // the column loop, with the wavenumber kx = index * 2 pi / Lx; on the 2 pi box the
+    // index itself, exactly as without a box option
+    auto columns = [&](auto scaled) {
+      constexpr bool SCALED = decltype(scaled)::value;
+      for (int j = threadIdx.x; j < N; j += XP_THREADS) {
+        const int kxi = kfreq(j, N);
+        const T kx = SCALED ? (T)kxi * ksx : (T)kxi;
+        const int pj = padp(j);
+        cx<T> n0 = mk((T)0, (T)0), n1 = n0, n2 = n0;
+        if (row_kept && kept(kxi, a.kmax3)) {
+          n0 = s[0 * LS + pj];
+          n1 = s[1 * LS + pj];
+          n2 = s[2 * LS + pj];
+          if (a.F) {  // external force (learned closure), masked like the nonlinear term
+            const cx<T>* F = reinterpret_cast<const cx<T>*>(a.F);
+            n0 = n0 + F[rb + j];
+            n1 = n1 + F[FS + rb + j];
+            n2 = n2 + F[2 * FS + rb + j];
+          }
+        }
+        const T k2 = kx * kx + kyv * kyv + kzv * kzv;
+        const T ik2 = k2 > (T)0 ? (T)1 / k2 : (T)0;
+        // P = (k . N_hat) / |k|^2   (Eq. mod_pressure without the factor i)
+        const cx<T> p = mk((kx * n0.x + kyv * n1.x + kzv * n2.x) * ik2, (kx * n0.y + kyv * n1.y + kzv * n2.y) * ik2);
+        const size_t gi = rb + j;
+        const cx<T> u0 = ld_s(0, j), u1 = ld_s(1, j), u2 = ld_s(2, j);
+        const T nk2 = nu * k2;
+        // dU = N_hat - k P - nu |k|^2 u_hat   (Eq. NSfinal)
+        const cx<T> d0 = mk(n0.x - kx * p.x - nk2 * u0.x, n0.y - kx * p.y - nk2 * u0.y);
+        const cx<T> d1 = mk(n1.x - kyv * p.x - nk2 * u1.x, n1.y - kyv * p.y - nk2 * u1.y);
+        const cx<T> d2 = mk(n2.x - kzv * p.x - nk2 * u2.x, n2.y - kzv * p.y - nk2 * u2.y);
+        if constexpr (MODE == XM_RHS) {
+          cx<T>* out = reinterpret_cast<cx<T>*>(a.out);
+          out[gi] = d0;
+          out[FS + gi] = d1;
+          out[2 * FS + gi] = d2;
+        } else {
+          cx<T> v0, v1, v2;
+          if (stage == 0 && last == 0) {  // one-stage step (forward Euler): u += a_0 dt dU
+            v0 = u0 + scal(d0, cA);
+            v1 = u1 + scal(d1, cA);
+            v2 = u2 + scal(d2, cA);
+            U[gi] = v0;
+            U[FS + gi] = v1;
+            U[2 * FS + gi] = v2;
+          } else if (stage == 0) {
+            U1[gi] = u0 + scal(d0, cA);
+            U1[FS + gi] = u1 + scal(d1, cA);
+            U1[2 * FS + gi] = u2 + scal(d2, cA);
+            v0 = u0 + scal(d0, cB);
+            v1 = u1 + scal(d1, cB);
+            v2 = u2 + scal(d2, cB);
+            US[gi] = v0;
+            US[FS + gi] = v1;
+            US[2 * FS + gi] = v2;
+          } else if (stage < last) {
+            const cx<T> b0 = ld_0(0, j), b1 = ld_0(1, j), b2 = ld_0(2, j);
+            U1[gi] = ld_1(0, j) + scal(d0, cA);
+            U1[FS + gi] = ld_1(1, j) + scal(d1, cA);
+            U1[2 * FS + gi] = ld_1(2, j) + scal(d2, cA);
+            v0 = b0 + scal(d0, cB);
+            v1 = b1 + scal(d1, cB);
+            v2 = b2 + scal(d2, cB);
+            US[gi] = v0;
+            US[FS + gi] = v1;
+            US[2 * FS + gi] = v2;
+          } else {
+            v0 = ld_1(0, j) + scal(d0, cA);
+            v1 = ld_1(1, j) + scal(d1, cA);
+            v2 = ld_1(2, j) + scal(d2, cA);
+            U[gi] = v0;
+            U[FS + gi] = v1;
+            U[2 * FS + gi] = v2;
+          }
+          if constexpr (G::XPRE && !G::XWIDE) {
+            // u into lines 0-2 (padded, where this thread read N_hat), omega into
+            // state rows 0-2 (unpadded, where this thread read the stage state)
+            const cx<T> s0 = scal(v0, sc), s1 = scal(v1, sc), s2 = scal(v2, sc);
+            s[0 * LS + pj] = conjg(s0);
+            s[1 * LS + pj] = conjg(s1);
+            s[2 * LS + pj] = conjg(s2);
+            st[0 * N + j] = conjg(mul_pi(mk(kyv * s2.x - kzv * s1.x, kyv * s2.y - kzv * s1.y)));
+            st[1 * N + j] = conjg(mul_pi(mk(kzv * s0.x - kx * s2.x, kzv * s0.y - kx * s2.y)));
+            st[2 * N + j] = conjg(mul_pi(mk(kx * s1.x - kyv * s0.x, kx * s1.y - kyv * s0.y)));
+          } else {
+            put_curl_lines<T>(s, pj, LS, v0, v1, v2, kx, kyv, kzv, sc);
+          }
         }
       }
-      const T k2 = kx * kx + kyv * kyv + kzv * kzv;
-      const T ik2 = k2 > (T)0 ? (T)1 / k2 : (T)0;
-      // P = (k . N_hat) / |k|^2   (Eq. mod_pressure without the factor i)
-      const cx<T> p = mk((kx * n0.x + kyv * n1.x + kzv * n2.x) * ik2, (kx * n0.y + kyv * n1.y + kzv * n2.y) * ik2);
-      const size_t gi = rb + j;
-      const cx<T> u0 = ld_s(0, j), u1 = ld_s(1, j), u2 = ld_s(2, j);
-      const T nk2 = nu * k2;
-      // dU = N_hat - k P - nu |k|^2 u_hat   (Eq. NSfinal)
-      const cx<T> d0 = mk(n0.x - kx * p.x - nk2 * u0.x, n0.y - kx * p.y - nk2 * u0.y);
-      const cx<T> d1 = mk(n1.x - kyv * p.x - nk2 * u1.x, n1.y - kyv * p.y - nk2 * u1.y);
-      const cx<T> d2 = mk(n2.x - kzv * p.x - nk2 * u2.x, n2.y - kzv * p.y - nk2 * u2.y);
-      if constexpr (MODE == XM_RHS) {
-        cx<T>* out = reinterpret_cast<cx<T>*>(a.out);
-        out[gi] = d0;
-        out[FS + gi] = d1;
-        out[2 * FS + gi] = d2;
-      } else {
-        cx<T> v0, v1, v2;
-        if (stage == 0 && last == 0) {  // one-stage step (forward Euler): u += a_0 dt dU
-          v0 = u0 + scal(d0, cA);
-          v1 = u1 + scal(d1, cA);
-          v2 = u2 + scal(d2, cA);
-          U[gi] = v0;
-          U[FS + gi] = v1;
-          U[2 * FS + gi] = v2;
-        } else if (stage == 0) {
-          U1[gi] = u0 + scal(d0, cA);
-          U1[FS + gi] = u1 + scal(d1, cA);
-          U1[2 * FS + gi] = u2 + scal(d2, cA);
-          v0 = u0 + scal(d0, cB);
-          v1 = u1 + scal(d1, cB);
-          v2 = u2 + scal(d2, cB);
-          US[gi] = v0;
-          US[FS + gi] = v1;
-          US[2 * FS + gi] = v2;
-        } else if (stage < last) {
-          const cx<T> b0 = ld_0(0, j), b1 = ld_0(1, j), b2 = ld_0(2, j);
-          U1[gi] = ld_1(0, j) + scal(d0, cA);
-          U1[FS + gi] = ld_1(1, j) + scal(d1, cA);
-          U1[2 * FS + gi] = ld_1(2, j) + scal(d2, cA);
-          v0 = b0 + scal(d0, cB);
-          v1 = b1 + scal(d1, cB);
-          v2 = b2 + scal(d2, cB);
-          US[gi] = v0;
-          US[FS + gi] = v1;
-          US[2 * FS + gi] = v2;
-        } else {
-          v0 = ld_1(0, j) + scal(d0, cA);
-          v1 = ld_1(1, j) + scal(d1, cA);
-          v2 = ld_1(2, j) + scal(d2, cA);
-          U[gi] = v0;
-          U[FS + gi] = v1;
-          U[2 * FS + gi] = v2;
-        }
-        if constexpr (G::XPRE && !G::XWIDE) {
-          // u into lines 0-2 (padded, where this thread read N_hat), omega into
-          // state rows 0-2 (unpadded, where this thread read the stage state)
-          const cx<T> s0 = scal(v0, sc), s1 = scal(v1, sc), s2 = scal(v2, sc);
-          s[0 * LS + pj] = conjg(s0);
-          s[1 * LS + pj] = conjg(s1);
-          s[2 * LS + pj] = conjg(s2);
-          st[0 * N + j] = conjg(mul_pi(mk(kyv * s2.x - kzv * s1.x, kyv * s2.y - kzv * s1.y)));
-          st[1 * N + j] = conjg(mul_pi(mk(kzv * s0.x - kx * s2.x, kzv * s0.y - kx * s2.y)));
-          st[2 * N + j] = conjg(mul_pi(mk(kx * s1.x - kyv * s0.x, kx * s1.y - kyv * s0.y)));
-        } else {
-          put_curl_lines<T>(s, pj, LS, v0, v1, v2, kx, kyv, kzv, sc);
-        }
-      }
-    }
+    };
+    if (ksx == (T)1)
+      columns(std::false_type{});
+    else
+      columns(std::true_type{});
     if constexpr (MODE == XM_STAGE) {
       __syncthreads();
       if constexpr (G::XPRE && !G::XWIDE) {
@@ -311,7 +339,7 @@ __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
       const size_t gi = rb + j;
       const int pj = padp(j);
       const cx<T> u0 = U[gi], u1 = U[FS + gi], u2 = U[2 * FS + gi];
-      const T kx = (T)kfreq(j, N);
+      const T kx = (T)kfreq(j, N) * ksx;
       if constexpr (MODE == XM_INV_CURL) {
         put_curl_lines<T>(s, pj, LS, u0, u1, u2, kx, kyv, kzv, sc);
       } else if constexpr (MODE == XM_INV_PLAIN) {
@@ -1570,7 +1598,7 @@ __global__ void __launch_bounds__(DG_THREADS) k_diag(PassArgs a) {
   double se = 0, sz = 0, sh = 0, bad = 0;
   for (size_t i = (size_t)blockIdx.x * DG_THREADS + threadIdx.x; i < FS; i += (size_t)gridDim.x * DG_THREADS) {
     const int kxi = (int)(i % N), kyi = (int)((i / N) % N), kzi = (int)(i / ((size_t)N * N));
-    const double kx = kfreq(kxi, N), ky = kfreq(kyi, N), kz = kzi;
+    const double kx = kfreq(kxi, N) * a.ks[0], ky = kfreq(kyi, N) * a.ks[1], kz = kzi * a.ks[2];
     const double w = kzi == 0 ? 1.0 : 2.0;
     const cx<T> a0 = U[i], a1 = U[FS + i], a2 = U[2 * FS + i];
     const double u0r = a0.x, u0i = a0.y, u1r = a1.x, u1i = a1.y, u2r = a2.x, u2i = a2.y;
@@ -1698,7 +1726,7 @@ struct SolverImpl {
   static cudaError_t x_inverse_curl(const PassArgs& a0, int from_stage, cudaStream_t st) {
     PassArgs a = a0;
     if (from_stage) a.U = a.US;
-    k_xpass<T, N, XM_INV_CURL><<<M * N, XP_THREADS, G::XSMEM, st>>>(a);
+    k_xpass<T, N, XM_INV_CURL><<<M * N, XP_THREADS, G::XSMEM, st>>>(f32args(a));
     return cudaGetLastError();
   }
 
@@ -1712,7 +1740,7 @@ struct SolverImpl {
 
   static cudaError_t rk_stage(const PassArgs& a, cudaStream_t st) {
     rhs_front(a, st);
-    k_xpass<T, N, XM_STAGE><<<M * N, XP_THREADS, xsmem_stage(a.stage, a.last), st>>>(a);
+    k_xpass<T, N, XM_STAGE><<<M * N, XP_THREADS, xsmem_stage(a.stage, a.last), st>>>(f32args(a));
     return cudaGetLastError();
   }
 
@@ -1723,7 +1751,7 @@ struct SolverImpl {
       case 0: k_ypass<T, N, 1, 0><<<dim3(N / YCfg<T, N, 1>::TX, M, 6), YCfg<T, N, 1>::THREADS, YCfg<T, N, 1>::SMEM, st>>>(W, tw, a.kmax3); break;
       case 1: z_cross(a, st); break;
       case 2: k_ypass<T, N, 0, 1><<<dim3(N / YCfg<T, N, 0>::TX, kc_of(a.kmax3), 3), YCfg<T, N, 0>::THREADS, YCfg<T, N, 0>::SMEM, st>>>(W, tw, a.kmax3); break;
-      default: k_xpass<T, N, XM_STAGE><<<M * N, XP_THREADS, xsmem_stage(a.stage, a.last), st>>>(a); break;
+      default: k_xpass<T, N, XM_STAGE><<<M * N, XP_THREADS, xsmem_stage(a.stage, a.last), st>>>(f32args(a)); break;
     }
     return cudaGetLastError();
   }
@@ -1732,7 +1760,7 @@ struct SolverImpl {
     if constexpr (N <= BATCH_MAX_N && N != 512 && N != 1024 && !ZCross<T, N>::enabled) {
       if (count < 1 || count > BATCH_MAX_COUNT) return cudaErrorInvalidValue;
       BatchArgs B;
-      for (int i = 0; i < count; ++i) B.a[i] = A[i];
+      for (int i = 0; i < count; ++i) B.a[i] = f32args(A[i]);
       k_ypass_b<T, N, 1, 0><<<dim3(N / YCfg<T, N, 1>::TX, M, 6 * count), YCfg<T, N, 1>::THREADS, YCfg<T, N, 1>::SMEM, st>>>(B, 6);
       k_zpass_b<T, N, ZM_CROSS><<<dim3(N / G::ZTX, N, count), ZP_THREADS, G::ZSMEM, st>>>(B);
       k_ypass_b<T, N, 0, 1><<<dim3(N / YCfg<T, N, 0>::TX, kc_of(kmax3), 3 * count), YCfg<T, N, 0>::THREADS, YCfg<T, N, 0>::SMEM, st>>>(B, 3);
@@ -1749,7 +1777,7 @@ struct SolverImpl {
     rhs_front(a, st);
     PassArgs b = a;
     b.stage = 0;
-    k_xpass<T, N, XM_RHS><<<M * N, XP_THREADS, xsmem_stage(0, 3), st>>>(b);
+    k_xpass<T, N, XM_RHS><<<M * N, XP_THREADS, xsmem_stage(0, 3), st>>>(f32args(b));
     return cudaGetLastError();
   }
 
@@ -1757,12 +1785,12 @@ struct SolverImpl {
     k_zpass<T, N, ZM_LOAD><<<dim3(N / G::ZTX, N), ZP_THREADS, G::ZSMEM, st>>>(a);
     k_ypass<T, N, 0, 0><<<dim3(N / YCfg<T, N, 0>::TX, M, 3), YCfg<T, N, 0>::THREADS, YCfg<T, N, 0>::SMEM, st>>>(
         reinterpret_cast<cx<T>*>(a.U), reinterpret_cast<const cx<T>*>(a.tw), a.kmax3);
-    k_xpass<T, N, XM_FWD_STORE><<<M * N, XP_THREADS, G::XSMEM, st>>>(a);
+    k_xpass<T, N, XM_FWD_STORE><<<M * N, XP_THREADS, G::XSMEM, st>>>(f32args(a));
     return cudaGetLastError();
   }
 
   static cudaError_t inverse3d(const PassArgs& a, cudaStream_t st) {
-    k_xpass<T, N, XM_INV_PLAIN><<<M * N, XP_THREADS, G::XSMEM, st>>>(a);
+    k_xpass<T, N, XM_INV_PLAIN><<<M * N, XP_THREADS, G::XSMEM, st>>>(f32args(a));
     k_ypass<T, N, 1, 0><<<dim3(N / YCfg<T, N, 1>::TX, M, 3), YCfg<T, N, 1>::THREADS, YCfg<T, N, 1>::SMEM, st>>>(
         reinterpret_cast<cx<T>*>(a.W), reinterpret_cast<const cx<T>*>(a.tw), a.kmax3);
     k_zpass<T, N, ZM_STORE><<<dim3(N / G::ZTX, N), ZP_THREADS, G::ZSMEM, st>>>(a);
@@ -1772,7 +1800,7 @@ struct SolverImpl {
   static cudaError_t diag(const PassArgs& a, cudaStream_t st) {
     k_diag<T, N><<<DIAG_BLOCKS, DG_THREADS, 0, st>>>(a);
     k_diag_final<<<1, 32, 0, st>>>(a.partials, DIAG_BLOCKS);
-    k_xpass<T, N, XM_INV_DIV><<<M * N, XP_THREADS, G::XSMEM, st>>>(a);
+    k_xpass<T, N, XM_INV_DIV><<<M * N, XP_THREADS, G::XSMEM, st>>>(f32args(a));
     k_ypass<T, N, 1, 0><<<dim3(N / YCfg<T, N, 1>::TX, M, 1), YCfg<T, N, 1>::THREADS, YCfg<T, N, 1>::SMEM, st>>>(
         reinterpret_cast<cx<T>*>(a.D), reinterpret_cast<const cx<T>*>(a.tw), a.kmax3);
     cudaMemsetAsync(a.maxbits, 0, sizeof(unsigned long long), st);

@@ -48,10 +48,11 @@ INTEGRATORS = {"rk4": 0, "euler": 1, "heun": 2, "midpoint": 3}
 
 class Solver:
     """One dns_handle: N^3 grid, viscosity nu, time step dt, 'f32' or 'f64'; integrator
-    'rk4' (the Appendix driver, default), 'euler', 'heun' or 'midpoint'."""
+    'rk4' (the Appendix driver, default), 'euler', 'heun' or 'midpoint'; box lengths
+    (Lx, Ly, Lz), default (2 pi, 2 pi, 2 pi)."""
 
     def __init__(self, N: int, nu: float, dt: float, dtype: str = "f32", dealias_variant: int = 0,
-                 integrator: str = "rk4"):
+                 integrator: str = "rk4", lengths=None):
         if integrator not in INTEGRATORS:
             raise ValueError(f"integrator must be one of {sorted(INTEGRATORS)}, got {integrator!r}")
         self.N = int(N)
@@ -66,6 +67,9 @@ class Solver:
             self.set_option("dealias_variant", dealias_variant)
         if integrator != "rk4":
             self.set_option("integrator", INTEGRATORS[integrator])
+        if lengths is not None:  # box lengths (Lx, Ly, Lz); default 2 pi each
+            for key, L in zip(("Lx", "Ly", "Lz"), lengths):
+                self.set_option(key, float(L))
 
     @classmethod
     def _borrow(cls, handle: ctypes.c_void_p, N: int, dtype: str):
