@@ -103,11 +103,31 @@ int dns_set_stream(dns_handle* h, void* stream);
  *                      Lx / N and the wavenumber of index l is 2 pi l / Lx (Sec. 2
  *                      footnote, Sec. 3.1: other box sizes by scaling). The 2/3
  *                      rule acts on the indices; the SGS helpers assume 2 pi.
+ *   "y_tile_inverse", "y_tile_forward"
+ *                      x columns per block of the stage's inverse and forward
+ *                      y-passes: 0 (default) or a width the grid offers (4, 8, 16,
+ *                      32 as far as they divide N and fit 256-byte rows; N <= 128
+ *                      only). The arithmetic of every column is the same, so the
+ *                      results do not depend on it; see dns_tune_y_tiles.
  *   "use_graph"        1: dns_step replays a captured CUDA graph (default)
  *   "nu", "dt"         change the viscosity / time step
  *   "time"             set the simulated time reported by dns_diagnostics
  * Errors: DNS_ERR_ARG for an unknown key or a value out of range. */
 int dns_set_option(dns_handle* h, const char* key, double value);
+
+/* The current value of an option of dns_set_option ("time" included) in *value.
+ * Errors: DNS_ERR_ARG for an unknown key or a NULL pointer. */
+int dns_get_option(const dns_handle* h, const char* key, double* value);
+
+/* Schedule tuner for the small grids: times dns_step with every y-pass tile width
+ * the grid offers (default included), `steps` graph replays each after a capture
+ * and a warm-up step, first over the inverse pass's width, then over the forward
+ * pass's; keeps the fastest pair (written to *best_inverse, *best_forward; 0 =
+ * default). Every candidate starts from the same state, and the state and time are
+ * restored at the end; the results of later steps do not depend on the choice.
+ * Allocates and frees one state copy (3 fields). Synchronises. Errors: DNS_ERR_ARG
+ * (steps < 1, NULL outputs), DNS_ERR_OOM, DNS_ERR_CUDA. */
+int dns_tune_y_tiles(dns_handle* h, int steps, int* best_inverse, int* best_forward);
 
 /* State from a physical velocity field u (3,N,N,N): u_hat = F(u) with the
  * Nyquist modes zeroed (Eq. iffteq forward transform; no projection).
@@ -192,7 +212,11 @@ int dns_spectral_sums_noalloc(const void* uhat, int N, int dtype, double nu, dou
  * coefficients passed as kernel parameters); every batch, and every member that is not batched, is
  * a parallel branch of the graph. With batching off (max_batch = 0) every
  * member runs its own kernels and the members are spread over `streams`
- * branches (0 = one branch per member). dns_ensemble_tune times a set of
+ * branches (0 = one branch per member). dns_ensemble_tune first tunes the
+ * y-pass tile widths of each grid size class on one of its members
+ * (dns_tune_y_tiles; that member's state is kept) and gives every member of the
+ * class the widths found (they apply to per-member launches; batched launches
+ * keep the default), then times a set of
  * schedules (batched, and per-member over 1 .. count branches) on the actual
  * members and keeps the fastest; it ADVANCES every member by 2 steps per
  * schedule tried (the count is returned in the members' time, dns_diag.t) and

@@ -170,6 +170,7 @@ struct dns_handle {
   int variant = 0;
   int integrator = 0;  // index into RK_SCHEMES
   double L[3] = {kTwoPi, kTwoPi, kTwoPi};  // box lengths along x, y, z
+  int ytile[2] = {0, 0};  // y-pass tile widths of the stage (inverse, forward); 0 = default
   int use_graph = 1;
   double nu = 0.0, dt = 0.0, t = 0.0;
   const DnsOps* ops = nullptr;
@@ -236,6 +237,8 @@ PassArgs base_args(const dns_handle* h) {
   a.nu = h->nu;
   a.kmax3 = h->N + 2 * h->variant;
   for (int i = 0; i < 3; ++i) a.ks[i] = kTwoPi / h->L[i];  // exactly 1 on the 2 pi box
+  a.ytile[0] = h->ytile[0];
+  a.ytile[1] = h->ytile[1];
   a.partials = h->diag;
   a.maxbits = reinterpret_cast<unsigned long long*>(h->diag + DIAG_BLOCKS * 4 + 4);
   return a;
@@ -402,6 +405,13 @@ int dns_set_option(dns_handle* h, const char* key, double value) {
   } else if (!strcmp(key, "Lx") || !strcmp(key, "Ly") || !strcmp(key, "Lz")) {
     if (!(value > 0.0) || !std::isfinite(value)) return fail(DNS_ERR_ARG, "%s must be finite and > 0", key);
     h->L[key[1] - 'x'] = value;
+  } else if (!strcmp(key, "y_tile_inverse") || !strcmp(key, "y_tile_forward")) {
+    int tiles[8];
+    const int n = h->ops->y_tiles(tiles, 8);
+    bool ok = value == 0.0;
+    for (int i = 0; i < n; ++i) ok = ok || value == (double)tiles[i];
+    if (!ok) return fail(DNS_ERR_ARG, "%s: %g is not a tile width of this grid", key, value);
+    h->ytile[key[7] == 'i' ? 0 : 1] = (int)value;
   } else if (!strcmp(key, "use_graph")) {
     if (value != 0.0 && value != 1.0) return fail(DNS_ERR_ARG, "use_graph must be 0 or 1");
     h->use_graph = (int)value;
@@ -422,6 +432,95 @@ int dns_set_option(dns_handle* h, const char* key, double value) {
   ++h->epoch;
   h->w_valid = false;  // the x-inverse in W does not depend on these, but keep it simple
   return DNS_OK;
+}
+
+int dns_get_option(const dns_handle* h, const char* key, double* value) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!key || !value) return fail(DNS_ERR_ARG, "dns_get_option: key or value is NULL");
+  if (!strcmp(key, "dealias_variant")) *value = h->variant;
+  else if (!strcmp(key, "integrator")) *value = h->integrator;
+  else if (!strcmp(key, "Lx") || !strcmp(key, "Ly") || !strcmp(key, "Lz")) *value = h->L[key[1] - 'x'];
+  else if (!strcmp(key, "y_tile_inverse")) *value = h->ytile[0];
+  else if (!strcmp(key, "y_tile_forward")) *value = h->ytile[1];
+  else if (!strcmp(key, "use_graph")) *value = h->use_graph;
+  else if (!strcmp(key, "nu")) *value = h->nu;
+  else if (!strcmp(key, "dt")) *value = h->dt;
+  else if (!strcmp(key, "time")) *value = h->t;
+  else return fail(DNS_ERR_ARG, "dns_get_option: unknown key '%s'", key);
+  return DNS_OK;
+}
+
+int dns_tune_y_tiles(dns_handle* h, int steps, int* best_inverse, int* best_forward) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (steps < 1 || !best_inverse || !best_forward) return fail(DNS_ERR_ARG, "dns_tune_y_tiles: bad arguments");
+  if ((rc = use_device(h))) return rc;
+  int cand[9] = {0};
+  const int nc = 1 + h->ops->y_tiles(cand + 1, 8);
+  if (nc == 1) {  // this grid offers the default width only
+    *best_inverse = h->ytile[0];
+    *best_forward = h->ytile[1];
+    return DNS_OK;
+  }
+  const size_t bytes = 3 * h->fs * h->ops->elem_bytes;
+  void* save = nullptr;
+  if ((rc = dev_alloc(h, &save, bytes, "tuning copy of the state"))) return rc;
+  const double t0 = h->t;
+  const int keep[2] = {h->ytile[0], h->ytile[1]};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t err = cudaMemcpyAsync(save, h->U, bytes, cudaMemcpyDeviceToDevice, h->stream);
+  if (err == cudaSuccess) err = cudaEventCreate(&e0);
+  if (err == cudaSuccess) err = cudaEventCreate(&e1);
+  if (err != cudaSuccess) rc = cuda_fail(err, "dns_tune_y_tiles set-up");
+  // each candidate starts from the saved state: capture and one warm-up step, then
+  // `steps` timed steps exactly as dns_step runs them
+  auto timed = [&](int ti, int tf, float* ms) -> int {
+    h->ytile[0] = ti;
+    h->ytile[1] = tf;
+    h->graph_dirty = true;
+    cudaError_t ce = cudaMemcpyAsync(h->U, save, bytes, cudaMemcpyDeviceToDevice, h->stream);
+    if (ce != cudaSuccess) return cuda_fail(ce, "dns_tune_y_tiles copy");
+    h->w_valid = false;
+    int r = dns_step(h, 1);
+    if (r) return r;
+    if ((ce = cudaEventRecord(e0, h->stream)) != cudaSuccess) return cuda_fail(ce, "dns_tune_y_tiles event");
+    if ((r = dns_step(h, steps))) return r;
+    if ((ce = cudaEventRecord(e1, h->stream)) == cudaSuccess) ce = cudaEventSynchronize(e1);
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(ms, e0, e1);
+    return ce == cudaSuccess ? DNS_OK : cuda_fail(ce, "dns_tune_y_tiles timing");
+  };
+  // inverse widths with the forward width kept, then forward widths with the best inverse
+  int bi = keep[0], bf = keep[1];
+  float best = 1e30f, ms = 0.f;
+  for (int c = 0; c < nc && !rc; ++c)
+    if (!(rc = timed(cand[c], keep[1], &ms)) && ms < best) {
+      best = ms;
+      bi = cand[c];
+    }
+  best = 1e30f;
+  for (int c = 0; c < nc && !rc; ++c)
+    if (!(rc = timed(bi, cand[c], &ms)) && ms < best) {
+      best = ms;
+      bf = cand[c];
+    }
+  // the state and time as before; the fastest widths kept
+  err = cudaMemcpyAsync(h->U, save, bytes, cudaMemcpyDeviceToDevice, h->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(h->stream);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(save);
+  h->bytes -= bytes;
+  h->t = t0;
+  h->w_valid = false;
+  h->ytile[0] = rc ? keep[0] : bi;
+  h->ytile[1] = rc ? keep[1] : bf;
+  h->graph_dirty = true;
+  ++h->epoch;
+  if (!rc && err != cudaSuccess) rc = cuda_fail(err, "dns_tune_y_tiles restore");
+  *best_inverse = h->ytile[0];
+  *best_forward = h->ytile[1];
+  return rc;
 }
 
 int dns_set_state(dns_handle* h, const void* u, int on_device) {
@@ -930,7 +1029,27 @@ int dns_ensemble_step(dns_ensemble* e, int n) {
 
 int dns_ensemble_tune(dns_ensemble* e, int* best_streams) {
   if (!e) return fail(DNS_ERR_ARG, "dns_ensemble_tune: ensemble is NULL");
-  int rc = ens_prepare_members(e);
+  // y-pass tile widths per size class: tuned on one member (its state is kept),
+  // applied to every member of the class
+  int rc = DNS_OK;
+  std::vector<const DnsOps*> done_ops;
+  std::vector<std::pair<int, int>> done_tiles;
+  for (dns_handle* h : e->m) {
+    size_t k = 0;
+    while (k < done_ops.size() && done_ops[k] != h->ops) ++k;
+    if (k == done_ops.size()) {
+      int ti = 0, tf = 0;
+      if ((rc = dns_tune_y_tiles(h, 5, &ti, &tf))) return rc;
+      done_ops.push_back(h->ops);
+      done_tiles.push_back({ti, tf});
+    } else if (h->ytile[0] != done_tiles[k].first || h->ytile[1] != done_tiles[k].second) {
+      h->ytile[0] = done_tiles[k].first;
+      h->ytile[1] = done_tiles[k].second;
+      h->graph_dirty = true;
+      ++h->epoch;
+    }
+  }
+  rc = ens_prepare_members(e);
   if (rc) return rc;
   const int n = (int)e->m.size();
   // candidate schedules: batched launches (whole groups, then smaller batches,

@@ -31,6 +31,7 @@ struct PassArgs {
   // launched), so that they need no double-to-float conversion per thread
   float f_nu = 0.f, f_cA = 0.f, f_cB = 0.f;
   float f_ks[3] = {1.f, 1.f, 1.f};
+  int ytile[2] = {0, 0};  // y-pass tile widths of the stage launches (inverse, forward); 0 = default
   const void* in = nullptr;  // physical input (3,N,N,N) for set_state
   void* out = nullptr;       // physical output (3,N,N,N) / RHS output
   double* partials = nullptr;          // diagnostics block partials
@@ -63,6 +64,9 @@ struct DnsOps {
   // the arguments travelling as kernel parameters. nullptr where one member
   // already fills the GPU (N > BATCH_MAX_N).
   cudaError_t (*rk_stage_batch)(const PassArgs* A, int count, int kmax3, cudaStream_t s);
+  // tile widths (x columns per block) the stage's y-passes offer besides the
+  // default, written to tiles[0..count); returns count (<= max)
+  int (*y_tiles)(int* tiles, int max);
 };
 
 constexpr int BATCH_MAX_N = 128;
@@ -70,6 +74,7 @@ constexpr int BATCH_MAX_COUNT = 32;
 struct BatchArgs {  // by-value kernel parameter (constant bank) of the batched passes
   PassArgs a[BATCH_MAX_COUNT];
 };
+static_assert(sizeof(BatchArgs) <= 32764, "kernel parameters are limited to 32764 bytes");
 
 constexpr int DIAG_BLOCKS = 592;  // 4 x 148..152 SMs: one wave of 4 blocks per SM
 

@@ -78,10 +78,11 @@ struct Geometry {
 // SM); the forward pass (3 fields, pruned) takes 64-byte rows, one warp per column, 4
 // blocks per SM (both measured at 512^3). FP64 keeps 128-byte rows up to N = 512,
 // 64-byte rows above.
-template <typename T, int N, int INV>
+// TXO > 0 replaces the tile width (a tuned schedule of the small grids).
+template <typename T, int N, int INV, int TXO = 0>
 struct YCfg {
   static constexpr int CB = (int)sizeof(cx<T>);
-  static constexpr int TX = cmin(((INV || CB == 16) && N <= 512 ? 128 : 64) / CB, pow2_part(N));
+  static constexpr int TX = TXO > 0 ? TXO : cmin(((INV || CB == 16) && N <= 512 ? 128 : 64) / CB, pow2_part(N));
   static constexpr int THREADS = cmin(32 * TX, 256);
   static constexpr int LD = odd_ld(TX);
   static constexpr size_t SMEM = (size_t)padded_len(N) * LD * CB;
@@ -393,12 +394,12 @@ __device__ __forceinline__ int ywalk_row(int r) {
   }
 }
 
-template <typename T, int N, int INV, int PRUNE>
-__global__ void __launch_bounds__(YCfg<T, N, INV>::THREADS, (YCfg<T, N, INV>::MINB)) k_ypass(cx<T>* __restrict__ F,
+template <typename T, int N, int INV, int PRUNE, int TXO = 0>
+__global__ void __launch_bounds__(YCfg<T, N, INV, TXO>::THREADS, (YCfg<T, N, INV, TXO>::MINB)) k_ypass(cx<T>* __restrict__ F,
                                                                                          const cx<T>* __restrict__ tw,
                                                                                          int kmax3) {
   using G = Geometry<T, N>;
-  using Y = YCfg<T, N, INV>;
+  using Y = YCfg<T, N, INV, TXO>;
   constexpr int TX = Y::TX;
   constexpr int LD = Y::LD;
   constexpr int NT = Y::THREADS;  // warps loop over the columns
@@ -1659,8 +1660,47 @@ struct SolverImpl {
     return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   }
 
+  // y-pass tile widths offered to a tuner besides the default (grids of the
+  // ensembles only, to bound the number of instantiations)
+  static constexpr bool ytile_ok(int t) {
+    return N <= BATCH_MAX_N && t >= 4 && t <= 32 && pow2_part(N) % t == 0 && t * (int)sizeof(cx<T>) <= 256;
+  }
+  template <int TXO>
+  static void tile_attr(cudaError_t& e) {
+    if constexpr (ytile_ok(TXO)) {
+      if (e == cudaSuccess) e = smem_attr(k_ypass<T, N, 1, 0, TXO>, YCfg<T, N, 1, TXO>::SMEM);
+      if (e == cudaSuccess) e = smem_attr(k_ypass<T, N, 0, 1, TXO>, YCfg<T, N, 0, TXO>::SMEM);
+    }
+  }
+  static int y_tiles(int* tiles, int max) {
+    int n = 0;
+    for (int t = 4; t <= 32; t *= 2)
+      if (ytile_ok(t) && n < max) tiles[n++] = t;
+    return n;
+  }
+  template <int INV, int PRUNE, int TXO>
+  static void y_go(cx<T>* F, const cx<T>* tw, int kmax3, int planes, int fields, cudaStream_t st) {
+    using Y = YCfg<T, N, INV, TXO>;
+    k_ypass<T, N, INV, PRUNE, TXO><<<dim3(N / Y::TX, planes, fields), Y::THREADS, Y::SMEM, st>>>(F, tw, kmax3);
+  }
+  // the stage's y-pass with tile width `tile` (0, or a width not offered: the default)
+  template <int INV, int PRUNE>
+  static void y_stage(int tile, cx<T>* F, const cx<T>* tw, int kmax3, int planes, int fields, cudaStream_t st) {
+    if constexpr (N <= BATCH_MAX_N) {
+      if constexpr (ytile_ok(4)) if (tile == 4) return y_go<INV, PRUNE, 4>(F, tw, kmax3, planes, fields, st);
+      if constexpr (ytile_ok(8)) if (tile == 8) return y_go<INV, PRUNE, 8>(F, tw, kmax3, planes, fields, st);
+      if constexpr (ytile_ok(16)) if (tile == 16) return y_go<INV, PRUNE, 16>(F, tw, kmax3, planes, fields, st);
+      if constexpr (ytile_ok(32)) if (tile == 32) return y_go<INV, PRUNE, 32>(F, tw, kmax3, planes, fields, st);
+    }
+    y_go<INV, PRUNE, 0>(F, tw, kmax3, planes, fields, st);
+  }
+
   static cudaError_t prepare() {
     cudaError_t e = cudaSuccess;
+    tile_attr<4>(e);
+    tile_attr<8>(e);
+    tile_attr<16>(e);
+    tile_attr<32>(e);
 #define DNS_ATTR(kern, bytes) \
   if (e == cudaSuccess) e = smem_attr(kern, bytes)
     DNS_ATTR((k_xpass<T, N, XM_INV_CURL>), G::XSMEM);
@@ -1733,9 +1773,9 @@ struct SolverImpl {
   static void rhs_front(const PassArgs& a, cudaStream_t st) {
     cx<T>* W = reinterpret_cast<cx<T>*>(a.W);
     const cx<T>* tw = reinterpret_cast<const cx<T>*>(a.tw);
-    k_ypass<T, N, 1, 0><<<dim3(N / YCfg<T, N, 1>::TX, M, 6), YCfg<T, N, 1>::THREADS, YCfg<T, N, 1>::SMEM, st>>>(W, tw, a.kmax3);
+    y_stage<1, 0>(a.ytile[0], W, tw, a.kmax3, M, 6, st);
     z_cross(a, st);
-    k_ypass<T, N, 0, 1><<<dim3(N / YCfg<T, N, 0>::TX, kc_of(a.kmax3), 3), YCfg<T, N, 0>::THREADS, YCfg<T, N, 0>::SMEM, st>>>(W, tw, a.kmax3);
+    y_stage<0, 1>(a.ytile[1], W, tw, a.kmax3, kc_of(a.kmax3), 3, st);
   }
 
   static cudaError_t rk_stage(const PassArgs& a, cudaStream_t st) {
@@ -1748,9 +1788,9 @@ struct SolverImpl {
     cx<T>* W = reinterpret_cast<cx<T>*>(a.W);
     const cx<T>* tw = reinterpret_cast<const cx<T>*>(a.tw);
     switch (part) {
-      case 0: k_ypass<T, N, 1, 0><<<dim3(N / YCfg<T, N, 1>::TX, M, 6), YCfg<T, N, 1>::THREADS, YCfg<T, N, 1>::SMEM, st>>>(W, tw, a.kmax3); break;
+      case 0: y_stage<1, 0>(a.ytile[0], W, tw, a.kmax3, M, 6, st); break;
       case 1: z_cross(a, st); break;
-      case 2: k_ypass<T, N, 0, 1><<<dim3(N / YCfg<T, N, 0>::TX, kc_of(a.kmax3), 3), YCfg<T, N, 0>::THREADS, YCfg<T, N, 0>::SMEM, st>>>(W, tw, a.kmax3); break;
+      case 2: y_stage<0, 1>(a.ytile[1], W, tw, a.kmax3, kc_of(a.kmax3), 3, st); break;
       default: k_xpass<T, N, XM_STAGE><<<M * N, XP_THREADS, xsmem_stage(a.stage, a.last), st>>>(f32args(a)); break;
     }
     return cudaGetLastError();
@@ -1812,7 +1852,7 @@ struct SolverImpl {
     constexpr bool batched = N <= BATCH_MAX_N && !ZCross<T, N>::enabled;
     static const DnsOps o = {N,         sizeof(T) == 4 ? 0 : 1, sizeof(cx<T>), &prepare,   &x_inverse_curl,
                              &rk_stage, &rk_stage_part,        &rhs,          &forward3d, &inverse3d,
-                             &diag,     batched ? &rk_stage_batch : nullptr};
+                             &diag,     batched ? &rk_stage_batch : nullptr, &y_tiles};
     return &o;
   }
 };

@@ -124,6 +124,19 @@ class Solver:
     def set_option(self, key: str, value: float):
         _lib.check(_lib.lib().dns_set_option(self._h, key.encode(), float(value)), "dns_set_option")
 
+    def get_option(self, key: str) -> float:
+        v = ctypes.c_double()
+        _lib.check(_lib.lib().dns_get_option(self._h, key.encode(), ctypes.byref(v)), "dns_get_option")
+        return v.value
+
+    def tune_y_tiles(self, steps: int = 5) -> tuple:
+        """Time dns_step with each y-pass tile width the grid offers; keep the fastest
+        (inverse, forward) pair (0 = default). The state and time are left unchanged."""
+        ti, tf = ctypes.c_int(), ctypes.c_int()
+        _lib.check(_lib.lib().dns_tune_y_tiles(self._h, int(steps), ctypes.byref(ti), ctypes.byref(tf)),
+                   "dns_tune_y_tiles")
+        return ti.value, tf.value
+
     def set_state(self, u):
         p, dev = _ptr(u, self.phys_shape, self._rb, False)
         _lib.check(_lib.lib().dns_set_state(self._h, p, dev), "dns_set_state")
@@ -203,10 +216,14 @@ class Ensemble:
         _lib.check(_lib.lib().dns_ensemble_step(self._e, int(n)), "dns_ensemble_step")
 
     def tune(self) -> dict:
-        """Pick the schedule (batching, branch count) by timing; advances every member (see include/dns.h)."""
+        """Pick the y-pass tile widths per grid size and the schedule (batching, branch
+        count) by timing; advances every member (see include/dns.h)."""
         k = ctypes.c_int()
         _lib.check(_lib.lib().dns_ensemble_tune(self._e, ctypes.byref(k)), "dns_ensemble_tune")
-        return {"batching": self.batching, "streams": k.value}
+        tiles = {}
+        for m in self.members:
+            tiles.setdefault(m.N, [int(m.get_option("y_tile_inverse")), int(m.get_option("y_tile_forward"))])
+        return {"batching": self.batching, "streams": k.value, "y_tiles": tiles}
 
     def set_batching(self, max_batch: int):
         """0: every member runs its own kernels; n >= 1: up to n equal-size members share each launch."""
