@@ -185,6 +185,25 @@ def test_split_steps_equal_one_call():
     assert abs(t - 0.07) < 1e-15
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_checkpoint_and_resume_equal_an_uninterrupted_run(dtype):
+    # checkpoint = the spectral state and the time; a new handle resumes from it
+    N, nu, dt = 24, 0.01, 0.005
+    uh = iso_state(N, 33, dtype)
+    with Solver(N, nu, dt, dtype) as s:
+        s.set_state_spectral(uh)
+        s.step(4)
+        ck, t = s.get_state_spectral(), s.diagnostics()["t"]
+    with Solver(N, nu, dt, dtype) as r:
+        r.set_state_spectral(ck)
+        r.set_option("time", t)
+        r.step(3)
+        resumed, tr = r.get_state_spectral(), r.diagnostics()["t"]
+    ref, d = _run_gpu(N, nu, dt, 7, dtype, uh=uh)
+    assert np.array_equal(resumed, ref)
+    assert tr == d["t"]
+
+
 def test_abc_flow_decays_by_rk4_polynomial_on_gpu():
     N, nu, dt, n = 16, 0.2, 0.1, 7
     u = inputs.abc_flow(N)
