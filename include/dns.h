@@ -108,7 +108,10 @@ int dns_set_stream(dns_handle* h, void* stream);
  *                      y-passes: 0 (default) or a width the grid offers (4, 8, 16,
  *                      32 as far as they divide N and fit 256-byte rows; N <= 128
  *                      only). The arithmetic of every column is the same, so the
- *                      results do not depend on it; see dns_tune_y_tiles.
+ *                      results do not depend on it; see dns_tune_tiles.
+ *   "z_tile"           x columns per block of the generic z-pass of the small
+ *                      grids: 0 (default) or an offered width (4 .. 32); results
+ *                      independent of it, see dns_tune_tiles.
  *   "use_graph"        1: dns_step replays a captured CUDA graph (default)
  *   "nu", "dt"         change the viscosity / time step
  *   "time"             set the simulated time reported by dns_diagnostics
@@ -119,15 +122,16 @@ int dns_set_option(dns_handle* h, const char* key, double value);
  * Errors: DNS_ERR_ARG for an unknown key or a NULL pointer. */
 int dns_get_option(const dns_handle* h, const char* key, double* value);
 
-/* Schedule tuner for the small grids: times dns_step with every y-pass tile width
- * the grid offers (default included), `steps` graph replays each after a capture
- * and a warm-up step, first over the inverse pass's width, then over the forward
- * pass's; keeps the fastest pair (written to *best_inverse, *best_forward; 0 =
- * default). Every candidate starts from the same state, and the state and time are
- * restored at the end; the results of later steps do not depend on the choice.
- * Allocates and frees one state copy (3 fields). Synchronises. Errors: DNS_ERR_ARG
- * (steps < 1, NULL outputs), DNS_ERR_OOM, DNS_ERR_CUDA. */
-int dns_tune_y_tiles(dns_handle* h, int steps, int* best_inverse, int* best_forward);
+/* Schedule tuner for the small grids: times dns_step with every tile width the
+ * grid offers for the y-inverse, the y-forward and the z-pass (default included),
+ * one pass at a time with the best widths found before it, `steps` graph replays
+ * each after a capture and a warm-up step; keeps the fastest widths (written to
+ * *y_inverse, *y_forward, *z; 0 = default). Every candidate starts from the same
+ * state, and the state and time are restored at the end; the results of later
+ * steps do not depend on the choice. Allocates and frees one state copy (3
+ * fields). Synchronises. Errors: DNS_ERR_ARG (steps < 1, NULL outputs),
+ * DNS_ERR_OOM, DNS_ERR_CUDA. */
+int dns_tune_tiles(dns_handle* h, int steps, int* y_inverse, int* y_forward, int* z);
 
 /* State from a physical velocity field u (3,N,N,N): u_hat = F(u) with the
  * Nyquist modes zeroed (Eq. iffteq forward transform; no projection).
@@ -213,10 +217,10 @@ int dns_spectral_sums_noalloc(const void* uhat, int N, int dtype, double nu, dou
  * a parallel branch of the graph. With batching off (max_batch = 0) every
  * member runs its own kernels and the members are spread over `streams`
  * branches (0 = one branch per member). dns_ensemble_tune first tunes the
- * y-pass tile widths of each grid size class on one of its members
- * (dns_tune_y_tiles; that member's state is kept) and gives every member of the
- * class the widths found (they apply to per-member launches; batched launches
- * keep the default), then times a set of
+ * tile widths of each grid size class on one of its members
+ * (dns_tune_tiles, y- and z-pass widths; that member's state is kept) and gives
+ * every member of the class the widths found (they apply to per-member launches;
+ * batched launches keep the default), then times a set of
  * schedules (batched, and per-member over 1 .. count branches) on the actual
  * members and keeps the fastest; it ADVANCES every member by 2 steps per
  * schedule tried (the count is returned in the members' time, dns_diag.t) and

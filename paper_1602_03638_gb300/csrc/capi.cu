@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -171,6 +172,7 @@ struct dns_handle {
   int integrator = 0;  // index into RK_SCHEMES
   double L[3] = {kTwoPi, kTwoPi, kTwoPi};  // box lengths along x, y, z
   int ytile[2] = {0, 0};  // y-pass tile widths of the stage (inverse, forward); 0 = default
+  int ztile = 0;          // z-pass tile width of the stage; 0 = default
   int use_graph = 1;
   double nu = 0.0, dt = 0.0, t = 0.0;
   const DnsOps* ops = nullptr;
@@ -239,6 +241,7 @@ PassArgs base_args(const dns_handle* h) {
   for (int i = 0; i < 3; ++i) a.ks[i] = kTwoPi / h->L[i];  // exactly 1 on the 2 pi box
   a.ytile[0] = h->ytile[0];
   a.ytile[1] = h->ytile[1];
+  a.ztile = h->ztile;
   a.partials = h->diag;
   a.maxbits = reinterpret_cast<unsigned long long*>(h->diag + DIAG_BLOCKS * 4 + 4);
   return a;
@@ -412,6 +415,13 @@ int dns_set_option(dns_handle* h, const char* key, double value) {
     for (int i = 0; i < n; ++i) ok = ok || value == (double)tiles[i];
     if (!ok) return fail(DNS_ERR_ARG, "%s: %g is not a tile width of this grid", key, value);
     h->ytile[key[7] == 'i' ? 0 : 1] = (int)value;
+  } else if (!strcmp(key, "z_tile")) {
+    int tiles[8];
+    const int n = h->ops->z_tiles(tiles, 8);
+    bool ok = value == 0.0;
+    for (int i = 0; i < n; ++i) ok = ok || value == (double)tiles[i];
+    if (!ok) return fail(DNS_ERR_ARG, "z_tile: %g is not a tile width of this grid", value);
+    h->ztile = (int)value;
   } else if (!strcmp(key, "use_graph")) {
     if (value != 0.0 && value != 1.0) return fail(DNS_ERR_ARG, "use_graph must be 0 or 1");
     h->use_graph = (int)value;
@@ -443,6 +453,7 @@ int dns_get_option(const dns_handle* h, const char* key, double* value) {
   else if (!strcmp(key, "Lx") || !strcmp(key, "Ly") || !strcmp(key, "Lz")) *value = h->L[key[1] - 'x'];
   else if (!strcmp(key, "y_tile_inverse")) *value = h->ytile[0];
   else if (!strcmp(key, "y_tile_forward")) *value = h->ytile[1];
+  else if (!strcmp(key, "z_tile")) *value = h->ztile;
   else if (!strcmp(key, "use_graph")) *value = h->use_graph;
   else if (!strcmp(key, "nu")) *value = h->nu;
   else if (!strcmp(key, "dt")) *value = h->dt;
@@ -451,58 +462,68 @@ int dns_get_option(const dns_handle* h, const char* key, double* value) {
   return DNS_OK;
 }
 
-int dns_tune_y_tiles(dns_handle* h, int steps, int* best_inverse, int* best_forward) {
+int dns_tune_tiles(dns_handle* h, int steps, int* y_inverse, int* y_forward, int* z) {
   int rc = check_handle(h);
   if (rc) return rc;
-  if (steps < 1 || !best_inverse || !best_forward) return fail(DNS_ERR_ARG, "dns_tune_y_tiles: bad arguments");
+  if (steps < 1 || !y_inverse || !y_forward || !z) return fail(DNS_ERR_ARG, "dns_tune_tiles: bad arguments");
   if ((rc = use_device(h))) return rc;
-  int cand[9] = {0};
-  const int nc = 1 + h->ops->y_tiles(cand + 1, 8);
-  if (nc == 1) {  // this grid offers the default width only
-    *best_inverse = h->ytile[0];
-    *best_forward = h->ytile[1];
+  int ycand[9] = {0}, zcand[9] = {0};
+  const int ny = 1 + h->ops->y_tiles(ycand + 1, 8);
+  const int nz = 1 + h->ops->z_tiles(zcand + 1, 8);
+  if (ny == 1 && nz == 1) {  // this grid offers the default widths only
+    *y_inverse = h->ytile[0];
+    *y_forward = h->ytile[1];
+    *z = h->ztile;
     return DNS_OK;
   }
   const size_t bytes = 3 * h->fs * h->ops->elem_bytes;
   void* save = nullptr;
   if ((rc = dev_alloc(h, &save, bytes, "tuning copy of the state"))) return rc;
   const double t0 = h->t;
-  const int keep[2] = {h->ytile[0], h->ytile[1]};
+  const int keep[3] = {h->ytile[0], h->ytile[1], h->ztile};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t err = cudaMemcpyAsync(save, h->U, bytes, cudaMemcpyDeviceToDevice, h->stream);
   if (err == cudaSuccess) err = cudaEventCreate(&e0);
   if (err == cudaSuccess) err = cudaEventCreate(&e1);
-  if (err != cudaSuccess) rc = cuda_fail(err, "dns_tune_y_tiles set-up");
+  if (err != cudaSuccess) rc = cuda_fail(err, "dns_tune_tiles set-up");
   // each candidate starts from the saved state: capture and one warm-up step, then
   // `steps` timed steps exactly as dns_step runs them
-  auto timed = [&](int ti, int tf, float* ms) -> int {
+  auto timed = [&](int ti, int tf, int tz, float* ms) -> int {
     h->ytile[0] = ti;
     h->ytile[1] = tf;
+    h->ztile = tz;
     h->graph_dirty = true;
     cudaError_t ce = cudaMemcpyAsync(h->U, save, bytes, cudaMemcpyDeviceToDevice, h->stream);
-    if (ce != cudaSuccess) return cuda_fail(ce, "dns_tune_y_tiles copy");
+    if (ce != cudaSuccess) return cuda_fail(ce, "dns_tune_tiles copy");
     h->w_valid = false;
     int r = dns_step(h, 1);
     if (r) return r;
-    if ((ce = cudaEventRecord(e0, h->stream)) != cudaSuccess) return cuda_fail(ce, "dns_tune_y_tiles event");
+    if ((ce = cudaEventRecord(e0, h->stream)) != cudaSuccess) return cuda_fail(ce, "dns_tune_tiles event");
     if ((r = dns_step(h, steps))) return r;
     if ((ce = cudaEventRecord(e1, h->stream)) == cudaSuccess) ce = cudaEventSynchronize(e1);
     if (ce == cudaSuccess) ce = cudaEventElapsedTime(ms, e0, e1);
-    return ce == cudaSuccess ? DNS_OK : cuda_fail(ce, "dns_tune_y_tiles timing");
+    return ce == cudaSuccess ? DNS_OK : cuda_fail(ce, "dns_tune_tiles timing");
   };
-  // inverse widths with the forward width kept, then forward widths with the best inverse
-  int bi = keep[0], bf = keep[1];
+  // one pass at a time, the others kept: the y-inverse width, the y-forward width,
+  // then the z width, each with the best widths found before it
+  int bi = keep[0], bf = keep[1], bz = keep[2];
   float best = 1e30f, ms = 0.f;
-  for (int c = 0; c < nc && !rc; ++c)
-    if (!(rc = timed(cand[c], keep[1], &ms)) && ms < best) {
+  for (int c = 0; c < ny && !rc; ++c)
+    if (!(rc = timed(ycand[c], bf, bz, &ms)) && ms < best) {
       best = ms;
-      bi = cand[c];
+      bi = ycand[c];
     }
   best = 1e30f;
-  for (int c = 0; c < nc && !rc; ++c)
-    if (!(rc = timed(bi, cand[c], &ms)) && ms < best) {
+  for (int c = 0; c < ny && !rc; ++c)
+    if (!(rc = timed(bi, ycand[c], bz, &ms)) && ms < best) {
       best = ms;
-      bf = cand[c];
+      bf = ycand[c];
+    }
+  best = 1e30f;
+  for (int c = 0; c < nz && !rc; ++c)
+    if (!(rc = timed(bi, bf, zcand[c], &ms)) && ms < best) {
+      best = ms;
+      bz = zcand[c];
     }
   // the state and time as before; the fastest widths kept
   err = cudaMemcpyAsync(h->U, save, bytes, cudaMemcpyDeviceToDevice, h->stream);
@@ -515,11 +536,13 @@ int dns_tune_y_tiles(dns_handle* h, int steps, int* best_inverse, int* best_forw
   h->w_valid = false;
   h->ytile[0] = rc ? keep[0] : bi;
   h->ytile[1] = rc ? keep[1] : bf;
+  h->ztile = rc ? keep[2] : bz;
   h->graph_dirty = true;
   ++h->epoch;
-  if (!rc && err != cudaSuccess) rc = cuda_fail(err, "dns_tune_y_tiles restore");
-  *best_inverse = h->ytile[0];
-  *best_forward = h->ytile[1];
+  if (!rc && err != cudaSuccess) rc = cuda_fail(err, "dns_tune_tiles restore");
+  *y_inverse = h->ytile[0];
+  *y_forward = h->ytile[1];
+  *z = h->ztile;
   return rc;
 }
 
@@ -1029,22 +1052,23 @@ int dns_ensemble_step(dns_ensemble* e, int n) {
 
 int dns_ensemble_tune(dns_ensemble* e, int* best_streams) {
   if (!e) return fail(DNS_ERR_ARG, "dns_ensemble_tune: ensemble is NULL");
-  // y-pass tile widths per size class: tuned on one member (its state is kept),
-  // applied to every member of the class
+  // y- and z-pass tile widths per size class: tuned on one member (its state is
+  // kept), applied to every member of the class
   int rc = DNS_OK;
   std::vector<const DnsOps*> done_ops;
-  std::vector<std::pair<int, int>> done_tiles;
+  std::vector<std::array<int, 3>> done_tiles;
   for (dns_handle* h : e->m) {
     size_t k = 0;
     while (k < done_ops.size() && done_ops[k] != h->ops) ++k;
     if (k == done_ops.size()) {
-      int ti = 0, tf = 0;
-      if ((rc = dns_tune_y_tiles(h, 5, &ti, &tf))) return rc;
+      int ti = 0, tf = 0, tz = 0;
+      if ((rc = dns_tune_tiles(h, 5, &ti, &tf, &tz))) return rc;
       done_ops.push_back(h->ops);
-      done_tiles.push_back({ti, tf});
-    } else if (h->ytile[0] != done_tiles[k].first || h->ytile[1] != done_tiles[k].second) {
-      h->ytile[0] = done_tiles[k].first;
-      h->ytile[1] = done_tiles[k].second;
+      done_tiles.push_back({ti, tf, tz});
+    } else if (h->ytile[0] != done_tiles[k][0] || h->ytile[1] != done_tiles[k][1] || h->ztile != done_tiles[k][2]) {
+      h->ytile[0] = done_tiles[k][0];
+      h->ytile[1] = done_tiles[k][1];
+      h->ztile = done_tiles[k][2];
       h->graph_dirty = true;
       ++h->epoch;
     }

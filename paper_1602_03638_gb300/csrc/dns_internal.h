@@ -32,6 +32,7 @@ struct PassArgs {
   float f_nu = 0.f, f_cA = 0.f, f_cB = 0.f;
   float f_ks[3] = {1.f, 1.f, 1.f};
   int ytile[2] = {0, 0};  // y-pass tile widths of the stage launches (inverse, forward); 0 = default
+  int ztile = 0;          // z-pass tile width of the stage launches; 0 = default
   const void* in = nullptr;  // physical input (3,N,N,N) for set_state
   void* out = nullptr;       // physical output (3,N,N,N) / RHS output
   double* partials = nullptr;          // diagnostics block partials
@@ -67,6 +68,8 @@ struct DnsOps {
   // tile widths (x columns per block) the stage's y-passes offer besides the
   // default, written to tiles[0..count); returns count (<= max)
   int (*y_tiles)(int* tiles, int max);
+  // the same for the z-pass
+  int (*z_tiles)(int* tiles, int max);
 };
 
 constexpr int BATCH_MAX_N = 128;

@@ -482,12 +482,12 @@ __global__ void __launch_bounds__(YCfg<T, N, INV>::THREADS, (YCfg<T, N, INV>::MI
 // (k, M-k); the imaginary part of the kz = 0 coefficient is ignored and the
 // kz = N/2 coefficient is zero (it is not stored).
 // ---------------------------------------------------------------------------
-template <typename T, int N, int MODE>
+template <typename T, int N, int MODE, int TXO = 0>
 __device__ __forceinline__ void zpass_body(const PassArgs a, const int bx, const int by) {
   using G = Geometry<T, N>;
   constexpr int M = G::M;
-  constexpr int TX = G::ZTX;
-  constexpr int LD = G::ZLD;
+  constexpr int TX = TXO > 0 ? TXO : G::ZTX;  // TXO: a tuned tile width of the small grids
+  constexpr int LD = odd_ld(6 * TX);
   constexpr size_t FS = G::FS;
   constexpr int NF = (MODE == ZM_CROSS) ? 6 : (MODE == ZM_MAXABS ? 1 : 3);
   extern __shared__ unsigned char smraw[];
@@ -601,9 +601,9 @@ __device__ __forceinline__ void zpass_body(const PassArgs a, const int bx, const
   }
 }
 
-template <typename T, int N, int MODE>
+template <typename T, int N, int MODE, int TXO = 0>
 __global__ void __launch_bounds__(ZP_THREADS, (Geometry<T, N>::ZMIN)) k_zpass(PassArgs a) {
-  zpass_body<T, N, MODE>(a, blockIdx.x, blockIdx.y);
+  zpass_body<T, N, MODE, TXO>(a, blockIdx.x, blockIdx.y);
 }
 
 // Batched form (ensembles): member blockIdx.z.
@@ -1678,6 +1678,27 @@ struct SolverImpl {
       if (ytile_ok(t) && n < max) tiles[n++] = t;
     return n;
   }
+  // z-pass tile widths offered besides the default (the generic z-pass of the small grids)
+  static constexpr bool ztile_ok(int t) {
+    return N <= BATCH_MAX_N && !ZCross<T, N>::enabled && t >= 4 && t <= 32 && pow2_part(N) % t == 0 &&
+           G::zbytes(t) <= 112 * 1024;
+  }
+  template <int TXO>
+  static void ztile_attr(cudaError_t& e) {
+    if constexpr (ztile_ok(TXO))
+      if (e == cudaSuccess) e = smem_attr(k_zpass<T, N, ZM_CROSS, TXO>, G::zbytes(TXO));
+  }
+  static int z_tiles(int* tiles, int max) {
+    int n = 0;
+    for (int t = 4; t <= 32; t *= 2)
+      if (ztile_ok(t) && n < max) tiles[n++] = t;
+    return n;
+  }
+  template <int TXO>
+  static void z_go(const PassArgs& a, cudaStream_t st) {
+    constexpr int TX = TXO > 0 ? TXO : G::ZTX;
+    k_zpass<T, N, ZM_CROSS, TXO><<<dim3(N / TX, N), ZP_THREADS, G::zbytes(TX), st>>>(a);
+  }
   template <int INV, int PRUNE, int TXO>
   static void y_go(cx<T>* F, const cx<T>* tw, int kmax3, int planes, int fields, cudaStream_t st) {
     using Y = YCfg<T, N, INV, TXO>;
@@ -1701,6 +1722,10 @@ struct SolverImpl {
     tile_attr<8>(e);
     tile_attr<16>(e);
     tile_attr<32>(e);
+    ztile_attr<4>(e);
+    ztile_attr<8>(e);
+    ztile_attr<16>(e);
+    ztile_attr<32>(e);
 #define DNS_ATTR(kern, bytes) \
   if (e == cudaSuccess) e = smem_attr(kern, bytes)
     DNS_ATTR((k_xpass<T, N, XM_INV_CURL>), G::XSMEM);
@@ -1742,8 +1767,13 @@ struct SolverImpl {
       k_zcross8q<T, N><<<dim3(N / Z8Q<T>::TX, N), 32 * Z8Q<T>::NW, Z8Q<T>::SMEM, st>>>(a);
     else if constexpr (ZCross<T, N>::enabled)
       k_zcross<T, N><<<dim3(N / G::ZTX, N), 32 * ZCrossWarps<T, N>::value, G::ZSMEM, st>>>(a);
-    else
-      k_zpass<T, N, ZM_CROSS><<<dim3(N / G::ZTX, N), ZP_THREADS, G::ZSMEM, st>>>(a);
+    else {
+      if constexpr (ztile_ok(4)) if (a.ztile == 4) return z_go<4>(a, st);
+      if constexpr (ztile_ok(8)) if (a.ztile == 8) return z_go<8>(a, st);
+      if constexpr (ztile_ok(16)) if (a.ztile == 16) return z_go<16>(a, st);
+      if constexpr (ztile_ok(32)) if (a.ztile == 32) return z_go<32>(a, st);
+      z_go<0>(a, st);
+    }
   }
 
   // shared memory of a stage-update launch: with the wide layout only the rows
@@ -1852,7 +1882,7 @@ struct SolverImpl {
     constexpr bool batched = N <= BATCH_MAX_N && !ZCross<T, N>::enabled;
     static const DnsOps o = {N,         sizeof(T) == 4 ? 0 : 1, sizeof(cx<T>), &prepare,   &x_inverse_curl,
                              &rk_stage, &rk_stage_part,        &rhs,          &forward3d, &inverse3d,
-                             &diag,     batched ? &rk_stage_batch : nullptr, &y_tiles};
+                             &diag,     batched ? &rk_stage_batch : nullptr, &y_tiles, &z_tiles};
     return &o;
   }
 };

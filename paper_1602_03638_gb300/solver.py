@@ -129,13 +129,14 @@ class Solver:
         _lib.check(_lib.lib().dns_get_option(self._h, key.encode(), ctypes.byref(v)), "dns_get_option")
         return v.value
 
-    def tune_y_tiles(self, steps: int = 5) -> tuple:
-        """Time dns_step with each y-pass tile width the grid offers; keep the fastest
-        (inverse, forward) pair (0 = default). The state and time are left unchanged."""
-        ti, tf = ctypes.c_int(), ctypes.c_int()
-        _lib.check(_lib.lib().dns_tune_y_tiles(self._h, int(steps), ctypes.byref(ti), ctypes.byref(tf)),
-                   "dns_tune_y_tiles")
-        return ti.value, tf.value
+    def tune_tiles(self, steps: int = 5) -> tuple:
+        """Time dns_step with each y- and z-pass tile width the grid offers; keep the
+        fastest (y_inverse, y_forward, z) widths (0 = default). The state and time are
+        left unchanged."""
+        ti, tf, tz = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _lib.check(_lib.lib().dns_tune_tiles(self._h, int(steps), ctypes.byref(ti), ctypes.byref(tf), ctypes.byref(tz)),
+                   "dns_tune_tiles")
+        return ti.value, tf.value, tz.value
 
     def set_state(self, u):
         p, dev = _ptr(u, self.phys_shape, self._rb, False)
@@ -216,14 +217,16 @@ class Ensemble:
         _lib.check(_lib.lib().dns_ensemble_step(self._e, int(n)), "dns_ensemble_step")
 
     def tune(self) -> dict:
-        """Pick the y-pass tile widths per grid size and the schedule (batching, branch
-        count) by timing; advances every member (see include/dns.h)."""
+        """Pick the y- and z-pass tile widths per grid size and the schedule (batching,
+        branch count) by timing; advances every member (see include/dns.h)."""
         k = ctypes.c_int()
         _lib.check(_lib.lib().dns_ensemble_tune(self._e, ctypes.byref(k)), "dns_ensemble_tune")
         tiles = {}
         for m in self.members:
-            tiles.setdefault(m.N, [int(m.get_option("y_tile_inverse")), int(m.get_option("y_tile_forward"))])
-        return {"batching": self.batching, "streams": k.value, "y_tiles": tiles}
+            tiles.setdefault(m.N, {"y_inverse": int(m.get_option("y_tile_inverse")),
+                                   "y_forward": int(m.get_option("y_tile_forward")),
+                                   "z": int(m.get_option("z_tile"))})
+        return {"batching": self.batching, "streams": k.value, "tiles": tiles}
 
     def set_batching(self, max_batch: int):
         """0: every member runs its own kernels; n >= 1: up to n equal-size members share each launch."""

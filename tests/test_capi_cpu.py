@@ -64,8 +64,8 @@ def test_argument_validation_without_device(L):
     assert L.dns_debug_fail_alloc_after(0) == _lib.DNS_OK
     v = ctypes.c_double()
     assert L.dns_get_option(None, b"nu", ctypes.byref(v)) == _lib.DNS_ERR_ARG
-    a, b = ctypes.c_int(), ctypes.c_int()
-    assert L.dns_tune_y_tiles(None, 5, ctypes.byref(a), ctypes.byref(b)) == _lib.DNS_ERR_ARG
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    assert L.dns_tune_tiles(None, 5, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)) == _lib.DNS_ERR_ARG
 
 
 def test_create_reports_missing_device_instead_of_crashing(L):

@@ -1,8 +1,9 @@
-"""GPU tests of the y-pass tile widths and their tuner (options "y_tile_inverse",
-"y_tile_forward", dns_tune_y_tiles, and the tile step of dns_ensemble_tune).
+"""GPU tests of the y- and z-pass tile widths and their tuner (options
+"y_tile_inverse", "y_tile_forward", "z_tile", dns_tune_tiles, and the tile step of
+dns_ensemble_tune).
 
-A tile width only decides how many x columns one block of the y-pass transforms;
-each column's arithmetic is the same, so every offered width must give the default's
+A tile width only decides how many x columns one block of a pass transforms; each
+column's arithmetic is the same, so every offered width must give the default's
 result bit for bit, and tuning must not change the state or the time.
 """
 
@@ -28,22 +29,23 @@ def _built():
     build.build()
 
 
-def _offered(s):
+def _offered(s, key="y_tile_inverse"):
     out = []
     for t in (4, 8, 16, 32):
         try:
-            s.set_option("y_tile_inverse", t)
+            s.set_option(key, t)
             out.append(t)
         except RuntimeError:
             pass
-    s.set_option("y_tile_inverse", 0)
+    s.set_option(key, 0)
     return out
 
 
-def _steps(N, dtype, uh, ti=0, tf=0, n=3):
+def _steps(N, dtype, uh, ti=0, tf=0, tz=0, n=3):
     with Solver(N, 0.01, 0.004, dtype) as s:
         s.set_option("y_tile_inverse", ti)
         s.set_option("y_tile_forward", tf)
+        s.set_option("z_tile", tz)
         s.set_state_spectral(uh)
         s.step(n)
         return s.get_state_spectral()
@@ -54,17 +56,21 @@ def test_every_offered_tile_width_gives_the_default_result(N, dtype):
     uh = inputs.isotropic_spectral(N, seed=N, k0=3.0).numpy().astype(CPLX[dtype])
     with Solver(N, 0.01, 0.004, dtype) as s:
         tiles = _offered(s)
-    assert tiles, "the small grids offer tile widths"
+        ztiles = _offered(s, "z_tile")
+    assert tiles and ztiles, "the small grids offer tile widths"
     ref = _steps(N, dtype, uh)
     for t in tiles:
         assert np.array_equal(_steps(N, dtype, uh, ti=t), ref), f"inverse width {t}"
         assert np.array_equal(_steps(N, dtype, uh, tf=t), ref), f"forward width {t}"
+    for t in ztiles:
+        assert np.array_equal(_steps(N, dtype, uh, tz=t), ref), f"z width {t}"
 
 
 def test_large_grids_offer_only_the_default():
     with Solver(256, 0.01, 0.004, "f32") as s:
-        assert _offered(s) == []
+        assert _offered(s) == [] and _offered(s, "z_tile") == []
         s.set_option("y_tile_forward", 0)
+        assert s.tune_tiles(2) == (0, 0, 0)
 
 
 def test_tuner_keeps_state_and_time_and_picks_an_offered_width():
@@ -75,10 +81,10 @@ def test_tuner_keeps_state_and_time_and_picks_an_offered_width():
         s.step(2)
         before = s.get_state_spectral()
         t_before = s.diagnostics()["t"]
-        offered = _offered(s)
-        ti, tf = s.tune_y_tiles(3)
-        assert ti in [0] + offered and tf in [0] + offered
-        assert (s.get_option("y_tile_inverse"), s.get_option("y_tile_forward")) == (ti, tf)
+        offered, zoffered = _offered(s), _offered(s, "z_tile")
+        ti, tf, tz = s.tune_tiles(3)
+        assert ti in [0] + offered and tf in [0] + offered and tz in [0] + zoffered
+        assert (s.get_option("y_tile_inverse"), s.get_option("y_tile_forward"), s.get_option("z_tile")) == (ti, tf, tz)
         assert np.array_equal(s.get_state_spectral(), before)
         assert s.diagnostics()["t"] == t_before
         s.step(3)
@@ -108,7 +114,7 @@ def test_tuned_ensemble_members_match_solo_runs():
         for m, uh in zip(ens.members, ics):
             m.set_state_spectral(uh)
         sched = ens.tune()
-        assert set(sched["y_tiles"]) == set(Ns)
+        assert set(sched["tiles"]) == set(Ns)
         taken = [m.diagnostics()["t"] for m in ens.members]
         ens.step(3)
         got = [m.get_state_spectral() for m in ens.members]
