@@ -132,3 +132,28 @@ def test_z256_quarter_warp_maps():
             # r2c partner Z_{M-k}: lane (8 - h) & 7, slot 15 - m (lane 0: slot (16 - m) & 15)
             src_h, src_m = ((8 - h) & 7, 15 - m) if h else (0, (16 - m) & 15)
             assert (src_h + 8 * src_m) % M == (M - k) % M
+
+
+def _zbytes(N, t, cb):
+    return padded_len(N // 2) * odd_ld(6 * t) * cb
+
+
+@pytest.mark.parametrize("cb", [8, 16])
+@pytest.mark.parametrize("N", [n for n in SIZES if n <= 128])
+def test_offered_tile_widths_divide_the_grid_and_fit(N, cb):
+    # the widths a tuner may pick (y-pass: x columns per block; z-pass: x per tile)
+    y = [t for t in (4, 8, 16, 32) if pow2_part(N) % t == 0 and t * cb <= 256]
+    z = [t for t in (4, 8, 16, 32) if pow2_part(N) % t == 0 and _zbytes(N, t, cb) <= 112 * 1024]
+    for t in y:
+        assert N % t == 0
+        assert padded_len(N) * odd_ld(t) * cb <= 227 * 1024
+        seen = set()
+        for e in range(t * N):
+            x, row = e % t, ywalk_row(e // t, cb, t, N)
+            assert 0 <= row < N and padp(row) * odd_ld(t) + x < padded_len(N) * odd_ld(t)
+            seen.add((row, x))
+        assert len(seen) == t * N
+    for t in z:
+        assert N % t == 0
+        # tile rows padp(k) (k < N/2) of 6 fields x t columns inside the allocation
+        assert padp(N // 2 - 1) * odd_ld(6 * t) + 6 * t - 1 < padded_len(N // 2) * odd_ld(6 * t)
