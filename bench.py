@@ -17,10 +17,11 @@ Printed on rank 0 as one JSON line, with
                 bytes per launch over its mean CUDA-event duration) against
                 the measured copy bandwidth
   step_roofline the whole step against the 132-component-volume minimum
-  forms         FP64 at 512^3, FP32 at 1024^3, both at 256^3, and the error of each
+  forms         FP64 at 512^3, FP32 and FP64 at 1024^3, both at 256^3, and the error of each
                 precision against the FP64 CPU oracle at 128^3
   ensemble      128 members of mixed sizes: one graph launch per step versus
                 sequential per-member launches
+  plane_schedule  the same workload with the plane-pass schedule (fused_planes = 1)
   cufft_comparison  the same step composed from torch.fft (cuFFT) and torch
                 elementwise calls (a library comparison, not the product path)
   closure       learned subgrid closure (512^3 DNS -> 64^3): training cost,
@@ -50,16 +51,47 @@ METRIC = "grid-points x RK4 steps/s (Taylor-Green 512^3 FP32; FP64 and 1024^3 in
 UNIT = "points*steps/s"
 N_MAIN, NU, DT = 512, 1.0 / 1600.0, 1e-3
 SPEC_HBM_GBS = 8000.0
-# Bytes each kernel class must move per launch, in component-volumes cv = N^2 (N/2+1)
-# complex values: y-inverse reads and writes the 6 fields of u and omega (12); the z-pass
-# reads 6 and writes the 3 products (9); the y-forward reads and writes 3 (6); the x-stage
-# reads the 3 products and the stage state (6), writes u and omega (6) and moves 36 cv of
-# RK4 state per step, 9 per stage on average (21). STEP_CV: the fused two-pass model of one
-# RK4 step (x and y transforms in one sweep): 24 cv per stage plus 36 cv of RK4 state.
-KERNEL_CV = {"y_inverse": 12.0, "z_pass": 9.0, "y_forward": 6.0, "x_stage": 21.0}
+# STEP_CV: the fused two-pass model of one RK4 step (x and y transforms in one sweep, 24 cv
+# per stage plus 36 cv of RK4 state), in component-volumes cv = N^2 (N/2+1) complex values.
 STEP_CV = 132.0
 CPU_N, CPU_STEPS = 128, 8
 PAPER_TG512_PTS_STEPS_PER_S = 6.2e7  # Sec. 4 verification run, 2048 Shaheen cores (context)
+
+
+def pass_bytes(N, real_bytes, stages=4):
+    """Algorithmic bytes per launch of each kernel class (mean over the RK4 stages).
+
+    Counted from the 2/3 mask: a field-volume FV = N^2 (N/2) complex values (the stored half
+    spectrum; the kz = N/2 plane is identically zero); kc = (N+2)//3 planes kz < N/3 and
+    2 kc - 1 rows |ky| < N/3 carry the nonlinear term, nothing else of it is read or written.
+      y_inverse  R 6 FV + W 6 FV (u and omega, every mode)
+      z_pass     R 6 FV + W 3 (kc/M) FV (products kz < N/3)
+      y_forward  R 3 (kc/M) FV + W 3 (kc/M)(2kc-1)/N FV (rows |ky| < N/3)
+      x_stage    R 3 (kc/M)(2kc-1)/N FV (N_hat rows) + RK state + W 6 FV (u, omega)
+      plane_pass (y-forward, x-stage and y-inverse in one launch, planes handed over in L2)
+                 R 3 (kc/M) FV (products) + RK state + W 6 FV (u and omega, y-inverted)
+    RK state per stage: stage 0 reads u (3) and writes u1, us (6); a middle stage reads us,
+    u1, u (9) and writes u1, us (6); the last reads us, u1 (6) and writes u (3).
+    """
+    M = N // 2
+    fv = N * N * M * 2 * real_bytes
+    kc = (N + 2) // 3
+    zk = kc / M
+    yk = (2 * kc - 1) / N
+    rk = []
+    for s_ in range(stages):
+        if stages == 1:
+            r, w = 3, 3
+        elif s_ == 0:
+            r, w = 3, 6
+        elif s_ < stages - 1:
+            r, w = 9, 6
+        else:
+            r, w = 6, 3
+        rk.append(r + w)
+    rk_mean = sum(rk) / len(rk)
+    return {"y_inverse": 12.0 * fv, "z_pass": (6.0 + 3.0 * zk) * fv, "y_forward": (3.0 * zk + 3.0 * zk * yk) * fv,
+            "x_stage": (3.0 * zk * yk + rk_mean + 6.0) * fv, "plane_pass": (3.0 * zk + rk_mean + 6.0) * fv}
 
 
 def cv_bytes(N, real_bytes):
@@ -182,12 +214,13 @@ def run_reference(args):
         uh = sn.rk4_step(uh, g, NU, DT)
     secs = time.perf_counter() - t0
     value = N ** 3 * args.steps / secs
-    sample = f"Taylor-Green {N}^3 FP64 oracle, one RK4 step per bench step (nu=1/1600, dt=1e-3), scipy.fft workers={sn.WORKERS}"
+    sample = (f"bounded sample of the Taylor-Green workload: one RK4 step of the FP64 oracle at {N}^3 per bench "
+              f"step (nu=1/1600, dt=1e-3; a 512^3 oracle step takes about a minute), scipy.fft workers={sn.WORKERS}")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic (Taylor-Green initial condition)",
-        "config": main_config(world),
+        "config": reference_config(world, N),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": sn.WORKERS, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -199,6 +232,14 @@ def main_config(world, N=N_MAIN):
     return {"workload": f"taylor_green_{N}_f32", "model": "pseudo-spectral NS, RK4, 2/3 dealiasing", "N": N,
             "nu": NU, "dt": DT, "global_batch": world, "seq_len": None, "parallelism": f"replicas{world}",
             "l2": "no flush needed: every pass streams 1.6-3.2 GB, > 129 MB L2"}
+
+
+def reference_config(world, N):
+    """The reference arm's own workload: Taylor-Green at N^3 in FP64 (the GPU arm's 512^3 FP32
+    case is too large for the CPU oracle within a bench run); named as such."""
+    return {"workload": f"taylor_green_{N}_f64", "model": "pseudo-spectral NS, RK4, 2/3 dealiasing (CPU oracle)",
+            "N": N, "nu": NU, "dt": DT, "global_batch": 1, "seq_len": None, "parallelism": "cpu",
+            "sample_of": f"taylor_green_{N_MAIN}_f32"}
 
 
 def time_steps(torch, s, st, steps):
@@ -230,12 +271,52 @@ def run_form(torch, Solver, inputs, N, dtype, warm, steps):
            "hbm_roofline_frac_of_measured": model_ms / ms}
     if dtype == "f64":
         # FP64 arithmetic bound: ~270 N^3 log2 N flops per RK4 step (36 scalar 3D transforms,
-        # radix-2 count) against 152 SMs x 2 FP64 FMA/clock x 2 flops x 2.07 GHz = 1.26 TFLOP/s
+        # radix-2 count) against the FP64 FMA rate measured on this GPU (dns_measure_fp64_peak)
         flops = 270.0 * N ** 3 * math.log2(N)
-        peak = 152 * 2 * 2 * 2.07e9
+        peak = fp64_peak_tflops() * 1e12
         out["roofline"] = {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": peak / 1e12,
-                           "unit": "TFLOP/s", "frac": flops / (ms * 1e-3) / peak, "flops_per_step": flops}
+                           "unit": "TFLOP/s", "frac": flops / (ms * 1e-3) / peak, "flops_per_step": flops,
+                           "peak_kind": "measured (dependent-FMA probe, CUDA events)"}
     return out
+
+
+_FP64_PEAK = None
+
+
+def fp64_peak_tflops():
+    global _FP64_PEAK
+    if _FP64_PEAK is None:
+        import ctypes
+
+        from paper_1602_03638_gb300 import _lib
+
+        v = ctypes.c_double()
+        _lib.check(_lib.lib().dns_measure_fp64_peak(ctypes.byref(v)), "dns_measure_fp64_peak")
+        _FP64_PEAK = float(v.value)
+    return _FP64_PEAK
+
+
+def run_plane_schedule(torch, Solver, inputs, N=N_MAIN, warm=3, steps=10):
+    """Taylor-Green N^3 FP32 with the plane-pass schedule (option fused_planes = 1): each stage
+    as the z-pass plus one persistent launch doing the y-forward, x-stage and y-inverse plane by
+    plane with the plane data handed over in L2. Same results as the default schedule (bitwise);
+    step time and per-kernel split for comparison."""
+    with Solver(N, NU, DT, "f32") as s:
+        s.set_option("fused_planes", 1)
+        st = torch.cuda.current_stream()
+        s.set_stream(st)
+        u = inputs.taylor_green_torch(N, device="cuda", dtype=torch.float32)
+        s.set_state(u)
+        del u
+        for _ in range(warm):
+            s.step(1)
+        torch.cuda.synchronize()
+        ms = time_steps(torch, s, st, steps) / steps
+        prof = s.profile_steps(steps)
+    kb = pass_bytes(N, 4)
+    return {"N": N, "dtype": "f32", "ms_per_step": ms, "value": N ** 3 / (ms * 1e-3),
+            "kernels": {k: {"ms_per_launch": v[0] / v[1], "algorithmic_bytes_per_launch": kb[k],
+                            "algorithmic_GBps": kb[k] / (v[0] / v[1] * 1e-3) / 1e9} for k, v in prof.items()}}
 
 
 def run_integrators(torch, Solver, inputs, N=512, warm=3, steps=10):
@@ -277,10 +358,7 @@ def run_ensemble(torch, np, steps=10):
         best = ens.tune()
         ens.step(2)
         ens.synchronize()
-        t0 = time.perf_counter()
-        ens.step(steps)
-        ens.synchronize()
-        batched = (time.perf_counter() - t0) / steps
+        graph = ens.time_steps(steps) * 1e-3 / steps
         for m in ens.members:  # warm the per-member graphs
             m.step(1)
         ens.synchronize()
@@ -291,10 +369,16 @@ def run_ensemble(torch, np, steps=10):
         ens.synchronize()
         sequential = (time.perf_counter() - t0) / steps
         pts = sum(N ** 3 for N in Ns)
+    model = sum(STEP_CV * cv_bytes(N, 4) for N in Ns)
+    peak, kind = measured_peaks()
     return {"members": len(Ns), "sizes": {str(n): Ns.count(n) for n in sizes}, "dtype": "f32", "nu": nu, "dt": dt,
-            "schedule": best, "batched_ms_per_step": 1e3 * batched, "sequential_ms_per_step": 1e3 * sequential,
-            "speedup": sequential / batched, "points_steps_per_s_batched": pts / batched,
-            "timing": "host wall clock around K steps + stream synchronize"}
+            "schedule": best, "graph_ms_per_step": 1e3 * graph, "sequential_ms_per_step": 1e3 * sequential,
+            "speedup": sequential / graph, "points_steps_per_s": pts / graph,
+            "roofline": {"model_bytes_per_step": model, "achieved_GBps": model / graph / 1e9, "peak": peak,
+                         "frac": model / graph / 1e9 / peak, "peak_kind": kind,
+                         "what": "132-cv step model summed over the members / device-timed step"},
+            "timing": "graph: CUDA events on the ensemble stream around K graph launches; sequential: host "
+                      "wall clock around K rounds of per-member dns_step calls + synchronize"}
 
 
 def run_cufft_comparison(torch, N=N_MAIN, steps=3, warm=2):
@@ -390,7 +474,7 @@ def combine_replicas(ms_local, steps, points, dist=None, device="cpu"):
 
 def step_traffic(N, dtype):
     """DRAM bytes per RK4 step from the per-launch ncu traffic (4 launches of each kernel), or None."""
-    parts = [ncu_traffic(k, N, dtype) for k in KERNEL_CV]
+    parts = [ncu_traffic(k, N, dtype) for k in ("z_pass", "plane_pass")]
     return None if any(p is None for p in parts) else 4.0 * sum(parts)
 
 
@@ -417,6 +501,8 @@ def run_ours(args):
     N, dtype = args.N, "f32"
     peak, peak_kind = measured_peaks()
     s = Solver(N, NU, DT, dtype)
+    if args.schedule != "auto":
+        s.set_option("fused_planes", 1 if args.schedule == "plane" else 0)
     st = torch.cuda.current_stream()
     s.set_stream(st)
     u = inputs.taylor_green_torch(N, device="cuda", dtype=torch.float32)
@@ -440,9 +526,11 @@ def run_ours(args):
     dom = max(prof, key=lambda k: prof[k][0])
     dom_ms = prof[dom][0] / prof[dom][1]
     cvb = cv_bytes(N, 4)
-    achieved = KERNEL_CV[dom] * cvb / (dom_ms * 1e-3) / 1e9
+    kb = pass_bytes(N, 4)
+    achieved = kb[dom] / (dom_ms * 1e-3) / 1e9
     kernels = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1], "share": v[0] / sum(x[0] for x in prof.values()),
-                   "algorithmic_GBps": KERNEL_CV[k] * cvb / (v[0] / v[1] * 1e-3) / 1e9} for k, v in prof.items()}
+                   "algorithmic_bytes_per_launch": kb[k],
+                   "algorithmic_GBps": kb[k] / (v[0] / v[1] * 1e-3) / 1e9} for k, v in prof.items()}
     s.close()
 
     if rank != 0:
@@ -456,11 +544,11 @@ def run_ours(args):
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": value / PAPER_TG512_PTS_STEPS_PER_S, "dtype": "f32",
         "data": "synthetic (Taylor-Green initial condition on device)", "config": main_config(world, N),
-        "gpu_launches": 16 * args.steps,
+        "gpu_launches": 4 * len(prof) * args.steps,  # kernels per RK4 stage x 4 stages x steps
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind,
                      "traffic": ncu_traffic(dom, N, dtype),
-                     "algorithmic_bytes_per_launch": KERNEL_CV[dom] * cvb},
+                     "algorithmic_bytes_per_launch": kb[dom]},
         "step_roofline": {"model_bytes_per_step": step_bytes, "achieved_GBps": step_bytes / (ms_step * 1e-3) / 1e9,
                           "frac_of_measured": step_bytes / (ms_step * 1e-3) / 1e9 / peak,
                           "frac_of_spec_8TBps": step_bytes / (ms_step * 1e-3) / 1e9 / SPEC_HBM_GBS,
@@ -496,6 +584,7 @@ def run_ours(args):
                            "final_energy": d["energy"]}
         # precision forms
         forms = [run_form(torch, Solver, inputs, 512, "f64", 2, 3), run_form(torch, Solver, inputs, 1024, "f32", 2, 3),
+                 run_form(torch, Solver, inputs, 1024, "f64", 1, 2),
                  run_form(torch, Solver, inputs, 256, "f32", 3, 20), run_form(torch, Solver, inputs, 256, "f64", 2, 5)]
         # CPU oracle baseline and error of each GPU precision against it
         secs, ref, cores = oracle_sample(CPU_N, CPU_STEPS, NU, DT)
@@ -508,6 +597,7 @@ def run_ours(args):
             errs[dt_] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
         line["forms"] = forms
         line["integrators"] = run_integrators(torch, Solver, inputs)
+        line["plane_schedule"] = run_plane_schedule(torch, Solver, inputs)
         line["ensemble"] = run_ensemble(torch, np)
         line["cufft_comparison"] = run_cufft_comparison(torch)
         line["closure"] = run_closure()
@@ -530,6 +620,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, forms and the CPU baseline")
     ap.add_argument("--N", type=int, default=N_MAIN, help="grid size of the timed workload (profiling runs only)")
+    ap.add_argument("--schedule", choices=["auto", "plane", "four"], default="auto",
+                    help="stage schedule of the timed solver: plane pass where compiled (auto), or the four-pass "
+                         "schedule (profiling comparisons only)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -55,7 +55,7 @@ typedef enum {
   DNS_ERR_OOM = -2,         /* device allocation failed */
   DNS_ERR_CUDA = -3,        /* a CUDA call or kernel failed */
   DNS_ERR_NONFINITE = -4,   /* the state holds NaN or Inf */
-  DNS_ERR_TIMEOUT = -5,     /* reserved: a bounded device wait expired */
+  DNS_ERR_TIMEOUT = -5,     /* a bounded device wait of the plane pass gave up (1 s) */
   DNS_ERR_UNSUPPORTED = -6  /* no usable sm_103 device, or N not instantiated */
 } dns_status;
 
@@ -113,6 +113,24 @@ int dns_set_stream(dns_handle* h, void* stream);
  *                      grids: 0 (default) or an offered width (4 .. 32); results
  *                      independent of it, see dns_tune_tiles.
  *   "use_graph"        1: dns_step replays a captured CUDA graph (default)
+ *   "fused_planes"     0 (default) or 1 where compiled (N >= 256): 1 runs each RK
+ *                      stage as two launches, the z-pass and one persistent plane pass that
+ *                      walks the kz planes and does the y-forward, x-stage and
+ *                      y-inverse of each plane while its data is in L2 (the three
+ *                      are local to a kz plane; Sec. 3.2 transposes become changes
+ *                      of pass direction). 0: four launches per stage (y-inverse,
+ *                      z-pass, y-forward, x-stage). Same arithmetic, bit-identical
+ *                      results. The plane pass moves fewer DRAM bytes but, on
+ *                      GB300, runs slower than the four passes at 256^3 - 1024^3.
+ *                      The plane pass orders its work items through per-plane
+ *                      counters in device memory; a wait that gives up after 1 s
+ *                      (never in a correct run) makes the next synchronising call
+ *                      (dns_get_state*, dns_diagnostics, dns_profile_steps) return
+ *                      DNS_ERR_TIMEOUT.
+ *   "plane_lag"        0 (default: chosen from the launch's block count) or 1 .. 8:
+ *                      queue steps between a plane's y-forward and x-stage work and
+ *                      between its x-stage and y-inverse work in the plane pass.
+ *                      A schedule knob only: results do not depend on it.
  *   "nu", "dt"         change the viscosity / time step
  *   "time"             set the simulated time reported by dns_diagnostics
  * Errors: DNS_ERR_ARG for an unknown key or a value out of range. */
@@ -166,10 +184,19 @@ int dns_diagnostics(dns_handle* h, dns_diag* out);
 /* Measurement aid: advances n >= 1 steps exactly like dns_step but
  * launches the kernels one by one (no graph) with a CUDA event after each,
  * and returns per kernel class the summed device time in ms[c] and the
- * launch count in launches[c]: c = 0 y-inverse, 1 z-pass (c2r, u x omega,
- * r2c), 2 y-forward, 3 x-stage (forward x, mask, projection, viscous term,
- * stage update, next inverse x). nclass must be >= 4. Synchronises. */
+ * launch count in launches[c]. Four-pass schedule: c = 0 y-inverse, 1 z-pass
+ * (c2r, u x omega, r2c), 2 y-forward, 3 x-stage (forward x, mask, projection,
+ * viscous term, stage update, next inverse x). Plane-pass schedule (option
+ * "fused_planes"): c = 0 z-pass, 1 plane pass (y-forward, x-stage, y-inverse),
+ * classes 2 and 3 zero. nclass must be >= 4. Synchronises. */
 int dns_profile_steps(dns_handle* h, int n, double* ms, int* launches, int nclass);
+
+/* Measured FP64 FMA throughput of the current device in TFLOP/s (2 flops per
+ * FMA): independent chains of dependent FMAs on 4 blocks of 256 threads per SM,
+ * best of three CUDA-event-timed launches after one warm-up. The denominator of
+ * the FP64 form's arithmetic roofline (its step is bound by FP64 arithmetic, not
+ * HBM). Allocates 8 bytes; synchronous. The paper has no counterpart. */
+int dns_measure_fp64_peak(double* tflops);
 
 /* Bytes of device memory the handle owns. */
 size_t dns_device_bytes(const dns_handle* h);
@@ -192,7 +219,11 @@ const char* dns_last_error(const dns_handle* h);
  *   nu     viscosity used for the dissipation
  *   out    device pointer to 5 doubles, 8-byte aligned: energy, dissipation,
  *          helicity, enstrophy (same definitions and FP64 sums as
- *          dns_diagnostics), then the number of non-finite modes
+ *          dns_diagnostics on the [0, 2 pi]^3 box), then the number of
+ *          non-finite modes. The wavenumber of index k is k: for a field of a
+ *          handle whose box lengths were changed (options "Lx", "Ly", "Lz"),
+ *          dns_diagnostics scales each index by 2 pi / L and the vorticity sums
+ *          (dissipation, helicity, enstrophy) differ from these
  *   stream cudaStream_t the two kernels are enqueued on (NULL = legacy default)
  *
  * Asynchronous: returns after enqueueing; read `out` after synchronising.
@@ -200,9 +231,11 @@ const char* dns_last_error(const dns_handle* h);
  * loading the library holds until exit; every call overwrites all of it before
  * reading it. Calls that overlap on the GPU (e.g. on two streams at once) share
  * that array and race: serialise them. The first call on each device looks up
- * the array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture. Calls no cudaMalloc, cudaFree or other allocating
- * routine. */
+ * the array's device address (cudaGetSymbolAddress) and keeps it for the life
+ * of the process; make that first call before any stream capture, and do not
+ * call this entry point after a cudaDeviceReset of that device in the same
+ * process (the kept address would be stale). Calls no cudaMalloc, cudaFree or
+ * other allocating routine. */
 int dns_spectral_sums_noalloc(const void* uhat, int N, int dtype, double nu, double* out, void* stream);
 
 /* ---- Ensembles (many independent runs of mixed grid sizes) ------------------
@@ -242,6 +275,10 @@ int dns_ensemble_batching(const dns_ensemble* e);              /* current max_ba
 int dns_ensemble_tune(dns_ensemble* e, int* best_streams);  /* advances the members, see above */
 int dns_ensemble_step(dns_ensemble* e, int n);              /* asynchronous */
 int dns_ensemble_synchronize(dns_ensemble* e);
+/* n ensemble steps timed on the device: CUDA events recorded on the ensemble's
+ * stream around the n graph launches; synchronises and writes the elapsed
+ * milliseconds to *ms. Advances every member by n steps like dns_ensemble_step. */
+int dns_ensemble_time_steps(dns_ensemble* e, int n, double* ms);
 
 /* ---- Transforms and forcing on a handle ---------------------------------------
  * dns_transform_r2c: F of 3 physical fields (3,N,N,N) (device) into the public
@@ -304,6 +341,16 @@ int dns_mlp_train_step(dns_mlp* net, const float* X, const float* T, int P, doub
  * by the library from now on (n >= 1) reports DNS_ERR_OOM without touching
  * the device; n = 0 disables the hook. */
 int dns_debug_fail_alloc_after(int n);
+
+/* Test hook for the bounded waits of the plane pass (no counterpart in the
+ * paper): runs one plane pass of stage 0 whose work queue starts past the
+ * y-forward and x-stage items its first y-inverse items wait for, so those
+ * waits give up after 1 s; every block then stops. Returns DNS_ERR_TIMEOUT
+ * (the expected outcome: the error flag was read back and cleared),
+ * DNS_ERR_ARG if the waits did not give up, DNS_ERR_UNSUPPORTED for a grid
+ * without a plane pass. The state u_hat is untouched (stage 0 does not write
+ * it); the work fields are re-primed by the next step. Synchronises. */
+int dns_debug_plane_wait_timeout(dns_handle* h);
 
 #ifdef __cplusplus
 }

@@ -59,6 +59,7 @@ SIGNATURES = {
     "dns_device_bytes": (ctypes.c_size_t, [_P]),
     "dns_last_error": (ctypes.c_char_p, [_P]),
     "dns_debug_fail_alloc_after": (_I, [_I]),
+    "dns_debug_plane_wait_timeout": (_I, [_P]),
     "dns_spectral_sums_noalloc": (_I, [_P, _I, _I, _D, _P, _P]),
     "dns_ensemble_create": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_D), _I, ctypes.POINTER(_P)]),
     "dns_ensemble_destroy": (_I, [_P]),
@@ -87,6 +88,8 @@ SIGNATURES = {
     "dns_mlp_train_step": (_I, [_P, _P, _P, _I, _D, ctypes.POINTER(ctypes.c_float), _P]),
     "dns_ensemble_step": (_I, [_P, _I]),
     "dns_ensemble_synchronize": (_I, [_P]),
+    "dns_ensemble_time_steps": (_I, [_P, _I, ctypes.POINTER(_D)]),
+    "dns_measure_fp64_peak": (_I, [ctypes.POINTER(_D)]),
 }
 
 _lib = None

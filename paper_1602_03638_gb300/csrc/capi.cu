@@ -83,6 +83,24 @@ __global__ void k_internal_to_paper(const cx<T>* __restrict__ O, cx<T>* __restri
   }
 }
 
+// FP64 FMA throughput probe: FMA_PROBE_CHAINS independent dependent-FMA chains
+// per thread, x <- x * a + b, so that the FP64 pipe, not latency, sets the rate.
+constexpr int FMA_PROBE_CHAINS = 8;
+constexpr int FMA_PROBE_THREADS = 256;
+__global__ void __launch_bounds__(FMA_PROBE_THREADS) k_fp64_fma_probe(double* sink, int iters, double a, double b) {
+  double x[FMA_PROBE_CHAINS];
+#pragma unroll
+  for (int i = 0; i < FMA_PROBE_CHAINS; ++i) x[i] = 1e-3 * threadIdx.x + i;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < FMA_PROBE_CHAINS; ++i) x[i] = fma(x[i], a, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < FMA_PROBE_CHAINS; ++i) s += x[i];
+  if (s == -1.0) *sink = s;  // never true: keeps the chains live
+}
+
 }  // namespace dns
 
 using namespace dns;
@@ -174,6 +192,8 @@ struct dns_handle {
   int ytile[2] = {0, 0};  // y-pass tile widths of the stage (inverse, forward); 0 = default
   int ztile = 0;          // z-pass tile width of the stage; 0 = default
   int use_graph = 1;
+  int fused = 0;  // plane-pass schedule (option "fused_planes"; measured slower than the four passes)
+  int plane_lag = 0;  // option "plane_lag" (0: automatic)
   double nu = 0.0, dt = 0.0, t = 0.0;
   const DnsOps* ops = nullptr;
   int device = 0;
@@ -187,6 +207,7 @@ struct dns_handle {
   bool has_force = false;
   void* tw = nullptr;
   double* diag = nullptr;
+  int* ctl = nullptr;  // plane-pass control block (ops->plane_ctl_words ints)
   size_t bytes = 0;
   size_t fs = 0;  // complex values per field
   bool w_valid = false;
@@ -220,7 +241,7 @@ int dev_alloc(dns_handle* h, void** p, size_t bytes, const char* what) {
 void release(dns_handle* h) {
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->graph) cudaGraphDestroy(h->graph);
-  void* bufs[] = {h->U, h->U1, h->US, h->W, h->D, h->F, h->tw, h->diag};
+  void* bufs[] = {h->U, h->U1, h->US, h->W, h->D, h->F, h->tw, h->diag, h->ctl};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -242,12 +263,35 @@ PassArgs base_args(const dns_handle* h) {
   a.ytile[0] = h->ytile[0];
   a.ytile[1] = h->ytile[1];
   a.ztile = h->ztile;
+  a.ctl = h->ctl;
+  a.plane_lag = h->plane_lag;
   a.partials = h->diag;
   a.maxbits = reinterpret_cast<unsigned long long*>(h->diag + DIAG_BLOCKS * 4 + 4);
   return a;
 }
 
 int rk_stages(const dns_handle* h) { return RK_SCHEMES[h->integrator].stages; }
+
+bool use_fused(const dns_handle* h) { return h->fused && h->ops->rk_stage_fused && h->ctl; }
+
+// Brings W into the form the stage launches expect: the x-inverse of u and omega
+// (four-pass schedule) or their x- and y-inverse (plane-pass schedule).
+cudaError_t prime_work(dns_handle* h, cudaStream_t st) {
+  PassArgs a = base_args(h);
+  return use_fused(h) ? h->ops->prime_fused(a, 0, st) : h->ops->x_inverse_curl(a, 0, st);
+}
+
+// Reports (and clears) a plane-pass wait that gave up; the stream is synchronised.
+int check_plane_error(dns_handle* h, const char* where) {
+  if (!h->ctl) return DNS_OK;
+  int err = 0;
+  DNS_CUDA(cudaMemcpyAsync(&err, h->ctl, sizeof(int), cudaMemcpyDeviceToHost, h->stream), where);
+  DNS_CUDA(cudaStreamSynchronize(h->stream), where);
+  if (!err) return DNS_OK;
+  DNS_CUDA(cudaMemsetAsync(h->ctl, 0, sizeof(int), h->stream), where);
+  h->w_valid = false;
+  return fail(DNS_ERR_TIMEOUT, "%s: a plane-pass wait gave up after 1 s; the state is not valid", where);
+}
 
 // stage s of the handle's scheme: its coefficients times dt and the index of the last stage
 void set_stage(const dns_handle* h, int s, PassArgs& a) {
@@ -260,9 +304,10 @@ void set_stage(const dns_handle* h, int s, PassArgs& a) {
 
 cudaError_t enqueue_step(dns_handle* h, cudaStream_t st) {
   PassArgs a = base_args(h);
+  const bool fused = use_fused(h);
   for (int s = 0; s < rk_stages(h); ++s) {
     set_stage(h, s, a);
-    cudaError_t e = h->ops->rk_stage(a, st);
+    cudaError_t e = fused ? h->ops->rk_stage_fused(a, st) : h->ops->rk_stage(a, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -354,6 +399,13 @@ int dns_create(int N, double nu, double dt, int dtype, dns_handle** out) {
   if (rc == DNS_OK) rc = dev_alloc(h, &h->D, h->fs * cb, "divergence field");
   if (rc == DNS_OK) rc = dev_alloc(h, &h->tw, (size_t)N * cb, "twiddles");
   if (rc == DNS_OK) rc = dev_alloc(h, (void**)&h->diag, (DIAG_BLOCKS * 4 + 8) * sizeof(double), "diagnostics");
+  if (rc == DNS_OK && ops->plane_ctl_words > 0) {
+    rc = dev_alloc(h, (void**)&h->ctl, (size_t)ops->plane_ctl_words * sizeof(int), "plane-pass control block");
+    if (rc == DNS_OK) {
+      ce = cudaMemset(h->ctl, 0, (size_t)ops->plane_ctl_words * sizeof(int));
+      if (ce != cudaSuccess) rc = cuda_fail(ce, "dns_create control block");
+    }
+  }
   if (rc == DNS_OK) {
     std::vector<double> t64(2 * N);
     for (int t = 0; t < N; ++t) twiddle(t, N, &t64[2 * t], &t64[2 * t + 1]);
@@ -425,6 +477,15 @@ int dns_set_option(dns_handle* h, const char* key, double value) {
   } else if (!strcmp(key, "use_graph")) {
     if (value != 0.0 && value != 1.0) return fail(DNS_ERR_ARG, "use_graph must be 0 or 1");
     h->use_graph = (int)value;
+  } else if (!strcmp(key, "fused_planes")) {
+    if (value != 0.0 && value != 1.0) return fail(DNS_ERR_ARG, "fused_planes must be 0 or 1");
+    if (value == 1.0 && !h->ops->rk_stage_fused)
+      return fail(DNS_ERR_ARG, "fused_planes: N = %d has no plane-pass schedule", h->N);
+    h->fused = (int)value;
+  } else if (!strcmp(key, "plane_lag")) {
+    if (!(value >= 0.0 && value <= 8.0) || value != std::floor(value))
+      return fail(DNS_ERR_ARG, "plane_lag must be an integer in 0 .. 8");
+    h->plane_lag = (int)value;
   } else if (!strcmp(key, "nu")) {
     if (!(value >= 0.0) || !std::isfinite(value)) return fail(DNS_ERR_ARG, "nu must be finite and >= 0");
     h->nu = value;
@@ -455,6 +516,8 @@ int dns_get_option(const dns_handle* h, const char* key, double* value) {
   else if (!strcmp(key, "y_tile_forward")) *value = h->ytile[1];
   else if (!strcmp(key, "z_tile")) *value = h->ztile;
   else if (!strcmp(key, "use_graph")) *value = h->use_graph;
+  else if (!strcmp(key, "fused_planes")) *value = use_fused(h) ? 1.0 : 0.0;
+  else if (!strcmp(key, "plane_lag")) *value = h->plane_lag;
   else if (!strcmp(key, "nu")) *value = h->nu;
   else if (!strcmp(key, "dt")) *value = h->dt;
   else if (!strcmp(key, "time")) *value = h->t;
@@ -591,7 +654,7 @@ int dns_step(dns_handle* h, int n) {
   if (n == 0) return DNS_OK;
   if ((rc = use_device(h))) return rc;
   if (!h->w_valid) {
-    DNS_CUDA(h->ops->x_inverse_curl(base_args(h), 0, h->stream), "dns_step initial transform");
+    DNS_CUDA(prime_work(h, h->stream), "dns_step initial transform");
     h->w_valid = true;
   }
   if (h->use_graph) {
@@ -630,7 +693,7 @@ int dns_get_state(dns_handle* h, void* u, int on_device) {
     DNS_CUDA(cudaMemcpyAsync(u, dst, phys_bytes(h), cudaMemcpyDeviceToHost, h->stream), "dns_get_state copy");
   DNS_CUDA(cudaStreamSynchronize(h->stream), "dns_get_state");
   h->w_valid = false;
-  return DNS_OK;
+  return check_plane_error(h, "dns_get_state");
 }
 
 int dns_get_state_spectral(dns_handle* h, void* uhat, int on_device) {
@@ -648,7 +711,7 @@ int dns_get_state_spectral(dns_handle* h, void* uhat, int on_device) {
     h->w_valid = false;
   }
   DNS_CUDA(cudaStreamSynchronize(h->stream), "dns_get_state_spectral");
-  return DNS_OK;
+  return check_plane_error(h, "dns_get_state_spectral");
 }
 
 int dns_rhs(dns_handle* h, void* duhat, int on_device) {
@@ -680,6 +743,7 @@ int dns_diagnostics(dns_handle* h, dns_diag* out) {
   DNS_CUDA(cudaMemcpyAsync(r, h->diag + DIAG_BLOCKS * 4, sizeof(r), cudaMemcpyDeviceToHost, h->stream),
            "dns_diagnostics copy");
   DNS_CUDA(cudaStreamSynchronize(h->stream), "dns_diagnostics");
+  if ((rc = check_plane_error(h, "dns_diagnostics"))) return rc;
   const double n6 = std::pow((double)h->N, 6.0);
   unsigned long long bits;
   memcpy(&bits, &r[4], sizeof(bits));
@@ -763,10 +827,12 @@ int dns_profile_steps(dns_handle* h, int n, double* ms, int* launches, int nclas
   if (n < 1 || !ms || !launches || nclass < 4) return fail(DNS_ERR_ARG, "dns_profile_steps: bad arguments");
   if ((rc = use_device(h))) return rc;
   if (!h->w_valid) {
-    DNS_CUDA(h->ops->x_inverse_curl(base_args(h), 0, h->stream), "dns_profile_steps initial transform");
+    DNS_CUDA(prime_work(h, h->stream), "dns_profile_steps initial transform");
     h->w_valid = true;
   }
-  const int nk = 4 * rk_stages(h) * n;
+  const bool fused = use_fused(h);
+  const int parts = fused ? 2 : 4;  // plane-pass schedule: z-pass, plane pass
+  const int nk = parts * rk_stages(h) * n;
   std::vector<cudaEvent_t> ev(nk + 1);
   for (auto& e : ev) DNS_CUDA(cudaEventCreate(&e), "cudaEventCreate");
   PassArgs a = base_args(h);
@@ -775,8 +841,8 @@ int dns_profile_steps(dns_handle* h, int n, double* ms, int* launches, int nclas
   for (int i = 0; i < n && err == cudaSuccess; ++i) {
     for (int s = 0; s < rk_stages(h) && err == cudaSuccess; ++s) {
       set_stage(h, s, a);
-      for (int p = 0; p < 4 && err == cudaSuccess; ++p) {
-        err = h->ops->rk_stage_part(a, p, h->stream);
+      for (int p = 0; p < parts && err == cudaSuccess; ++p) {
+        err = fused ? h->ops->rk_stage_fused_part(a, p, h->stream) : h->ops->rk_stage_part(a, p, h->stream);
         if (err == cudaSuccess) err = cudaEventRecord(ev[++k], h->stream);
       }
     }
@@ -789,13 +855,13 @@ int dns_profile_steps(dns_handle* h, int n, double* ms, int* launches, int nclas
   for (int j = 1; j <= k && err == cudaSuccess; ++j) {
     float t = 0.f;
     err = cudaEventElapsedTime(&t, ev[j - 1], ev[j]);
-    ms[(j - 1) % 4] += t;
-    launches[(j - 1) % 4] += 1;
+    ms[(j - 1) % parts] += t;
+    launches[(j - 1) % parts] += 1;
   }
   for (auto& e : ev) cudaEventDestroy(e);
   if (err != cudaSuccess) return cuda_fail(err, "dns_profile_steps");
   h->t += n * h->dt;
-  return DNS_OK;
+  return check_plane_error(h, "dns_profile_steps");
 }
 
 size_t dns_device_bytes(const dns_handle* h) { return h ? h->bytes : 0; }
@@ -803,6 +869,52 @@ size_t dns_device_bytes(const dns_handle* h) { return h ? h->bytes : 0; }
 const char* dns_last_error(const dns_handle* h) {
   (void)h;
   return g_err.c_str();
+}
+
+int dns_debug_plane_wait_timeout(dns_handle* h) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!h->ops->plane_wait_test || !h->ctl)
+    return fail(DNS_ERR_UNSUPPORTED, "dns_debug_plane_wait_timeout: N = %d has no plane pass", h->N);
+  if ((rc = use_device(h))) return rc;
+  PassArgs a = base_args(h);
+  set_stage(h, 0, a);
+  h->w_valid = false;  // W is left partly transformed; the next step re-primes it
+  DNS_CUDA(h->ops->plane_wait_test(a, h->stream), "dns_debug_plane_wait_timeout");
+  rc = check_plane_error(h, "dns_debug_plane_wait_timeout");
+  if (rc == DNS_OK) return fail(DNS_ERR_ARG, "dns_debug_plane_wait_timeout: the waits did not give up");
+  return rc;
+}
+
+int dns_measure_fp64_peak(double* tflops) {
+  if (!tflops) return fail(DNS_ERR_ARG, "dns_measure_fp64_peak: tflops is NULL");
+  int dev = 0, sms = 0;
+  DNS_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+  DNS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
+  const int blocks = 4 * sms, iters = 8192;
+  double* sink = nullptr;
+  DNS_CUDA(cudaMalloc(&sink, sizeof(double)), "dns_measure_fp64_peak sink");
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  cudaError_t ce = cudaEventCreate(&t0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&t1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 4 && ce == cudaSuccess; ++rep) {  // first launch warms up
+    ce = cudaEventRecord(t0, 0);
+    k_fp64_fma_probe<<<blocks, FMA_PROBE_THREADS>>>(sink, iters, 0.9999999, 1e-9);
+    if (ce == cudaSuccess) ce = cudaGetLastError();
+    if (ce == cudaSuccess) ce = cudaEventRecord(t1, 0);
+    if (ce == cudaSuccess) ce = cudaEventSynchronize(t1);
+    float f = 0.f;
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&f, t0, t1);
+    if (ce == cudaSuccess && rep > 0 && f < best) best = f;
+  }
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  cudaFree(sink);
+  if (ce != cudaSuccess) return cuda_fail(ce, "dns_measure_fp64_peak");
+  const double flops = 2.0 * FMA_PROBE_CHAINS * (double)iters * blocks * FMA_PROBE_THREADS;
+  *tflops = flops / (best * 1e-3) / 1e12;
+  return DNS_OK;
 }
 
 int dns_debug_fail_alloc_after(int n) {
@@ -954,7 +1066,7 @@ int ens_capture(dns_ensemble* e, int K) {
 int ens_prepare_members(dns_ensemble* e) {
   for (dns_handle* h : e->m) {
     if (!h->w_valid) {
-      DNS_CUDA(h->ops->x_inverse_curl(base_args(h), 0, e->main), "ensemble initial transform");
+      DNS_CUDA(prime_work(h, e->main), "ensemble initial transform");
       h->w_valid = true;
     }
   }
@@ -1126,6 +1238,30 @@ int dns_ensemble_streams(const dns_ensemble* e) { return e ? e->streams : 0; }
 int dns_ensemble_synchronize(dns_ensemble* e) {
   if (!e) return fail(DNS_ERR_ARG, "dns_ensemble_synchronize: ensemble is NULL");
   DNS_CUDA(cudaStreamSynchronize(e->main), "dns_ensemble_synchronize");
+  return DNS_OK;
+}
+
+int dns_ensemble_time_steps(dns_ensemble* e, int n, double* ms) {
+  if (!e || n < 1 || !ms) return fail(DNS_ERR_ARG, "dns_ensemble_time_steps: bad arguments");
+  int rc = ens_prepare_members(e);
+  if (rc) return rc;
+  if (e->dirty || !e->gexec) {
+    if ((rc = ens_capture(e, e->streams))) return rc;
+  }
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  cudaError_t ce = cudaEventCreate(&t0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&t1);
+  if (ce == cudaSuccess) ce = cudaEventRecord(t0, e->main);
+  for (int i = 0; i < n && ce == cudaSuccess; ++i) ce = cudaGraphLaunch(e->gexec, e->main);
+  if (ce == cudaSuccess) ce = cudaEventRecord(t1, e->main);
+  if (ce == cudaSuccess) ce = cudaEventSynchronize(t1);
+  float f = 0.f;
+  if (ce == cudaSuccess) ce = cudaEventElapsedTime(&f, t0, t1);
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  if (ce != cudaSuccess) return cuda_fail(ce, "dns_ensemble_time_steps");
+  for (dns_handle* h : e->m) h->t += n * h->dt;
+  *ms = f;
   return DNS_OK;
 }
 

@@ -35,6 +35,8 @@ struct PassArgs {
   int ztile = 0;          // z-pass tile width of the stage launches; 0 = default
   const void* in = nullptr;  // physical input (3,N,N,N) for set_state
   void* out = nullptr;       // physical output (3,N,N,N) / RHS output
+  int* ctl = nullptr;  // plane-pass control block (error flag, queue head, per-plane counters)
+  int plane_lag = 0;   // plane-pass lag in queue steps (0: chosen from the block count)
   double* partials = nullptr;          // diagnostics block partials
   unsigned long long* maxbits = nullptr;  // diagnostics max|div| (bits of a double)
 };
@@ -70,6 +72,18 @@ struct DnsOps {
   int (*y_tiles)(int* tiles, int max);
   // the same for the z-pass
   int (*z_tiles)(int* tiles, int max);
+  // Plane-pass schedule (nullptr where not compiled): the stage as two launches,
+  // z-pass then one persistent plane pass (y-forward, x-stage, y-inverse walked by
+  // kz plane); W then holds the x- and y-inverse of u and omega between stages.
+  // prime_fused brings W into that form from the state (x inverse, then y inverse).
+  cudaError_t (*rk_stage_fused)(const PassArgs& a, cudaStream_t s);
+  cudaError_t (*prime_fused)(const PassArgs& a, int from_stage, cudaStream_t s);
+  // part 0: z-pass (with the control-block reset), part 1: plane pass
+  cudaError_t (*rk_stage_fused_part)(const PassArgs& a, int part, cudaStream_t s);
+  // one plane pass whose queue starts at its first y-inverse item of plane 0, so
+  // that its waits cannot be met (test of the bounded waits)
+  cudaError_t (*plane_wait_test)(const PassArgs& a, cudaStream_t s);
+  int plane_ctl_words;  // ints of the plane-pass control block (0: no plane pass)
 };
 
 constexpr int BATCH_MAX_N = 128;

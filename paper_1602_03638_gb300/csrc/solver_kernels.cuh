@@ -132,6 +132,19 @@ __device__ __forceinline__ void put_curl_lines(cx<T>* s, int pos, int LS, cx<T> 
   p[5 * LS] = conjg(w2);
 }
 
+// Global store of one complex value; with HINT, marked evict-first in L2 (the
+// RK state the plane pass streams past the plane data it keeps in L2).
+template <bool HINT, typename T>
+__device__ __forceinline__ void st_state(cx<T>* p, cx<T> v, unsigned long long pol) {
+  if constexpr (!HINT) {
+    *p = v;
+  } else if constexpr (sizeof(T) == 4) {
+    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(v.x), "f"(v.y), "l"(pol) : "memory");
+  } else {
+    asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(p), "d"(v.x), "d"(v.y), "l"(pol) : "memory");
+  }
+}
+
 // Global store of a forward-transformed state row with the Nyquist modes zeroed.
 template <typename T>
 struct GStoreNyquistFree {
@@ -148,8 +161,16 @@ struct GStoreNyquistFree {
 // ---------------------------------------------------------------------------
 // x-pass: one block owns one row (kz, ky) of length N; warp f transforms line f.
 // ---------------------------------------------------------------------------
-template <typename T, int N, int MODE>
+// NT: threads of the calling block (XP_THREADS for k_xpass; the plane pass runs the
+// stage update with 256, its warps 6 and 7 idle during the line transforms).
+template <typename T, int N, int MODE, int NT = XP_THREADS>
 __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
+  static_assert(NT >= XP_THREADS && NT % 32 == 0, "the x-pass needs at least one warp per line");
+  // in the plane pass the RK state is a stream past the plane data kept in L2 (FP32
+  // instances only: the hinted FP64 512^3 plane pass raised an illegal-instruction
+  // fault whose cause was not found, so FP64 keeps plain accesses)
+  constexpr bool HINT = NT != XP_THREADS && MODE == XM_STAGE && sizeof(T) == 4;
+  const unsigned long long pol = HINT ? l2_evict_first_policy() : 0ull;
   using G = Geometry<T, N>;
   constexpr int LS = G::XLS;
   constexpr size_t FS = G::FS;
@@ -181,7 +202,7 @@ __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
     cx<T>* const st = s + G::XST;  // XPRE: rows [Sst 0..2][U1 0..2][U 0..2], N values each
     if constexpr (G::XPRE) {
       if (row_kept) {
-        for (int e = threadIdx.x; e < 3 * N; e += XP_THREADS) {
+        for (int e = threadIdx.x; e < 3 * N; e += NT) {
           const int f = e / N, j = e % N;
           cp_async<sizeof(cx<T>)>(s + f * LS + padp(j), W + f * FS + rb + j);
         }
@@ -189,9 +210,10 @@ __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
       cp_async_commit();
       constexpr int PK = 16 / (int)sizeof(cx<T>);  // complex values per 16-byte copy
       auto fetch_rows = [&](const cx<T>* src, cx<T>* dst) {
-        for (int e = threadIdx.x; e < 3 * N / PK; e += XP_THREADS) {
+        for (int e = threadIdx.x; e < 3 * N / PK; e += NT) {
           const int f = (e * PK) / N, j = (e * PK) % N;
-          cp_async<16>(dst + f * N + j, src + f * FS + rb + j);
+          if constexpr (HINT) cp_async16_hint(dst + f * N + j, src + f * FS + rb + j, pol);
+          else cp_async<16>(dst + f * N + j, src + f * FS + rb + j);
         }
       };
       fetch_rows(Sst, st);
@@ -220,7 +242,7 @@ __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
     // index itself, exactly as without a box option
     auto columns = [&](auto scaled) {
       constexpr bool SCALED = decltype(scaled)::value;
-      for (int j = threadIdx.x; j < N; j += XP_THREADS) {
+      for (int j = threadIdx.x; j < N; j += NT) {
         const int kxi = kfreq(j, N);
         const T kx = SCALED ? (T)kxi * ksx : (T)kxi;
         const int pj = padp(j);
@@ -258,37 +280,37 @@ __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
             v0 = u0 + scal(d0, cA);
             v1 = u1 + scal(d1, cA);
             v2 = u2 + scal(d2, cA);
-            U[gi] = v0;
-            U[FS + gi] = v1;
-            U[2 * FS + gi] = v2;
+            st_state<HINT>(U + gi, v0, pol);
+            st_state<HINT>(U + FS + gi, v1, pol);
+            st_state<HINT>(U + 2 * FS + gi, v2, pol);
           } else if (stage == 0) {
-            U1[gi] = u0 + scal(d0, cA);
-            U1[FS + gi] = u1 + scal(d1, cA);
-            U1[2 * FS + gi] = u2 + scal(d2, cA);
+            st_state<HINT>(U1 + gi, u0 + scal(d0, cA), pol);
+            st_state<HINT>(U1 + FS + gi, u1 + scal(d1, cA), pol);
+            st_state<HINT>(U1 + 2 * FS + gi, u2 + scal(d2, cA), pol);
             v0 = u0 + scal(d0, cB);
             v1 = u1 + scal(d1, cB);
             v2 = u2 + scal(d2, cB);
-            US[gi] = v0;
-            US[FS + gi] = v1;
-            US[2 * FS + gi] = v2;
+            st_state<HINT>(US + gi, v0, pol);
+            st_state<HINT>(US + FS + gi, v1, pol);
+            st_state<HINT>(US + 2 * FS + gi, v2, pol);
           } else if (stage < last) {
             const cx<T> b0 = ld_0(0, j), b1 = ld_0(1, j), b2 = ld_0(2, j);
-            U1[gi] = ld_1(0, j) + scal(d0, cA);
-            U1[FS + gi] = ld_1(1, j) + scal(d1, cA);
-            U1[2 * FS + gi] = ld_1(2, j) + scal(d2, cA);
+            st_state<HINT>(U1 + gi, ld_1(0, j) + scal(d0, cA), pol);
+            st_state<HINT>(U1 + FS + gi, ld_1(1, j) + scal(d1, cA), pol);
+            st_state<HINT>(U1 + 2 * FS + gi, ld_1(2, j) + scal(d2, cA), pol);
             v0 = b0 + scal(d0, cB);
             v1 = b1 + scal(d1, cB);
             v2 = b2 + scal(d2, cB);
-            US[gi] = v0;
-            US[FS + gi] = v1;
-            US[2 * FS + gi] = v2;
+            st_state<HINT>(US + gi, v0, pol);
+            st_state<HINT>(US + FS + gi, v1, pol);
+            st_state<HINT>(US + 2 * FS + gi, v2, pol);
           } else {
             v0 = ld_1(0, j) + scal(d0, cA);
             v1 = ld_1(1, j) + scal(d1, cA);
             v2 = ld_1(2, j) + scal(d2, cA);
-            U[gi] = v0;
-            U[FS + gi] = v1;
-            U[2 * FS + gi] = v2;
+            st_state<HINT>(U + gi, v0, pol);
+            st_state<HINT>(U + FS + gi, v1, pol);
+            st_state<HINT>(U + 2 * FS + gi, v2, pol);
           }
           if constexpr (G::XPRE && !G::XWIDE) {
             // u into lines 0-2 (padded, where this thread read N_hat), omega into
@@ -312,6 +334,7 @@ __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
       columns(std::true_type{});
     if constexpr (MODE == XM_STAGE) {
       __syncthreads();
+      if (NT > XP_THREADS && warp >= 6) return;  // one warp per line of u and omega
       if constexpr (G::XPRE && !G::XWIDE) {
         if (warp < 3) {
           const SLine<T, 1> line{s + warp * LS};
@@ -336,7 +359,7 @@ __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
     // inverse x transform of u and omega (XM_INV_CURL), of u alone
     // (XM_INV_PLAIN) or of i k . u (XM_INV_DIV), all scaled by 1/N^3
     constexpr int NF = (MODE == XM_INV_CURL) ? 6 : (MODE == XM_INV_PLAIN ? 3 : 1);
-    for (int j = threadIdx.x; j < N; j += XP_THREADS) {
+    for (int j = threadIdx.x; j < N; j += NT) {
       const size_t gi = rb + j;
       const int pj = padp(j);
       const cx<T> u0 = U[gi], u1 = U[FS + gi], u2 = U[2 * FS + gi];
@@ -394,19 +417,16 @@ __device__ __forceinline__ int ywalk_row(int r) {
   }
 }
 
-template <typename T, int N, int INV, int PRUNE, int TXO = 0>
-__global__ void __launch_bounds__(YCfg<T, N, INV, TXO>::THREADS, (YCfg<T, N, INV, TXO>::MINB)) k_ypass(cx<T>* __restrict__ F,
-                                                                                         const cx<T>* __restrict__ tw,
-                                                                                         int kmax3) {
-  using G = Geometry<T, N>;
+// One y tile: TX adjacent columns starting at `base` (field, kz plane and first
+// column already applied), transformed along y in place. NT: threads of the block.
+template <typename T, int N, int INV, int PRUNE, int TXO, int NT>
+__device__ __forceinline__ void ypass_tile(cx<T>* base, const cx<T>* __restrict__ tw, int kmax3) {
   using Y = YCfg<T, N, INV, TXO>;
   constexpr int TX = Y::TX;
   constexpr int LD = Y::LD;
-  constexpr int NT = Y::THREADS;  // warps loop over the columns
   extern __shared__ unsigned char smraw[];
   cx<T>* s = reinterpret_cast<cx<T>*>(smraw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  cx<T>* base = F + blockIdx.z * G::FS + (size_t)blockIdx.y * N * N + blockIdx.x * TX;
   // the whole tile in flight at once (cp.async, no register staging); the
   // inverse's conjugation is applied when the first pass reads it
 #pragma unroll 8
@@ -418,7 +438,7 @@ __global__ void __launch_bounds__(YCfg<T, N, INV, TXO>::THREADS, (YCfg<T, N, INV
   cp_async_wait<0>();
   __syncthreads();
 #pragma unroll 1
-  for (int c = warp; c < TX; c += NT / 32) {
+  for (int c = warp; c < TX; c += NT / 32) {  // warps loop over the columns
     const SLine<T, LD> line{s + c};
     if constexpr (INV) warp_fft<T, N, N>(SLineConj<T, LD>{s + c}, line, line, tw, lane);
     else warp_fft<T, N, N>(line, line, line, tw, lane);
@@ -433,6 +453,16 @@ __global__ void __launch_bounds__(YCfg<T, N, INV, TXO>::THREADS, (YCfg<T, N, INV
   }
 }
 
+template <typename T, int N, int INV, int PRUNE, int TXO = 0>
+__global__ void __launch_bounds__(YCfg<T, N, INV, TXO>::THREADS, (YCfg<T, N, INV, TXO>::MINB)) k_ypass(cx<T>* __restrict__ F,
+                                                                                         const cx<T>* __restrict__ tw,
+                                                                                         int kmax3) {
+  using G = Geometry<T, N>;
+  using Y = YCfg<T, N, INV, TXO>;
+  cx<T>* base = F + blockIdx.z * G::FS + (size_t)blockIdx.y * N * N + blockIdx.x * Y::TX;
+  ypass_tile<T, N, INV, PRUNE, TXO, Y::THREADS>(base, tw, kmax3);
+}
+
 // Batched form on the members' work arrays (ensembles): blockIdx.z = member *
 // fields + field; otherwise the same steps as k_ypass.
 template <typename T, int N, int INV, int PRUNE>
@@ -440,39 +470,10 @@ __global__ void __launch_bounds__(YCfg<T, N, INV>::THREADS, (YCfg<T, N, INV>::MI
                                                                                            int fields) {
   using G = Geometry<T, N>;
   using Y = YCfg<T, N, INV>;
-  constexpr int TX = Y::TX;
-  constexpr int LD = Y::LD;
-  constexpr int NT = Y::THREADS;
-  extern __shared__ unsigned char smraw[];
-  cx<T>* s = reinterpret_cast<cx<T>*>(smraw);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const PassArgs& a = B.a[blockIdx.z / fields];
-  const cx<T>* tw = reinterpret_cast<const cx<T>*>(a.tw);
-  const int kmax3 = a.kmax3;
   cx<T>* base = reinterpret_cast<cx<T>*>(a.W) + (blockIdx.z % fields) * G::FS + (size_t)blockIdx.y * N * N +
-                blockIdx.x * TX;
-#pragma unroll 8
-  for (int e = threadIdx.x; e < TX * N; e += NT) {
-    const int x = e % TX, y = ywalk_row<T, TX, N>(e / TX);
-    cp_async<sizeof(cx<T>)>(s + padp(y) * LD + x, base + (size_t)y * N + x);
-  }
-  cp_async_commit();
-  cp_async_wait<0>();
-  __syncthreads();
-#pragma unroll 1
-  for (int c = warp; c < TX; c += NT / 32) {
-    const SLine<T, LD> line{s + c};
-    if constexpr (INV) warp_fft<T, N, N>(SLineConj<T, LD>{s + c}, line, line, tw, lane);
-    else warp_fft<T, N, N>(line, line, line, tw, lane);
-  }
-  __syncthreads();
-#pragma unroll 8
-  for (int e = threadIdx.x; e < TX * N; e += NT) {
-    const int x = e % TX, y = ywalk_row<T, TX, N>(e / TX);
-    if (PRUNE && !kept(kfreq(y, N), kmax3)) continue;
-    const cx<T> v = s[padp(y) * LD + x];
-    base[(size_t)y * N + x] = INV ? conjg(v) : v;
-  }
+                blockIdx.x * Y::TX;
+  ypass_tile<T, N, INV, PRUNE, 0, Y::THREADS>(base, reinterpret_cast<const cx<T>*>(a.tw), a.kmax3);
 }
 
 // ---------------------------------------------------------------------------
@@ -1635,6 +1636,193 @@ __global__ void __launch_bounds__(DG_THREADS) k_diag(PassArgs a) {
 __global__ void k_diag_final(double* partials, int nblocks);
 
 // ---------------------------------------------------------------------------
+// Plane pass: the y-forward, x-stage and y-inverse of one RK stage in ONE
+// persistent launch, walked in kz-plane order so that each plane's data passes
+// from one step to the next through L2 instead of HBM. The three steps of a
+// stage are local to a kz plane (they transform along y and x only): the y
+// forward of plane p feeds the x-stage rows of plane p, whose u and omega feed
+// the y inverse of plane p. Only the z-pass, a separate launch, couples planes
+// (the change of pass direction that replaces the paper's slab transposes,
+// Sec. 3.2).
+//
+// Work is taken in chunks (CYF y-forward tiles, CX x-stage rows or CYI y-inverse
+// tiles of one plane) from one atomic counter, in a fixed order of steps q:
+//   step q = [Yf(q) if q < kc] [X(q - L) if L <= q < M + L] [Yi(q - 2L) if q >= 2L]
+// so that a plane's x-stage rows come L steps after its y-forward tiles and its
+// y-inverse tiles L steps after its rows (L, the lag, is chosen by the host so
+// that L steps span more chunks than there are blocks: the producers are done
+// when their consumers are taken). X(p) waits until every Yf(p) chunk is
+// released, Yi(p) until every X(p) chunk is; each warp releases its own stores
+// (red.release after __syncwarp), so a chunk counts PLANE_THREADS / 32 releases.
+// Every chunk a chunk waits for comes earlier in the order and was taken by a
+// block that is running (or holds it as its prefetched next chunk while it
+// finishes an earlier one), so the earliest unfinished chunk always progresses:
+// no residency assumption is needed. A wait still gives up after PLANE_WAIT_NS
+// (an error flag that the host reports as DNS_ERR_TIMEOUT and a stop flag that
+// ends every block's loop).
+// ---------------------------------------------------------------------------
+constexpr int PLANE_THREADS = 256;
+constexpr int PLANE_WARPS = PLANE_THREADS / 32;
+// control block: [0] error (sticky; cleared by the host when reported), [1] queue
+// head, [2] stop flag, [3] unused, then the per-plane counters yf_done[M], x_done[M].
+// Words 1.. are zeroed before every launch.
+constexpr int PLANE_CTL_ERR = 0, PLANE_CTL_HEAD = 1, PLANE_CTL_STOP = 2, PLANE_CTL_WORDS = 4;
+constexpr unsigned long long PLANE_WAIT_NS = 1000000000ull;  // 1 s
+
+template <typename T, int N>
+struct PlaneCfg {
+  using YI = YCfg<T, N, 1>;
+  using YF = YCfg<T, N, 0>;
+  static constexpr int NTI = N / YI::TX;  // y-inverse tiles per field and plane
+  static constexpr int NTF = N / YF::TX;  // y-forward tiles per field and plane
+  static constexpr int CX = 4, CYF = 2, CYI = 2;  // rows / tiles per chunk
+  static constexpr int NYF = 3 * NTF / CYF;  // y-forward chunks per plane
+  static constexpr int NX = N / CX;          // x-stage chunks per plane
+  static constexpr int NYI = 6 * NTI / CYI;  // y-inverse chunks per plane
+  static constexpr bool enabled = N >= 256;
+  static_assert(!enabled || (3 * NTF % CYF == 0 && N % CX == 0 && 6 * NTI % CYI == 0), "plane-pass chunks");
+  static constexpr int MINB = (sizeof(T) == 4 && N <= 512) ? 3 : 2;
+  static constexpr size_t SMEM_Y = YI::SMEM > YF::SMEM ? YI::SMEM : YF::SMEM;
+  static constexpr int ctl_words() { return PLANE_CTL_WORDS + N; }  // 2 counters per plane, M = N/2 planes
+  // the lag: L steps hold at least 1.5x as many chunks as the launch has blocks
+  static int lag(int blocks) {
+    const int per_step = NYF + NX + NYI;
+    int L = (3 * blocks + 2 * per_step - 1) / (2 * per_step);
+    return L < 1 ? 1 : (L > 8 ? 8 : L);
+  }
+};
+
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_gpu(int* p, int v) {
+  asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Waits until *cnt >= target; false if the pass was stopped or the wait gave up.
+static __device__ __noinline__ bool plane_wait(const int* cnt, int target, int* ctl) {
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    __nanosleep(64);
+    if (ld_acquire_gpu(cnt) >= target) return true;
+    if (ld_acquire_gpu(ctl + PLANE_CTL_STOP)) return false;
+    if (global_ns() - t0 > PLANE_WAIT_NS) {
+      atomicExch(ctl + PLANE_CTL_ERR, 1);
+      atomicExch(ctl + PLANE_CTL_STOP, 1);
+      return false;
+    }
+  }
+}
+
+template <typename T, int N>
+__device__ __forceinline__ int plane_step_chunks(int q, int kc, int L) {
+  using P = PlaneCfg<T, N>;
+  constexpr int M = N / 2;
+  return (q < kc ? P::NYF : 0) + (q >= L && q < M + L ? P::NX : 0) + (q >= 2 * L ? P::NYI : 0);
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(PLANE_THREADS, (PlaneCfg<T, N>::MINB))
+    k_plane(PassArgs a, int* __restrict__ ctl, int L) {
+  using G = Geometry<T, N>;
+  using P = PlaneCfg<T, N>;
+  constexpr int M = N / 2;
+  __shared__ int s_kind, s_plane, s_chunk;
+  int kc = (a.kmax3 + 2) / 3;
+  if (kc > M) kc = M;
+  int* yf_done = ctl + PLANE_CTL_WORDS;
+  int* x_done = yf_done + M;
+  const int total = P::NYF * kc + P::NX * M + P::NYI * M;
+  cx<T>* W = reinterpret_cast<cx<T>*>(a.W);
+  const cx<T>* tw = reinterpret_cast<const cx<T>*>(a.tw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // thread 0: the prefetched next chunk, and the cursor of the queue (step q
+  // holds chunks [qbeg, qbeg + plane_step_chunks(q)))
+  int nxt = 0, q = 0, qbeg = 0;
+  if (threadIdx.x == 0) nxt = atomicAdd(ctl + PLANE_CTL_HEAD, 1);
+  for (;;) {
+    if (threadIdx.x == 0) {
+      int kind = -1, plane = 0, chunk = 0;
+      const int item = nxt;
+      if (item < total) {
+        int n = plane_step_chunks<T, N>(q, kc, L);
+        while (item >= qbeg + n) {
+          qbeg += n;
+          ++q;
+          n = plane_step_chunks<T, N>(q, kc, L);
+        }
+        const int r = item - qbeg;
+        const int nyf = q < kc ? P::NYF : 0;
+        const int nx = (q >= L && q < M + L) ? P::NX : 0;
+        const int* dep = nullptr;
+        int target = 0;
+        if (r < nyf) {
+          kind = 0;
+          plane = q;
+          chunk = r;
+        } else if (r < nyf + nx) {
+          kind = 1;
+          plane = q - L;
+          chunk = r - nyf;
+          if (plane < kc) {
+            dep = yf_done + plane;
+            target = P::NYF * PLANE_WARPS;
+          }
+        } else {
+          kind = 2;
+          plane = q - 2 * L;
+          chunk = r - nyf - nx;
+          dep = x_done + plane;
+          target = P::NX * PLANE_WARPS;
+        }
+        if (dep && ld_acquire_gpu(dep) < target && !plane_wait(dep, target, ctl)) kind = -1;
+        if (kind >= 0) nxt = atomicAdd(ctl + PLANE_CTL_HEAD, 1);  // used by the next iteration
+      }
+      s_kind = kind;
+      s_plane = plane;
+      s_chunk = chunk;
+    }
+    __syncthreads();  // publishes the chunk; the previous chunk's shared memory is free
+    const int kind = s_kind, plane = s_plane, chunk = s_chunk;
+    if (kind < 0) break;
+    if (kind == 0) {
+#pragma unroll 1
+      for (int k = 0; k < P::CYF; ++k) {
+        if (k) __syncthreads();
+        const int t = chunk * P::CYF + k;
+        cx<T>* base = W + (t / P::NTF) * G::FS + (size_t)plane * N * N + (t % P::NTF) * P::YF::TX;
+        ypass_tile<T, N, 0, 1, 0, PLANE_THREADS>(base, tw, a.kmax3);
+      }
+    } else if (kind == 1) {
+#pragma unroll 1
+      for (int k = 0; k < P::CX; ++k) {
+        if (k) __syncthreads();
+        xpass_body<T, N, XM_STAGE, PLANE_THREADS>(a, plane * N + chunk * P::CX + k);
+      }
+    } else {
+#pragma unroll 1
+      for (int k = 0; k < P::CYI; ++k) {
+        if (k) __syncthreads();
+        const int t = chunk * P::CYI + k;
+        cx<T>* base = W + (t / P::NTI) * G::FS + (size_t)plane * N * N + (t % P::NTI) * P::YI::TX;
+        ypass_tile<T, N, 1, 0, 0, PLANE_THREADS>(base, tw, a.kmax3);
+      }
+    }
+    if (kind < 2) {  // each warp releases its own stores of the chunk
+      __syncwarp();
+      if (lane == 0) red_release_gpu(kind == 0 ? yf_done + plane : x_done + plane, 1);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Host launchers for one (T, N).
 // ---------------------------------------------------------------------------
 // Number of SMs of the current device (persistent kernels launch one block each).
@@ -1743,6 +1931,7 @@ struct SolverImpl {
     if constexpr (N == 512 && sizeof(T) == 4) DNS_ATTR((k_zcross16p<T, N>), Z16P<T>::SMEM);
     if constexpr (N == 1024 && sizeof(T) == 4) DNS_ATTR((k_zcross32p<T, N>), Z32P<T>::SMEM);
     if constexpr (N == 256 && sizeof(T) == 4) DNS_ATTR((k_zcross8q<T, N>), Z8Q<T>::SMEM);
+    if constexpr (PlaneCfg<T, N>::enabled) DNS_ATTR((k_plane<T, N>), (plane_smem(1, 3)));
     DNS_ATTR((k_zpass<T, N, ZM_STORE>), G::ZSMEM);
     DNS_ATTR((k_zpass<T, N, ZM_LOAD>), G::ZSMEM);
     DNS_ATTR((k_zpass<T, N, ZM_MAXABS>), G::ZSMEM);
@@ -1841,6 +2030,71 @@ struct SolverImpl {
     }
   }
 
+  // ---- plane-pass schedule
+  using PC = PlaneCfg<T, N>;
+  static size_t plane_smem(int stage, int last) {
+    const size_t x = xsmem_stage(stage, last);
+    return x > PC::SMEM_Y ? x : PC::SMEM_Y;
+  }
+  static cudaError_t plane_reset(const PassArgs& a, cudaStream_t st) {
+    return cudaMemsetAsync(a.ctl + 1, 0, (size_t)(PC::ctl_words() - 1) * sizeof(int), st);
+  }
+  static void plane_launch(const PassArgs& a, cudaStream_t st) {
+    const int blocks = num_sms() * PC::MINB;
+    const int L = a.plane_lag > 0 ? a.plane_lag : PC::lag(blocks);
+    k_plane<T, N><<<blocks, PLANE_THREADS, plane_smem(a.stage, a.last), st>>>(f32args(a), a.ctl, L);
+  }
+  static cudaError_t rk_stage_fused(const PassArgs& a, cudaStream_t st) {
+    if constexpr (PC::enabled) {
+      cudaError_t e = plane_reset(a, st);
+      if (e != cudaSuccess) return e;
+      z_cross(a, st);
+      plane_launch(a, st);
+      return cudaGetLastError();
+    } else {
+      return cudaErrorNotSupported;
+    }
+  }
+  static cudaError_t rk_stage_fused_part(const PassArgs& a, int part, cudaStream_t st) {
+    if constexpr (PC::enabled) {
+      if (part == 0) {
+        cudaError_t e = plane_reset(a, st);
+        if (e != cudaSuccess) return e;
+        z_cross(a, st);
+      } else {
+        plane_launch(a, st);
+      }
+      return cudaGetLastError();
+    } else {
+      return cudaErrorNotSupported;
+    }
+  }
+  static cudaError_t prime_fused(const PassArgs& a, int from_stage, cudaStream_t st) {
+    cudaError_t e = x_inverse_curl(a, from_stage, st);
+    if (e != cudaSuccess) return e;
+    y_go<1, 0, 0>(reinterpret_cast<cx<T>*>(a.W), reinterpret_cast<const cx<T>*>(a.tw), a.kmax3, M, 6, st);
+    return cudaGetLastError();
+  }
+  static cudaError_t plane_wait_test(const PassArgs& a, cudaStream_t st) {
+    if constexpr (PC::enabled) {
+      int kc = (a.kmax3 + 2) / 3;
+      if (kc > M) kc = M;
+      // the chunks of steps 0 .. 2L-1 and step 2L's y-forward and x-stage chunks
+      const int L = a.plane_lag > 0 ? a.plane_lag : PC::lag(num_sms() * PC::MINB);
+      int first_yi = 0;  // no step before 2L holds y-inverse chunks
+      for (int q = 0; q <= 2 * L; ++q) first_yi += (q < kc ? PC::NYF : 0) + (q >= L && q < M + L ? PC::NX : 0);
+      cudaError_t e = plane_reset(a, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(a.ctl + PLANE_CTL_HEAD, &first_yi, sizeof(int), cudaMemcpyHostToDevice, st);
+      if (e != cudaSuccess) return e;
+      plane_launch(a, st);
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // first_yi lives on this stack
+      return e;
+    } else {
+      return cudaErrorNotSupported;
+    }
+  }
+
   static cudaError_t rhs(const PassArgs& a, cudaStream_t st) {
     cudaError_t e = x_inverse_curl(a, 0, st);
     if (e != cudaSuccess) return e;
@@ -1880,9 +2134,13 @@ struct SolverImpl {
 
   static const DnsOps* ops() {
     constexpr bool batched = N <= BATCH_MAX_N && !ZCross<T, N>::enabled;
+    constexpr bool plane = PlaneCfg<T, N>::enabled;
     static const DnsOps o = {N,         sizeof(T) == 4 ? 0 : 1, sizeof(cx<T>), &prepare,   &x_inverse_curl,
                              &rk_stage, &rk_stage_part,        &rhs,          &forward3d, &inverse3d,
-                             &diag,     batched ? &rk_stage_batch : nullptr, &y_tiles, &z_tiles};
+                             &diag,     batched ? &rk_stage_batch : nullptr, &y_tiles, &z_tiles,
+                             plane ? &rk_stage_fused : nullptr, &prime_fused,
+                             plane ? &rk_stage_fused_part : nullptr, plane ? &plane_wait_test : nullptr,
+                             plane ? PlaneCfg<T, N>::ctl_words() : 0};
     return &o;
   }
 };

@@ -178,13 +178,20 @@ class Solver:
         return {k: getattr(d, k) for k, _ in d._fields_}
 
     KERNEL_CLASSES = ("y_inverse", "z_pass", "y_forward", "x_stage")
+    PLANE_CLASSES = ("z_pass", "plane_pass")
 
     def profile_steps(self, n: int) -> dict:
-        """Advance n steps eagerly; per kernel class (total ms, launches)."""
+        """Advance n steps eagerly; per kernel class (total ms, launches). The classes are
+        those of the handle's schedule: four passes, or z-pass and plane pass."""
         ms = (ctypes.c_double * 4)()
         ln = (ctypes.c_int * 4)()
         _lib.check(_lib.lib().dns_profile_steps(self._h, int(n), ms, ln, 4), "dns_profile_steps")
-        return {k: (ms[i], ln[i]) for i, k in enumerate(self.KERNEL_CLASSES)}
+        names = self.PLANE_CLASSES if self.get_option("fused_planes") else self.KERNEL_CLASSES
+        return {k: (ms[i], ln[i]) for i, k in enumerate(names)}
+
+    def plane_wait_timeout_test(self) -> int:
+        """Runs dns_debug_plane_wait_timeout; returns its status code (DNS_ERR_TIMEOUT expected)."""
+        return int(_lib.lib().dns_debug_plane_wait_timeout(self._h))
 
     def device_bytes(self) -> int:
         return int(_lib.lib().dns_device_bytes(self._h))
@@ -242,6 +249,12 @@ class Ensemble:
     @property
     def streams(self) -> int:
         return int(_lib.lib().dns_ensemble_streams(self._e))
+
+    def time_steps(self, n: int) -> float:
+        """n ensemble steps timed with CUDA events on the ensemble's stream; milliseconds."""
+        ms = ctypes.c_double()
+        _lib.check(_lib.lib().dns_ensemble_time_steps(self._e, int(n), ctypes.byref(ms)), "dns_ensemble_time_steps")
+        return float(ms.value)
 
     def synchronize(self):
         _lib.check(_lib.lib().dns_ensemble_synchronize(self._e), "dns_ensemble_synchronize")

@@ -4,8 +4,13 @@ kernel; 1024: the pipelined canonical kernel).
 
 256^3 and 512^3 compare every mode with the FP64 oracle (a random physical field
 with energy in all modes, the oracle run in full on the host cores). At 1024^3
-the oracle is too large for a test, so the right-hand side of a random
-divergence-free field filling the 2/3 box is checked against what holds at any
+the oracle is too large for a test. There, first, a dense random divergence-free
+field band-limited to |k_i| <= 85 is compared mode by mode with the oracle at
+512^3: its products reach |k_i| <= 170, which neither grid aliases (170 < 256)
+nor masks (3 * 170 < 512), so the right-hand side is the same trigonometric
+polynomial on both grids and its unnormalised coefficients differ by the factor
+(1024/512)^3 = 8. Second, the right-hand side of a random divergence-free field
+filling the 2/3 box is checked against what holds at any
 size (Eq. NSfinal, Sec. 2): the projected, dealiased nonlinear term transfers no
 energy and no helicity (u.(u x w) = w.(u x w) = 0 pointwise, and the mask and the
 projection are the identity on the state), it is divergence-free, and the
@@ -31,7 +36,8 @@ def _built():
     build.build()
 
 
-@pytest.mark.parametrize("N,dtype,tol", [(256, "f64", 1e-12), (256, "f32", 2e-5), (512, "f32", 2e-5)])
+@pytest.mark.parametrize("N,dtype,tol", [(256, "f64", 1e-12), (256, "f32", 2e-5), (512, "f32", 2e-5),
+                                         (512, "f64", 1e-12)])
 def test_rhs_of_random_full_spectrum_field_matches_oracle(N, dtype, tol):
     rng = np.random.default_rng(4000 + N)
     u = rng.standard_normal((3, N, N, N)).astype(np.float32 if dtype == "f32" else np.float64)
@@ -60,6 +66,51 @@ def _release_cached_memory():
     yield
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
+
+
+def _embed(src, N, dev, dtype):
+    """Half spectrum (3, n, n, n/2+1) of |k_i| <= kb modes placed into an N grid (N > 2 n)."""
+    n = src.shape[1]
+    out = torch.zeros((3, N, N, N // 2 + 1), dtype=dtype, device=dev)
+    lo, hi = n // 2, n - n // 2  # indices 0..lo-1 are k >= 0, lo..n-1 are k < 0
+    s = src.to(device=dev, dtype=dtype)
+    kz = min(n // 2 + 1, N // 2 + 1)
+    for a_src, a_dst in ((slice(0, lo), slice(0, lo)), (slice(lo, n), slice(N - hi, N))):
+        for b_src, b_dst in ((slice(0, lo), slice(0, lo)), (slice(lo, n), slice(N - hi, N))):
+            out[:, a_dst, b_dst, :kz] = s[:, a_src, b_src, :kz]
+    return out
+
+
+@pytest.fixture(scope="module")
+def band_limited_case():
+    """A dense divergence-free field with |k_i| <= 85 (the 2/3 box of a 256 grid) and the FP64
+    oracle's right-hand side of it on the 512 grid (nu = 0.004)."""
+    nu = 0.004
+    u256 = inputs.isotropic_spectral(256, seed=31, k0=256 / 5.0, energy=1.0)
+    u512 = _embed(u256, 512, "cpu", torch.complex128) * 8.0
+    ref = sn.rhs(u512.numpy(), sn.Grid(512), nu)
+    return u256, torch.from_numpy(ref), nu
+
+
+@pytest.mark.parametrize("dtype,tol", [("f32", 3e-5), ("f64", 1e-12)])
+def test_rhs_of_band_limited_field_at_1024_matches_oracle_at_512(band_limited_case, dtype, tol):
+    u256, ref512, nu = band_limited_case
+    N, dev = 1024, "cuda"
+    cdt = torch.complex64 if dtype == "f32" else torch.complex128
+    uh = _embed(u256, N, dev, cdt) * 64.0
+    out = torch.empty_like(uh)
+    with Solver(N, nu, 1e-3, dtype) as s:
+        s.set_state_spectral(uh)
+        del uh
+        s.rhs(out)
+    torch.cuda.synchronize()
+    expect = _embed(ref512, N, dev, torch.complex128)  # modes |k_i| <= 255, zero beyond
+    scale = 8.0 * float(ref512.abs().max())
+    err = 0.0
+    for sl in _slabs(N):
+        e = (out[:, sl].to(torch.complex128) - 8.0 * expect[:, sl]).abs().max()
+        err = max(err, float(e) / scale)
+    assert err < tol, err
 
 
 def test_rhs_invariants_at_1024():

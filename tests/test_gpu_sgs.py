@@ -127,6 +127,37 @@ def test_network_gradient_matches_bf16_reference():
     net.close()
 
 
+def test_adam_update_matches_reference():
+    """Three dns_mlp_train_step calls against the FP64 Adam of the reference fed with the same
+    FP32 gradient (dns_mlp_loss_grad on the same batch just before each step): the parameter
+    trajectories agree to FP32 rounding of an update of size ~lr."""
+    sgs = _sgs()
+    rng = np.random.default_rng(11)
+    P = 2048
+    X = rng.normal(size=(P, 10))
+    Tt = rng.normal(size=(P, 6))
+    p = _params_with_norm(4, X)
+    net = sgs.MLP(sg.flatten(p).astype(np.float32))
+    Xd = torch.from_numpy(X.T.astype(np.float32)).cuda().contiguous()
+    Td = torch.from_numpy(Tt.T.astype(np.float32)).cuda().contiguous()
+    lr = 1e-2
+    start = sg.unflatten(net.get_params().astype(np.float64))
+    ref, st = start, sg.adam_init(start)
+    for _ in range(3):
+        _, g = net.loss_grad(Xd, Td)
+        net.train_step(Xd, Td, lr, want_loss=False)
+        got = sg.unflatten(net.get_params().astype(np.float64))
+        ref, st = sg.adam_step(ref, sg.unflatten(g.astype(np.float64)), st, lr)
+        for name in sg.PARAM_ORDER:
+            err = np.abs(got[name] - ref[name]).max()
+            assert err < 1e-4 * lr + 2e-7 * np.abs(ref[name]).max(), (st["t"], name, err)
+    moved = np.abs(sg.flatten(got) - sg.flatten(start))
+    assert np.median(moved[20:5274]) > 0.5 * lr  # Adam moves most weights by ~lr per step
+    for name in ("in_shift", "in_scale", "out_scale", "out_shift"):
+        assert np.array_equal(got[name], start[name])
+    net.close()
+
+
 def test_network_training_reduces_loss():
     sgs = _sgs()
     rng = np.random.default_rng(8)
