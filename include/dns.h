@@ -90,15 +90,21 @@ int dns_set_stream(dns_handle* h, void* stream);
 /* Options:
  *   "dealias_variant"  0: keep |k_i| < N/3 (Sec. 3.1 text, default)
  *                      1: keep |k_i| < 2/3 (N/2+1) (the Appendix script)
- *   "integrator"       explicit Runge-Kutta scheme of dns_step, each in the
+ *   "integrator"       explicit Runge-Kutta scheme of dns_step; 0 - 3 in the
  *                      two-register form of the Appendix driver (stage s + 1
  *                      starts from u0 + b_s dt dU_s, the new state is
- *                      u0 + sum_s a_s dt dU_s):
+ *                      u0 + sum_s a_s dt dU_s), 4 - 5 in Williamson's 2N
+ *                      low-storage form (see dns_set_rk_tableau):
  *                      0: classical RK4, a = 1/6,1/3,1/3,1/6, b = 1/2,1/2,1
  *                         (Appendix, default)
  *                      1: forward Euler, a = 1 (the integrator loop of Sec. 3.1)
  *                      2: Heun, a = 1/2,1/2, b = 1
  *                      3: midpoint, a = 0,1, b = 1/2
+ *                      4: Williamson's 3-stage 3rd-order 2N scheme
+ *                         (A = 0, -5/9, -153/128; B = 1/3, 15/16, 8/15)
+ *                      5: Carpenter & Kennedy's 5-stage 4th-order 2N scheme
+ *                      dns_get_option reports -1 after dns_set_rk_tableau set a
+ *                      scheme that is none of these
  *   "Lx", "Ly", "Lz"   box lengths (default 2 pi each): the mesh spacing along x is
  *                      Lx / N and the wavenumber of index l is 2 pi l / Lx (Sec. 2
  *                      footnote, Sec. 3.1: other box sizes by scaling). The 2/3
@@ -139,6 +145,20 @@ int dns_set_option(dns_handle* h, const char* key, double value);
 /* The current value of an option of dns_set_option ("time" included) in *value.
  * Errors: DNS_ERR_ARG for an unknown key or a NULL pointer. */
 int dns_get_option(const dns_handle* h, const char* key, double* value);
+
+/* A user-supplied explicit Runge-Kutta scheme for dns_step (Sec. 3.1: "more
+ * advanced integrators may be easily added"), in one of two two-register forms:
+ *   form 0 (the Appendix driver's): stages >= 1 weights a[0..stages-1] and
+ *     offsets b[0..stages-2]; stage s evaluates dU_s = RHS(stage state), stage
+ *     s + 1 starts from u0 + b_s dt dU_s, the new state is u0 + sum a_s dt dU_s
+ *     (Butcher tableaux whose only non-zero entries are A[s+1][s] = b_s);
+ *   form 1 (Williamson's 2N low-storage form): A = a[0..stages-1], B =
+ *     b[0..stages-1]; stage s does dU <- A_s dU + dt RHS(u), u <- u + B_s dU
+ *     (a[0] multiplies a zero register and is ignored).
+ * 1 <= stages <= 8; coefficients must be finite. The arrays are copied. Each
+ * stage costs the same four passes; the step reads and writes the same state
+ * arrays as the built-in schemes. Errors: DNS_ERR_ARG. */
+int dns_set_rk_tableau(dns_handle* h, int form, int stages, const double* a, const double* b);
 
 /* Schedule tuner for the small grids: times dns_step with every tile width the
  * grid offers for the y-inverse, the y-forward and the z-pass (default included),

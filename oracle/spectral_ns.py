@@ -53,6 +53,22 @@ RK_SCHEMES = {
 }
 
 
+# Low-storage explicit Runge-Kutta schemes in Williamson's 2N form (Williamson 1980,
+# J. Comput. Phys. 35): two registers u and dU; stage j does dU <- A_j dU + dt RHS(u),
+# then u <- u + B_j dU, with A_1 = 0. The Sec. 3.1 remark that more advanced
+# integrators may be added is read as this family (the paper names none).
+# "williamson3": Williamson's three-stage third-order scheme; "ck45": the five-stage
+# fourth-order scheme of Carpenter & Kennedy (1994, NASA TM-109112).
+LSRK_SCHEMES = {
+    "williamson3": ((0.0, -5.0 / 9.0, -153.0 / 128.0), (1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0)),
+    "ck45": ((0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+              -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0),
+             (1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+              1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+              2277821191437.0 / 14882151754819.0)),
+}
+
+
 def set_workers(n: int) -> None:
     """Thread count for the library FFT (the CPU baseline reports it)."""
     global WORKERS
@@ -242,11 +258,22 @@ def rk_step(uh: np.ndarray, g: Grid, nu: float, dt: float, scheme: str = "rk4") 
     return u1
 
 
+def lsrk_step(uh: np.ndarray, g: Grid, nu: float, dt: float, A, B) -> np.ndarray:
+    """One step of a low-storage scheme in Williamson's 2N form: for each stage j,
+    dU <- A_j dU + dt RHS(u); u <- u + B_j dU (A_1 multiplies a zero register)."""
+    u = uh.copy()
+    dU = np.zeros_like(uh)
+    for Aj, Bj in zip(A, B):
+        dU = Aj * dU + dt * rhs(u, g, nu)
+        u = u + Bj * dU
+    return u
+
+
 def run(uh: np.ndarray, N: int, nu: float, dt: float, nsteps: int, variant: int = 0,
         paper_reuse_u: bool = False, u0_phys: np.ndarray | None = None, scheme: str = "rk4",
         lengths=None) -> np.ndarray:
     """Advance ``nsteps`` steps (the step count is round(T/dt), reading of the while loop)
-    of the Appendix's RK4, or of another scheme of RK_SCHEMES.
+    of the Appendix's RK4, or of another scheme of RK_SCHEMES or LSRK_SCHEMES.
 
     paper_reuse_u=True mimics the Appendix: the physical U used at stage 0 is
     the one computed at the end of the previous step (the initial physical
@@ -254,6 +281,13 @@ def run(uh: np.ndarray, N: int, nu: float, dt: float, nsteps: int, variant: int 
     box lengths (Lx, Ly, Lz), default 2 pi each.
     """
     g = Grid(N, variant, lengths)
+    if scheme in LSRK_SCHEMES:
+        if paper_reuse_u:
+            raise ValueError("paper_reuse_u applies to the Appendix RK4 driver only")
+        A, B = LSRK_SCHEMES[scheme]
+        for _ in range(nsteps):
+            uh = lsrk_step(uh, g, nu, dt, A, B)
+        return uh
     if scheme != "rk4":
         if paper_reuse_u:
             raise ValueError("paper_reuse_u applies to the Appendix RK4 driver only")

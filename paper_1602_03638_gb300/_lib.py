@@ -48,6 +48,7 @@ SIGNATURES = {
     "dns_set_option": (_I, [_P, ctypes.c_char_p, _D]),
     "dns_get_option": (_I, [_P, ctypes.c_char_p, ctypes.POINTER(_D)]),
     "dns_tune_tiles": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "dns_set_rk_tableau": (_I, [_P, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "dns_set_state": (_I, [_P, _P, _I]),
     "dns_set_state_spectral": (_I, [_P, _P, _I]),
     "dns_step": (_I, [_P, _I]),

@@ -130,24 +130,45 @@ int cuda_fail(cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail(e_, where); \
   } while (0)
 
-// Explicit Runge-Kutta schemes in the two-register form of the Appendix driver:
-// stage s evaluates dU_s on its stage state, stage s + 1 starts from
-// u0 + b_s dt dU_s, and the new state is u0 + sum_s a_s dt dU_s. Index 0 is the
-// classical RK4 of the Appendix (the default), 1 forward Euler (the integrator
-// loop of Sec. 3.1), 2 and 3 the two-stage Heun and midpoint rules.
+// Explicit Runge-Kutta schemes, each in one of two two-register forms.
+// Form 0, the Appendix driver's: stage s evaluates dU_s on its stage state, stage
+// s + 1 starts from u0 + b_s dt dU_s, and the new state is u0 + sum_s a_s dt dU_s.
+// Form 1, Williamson's 2N low-storage form: stage s does dU <- a_s dU + dt RHS(u),
+// u <- u + b_s dU (a_0 multiplies a zero register and is ignored).
+// Index 0 is the classical RK4 of the Appendix (the default), 1 forward Euler (the
+// integrator loop of Sec. 3.1), 2 and 3 the two-stage Heun and midpoint rules, 4
+// Williamson's three-stage third-order 2N scheme, 5 the five-stage fourth-order 2N
+// scheme of Carpenter & Kennedy (1994). Sec. 3.1 notes that other integrators may
+// be added; dns_set_rk_tableau takes any scheme of either form.
 const double kTwoPi = 6.283185307179586476925286766559;
 
+constexpr int RK_MAX_STAGES = 8;
 struct RkScheme {
-  int stages;
-  double a[4];
-  double b[3];
+  int form;    // 0: Appendix two-register form, 1: Williamson 2N form
+  int stages;  // 1 .. RK_MAX_STAGES
+  double a[RK_MAX_STAGES];
+  double b[RK_MAX_STAGES];
 };
-const RkScheme RK_SCHEMES[4] = {
-    {4, {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0}, {0.5, 0.5, 1.0}},
-    {1, {1.0, 0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}},
-    {2, {0.5, 0.5, 0.0, 0.0}, {1.0, 0.0, 0.0}},
-    {2, {0.0, 1.0, 0.0, 0.0}, {0.5, 0.0, 0.0}},
+const RkScheme RK_SCHEMES[6] = {
+    {0, 4, {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0}, {0.5, 0.5, 1.0}},
+    {0, 1, {1.0}, {0.0}},
+    {0, 2, {0.5, 0.5}, {1.0}},
+    {0, 2, {0.0, 1.0}, {0.5}},
+    {1, 3, {0.0, -5.0 / 9.0, -153.0 / 128.0}, {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0}},
+    {1, 5,
+     {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+      -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0},
+     {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0, 1720146321549.0 / 2090206949498.0,
+      3134564353537.0 / 4481467310338.0, 2277821191437.0 / 14882151754819.0}},
 };
+constexpr int RK_BUILTIN = 6;
+
+bool same_scheme(const RkScheme& x, const RkScheme& y) {
+  if (x.form != y.form || x.stages != y.stages) return false;
+  for (int i = 0; i < x.stages; ++i)
+    if (x.a[i] != y.a[i] || x.b[i] != y.b[i]) return false;
+  return true;
+}
 
 // exp(-2 pi i t / N) in FP64 with exact quadrant/octant symmetry.
 void twiddle(long t, long N, double* re, double* im) {
@@ -187,7 +208,8 @@ struct dns_handle {
   int N = 0;
   int dtype = 0;
   int variant = 0;
-  int integrator = 0;  // index into RK_SCHEMES
+  int integrator = 0;  // index into RK_SCHEMES, -1 for a scheme set by dns_set_rk_tableau
+  RkScheme rk = RK_SCHEMES[0];
   double L[3] = {kTwoPi, kTwoPi, kTwoPi};  // box lengths along x, y, z
   int ytile[2] = {0, 0};  // y-pass tile widths of the stage (inverse, forward); 0 = default
   int ztile = 0;          // z-pass tile width of the stage; 0 = default
@@ -270,7 +292,7 @@ PassArgs base_args(const dns_handle* h) {
   return a;
 }
 
-int rk_stages(const dns_handle* h) { return RK_SCHEMES[h->integrator].stages; }
+int rk_stages(const dns_handle* h) { return h->rk.stages; }
 
 bool use_fused(const dns_handle* h) { return h->fused && h->ops->rk_stage_fused && h->ctl; }
 
@@ -295,11 +317,20 @@ int check_plane_error(dns_handle* h, const char* where) {
 
 // stage s of the handle's scheme: its coefficients times dt and the index of the last stage
 void set_stage(const dns_handle* h, int s, PassArgs& a) {
-  const RkScheme& r = RK_SCHEMES[h->integrator];
+  const RkScheme& r = h->rk;
   a.stage = s;
   a.last = r.stages - 1;
-  a.cA = r.a[s] * h->dt;
-  a.cB = s < r.stages - 1 ? r.b[s] * h->dt : 0.0;
+  if (r.form == 1) {  // 2N: the coefficients as given, dt separately
+    a.lsrk = 1;
+    a.cA = s > 0 ? r.a[s] : 0.0;
+    a.cB = r.b[s];
+    a.cC = h->dt;
+  } else {
+    a.lsrk = 0;
+    a.cA = r.a[s] * h->dt;
+    a.cB = s < r.stages - 1 ? r.b[s] * h->dt : 0.0;
+    a.cC = 0.0;
+  }
 }
 
 cudaError_t enqueue_step(dns_handle* h, cudaStream_t st) {
@@ -454,9 +485,12 @@ int dns_set_option(dns_handle* h, const char* key, double value) {
     if (value != 0.0 && value != 1.0) return fail(DNS_ERR_ARG, "dealias_variant must be 0 or 1");
     h->variant = (int)value;
   } else if (!strcmp(key, "integrator")) {
-    if (value != 0.0 && value != 1.0 && value != 2.0 && value != 3.0)
-      return fail(DNS_ERR_ARG, "integrator must be 0 (RK4), 1 (Euler), 2 (Heun) or 3 (midpoint)");
+    if (!(value >= 0.0 && value < RK_BUILTIN) || value != std::floor(value))
+      return fail(DNS_ERR_ARG,
+                  "integrator must be 0 (RK4), 1 (Euler), 2 (Heun), 3 (midpoint), 4 (Williamson 2N RK3) "
+                  "or 5 (Carpenter-Kennedy 2N RK4)");
     h->integrator = (int)value;
+    h->rk = RK_SCHEMES[h->integrator];
   } else if (!strcmp(key, "Lx") || !strcmp(key, "Ly") || !strcmp(key, "Lz")) {
     if (!(value > 0.0) || !std::isfinite(value)) return fail(DNS_ERR_ARG, "%s must be finite and > 0", key);
     h->L[key[1] - 'x'] = value;
@@ -522,6 +556,35 @@ int dns_get_option(const dns_handle* h, const char* key, double* value) {
   else if (!strcmp(key, "dt")) *value = h->dt;
   else if (!strcmp(key, "time")) *value = h->t;
   else return fail(DNS_ERR_ARG, "dns_get_option: unknown key '%s'", key);
+  return DNS_OK;
+}
+
+int dns_set_rk_tableau(dns_handle* h, int form, int stages, const double* a, const double* b) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (form != 0 && form != 1) return fail(DNS_ERR_ARG, "dns_set_rk_tableau: form must be 0 or 1");
+  if (stages < 1 || stages > RK_MAX_STAGES)
+    return fail(DNS_ERR_ARG, "dns_set_rk_tableau: stages must be in 1 .. %d", RK_MAX_STAGES);
+  const int nb = form == 0 ? stages - 1 : stages;
+  if (!a || (nb > 0 && !b)) return fail(DNS_ERR_ARG, "dns_set_rk_tableau: coefficient array is NULL");
+  RkScheme r{};
+  r.form = form;
+  r.stages = stages;
+  for (int i = 0; i < stages; ++i) {
+    r.a[i] = (form == 1 && i == 0) ? 0.0 : a[i];
+    if (!std::isfinite(a[i])) return fail(DNS_ERR_ARG, "dns_set_rk_tableau: a[%d] is not finite", i);
+  }
+  for (int i = 0; i < nb; ++i) {
+    if (!std::isfinite(b[i])) return fail(DNS_ERR_ARG, "dns_set_rk_tableau: b[%d] is not finite", i);
+    r.b[i] = b[i];
+  }
+  h->rk = r;
+  h->integrator = -1;
+  for (int k = 0; k < RK_BUILTIN; ++k)
+    if (same_scheme(r, RK_SCHEMES[k])) h->integrator = k;
+  h->graph_dirty = true;
+  ++h->epoch;
+  h->w_valid = false;
   return DNS_OK;
 }
 
@@ -977,7 +1040,7 @@ std::vector<EnsUnit> ens_units(const dns_ensemble* e) {
       std::vector<int> group;
       for (int j = i; j < n; ++j) {
         const dns_handle* g = e->m[j];
-        if (!done[j] && g->ops == h->ops && g->variant == h->variant && g->integrator == h->integrator) {
+        if (!done[j] && g->ops == h->ops && g->variant == h->variant && same_scheme(g->rk, h->rk)) {
           group.push_back(j);
           done[j] = true;
         }

@@ -23,13 +23,17 @@ struct PassArgs {
   double nu = 0.0;
   double cA = 0.0;  // a_s * dt
   double cB = 0.0;  // b_s * dt
+  // low-storage 2N stage (Williamson): dU <- cA dU + cC RHS; u <- u + cB dU, with
+  // cA = A_s, cB = B_s, cC = dt; U holds u and U1 holds dU
+  int lsrk = 0;
+  double cC = 0.0;
   int stage = 0;    // stage of the step, 0..last
   int last = 3;     // the step's final stage (it writes the new state); 3 for RK4
   int kmax3 = 0;    // a mode is kept by the 2/3 rule iff 3|k_i| < kmax3
   double ks[3] = {1.0, 1.0, 1.0};  // 2 pi / L along x, y, z: the wavenumber of index 1
   // FP32 copies of nu, cA, cB and ks for the FP32 kernels (filled when a kernel is
   // launched), so that they need no double-to-float conversion per thread
-  float f_nu = 0.f, f_cA = 0.f, f_cB = 0.f;
+  float f_nu = 0.f, f_cA = 0.f, f_cB = 0.f, f_cC = 0.f;
   float f_ks[3] = {1.f, 1.f, 1.f};
   int ytile[2] = {0, 0};  // y-pass tile widths of the stage launches (inverse, forward); 0 = default
   int ztile = 0;          // z-pass tile width of the stage launches; 0 = default

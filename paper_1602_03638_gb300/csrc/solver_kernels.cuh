@@ -96,6 +96,7 @@ inline PassArgs f32args(PassArgs a) {
   a.f_nu = (float)a.nu;
   a.f_cA = (float)a.cA;
   a.f_cB = (float)a.cB;
+  a.f_cC = (float)a.cC;
   for (int i = 0; i < 3; ++i) a.f_ks[i] = (float)a.ks[i];
   return a;
 }
@@ -195,10 +196,13 @@ __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
     const bool row_kept = (3 * kz < a.kmax3) && kept(kfreq(ky, N), a.kmax3);
     const T nu = par<T>(a.nu, a.f_nu), cA = par<T>(a.cA, a.f_cA), cB = par<T>(a.cB, a.f_cB);
     const int stage = a.stage, last = a.last;
-    const cx<T>* Sst = (stage == 0) ? U : US;
+    // Williamson 2N stages keep the stage state in U (updated in place) and dU in U1
+    const bool lsrk = MODE == XM_STAGE && a.lsrk;
+    const cx<T>* Sst = (stage == 0 || lsrk) ? U : US;
     // state rows read by the update: stage state (all stages), accumulator
-    // (stages after the first), step-start state (the stages between first and last)
-    const bool need1 = MODE == XM_STAGE && stage > 0, need0 = MODE == XM_STAGE && stage > 0 && stage < last;
+    // (stages after the first), step-start state (the stages between first and
+    // last of the two-register form)
+    const bool need1 = MODE == XM_STAGE && stage > 0, need0 = MODE == XM_STAGE && stage > 0 && stage < last && !lsrk;
     cx<T>* const st = s + G::XST;  // XPRE: rows [Sst 0..2][U1 0..2][U 0..2], N values each
     if constexpr (G::XPRE) {
       if (row_kept) {
@@ -276,7 +280,26 @@ __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
           out[2 * FS + gi] = d2;
         } else {
           cx<T> v0, v1, v2;
-          if (stage == 0 && last == 0) {  // one-stage step (forward Euler): u += a_0 dt dU
+          if (lsrk) {  // 2N stage: dU <- A_s dU + dt RHS, u <- u + B_s dU
+            const T cC = par<T>(a.cC, a.f_cC);
+            cx<T> e0 = scal(d0, cC), e1 = scal(d1, cC), e2 = scal(d2, cC);
+            if (stage > 0) {
+              e0 = e0 + scal(ld_1(0, j), cA);
+              e1 = e1 + scal(ld_1(1, j), cA);
+              e2 = e2 + scal(ld_1(2, j), cA);
+            }
+            if (stage < last) {
+              st_state<HINT>(U1 + gi, e0, pol);
+              st_state<HINT>(U1 + FS + gi, e1, pol);
+              st_state<HINT>(U1 + 2 * FS + gi, e2, pol);
+            }
+            v0 = u0 + scal(e0, cB);
+            v1 = u1 + scal(e1, cB);
+            v2 = u2 + scal(e2, cB);
+            st_state<HINT>(U + gi, v0, pol);
+            st_state<HINT>(U + FS + gi, v1, pol);
+            st_state<HINT>(U + 2 * FS + gi, v2, pol);
+          } else if (stage == 0 && last == 0) {  // one-stage step (forward Euler): u += a_0 dt dU
             v0 = u0 + scal(d0, cA);
             v1 = u1 + scal(d1, cA);
             v2 = u2 + scal(d2, cA);

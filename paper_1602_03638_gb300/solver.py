@@ -43,7 +43,7 @@ def _ptr(arr, shape, real_dtype_bytes, complex_):
 
 
 # explicit Runge-Kutta schemes of dns_step ("integrator" option of the C ABI)
-INTEGRATORS = {"rk4": 0, "euler": 1, "heun": 2, "midpoint": 3}
+INTEGRATORS = {"rk4": 0, "euler": 1, "heun": 2, "midpoint": 3, "williamson3": 4, "ck45": 5}
 
 
 class Solver:
@@ -128,6 +128,13 @@ class Solver:
         v = ctypes.c_double()
         _lib.check(_lib.lib().dns_get_option(self._h, key.encode(), ctypes.byref(v)), "dns_get_option")
         return v.value
+
+    def set_rk_tableau(self, form: int, a, b=()):
+        """A user-supplied explicit RK scheme (dns_set_rk_tableau): form 0 = the Appendix
+        two-register form (weights a, offsets b), form 1 = Williamson's 2N form (A = a, B = b)."""
+        av = (ctypes.c_double * max(1, len(a)))(*[float(x) for x in a])
+        bv = (ctypes.c_double * max(1, len(b)))(*[float(x) for x in b])
+        _lib.check(_lib.lib().dns_set_rk_tableau(self._h, int(form), len(a), av, bv), "dns_set_rk_tableau")
 
     def tune_tiles(self, steps: int = 5) -> tuple:
         """Time dns_step with each y- and z-pass tile width the grid offers; keep the

@@ -58,6 +58,8 @@ def test_argument_validation_without_device(L):
     assert L.dns_step(None, 1) == _lib.DNS_ERR_ARG
     assert L.dns_diagnostics(None, None) == _lib.DNS_ERR_ARG
     assert L.dns_set_option(None, b"nu", 0.1) == _lib.DNS_ERR_ARG
+    coef = (ctypes.c_double * 3)(0.0, 1.0, 2.0)
+    assert L.dns_set_rk_tableau(None, 1, 3, coef, coef) == _lib.DNS_ERR_ARG
     assert L.dns_destroy(None) == _lib.DNS_OK
     assert L.dns_device_bytes(None) == 0
     assert L.dns_debug_fail_alloc_after(-1) == _lib.DNS_ERR_ARG

@@ -65,12 +65,12 @@ def _oracle_256(variant, integrator, nu, dt):
     key = (variant, integrator)
     if key not in _ORACLE:
         uh = inputs.isotropic_spectral(256, seed=7, k0=12.0).numpy()
-        _ORACLE[key] = (uh, sn.rk_step(uh, sn.Grid(256, variant), nu, dt, integrator))
+        _ORACLE[key] = (uh, sn.run(uh, 256, nu, dt, 1, variant=variant, scheme=integrator))
     return _ORACLE[key]
 
 
 @pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 1e-5)])
-@pytest.mark.parametrize("variant,integrator", [(0, "rk4"), (1, "rk4"), (0, "euler"), (0, "heun")])
+@pytest.mark.parametrize("variant,integrator", [(0, "rk4"), (1, "rk4"), (0, "euler"), (0, "heun"), (0, "williamson3")])
 def test_plane_pass_matches_oracle_at_256(dtype, tol, variant, integrator):
     N, nu, dt = 256, 0.004, 2e-3
     uh, ref = _oracle_256(variant, integrator, nu, dt)

@@ -1,5 +1,6 @@
 """Pins of the oracle's explicit Runge-Kutta schemes other than the Appendix RK4
-(forward Euler of Sec. 3.1; the two-stage Heun and midpoint rules).
+(forward Euler of Sec. 3.1; the two-stage Heun and midpoint rules; the low-storage
+2N schemes of Williamson (3 stages, order 3) and Carpenter & Kennedy (5 stages, order 4)).
 
 * Linear decay: the ABC (Beltrami) flow has u x omega = 0, so each step multiplies
   u_hat by the scheme's stability polynomial R(z), z = -nu |k|^2 dt, exactly:
@@ -79,3 +80,71 @@ def test_energy_of_abc_under_euler_matches_closed_form():
     E0 = 1.5  # A = B = C = 1
     assert abs(sn.energy(uh) / E0 - (1.0 - nu * dt) ** (2 * n)) < 1e-12
     assert abs(sn.energy(uh) / E0 - math.exp(-2 * nu * n * dt)) > 1e-7  # Euler is not exact
+
+
+# ---------------------------------------------------------------- low-storage (2N) schemes
+
+def _butcher_from_2n(A, B):
+    """Butcher matrix and weights of a 2N scheme, from the recurrence written out by hand:
+    u_j = u_0 + dt sum_i k_i sum_{l=i..j} B_l prod_{m=i+1..l} A_m, stage j + 1 starts from u_j."""
+    s = len(A)
+
+    def coef(i, j):
+        return sum(B[l] * math.prod(A[m] for m in range(i + 1, l + 1)) for l in range(i, j + 1))
+
+    a = np.zeros((s, s))
+    for j in range(1, s):
+        for i in range(j):
+            a[j, i] = coef(i, j - 1)
+    return a, np.array([coef(i, s - 1) for i in range(s)])
+
+
+def _stability(A, B, z):
+    a, b = _butcher_from_2n(A, B)
+    s = len(b)
+    return 1.0 + z * b @ np.linalg.solve(np.eye(s) - z * a, np.ones(s))
+
+
+@pytest.mark.parametrize("scheme,order", [("williamson3", 3), ("ck45", 4)])
+def test_2n_coefficients_satisfy_the_order_conditions(scheme, order):
+    a, b = _butcher_from_2n(*sn.LSRK_SCHEMES[scheme])
+    c = a.sum(1)
+    conds = [b.sum() - 1, b @ c - 1 / 2, b @ c ** 2 - 1 / 3, b @ a @ c - 1 / 6]
+    if order >= 4:
+        conds += [b @ c ** 3 - 1 / 4, b @ (c * (a @ c)) - 1 / 8, b @ a @ c ** 2 - 1 / 12, b @ a @ a @ c - 1 / 24]
+    assert max(abs(x) for x in conds) < 1e-14
+    if order == 3:  # third order only: an order-four condition fails
+        assert abs(b @ c ** 3 - 1 / 4) > 1e-3
+
+
+@pytest.mark.parametrize("scheme", ["williamson3", "ck45"])
+def test_abc_decays_by_the_2n_stability_polynomial(scheme):
+    N, nu, dt, n = 16, 0.2, 0.1, 7
+    uh0 = sn.to_spectral(inputs.abc_flow(N))
+    uh = sn.run(uh0, N, nu, dt, n, scheme=scheme)
+    A, B = sn.LSRK_SCHEMES[scheme]
+    z = -nu * dt
+    expect = uh0 * _stability(A, B, z) ** n
+    assert np.abs(uh - expect).max() < 1e-13 * np.abs(uh0).max()
+    # the polynomial agrees with exp(z) to the scheme's order: 1 + z + z^2/2 + z^3/6 (+ z^4/24)
+    taylor = sum(z ** k / math.factorial(k) for k in range(4 if scheme == "williamson3" else 5))
+    assert abs(_stability(A, B, z) - taylor) < 1e-5
+
+
+@pytest.mark.parametrize("scheme,order", [("williamson3", 3), ("ck45", 4)])
+def test_2n_order_on_the_nonlinear_system(scheme, order):
+    e1, e2 = _error(scheme, 0.1), _error(scheme, 0.05)
+    ratio = e1 / e2
+    assert 0.75 * 2 ** order < ratio < 1.4 * 2 ** order, ratio
+
+
+def test_planted_2n_mistake_is_caught(monkeypatch):
+    # dropping the A_j dU term (dU = dt RHS) turns the scheme into stages of forward Euler
+    bad = dict(sn.LSRK_SCHEMES)
+    A, B = bad["williamson3"]
+    bad["williamson3"] = ((0.0, 0.0, 0.0), B)
+    monkeypatch.setattr(sn, "LSRK_SCHEMES", bad)
+    N, nu, dt, n = 16, 0.2, 0.1, 7
+    uh0 = sn.to_spectral(inputs.abc_flow(N))
+    uh = sn.run(uh0, N, nu, dt, n, scheme="williamson3")
+    assert np.abs(uh - uh0 * _stability(A, B, -nu * dt) ** n).max() > 1e-4 * np.abs(uh0).max()
