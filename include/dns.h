@@ -162,14 +162,23 @@ int dns_set_rk_tableau(dns_handle* h, int form, int stages, const double* a, con
 
 /* Schedule tuner for the small grids: times dns_step with every tile width the
  * grid offers for the y-inverse, the y-forward and the z-pass (default included),
- * one pass at a time with the best widths found before it, `steps` graph replays
- * each after a capture and a warm-up step; keeps the fastest widths (written to
- * *y_inverse, *y_forward, *z; 0 = default). Every candidate starts from the same
+ * one pass at a time with the best widths found before it, three timings of
+ * `steps` graph replays each after a capture and a warm-up step; a width replaces
+ * the one kept so far (starting from the default) only if its median time beats
+ * that one's median by more than that one's spread (max - min); the kept widths
+ * are written to *y_inverse, *y_forward, *z (0 = default). Every candidate starts from the same
  * state, and the state and time are restored at the end; the results of later
  * steps do not depend on the choice. Allocates and frees one state copy (3
  * fields). Synchronises. Errors: DNS_ERR_ARG (steps < 1, NULL outputs),
  * DNS_ERR_OOM, DNS_ERR_CUDA. */
 int dns_tune_tiles(dns_handle* h, int steps, int* y_inverse, int* y_forward, int* z);
+
+/* The tile widths a grid offers the tuner besides the default: which = 0 the
+ * y-passes ("y_tile_inverse", "y_tile_forward"), 1 the z-pass ("z_tile"), for
+ * the compiled grid (N, dtype). Writes up to `max` widths to `widths` and returns
+ * their count (0: the grid offers the defaults only), or DNS_ERR_ARG. Needs no
+ * device. The paper has no counterpart. */
+int dns_tile_widths(int N, int dtype, int which, int* widths, int max);
 
 /* State from a physical velocity field u (3,N,N,N): u_hat = F(u) with the
  * Nyquist modes zeroed (Eq. iffteq forward transform; no projection).
@@ -350,12 +359,35 @@ int dns_mlp_destroy(dns_mlp* net);
 int dns_mlp_set_params(dns_mlp* net, const float* host_params, int count); /* resets Adam */
 int dns_mlp_get_params(dns_mlp* net, float* host_params, int count);
 int dns_mlp_forward(dns_mlp* net, const float* X, float* tau, int P, void* stream);
+/* Sets the normalisation entries from data: in_shift = mean and in_scale = 1 /
+ * std of each feature row of X (scale 1 where std <= 1e-12), out_shift = mean
+ * and out_scale = std of each stress row of T (1 where std <= 1e-30); std is the
+ * unbiased (P - 1) standard deviation, both sums in FP64 in a device kernel.
+ * X (10 x P) and T (6 x P) device arrays, P >= 2; asynchronous on `stream`. */
+int dns_mlp_set_normalisation(dns_mlp* net, const float* X, const float* T, int P, void* stream);
 /* loss and the gradient of every parameter (zeros for the normalisation entries), synchronous */
 int dns_mlp_loss_grad(dns_mlp* net, const float* X, const float* T, int P, float* grad_host, float* loss_host,
                       void* stream);
 /* one Adam step on the full batch; loss_host (may be NULL) receives the loss before the update */
 int dns_mlp_train_step(dns_mlp* net, const float* X, const float* T, int P, double lr, float* loss_host,
                        void* stream);
+
+/* Attaches the network as a subgrid-stress closure of the handle's run (no
+ * counterpart in the paper: the learned closure of the coarse-grid runs). From
+ * the next step on, every dns_step (and dns_rhs) first evaluates, on the
+ * handle's stream and inside its captured graph, with no host synchronisation:
+ * the resolved velocity gradients A_ij = F^{-1}(i k_j u_hat_i) (9 inverse
+ * transforms) and the filter width `delta` as the 10 features of every grid
+ * point, the network's stress tau (6 components), its forward transforms, and
+ * the force f_i = -i k_j tau_hat_ij, which is added to the nonlinear term before
+ * the 2/3 mask and the projection in every stage of the step (held over the
+ * step, as the force of dns_set_forcing). `net` is borrowed: keep it alive and
+ * attached only while the handle steps (parameter changes by training between
+ * steps are seen by the next step); net = NULL detaches. FP32 handles on the
+ * 2 pi box only (DNS_ERR_UNSUPPORTED otherwise); not together with
+ * dns_set_forcing (DNS_ERR_ARG). Allocates its scratch (10 + 6 floats per grid
+ * point and 12 spectral fields) on the first attach. */
+int dns_set_closure(dns_handle* h, dns_mlp* net, double delta);
 
 /* Test hook for allocation-failure handling: the n-th device allocation made
  * by the library from now on (n >= 1) reports DNS_ERR_OOM without touching

@@ -49,6 +49,7 @@ SIGNATURES = {
     "dns_get_option": (_I, [_P, ctypes.c_char_p, ctypes.POINTER(_D)]),
     "dns_tune_tiles": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "dns_set_rk_tableau": (_I, [_P, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "dns_tile_widths": (_I, [_I, _I, _I, ctypes.POINTER(_I), _I]),
     "dns_set_state": (_I, [_P, _P, _I]),
     "dns_set_state_spectral": (_I, [_P, _P, _I]),
     "dns_step": (_I, [_P, _I]),
@@ -85,6 +86,8 @@ SIGNATURES = {
     "dns_mlp_set_params": (_I, [_P, ctypes.POINTER(ctypes.c_float), _I]),
     "dns_mlp_get_params": (_I, [_P, ctypes.POINTER(ctypes.c_float), _I]),
     "dns_mlp_forward": (_I, [_P, _P, _P, _I, _P]),
+    "dns_mlp_set_normalisation": (_I, [_P, _P, _P, _I, _P]),
+    "dns_set_closure": (_I, [_P, _P, _D]),
     "dns_mlp_loss_grad": (_I, [_P, _P, _P, _I, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), _P]),
     "dns_mlp_train_step": (_I, [_P, _P, _P, _I, _D, ctypes.POINTER(ctypes.c_float), _P]),
     "dns_ensemble_step": (_I, [_P, _I]),

@@ -227,6 +227,16 @@ struct dns_handle {
   void* D = nullptr;
   void* F = nullptr;  // optional force, internal layout
   bool has_force = false;
+  // learned closure evaluated at the start of every step (dns_set_closure): the network
+  // (borrowed), the filter width, and scratch: features (10 x N^3 floats), stress
+  // (6 x N^3 floats), 6 spectral fields, 3 spectral work fields, the force (3 fields)
+  dns_mlp* closure = nullptr;
+  double closure_delta = 0.0;
+  void* CX = nullptr;
+  void* CT = nullptr;
+  void* CS = nullptr;
+  void* CW = nullptr;
+  void* FC = nullptr;
   void* tw = nullptr;
   double* diag = nullptr;
   int* ctl = nullptr;  // plane-pass control block (ops->plane_ctl_words ints)
@@ -263,7 +273,7 @@ int dev_alloc(dns_handle* h, void** p, size_t bytes, const char* what) {
 void release(dns_handle* h) {
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->graph) cudaGraphDestroy(h->graph);
-  void* bufs[] = {h->U, h->U1, h->US, h->W, h->D, h->F, h->tw, h->diag, h->ctl};
+  void* bufs[] = {h->U, h->U1, h->US, h->W, h->D, h->F, h->tw, h->diag, h->ctl, h->CX, h->CT, h->CS, h->CW, h->FC};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -278,7 +288,7 @@ PassArgs base_args(const dns_handle* h) {
   a.W = h->W;
   a.D = h->D;
   a.tw = h->tw;
-  a.F = h->has_force ? h->F : nullptr;
+  a.F = h->has_force ? h->F : (h->closure ? h->FC : nullptr);
   a.nu = h->nu;
   a.kmax3 = h->N + 2 * h->variant;
   for (int i = 0; i < 3; ++i) a.ks[i] = kTwoPi / h->L[i];  // exactly 1 on the 2 pi box
@@ -333,7 +343,39 @@ void set_stage(const dns_handle* h, int s, PassArgs& a) {
   }
 }
 
+// The closure force of the current state into FC (dns_set_closure): velocity
+// gradients i k_j u_hat_i -> 9 inverse transforms -> features; the network -> the 6
+// stress components -> 2 x 3 forward transforms -> f_i = -i k_j tau_hat_ij. FP32
+// handles on the 2 pi box; everything on the stream, no host synchronisation.
+cudaError_t closure_eval(dns_handle* h, cudaStream_t st) {
+  const int N = h->N;
+  const size_t P = (size_t)N * N * N, cb = h->ops->elem_bytes;
+  PassArgs a = base_args(h);
+  cudaError_t e = cudaSuccess;
+  for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
+    e = closure_gradient(h->U, N, c, h->CS, h->dtype, st);
+    PassArgs g = a;
+    g.U = h->CS;
+    g.W = h->CW;
+    g.out = (float*)h->CX + 3 * c * P;
+    if (e == cudaSuccess) e = h->ops->inverse3d(g, st);
+  }
+  if (e == cudaSuccess) e = mlp_forward_async(h->closure, (const float*)h->CX, (float*)h->CT, (int)P, st);
+  for (int r = 0; r < 6 && e == cudaSuccess; r += 3) {
+    PassArgs f = a;
+    f.in = (const float*)h->CT + r * P;
+    f.U = (char*)h->CS + r * h->fs * cb;
+    e = h->ops->forward3d(f, st);
+  }
+  if (e == cudaSuccess) e = closure_force(h->CS, N, h->FC, h->dtype, st);
+  return e;
+}
+
 cudaError_t enqueue_step(dns_handle* h, cudaStream_t st) {
+  if (h->closure) {
+    cudaError_t e = closure_eval(h, st);
+    if (e != cudaSuccess) return e;
+  }
   PassArgs a = base_args(h);
   const bool fused = use_fused(h);
   for (int s = 0; s < rk_stages(h); ++s) {
@@ -613,8 +655,9 @@ int dns_tune_tiles(dns_handle* h, int steps, int* y_inverse, int* y_forward, int
   if (err == cudaSuccess) err = cudaEventCreate(&e1);
   if (err != cudaSuccess) rc = cuda_fail(err, "dns_tune_tiles set-up");
   // each candidate starts from the saved state: capture and one warm-up step, then
-  // `steps` timed steps exactly as dns_step runs them
-  auto timed = [&](int ti, int tf, int tz, float* ms) -> int {
+  // three timings of `steps` steps exactly as dns_step runs them; *ms = their median,
+  // *spread = their range
+  auto timed = [&](int ti, int tf, int tz, float* ms, float* spread) -> int {
     h->ytile[0] = ti;
     h->ytile[1] = tf;
     h->ztile = tz;
@@ -624,33 +667,40 @@ int dns_tune_tiles(dns_handle* h, int steps, int* y_inverse, int* y_forward, int
     h->w_valid = false;
     int r = dns_step(h, 1);
     if (r) return r;
-    if ((ce = cudaEventRecord(e0, h->stream)) != cudaSuccess) return cuda_fail(ce, "dns_tune_tiles event");
-    if ((r = dns_step(h, steps))) return r;
-    if ((ce = cudaEventRecord(e1, h->stream)) == cudaSuccess) ce = cudaEventSynchronize(e1);
-    if (ce == cudaSuccess) ce = cudaEventElapsedTime(ms, e0, e1);
-    return ce == cudaSuccess ? DNS_OK : cuda_fail(ce, "dns_tune_tiles timing");
+    float t[3];
+    for (int k = 0; k < 3; ++k) {
+      if ((ce = cudaEventRecord(e0, h->stream)) != cudaSuccess) return cuda_fail(ce, "dns_tune_tiles event");
+      if ((r = dns_step(h, steps))) return r;
+      if ((ce = cudaEventRecord(e1, h->stream)) == cudaSuccess) ce = cudaEventSynchronize(e1);
+      if (ce == cudaSuccess) ce = cudaEventElapsedTime(&t[k], e0, e1);
+      if (ce != cudaSuccess) return cuda_fail(ce, "dns_tune_tiles timing");
+    }
+    std::sort(t, t + 3);
+    *ms = t[1];
+    *spread = t[2] - t[0];
+    return DNS_OK;
   };
   // one pass at a time, the others kept: the y-inverse width, the y-forward width,
-  // then the z width, each with the best widths found before it
+  // then the z width, each with the best widths found before it. The first candidate is
+  // the default width; another replaces the one kept so far only if its median beats that
+  // one's median by more than that one's spread (differences inside the timing noise keep
+  // the earlier choice).
   int bi = keep[0], bf = keep[1], bz = keep[2];
-  float best = 1e30f, ms = 0.f;
-  for (int c = 0; c < ny && !rc; ++c)
-    if (!(rc = timed(ycand[c], bf, bz, &ms)) && ms < best) {
-      best = ms;
-      bi = ycand[c];
+  auto pick = [&](int n, const int* cand, int which) {
+    float best = 0.f, best_spread = 0.f, ms = 0.f, spread = 0.f;
+    for (int c = 0; c < n && !rc; ++c) {
+      const int ti = which == 0 ? cand[c] : bi, tf = which == 1 ? cand[c] : bf, tz = which == 2 ? cand[c] : bz;
+      if ((rc = timed(ti, tf, tz, &ms, &spread))) return;
+      if (c == 0 || ms < best - best_spread) {
+        best = ms;
+        best_spread = spread;
+        (which == 0 ? bi : which == 1 ? bf : bz) = cand[c];
+      }
     }
-  best = 1e30f;
-  for (int c = 0; c < ny && !rc; ++c)
-    if (!(rc = timed(bi, ycand[c], bz, &ms)) && ms < best) {
-      best = ms;
-      bf = ycand[c];
-    }
-  best = 1e30f;
-  for (int c = 0; c < nz && !rc; ++c)
-    if (!(rc = timed(bi, bf, zcand[c], &ms)) && ms < best) {
-      best = ms;
-      bz = zcand[c];
-    }
+  };
+  pick(ny, ycand, 0);
+  pick(ny, ycand, 1);
+  pick(nz, zcand, 2);
   // the state and time as before; the fastest widths kept
   err = cudaMemcpyAsync(h->U, save, bytes, cudaMemcpyDeviceToDevice, h->stream);
   if (err == cudaSuccess) err = cudaStreamSynchronize(h->stream);
@@ -670,6 +720,13 @@ int dns_tune_tiles(dns_handle* h, int steps, int* y_inverse, int* y_forward, int
   *y_forward = h->ytile[1];
   *z = h->ztile;
   return rc;
+}
+
+int dns_tile_widths(int N, int dtype, int which, int* widths, int max) {
+  if (!widths || max < 1 || (which != 0 && which != 1)) return fail(DNS_ERR_ARG, "dns_tile_widths: bad arguments");
+  const DnsOps* ops = find_ops(dtype, N);
+  if (!ops) return fail(DNS_ERR_ARG, "dns_tile_widths: N = %d, dtype %d is not compiled", N, dtype);
+  return which == 0 ? ops->y_tiles(widths, max) : ops->z_tiles(widths, max);
 }
 
 int dns_set_state(dns_handle* h, const void* u, int on_device) {
@@ -783,6 +840,7 @@ int dns_rhs(dns_handle* h, void* duhat, int on_device) {
   if (!duhat) return fail(DNS_ERR_ARG, "dns_rhs: duhat is NULL");
   if ((rc = use_device(h))) return rc;
   if (on_device && (uintptr_t)duhat % 16) return fail(DNS_ERR_ARG, "dns_rhs: device pointer must be 16-byte aligned");
+  if (h->closure) DNS_CUDA(closure_eval(h, h->stream), "dns_rhs closure");
   PassArgs a = base_args(h);
   a.out = h->W;  // dU overwrites the forward-transformed product in place
   DNS_CUDA(h->ops->rhs(a, h->stream), "dns_rhs");
@@ -855,6 +913,7 @@ int dns_transform_c2r(dns_handle* h, const void* spec3, void* phys3) {
 int dns_set_forcing(dns_handle* h, const void* f3, int on_device) {
   int rc = check_handle(h);
   if (rc) return rc;
+  if (f3 && h->closure) return fail(DNS_ERR_ARG, "dns_set_forcing: a closure is attached (dns_set_closure)");
   if ((rc = use_device(h))) return rc;
   if (!f3) {
     if (h->has_force) {
@@ -881,6 +940,40 @@ int dns_set_forcing(dns_handle* h, const void* f3, int on_device) {
     ++h->epoch;
   }
   h->has_force = true;
+  return DNS_OK;
+}
+
+int dns_set_closure(dns_handle* h, dns_mlp* net, double delta) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!net) {
+    if (h->closure) {
+      h->closure = nullptr;
+      h->graph_dirty = true;
+      ++h->epoch;
+    }
+    return DNS_OK;
+  }
+  if (h->dtype != DNS_F32) return fail(DNS_ERR_UNSUPPORTED, "dns_set_closure: the closure runs on FP32 handles");
+  for (int i = 0; i < 3; ++i)
+    if (h->L[i] != kTwoPi) return fail(DNS_ERR_UNSUPPORTED, "dns_set_closure: the closure assumes the 2 pi box");
+  if (h->has_force) return fail(DNS_ERR_ARG, "dns_set_closure: a force is set (dns_set_forcing)");
+  if (!(delta > 0.0) || !std::isfinite(delta)) return fail(DNS_ERR_ARG, "dns_set_closure: delta must be finite and > 0");
+  if (net == h->closure && delta == h->closure_delta) return DNS_OK;  // already attached: the graph stays
+  if ((rc = use_device(h))) return rc;
+  const size_t P = (size_t)h->N * h->N * h->N, cb = h->ops->elem_bytes;
+  if (!h->CX) {
+    if ((rc = dev_alloc(h, &h->CX, 10 * P * sizeof(float), "closure features"))) return rc;
+    if ((rc = dev_alloc(h, &h->CT, 6 * P * sizeof(float), "closure stress"))) return rc;
+    if ((rc = dev_alloc(h, &h->CS, 6 * h->fs * cb, "closure spectral fields"))) return rc;
+    if ((rc = dev_alloc(h, &h->CW, 3 * h->fs * cb, "closure work fields"))) return rc;
+    if ((rc = dev_alloc(h, &h->FC, 3 * h->fs * cb, "closure force"))) return rc;
+  }
+  DNS_CUDA(fill_f32((float*)h->CX + 9 * P, P, (float)delta, h->stream), "dns_set_closure");
+  h->closure = net;
+  h->closure_delta = delta;
+  h->graph_dirty = true;
+  ++h->epoch;
   return DNS_OK;
 }
 
@@ -1036,11 +1129,11 @@ std::vector<EnsUnit> ens_units(const dns_ensemble* e) {
   if (e->batch > 0) {
     for (int i = 0; i < n; ++i) {
       const dns_handle* h = e->m[i];
-      if (done[i] || !h->ops->rk_stage_batch) continue;
+      if (done[i] || !h->ops->rk_stage_batch || h->closure) continue;
       std::vector<int> group;
       for (int j = i; j < n; ++j) {
         const dns_handle* g = e->m[j];
-        if (!done[j] && g->ops == h->ops && g->variant == h->variant && same_scheme(g->rk, h->rk)) {
+        if (!done[j] && !g->closure && g->ops == h->ops && g->variant == h->variant && same_scheme(g->rk, h->rk)) {
           group.push_back(j);
           done[j] = true;
         }

@@ -7,7 +7,12 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+struct dns_mlp;
+
 namespace dns {
+
+// Network forward on the given stream (mlp.cu): tau (6 x P) from features X (10 x P).
+cudaError_t mlp_forward_async(::dns_mlp* net, const float* X, float* Y, int P, cudaStream_t st);
 
 // Device buffers and scalars shared by all passes. Complex arrays use the
 // internal spectral layout [component][kz][ky][kx] with kz < N/2 (the
@@ -101,5 +106,12 @@ constexpr int DIAG_BLOCKS = 592;  // 4 x 148..152 SMs: one wave of 4 blocks per 
 
 // Lookup of the instantiation for (dtype, N); nullptr if unsupported.
 const DnsOps* find_ops(int dtype, int N);
+
+// Closure helpers on the internal layout (sgs.cu): G3 = i k_j u_hat_comp (j = 0..2),
+// F3 = -i k_j tau_hat_ij from the 6 stress components (00 11 22 01 02 12); fill of a
+// float array.
+cudaError_t closure_gradient(const void* U, int N, int comp, void* G3, int dtype, cudaStream_t st);
+cudaError_t closure_force(const void* S6, int N, void* F3, int dtype, cudaStream_t st);
+cudaError_t fill_f32(float* p, size_t n, float v, cudaStream_t st);
 
 }  // namespace dns

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "../../include/dns.h"
+#include "dns_internal.h"
 
 namespace dns {
 void set_error_message(const char* msg);
@@ -364,9 +365,67 @@ int mlp_run_grad(dns_mlp* net, const float* X, const float* T, int P, cudaStream
   return DNS_OK;
 }
 
+// Mean and unbiased standard deviation of each feature row of X (10 x P) and each
+// stress row of T (6 x P), in FP64, written into the normalisation entries of the
+// parameter vector: in_shift = mean, in_scale = 1/std (1 where std <= 1e-12),
+// out_scale = std (1 where std <= 1e-30), out_shift = mean. One block per row.
+constexpr int NORM_THREADS = 256;
+__global__ void __launch_bounds__(NORM_THREADS) k_norm(float* __restrict__ prm, const float* __restrict__ X,
+                                                       const float* __restrict__ T, int P) {
+  const int r = blockIdx.x;
+  const float* row = r < NIN ? X + (size_t)r * P : T + (size_t)(r - NIN) * P;
+  __shared__ double red[NORM_THREADS / 32];
+  __shared__ double s_mean;
+  auto block_sum = [&](double v) -> double {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < NORM_THREADS / 32; ++w) t += red[w];
+    return t;
+  };
+  double s = 0.0;
+  for (int i = threadIdx.x; i < P; i += NORM_THREADS) s += (double)row[i];
+  const double tot = block_sum(s);
+  if (threadIdx.x == 0) s_mean = tot / (double)P;
+  __syncthreads();
+  const double mean = s_mean;
+  double q = 0.0;
+  for (int i = threadIdx.x; i < P; i += NORM_THREADS) {
+    const double d = (double)row[i] - mean;
+    q += d * d;
+  }
+  const double ss = block_sum(q);
+  if (threadIdx.x == 0) {
+    const double sd = P > 1 ? sqrt(ss / (double)(P - 1)) : 0.0;
+    if (r < NIN) {
+      prm[O_INSH + r] = (float)mean;
+      prm[O_INSC + r] = sd > 1e-12 ? (float)(1.0 / sd) : 1.f;
+    } else {
+      prm[O_OUTSC + r - NIN] = sd > 1e-30 ? (float)sd : 1.f;
+      prm[O_OUTSH + r - NIN] = (float)mean;
+    }
+  }
+}
+
 }  // namespace
 
+namespace dns {
+cudaError_t mlp_forward_async(::dns_mlp* n, const float* X, float* Y, int P, cudaStream_t st) {
+  k_mlp<0><<<mlp_blocks(P), THREADS, SMEM_B, st>>>(n->prm, n->pack, X, P, Y, nullptr, nullptr);
+  return cudaGetLastError();
+}
+}  // namespace dns
+
 extern "C" {
+
+int dns_mlp_set_normalisation(dns_mlp* n, const float* X, const float* T, int P, void* stream) {
+  if (!n || !X || !T || P < 2) return mlp_fail(DNS_ERR_ARG, "dns_mlp_set_normalisation: bad arguments");
+  k_norm<<<NIN + NOUT, NORM_THREADS, 0, (cudaStream_t)stream>>>(n->prm, X, T, P);
+  MLP_CUDA(cudaGetLastError(), "dns_mlp_set_normalisation launch");
+  return DNS_OK;
+}
 
 int dns_mlp_param_count(void) { return NPARAM; }
 

@@ -10,6 +10,7 @@
 #include <cstdint>
 
 #include "../../include/dns.h"
+#include "dns_internal.h"
 #include "fft_core.cuh"
 
 namespace dns {
@@ -133,7 +134,77 @@ int launched(const char* where) {
 
 bool ok_n(int N) { return N >= 2 && N % 2 == 0 && N <= 4096; }
 
+// ---------------------------------------------------------------------------
+// The same gradient and force on the solver's internal spectral layout
+// [c][kz][ky][kx] (kz < N/2, kx and ky in FFT order), used by the closure the
+// solver evaluates inside its step (dns_set_closure). The arithmetic of every
+// mode is that of k_gradient and k_stress_force.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_grad_internal(const cx<T>* __restrict__ U, int N, int comp, cx<T>* __restrict__ G3) {
+  const size_t per = (size_t)(N / 2) * N * N;
+  for (size_t i = blockIdx.x * (size_t)SGS_THREADS + threadIdx.x; i < per; i += (size_t)gridDim.x * SGS_THREADS) {
+    const int kx = (int)(i % N), ky = (int)((i / N) % N), kz = (int)(i / ((size_t)N * N));
+    const T k[3] = {(T)fftk(kx, N), (T)fftk(ky, N), (T)kz};
+    const cx<T> u = U[comp * per + i];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) G3[j * per + i] = mk(-k[j] * u.y, k[j] * u.x);  // i k_j u
+  }
+}
+
+template <typename T>
+__global__ void k_force_internal(const cx<T>* __restrict__ th, int N, cx<T>* __restrict__ f3) {
+  const size_t per = (size_t)(N / 2) * N * N;
+  const int idx[3][3] = {{0, 3, 4}, {3, 1, 5}, {4, 5, 2}};
+  for (size_t i = blockIdx.x * (size_t)SGS_THREADS + threadIdx.x; i < per; i += (size_t)gridDim.x * SGS_THREADS) {
+    const int kx = (int)(i % N), ky = (int)((i / N) % N), kz = (int)(i / ((size_t)N * N));
+    const T k[3] = {(T)fftk(kx, N), (T)fftk(ky, N), (T)kz};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      T re = 0, im = 0;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const cx<T> t = th[idx[c][j] * per + i];
+        re += k[j] * t.y;  // -i k t = k t.y - i k t.x
+        im -= k[j] * t.x;
+      }
+      f3[c * per + i] = mk(re, im);
+    }
+  }
+}
+
+__global__ void k_fill_f32(float* __restrict__ p, size_t n, float v) {
+  for (size_t i = blockIdx.x * (size_t)SGS_THREADS + threadIdx.x; i < n; i += (size_t)gridDim.x * SGS_THREADS) p[i] = v;
+}
+
 }  // namespace
+
+namespace dns {
+
+cudaError_t closure_gradient(const void* U, int N, int comp, void* G3, int dtype, cudaStream_t st) {
+  const size_t n = (size_t)(N / 2) * N * N;
+  if (dtype == DNS_F32)
+    k_grad_internal<float><<<grid_for(n), SGS_THREADS, 0, st>>>((const cx<float>*)U, N, comp, (cx<float>*)G3);
+  else
+    k_grad_internal<double><<<grid_for(n), SGS_THREADS, 0, st>>>((const cx<double>*)U, N, comp, (cx<double>*)G3);
+  return cudaGetLastError();
+}
+
+cudaError_t closure_force(const void* S6, int N, void* F3, int dtype, cudaStream_t st) {
+  const size_t n = (size_t)(N / 2) * N * N;
+  if (dtype == DNS_F32)
+    k_force_internal<float><<<grid_for(n), SGS_THREADS, 0, st>>>((const cx<float>*)S6, N, (cx<float>*)F3);
+  else
+    k_force_internal<double><<<grid_for(n), SGS_THREADS, 0, st>>>((const cx<double>*)S6, N, (cx<double>*)F3);
+  return cudaGetLastError();
+}
+
+cudaError_t fill_f32(float* p, size_t n, float v, cudaStream_t st) {
+  k_fill_f32<<<grid_for(n), SGS_THREADS, 0, st>>>(p, n, v);
+  return cudaGetLastError();
+}
+
+}  // namespace dns
 
 extern "C" {
 

@@ -487,16 +487,16 @@ __global__ void __launch_bounds__(YCfg<T, N, INV, TXO>::THREADS, (YCfg<T, N, INV
 }
 
 // Batched form on the members' work arrays (ensembles): blockIdx.z = member *
-// fields + field; otherwise the same steps as k_ypass.
-template <typename T, int N, int INV, int PRUNE>
-__global__ void __launch_bounds__(YCfg<T, N, INV>::THREADS, (YCfg<T, N, INV>::MINB)) k_ypass_b(const __grid_constant__ BatchArgs B,
-                                                                                           int fields) {
+// fields + field; otherwise the same steps as k_ypass (TXO: a tuned tile width).
+template <typename T, int N, int INV, int PRUNE, int TXO = 0>
+__global__ void __launch_bounds__(YCfg<T, N, INV, TXO>::THREADS, (YCfg<T, N, INV, TXO>::MINB))
+    k_ypass_b(const __grid_constant__ BatchArgs B, int fields) {
   using G = Geometry<T, N>;
-  using Y = YCfg<T, N, INV>;
+  using Y = YCfg<T, N, INV, TXO>;
   const PassArgs& a = B.a[blockIdx.z / fields];
   cx<T>* base = reinterpret_cast<cx<T>*>(a.W) + (blockIdx.z % fields) * G::FS + (size_t)blockIdx.y * N * N +
                 blockIdx.x * Y::TX;
-  ypass_tile<T, N, INV, PRUNE, 0, Y::THREADS>(base, reinterpret_cast<const cx<T>*>(a.tw), a.kmax3);
+  ypass_tile<T, N, INV, PRUNE, TXO, Y::THREADS>(base, reinterpret_cast<const cx<T>*>(a.tw), a.kmax3);
 }
 
 // ---------------------------------------------------------------------------
@@ -630,10 +630,10 @@ __global__ void __launch_bounds__(ZP_THREADS, (Geometry<T, N>::ZMIN)) k_zpass(Pa
   zpass_body<T, N, MODE, TXO>(a, blockIdx.x, blockIdx.y);
 }
 
-// Batched form (ensembles): member blockIdx.z.
-template <typename T, int N, int MODE>
+// Batched form (ensembles): member blockIdx.z (TXO: a tuned tile width).
+template <typename T, int N, int MODE, int TXO = 0>
 __global__ void __launch_bounds__(ZP_THREADS, (Geometry<T, N>::ZMIN)) k_zpass_b(const __grid_constant__ BatchArgs B) {
-  zpass_body<T, N, MODE>(B.a[blockIdx.z], blockIdx.x, blockIdx.y);
+  zpass_body<T, N, MODE, TXO>(B.a[blockIdx.z], blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -1881,6 +1881,10 @@ struct SolverImpl {
     if constexpr (ytile_ok(TXO)) {
       if (e == cudaSuccess) e = smem_attr(k_ypass<T, N, 1, 0, TXO>, YCfg<T, N, 1, TXO>::SMEM);
       if (e == cudaSuccess) e = smem_attr(k_ypass<T, N, 0, 1, TXO>, YCfg<T, N, 0, TXO>::SMEM);
+      if constexpr (!ZCross<T, N>::enabled) {
+        if (e == cudaSuccess) e = smem_attr(k_ypass_b<T, N, 1, 0, TXO>, YCfg<T, N, 1, TXO>::SMEM);
+        if (e == cudaSuccess) e = smem_attr(k_ypass_b<T, N, 0, 1, TXO>, YCfg<T, N, 0, TXO>::SMEM);
+      }
     }
   }
   static int y_tiles(int* tiles, int max) {
@@ -1896,8 +1900,10 @@ struct SolverImpl {
   }
   template <int TXO>
   static void ztile_attr(cudaError_t& e) {
-    if constexpr (ztile_ok(TXO))
+    if constexpr (ztile_ok(TXO)) {
       if (e == cudaSuccess) e = smem_attr(k_zpass<T, N, ZM_CROSS, TXO>, G::zbytes(TXO));
+      if (e == cudaSuccess) e = smem_attr(k_zpass_b<T, N, ZM_CROSS, TXO>, G::zbytes(TXO));
+    }
   }
   static int z_tiles(int* tiles, int max) {
     int n = 0;
@@ -2038,14 +2044,50 @@ struct SolverImpl {
     return cudaGetLastError();
   }
 
+  // batched passes with tile width TXO (0: default)
+  template <int INV, int PRUNE, int TXO>
+  static void yb_go(const BatchArgs& B, int count, int planes, int fields, cudaStream_t st) {
+    using Y = YCfg<T, N, INV, TXO>;
+    k_ypass_b<T, N, INV, PRUNE, TXO><<<dim3(N / Y::TX, planes, fields * count), Y::THREADS, Y::SMEM, st>>>(B, fields);
+  }
+  template <int INV, int PRUNE>
+  static void yb_stage(int tile, const BatchArgs& B, int count, int planes, int fields, cudaStream_t st) {
+    if constexpr (N <= BATCH_MAX_N) {
+      if constexpr (ytile_ok(4)) if (tile == 4) return yb_go<INV, PRUNE, 4>(B, count, planes, fields, st);
+      if constexpr (ytile_ok(8)) if (tile == 8) return yb_go<INV, PRUNE, 8>(B, count, planes, fields, st);
+      if constexpr (ytile_ok(16)) if (tile == 16) return yb_go<INV, PRUNE, 16>(B, count, planes, fields, st);
+      if constexpr (ytile_ok(32)) if (tile == 32) return yb_go<INV, PRUNE, 32>(B, count, planes, fields, st);
+    }
+    yb_go<INV, PRUNE, 0>(B, count, planes, fields, st);
+  }
+  template <int TXO>
+  static void zb_go(const BatchArgs& B, int count, cudaStream_t st) {
+    constexpr int TX = TXO > 0 ? TXO : G::ZTX;
+    k_zpass_b<T, N, ZM_CROSS, TXO><<<dim3(N / TX, N, count), ZP_THREADS, G::zbytes(TX), st>>>(B);
+  }
+  static void zb_stage(int tile, const BatchArgs& B, int count, cudaStream_t st) {
+    if constexpr (ztile_ok(4)) if (tile == 4) return zb_go<4>(B, count, st);
+    if constexpr (ztile_ok(8)) if (tile == 8) return zb_go<8>(B, count, st);
+    if constexpr (ztile_ok(16)) if (tile == 16) return zb_go<16>(B, count, st);
+    if constexpr (ztile_ok(32)) if (tile == 32) return zb_go<32>(B, count, st);
+    zb_go<0>(B, count, st);
+  }
+
   static cudaError_t rk_stage_batch(const PassArgs* A, int count, int kmax3, cudaStream_t st) {
     if constexpr (N <= BATCH_MAX_N && N != 512 && N != 1024 && !ZCross<T, N>::enabled) {
       if (count < 1 || count > BATCH_MAX_COUNT) return cudaErrorInvalidValue;
       BatchArgs B;
       for (int i = 0; i < count; ++i) B.a[i] = f32args(A[i]);
-      k_ypass_b<T, N, 1, 0><<<dim3(N / YCfg<T, N, 1>::TX, M, 6 * count), YCfg<T, N, 1>::THREADS, YCfg<T, N, 1>::SMEM, st>>>(B, 6);
-      k_zpass_b<T, N, ZM_CROSS><<<dim3(N / G::ZTX, N, count), ZP_THREADS, G::ZSMEM, st>>>(B);
-      k_ypass_b<T, N, 0, 1><<<dim3(N / YCfg<T, N, 0>::TX, kc_of(kmax3), 3 * count), YCfg<T, N, 0>::THREADS, YCfg<T, N, 0>::SMEM, st>>>(B, 3);
+      // the members' tile widths where they agree (a size class tuned together), else the defaults
+      int yi = A[0].ytile[0], yf = A[0].ytile[1], zt = A[0].ztile;
+      for (int i = 1; i < count; ++i) {
+        if (A[i].ytile[0] != yi) yi = 0;
+        if (A[i].ytile[1] != yf) yf = 0;
+        if (A[i].ztile != zt) zt = 0;
+      }
+      yb_stage<1, 0>(yi, B, count, M, 6, st);
+      zb_stage(zt, B, count, st);
+      yb_stage<0, 1>(yf, B, count, kc_of(kmax3), 3, st);
       k_xpass_b<T, N, XM_STAGE><<<dim3(M * N, count), XP_THREADS, xsmem_stage(A[0].stage, A[0].last), st>>>(B);
       return cudaGetLastError();
     } else {

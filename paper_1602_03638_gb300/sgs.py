@@ -187,6 +187,13 @@ class MLP:
                    "dns_mlp_get_params")
         return v
 
+    def set_normalisation(self, X: torch.Tensor, T: torch.Tensor):
+        """in_shift/in_scale and out_scale/out_shift from the mean and unbiased std of the rows of
+        the device arrays X (10, P) and T (6, P), computed by a device kernel (constant features
+        keep scale 1); the Adam state is kept."""
+        _lib.check(_lib.lib().dns_mlp_set_normalisation(self._h, _p(X), _p(T), X.shape[1], _stream()),
+                   "dns_mlp_set_normalisation")
+
     def forward(self, X: torch.Tensor) -> torch.Tensor:
         P = X.shape[1]
         Y = torch.empty((N_OUT, P), dtype=torch.float32, device=X.device)
@@ -250,23 +257,21 @@ def init_params(seed: int = 0) -> np.ndarray:
 
 
 def with_normalisation(params: np.ndarray, X: torch.Tensor, T: torch.Tensor) -> np.ndarray:
-    """Sets in_shift/in_scale and out_scale/out_shift from data statistics (constant features keep scale 1)."""
-    v = np.array(params, dtype=np.float32, copy=True)
-    xm = X.mean(dim=1).cpu().numpy()
-    xs = X.std(dim=1).cpu().numpy()
-    tm = T.mean(dim=1).cpu().numpy()
-    ts = T.std(dim=1).cpu().numpy()
-    v[0:10] = xm
-    v[10:20] = np.where(xs > 1e-12, 1.0 / np.maximum(xs, 1e-30), 1.0)
-    v[5274:5280] = np.where(ts > 1e-30, ts, 1.0)
-    v[5280:5286] = tm
+    """The parameter vector with in_shift/in_scale and out_scale/out_shift set from the data
+    statistics (MLP.set_normalisation on a temporary network)."""
+    m = MLP(params)
+    m.set_normalisation(X.contiguous(), T.contiguous())
+    v = m.get_params()
+    m.close()
     return v
 
 
 # ------------------------------------------------------------------ coarse runs
 
 def set_closure_force(coarse: Solver, mlp: MLP):
-    """Forcing f = -i k_j tau_hat_ij with tau = MLP(grad ubar) from the coarse solver's current state."""
+    """Forcing f = -i k_j tau_hat_ij with tau = MLP(grad ubar) from the coarse solver's current state,
+    composed from the library's separate calls (public layout, host waits between them): the
+    reference the in-step closure of dns_set_closure is tested against."""
     dev = "cuda"
     on_torch_stream(coarse)
     uh = torch.empty(coarse.spec_shape, dtype=_cdt(coarse.dtype), device=dev)
@@ -285,12 +290,11 @@ def set_closure_force(coarse: Solver, mlp: MLP):
 
 
 def run_coarse(coarse: Solver, steps: int, mlp: MLP | None = None):
-    """Advance the coarse solver; with a network the closure force is refreshed before every step
-    (evaluated at the start of the step and held over its four RK4 stages)."""
-    for _ in range(steps):
-        if mlp is not None:
-            set_closure_force(coarse, mlp)
-        coarse.step(1)
+    """Advance the coarse solver; with a network, the closure force is evaluated by the solver
+    itself at the start of every step (dns_set_closure: features, network, stress force and
+    forcing inside the step graph, held over its four RK4 stages); None detaches it."""
+    coarse.set_closure(mlp)
+    coarse.step(steps)
     torch.cuda.synchronize()
 
 
@@ -330,6 +334,17 @@ def eddy_turnover(s: Solver) -> dict:
     shells = np.arange(1, spec.size)
     L = math.pi / (2.0 * up * up) * float(np.sum(spec[1:] / shells))
     return {"energy": energy, "u_rms": up, "integral_scale": L, "T_e": L / up}
+
+
+def _device_ms(fn) -> float:
+    """Milliseconds between CUDA events on torch's current stream around fn()."""
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    st = torch.cuda.current_stream()
+    e0.record(st)
+    fn()
+    e1.record(st)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
 
 
 def closure_experiment(Nf: int = 512, Nc: int = 64, nu: float = 2e-3, dt_f: float = 1e-3, dt_c: float = 4e-3,
@@ -375,7 +390,7 @@ def closure_experiment(Nf: int = 512, Nc: int = 64, nu: float = 2e-3, dt_f: floa
         t_run = 2.0 * out["eddy"]["T_e"]
     out["t_run"] = t_run
     net = MLP(seed=seed)
-    net.set_params(with_normalisation(net.get_params(), X, T))
+    net.set_normalisation(X, T)
     t0 = time.perf_counter()
     hist = net.fit(X, T, iters=iters, lr=lr, batch=batch, seed=seed, log_every=max(1, iters // 5))
     torch.cuda.synchronize()
@@ -400,12 +415,8 @@ def closure_experiment(Nf: int = 512, Nc: int = 64, nu: float = 2e-3, dt_f: floa
         torch.cuda.synchronize()
         t_dns += time.perf_counter() - t0
         _, _, ref = filtered_training_data(fine, tool)
-        t0 = time.perf_counter()
-        run_coarse(plain, n_c, None)
-        t_plain += time.perf_counter() - t0
-        t0 = time.perf_counter()
-        run_coarse(model, n_c, net)
-        t_model += time.perf_counter() - t0
+        t_plain += _device_ms(lambda: run_coarse(plain, n_c, None))
+        t_model += _device_ms(lambda: run_coarse(model, n_c, net))
         tool.set_state_spectral(ref)
         d_ref = tool.diagnostics()["dissipation"]
         refn = ref.cpu().numpy()
@@ -419,8 +430,9 @@ def closure_experiment(Nf: int = 512, Nc: int = 64, nu: float = 2e-3, dt_f: floa
         rec.append(row)
     out["checkpoints"] = rec
     out["final"] = rec[-1]
-    out["coarse_ms_per_step_no_model"] = 1e3 * t_plain / (checkpoints * n_c)
-    out["coarse_ms_per_step_model"] = 1e3 * t_model / (checkpoints * n_c)
+    out["coarse_ms_per_step_no_model"] = t_plain / (checkpoints * n_c)
+    out["coarse_ms_per_step_model"] = t_model / (checkpoints * n_c)
+    out["coarse_timing"] = "CUDA events on the solvers' stream around each checkpoint's steps"
     out["dns_ms_per_step"] = 1e3 * t_dns / (checkpoints * n_f)
     for s in (plain, model, tool, fine):
         s.close()

@@ -129,6 +129,17 @@ class Solver:
         _lib.check(_lib.lib().dns_get_option(self._h, key.encode(), ctypes.byref(v)), "dns_get_option")
         return v.value
 
+    def set_closure(self, net=None, delta: float | None = None):
+        """Attach a closure network (sgs.MLP) that every step evaluates on the device before its
+        stages (dns_set_closure; FP32, 2 pi box); None detaches. delta: the filter-width feature
+        (default 2 pi / N). The solver keeps a reference to the network while attached."""
+        import math
+
+        h = net._h if net is not None else None
+        d = float(delta) if delta is not None else 2.0 * math.pi / self.N
+        _lib.check(_lib.lib().dns_set_closure(self._h, h, d), "dns_set_closure")
+        self._closure = net
+
     def set_rk_tableau(self, form: int, a, b=()):
         """A user-supplied explicit RK scheme (dns_set_rk_tableau): form 0 = the Appendix
         two-register form (weights a, offsets b), form 1 = Williamson's 2N form (A = a, B = b)."""

@@ -203,6 +203,93 @@ def test_forced_rhs_matches_reference():
     assert np.linalg.norm(stepped - cur) / np.linalg.norm(cur) < 1e-12
 
 
+def _closure_net(seed, N):
+    """A network with random weights and biases, normalised on the features of a random field."""
+    sgs = _sgs()
+    rng = np.random.default_rng(seed)
+    p = sg.init_params(seed)
+    p["b1"] = rng.normal(size=64) * 0.1
+    p["b2"] = rng.normal(size=64) * 0.1
+    p["b3"] = rng.normal(size=6) * 0.1
+    net = sgs.MLP(sg.flatten(p).astype(np.float32))
+    X = torch.from_numpy(rng.normal(size=(10, N ** 3)).astype(np.float32) * 3.0).cuda()
+    T = torch.from_numpy(rng.normal(size=(6, N ** 3)).astype(np.float32) * 0.01).cuda()
+    net.set_normalisation(X, T)
+    return net
+
+
+def test_normalisation_kernel_matches_mean_and_unbiased_std():
+    sgs = _sgs()
+    rng = np.random.default_rng(12)
+    P = 5000
+    X = rng.normal(size=(10, P)) * rng.uniform(0.1, 5.0, size=(10, 1)) + rng.normal(size=(10, 1))
+    X[9] = 0.25  # a constant feature keeps scale 1
+    T = rng.normal(size=(6, P)) * 0.02 + 0.3
+    net = sgs.MLP(seed=0)
+    before = sg.unflatten(net.get_params().astype(np.float64))
+    net.set_normalisation(torch.from_numpy(X.astype(np.float32)).cuda(), torch.from_numpy(T.astype(np.float32)).cuda())
+    got = sg.unflatten(net.get_params().astype(np.float64))
+    X32, T32 = X.astype(np.float32).astype(np.float64), T.astype(np.float32).astype(np.float64)
+    np.testing.assert_allclose(got["in_shift"], X32.mean(1), rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(got["in_scale"][:9], 1.0 / X32[:9].std(1, ddof=1), rtol=1e-6)
+    assert got["in_scale"][9] == 1.0
+    np.testing.assert_allclose(got["out_scale"], T32.std(1, ddof=1), rtol=1e-6)
+    np.testing.assert_allclose(got["out_shift"], T32.mean(1), rtol=1e-6)
+    for k in sg.TRAINABLE:
+        assert np.array_equal(got[k], before[k])
+    net.close()
+
+
+def test_in_step_closure_equals_the_composed_calls():
+    """dns_set_closure (features, network, force and forcing inside the step graph) against the
+    same closure composed from the library's separate calls before every step: bit for bit."""
+    sgs = _sgs()
+    N, nu, dt, steps = 32, 0.01, 0.005, 3
+    uh = inputs.isotropic_spectral(N, seed=21, k0=4.0).numpy().astype(np.complex64)
+    net = _closure_net(3, N)
+    with Solver(N, nu, dt, "f32") as a, Solver(N, nu, dt, "f32") as b:
+        sgs.on_torch_stream(a, b)
+        a.set_state_spectral(uh)
+        b.set_state_spectral(uh)
+        a.set_closure(net)
+        a.step(steps)
+        for _ in range(steps):
+            sgs.set_closure_force(b, net)
+            b.step(1)
+        ga, gb = a.get_state_spectral(), b.get_state_spectral()
+    assert np.abs(ga - uh).max() > 1e-4 * np.abs(uh).max()  # the state moved
+    np.testing.assert_array_equal(ga, gb)
+    net.close()
+
+
+def test_in_step_closure_rhs_matches_reference():
+    """dns_rhs with the closure attached against the reference: features from the reference's
+    velocity gradients, its BF16-rounded network, stress force and forced right-hand side."""
+    N, nu = 32, 0.01
+    uh = inputs.isotropic_spectral(N, seed=22, k0=4.0).numpy().astype(np.complex64)
+    net = _closure_net(4, N)
+    with Solver(N, nu, 0.005, "f32") as s:
+        s.set_state_spectral(uh)
+        s.set_closure(net)
+        got = s.rhs()
+        s.set_closure(None)
+        plain = s.rhs()
+    pv = sg.unflatten(net.get_params().astype(np.float64))
+    u64 = uh.astype(np.complex128)
+    A = sg.velocity_gradients(u64).reshape(9, -1)
+    X = np.concatenate([A, np.full((1, N ** 3), 2 * np.pi / N)]).T
+    tau = sg.forward(pv, X, round_bf16=True)["tau"].T.reshape(6, N, N, N)
+    f = sg.stress_force(tau)
+    g = sn.Grid(N)
+    ref = sg.rhs_forced(u64, g, nu, f)
+    fscale = np.abs(f * g.mask).max()
+    assert fscale > 1e-3 * np.abs(ref).max()  # the closure term is not negligible
+    assert np.abs(got - ref).max() < 2e-2 * fscale + 1e-5 * np.abs(ref).max()
+    # detaching restores the plain right-hand side
+    assert np.abs(plain - sn.rhs(u64, g, nu)).max() < 1e-5 * np.abs(ref).max()
+    net.close()
+
+
 def test_trained_closure_beats_the_unmodelled_coarse_run():
     """A-posteriori: 256^3 DNS (this solver) -> box-filtered 32^3 data -> network trained on the
     GPU -> coarse 32^3 runs with and without the closure, judged against the filtered DNS."""

@@ -29,3 +29,20 @@ def test_short_taylor_green_run_series():
         dEdt = (c["E"] - a["E"]) / (c["t"] - a["t"])
         assert abs(-dEdt - b["eps"]) < 1e-4 * b["eps"]
     assert max(x["max_div"] for x in s) < 1e-12
+
+
+def test_short_isotropic_run_compares_the_two_forms():
+    """The isotropic run module on a small grid: both forms start from the same unit-energy
+    field, lose energy at the rate eps (budget to 1e-3 with samples 10 steps apart), stay
+    divergence-free, and the FP32 form stays within FP32 round-off of the FP64 form."""
+    from paper_1602_03638_gb300 import iso_run
+
+    r = iso_run.run(N=64, steps=40, every=10, nu=1e-2, dt=2e-3, seed=3, k0=4.0)
+    for dtype in ("f64", "f32"):
+        s = r["runs"][dtype]["series"]
+        assert len(s) == 5 and abs(s[0]["E"] - 1.0) < 1e-6
+        for a, b, c in zip(s, s[1:], s[2:]):
+            dEdt = (c["E"] - a["E"]) / (c["t"] - a["t"])
+            assert abs(-dEdt - b["eps"]) < 1e-3 * b["eps"]
+        assert max(x["max_div"] for x in s) < (1e-4 if dtype == "f32" else 1e-12)
+    assert 1e-9 < r["rel_l2_f32_vs_f64"] < 1e-5

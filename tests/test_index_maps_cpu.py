@@ -134,6 +134,19 @@ def test_z256_quarter_warp_maps():
             assert (src_h + 8 * src_m) % M == (M - k) % M
 
 
+def _library_widths(N, cb, which):
+    import ctypes
+
+    from paper_1602_03638_gb300 import _lib
+    from paper_1602_03638_gb300 import build as B
+
+    B.build()
+    buf = (ctypes.c_int * 8)()
+    n = _lib.lib().dns_tile_widths(N, 0 if cb == 8 else 1, which, buf, 8)
+    assert n >= 0, _lib.last_error()
+    return list(buf[:n])
+
+
 def _zbytes(N, t, cb):
     return padded_len(N // 2) * odd_ld(6 * t) * cb
 
@@ -141,9 +154,12 @@ def _zbytes(N, t, cb):
 @pytest.mark.parametrize("cb", [8, 16])
 @pytest.mark.parametrize("N", [n for n in SIZES if n <= 128])
 def test_offered_tile_widths_divide_the_grid_and_fit(N, cb):
-    # the widths a tuner may pick (y-pass: x columns per block; z-pass: x per tile)
-    y = [t for t in (4, 8, 16, 32) if pow2_part(N) % t == 0 and t * cb <= 256]
-    z = [t for t in (4, 8, 16, 32) if pow2_part(N) % t == 0 and _zbytes(N, t, cb) <= 112 * 1024]
+    # the widths a tuner may pick (y-pass: x columns per block; z-pass: x per tile), as the
+    # library offers them (dns_tile_widths needs no device), against the rule restated here
+    y = _library_widths(N, cb, 0)
+    z = _library_widths(N, cb, 1)
+    assert y == [t for t in (4, 8, 16, 32) if pow2_part(N) % t == 0 and t * cb <= 256]
+    assert z == [t for t in (4, 8, 16, 32) if pow2_part(N) % t == 0 and _zbytes(N, t, cb) <= 112 * 1024]
     for t in y:
         assert N % t == 0
         assert padded_len(N) * odd_ld(t) * cb <= 227 * 1024
