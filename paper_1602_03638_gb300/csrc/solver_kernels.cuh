@@ -443,7 +443,7 @@ __device__ __forceinline__ int ywalk_row(int r) {
 // One y tile: TX adjacent columns starting at `base` (field, kz plane and first
 // column already applied), transformed along y in place. NT: threads of the block.
 template <typename T, int N, int INV, int PRUNE, int TXO, int NT>
-__device__ __forceinline__ void ypass_tile(cx<T>* base, const cx<T>* __restrict__ tw, int kmax3) {
+__device__ __forceinline__ void ypass_tile(cx<T>* __restrict__ base, const cx<T>* __restrict__ tw, int kmax3) {
   using Y = YCfg<T, N, INV, TXO>;
   constexpr int TX = Y::TX;
   constexpr int LD = Y::LD;
@@ -482,8 +482,37 @@ __global__ void __launch_bounds__(YCfg<T, N, INV, TXO>::THREADS, (YCfg<T, N, INV
                                                                                          int kmax3) {
   using G = Geometry<T, N>;
   using Y = YCfg<T, N, INV, TXO>;
-  cx<T>* base = F + blockIdx.z * G::FS + (size_t)blockIdx.y * N * N + blockIdx.x * Y::TX;
-  ypass_tile<T, N, INV, PRUNE, TXO, Y::THREADS>(base, tw, kmax3);
+  constexpr int TX = Y::TX;
+  constexpr int LD = Y::LD;
+  constexpr int NT = Y::THREADS;  // warps loop over the columns
+  extern __shared__ unsigned char smraw[];
+  cx<T>* s = reinterpret_cast<cx<T>*>(smraw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  cx<T>* base = F + blockIdx.z * G::FS + (size_t)blockIdx.y * N * N + blockIdx.x * TX;
+  // the whole tile in flight at once (cp.async, no register staging); the
+  // inverse's conjugation is applied when the first pass reads it
+#pragma unroll 8
+  for (int e = threadIdx.x; e < TX * N; e += NT) {
+    const int x = e % TX, y = ywalk_row<T, TX, N>(e / TX);
+    cp_async<sizeof(cx<T>)>(s + padp(y) * LD + x, base + (size_t)y * N + x);
+  }
+  cp_async_commit();
+  cp_async_wait<0>();
+  __syncthreads();
+#pragma unroll 1
+  for (int c = warp; c < TX; c += NT / 32) {
+    const SLine<T, LD> line{s + c};
+    if constexpr (INV) warp_fft<T, N, N>(SLineConj<T, LD>{s + c}, line, line, tw, lane);
+    else warp_fft<T, N, N>(line, line, line, tw, lane);
+  }
+  __syncthreads();
+#pragma unroll 8
+  for (int e = threadIdx.x; e < TX * N; e += NT) {
+    const int x = e % TX, y = ywalk_row<T, TX, N>(e / TX);
+    if (PRUNE && !kept(kfreq(y, N), kmax3)) continue;
+    const cx<T> v = s[padp(y) * LD + x];
+    base[(size_t)y * N + x] = INV ? conjg(v) : v;
+  }
 }
 
 // Batched form on the members' work arrays (ensembles): blockIdx.z = member *
