@@ -1095,14 +1095,17 @@ __global__ void __launch_bounds__(32 * Z16P<T>::NW, 1) k_zcross16p(PassArgs a) {
   cx<T>* const sl = s + padp(TX * kq) * LD + tx;
   const size_t lane_g = ((size_t)(TX * kq) * N) * N + tx;
 
-  // asynchronous fetch of fields f0 .. f0+2 of tile t into their lines
+  // asynchronous fetch of fields f0 .. f0+2 of tile t into their lines. Warp w takes the
+  // 16 consecutive walk items 16 w + j: with ITEMS = 8 TX = 128 its field (w / 8) and row
+  // group g = w % 8 are fixed and j is the row offset c, so the addresses are a per-warp
+  // base plus j times a constant stride.
+  static_assert(TX == 16 && ITEMS == 128 && 3 * ITEMS == 16 * NW, "z tile chunking");
   auto fetch = [&](int t, int f0) {
-    const cx<T>* gl = W + lane_g + (size_t)(t / XT) * N + (t % XT) * TX;
-#pragma unroll 4
-    for (int it = w; it < 3 * ITEMS; it += NW) {
-      const int f = f0 + it / ITEMS, r = it % ITEMS, g = r / TX, c = r % TX;
-      cp_async<sizeof(cx<T>)>(sl + (34 * g + c) * LD + f * TX, gl + f * FS + (size_t)(32 * g + c) * N * N);
-    }
+    const int f = f0 + w / 8, g = w % 8;
+    const cx<T>* gl = W + lane_g + (size_t)(t / XT) * N + (t % XT) * TX + (size_t)f * FS + (size_t)(32 * g) * N * N;
+    cx<T>* sd = sl + 34 * g * LD + f * TX;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) cp_async<sizeof(cx<T>)>(sd + j * LD, gl + (size_t)j * N * N);
   };
   // c2r of the TX lines of fields f0 .. f0+2, two lines per warp at a time
   HwTwL ht;
@@ -1218,10 +1221,13 @@ __global__ void __launch_bounds__(32 * Z16P<T>::NW, 1) k_zcross16p(PassArgs a) {
       }
     }
     __syncthreads();
-    cx<T>* gd = W + lane_g + (size_t)y * N + x0;
-    for (int it = w; it < 3 * ITEMS; it += NW) {
-      const int f = it / ITEMS, r = it % ITEMS, g = r / TX, c = r % TX;
-      if (32 * g + TX * kq + c < kc) gd[f * FS + (size_t)(32 * g + c) * N * N] = sl[(34 * g + c) * LD + f * TX];
+    {  // the same chunks as the fetch: field w / 8, rows 32 (w % 8) + TX kq + j
+      const int f = w / 8, g = w % 8, k0 = 32 * g + TX * kq;
+      cx<T>* gd = W + lane_g + (size_t)y * N + x0 + (size_t)f * FS + (size_t)(32 * g) * N * N;
+      const cx<T>* sd = sl + 34 * g * LD + f * TX;
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (k0 + j < kc) gd[(size_t)j * N * N] = sd[j * LD];
     }
     __syncthreads();  // the u lines have been read out
     if (tn < NT) fetch(tn, 0);
@@ -1351,13 +1357,17 @@ __global__ void __launch_bounds__(32 * Z32P<T>::NW, 1) k_zcross32p(PassArgs a) {
   // walk kz = 32 g + TX kq + c: padp(kz) = 34 g + padp(TX kq) + c
   cx<T>* const sl = s + padp(TX * kq) * LD + tx;
   const size_t lane_g = ((size_t)(TX * kq) * N) * N + tx;
+  // warp w takes the 32 consecutive walk items 32 w + j (j = 8 a + b): field f0 + w / 4, row
+  // group g = 4 (w % 4) + a, row offset c = b, so the addresses are a per-warp base plus
+  // compile-time offsets
+  static_assert(TX == 8 && ITEMS == 128 && 3 * ITEMS == 32 * NW, "z tile chunking");
   auto fetch = [&](int t, int f0) {
-    const cx<T>* gl = W + lane_g + (size_t)(t / XT) * N + (t % XT) * TX;
-#pragma unroll 4
-    for (int it = w; it < 3 * ITEMS; it += NW) {
-      const int f = f0 + it / ITEMS, r = it % ITEMS, g = r / TX, c = r % TX;
-      cp_async<sizeof(cx<T>)>(sl + (34 * g + c) * LD + f * TX, gl + f * FS + (size_t)(32 * g + c) * N * N);
-    }
+    const int f = f0 + w / 4, q = w % 4;
+    const cx<T>* gl = W + lane_g + (size_t)(t / XT) * N + (t % XT) * TX + (size_t)f * FS + (size_t)(128 * q) * N * N;
+    cx<T>* sd = sl + 136 * q * LD + f * TX;
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      cp_async<sizeof(cx<T>)>(sd + (34 * (j / 8) + j % 8) * LD, gl + (size_t)(32 * (j / 8) + j % 8) * N * N);
   };
   HwTw32 ht;
   ht.init(tw, h);
@@ -1466,10 +1476,13 @@ __global__ void __launch_bounds__(32 * Z32P<T>::NW, 1) k_zcross32p(PassArgs a) {
       }
     }
     __syncthreads();
-    cx<T>* gd = W + lane_g + (size_t)y * N + x0;
-    for (int it = w; it < 3 * ITEMS; it += NW) {
-      const int f = it / ITEMS, r = it % ITEMS, g = r / TX, c = r % TX;
-      if (32 * g + TX * kq + c < kc) gd[f * FS + (size_t)(32 * g + c) * N * N] = sl[(34 * g + c) * LD + f * TX];
+    {  // the same chunks as the fetch: field w / 4, rows 128 (w % 4) + 32 a + TX kq + b
+      const int f = w / 4, q = w % 4, k0 = 128 * q + TX * kq;
+      cx<T>* gd = W + lane_g + (size_t)y * N + x0 + (size_t)f * FS + (size_t)(128 * q) * N * N;
+      const cx<T>* sd = sl + 136 * q * LD + f * TX;
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (k0 + 32 * (j / 8) + j % 8 < kc) gd[(size_t)(32 * (j / 8) + j % 8) * N * N] = sd[(34 * (j / 8) + j % 8) * LD];
     }
     __syncthreads();  // the u lines have been read out
     if (tn < NT) fetch(tn, 0);
@@ -1546,10 +1559,16 @@ __global__ void __launch_bounds__(32 * Z8Q<T>::NW, 2) k_zcross8q(PassArgs a) {
   // walk kz = 32 g + TX kq + c: padp(kz) = 34 g + padp(TX kq) + c
   cx<T>* const sl = s + padp(TX * kq) * LD + tx;
   const cx<T>* gl = W + ((size_t)(TX * kq) * N + y) * N + x0 + tx;
-#pragma unroll 4
-  for (int it = w; it < 6 * ITEMS; it += NW) {
-    const int f = it / ITEMS, r = it % ITEMS, g = r / TX, c = r % TX;
-    cp_async<sizeof(cx<T>)>(sl + (34 * g + c) * LD + f * TX, gl + f * FS + (size_t)(32 * g + c) * N * N);
+  // warp w takes the 32 consecutive walk items 32 w + j (j = 16 a + b): field w / 2, row group
+  // g = 2 (w % 2) + a, row offset c = b: a per-warp base plus compile-time offsets
+  static_assert(TX == 16 && ITEMS == 64 && 6 * ITEMS == 32 * NW && 3 * ITEMS == 16 * NW, "z tile chunking");
+  {
+    const int f = w / 2, q = w % 2;
+    const cx<T>* gf = gl + (size_t)f * FS + (size_t)(64 * q) * N * N;
+    cx<T>* sd = sl + 68 * q * LD + f * TX;
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      cp_async<sizeof(cx<T>)>(sd + (34 * (j / 16) + j % 16) * LD, gf + (size_t)(32 * (j / 16) + j % 16) * N * N);
   }
   cp_async_commit();
   HwTwL qt;  // w = exp(-2 pi i h / 128), tl = exp(-2 pi i h / 256)
@@ -1632,10 +1651,13 @@ __global__ void __launch_bounds__(32 * Z8Q<T>::NW, 2) k_zcross8q(PassArgs a) {
     }
   }
   __syncthreads();
-  cx<T>* gd = W + ((size_t)(TX * kq) * N + y) * N + x0 + tx;
-  for (int it = w; it < 3 * ITEMS; it += NW) {
-    const int f = it / ITEMS, r = it % ITEMS, g = r / TX, c = r % TX;
-    if (32 * g + TX * kq + c < kc) gd[f * FS + (size_t)(32 * g + c) * N * N] = sl[(34 * g + c) * LD + f * TX];
+  {  // warp w stores items 16 w + j: field w / 4, rows 32 (w % 4) + TX kq + j
+    const int f = w / 4, g = w % 4, k0 = 32 * g + TX * kq;
+    cx<T>* gd = W + ((size_t)(TX * kq) * N + y) * N + x0 + tx + (size_t)f * FS + (size_t)(32 * g) * N * N;
+    const cx<T>* sd = sl + 34 * g * LD + f * TX;
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      if (k0 + j < kc) gd[(size_t)j * N * N] = sd[j * LD];
   }
 }
 
