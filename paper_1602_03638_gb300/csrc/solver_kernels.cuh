@@ -108,7 +108,9 @@ __device__ __forceinline__ T par(double d, float f) {
 }
 __device__ __forceinline__ bool kept(int k, int kmax3) { return 3 * (k < 0 ? -k : k) < kmax3; }
 
-enum XMode { XM_INV_CURL = 0, XM_STAGE = 1, XM_RHS = 2, XM_FWD_STORE = 3, XM_INV_PLAIN = 4, XM_INV_DIV = 5 };
+// XM_STAGE2N: the stage update of Williamson's 2N low-storage form (a mode of its
+// own, so that the two-register stage update compiles without its branch)
+enum XMode { XM_INV_CURL = 0, XM_STAGE = 1, XM_RHS = 2, XM_FWD_STORE = 3, XM_INV_PLAIN = 4, XM_INV_DIV = 5, XM_STAGE2N = 6 };
 enum ZMode { ZM_CROSS = 0, ZM_STORE = 1, ZM_LOAD = 2, ZM_MAXABS = 3 };
 
 // Writes conj(u/N^3) and conj(i k x u / N^3) of one mode into the 6 line
@@ -170,7 +172,8 @@ __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
   // in the plane pass the RK state is a stream past the plane data kept in L2 (FP32
   // instances only: the hinted FP64 512^3 plane pass raised an illegal-instruction
   // fault whose cause was not found, so FP64 keeps plain accesses)
-  constexpr bool HINT = NT != XP_THREADS && MODE == XM_STAGE && sizeof(T) == 4;
+  constexpr bool STAGE = MODE == XM_STAGE || MODE == XM_STAGE2N;  // a stage update (either form)
+  constexpr bool HINT = NT != XP_THREADS && STAGE && sizeof(T) == 4;
   const unsigned long long pol = HINT ? l2_evict_first_policy() : 0ull;
   using G = Geometry<T, N>;
   constexpr int LS = G::XLS;
@@ -191,18 +194,18 @@ __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
   const T ksx = par<T>(a.ks[0], a.f_ks[0]);
   const T kzv = (T)kz * par<T>(a.ks[2], a.f_ks[2]), kyv = (T)kfreq(ky, N) * par<T>(a.ks[1], a.f_ks[1]);
 
-  if constexpr (MODE == XM_STAGE || MODE == XM_RHS) {
+  if constexpr (STAGE || MODE == XM_RHS) {
     // rows outside the 2/3 box carry no nonlinear term: skip their transform
     const bool row_kept = (3 * kz < a.kmax3) && kept(kfreq(ky, N), a.kmax3);
     const T nu = par<T>(a.nu, a.f_nu), cA = par<T>(a.cA, a.f_cA), cB = par<T>(a.cB, a.f_cB);
     const int stage = a.stage, last = a.last;
     // Williamson 2N stages keep the stage state in U (updated in place) and dU in U1
-    const bool lsrk = MODE == XM_STAGE && a.lsrk;
+    constexpr bool lsrk = MODE == XM_STAGE2N;
     const cx<T>* Sst = (stage == 0 || lsrk) ? U : US;
     // state rows read by the update: stage state (all stages), accumulator
     // (stages after the first), step-start state (the stages between first and
     // last of the two-register form)
-    const bool need1 = MODE == XM_STAGE && stage > 0, need0 = MODE == XM_STAGE && stage > 0 && stage < last && !lsrk;
+    const bool need1 = STAGE && stage > 0, need0 = STAGE && stage > 0 && stage < last && !lsrk;
     cx<T>* const st = s + G::XST;  // XPRE: rows [Sst 0..2][U1 0..2][U 0..2], N values each
     if constexpr (G::XPRE) {
       if (row_kept) {
@@ -280,7 +283,7 @@ __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
           out[2 * FS + gi] = d2;
         } else {
           cx<T> v0, v1, v2;
-          if (lsrk) {  // 2N stage: dU <- A_s dU + dt RHS, u <- u + B_s dU
+          if constexpr (lsrk) {  // 2N stage: dU <- A_s dU + dt RHS, u <- u + B_s dU
             const T cC = par<T>(a.cC, a.f_cC);
             cx<T> e0 = scal(d0, cC), e1 = scal(d1, cC), e2 = scal(d2, cC);
             if (stage > 0) {
@@ -355,7 +358,7 @@ __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
       columns(std::false_type{});
     else
       columns(std::true_type{});
-    if constexpr (MODE == XM_STAGE) {
+    if constexpr (STAGE) {
       __syncthreads();
       if (NT > XP_THREADS && warp >= 6) return;  // one warp per line of u and omega
       if constexpr (G::XPRE && !G::XWIDE) {
@@ -1878,7 +1881,8 @@ __global__ void __launch_bounds__(PLANE_THREADS, (PlaneCfg<T, N>::MINB))
 #pragma unroll 1
       for (int k = 0; k < P::CX; ++k) {
         if (k) __syncthreads();
-        xpass_body<T, N, XM_STAGE, PLANE_THREADS>(a, plane * N + chunk * P::CX + k);
+        if (a.lsrk) xpass_body<T, N, XM_STAGE2N, PLANE_THREADS>(a, plane * N + chunk * P::CX + k);
+        else xpass_body<T, N, XM_STAGE, PLANE_THREADS>(a, plane * N + chunk * P::CX + k);
       }
     } else {
 #pragma unroll 1
@@ -1998,6 +2002,7 @@ struct SolverImpl {
   if (e == cudaSuccess) e = smem_attr(kern, bytes)
     DNS_ATTR((k_xpass<T, N, XM_INV_CURL>), G::XSMEM);
     DNS_ATTR((k_xpass<T, N, XM_STAGE>), G::XSMEM_ST);
+    DNS_ATTR((k_xpass<T, N, XM_STAGE2N>), G::XSMEM_ST);
     DNS_ATTR((k_xpass<T, N, XM_RHS>), G::XSMEM_ST);
     DNS_ATTR((k_xpass<T, N, XM_FWD_STORE>), G::XSMEM);
     DNS_ATTR((k_xpass<T, N, XM_INV_PLAIN>), G::XSMEM);
@@ -2020,6 +2025,7 @@ struct SolverImpl {
       DNS_ATTR((k_zpass_b<T, N, ZM_CROSS>), G::ZSMEM);
       DNS_ATTR((k_ypass_b<T, N, 0, 1>), (YCfg<T, N, 0>::SMEM));
       DNS_ATTR((k_xpass_b<T, N, XM_STAGE>), G::XSMEM_ST);
+      DNS_ATTR((k_xpass_b<T, N, XM_STAGE2N>), G::XSMEM_ST);
     }
 #undef DNS_ATTR
     return e;
@@ -2077,9 +2083,17 @@ struct SolverImpl {
     y_stage<0, 1>(a.ytile[1], W, tw, a.kmax3, kc_of(a.kmax3), 3, st);
   }
 
+  // the x-stage launch of a stage, in the form of the stage's scheme
+  static void x_stage(const PassArgs& a, cudaStream_t st) {
+    if (a.lsrk)
+      k_xpass<T, N, XM_STAGE2N><<<M * N, XP_THREADS, xsmem_stage(a.stage, a.last), st>>>(f32args(a));
+    else
+      k_xpass<T, N, XM_STAGE><<<M * N, XP_THREADS, xsmem_stage(a.stage, a.last), st>>>(f32args(a));
+  }
+
   static cudaError_t rk_stage(const PassArgs& a, cudaStream_t st) {
     rhs_front(a, st);
-    k_xpass<T, N, XM_STAGE><<<M * N, XP_THREADS, xsmem_stage(a.stage, a.last), st>>>(f32args(a));
+    x_stage(a, st);
     return cudaGetLastError();
   }
 
@@ -2090,7 +2104,7 @@ struct SolverImpl {
       case 0: y_stage<1, 0>(a.ytile[0], W, tw, a.kmax3, M, 6, st); break;
       case 1: z_cross(a, st); break;
       case 2: y_stage<0, 1>(a.ytile[1], W, tw, a.kmax3, kc_of(a.kmax3), 3, st); break;
-      default: k_xpass<T, N, XM_STAGE><<<M * N, XP_THREADS, xsmem_stage(a.stage, a.last), st>>>(f32args(a)); break;
+      default: x_stage(a, st); break;
     }
     return cudaGetLastError();
   }
@@ -2139,7 +2153,10 @@ struct SolverImpl {
       yb_stage<1, 0>(yi, B, count, M, 6, st);
       zb_stage(zt, B, count, st);
       yb_stage<0, 1>(yf, B, count, kc_of(kmax3), 3, st);
-      k_xpass_b<T, N, XM_STAGE><<<dim3(M * N, count), XP_THREADS, xsmem_stage(A[0].stage, A[0].last), st>>>(B);
+      if (A[0].lsrk)
+        k_xpass_b<T, N, XM_STAGE2N><<<dim3(M * N, count), XP_THREADS, xsmem_stage(A[0].stage, A[0].last), st>>>(B);
+      else
+        k_xpass_b<T, N, XM_STAGE><<<dim3(M * N, count), XP_THREADS, xsmem_stage(A[0].stage, A[0].last), st>>>(B);
       return cudaGetLastError();
     } else {
       return cudaErrorNotSupported;
