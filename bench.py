@@ -441,6 +441,46 @@ def run_cufft_comparison(torch, N=N_MAIN, steps=3, warm=2):
     return out
 
 
+def run_closure_share(torch, N=64, steps=50):
+    """Device time of the coarse 64^3 FP32 step with the closure inside the step graph, against
+    the same step without it, and of the network forward alone on the N^3 features (CUDA
+    events): the kernel-time share of the wmma network in the modelled step."""
+    import numpy as np
+
+    from paper_1602_03638_gb300 import Solver, inputs, sgs
+
+    st = torch.cuda.current_stream()
+
+    def timed(fn, n):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(n):
+            fn()
+        e1.record(st)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    net = sgs.MLP(seed=0)
+    X = torch.randn(10, N ** 3, device="cuda", dtype=torch.float32)
+    T = torch.randn(6, N ** 3, device="cuda", dtype=torch.float32) * 0.01
+    net.set_normalisation(X, T)
+    out = {"N": N}
+    with Solver(N, 2e-3, 4e-3, "f32") as s:
+        s.set_stream(st)
+        s.set_state_spectral(inputs.isotropic_spectral(N, seed=5, k0=4.0, device="cuda").to(torch.complex64))
+        s.step(3)
+        out["step_ms_no_model"] = timed(lambda: s.step(1), steps)
+        s.set_closure(net)
+        s.step(3)
+        out["step_ms_model"] = timed(lambda: s.step(1), steps)
+        s.set_closure(None)
+    out["mlp_forward_ms"] = timed(lambda: net.forward(X), steps)
+    out["mlp_share_of_model_step"] = out["mlp_forward_ms"] / out["step_ms_model"]
+    out["closure_overhead_ratio"] = out["step_ms_model"] / out["step_ms_no_model"]
+    net.close()
+    return out
+
+
 def run_closure():
     """Learned subgrid closure: 512^3 FP32 DNS (this solver) -> box filter width 2 pi/64 -> 64^3,
     BF16 network trained on the GPU, coarse runs with and without it against the filtered DNS over
@@ -601,6 +641,7 @@ def run_ours(args):
         line["ensemble"] = run_ensemble(torch, np)
         line["cufft_comparison"] = run_cufft_comparison(torch)
         line["closure"] = run_closure()
+        line["closure"]["in_graph"] = run_closure_share(torch)
         line["error_vs_oracle"] = {"case": f"Taylor-Green {CPU_N}^3, {CPU_STEPS} RK4 steps, nu=1/1600, dt=1e-3",
                                    "rel_l2_f32": errs["f32"], "rel_l2_f64": errs["f64"]}
         line["cpu_baseline"] = {"value": CPU_N ** 3 * CPU_STEPS / secs, "unit": UNIT, "cores": cores, "kind": "oracle",

@@ -1,7 +1,8 @@
 // Pointwise subgrid-stress network 10 -> 64 (SiLU) -> 64 (SiLU) -> 6 on BF16
-// tensor cores (WMMA m16n16k16, FP32 accumulation): inference, training
-// (forward + backward with the weight-gradient products also on the tensor
-// cores) and Adam on FP32 master weights.
+// tensor cores with FP32 accumulation: inference on the 5th-generation tensor
+// cores (tcgen05.mma, accumulators in TMEM, k_mlp_tc), training (forward +
+// backward with the weight-gradient products also on the tensor cores, WMMA
+// m16n16k16 fragments, k_mlp<1>) and Adam on FP32 master weights.
 //
 // Parameter vector (floats), in this order:
 //   in_shift[10] in_scale[10] W1[10][64] b1[64] W2[64][64] b2[64] W3[64][6]
@@ -49,9 +50,12 @@ constexpr int OFF_A0 = 0, OFF_Z1 = OFF_A0 + A0_B, OFF_H1 = OFF_Z1 + Z1_B, OFF_Z2
 constexpr int BLK_W_B = NPACK * 2, BLK_G = TRAIN_END - TRAIN_BEGIN;
 constexpr int SMEM_B = BLK_W_B + WARPS * WARP_B + (BLK_G + 8) * 4;
 
-__device__ __forceinline__ float silu(float z) { return z / (1.f + expf(-z)); }
+
+// SiLU and its derivative with the fast exponential and division intrinsics (their
+// relative error, ~1e-6, is far below the BF16 rounding the activations then take)
+__device__ __forceinline__ float silu(float z) { return __fdividef(z, 1.f + __expf(-z)); }
 __device__ __forceinline__ float dsilu(float z) {
-  const float s = 1.f / (1.f + expf(-z));
+  const float s = __fdividef(1.f, 1.f + __expf(-z));
   return s * (1.f + z * (1.f - s));
 }
 
@@ -109,7 +113,9 @@ __global__ void __launch_bounds__(THREADS) k_mlp(const float* __restrict__ prm, 
   float* TT = reinterpret_cast<float*>(wb + OFF_T);
   float* acc = reinterpret_cast<float*>(sm + BLK_W_B + WARPS * WARP_B);  // [BLK_G] + loss
 
-  for (int i = threadIdx.x; i < NPACK; i += THREADS) sw[i] = wpack[i];
+  static_assert(NPACK % 8 == 0, "16-byte weight staging");
+  for (int i = threadIdx.x; i < NPACK / 8; i += THREADS)
+    reinterpret_cast<uint4*>(sw)[i] = reinterpret_cast<const uint4*>(wpack)[i];
   if (TRAIN)
     for (int i = threadIdx.x; i < BLK_G + 8; i += THREADS) acc[i] = 0.f;
   __syncthreads();
@@ -150,7 +156,7 @@ __global__ void __launch_bounds__(THREADS) k_mlp(const float* __restrict__ prm, 
     __syncwarp();
     for (int e = lane; e < 1024; e += 32) {
       const float z = Z1[e] + prm[O_B1 + (e & 63)];
-      Z1[e] = z;
+      if (TRAIN) Z1[e] = z;  // the backward pass reads the pre-activation
       H1[e] = __float2bfloat16(silu(z));
     }
     __syncwarp();
@@ -169,7 +175,7 @@ __global__ void __launch_bounds__(THREADS) k_mlp(const float* __restrict__ prm, 
     __syncwarp();
     for (int e = lane; e < 1024; e += 32) {
       const float z = Z2[e] + prm[O_B2 + (e & 63)];
-      Z2[e] = z;
+      if (TRAIN) Z2[e] = z;
       H2[e] = __float2bfloat16(silu(z));
     }
     __syncwarp();
@@ -314,6 +320,230 @@ __global__ void __launch_bounds__(THREADS) k_mlp(const float* __restrict__ prm, 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Inference on the 5th-generation tensor cores (tcgen05, sm_100-class): tiles of
+// 128 points, one TMEM lane (one thread of the 4 warps) per point. Operands are
+// BF16 in shared memory in the K-major layout without swizzle: 8 x 8 core
+// matrices of 128 contiguous bytes (row r of a core matrix at 16 r bytes), core
+// matrices adjacent along K 128 bytes apart (the leading-dimension offset) and
+// row groups of 8 rows K/8 * 128 bytes apart (the stride offset). One thread
+// issues the MMAs of a layer (K = 16 per instruction, FP32 accumulation in TMEM)
+// and commits them to an mbarrier; then every thread reads its row of the
+// accumulator (tcgen05.ld), adds the bias, applies SiLU and writes the BF16 row
+// of the next layer's A operand.
+//   layer 1: D1 (TMEM columns 0..63)   = X (128 x 16) . W1 (16 x 64)
+//   layer 2: D2 (TMEM columns 64..127) = H1 (128 x 64) . W2 (64 x 64)
+//   layer 3: D3 (TMEM columns 0..15)   = H2 (128 x 64) . W3 (64 x 16, columns >= 6 zero)
+// ---------------------------------------------------------------------------
+constexpr int TC_M = 128, TC_THREADS = 128, TC_TMEM_COLS = 128;
+// shared memory: A operands X (4 KB), H1, H2 (16 KB each); B operands W1^T (64 x 16, 2 KB),
+// W2^T (64 x 64, 8 KB), W3^T (16 x 64, 2 KB); then the mbarrier and the TMEM address
+constexpr int TC_X = 0, TC_H1 = TC_X + 128 * 16 * 2, TC_H2 = TC_H1 + 128 * 64 * 2, TC_W1 = TC_H2 + 128 * 64 * 2,
+              TC_W2 = TC_W1 + 64 * 16 * 2, TC_W3 = TC_W2 + 64 * 64 * 2, TC_BAR = TC_W3 + 16 * 64 * 2,
+              TC_SMEM = TC_BAR + 16;
+constexpr unsigned long long TC_WAIT_NS = 1000000000ull;  // 1 s bound on every mbarrier wait
+
+// byte offset of element (r, k) of a K-major operand with K columns in the core-matrix layout
+__device__ __forceinline__ int tc_off(int r, int k, int K) {
+  return ((r >> 3) * (K >> 3) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+// shared-memory matrix descriptor: start address, leading (K) and stride (row-group)
+// byte offsets, the fixed version bits 46-47 = 1, no swizzle
+__device__ __forceinline__ unsigned long long tc_desc(unsigned saddr, unsigned lbo, unsigned sbo) {
+  return (unsigned long long)((saddr & 0x3FFFF) >> 4) | ((unsigned long long)(lbo >> 4) << 16) |
+         ((unsigned long long)(sbo >> 4) << 32) | (1ull << 46);
+}
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major, M x N
+__host__ __device__ constexpr unsigned tc_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);
+}
+__device__ __forceinline__ void tc_mma(unsigned dt, unsigned long long ad, unsigned long long bd, unsigned idesc,
+                                       int acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(unsigned bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar) : "memory");
+}
+// waits for the phase `parity` of the mbarrier; false if it did not complete within TC_WAIT_NS
+__device__ __forceinline__ bool tc_wait(unsigned bar, unsigned parity) {
+  unsigned long long t0 = 0;
+  for (int it = 0;; ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (it == 0) t0 = t;
+    else if (t - t0 > TC_WAIT_NS) return false;
+  }
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// 16 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tc_ld16(unsigned taddr, float (&v)[16]) {
+  unsigned r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// bias + SiLU of this thread's 64 accumulator columns at TMEM column c0, written as the
+// thread's BF16 row of a K = 64 A operand at `dst`
+__device__ __forceinline__ void tc_hidden(unsigned trow, int c0, const float* __restrict__ bias, unsigned char* dst,
+                                          int row) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float v[16];
+    tc_ld16(trow + c0 + 16 * q, v);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {  // two 8-element core-matrix rows of 16 bytes
+      __align__(16) bf o[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) o[i] = __float2bfloat16(silu(v[8 * h + i] + bias[16 * q + 8 * h + i]));
+      *reinterpret_cast<uint4*>(dst + tc_off(row, 16 * q + 8 * h, 64)) = *reinterpret_cast<const uint4*>(o);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(TC_THREADS) k_mlp_tc(const float* __restrict__ prm, const bf* __restrict__ wpack,
+                                                       const float* __restrict__ X, int P, float* __restrict__ Y,
+                                                       int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  __shared__ unsigned s_taddr;
+  __shared__ float s_b[2 * NH + 16];  // b1, b2, b3
+  const int t = threadIdx.x, warp = t >> 5;
+  const unsigned sbase = (unsigned)__cvta_generic_to_shared(tsm);
+  const unsigned bar = sbase + TC_BAR;
+  // B operands from the packed weights: W^T rows n, columns k
+  for (int i = t; i < 64 * 16; i += TC_THREADS) {  // W1^T (64 x 16): W1p[k][n]
+    const int n = i >> 4, k = i & 15;
+    *reinterpret_cast<bf*>(tsm + TC_W1 + tc_off(n, k, 16)) = wpack[PW1 + k * 64 + n];
+  }
+  for (int i = t; i < 64 * 64; i += TC_THREADS) {  // W2^T (64 x 64): W2[k][n]
+    const int n = i >> 6, k = i & 63;
+    *reinterpret_cast<bf*>(tsm + TC_W2 + tc_off(n, k, 64)) = wpack[PW2 + k * 64 + n];
+  }
+  for (int i = t; i < 16 * 64; i += TC_THREADS) {  // W3^T (16 x 64): W3p[k][n]
+    const int n = i >> 6, k = i & 63;
+    *reinterpret_cast<bf*>(tsm + TC_W3 + tc_off(n, k, 64)) = wpack[PW3 + k * 16 + n];
+  }
+  for (int i = t; i < 2 * NH + 16; i += TC_THREADS)
+    s_b[i] = i < NH ? prm[O_B1 + i] : (i < 2 * NH ? prm[O_B2 + i - NH] : (i - 2 * NH < NOUT ? prm[O_B3 + i - 2 * NH] : 0.f));
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     (unsigned)__cvta_generic_to_shared(&s_taddr)),
+                 "r"(TC_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  proxy_fence();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned tmem = s_taddr;
+  const unsigned trow = tmem + ((unsigned)(32 * warp) << 16);  // this warp's 32 lanes
+  const unsigned long long dW1 = tc_desc(sbase + TC_W1, 128, 2 * 128);
+  const unsigned long long dW2 = tc_desc(sbase + TC_W2, 128, 8 * 128);
+  const unsigned long long dW3 = tc_desc(sbase + TC_W3, 128, 8 * 128);
+  const unsigned long long dX = tc_desc(sbase + TC_X, 128, 2 * 128);
+  const unsigned long long dH1 = tc_desc(sbase + TC_H1, 128, 8 * 128);
+  const unsigned long long dH2 = tc_desc(sbase + TC_H2, 128, 8 * 128);
+  constexpr unsigned ID64 = tc_idesc(128, 64), ID16 = tc_idesc(128, 16);
+  constexpr unsigned long long KSTEP = (2 * 128) >> 4;  // descriptor start address step of K = 16
+  unsigned phase = 0;
+  bool ok = true;
+  const int ntiles = (P + TC_M - 1) / TC_M;
+  for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    const int p = tile * TC_M + t;
+    {  // A operand of layer 1: the standardised features of point p, BF16, features >= 10 zero
+      __align__(16) bf o[16];
+#pragma unroll
+      for (int f = 0; f < 16; ++f) {
+        float v = 0.f;
+        if (f < NIN && p < P) v = (X[(size_t)f * P + p] - prm[O_INSH + f]) * prm[O_INSC + f];
+        o[f] = __float2bfloat16(v);
+      }
+      *reinterpret_cast<uint4*>(tsm + TC_X + tc_off(t, 0, 16)) = *reinterpret_cast<const uint4*>(o);
+      *reinterpret_cast<uint4*>(tsm + TC_X + tc_off(t, 8, 16)) = *reinterpret_cast<const uint4*>(o + 8);
+    }
+    proxy_fence();
+    tc_fence_before();
+    __syncthreads();
+    if (t == 0) {
+      tc_fence_after();
+      tc_mma(tmem, dX, dW1, ID64, 0);
+      tc_commit(bar);
+    }
+    // every thread takes the same barriers whatever its waits returned; the block leaves
+    // the loop together at the end of the tile (__syncthreads_and)
+    ok = tc_wait(bar, phase) && ok;
+    phase ^= 1;
+    tc_fence_after();
+    tc_hidden(trow, 0, s_b, tsm + TC_H1, t);
+    proxy_fence();
+    tc_fence_before();
+    __syncthreads();
+    if (t == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) tc_mma(tmem + 64, dH1 + kk * KSTEP, dW2 + kk * KSTEP, ID64, kk);
+      tc_commit(bar);
+    }
+    ok = tc_wait(bar, phase) && ok;
+    phase ^= 1;
+    tc_fence_after();
+    tc_hidden(trow, 64, s_b + NH, tsm + TC_H2, t);
+    proxy_fence();
+    tc_fence_before();
+    __syncthreads();
+    if (t == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) tc_mma(tmem, dH2 + kk * KSTEP, dW3 + kk * KSTEP, ID16, kk);
+      tc_commit(bar);
+    }
+    ok = tc_wait(bar, phase) && ok;
+    phase ^= 1;
+    tc_fence_after();
+    {
+      float v[16];
+      tc_ld16(trow, v);
+      if (p < P) {
+#pragma unroll
+        for (int c = 0; c < NOUT; ++c) Y[(size_t)c * P + p] = (v[c] + s_b[2 * NH + c]) * prm[O_OUTSC + c] + prm[O_OUTSH + c];
+      }
+    }
+    tc_fence_before();
+    ok = __syncthreads_and(ok);  // shared operands and TMEM columns are free for the next tile
+    tc_fence_after();
+  }
+  if (!ok && t == 0) atomicExch(err, 1);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+}
+
 // Adam on the trainable range; moments m, v; step t >= 1; clears the gradient sums.
 __global__ void k_adam(float* __restrict__ prm, float* __restrict__ gsum, float* __restrict__ m,
                        float* __restrict__ v, float lr, float b1, float b2, float eps, float c1, float c2) {
@@ -336,6 +566,7 @@ struct dns_mlp {
   float* m = nullptr;
   float* v = nullptr;
   bf* pack = nullptr;  // NPACK (device)
+  int* err = nullptr;  // device flag: a tensor-core wait of the inference kernel gave up
   int t = 0;           // Adam steps taken
 };
 
@@ -351,6 +582,19 @@ int mlp_fail(int code, const char* msg) {
     cudaError_t e_ = (call);                       \
     if (e_ != cudaSuccess) return mlp_fail(DNS_ERR_CUDA, where); \
   } while (0)
+
+// inference grid: four blocks per SM (4 x 128 TMEM columns fill an SM's 512), each block
+// walking several 128-point tiles
+int mlp_blocks_tc(int P) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 148;
+  }
+  const int tiles = (P + TC_M - 1) / TC_M;
+  return tiles < 4 * sms ? (tiles < 1 ? 1 : tiles) : 4 * sms;
+}
 
 int mlp_blocks(int P) {
   int tiles = (P + 15) / 16;
@@ -409,11 +653,20 @@ __global__ void __launch_bounds__(NORM_THREADS) k_norm(float* __restrict__ prm, 
   }
 }
 
+// Reports (and clears) a tensor-core wait of the inference kernel that gave up; synchronises.
+int mlp_check_err(dns_mlp* n, const char* where) {
+  int err = 0;
+  MLP_CUDA(cudaMemcpy(&err, n->err, sizeof(int), cudaMemcpyDeviceToHost), where);
+  if (!err) return DNS_OK;
+  MLP_CUDA(cudaMemset(n->err, 0, sizeof(int)), where);
+  return mlp_fail(DNS_ERR_TIMEOUT, "dns_mlp: an inference kernel's tensor-core wait gave up after 1 s; its output is not valid");
+}
+
 }  // namespace
 
 namespace dns {
 cudaError_t mlp_forward_async(::dns_mlp* n, const float* X, float* Y, int P, cudaStream_t st) {
-  k_mlp<0><<<mlp_blocks(P), THREADS, SMEM_B, st>>>(n->prm, n->pack, X, P, Y, nullptr, nullptr);
+  k_mlp_tc<<<mlp_blocks_tc(P), TC_THREADS, TC_SMEM, st>>>(n->prm, n->pack, X, P, Y, n->err);
   return cudaGetLastError();
 }
 }  // namespace dns
@@ -438,11 +691,13 @@ int dns_mlp_create(dns_mlp** out) {
   if (e == cudaSuccess) e = cudaMalloc(&n->m, NPARAM * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&n->v, NPARAM * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&n->pack, NPACK * sizeof(bf));
+  if (e == cudaSuccess) e = cudaMalloc(&n->err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(n->err, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(n->prm, 0, NPARAM * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(n->gsum, 0, (NPARAM + 1) * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(n->m, 0, NPARAM * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(n->v, 0, NPARAM * sizeof(float));
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_B);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_B);
   if (e != cudaSuccess) {
     dns_mlp_destroy(n);
@@ -460,6 +715,7 @@ int dns_mlp_destroy(dns_mlp* n) {
   cudaFree(n->m);
   cudaFree(n->v);
   cudaFree(n->pack);
+  cudaFree(n->err);
   delete n;
   return DNS_OK;
 }
@@ -480,12 +736,12 @@ int dns_mlp_get_params(dns_mlp* n, float* host, int count) {
   if (!n || !host || count != NPARAM) return mlp_fail(DNS_ERR_ARG, "dns_mlp_get_params: need 5286 host floats");
   MLP_CUDA(cudaDeviceSynchronize(), "dns_mlp_get_params");
   MLP_CUDA(cudaMemcpy(host, n->prm, NPARAM * sizeof(float), cudaMemcpyDeviceToHost), "dns_mlp_get_params copy");
-  return DNS_OK;
+  return mlp_check_err(n, "dns_mlp_get_params");
 }
 
 int dns_mlp_forward(dns_mlp* n, const float* X, float* Y, int P, void* stream) {
   if (!n || !X || !Y || P < 1) return mlp_fail(DNS_ERR_ARG, "dns_mlp_forward: bad arguments");
-  k_mlp<0><<<mlp_blocks(P), THREADS, SMEM_B, (cudaStream_t)stream>>>(n->prm, n->pack, X, P, Y, nullptr, nullptr);
+  k_mlp_tc<<<mlp_blocks_tc(P), TC_THREADS, TC_SMEM, (cudaStream_t)stream>>>(n->prm, n->pack, X, P, Y, n->err);
   MLP_CUDA(cudaGetLastError(), "dns_mlp_forward launch");
   return DNS_OK;
 }

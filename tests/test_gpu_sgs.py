@@ -105,6 +105,28 @@ def test_network_forward_matches_bf16_reference():
     net.close()
 
 
+def test_tensor_core_forward_agrees_with_the_training_kernel():
+    """Inference (tcgen05, 128-point tiles in TMEM) against the training kernel's own forward
+    pass (wmma): the loss of the inferred stress equals the loss the training kernel reports."""
+    sgs = _sgs()
+    rng = np.random.default_rng(15)
+    P = 3 * 128 + 77
+    X = rng.normal(size=(P, 10))
+    Tt = rng.normal(size=(P, 6))
+    p = _params_with_norm(7, X)
+    net = sgs.MLP(sg.flatten(p).astype(np.float32))
+    pv = sg.unflatten(net.get_params().astype(np.float64))
+    Xd = torch.from_numpy(X.T.astype(np.float32)).cuda().contiguous()
+    Td = torch.from_numpy(Tt.T.astype(np.float32)).cuda().contiguous()
+    tau = net.forward(Xd).cpu().numpy().astype(np.float64).T
+    y = (tau - pv["out_shift"]) / pv["out_scale"]
+    tn = (Tt.astype(np.float32).astype(np.float64) - pv["out_shift"]) / pv["out_scale"]
+    loss_tc = float(np.mean((y - tn) ** 2))
+    loss_train, _ = net.loss_grad(Xd, Td)
+    assert abs(loss_tc - loss_train) < 1e-4 * loss_train, (loss_tc, loss_train)
+    net.close()
+
+
 def test_network_gradient_matches_bf16_reference():
     sgs = _sgs()
     rng = np.random.default_rng(6)
