@@ -661,6 +661,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, forms and the CPU baseline")
     ap.add_argument("--N", type=int, default=N_MAIN, help="grid size of the timed workload (profiling runs only)")
+    ap.add_argument("--closure-only", action="store_true",
+                    help="print only the in-graph closure timing at 64^3 (run_closure_share) and exit")
     ap.add_argument("--schedule", choices=["auto", "plane", "four"], default="auto",
                     help="stage schedule of the timed solver: plane pass where compiled (auto), or the four-pass "
                          "schedule (profiling comparisons only)")
@@ -669,6 +671,14 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.closure_only:
+        import torch
+
+        from paper_1602_03638_gb300 import build
+
+        build.build()
+        print(json.dumps(run_closure_share(torch)), flush=True)
+        return 0
     return run_ours(args)
 
 
