@@ -14,6 +14,9 @@ physical   u[c, i, j, k] = u_c(x_i, y_j, z_k),  x_i = 2*pi*i/N       (Eq. realme
 spectral  uh[c, l, m, n]: kx = fftfreq order over l, ky = fftfreq order
            over m, kz = n = 0..N/2 with the last entry stored as +N/2
            (the wavenumber listing of Sec. 3.1; Eq. kmesh)
+Every function also takes per-direction point counts (Nx, Ny, Nz) (the Sec. 2
+footnote: other numbers of points per direction); N then stands for the count of
+the direction in question, and N^3 for Nx Ny Nz.
 
 Readings of the paper that this module takes (each is stated where used):
   * F is the unnormalised forward transform with e^{-ik.x}; F^{-1} carries
@@ -79,37 +82,58 @@ def set_workers(n: int) -> None:
 # Mesh and wavenumbers (Eq. realmesh, Eq. kmesh, Sec. 3.1)
 # --------------------------------------------------------------------------
 
-def mesh(N: int, lengths=None) -> np.ndarray:
-    """Physical mesh x_i = 2*pi*i/N in each direction (Eq. realmesh); shape (3,N,N,N).
-    With box lengths (Lx, Ly, Lz) (Sec. 2 footnote) x_i = Lx*i/N, and so on."""
+def dims(N) -> tuple:
+    """(Nx, Ny, Nz) from one point count or three (Sec. 2 footnote: the number of points
+    may differ per direction); each must be even."""
+    n = (int(N),) * 3 if np.ndim(N) == 0 else tuple(int(v) for v in N)
+    if len(n) != 3 or any(v < 2 or v % 2 for v in n):
+        raise ValueError("N must be even in every direction")
+    return n
+
+
+def shape_of(uh: np.ndarray) -> tuple:
+    """(Nx, Ny, Nz) of a half spectrum (..., Nx, Ny, Nz/2+1)."""
+    return (uh.shape[-3], uh.shape[-2], 2 * (uh.shape[-1] - 1))
+
+
+def mesh(N, lengths=None) -> np.ndarray:
+    """Physical mesh x_i = 2*pi*i/N in each direction (Eq. realmesh); shape (3,Nx,Ny,Nz).
+    With box lengths (Lx, Ly, Lz) (Sec. 2 footnote) x_i = Lx*i/Nx, and so on; N may be
+    one point count or three (Nx, Ny, Nz)."""
+    n = dims(N)
     L = (2.0 * np.pi,) * 3 if lengths is None else tuple(float(v) for v in lengths)
-    xs = [L[d] * np.arange(N, dtype=np.float64) / N for d in range(3)]
+    xs = [L[d] * np.arange(n[d], dtype=np.float64) / n[d] for d in range(3)]
     return np.array(np.meshgrid(*xs, indexing="ij"))
 
 
-def wavenumbers(N: int) -> np.ndarray:
-    """Integer wavenumber mesh K of shape (3, N, N, N/2+1) (Sec. 3.1).
+def wavenumbers(N) -> np.ndarray:
+    """Integer wavenumber mesh K of shape (3, Nx, Ny, Nz/2+1) (Sec. 3.1).
 
-    kx and ky follow the FFT ordering (0..N/2-1, -N/2..-1); kz is the
-    real-transform axis with entries 0..N/2, the last one stored as +N/2.
+    kx and ky follow the FFT ordering (0..N/2-1, -N/2..-1) of their own point
+    counts; kz is the real-transform axis with entries 0..Nz/2, the last one stored
+    as +Nz/2.
     """
-    if N % 2:
-        raise ValueError("N must be even")
-    k = np.rint(sfft.fftfreq(N, 1.0 / N)).astype(np.int64)
-    kz = k[: N // 2 + 1].copy()
+    nx, ny, nz = dims(N)
+    kx = np.rint(sfft.fftfreq(nx, 1.0 / nx)).astype(np.int64)
+    ky = np.rint(sfft.fftfreq(ny, 1.0 / ny)).astype(np.int64)
+    kz = np.rint(sfft.fftfreq(nz, 1.0 / nz)).astype(np.int64)[: nz // 2 + 1].copy()
     kz[-1] *= -1
-    return np.array(np.meshgrid(k, k, kz, indexing="ij"), dtype=np.int64)
+    return np.array(np.meshgrid(kx, ky, kz, indexing="ij"), dtype=np.int64)
 
 
-def dealias_mask(N: int, variant: int = 0) -> np.ndarray:
+def dealias_mask(N, variant: int = 0) -> np.ndarray:
     """2/3-rule box mask on the half spectrum (Sec. 3.1, dealiasing paragraph).
 
-    variant 0: keep modes with |kx|,|ky|,|kz| < N/3 ("2/3 of the Nyquist mode").
-    variant 1: the Appendix script's cut-off 2/3*(N/2+1), also strict.
+    variant 0: keep modes with |k_i| < N_i/3 ("2/3 of the Nyquist mode") in each
+    direction i, with that direction's point count.
+    variant 1: the Appendix script's cut-off 2/3*(N_i/2+1), also strict.
     """
     K = wavenumbers(N)
-    kmax = N / 3.0 if variant == 0 else 2.0 / 3.0 * (N // 2 + 1)
-    return (np.abs(K[0]) < kmax) & (np.abs(K[1]) < kmax) & (np.abs(K[2]) < kmax)
+    keep = np.ones(K.shape[1:], dtype=bool)
+    for d, n in enumerate(dims(N)):
+        kmax = n / 3.0 if variant == 0 else 2.0 / 3.0 * (n // 2 + 1)
+        keep &= np.abs(K[d]) < kmax
+    return keep
 
 
 @dataclass
@@ -118,10 +142,10 @@ class Grid:
 
     With box lengths (Lx, Ly, Lz) the wavenumber of index l along x is 2*pi*l/Lx
     (Sec. 2 footnote; Sec. 3.1: other box sizes by scaling); the 2/3 mask stays on
-    the integer indices.
+    the integer indices. N is one point count or three (Nx, Ny, Nz).
     """
 
-    N: int
+    N: int | tuple
     variant: int = 0
     lengths: tuple | None = None
 
@@ -144,33 +168,32 @@ def forward(u: np.ndarray) -> np.ndarray:
     """F: unnormalised real-to-complex 3D DFT with e^{-ik.x} over the last 3 axes.
 
     The real transform is taken along z (last axis), then complex ones along
-    y and x (Eq. fft). Output shape (..., N, N, N/2+1).
+    y and x (Eq. fft). Output shape (..., Nx, Ny, Nz/2+1).
     """
     return sfft.rfftn(np.asarray(u, dtype=np.float64), axes=(-3, -2, -1), workers=WORKERS)
 
 
 def inverse(uh: np.ndarray) -> np.ndarray:
-    """F^{-1}: complex-to-real 3D inverse DFT including the 1/N^3 factor (Eq. ifft).
+    """F^{-1}: complex-to-real 3D inverse DFT including the 1/(Nx Ny Nz) factor (Eq. ifft).
 
     Complex inverse transforms along x and y, then the real one along z; the
-    z step uses only the real parts of the kz=0 and kz=N/2 coefficients.
+    z step uses only the real parts of the kz=0 and kz=Nz/2 coefficients.
     """
-    N = uh.shape[-3]
-    return sfft.irfftn(np.asarray(uh, dtype=np.complex128), s=(N, N, N), axes=(-3, -2, -1), workers=WORKERS)
+    return sfft.irfftn(np.asarray(uh, dtype=np.complex128), s=shape_of(uh), axes=(-3, -2, -1), workers=WORKERS)
 
 
 def zero_nyquist(uh: np.ndarray) -> np.ndarray:
-    """Zero every mode with |kx| = N/2, |ky| = N/2 or kz = N/2 (Sec. 3.3 drops these)."""
-    N = uh.shape[-3]
+    """Zero every mode with |kx| = Nx/2, |ky| = Ny/2 or kz = Nz/2 (Sec. 3.3 drops these)."""
+    nx, ny, nz = shape_of(uh)
     uh = uh.copy()
-    uh[..., N // 2, :, :] = 0.0
-    uh[..., :, N // 2, :] = 0.0
-    uh[..., :, :, N // 2] = 0.0
+    uh[..., nx // 2, :, :] = 0.0
+    uh[..., :, ny // 2, :] = 0.0
+    uh[..., :, :, nz // 2] = 0.0
     return uh
 
 
 def to_spectral(u: np.ndarray) -> np.ndarray:
-    """State from a physical velocity (3,N,N,N): F of each component, Nyquist zeroed."""
+    """State from a physical velocity (3,Nx,Ny,Nz): F of each component, Nyquist zeroed."""
     return zero_nyquist(forward(u))
 
 
@@ -269,7 +292,7 @@ def lsrk_step(uh: np.ndarray, g: Grid, nu: float, dt: float, A, B) -> np.ndarray
     return u
 
 
-def run(uh: np.ndarray, N: int, nu: float, dt: float, nsteps: int, variant: int = 0,
+def run(uh: np.ndarray, N, nu: float, dt: float, nsteps: int, variant: int = 0,
         paper_reuse_u: bool = False, u0_phys: np.ndarray | None = None, scheme: str = "rk4",
         lengths=None) -> np.ndarray:
     """Advance ``nsteps`` steps (the step count is round(T/dt), reading of the while loop)
@@ -307,10 +330,9 @@ def run(uh: np.ndarray, N: int, nu: float, dt: float, nsteps: int, variant: int 
 # --------------------------------------------------------------------------
 
 def energy(uh: np.ndarray) -> float:
-    """E = 1/2 * sum(U*U) / N^3 on the physical mesh (the Appendix's final reduce)."""
+    """E = 1/2 * sum(U*U) / (Nx Ny Nz) on the physical mesh (the Appendix's final reduce)."""
     u = inverse(uh)
-    N = uh.shape[-3]
-    return float(0.5 * np.sum(u * u) / N**3)
+    return float(0.5 * np.sum(u * u) / float(np.prod(shape_of(uh))))
 
 
 def diagnostics(uh: np.ndarray, nu: float, lengths=None) -> dict:
@@ -320,11 +342,11 @@ def diagnostics(uh: np.ndarray, nu: float, lengths=None) -> dict:
     without defining it; this is the standard form for periodic incompressible
     flow), H = <u . omega>, Z = 1/2 <|omega|^2>, div = max_x |F^{-1}(i k . u_hat)|.
     """
-    N = uh.shape[-3]
-    g = Grid(N, 0, lengths)
+    n = shape_of(uh)
+    g = Grid(n, 0, lengths)
     u = inverse(uh)
     w = inverse(curl_hat(uh, g))
-    n3 = float(N) ** 3
+    n3 = float(np.prod(n))
     div = inverse(1j * np.sum(g.K * uh, axis=0))
     return {
         "energy": float(0.5 * np.sum(u * u) / n3),
@@ -338,14 +360,14 @@ def diagnostics(uh: np.ndarray, nu: float, lengths=None) -> dict:
 def energy_spectrum(uh: np.ndarray) -> np.ndarray:
     """Shell-summed energy spectrum E(k), k = round(|k|) (for closure and decay checks).
 
-    Uses the half-spectrum weight 1 at kz = 0 and kz = N/2 and 2 otherwise,
+    Uses the half-spectrum weight 1 at kz = 0 and kz = Nz/2 and 2 otherwise,
     so that sum(E(k)) equals the grid-mean energy.
     """
-    N = uh.shape[-3]
-    K = wavenumbers(N)
+    n = shape_of(uh)
+    K = wavenumbers(n)
     kmag = np.rint(np.sqrt(np.sum(K * K, axis=0).astype(np.float64))).astype(np.int64)
     w = np.full(K.shape[1:], 2.0)
     w[:, :, 0] = 1.0
-    w[:, :, N // 2] = 1.0
-    e = 0.5 * w * np.sum(np.abs(uh) ** 2, axis=0) / float(N) ** 6
+    w[:, :, n[2] // 2] = 1.0
+    e = 0.5 * w * np.sum(np.abs(uh) ** 2, axis=0) / float(np.prod(n)) ** 2
     return np.bincount(kmag.ravel(), weights=e.ravel())

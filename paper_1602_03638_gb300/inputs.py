@@ -48,46 +48,49 @@ def taylor_green_torch(N: int, device="cpu", dtype=torch.float32) -> torch.Tenso
     return u
 
 
-def abc_flow(N: int, A: float = 1.0, B: float = 1.0, C: float = 1.0, dtype=np.float64) -> np.ndarray:
-    """ABC flow u = (A sin z + C cos y, B sin x + A cos z, C sin y + B cos x); curl u = u."""
-    x = 2.0 * np.pi * np.arange(N) / N
-    X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
-    u = np.empty((3, N, N, N), dtype=dtype)
+def abc_flow(N, A: float = 1.0, B: float = 1.0, C: float = 1.0, dtype=np.float64) -> np.ndarray:
+    """ABC flow u = (A sin z + C cos y, B sin x + A cos z, C sin y + B cos x); curl u = u.
+    N: one point count or three (Nx, Ny, Nz)."""
+    n = _dims(N)
+    X, Y, Z = np.meshgrid(*(2.0 * np.pi * np.arange(v) / v for v in n), indexing="ij")
+    u = np.empty((3,) + n, dtype=dtype)
     u[0] = A * np.sin(Z) + C * np.cos(Y)
     u[1] = B * np.sin(X) + A * np.cos(Z)
     u[2] = C * np.sin(Y) + B * np.cos(X)
     return u
 
 
-def _half_spectrum_k(N: int, device, dtype):
-    k = torch.arange(N, device=device)
-    k = torch.where(k < N // 2, k, k - N).to(dtype)
-    kz = torch.arange(N // 2 + 1, device=device).to(dtype)
-    return k, kz
+def _dims(N) -> tuple:
+    return (int(N),) * 3 if np.ndim(N) == 0 else tuple(int(v) for v in N)
 
 
-def isotropic_spectral(N: int, seed: int = 0, k0: float = 4.0, energy: float = 1.0,
+def _freq(n: int, device, dtype):
+    k = torch.arange(n, device=device)
+    return torch.where(k < n // 2, k, k - n).to(dtype)
+
+
+def isotropic_spectral(N, seed: int = 0, k0: float = 4.0, energy: float = 1.0,
                        device="cpu", dtype=torch.complex128) -> torch.Tensor:
-    """Random divergence-free field in the half spectrum (3, N, N, N/2+1), paper order.
+    """Random divergence-free field in the half spectrum (3, Nx, Ny, Nz/2+1), paper order.
 
-    Each mode with 0 < |k| and |k_i| < N/3 gets amplitude sqrt(E(|k|)/(4 pi |k|^2)),
-    E(k) = k^4 exp(-2 (k/k0)^2), along a random direction perpendicular to k,
-    with uniform random phases (Rogallo 1981 style). The kz = 0 plane is made
-    Hermitian by averaging each mode with the conjugate of its mirror, Nyquist
-    modes are zero, and the field is scaled so that
-    1/2 N^-6 sum_k w_k |u_hat_k|^2 = ``energy`` (w = 1 at kz = 0, else 2).
+    N is one point count or three (Nx, Ny, Nz). Each mode with 0 < |k| and
+    |k_i| < N_i/3 gets amplitude sqrt(E(|k|)/(4 pi |k|^2)), E(k) = k^4 exp(-2 (k/k0)^2),
+    along a random direction perpendicular to k, with uniform random phases (Rogallo
+    1981 style). The kz = 0 plane is made Hermitian by averaging each mode with the
+    conjugate of its mirror, Nyquist modes are zero, and the field is scaled so that
+    1/2 (Nx Ny Nz)^-2 sum_k w_k |u_hat_k|^2 = ``energy`` (w = 1 at kz = 0, else 2).
     Random numbers come from a seeded torch generator on ``device``.
     """
+    nx, ny, nz = _dims(N)
+    h = nz // 2 + 1
     rdt = torch.float64 if dtype == torch.complex128 else torch.float32
     gen = torch.Generator(device=device)
     gen.manual_seed(int(seed))
-    k, kz = _half_spectrum_k(N, device, rdt)
-    KX = k[:, None, None].expand(N, N, N // 2 + 1)
-    KY = k[None, :, None].expand(N, N, N // 2 + 1)
-    KZ = kz[None, None, :].expand(N, N, N // 2 + 1)
+    KX = _freq(nx, device, rdt)[:, None, None].expand(nx, ny, h)
+    KY = _freq(ny, device, rdt)[None, :, None].expand(nx, ny, h)
+    KZ = torch.arange(h, device=device).to(rdt)[None, None, :].expand(nx, ny, h)
     kk = torch.sqrt(KX * KX + KY * KY + KZ * KZ)
-    kmax = N / 3.0
-    inside = (KX.abs() < kmax) & (KY.abs() < kmax) & (KZ < kmax) & (kk > 0)
+    inside = (KX.abs() < nx / 3.0) & (KY.abs() < ny / 3.0) & (KZ < nz / 3.0) & (kk > 0)
     kk_safe = torch.where(kk > 0, kk, torch.ones_like(kk))
     spec = kk_safe ** 4 * torch.exp(-2.0 * (kk_safe / k0) ** 2)
     amp = torch.sqrt(spec / (4.0 * math.pi * kk_safe ** 2)) * inside
@@ -107,7 +110,7 @@ def isotropic_spectral(N: int, seed: int = 0, k0: float = 4.0, energy: float = 1
     e2y = (KZ * e1x - KX * e1z) / kk_safe
     e2z = (KX * e1y - KY * e1x) / kk_safe
 
-    shape = (N, N, N // 2 + 1)
+    shape = (nx, ny, h)
     th1 = torch.rand(shape, generator=gen, device=device, dtype=rdt) * (2.0 * math.pi)
     th2 = torch.rand(shape, generator=gen, device=device, dtype=rdt) * (2.0 * math.pi)
     phi = torch.rand(shape, generator=gen, device=device, dtype=rdt) * (2.0 * math.pi)
@@ -116,19 +119,20 @@ def isotropic_spectral(N: int, seed: int = 0, k0: float = 4.0, energy: float = 1
     uh = torch.stack([a1 * e1x + a2 * e2x, a1 * e1y + a2 * e2y, a1 * e1z + a2 * e2z]).to(dtype)
 
     # Hermitian kz = 0 plane: u(-kx,-ky,0) = conj(u(kx,ky,0)).
-    idx = (-torch.arange(N, device=device)) % N
+    ix = (-torch.arange(nx, device=device)) % nx
+    iy = (-torch.arange(ny, device=device)) % ny
     p0 = uh[:, :, :, 0]
-    mirror = p0[:, idx][:, :, idx]
+    mirror = p0[:, ix][:, :, iy]
     uh[:, :, :, 0] = 0.5 * (p0 + mirror.conj())
-    uh[:, N // 2, :, :] = 0
-    uh[:, :, N // 2, :] = 0
-    uh[:, :, :, N // 2] = 0
+    uh[:, nx // 2, :, :] = 0
+    uh[:, :, ny // 2, :] = 0
+    uh[:, :, :, nz // 2] = 0
     uh[:, 0, 0, 0] = 0
 
-    w = torch.full((N // 2 + 1,), 2.0, device=device, dtype=rdt)
+    w = torch.full((h,), 2.0, device=device, dtype=rdt)
     w[0] = 1.0
-    w[N // 2] = 1.0
-    e = 0.5 * torch.sum(w * torch.sum(uh.real ** 2 + uh.imag ** 2, dim=0)) / float(N) ** 6
+    w[nz // 2] = 1.0
+    e = 0.5 * torch.sum(w * torch.sum(uh.real ** 2 + uh.imag ** 2, dim=0)) / (float(nx) * ny * nz) ** 2
     uh *= math.sqrt(energy / float(e))
     return uh
 
