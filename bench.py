@@ -60,6 +60,8 @@ PAPER_TG512_PTS_STEPS_PER_S = 6.2e7  # Sec. 4 verification run, 2048 Shaheen cor
 
 def pass_bytes(N, real_bytes, stages=4):
     """Algorithmic bytes per launch of each kernel class (mean over the RK4 stages).
+    N: one point count, or (Nx, Ny, Nz) for a grid with other counts per direction (then
+    FV = Nx Ny (Nz/2), kc = (Nz+2)//3 planes and the rows |ky| < Ny/3 of Ny).
 
     Counted from the 2/3 mask: a field-volume FV = N^2 (N/2) complex values (the stored half
     spectrum; the kz = N/2 plane is identically zero); kc = (N+2)//3 planes kz < N/3 and
@@ -73,11 +75,12 @@ def pass_bytes(N, real_bytes, stages=4):
     RK state per stage: stage 0 reads u (3) and writes u1, us (6); a middle stage reads us,
     u1, u (9) and writes u1, us (6); the last reads us, u1 (6) and writes u (3).
     """
-    M = N // 2
-    fv = N * N * M * 2 * real_bytes
-    kc = (N + 2) // 3
+    nx, ny, nz = (N,) * 3 if isinstance(N, int) else tuple(N)
+    M = nz // 2
+    fv = nx * ny * M * 2 * real_bytes
+    kc = (nz + 2) // 3
     zk = kc / M
-    yk = (2 * kc - 1) / N
+    yk = (2 * ((ny + 2) // 3) - 1) / ny
     rk = []
     for s_ in range(stages):
         if stages == 1:
@@ -95,7 +98,8 @@ def pass_bytes(N, real_bytes, stages=4):
 
 
 def cv_bytes(N, real_bytes):
-    return N * N * (N // 2 + 1) * 2 * real_bytes
+    nx, ny, nz = (N,) * 3 if isinstance(N, int) else tuple(N)
+    return nx * ny * (nz // 2 + 1) * 2 * real_bytes
 
 
 def measured_peaks():
@@ -317,6 +321,40 @@ def run_plane_schedule(torch, Solver, inputs, N=N_MAIN, warm=3, steps=10):
     return {"N": N, "dtype": "f32", "ms_per_step": ms, "value": N ** 3 / (ms * 1e-3),
             "kernels": {k: {"ms_per_launch": v[0] / v[1], "algorithmic_bytes_per_launch": kb[k],
                             "algorithmic_GBps": kb[k] / (v[0] / v[1] * 1e-3) / 1e9} for k, v in prof.items()}}
+
+
+def run_grids(torch, Solver, inputs, shape=(1024, 512, 256), warm=3, steps=10):
+    """A grid with other point counts per direction (1024 x 512 x 256, as many points as
+    512^3; generic passes): step time in both precisions, and the FP32 kernel classes
+    against their algorithmic bytes (pass_bytes) at the measured HBM peak."""
+    out = {"shape": list(shape), "steps": steps, "forms": []}
+    peak, kind = measured_peaks()
+    for dtype in ("f32", "f64"):
+        cdt = torch.complex64 if dtype == "f32" else torch.complex128
+        rb = 4 if dtype == "f32" else 8
+        with Solver(shape, NU, DT, dtype) as s:
+            st = torch.cuda.current_stream()
+            s.set_stream(st)
+            uh = inputs.isotropic_spectral(shape, seed=1, k0=8.0, device="cuda").to(cdt)
+            s.set_state_spectral(uh)
+            del uh
+            for _ in range(warm):
+                s.step(1)
+            torch.cuda.synchronize()
+            n = steps if dtype == "f32" else max(2, steps // 5)
+            ms = time_steps(torch, s, st, n) / n
+            form = {"dtype": dtype, "ms_per_step": ms, "value": shape[0] * shape[1] * shape[2] / (ms * 1e-3),
+                    "hbm_roofline_frac_of_measured": STEP_CV * cv_bytes(shape, rb) / (peak * 1e9) / (ms * 1e-3)}
+            if dtype == "f32":
+                prof = s.profile_steps(n)
+                kb = pass_bytes(shape, rb)
+                form["kernels"] = {k: {"ms_per_launch": t / c, "launches": c,
+                                       "achieved_gbs": kb[k] / (t / c * 1e-3) / 1e9,
+                                       "frac_of_peak": kb[k] / (t / c * 1e-3) / 1e9 / peak}
+                                   for k, (t, c) in prof.items()}
+            out["forms"].append(form)
+    out["peak_gbs"], out["peak_kind"] = peak, kind
+    return out
 
 
 def run_integrators(torch, Solver, inputs, N=512, warm=3, steps=10):
@@ -637,6 +675,7 @@ def run_ours(args):
             errs[dt_] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
         line["forms"] = forms
         line["integrators"] = run_integrators(torch, Solver, inputs)
+        line["grids"] = run_grids(torch, Solver, inputs)
         line["plane_schedule"] = run_plane_schedule(torch, Solver, inputs)
         line["ensemble"] = run_ensemble(torch, np)
         line["cufft_comparison"] = run_cufft_comparison(torch)

@@ -35,6 +35,11 @@
  *   dns_step returns after enqueueing, and kernel errors surface at the next
  *   call that synchronises (dns_get_state*, dns_diagnostics, dns_rhs).
  * - Supported N: 8, 12, 16, 24, 32, 48, 64, 96, 128, 256, 512, 1024.
+ * - Grids with other point counts per direction (dns_create3): the shapes above
+ *   become (3, Nx, Ny, Nz) and (3, Nx, Ny, Nz/2+1), kx in the FFT order of Nx, ky
+ *   of Ny, kz = 0..Nz/2; the inverse carries 1/(Nx Ny Nz) and the Nyquist modes
+ *   are |kx| = Nx/2, |ky| = Ny/2, kz = Nz/2. Compiled: 32 x 16 x 24,
+ *   24 x 48 x 16 and 1024 x 512 x 256 in both precisions.
  */
 #ifndef DNS_GB300_H
 #define DNS_GB300_H
@@ -79,6 +84,20 @@ typedef struct {
  * Errors: DNS_ERR_ARG (N unsupported, nu < 0, dt <= 0, dtype, out NULL),
  * DNS_ERR_UNSUPPORTED (no compute capability 10.3 device), DNS_ERR_OOM. */
 int dns_create(int N, double nu, double dt, int dtype, dns_handle** out);
+
+/* Creates a solver for a grid of Nx x Ny x Nz points (x, y, z), the Sec. 2
+ * footnote's other numbers of points per direction: x_i = Lx i / Nx and so on
+ * (Eq. realmesh per direction), wavenumbers in the FFT order of each count
+ * (Sec. 3.1), the 2/3 rule |k_i| < N_i/3 per direction (2/3 (N_i/2+1) with
+ * "dealias_variant" 1), the inverse transform normalised by 1/(Nx Ny Nz).
+ * Array shapes and errors as for dns_create; Nx = Ny = Nz is the same as
+ * dns_create(Nx, ...). The other counts run the generic passes: the options
+ * "fused_planes", "y_tile_*" and "z_tile" offer only their defaults, and
+ * dns_set_closure and ensembles take cubic grids only. dns_get_option reads
+ * the counts back as "Nx", "Ny", "Nz" (on any handle).
+ * Errors: DNS_ERR_ARG (the shape is not compiled, see the list above), as for
+ * dns_create otherwise. */
+int dns_create3(int Nx, int Ny, int Nz, double nu, double dt, int dtype, dns_handle** out);
 
 /* Frees everything the handle owns. NULL is accepted. */
 int dns_destroy(dns_handle* h);
@@ -142,7 +161,8 @@ int dns_set_stream(dns_handle* h, void* stream);
  * Errors: DNS_ERR_ARG for an unknown key or a value out of range. */
 int dns_set_option(dns_handle* h, const char* key, double value);
 
-/* The current value of an option of dns_set_option ("time" included) in *value.
+/* The current value of an option of dns_set_option ("time" included), or of the
+ * read-only grid counts "Nx", "Ny", "Nz", in *value.
  * Errors: DNS_ERR_ARG for an unknown key or a NULL pointer. */
 int dns_get_option(const dns_handle* h, const char* key, double* value);
 
@@ -383,8 +403,8 @@ int dns_mlp_train_step(dns_mlp* net, const float* X, const float* T, int P, doub
  * the 2/3 mask and the projection in every stage of the step (held over the
  * step, as the force of dns_set_forcing). `net` is borrowed: keep it alive and
  * attached only while the handle steps (parameter changes by training between
- * steps are seen by the next step); net = NULL detaches. FP32 handles on the
- * 2 pi box only (DNS_ERR_UNSUPPORTED otherwise); not together with
+ * steps are seen by the next step); net = NULL detaches. FP32 handles of cubic
+ * grids on the 2 pi box only (DNS_ERR_UNSUPPORTED otherwise); not together with
  * dns_set_forcing (DNS_ERR_ARG). Allocates its scratch (10 + 6 floats per grid
  * point and 12 spectral fields) on the first attach. */
 int dns_set_closure(dns_handle* h, dns_mlp* net, double delta);

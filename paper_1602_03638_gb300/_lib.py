@@ -43,6 +43,7 @@ _I = ctypes.c_int
 _D = ctypes.c_double
 SIGNATURES = {
     "dns_create": (_I, [_I, _D, _D, _I, ctypes.POINTER(_P)]),
+    "dns_create3": (_I, [_I, _I, _I, _D, _D, _I, ctypes.POINTER(_P)]),
     "dns_destroy": (_I, [_P]),
     "dns_set_stream": (_I, [_P, _P]),
     "dns_set_option": (_I, [_P, ctypes.c_char_p, _D]),

@@ -1,6 +1,7 @@
 """Builds the CUDA library libdns_gb300.so in-tree with nvcc for sm_103a.
 
-One translation unit per (precision, N) instance listed in csrc/instances.h,
+One translation unit per (precision, N) instance listed in csrc/instances.h
+(and per (precision, Nx, Ny, Nz) grid with other counts per direction),
 plus the C-ABI unit, compiled in parallel and linked into a shared library
 under paper_1602_03638_gb300/lib/. Object files go to _build/ (git-ignored).
 """
@@ -40,6 +41,14 @@ def instances():
     with open(os.path.join(CSRC, "instances.h")) as f:
         text = f.read()
     return [(t, tag, int(n)) for t, tag, n in re.findall(r"X\((float|double),\s*(f32|f64),\s*(\d+)\)", text)]
+
+
+def box_instances():
+    """(ctype, tag, Nx, Ny, Nz) of the grids with other counts per direction (csrc/instances.h)."""
+    with open(os.path.join(CSRC, "instances.h")) as f:
+        text = f.read()
+    pat = r"B\((float|double),\s*(f32|f64),\s*(\d+),\s*(\d+),\s*(\d+)\)"
+    return [(t, tag, int(a), int(b), int(c)) for t, tag, a, b, c in re.findall(pat, text)]
 
 
 def _sources_digest() -> str:
@@ -85,6 +94,13 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
         obj = os.path.join(BUILD, f"inst_{tag}_{n}.o")
         cmd = [nvcc, *ARCH, *FLAGS, f"-DDNS_INST_T={ctype}", f"-DDNS_INST_N={n}",
                f"-DDNS_INST_FN=dns_ops_{tag}_{n}", "-c", os.path.join(CSRC, "solver_inst.cu"), "-o", obj]
+        jobs_list.append((obj, cmd))
+    for ctype, tag, nx, ny, nz in box_instances():
+        shape = f"{nx}x{ny}x{nz}"
+        obj = os.path.join(BUILD, f"inst_{tag}_{shape}.o")
+        cmd = [nvcc, *ARCH, *FLAGS, f"-DDNS_INST_T={ctype}", f"-DDNS_INST_N={nx}", f"-DDNS_INST_NY={ny}",
+               f"-DDNS_INST_NZ={nz}", f"-DDNS_INST_FN=dns_ops_{tag}_{shape}", "-c",
+               os.path.join(CSRC, "solver_inst.cu"), "-o", obj]
         jobs_list.append((obj, cmd))
     extra = ["capi.cu", "noalloc.cu", "sgs.cu", "mlp.cu"]
     for name in extra:

@@ -23,12 +23,24 @@ namespace dns {
 #define DNS_DECL(T, tag, N) const DnsOps* dns_ops_##tag##_##N();
 DNS_INSTANCES(DNS_DECL)
 #undef DNS_DECL
+#define DNS_DECL3(T, tag, NX, NY, NZ) const DnsOps* dns_ops_##tag##_##NX##x##NY##x##NZ();
+DNS_BOX_INSTANCES(DNS_DECL3)
+#undef DNS_DECL3
 
 const DnsOps* find_ops(int dtype, int N) {
 #define DNS_FIND(T, tag, NN) \
   if (N == NN && dtype == (sizeof(T) == 4 ? 0 : 1)) return dns_ops_##tag##_##NN();
   DNS_INSTANCES(DNS_FIND)
 #undef DNS_FIND
+  return nullptr;
+}
+
+const DnsOps* find_ops3(int dtype, int Nx, int Ny, int Nz) {
+  if (Nx == Ny && Ny == Nz) return find_ops(dtype, Nx);
+#define DNS_FIND3(T, tag, NX, NY, NZ) \
+  if (Nx == NX && Ny == NY && Nz == NZ && dtype == (sizeof(T) == 4 ? 0 : 1)) return dns_ops_##tag##_##NX##x##NY##x##NZ();
+  DNS_BOX_INSTANCES(DNS_FIND3)
+#undef DNS_FIND3
   return nullptr;
 }
 
@@ -40,45 +52,45 @@ __global__ void k_diag_final(double* partials, int nblocks) {
   }
 }
 
-// Paper order P[c][kx][ky][kz'] (kz' <= N/2)  <->  internal O[c][kz][ky][kx] (kz < N/2).
-// grid = (ceil(N/32), ceil(kzcount/32), 3*N), block = (32, 8)
+// Paper order P[c][kx][ky][kz'] (kz' <= Nz/2)  <->  internal O[c][kz][ky][kx] (kz < Nz/2).
+// grid = (ceil(Nx/32), ceil(kzcount/32), 3*Ny), block = (32, 8)
 template <typename T>
-__global__ void k_paper_to_internal(const cx<T>* __restrict__ P, cx<T>* __restrict__ O, int N) {
+__global__ void k_paper_to_internal(const cx<T>* __restrict__ P, cx<T>* __restrict__ O, int Nx, int Ny, int Nz) {
   __shared__ cx<T> tile[32][33];
-  const int M = N / 2;
-  const int c = blockIdx.z / N, ky = blockIdx.z % N;
+  const int M = Nz / 2;
+  const int c = blockIdx.z / Ny, ky = blockIdx.z % Ny;
   const int kx0 = blockIdx.x * 32, kz0 = blockIdx.y * 32;
   for (int i = threadIdx.y; i < 32; i += 8) {
     const int kx = kx0 + i, kz = kz0 + threadIdx.x;
-    if (kx < N && kz < M) tile[i][threadIdx.x] = P[(((size_t)c * N + kx) * N + ky) * (M + 1) + kz];
+    if (kx < Nx && kz < M) tile[i][threadIdx.x] = P[(((size_t)c * Nx + kx) * Ny + ky) * (M + 1) + kz];
   }
   __syncthreads();
   for (int i = threadIdx.y; i < 32; i += 8) {
     const int kz = kz0 + i, kx = kx0 + threadIdx.x;
-    if (kx < N && kz < M) {
+    if (kx < Nx && kz < M) {
       cx<T> v = tile[threadIdx.x][i];
-      if (kx == N / 2 || ky == N / 2) v = mk((T)0, (T)0);
-      O[(((size_t)c * M + kz) * N + ky) * N + kx] = v;
+      if (kx == Nx / 2 || ky == Ny / 2) v = mk((T)0, (T)0);
+      O[(((size_t)c * M + kz) * Ny + ky) * Nx + kx] = v;
     }
   }
 }
 
 template <typename T>
-__global__ void k_internal_to_paper(const cx<T>* __restrict__ O, cx<T>* __restrict__ P, int N) {
+__global__ void k_internal_to_paper(const cx<T>* __restrict__ O, cx<T>* __restrict__ P, int Nx, int Ny, int Nz) {
   __shared__ cx<T> tile[32][33];
-  const int M = N / 2;
-  const int c = blockIdx.z / N, ky = blockIdx.z % N;
+  const int M = Nz / 2;
+  const int c = blockIdx.z / Ny, ky = blockIdx.z % Ny;
   const int kx0 = blockIdx.x * 32, kz0 = blockIdx.y * 32;
   for (int i = threadIdx.y; i < 32; i += 8) {
     const int kz = kz0 + i, kx = kx0 + threadIdx.x;
-    if (kx < N && kz < M) tile[i][threadIdx.x] = O[(((size_t)c * M + kz) * N + ky) * N + kx];
+    if (kx < Nx && kz < M) tile[i][threadIdx.x] = O[(((size_t)c * M + kz) * Ny + ky) * Nx + kx];
   }
   __syncthreads();
   for (int i = threadIdx.y; i < 32; i += 8) {
     const int kx = kx0 + i, kz = kz0 + threadIdx.x;
-    if (kx < N && kz <= M) {
+    if (kx < Nx && kz <= M) {
       const cx<T> v = kz < M ? tile[threadIdx.x][i] : mk((T)0, (T)0);
-      P[(((size_t)c * N + kx) * N + ky) * (M + 1) + kz] = v;
+      P[(((size_t)c * Nx + kx) * Ny + ky) * (M + 1) + kz] = v;
     }
   }
 }
@@ -205,7 +217,8 @@ void set_error_message(const char* msg) { g_err = msg; }
 }  // namespace dns
 
 struct dns_handle {
-  int N = 0;
+  int N = 0;  // points along x (and along y and z on a cubic grid)
+  int Ny = 0, Nz = 0;  // points along y and z
   int dtype = 0;
   int variant = 0;
   int integrator = 0;  // index into RK_SCHEMES, -1 for a scheme set by dns_set_rk_tableau
@@ -228,7 +241,7 @@ struct dns_handle {
   void* F = nullptr;  // optional force, internal layout
   bool has_force = false;
   // learned closure evaluated at the start of every step (dns_set_closure): the network
-  // (borrowed), the filter width, and scratch: features (10 x N^3 floats), stress
+  // (borrowed), the filter width, and scratch (cubic grids): features (10 x N^3 floats), stress
   // (6 x N^3 floats), 6 spectral fields, 3 spectral work fields, the force (3 fields)
   dns_mlp* closure = nullptr;
   double closure_delta = 0.0;
@@ -291,6 +304,8 @@ PassArgs base_args(const dns_handle* h) {
   a.F = h->has_force ? h->F : (h->closure ? h->FC : nullptr);
   a.nu = h->nu;
   a.kmax3 = h->N + 2 * h->variant;
+  a.kmax3y = h->Ny + 2 * h->variant;
+  a.kmax3z = h->Nz + 2 * h->variant;
   for (int i = 0; i < 3; ++i) a.ks[i] = kTwoPi / h->L[i];  // exactly 1 on the 2 pi box
   a.ytile[0] = h->ytile[0];
   a.ytile[1] = h->ytile[1];
@@ -397,25 +412,25 @@ int use_device(const dns_handle* h) {
   return DNS_OK;
 }
 
-size_t phys_bytes(const dns_handle* h) { return (size_t)3 * h->N * h->N * h->N * (h->dtype ? 8 : 4); }
+size_t phys_bytes(const dns_handle* h) { return (size_t)3 * h->N * h->Ny * h->Nz * (h->dtype ? 8 : 4); }
 size_t paper_spec_bytes(const dns_handle* h) {
-  return (size_t)3 * h->N * h->N * (h->N / 2 + 1) * h->ops->elem_bytes;
+  return (size_t)3 * h->N * h->Ny * (h->Nz / 2 + 1) * h->ops->elem_bytes;
 }
 
 cudaError_t launch_transpose(dns_handle* h, const void* src, void* dst, bool to_internal) {
-  const int N = h->N, M = N / 2;
+  const int Nx = h->N, Ny = h->Ny, Nz = h->Nz, M = Nz / 2;
   dim3 block(32, 8);
-  dim3 grid((N + 31) / 32, ((to_internal ? M : M + 1) + 31) / 32, 3 * N);
+  dim3 grid((Nx + 31) / 32, ((to_internal ? M : M + 1) + 31) / 32, 3 * Ny);
   if (h->dtype == 0) {
     if (to_internal)
-      k_paper_to_internal<float><<<grid, block, 0, h->stream>>>((const cx<float>*)src, (cx<float>*)dst, N);
+      k_paper_to_internal<float><<<grid, block, 0, h->stream>>>((const cx<float>*)src, (cx<float>*)dst, Nx, Ny, Nz);
     else
-      k_internal_to_paper<float><<<grid, block, 0, h->stream>>>((const cx<float>*)src, (cx<float>*)dst, N);
+      k_internal_to_paper<float><<<grid, block, 0, h->stream>>>((const cx<float>*)src, (cx<float>*)dst, Nx, Ny, Nz);
   } else {
     if (to_internal)
-      k_paper_to_internal<double><<<grid, block, 0, h->stream>>>((const cx<double>*)src, (cx<double>*)dst, N);
+      k_paper_to_internal<double><<<grid, block, 0, h->stream>>>((const cx<double>*)src, (cx<double>*)dst, Nx, Ny, Nz);
     else
-      k_internal_to_paper<double><<<grid, block, 0, h->stream>>>((const cx<double>*)src, (cx<double>*)dst, N);
+      k_internal_to_paper<double><<<grid, block, 0, h->stream>>>((const cx<double>*)src, (cx<double>*)dst, Nx, Ny, Nz);
   }
   return cudaGetLastError();
 }
@@ -425,13 +440,21 @@ cudaError_t launch_transpose(dns_handle* h, const void* src, void* dst, bool to_
 extern "C" {
 
 int dns_create(int N, double nu, double dt, int dtype, dns_handle** out) {
+  return dns_create3(N, N, N, nu, dt, dtype, out);
+}
+
+int dns_create3(int Nx, int Ny, int Nz, double nu, double dt, int dtype, dns_handle** out) {
   if (!out) return fail(DNS_ERR_ARG, "dns_create: out is NULL");
   *out = nullptr;
   if (dtype != DNS_F32 && dtype != DNS_F64) return fail(DNS_ERR_ARG, "dns_create: dtype %d is not DNS_F32/DNS_F64", dtype);
   if (!(nu >= 0.0) || !std::isfinite(nu)) return fail(DNS_ERR_ARG, "dns_create: nu must be finite and >= 0");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(DNS_ERR_ARG, "dns_create: dt must be finite and > 0");
-  const DnsOps* ops = find_ops(dtype, N);
-  if (!ops) return fail(DNS_ERR_ARG, "dns_create: N = %d is not a supported grid size", N);
+  const DnsOps* ops = find_ops3(dtype, Nx, Ny, Nz);
+  if (!ops) {
+    if (Nx == Ny && Ny == Nz) return fail(DNS_ERR_ARG, "dns_create: N = %d is not a supported grid size", Nx);
+    return fail(DNS_ERR_ARG, "dns_create3: %d x %d x %d is not a compiled grid", Nx, Ny, Nz);
+  }
+  const int N = Nx;
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
   if (e != cudaSuccess || ndev == 0) {
@@ -448,13 +471,15 @@ int dns_create(int N, double nu, double dt, int dtype, dns_handle** out) {
 
   dns_handle* h = new dns_handle();
   h->N = N;
+  h->Ny = Ny;
+  h->Nz = Nz;
   h->dtype = dtype;
   h->nu = nu;
   h->dt = dt;
   h->ops = ops;
   h->device = dev;
-  const int M = N / 2;
-  h->fs = (size_t)M * N * N;
+  const int M = Nz / 2;
+  h->fs = (size_t)M * Ny * N;
   const size_t cb = ops->elem_bytes;
   int rc = DNS_OK;
   cudaError_t ce = ops->prepare();
@@ -468,9 +493,10 @@ int dns_create(int N, double nu, double dt, int dtype, dns_handle** out) {
   if (rc == DNS_OK) rc = dev_alloc(h, &h->U, 3 * h->fs * cb, "state U");
   if (rc == DNS_OK) rc = dev_alloc(h, &h->U1, 3 * h->fs * cb, "RK4 accumulator");
   if (rc == DNS_OK) rc = dev_alloc(h, &h->US, 3 * h->fs * cb, "RK4 stage state");
-  if (rc == DNS_OK) rc = dev_alloc(h, &h->W, (6 * h->fs + (size_t)3 * N * N) * cb, "work fields");
+  if (rc == DNS_OK) rc = dev_alloc(h, &h->W, (6 * h->fs + (size_t)3 * N * Ny) * cb, "work fields");
   if (rc == DNS_OK) rc = dev_alloc(h, &h->D, h->fs * cb, "divergence field");
-  if (rc == DNS_OK) rc = dev_alloc(h, &h->tw, (size_t)N * cb, "twiddles");
+  const int TW = ops->TW;  // exp(-2 pi i t / TW): N on a cubic grid, else a common multiple of the counts
+  if (rc == DNS_OK) rc = dev_alloc(h, &h->tw, (size_t)TW * cb, "twiddles");
   if (rc == DNS_OK) rc = dev_alloc(h, (void**)&h->diag, (DIAG_BLOCKS * 4 + 8) * sizeof(double), "diagnostics");
   if (rc == DNS_OK && ops->plane_ctl_words > 0) {
     rc = dev_alloc(h, (void**)&h->ctl, (size_t)ops->plane_ctl_words * sizeof(int), "plane-pass control block");
@@ -480,11 +506,11 @@ int dns_create(int N, double nu, double dt, int dtype, dns_handle** out) {
     }
   }
   if (rc == DNS_OK) {
-    std::vector<double> t64(2 * N);
-    for (int t = 0; t < N; ++t) twiddle(t, N, &t64[2 * t], &t64[2 * t + 1]);
+    std::vector<double> t64(2 * TW);
+    for (int t = 0; t < TW; ++t) twiddle(t, TW, &t64[2 * t], &t64[2 * t + 1]);
     if (dtype == DNS_F32) {
-      std::vector<float> t32(2 * N);
-      for (int i = 0; i < 2 * N; ++i) t32[i] = (float)t64[i];
+      std::vector<float> t32(2 * TW);
+      for (int i = 0; i < 2 * TW; ++i) t32[i] = (float)t64[i];
       ce = cudaMemcpy(h->tw, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice);
     } else {
       ce = cudaMemcpy(h->tw, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice);
@@ -597,6 +623,9 @@ int dns_get_option(const dns_handle* h, const char* key, double* value) {
   else if (!strcmp(key, "nu")) *value = h->nu;
   else if (!strcmp(key, "dt")) *value = h->dt;
   else if (!strcmp(key, "time")) *value = h->t;
+  else if (!strcmp(key, "Nx")) *value = h->N;
+  else if (!strcmp(key, "Ny")) *value = h->Ny;
+  else if (!strcmp(key, "Nz")) *value = h->Nz;
   else return fail(DNS_ERR_ARG, "dns_get_option: unknown key '%s'", key);
   return DNS_OK;
 }
@@ -865,7 +894,8 @@ int dns_diagnostics(dns_handle* h, dns_diag* out) {
            "dns_diagnostics copy");
   DNS_CUDA(cudaStreamSynchronize(h->stream), "dns_diagnostics");
   if ((rc = check_plane_error(h, "dns_diagnostics"))) return rc;
-  const double n6 = std::pow((double)h->N, 6.0);
+  const double n3 = (double)h->N * (double)h->Ny * (double)h->Nz;
+  const double n6 = n3 * n3;
   unsigned long long bits;
   memcpy(&bits, &r[4], sizeof(bits));
   double mdiv;
@@ -955,6 +985,8 @@ int dns_set_closure(dns_handle* h, dns_mlp* net, double delta) {
     return DNS_OK;
   }
   if (h->dtype != DNS_F32) return fail(DNS_ERR_UNSUPPORTED, "dns_set_closure: the closure runs on FP32 handles");
+  if (h->Ny != h->N || h->Nz != h->N)
+    return fail(DNS_ERR_UNSUPPORTED, "dns_set_closure: the closure runs on cubic grids");
   for (int i = 0; i < 3; ++i)
     if (h->L[i] != kTwoPi) return fail(DNS_ERR_UNSUPPORTED, "dns_set_closure: the closure assumes the 2 pi box");
   if (h->has_force) return fail(DNS_ERR_ARG, "dns_set_closure: a force is set (dns_set_forcing)");

@@ -15,15 +15,15 @@ namespace dns {
 cudaError_t mlp_forward_async(::dns_mlp* net, const float* X, float* Y, int P, cudaStream_t st);
 
 // Device buffers and scalars shared by all passes. Complex arrays use the
-// internal spectral layout [component][kz][ky][kx] with kz < N/2 (the
-// Nyquist plane kz = N/2 is identically zero and not stored).
+// internal spectral layout [component][kz][ky][kx] with kz < Nz/2 (the
+// Nyquist plane kz = Nz/2 is identically zero and not stored).
 struct PassArgs {
   void* U = nullptr;   // state u_hat at the start of the RK4 step (3 fields)
   void* U1 = nullptr;  // RK4 accumulator (3 fields)
   void* US = nullptr;  // RK4 stage state (3 fields)
   void* W = nullptr;   // work: 6 fields, transforms in flight
   void* D = nullptr;   // work: 1 field, divergence diagnostic
-  const void* tw = nullptr;  // exp(-2 pi i t / N), t < N
+  const void* tw = nullptr;  // exp(-2 pi i t / TW), t < TW (TW = N on a cubic grid)
   const void* F = nullptr;   // optional force (3 fields, internal layout) added to N_hat
   double nu = 0.0;
   double cA = 0.0;  // a_s * dt
@@ -34,7 +34,9 @@ struct PassArgs {
   double cC = 0.0;
   int stage = 0;    // stage of the step, 0..last
   int last = 3;     // the step's final stage (it writes the new state); 3 for RK4
-  int kmax3 = 0;    // a mode is kept by the 2/3 rule iff 3|k_i| < kmax3
+  int kmax3 = 0;    // a mode is kept by the 2/3 rule iff 3|k_i| < kmax3 (along x; all
+                    // directions on a cubic grid)
+  int kmax3y = 0, kmax3z = 0;  // the same along y and z (read where the counts differ)
   double ks[3] = {1.0, 1.0, 1.0};  // 2 pi / L along x, y, z: the wavenumber of index 1
   // FP32 copies of nu, cA, cB and ks for the FP32 kernels (filled when a kernel is
   // launched), so that they need no double-to-float conversion per thread
@@ -42,8 +44,8 @@ struct PassArgs {
   float f_ks[3] = {1.f, 1.f, 1.f};
   int ytile[2] = {0, 0};  // y-pass tile widths of the stage launches (inverse, forward); 0 = default
   int ztile = 0;          // z-pass tile width of the stage launches; 0 = default
-  const void* in = nullptr;  // physical input (3,N,N,N) for set_state
-  void* out = nullptr;       // physical output (3,N,N,N) / RHS output
+  const void* in = nullptr;  // physical input (3,Nx,Ny,Nz) for set_state
+  void* out = nullptr;       // physical output (3,Nx,Ny,Nz) / RHS output
   int* ctl = nullptr;  // plane-pass control block (error flag, queue head, per-plane counters)
   int plane_lag = 0;   // plane-pass lag in queue steps (0: chosen from the block count)
   double* partials = nullptr;          // diagnostics block partials
@@ -93,6 +95,8 @@ struct DnsOps {
   // that its waits cannot be met (test of the bounded waits)
   cudaError_t (*plane_wait_test)(const PassArgs& a, cudaStream_t s);
   int plane_ctl_words;  // ints of the plane-pass control block (0: no plane pass)
+  int NY, NZ;  // points along y and z (N is the count along x)
+  int TW;      // length of the twiddle table exp(-2 pi i t / TW) (a multiple of N, NY, NZ)
 };
 
 constexpr int BATCH_MAX_N = 128;
@@ -104,8 +108,9 @@ static_assert(sizeof(BatchArgs) <= 32764, "kernel parameters are limited to 3276
 
 constexpr int DIAG_BLOCKS = 592;  // 4 x 148..152 SMs: one wave of 4 blocks per SM
 
-// Lookup of the instantiation for (dtype, N); nullptr if unsupported.
+// Lookup of the instantiation for (dtype, N) or (dtype, Nx, Ny, Nz); nullptr if unsupported.
 const DnsOps* find_ops(int dtype, int N);
+const DnsOps* find_ops3(int dtype, int Nx, int Ny, int Nz);
 
 // Closure helpers on the internal layout (sgs.cu): G3 = i k_j u_hat_comp (j = 0..2),
 // F3 = -i k_j tau_hat_ij from the 6 stress components (00 11 22 01 02 12); fill of a

@@ -1,5 +1,7 @@
 // Fused kernels of one RK4 right-hand-side evaluation and its stage update,
-// templated on the precision T and the grid size N (N = 2^a or 3*2^a).
+// templated on the precision T and the grid size N (N = 2^a or 3*2^a). The
+// generic passes also take per-direction point counts (Sec. 2 footnote): N is
+// then the count along x, NY and NZ those along y and z (defaults N).
 //
 // Per RK4 stage (Eq. NSfinal with the Appendix's RK4 driver) the state goes
 // through four passes over HBM:
@@ -36,11 +38,16 @@ constexpr int pow2_part(int n) {
 }
 constexpr int cmin(int a, int b) { return a < b ? a : b; }
 constexpr int odd_ld(int lines) { return (lines % 2) ? lines : lines + 1; }
+constexpr int igcd(int a, int b) { return b == 0 ? a : igcd(b, a % b); }
+constexpr int ilcm(int a, int b) { return a / igcd(a, b) * b; }
 
-template <typename T, int N>
+// Grid of N x NY x NZ points (x, y, z); the spectral fields hold kz < NZ/2.
+template <typename T, int N, int NY = N, int NZ = N>
 struct Geometry {
-  static constexpr int M = N / 2;
-  static constexpr size_t FS = (size_t)M * N * N;  // complex values per field
+  static constexpr int M = NZ / 2;
+  static constexpr size_t FS = (size_t)M * NY * N;  // complex values per field
+  // length of the twiddle table exp(-2 pi i t / TW): every line length divides it
+  static constexpr int TW = ilcm(ilcm(N, NY), NZ);
   static constexpr int CB = (int)sizeof(cx<T>);
   // x-pass: one row (fixed kz, ky) per block, 6 padded line buffers. The
   // stage update (XPRE, where it fits in 100 KB) uses 3 padded lines (the
@@ -79,14 +86,15 @@ struct Geometry {
 // blocks per SM (both measured at 512^3). FP64 keeps 128-byte rows up to N = 512,
 // 64-byte rows above.
 // TXO > 0 replaces the tile width (a tuned schedule of the small grids).
-template <typename T, int N, int INV, int TXO = 0>
+// NY: the line length (points along y) where it differs from N (the x extent).
+template <typename T, int N, int INV, int TXO = 0, int NY = N>
 struct YCfg {
   static constexpr int CB = (int)sizeof(cx<T>);
-  static constexpr int TX = TXO > 0 ? TXO : cmin(((INV || CB == 16) && N <= 512 ? 128 : 64) / CB, pow2_part(N));
+  static constexpr int TX = TXO > 0 ? TXO : cmin(((INV || CB == 16) && NY <= 512 ? 128 : 64) / CB, pow2_part(N));
   static constexpr int THREADS = cmin(32 * TX, 256);
   static constexpr int LD = odd_ld(TX);
-  static constexpr size_t SMEM = (size_t)padded_len(N) * LD * CB;
-  static constexpr int MINB = (CB == 8 && N <= 512) ? (INV ? 3 : 4) : 2;
+  static constexpr size_t SMEM = (size_t)padded_len(NY) * LD * CB;
+  static constexpr int MINB = (CB == 8 && NY <= 512) ? (INV ? 3 : 4) : 2;
 };
 
 __device__ __forceinline__ int kfreq(int i, int N) { return i < N / 2 ? i : i - N; }
@@ -166,7 +174,8 @@ struct GStoreNyquistFree {
 // ---------------------------------------------------------------------------
 // NT: threads of the calling block (XP_THREADS for k_xpass; the plane pass runs the
 // stage update with 256, its warps 6 and 7 idle during the line transforms).
-template <typename T, int N, int MODE, int NT = XP_THREADS>
+// NY, NZ: points along y and z where they differ from N (rows kz * NY + ky).
+template <typename T, int N, int MODE, int NT = XP_THREADS, int NY = N, int NZ = N>
 __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
   static_assert(NT >= XP_THREADS && NT % 32 == 0, "the x-pass needs at least one warp per line");
   // in the plane pass the RK state is a stream past the plane data kept in L2 (FP32
@@ -175,9 +184,10 @@ __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
   constexpr bool STAGE = MODE == XM_STAGE || MODE == XM_STAGE2N;  // a stage update (either form)
   constexpr bool HINT = NT != XP_THREADS && STAGE && sizeof(T) == 4;
   const unsigned long long pol = HINT ? l2_evict_first_policy() : 0ull;
-  using G = Geometry<T, N>;
+  using G = Geometry<T, N, NY, NZ>;
   constexpr int LS = G::XLS;
   constexpr size_t FS = G::FS;
+  constexpr int TW = G::TW;
   extern __shared__ unsigned char smraw[];
   cx<T>* s = reinterpret_cast<cx<T>*>(smraw);
   const cx<T>* tw = reinterpret_cast<const cx<T>*>(a.tw);
@@ -186,17 +196,19 @@ __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
   cx<T>* US = reinterpret_cast<cx<T>*>(a.US);
   cx<T>* W = reinterpret_cast<cx<T>*>(a.W);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row = bx;  // row = kz * N + ky
-  const int kz = row / N, ky = row % N;
+  const int row = bx;  // row = kz * NY + ky
+  const int kz = row / NY, ky = row % NY;
   const size_t rb = (size_t)row * N;
-  const T sc = (T)(1.0 / ((double)N * (double)N * (double)N));
+  const T sc = (T)(1.0 / ((double)N * (double)NY * (double)NZ));
   // wavenumbers of the row and of column j: integer index times 2 pi / L (1 on the 2 pi box)
   const T ksx = par<T>(a.ks[0], a.f_ks[0]);
-  const T kzv = (T)kz * par<T>(a.ks[2], a.f_ks[2]), kyv = (T)kfreq(ky, N) * par<T>(a.ks[1], a.f_ks[1]);
+  const T kzv = (T)kz * par<T>(a.ks[2], a.f_ks[2]), kyv = (T)kfreq(ky, NY) * par<T>(a.ks[1], a.f_ks[1]);
 
   if constexpr (STAGE || MODE == XM_RHS) {
     // rows outside the 2/3 box carry no nonlinear term: skip their transform
-    const bool row_kept = (3 * kz < a.kmax3) && kept(kfreq(ky, N), a.kmax3);
+    // (each direction's cut-off from its own point count)
+    const int k3y = NY == N ? a.kmax3 : a.kmax3y, k3z = NZ == N ? a.kmax3 : a.kmax3z;
+    const bool row_kept = (3 * kz < k3z) && kept(kfreq(ky, NY), k3y);
     const T nu = par<T>(a.nu, a.f_nu), cA = par<T>(a.cA, a.f_cA), cB = par<T>(a.cB, a.f_cB);
     const int stage = a.stage, last = a.last;
     // Williamson 2N stages keep the stage state in U (updated in place) and dU in U1
@@ -231,13 +243,13 @@ __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
       __syncthreads();
       if (row_kept && warp < 3) {
         const SLine<T, 1> line{s + warp * LS};
-        warp_fft<T, N, N>(line, line, line, tw, lane);
+        warp_fft<T, N, TW>(line, line, line, tw, lane);
       }
       cp_async_wait<0>();
     } else {
       if (row_kept && warp < 3) {
         const SLine<T, 1> line{s + warp * LS};
-        warp_fft<T, N, N>(GLoad<T, false>{W + warp * FS + rb}, line, line, tw, lane);
+        warp_fft<T, N, TW>(GLoad<T, false>{W + warp * FS + rb}, line, line, tw, lane);
       }
     }
     __syncthreads();
@@ -364,22 +376,22 @@ __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
       if constexpr (G::XPRE && !G::XWIDE) {
         if (warp < 3) {
           const SLine<T, 1> line{s + warp * LS};
-          warp_fft<T, N, N>(line, line, GStore<T, true>{W + warp * FS + rb}, tw, lane);
+          warp_fft<T, N, TW>(line, line, GStore<T, true>{W + warp * FS + rb}, tw, lane);
         } else {  // omega: from its unpadded row, through a padded work line over rows 3-8
           const int c = warp - 3;
           const SLine<T, 1> work{st + 3 * N + c * LS};
-          warp_fft<T, N, N>(SRow<T>{st + c * N}, work, GStore<T, true>{W + warp * FS + rb}, tw, lane);
+          warp_fft<T, N, TW>(SRow<T>{st + c * N}, work, GStore<T, true>{W + warp * FS + rb}, tw, lane);
         }
       } else {
         const SLine<T, 1> line{s + warp * LS};
-        warp_fft<T, N, N>(line, line, GStore<T, true>{W + warp * FS + rb}, tw, lane);
+        warp_fft<T, N, TW>(line, line, GStore<T, true>{W + warp * FS + rb}, tw, lane);
       }
     }
   } else if constexpr (MODE == XM_FWD_STORE) {
     if (warp < 3) {
       const SLine<T, 1> line{s + warp * LS};
-      warp_fft<T, N, N>(GLoad<T, false>{U + warp * FS + rb}, line,
-                        GStoreNyquistFree<T>{U + warp * FS + rb, N, ky == N / 2}, tw, lane);
+      warp_fft<T, N, TW>(GLoad<T, false>{U + warp * FS + rb}, line,
+                        GStoreNyquistFree<T>{U + warp * FS + rb, N, ky == NY / 2}, tw, lane);
     }
   } else {
     // inverse x transform of u and omega (XM_INV_CURL), of u alone
@@ -405,14 +417,14 @@ __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
     cx<T>* dst = (MODE == XM_INV_DIV) ? reinterpret_cast<cx<T>*>(a.D) : W;
     if (warp < NF) {
       const SLine<T, 1> line{s + warp * LS};
-      warp_fft<T, N, N>(line, line, GStore<T, true>{dst + warp * FS + rb}, tw, lane);
+      warp_fft<T, N, TW>(line, line, GStore<T, true>{dst + warp * FS + rb}, tw, lane);
     }
   }
 }
 
-template <typename T, int N, int MODE>
-__global__ void __launch_bounds__(XP_THREADS, (Geometry<T, N>::XMIN)) k_xpass(PassArgs a) {
-  xpass_body<T, N, MODE>(a, blockIdx.x);
+template <typename T, int N, int MODE, int NY = N, int NZ = N>
+__global__ void __launch_bounds__(XP_THREADS, (Geometry<T, N, NY, NZ>::XMIN)) k_xpass(PassArgs a) {
+  xpass_body<T, N, MODE, XP_THREADS, NY, NZ>(a, blockIdx.x);
 }
 
 // Batched form (ensembles): member blockIdx.y, its arguments in B.a[blockIdx.y].
@@ -479,24 +491,25 @@ __device__ __forceinline__ void ypass_tile(cx<T>* __restrict__ base, const cx<T>
   }
 }
 
-template <typename T, int N, int INV, int PRUNE, int TXO = 0>
-__global__ void __launch_bounds__(YCfg<T, N, INV, TXO>::THREADS, (YCfg<T, N, INV, TXO>::MINB)) k_ypass(cx<T>* __restrict__ F,
-                                                                                         const cx<T>* __restrict__ tw,
-                                                                                         int kmax3) {
-  using G = Geometry<T, N>;
-  using Y = YCfg<T, N, INV, TXO>;
+// NY, NZ: points along y and z where they differ from N (N: the x extent, the
+// row stride of the tile's columns).
+template <typename T, int N, int INV, int PRUNE, int TXO = 0, int NY = N, int NZ = N>
+__global__ void __launch_bounds__(YCfg<T, N, INV, TXO, NY>::THREADS, (YCfg<T, N, INV, TXO, NY>::MINB))
+    k_ypass(cx<T>* __restrict__ F, const cx<T>* __restrict__ tw, int kmax3) {
+  using G = Geometry<T, N, NY, NZ>;
+  using Y = YCfg<T, N, INV, TXO, NY>;
   constexpr int TX = Y::TX;
   constexpr int LD = Y::LD;
   constexpr int NT = Y::THREADS;  // warps loop over the columns
   extern __shared__ unsigned char smraw[];
   cx<T>* s = reinterpret_cast<cx<T>*>(smraw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  cx<T>* base = F + blockIdx.z * G::FS + (size_t)blockIdx.y * N * N + blockIdx.x * TX;
+  cx<T>* base = F + blockIdx.z * G::FS + (size_t)blockIdx.y * NY * N + blockIdx.x * TX;
   // the whole tile in flight at once (cp.async, no register staging); the
   // inverse's conjugation is applied when the first pass reads it
 #pragma unroll 8
-  for (int e = threadIdx.x; e < TX * N; e += NT) {
-    const int x = e % TX, y = ywalk_row<T, TX, N>(e / TX);
+  for (int e = threadIdx.x; e < TX * NY; e += NT) {
+    const int x = e % TX, y = ywalk_row<T, TX, NY>(e / TX);
     cp_async<sizeof(cx<T>)>(s + padp(y) * LD + x, base + (size_t)y * N + x);
   }
   cp_async_commit();
@@ -505,14 +518,14 @@ __global__ void __launch_bounds__(YCfg<T, N, INV, TXO>::THREADS, (YCfg<T, N, INV
 #pragma unroll 1
   for (int c = warp; c < TX; c += NT / 32) {
     const SLine<T, LD> line{s + c};
-    if constexpr (INV) warp_fft<T, N, N>(SLineConj<T, LD>{s + c}, line, line, tw, lane);
-    else warp_fft<T, N, N>(line, line, line, tw, lane);
+    if constexpr (INV) warp_fft<T, NY, G::TW>(SLineConj<T, LD>{s + c}, line, line, tw, lane);
+    else warp_fft<T, NY, G::TW>(line, line, line, tw, lane);
   }
   __syncthreads();
 #pragma unroll 8
-  for (int e = threadIdx.x; e < TX * N; e += NT) {
-    const int x = e % TX, y = ywalk_row<T, TX, N>(e / TX);
-    if (PRUNE && !kept(kfreq(y, N), kmax3)) continue;
+  for (int e = threadIdx.x; e < TX * NY; e += NT) {
+    const int x = e % TX, y = ywalk_row<T, TX, NY>(e / TX);
+    if (PRUNE && !kept(kfreq(y, NY), kmax3)) continue;
     const cx<T> v = s[padp(y) * LD + x];
     base[(size_t)y * N + x] = INV ? conjg(v) : v;
   }
@@ -538,10 +551,13 @@ __global__ void __launch_bounds__(YCfg<T, N, INV, TXO>::THREADS, (YCfg<T, N, INV
 // (k, M-k); the imaginary part of the kz = 0 coefficient is ignored and the
 // kz = N/2 coefficient is zero (it is not stored).
 // ---------------------------------------------------------------------------
-template <typename T, int N, int MODE, int TXO = 0>
+// NY, NZ: points along y and z where they differ from N (lines of NZ points at the
+// NX x NY positions; physical arrays (3, N, NY, NZ)).
+template <typename T, int N, int MODE, int TXO = 0, int NY = N, int NZ = N>
 __device__ __forceinline__ void zpass_body(const PassArgs a, const int bx, const int by) {
-  using G = Geometry<T, N>;
+  using G = Geometry<T, N, NY, NZ>;
   constexpr int M = G::M;
+  constexpr int TW = G::TW, TS = TW / NZ;  // exp(-2 pi i k / NZ) = tw[k * TS]
   constexpr int TX = TXO > 0 ? TXO : G::ZTX;  // TXO: a tuned tile width of the small grids
   constexpr int LD = odd_ld(6 * TX);
   constexpr size_t FS = G::FS;
@@ -558,14 +574,14 @@ __device__ __forceinline__ void zpass_body(const PassArgs a, const int bx, const
     const cx<T>* in = reinterpret_cast<const cx<T>*>(a.in);
     for (int e = threadIdx.x; e < 3 * TX * M; e += ZP_THREADS) {
       const int n = e % M, x = (e / M) % TX, c = e / (M * TX);
-      s[padp(n) * LD + c * TX + x] = in[((size_t)(c * N + x0 + x) * N + y) * M + n];
+      s[padp(n) * LD + c * TX + x] = in[((size_t)(c * N + x0 + x) * NY + y) * M + n];
     }
     __syncthreads();
   } else {
     const cx<T>* src = reinterpret_cast<const cx<T>*>(MODE == ZM_MAXABS ? a.D : a.W);
     for (int e = threadIdx.x; e < NF * TX * M; e += ZP_THREADS) {
       const int x = e % TX, k = (e / TX) % M, f = e / (TX * M);
-      s[padp(k) * LD + f * TX + x] = src[f * FS + ((size_t)k * N + y) * N + x0 + x];
+      s[padp(k) * LD + f * TX + x] = src[f * FS + ((size_t)k * NY + y) * N + x0 + x];
     }
     __syncthreads();
     // c2r pre-processing: Z'_k = (X_k + conj X_{M-k}) + i e^{+2 pi i k/N} (X_k - conj X_{M-k}),
@@ -580,7 +596,7 @@ __device__ __forceinline__ void zpass_body(const PassArgs a, const int bx, const
         cx<T>* pk = s + padp(k) * LD + l;
         cx<T>* pm = s + padp(M - k) * LD + l;
         const cx<T> xk = *pk, xm = *pm;
-        const cx<T> wk = ldro(tw + k);  // exp(-2 pi i k / N)
+        const cx<T> wk = ldro(tw + k * TS);  // exp(-2 pi i k / NZ)
         const cx<T> A = xk + conjg(xm), B = xk - conjg(xm);
         *pk = conjg(A + mul_pi(cmul(conjg(wk), B)));
         if (k != M - k) {
@@ -593,7 +609,7 @@ __device__ __forceinline__ void zpass_body(const PassArgs a, const int bx, const
     __syncthreads();
     constexpr int GL = LinesPerWarp<M>::value <= TX ? LinesPerWarp<M>::value : TX;  // lines per warp
 #pragma unroll 1
-    for (int l = warp * GL; l < NL; l += (ZP_THREADS / 32) * GL) warp_fft_lines<T, M, N, GL, LD>(s + l, tw, lane);
+    for (int l = warp * GL; l < NL; l += (ZP_THREADS / 32) * GL) warp_fft_lines<T, M, TW, GL, LD>(s + l, tw, lane);
     __syncthreads();
     // now conj(s) = x_{2n} + i x_{2n+1} (physical values, unnormalised c2r)
   }
@@ -615,28 +631,28 @@ __device__ __forceinline__ void zpass_body(const PassArgs a, const int bx, const
   if constexpr (MODE == ZM_CROSS || MODE == ZM_LOAD) {
     constexpr int GL = LinesPerWarp<M>::value <= TX ? LinesPerWarp<M>::value : TX;
 #pragma unroll 1
-    for (int l = warp * GL; l < 3 * TX; l += (ZP_THREADS / 32) * GL) warp_fft_lines<T, M, N, GL, LD>(s + l, tw, lane);
+    for (int l = warp * GL; l < 3 * TX; l += (ZP_THREADS / 32) * GL) warp_fft_lines<T, M, TW, GL, LD>(s + l, tw, lane);
     __syncthreads();
     // r2c post-processing: X_k = 1/2 [(Z_k + conj Z_{M-k}) - i e^{-2 pi i k/N} (Z_k - conj Z_{M-k})]
     cx<T>* dst = reinterpret_cast<cx<T>*>(MODE == ZM_CROSS ? a.W : a.U);
     int kc = M;
     if (MODE == ZM_CROSS) {
-      kc = (a.kmax3 + 2) / 3;
+      kc = ((NZ == N ? a.kmax3 : a.kmax3z) + 2) / 3;
       if (kc > M) kc = M;
     }
     for (int e = threadIdx.x; e < 3 * TX * kc; e += ZP_THREADS) {
       const int x = e % TX, k = (e / TX) % kc, c = e / (TX * kc);
       const int l = c * TX + x;
       const cx<T> zk = s[padp(k) * LD + l], zm = s[padp((M - k) % M) * LD + l];
-      const cx<T> wk = ldro(tw + k);
+      const cx<T> wk = ldro(tw + k * TS);
       const cx<T> A = zk + conjg(zm), B = zk - conjg(zm);
-      dst[c * FS + ((size_t)k * N + y) * N + x0 + x] = scal(A + mul_mi(cmul(wk, B)), (T)0.5);
+      dst[c * FS + ((size_t)k * NY + y) * N + x0 + x] = scal(A + mul_mi(cmul(wk, B)), (T)0.5);
     }
   } else if constexpr (MODE == ZM_STORE) {
     cx<T>* out = reinterpret_cast<cx<T>*>(a.out);
     for (int e = threadIdx.x; e < 3 * TX * M; e += ZP_THREADS) {
       const int n = e % M, x = (e / M) % TX, c = e / (M * TX);
-      out[((size_t)(c * N + x0 + x) * N + y) * M + n] = conjg(s[padp(n) * LD + c * TX + x]);
+      out[((size_t)(c * N + x0 + x) * NY + y) * M + n] = conjg(s[padp(n) * LD + c * TX + x]);
     }
   } else if constexpr (MODE == ZM_MAXABS) {
     double m = 0.0;
@@ -657,9 +673,9 @@ __device__ __forceinline__ void zpass_body(const PassArgs a, const int bx, const
   }
 }
 
-template <typename T, int N, int MODE, int TXO = 0>
-__global__ void __launch_bounds__(ZP_THREADS, (Geometry<T, N>::ZMIN)) k_zpass(PassArgs a) {
-  zpass_body<T, N, MODE, TXO>(a, blockIdx.x, blockIdx.y);
+template <typename T, int N, int MODE, int TXO = 0, int NY = N, int NZ = N>
+__global__ void __launch_bounds__(ZP_THREADS, (Geometry<T, N, NY, NZ>::ZMIN)) k_zpass(PassArgs a) {
+  zpass_body<T, N, MODE, TXO, NY, NZ>(a, blockIdx.x, blockIdx.y);
 }
 
 // Batched form (ensembles): member blockIdx.z (TXO: a tuned tile width).
@@ -1669,15 +1685,15 @@ __global__ void __launch_bounds__(32 * Z8Q<T>::NW, 2) k_zcross8q(PassArgs a) {
 //   sum w|u|^2, sum w|omega|^2, sum w Re(conj(u).omega), count of non-finite,
 // w = 1 at kz = 0 and 2 otherwise (half spectrum; kz = N/2 is zero).
 // ---------------------------------------------------------------------------
-template <typename T, int N>
+template <typename T, int N, int NY = N, int NZ = N>
 __global__ void __launch_bounds__(DG_THREADS) k_diag(PassArgs a) {
-  using G = Geometry<T, N>;
+  using G = Geometry<T, N, NY, NZ>;
   constexpr size_t FS = G::FS;
   const cx<T>* U = reinterpret_cast<const cx<T>*>(a.U);
   double se = 0, sz = 0, sh = 0, bad = 0;
   for (size_t i = (size_t)blockIdx.x * DG_THREADS + threadIdx.x; i < FS; i += (size_t)gridDim.x * DG_THREADS) {
-    const int kxi = (int)(i % N), kyi = (int)((i / N) % N), kzi = (int)(i / ((size_t)N * N));
-    const double kx = kfreq(kxi, N) * a.ks[0], ky = kfreq(kyi, N) * a.ks[1], kz = kzi * a.ks[2];
+    const int kxi = (int)(i % N), kyi = (int)((i / N) % NY), kzi = (int)(i / ((size_t)N * NY));
+    const double kx = kfreq(kxi, N) * a.ks[0], ky = kfreq(kyi, NY) * a.ks[1], kz = kzi * a.ks[2];
     const double w = kzi == 0 ? 1.0 : 2.0;
     const cx<T> a0 = U[i], a1 = U[FS + i], a2 = U[2 * FS + i];
     const double u0r = a0.x, u0i = a0.y, u1r = a1.x, u1i = a1.y, u2r = a2.x, u2i = a2.y;
@@ -1916,10 +1932,20 @@ inline int num_sms() {
   return n;
 }
 
-template <typename T, int N>
+// NY, NZ: points along y and z where they differ from N (a non-cubic grid runs the
+// generic passes only: no tuned tile widths, specialised z-passes, batched
+// ensembles or plane pass).
+template <typename T, int N, int NY = N, int NZ = N>
 struct SolverImpl {
-  using G = Geometry<T, N>;
+  using G = Geometry<T, N, NY, NZ>;
   static constexpr int M = G::M;
+  static constexpr bool ISO = NY == N && NZ == N;
+  static constexpr int ROWS = M * NY;  // x-pass rows (kz, ky)
+  static constexpr bool BATCHED = ISO && N <= BATCH_MAX_N && !ZCross<T, N>::enabled;
+  static constexpr bool PLANE = ISO && PlaneCfg<T, N>::enabled;
+  // each direction's 2/3 cut-off (3|k_i| < kmax3 of that direction)
+  static int k3y(const PassArgs& a) { return NY == N ? a.kmax3 : a.kmax3y; }
+  static int k3z(const PassArgs& a) { return NZ == N ? a.kmax3 : a.kmax3z; }
 
   template <class K>
   static cudaError_t smem_attr(K k, size_t bytes) {
@@ -1929,7 +1955,7 @@ struct SolverImpl {
   // y-pass tile widths offered to a tuner besides the default (grids of the
   // ensembles only, to bound the number of instantiations)
   static constexpr bool ytile_ok(int t) {
-    return N <= BATCH_MAX_N && t >= 4 && t <= 32 && pow2_part(N) % t == 0 && t * (int)sizeof(cx<T>) <= 256;
+    return ISO && N <= BATCH_MAX_N && t >= 4 && t <= 32 && pow2_part(N) % t == 0 && t * (int)sizeof(cx<T>) <= 256;
   }
   template <int TXO>
   static void tile_attr(cudaError_t& e) {
@@ -1950,7 +1976,7 @@ struct SolverImpl {
   }
   // z-pass tile widths offered besides the default (the generic z-pass of the small grids)
   static constexpr bool ztile_ok(int t) {
-    return N <= BATCH_MAX_N && !ZCross<T, N>::enabled && t >= 4 && t <= 32 && pow2_part(N) % t == 0 &&
+    return ISO && N <= BATCH_MAX_N && !ZCross<T, N>::enabled && t >= 4 && t <= 32 && pow2_part(N) % t == 0 &&
            G::zbytes(t) <= 112 * 1024;
   }
   template <int TXO>
@@ -1969,17 +1995,17 @@ struct SolverImpl {
   template <int TXO>
   static void z_go(const PassArgs& a, cudaStream_t st) {
     constexpr int TX = TXO > 0 ? TXO : G::ZTX;
-    k_zpass<T, N, ZM_CROSS, TXO><<<dim3(N / TX, N), ZP_THREADS, G::zbytes(TX), st>>>(a);
+    k_zpass<T, N, ZM_CROSS, TXO, NY, NZ><<<dim3(N / TX, NY), ZP_THREADS, G::zbytes(TX), st>>>(a);
   }
   template <int INV, int PRUNE, int TXO>
   static void y_go(cx<T>* F, const cx<T>* tw, int kmax3, int planes, int fields, cudaStream_t st) {
-    using Y = YCfg<T, N, INV, TXO>;
-    k_ypass<T, N, INV, PRUNE, TXO><<<dim3(N / Y::TX, planes, fields), Y::THREADS, Y::SMEM, st>>>(F, tw, kmax3);
+    using Y = YCfg<T, N, INV, TXO, NY>;
+    k_ypass<T, N, INV, PRUNE, TXO, NY, NZ><<<dim3(N / Y::TX, planes, fields), Y::THREADS, Y::SMEM, st>>>(F, tw, kmax3);
   }
   // the stage's y-pass with tile width `tile` (0, or a width not offered: the default)
   template <int INV, int PRUNE>
   static void y_stage(int tile, cx<T>* F, const cx<T>* tw, int kmax3, int planes, int fields, cudaStream_t st) {
-    if constexpr (N <= BATCH_MAX_N) {
+    if constexpr (ISO && N <= BATCH_MAX_N) {
       if constexpr (ytile_ok(4)) if (tile == 4) return y_go<INV, PRUNE, 4>(F, tw, kmax3, planes, fields, st);
       if constexpr (ytile_ok(8)) if (tile == 8) return y_go<INV, PRUNE, 8>(F, tw, kmax3, planes, fields, st);
       if constexpr (ytile_ok(16)) if (tile == 16) return y_go<INV, PRUNE, 16>(F, tw, kmax3, planes, fields, st);
@@ -2000,27 +2026,27 @@ struct SolverImpl {
     ztile_attr<32>(e);
 #define DNS_ATTR(kern, bytes) \
   if (e == cudaSuccess) e = smem_attr(kern, bytes)
-    DNS_ATTR((k_xpass<T, N, XM_INV_CURL>), G::XSMEM);
-    DNS_ATTR((k_xpass<T, N, XM_STAGE>), G::XSMEM_ST);
-    DNS_ATTR((k_xpass<T, N, XM_STAGE2N>), G::XSMEM_ST);
-    DNS_ATTR((k_xpass<T, N, XM_RHS>), G::XSMEM_ST);
-    DNS_ATTR((k_xpass<T, N, XM_FWD_STORE>), G::XSMEM);
-    DNS_ATTR((k_xpass<T, N, XM_INV_PLAIN>), G::XSMEM);
-    DNS_ATTR((k_xpass<T, N, XM_INV_DIV>), G::XSMEM);
-    DNS_ATTR((k_ypass<T, N, 1, 0>), (YCfg<T, N, 1>::SMEM));
-    DNS_ATTR((k_ypass<T, N, 0, 1>), (YCfg<T, N, 0>::SMEM));
-    DNS_ATTR((k_ypass<T, N, 0, 0>), (YCfg<T, N, 0>::SMEM));
-    DNS_ATTR((k_zpass<T, N, ZM_CROSS>), G::ZSMEM);
-    if constexpr (ZCross<T, N>::enabled) DNS_ATTR((k_zcross<T, N>), G::ZSMEM);
-    if constexpr (N == 512) DNS_ATTR((k_zcross16<T, N>), G::ZSMEM);
-    if constexpr (N == 512 && sizeof(T) == 4) DNS_ATTR((k_zcross16p<T, N>), Z16P<T>::SMEM);
-    if constexpr (N == 1024 && sizeof(T) == 4) DNS_ATTR((k_zcross32p<T, N>), Z32P<T>::SMEM);
-    if constexpr (N == 256 && sizeof(T) == 4) DNS_ATTR((k_zcross8q<T, N>), Z8Q<T>::SMEM);
-    if constexpr (PlaneCfg<T, N>::enabled) DNS_ATTR((k_plane<T, N>), (plane_smem(1, 3)));
-    DNS_ATTR((k_zpass<T, N, ZM_STORE>), G::ZSMEM);
-    DNS_ATTR((k_zpass<T, N, ZM_LOAD>), G::ZSMEM);
-    DNS_ATTR((k_zpass<T, N, ZM_MAXABS>), G::ZSMEM);
-    if constexpr (N <= BATCH_MAX_N && !ZCross<T, N>::enabled) {
+    DNS_ATTR((k_xpass<T, N, XM_INV_CURL, NY, NZ>), G::XSMEM);
+    DNS_ATTR((k_xpass<T, N, XM_STAGE, NY, NZ>), G::XSMEM_ST);
+    DNS_ATTR((k_xpass<T, N, XM_STAGE2N, NY, NZ>), G::XSMEM_ST);
+    DNS_ATTR((k_xpass<T, N, XM_RHS, NY, NZ>), G::XSMEM_ST);
+    DNS_ATTR((k_xpass<T, N, XM_FWD_STORE, NY, NZ>), G::XSMEM);
+    DNS_ATTR((k_xpass<T, N, XM_INV_PLAIN, NY, NZ>), G::XSMEM);
+    DNS_ATTR((k_xpass<T, N, XM_INV_DIV, NY, NZ>), G::XSMEM);
+    DNS_ATTR((k_ypass<T, N, 1, 0, 0, NY, NZ>), (YCfg<T, N, 1, 0, NY>::SMEM));
+    DNS_ATTR((k_ypass<T, N, 0, 1, 0, NY, NZ>), (YCfg<T, N, 0, 0, NY>::SMEM));
+    DNS_ATTR((k_ypass<T, N, 0, 0, 0, NY, NZ>), (YCfg<T, N, 0, 0, NY>::SMEM));
+    DNS_ATTR((k_zpass<T, N, ZM_CROSS, 0, NY, NZ>), G::ZSMEM);
+    if constexpr (ISO && ZCross<T, N>::enabled) DNS_ATTR((k_zcross<T, N>), G::ZSMEM);
+    if constexpr (ISO && N == 512) DNS_ATTR((k_zcross16<T, N>), G::ZSMEM);
+    if constexpr (ISO && N == 512 && sizeof(T) == 4) DNS_ATTR((k_zcross16p<T, N>), Z16P<T>::SMEM);
+    if constexpr (ISO && N == 1024 && sizeof(T) == 4) DNS_ATTR((k_zcross32p<T, N>), Z32P<T>::SMEM);
+    if constexpr (ISO && N == 256 && sizeof(T) == 4) DNS_ATTR((k_zcross8q<T, N>), Z8Q<T>::SMEM);
+    if constexpr (PLANE) DNS_ATTR((k_plane<T, N>), (plane_smem(1, 3)));
+    DNS_ATTR((k_zpass<T, N, ZM_STORE, 0, NY, NZ>), G::ZSMEM);
+    DNS_ATTR((k_zpass<T, N, ZM_LOAD, 0, NY, NZ>), G::ZSMEM);
+    DNS_ATTR((k_zpass<T, N, ZM_MAXABS, 0, NY, NZ>), G::ZSMEM);
+    if constexpr (BATCHED) {
       DNS_ATTR((k_ypass_b<T, N, 1, 0>), (YCfg<T, N, 1>::SMEM));
       DNS_ATTR((k_zpass_b<T, N, ZM_CROSS>), G::ZSMEM);
       DNS_ATTR((k_ypass_b<T, N, 0, 1>), (YCfg<T, N, 0>::SMEM));
@@ -2032,7 +2058,9 @@ struct SolverImpl {
   }
 
   static void z_cross(const PassArgs& a, cudaStream_t st) {
-    if constexpr (N == 512 && sizeof(T) == 4)
+    if constexpr (!ISO)
+      z_go<0>(a, st);
+    else if constexpr (N == 512 && sizeof(T) == 4)
       k_zcross16p<T, N><<<num_sms(), 32 * Z16P<T>::NW, Z16P<T>::SMEM, st>>>(a);
     else if constexpr (N == 512)
       k_zcross16<T, N><<<dim3(N / G::ZTX, N), 32 * Z16Warps<T, N>::value, G::ZSMEM, st>>>(a);
@@ -2071,24 +2099,24 @@ struct SolverImpl {
   static cudaError_t x_inverse_curl(const PassArgs& a0, int from_stage, cudaStream_t st) {
     PassArgs a = a0;
     if (from_stage) a.U = a.US;
-    k_xpass<T, N, XM_INV_CURL><<<M * N, XP_THREADS, G::XSMEM, st>>>(f32args(a));
+    k_xpass<T, N, XM_INV_CURL, NY, NZ><<<ROWS, XP_THREADS, G::XSMEM, st>>>(f32args(a));
     return cudaGetLastError();
   }
 
   static void rhs_front(const PassArgs& a, cudaStream_t st) {
     cx<T>* W = reinterpret_cast<cx<T>*>(a.W);
     const cx<T>* tw = reinterpret_cast<const cx<T>*>(a.tw);
-    y_stage<1, 0>(a.ytile[0], W, tw, a.kmax3, M, 6, st);
+    y_stage<1, 0>(a.ytile[0], W, tw, k3y(a), M, 6, st);
     z_cross(a, st);
-    y_stage<0, 1>(a.ytile[1], W, tw, a.kmax3, kc_of(a.kmax3), 3, st);
+    y_stage<0, 1>(a.ytile[1], W, tw, k3y(a), kc_of(k3z(a)), 3, st);
   }
 
   // the x-stage launch of a stage, in the form of the stage's scheme
   static void x_stage(const PassArgs& a, cudaStream_t st) {
     if (a.lsrk)
-      k_xpass<T, N, XM_STAGE2N><<<M * N, XP_THREADS, xsmem_stage(a.stage, a.last), st>>>(f32args(a));
+      k_xpass<T, N, XM_STAGE2N, NY, NZ><<<ROWS, XP_THREADS, xsmem_stage(a.stage, a.last), st>>>(f32args(a));
     else
-      k_xpass<T, N, XM_STAGE><<<M * N, XP_THREADS, xsmem_stage(a.stage, a.last), st>>>(f32args(a));
+      k_xpass<T, N, XM_STAGE, NY, NZ><<<ROWS, XP_THREADS, xsmem_stage(a.stage, a.last), st>>>(f32args(a));
   }
 
   static cudaError_t rk_stage(const PassArgs& a, cudaStream_t st) {
@@ -2101,9 +2129,9 @@ struct SolverImpl {
     cx<T>* W = reinterpret_cast<cx<T>*>(a.W);
     const cx<T>* tw = reinterpret_cast<const cx<T>*>(a.tw);
     switch (part) {
-      case 0: y_stage<1, 0>(a.ytile[0], W, tw, a.kmax3, M, 6, st); break;
+      case 0: y_stage<1, 0>(a.ytile[0], W, tw, k3y(a), M, 6, st); break;
       case 1: z_cross(a, st); break;
-      case 2: y_stage<0, 1>(a.ytile[1], W, tw, a.kmax3, kc_of(a.kmax3), 3, st); break;
+      case 2: y_stage<0, 1>(a.ytile[1], W, tw, k3y(a), kc_of(k3z(a)), 3, st); break;
       default: x_stage(a, st); break;
     }
     return cudaGetLastError();
@@ -2117,7 +2145,7 @@ struct SolverImpl {
   }
   template <int INV, int PRUNE>
   static void yb_stage(int tile, const BatchArgs& B, int count, int planes, int fields, cudaStream_t st) {
-    if constexpr (N <= BATCH_MAX_N) {
+    if constexpr (ISO && N <= BATCH_MAX_N) {
       if constexpr (ytile_ok(4)) if (tile == 4) return yb_go<INV, PRUNE, 4>(B, count, planes, fields, st);
       if constexpr (ytile_ok(8)) if (tile == 8) return yb_go<INV, PRUNE, 8>(B, count, planes, fields, st);
       if constexpr (ytile_ok(16)) if (tile == 16) return yb_go<INV, PRUNE, 16>(B, count, planes, fields, st);
@@ -2139,7 +2167,7 @@ struct SolverImpl {
   }
 
   static cudaError_t rk_stage_batch(const PassArgs* A, int count, int kmax3, cudaStream_t st) {
-    if constexpr (N <= BATCH_MAX_N && N != 512 && N != 1024 && !ZCross<T, N>::enabled) {
+    if constexpr (BATCHED && N != 512 && N != 1024) {
       if (count < 1 || count > BATCH_MAX_COUNT) return cudaErrorInvalidValue;
       BatchArgs B;
       for (int i = 0; i < count; ++i) B.a[i] = f32args(A[i]);
@@ -2178,7 +2206,7 @@ struct SolverImpl {
     k_plane<T, N><<<blocks, PLANE_THREADS, plane_smem(a.stage, a.last), st>>>(f32args(a), a.ctl, L);
   }
   static cudaError_t rk_stage_fused(const PassArgs& a, cudaStream_t st) {
-    if constexpr (PC::enabled) {
+    if constexpr (PLANE) {
       cudaError_t e = plane_reset(a, st);
       if (e != cudaSuccess) return e;
       z_cross(a, st);
@@ -2189,7 +2217,7 @@ struct SolverImpl {
     }
   }
   static cudaError_t rk_stage_fused_part(const PassArgs& a, int part, cudaStream_t st) {
-    if constexpr (PC::enabled) {
+    if constexpr (PLANE) {
       if (part == 0) {
         cudaError_t e = plane_reset(a, st);
         if (e != cudaSuccess) return e;
@@ -2205,11 +2233,11 @@ struct SolverImpl {
   static cudaError_t prime_fused(const PassArgs& a, int from_stage, cudaStream_t st) {
     cudaError_t e = x_inverse_curl(a, from_stage, st);
     if (e != cudaSuccess) return e;
-    y_go<1, 0, 0>(reinterpret_cast<cx<T>*>(a.W), reinterpret_cast<const cx<T>*>(a.tw), a.kmax3, M, 6, st);
+    y_go<1, 0, 0>(reinterpret_cast<cx<T>*>(a.W), reinterpret_cast<const cx<T>*>(a.tw), k3y(a), M, 6, st);
     return cudaGetLastError();
   }
   static cudaError_t plane_wait_test(const PassArgs& a, cudaStream_t st) {
-    if constexpr (PC::enabled) {
+    if constexpr (PLANE) {
       int kc = (a.kmax3 + 2) / 3;
       if (kc > M) kc = M;
       // the chunks of steps 0 .. 2L-1 and step 2L's y-forward and x-stage chunks
@@ -2234,46 +2262,47 @@ struct SolverImpl {
     rhs_front(a, st);
     PassArgs b = a;
     b.stage = 0;
-    k_xpass<T, N, XM_RHS><<<M * N, XP_THREADS, xsmem_stage(0, 3), st>>>(f32args(b));
+    k_xpass<T, N, XM_RHS, NY, NZ><<<ROWS, XP_THREADS, xsmem_stage(0, 3), st>>>(f32args(b));
     return cudaGetLastError();
   }
 
   static cudaError_t forward3d(const PassArgs& a, cudaStream_t st) {
-    k_zpass<T, N, ZM_LOAD><<<dim3(N / G::ZTX, N), ZP_THREADS, G::ZSMEM, st>>>(a);
-    k_ypass<T, N, 0, 0><<<dim3(N / YCfg<T, N, 0>::TX, M, 3), YCfg<T, N, 0>::THREADS, YCfg<T, N, 0>::SMEM, st>>>(
-        reinterpret_cast<cx<T>*>(a.U), reinterpret_cast<const cx<T>*>(a.tw), a.kmax3);
-    k_xpass<T, N, XM_FWD_STORE><<<M * N, XP_THREADS, G::XSMEM, st>>>(f32args(a));
+    using Y = YCfg<T, N, 0, 0, NY>;
+    k_zpass<T, N, ZM_LOAD, 0, NY, NZ><<<dim3(N / G::ZTX, NY), ZP_THREADS, G::ZSMEM, st>>>(a);
+    k_ypass<T, N, 0, 0, 0, NY, NZ><<<dim3(N / Y::TX, M, 3), Y::THREADS, Y::SMEM, st>>>(
+        reinterpret_cast<cx<T>*>(a.U), reinterpret_cast<const cx<T>*>(a.tw), k3y(a));
+    k_xpass<T, N, XM_FWD_STORE, NY, NZ><<<ROWS, XP_THREADS, G::XSMEM, st>>>(f32args(a));
     return cudaGetLastError();
   }
 
   static cudaError_t inverse3d(const PassArgs& a, cudaStream_t st) {
-    k_xpass<T, N, XM_INV_PLAIN><<<M * N, XP_THREADS, G::XSMEM, st>>>(f32args(a));
-    k_ypass<T, N, 1, 0><<<dim3(N / YCfg<T, N, 1>::TX, M, 3), YCfg<T, N, 1>::THREADS, YCfg<T, N, 1>::SMEM, st>>>(
-        reinterpret_cast<cx<T>*>(a.W), reinterpret_cast<const cx<T>*>(a.tw), a.kmax3);
-    k_zpass<T, N, ZM_STORE><<<dim3(N / G::ZTX, N), ZP_THREADS, G::ZSMEM, st>>>(a);
+    using Y = YCfg<T, N, 1, 0, NY>;
+    k_xpass<T, N, XM_INV_PLAIN, NY, NZ><<<ROWS, XP_THREADS, G::XSMEM, st>>>(f32args(a));
+    k_ypass<T, N, 1, 0, 0, NY, NZ><<<dim3(N / Y::TX, M, 3), Y::THREADS, Y::SMEM, st>>>(
+        reinterpret_cast<cx<T>*>(a.W), reinterpret_cast<const cx<T>*>(a.tw), k3y(a));
+    k_zpass<T, N, ZM_STORE, 0, NY, NZ><<<dim3(N / G::ZTX, NY), ZP_THREADS, G::ZSMEM, st>>>(a);
     return cudaGetLastError();
   }
 
   static cudaError_t diag(const PassArgs& a, cudaStream_t st) {
-    k_diag<T, N><<<DIAG_BLOCKS, DG_THREADS, 0, st>>>(a);
+    using Y = YCfg<T, N, 1, 0, NY>;
+    k_diag<T, N, NY, NZ><<<DIAG_BLOCKS, DG_THREADS, 0, st>>>(a);
     k_diag_final<<<1, 32, 0, st>>>(a.partials, DIAG_BLOCKS);
-    k_xpass<T, N, XM_INV_DIV><<<M * N, XP_THREADS, G::XSMEM, st>>>(f32args(a));
-    k_ypass<T, N, 1, 0><<<dim3(N / YCfg<T, N, 1>::TX, M, 1), YCfg<T, N, 1>::THREADS, YCfg<T, N, 1>::SMEM, st>>>(
-        reinterpret_cast<cx<T>*>(a.D), reinterpret_cast<const cx<T>*>(a.tw), a.kmax3);
+    k_xpass<T, N, XM_INV_DIV, NY, NZ><<<ROWS, XP_THREADS, G::XSMEM, st>>>(f32args(a));
+    k_ypass<T, N, 1, 0, 0, NY, NZ><<<dim3(N / Y::TX, M, 1), Y::THREADS, Y::SMEM, st>>>(
+        reinterpret_cast<cx<T>*>(a.D), reinterpret_cast<const cx<T>*>(a.tw), k3y(a));
     cudaMemsetAsync(a.maxbits, 0, sizeof(unsigned long long), st);
-    k_zpass<T, N, ZM_MAXABS><<<dim3(N / G::ZTX, N), ZP_THREADS, G::ZSMEM, st>>>(a);
+    k_zpass<T, N, ZM_MAXABS, 0, NY, NZ><<<dim3(N / G::ZTX, NY), ZP_THREADS, G::ZSMEM, st>>>(a);
     return cudaGetLastError();
   }
 
   static const DnsOps* ops() {
-    constexpr bool batched = N <= BATCH_MAX_N && !ZCross<T, N>::enabled;
-    constexpr bool plane = PlaneCfg<T, N>::enabled;
     static const DnsOps o = {N,         sizeof(T) == 4 ? 0 : 1, sizeof(cx<T>), &prepare,   &x_inverse_curl,
                              &rk_stage, &rk_stage_part,        &rhs,          &forward3d, &inverse3d,
-                             &diag,     batched ? &rk_stage_batch : nullptr, &y_tiles, &z_tiles,
-                             plane ? &rk_stage_fused : nullptr, &prime_fused,
-                             plane ? &rk_stage_fused_part : nullptr, plane ? &plane_wait_test : nullptr,
-                             plane ? PlaneCfg<T, N>::ctl_words() : 0};
+                             &diag,     BATCHED ? &rk_stage_batch : nullptr, &y_tiles, &z_tiles,
+                             PLANE ? &rk_stage_fused : nullptr, &prime_fused,
+                             PLANE ? &rk_stage_fused_part : nullptr, PLANE ? &plane_wait_test : nullptr,
+                             PLANE ? PlaneCfg<T, N>::ctl_words() : 0, NY, NZ, G::TW};
     return &o;
   }
 };

@@ -46,22 +46,36 @@ def _ptr(arr, shape, real_dtype_bytes, complex_):
 INTEGRATORS = {"rk4": 0, "euler": 1, "heun": 2, "midpoint": 3, "williamson3": 4, "ck45": 5}
 
 
-class Solver:
-    """One dns_handle: N^3 grid, viscosity nu, time step dt, 'f32' or 'f64'; integrator
-    'rk4' (the Appendix driver, default), 'euler', 'heun' or 'midpoint'; box lengths
-    (Lx, Ly, Lz), default (2 pi, 2 pi, 2 pi)."""
+def _shape(N) -> tuple:
+    """(Nx, Ny, Nz) from one point count or three."""
+    if np.ndim(N) == 0:
+        return (int(N),) * 3
+    n = tuple(int(v) for v in N)
+    if len(n) != 3:
+        raise ValueError("N must be one point count or three (Nx, Ny, Nz)")
+    return n
 
-    def __init__(self, N: int, nu: float, dt: float, dtype: str = "f32", dealias_variant: int = 0,
+
+class Solver:
+    """One dns_handle: N^3 grid (or N = (Nx, Ny, Nz), a compiled grid with other point
+    counts per direction), viscosity nu, time step dt, 'f32' or 'f64'; integrator
+    'rk4' (the Appendix driver, default), 'euler', 'heun' or 'midpoint'; box lengths
+    (Lx, Ly, Lz), default (2 pi, 2 pi, 2 pi). ``shape`` is (Nx, Ny, Nz); ``N`` the count
+    along x."""
+
+    def __init__(self, N, nu: float, dt: float, dtype: str = "f32", dealias_variant: int = 0,
                  integrator: str = "rk4", lengths=None):
         if integrator not in INTEGRATORS:
             raise ValueError(f"integrator must be one of {sorted(INTEGRATORS)}, got {integrator!r}")
-        self.N = int(N)
+        self.shape = _shape(N)
+        self.N = self.shape[0]
         self.dtype = dtype
         self._code = {"f32": _lib.DNS_F32, "f64": _lib.DNS_F64}[dtype]
         self._rb = 4 if dtype == "f32" else 8
         self._owned = True
         h = ctypes.c_void_p()
-        _lib.check(_lib.lib().dns_create(self.N, float(nu), float(dt), self._code, ctypes.byref(h)), "dns_create")
+        nx, ny, nz = self.shape
+        _lib.check(_lib.lib().dns_create3(nx, ny, nz, float(nu), float(dt), self._code, ctypes.byref(h)), "dns_create")
         self._h = h
         if dealias_variant:
             self.set_option("dealias_variant", dealias_variant)
@@ -76,6 +90,7 @@ class Solver:
         """Wrap a handle owned elsewhere (an ensemble member); close() does not free it."""
         obj = cls.__new__(cls)
         obj.N, obj.dtype = int(N), dtype
+        obj.shape = (obj.N,) * 3
         obj._code = {"f32": _lib.DNS_F32, "f64": _lib.DNS_F64}[dtype]
         obj._rb = 4 if dtype == "f32" else 8
         obj._owned = False
@@ -108,11 +123,12 @@ class Solver:
     # -- shapes ---------------------------------------------------------------
     @property
     def phys_shape(self):
-        return (3, self.N, self.N, self.N)
+        return (3,) + self.shape
 
     @property
     def spec_shape(self):
-        return (3, self.N, self.N, self.N // 2 + 1)
+        nx, ny, nz = self.shape
+        return (3, nx, ny, nz // 2 + 1)
 
     # -- calls ----------------------------------------------------------------
     def set_stream(self, stream=None):
