@@ -902,9 +902,10 @@ struct HwTw {
 struct HwTwL {
   cx<float> p2[16];
   cx<float> tl;
-  __device__ __forceinline__ void init(const cx<float>* __restrict__ tw, int h) {
-    twiddle_powers<16>(ldro(tw + 2 * h), p2);
-    tl = ldro(tw + h);
+  // ts: stride into a twiddle table longer than the real line's own (1 on its own table)
+  __device__ __forceinline__ void init(const cx<float>* __restrict__ tw, int h, int ts = 1) {
+    twiddle_powers<16>(ldro(tw + 2 * h * ts), p2);
+    tl = ldro(tw + h * ts);
   }
   __device__ __forceinline__ cx<float> wk(const cx<float>* __restrict__, int, int m) const {
     constexpr float c[16][2] = {
@@ -1557,13 +1558,15 @@ struct Z8Q {
 // z-pass for N = 256, FP32: one tile (16 adjacent x at fixed y, 6 fields of 128
 // values) per block, fetched whole by cp.async, two blocks per SM; each warp
 // transforms four lines at once as quarter-warps (lines b, b + 8, b + 1, b + 9).
-template <typename T, int N>
+// NY, NZ: counts along y and z where they differ from N (NZ = 256; N a multiple of 16).
+template <typename T, int N, int NY = N, int NZ = N>
 __global__ void __launch_bounds__(32 * Z8Q<T>::NW, 2) k_zcross8q(PassArgs a) {
   using P = Z8Q<T>;
-  using G = Geometry<T, N>;
+  using G = Geometry<T, N, NY, NZ>;
   constexpr int M = P::M, TX = P::TX, LD = P::LD, NW = P::NW, ITEMS = P::ITEMS;
   constexpr size_t FS = G::FS;
-  static_assert(N == 256 && sizeof(T) == 4 && TX == 16, "k_zcross8q is the FP32 N = 256 z-pass");
+  constexpr size_t PL = (size_t)NY * N;  // one kz plane
+  static_assert(NZ == 256 && N % TX == 0 && sizeof(T) == 4 && TX == 16, "k_zcross8q is the FP32 256-point z-pass");
   static_assert((6 * ITEMS) % NW == 0, "z tile split");
   extern __shared__ unsigned char smraw[];
   cx<T>* s = reinterpret_cast<cx<T>*>(smraw);
@@ -1572,26 +1575,26 @@ __global__ void __launch_bounds__(32 * Z8Q<T>::NW, 2) k_zcross8q(PassArgs a) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int h = lane & 7, qw = lane >> 3;
   const int x0 = blockIdx.x * TX, y = blockIdx.y;
-  int kc = (a.kmax3 + 2) / 3;
+  int kc = ((NZ == N ? a.kmax3 : a.kmax3z) + 2) / 3;
   if (kc > M) kc = M;
   const int tx = lane % TX, kq = lane / TX;
   // walk kz = 32 g + TX kq + c: padp(kz) = 34 g + padp(TX kq) + c
   cx<T>* const sl = s + padp(TX * kq) * LD + tx;
-  const cx<T>* gl = W + ((size_t)(TX * kq) * N + y) * N + x0 + tx;
+  const cx<T>* gl = W + ((size_t)(TX * kq) * NY + y) * N + x0 + tx;
   // warp w takes the 32 consecutive walk items 32 w + j (j = 16 a + b): field w / 2, row group
   // g = 2 (w % 2) + a, row offset c = b: a per-warp base plus compile-time offsets
   static_assert(TX == 16 && ITEMS == 64 && 6 * ITEMS == 32 * NW && 3 * ITEMS == 16 * NW, "z tile chunking");
   {
     const int f = w / 2, q = w % 2;
-    const cx<T>* gf = gl + (size_t)f * FS + (size_t)(64 * q) * N * N;
+    const cx<T>* gf = gl + (size_t)f * FS + (size_t)(64 * q) * PL;
     cx<T>* sd = sl + 68 * q * LD + f * TX;
 #pragma unroll
     for (int j = 0; j < 32; ++j)
-      cp_async<sizeof(cx<T>)>(sd + (34 * (j / 16) + j % 16) * LD, gf + (size_t)(32 * (j / 16) + j % 16) * N * N);
+      cp_async<sizeof(cx<T>)>(sd + (34 * (j / 16) + j % 16) * LD, gf + (size_t)(32 * (j / 16) + j % 16) * PL);
   }
   cp_async_commit();
   HwTwL qt;  // w = exp(-2 pi i h / 128), tl = exp(-2 pi i h / 256)
-  qt.init(tw, h);
+  qt.init(tw, h, G::TW / NZ);
   // quarter-warp line of group gi (groups of 4 lines b, b + 8, b + 1, b + 9 with b = 16 f + 2 i)
   auto line_of = [&](int gi) { return 16 * (gi >> 2) + 2 * (gi & 3) + (qw & 1) * 8 + (qw >> 1); };
   cp_async_wait<0>();
@@ -1672,11 +1675,11 @@ __global__ void __launch_bounds__(32 * Z8Q<T>::NW, 2) k_zcross8q(PassArgs a) {
   __syncthreads();
   {  // warp w stores items 16 w + j: field w / 4, rows 32 (w % 4) + TX kq + j
     const int f = w / 4, g = w % 4, k0 = 32 * g + TX * kq;
-    cx<T>* gd = W + ((size_t)(TX * kq) * N + y) * N + x0 + tx + (size_t)f * FS + (size_t)(32 * g) * N * N;
+    cx<T>* gd = W + ((size_t)(TX * kq) * NY + y) * N + x0 + tx + (size_t)f * FS + (size_t)(32 * g) * PL;
     const cx<T>* sd = sl + 34 * g * LD + f * TX;
 #pragma unroll
     for (int j = 0; j < 16; ++j)
-      if (k0 + j < kc) gd[(size_t)j * N * N] = sd[j * LD];
+      if (k0 + j < kc) gd[(size_t)j * PL] = sd[j * LD];
   }
 }
 
@@ -1943,6 +1946,8 @@ struct SolverImpl {
   static constexpr int ROWS = M * NY;  // x-pass rows (kz, ky)
   static constexpr bool BATCHED = ISO && N <= BATCH_MAX_N && !ZCross<T, N>::enabled;
   static constexpr bool PLANE = ISO && PlaneCfg<T, N>::enabled;
+  // non-cubic grids with 256-point FP32 z-lines use the quarter-warp z-pass of 256^3
+  static constexpr bool Z8_BOX = !ISO && NZ == 256 && sizeof(T) == 4 && N % 16 == 0;
   // each direction's 2/3 cut-off (3|k_i| < kmax3 of that direction)
   static int k3y(const PassArgs& a) { return NY == N ? a.kmax3 : a.kmax3y; }
   static int k3z(const PassArgs& a) { return NZ == N ? a.kmax3 : a.kmax3z; }
@@ -2042,6 +2047,7 @@ struct SolverImpl {
     if constexpr (ISO && N == 512 && sizeof(T) == 4) DNS_ATTR((k_zcross16p<T, N>), Z16P<T>::SMEM);
     if constexpr (ISO && N == 1024 && sizeof(T) == 4) DNS_ATTR((k_zcross32p<T, N>), Z32P<T>::SMEM);
     if constexpr (ISO && N == 256 && sizeof(T) == 4) DNS_ATTR((k_zcross8q<T, N>), Z8Q<T>::SMEM);
+    if constexpr (Z8_BOX) DNS_ATTR((k_zcross8q<T, N, NY, NZ>), Z8Q<T>::SMEM);
     if constexpr (PLANE) DNS_ATTR((k_plane<T, N>), (plane_smem(1, 3)));
     DNS_ATTR((k_zpass<T, N, ZM_STORE, 0, NY, NZ>), G::ZSMEM);
     DNS_ATTR((k_zpass<T, N, ZM_LOAD, 0, NY, NZ>), G::ZSMEM);
@@ -2058,7 +2064,9 @@ struct SolverImpl {
   }
 
   static void z_cross(const PassArgs& a, cudaStream_t st) {
-    if constexpr (!ISO)
+    if constexpr (Z8_BOX)
+      k_zcross8q<T, N, NY, NZ><<<dim3(N / Z8Q<T>::TX, NY), 32 * Z8Q<T>::NW, Z8Q<T>::SMEM, st>>>(a);
+    else if constexpr (!ISO)
       z_go<0>(a, st);
     else if constexpr (N == 512 && sizeof(T) == 4)
       k_zcross16p<T, N><<<num_sms(), 32 * Z16P<T>::NW, Z16P<T>::SMEM, st>>>(a);
