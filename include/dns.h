@@ -137,6 +137,15 @@ int dns_set_stream(dns_handle* h, void* stream);
  *   "z_tile"           x columns per block of the generic z-pass of the small
  *                      grids: 0 (default) or an offered width (4 .. 32); results
  *                      independent of it, see dns_tune_tiles.
+ *   "fft_plan"         radix schedule of the line transforms of each pass of a stage,
+ *                      N <= 128 only: a bit mask, bit 0 the x-stage (and the x inverse
+ *                      before the first stage), bit 1 the y-inverse, bit 2 the z-pass,
+ *                      bit 3 the y-forward; a clear bit keeps the default schedule
+ *                      (radix-8/16 passes, radix 3 last), a set bit takes radix 3 first,
+ *                      then radix-4 passes (one radix-8 pass for odd powers of two).
+ *                      The same transforms with another rounding order: results agree
+ *                      to round-off, not bit for bit; dns_tune_tiles picks the bits by
+ *                      timing. 0 (default) .. 15; only 0 on the other grids.
  *   "use_graph"        1: dns_step replays a captured CUDA graph (default)
  *   "fused_planes"     0 (default) or 1 where compiled (N >= 256): 1 runs each RK
  *                      stage as two launches, the z-pass and one persistent plane pass that
@@ -180,15 +189,17 @@ int dns_get_option(const dns_handle* h, const char* key, double* value);
  * arrays as the built-in schemes. Errors: DNS_ERR_ARG. */
 int dns_set_rk_tableau(dns_handle* h, int form, int stages, const double* a, const double* b);
 
-/* Schedule tuner for the small grids: times dns_step with every tile width the
- * grid offers for the y-inverse, the y-forward and the z-pass (default included),
- * one pass at a time with the best widths found before it, three timings of
- * `steps` graph replays each after a capture and a warm-up step; a width replaces
- * the one kept so far (starting from the default) only if its median time beats
- * that one's median by more than that one's spread (max - min); the kept widths
- * are written to *y_inverse, *y_forward, *z (0 = default). Every candidate starts from the same
- * state, and the state and time are restored at the end; the results of later
- * steps do not depend on the choice. Allocates and frees one state copy (3
+/* Schedule tuner for the small grids: times dns_step with both radix plans of each
+ * pass ("fft_plan" bits) and every tile width the grid offers for the y-inverse, the
+ * y-forward and the z-pass (defaults included), one knob at a time (the plan bits first)
+ * with the best values found before it, three timings of `steps` graph replays each
+ * after a capture and a warm-up step; a candidate replaces the one kept so far
+ * (starting from the default) only if its median time beats that one's median by
+ * more than that one's spread (max - min); the kept widths are written to
+ * *y_inverse, *y_forward, *z (0 = default) and the kept plan is the handle's
+ * "fft_plan". Every candidate starts from the same state, and the state and time
+ * are restored at the end; the results of later steps do not depend on the widths
+ * (the plan changes their rounding only). Allocates and frees one state copy (3
  * fields). Synchronises. Errors: DNS_ERR_ARG (steps < 1, NULL outputs),
  * DNS_ERR_OOM, DNS_ERR_CUDA. */
 int dns_tune_tiles(dns_handle* h, int steps, int* y_inverse, int* y_forward, int* z);
@@ -293,16 +304,16 @@ int dns_spectral_sums_noalloc(const void* uhat, int N, int dtype, double nu, dou
  * integrator (RK4 unless set on the member's handle; Sec. 3, Appendix driver);
  * each step is one launch of a CUDA graph.
  * Schedule: with batching on (default), members of equal N (N <= 128),
- * precision, dealias option and integrator are advanced together, one kernel launch per
+ * precision, dealias option, radix plan and integrator are advanced together, one kernel launch per
  * pass for up to min(max_batch, 32) members (their pointers and RK
  * coefficients passed as kernel parameters); every batch, and every member that is not batched, is
  * a parallel branch of the graph. With batching off (max_batch = 0) every
  * member runs its own kernels and the members are spread over `streams`
  * branches (0 = one branch per member). dns_ensemble_tune first tunes the
- * tile widths of each grid size class on one of its members
- * (dns_tune_tiles, y- and z-pass widths; that member's state is kept) and gives
- * every member of the class the widths found (they apply to per-member launches;
- * batched launches keep the default), then times a set of
+ * radix plan and tile widths of each grid size class on one of its members
+ * (dns_tune_tiles, "fft_plan" and the y- and z-pass widths; that member's state is
+ * kept) and gives every member of the class the plan and widths found (batched
+ * launches use the widths where the batch's members agree), then times a set of
  * schedules (batched, and per-member over 1 .. count branches) on the actual
  * members and keeps the fastest; it ADVANCES every member by 2 steps per
  * schedule tried (the count is returned in the members' time, dns_diag.t) and

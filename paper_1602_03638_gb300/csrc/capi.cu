@@ -226,6 +226,7 @@ struct dns_handle {
   double L[3] = {kTwoPi, kTwoPi, kTwoPi};  // box lengths along x, y, z
   int ytile[2] = {0, 0};  // y-pass tile widths of the stage (inverse, forward); 0 = default
   int ztile = 0;          // z-pass tile width of the stage; 0 = default
+  int plan = 0;  // radix plan variant per pass of the stage's line transforms (option "fft_plan", bits PLAN_*)
   int use_graph = 1;
   int fused = 0;  // plane-pass schedule (option "fused_planes"; measured slower than the four passes)
   int plane_lag = 0;  // option "plane_lag" (0: automatic)
@@ -310,6 +311,7 @@ PassArgs base_args(const dns_handle* h) {
   a.ytile[0] = h->ytile[0];
   a.ytile[1] = h->ytile[1];
   a.ztile = h->ztile;
+  a.plan = h->plan;
   a.ctl = h->ctl;
   a.plane_lag = h->plane_lag;
   a.partials = h->diag;
@@ -576,6 +578,11 @@ int dns_set_option(dns_handle* h, const char* key, double value) {
     for (int i = 0; i < n; ++i) ok = ok || value == (double)tiles[i];
     if (!ok) return fail(DNS_ERR_ARG, "z_tile: %g is not a tile width of this grid", value);
     h->ztile = (int)value;
+  } else if (!strcmp(key, "fft_plan")) {
+    const int masks = h->ops->plans > 1 ? 1 << PLAN_BITS : 1;
+    if (!(value >= 0.0 && value < masks) || value != std::floor(value))
+      return fail(DNS_ERR_ARG, "fft_plan: %g is not a plan mask of this grid (0 .. %d)", value, masks - 1);
+    h->plan = (int)value;
   } else if (!strcmp(key, "use_graph")) {
     if (value != 0.0 && value != 1.0) return fail(DNS_ERR_ARG, "use_graph must be 0 or 1");
     h->use_graph = (int)value;
@@ -617,6 +624,7 @@ int dns_get_option(const dns_handle* h, const char* key, double* value) {
   else if (!strcmp(key, "y_tile_inverse")) *value = h->ytile[0];
   else if (!strcmp(key, "y_tile_forward")) *value = h->ytile[1];
   else if (!strcmp(key, "z_tile")) *value = h->ztile;
+  else if (!strcmp(key, "fft_plan")) *value = h->plan;
   else if (!strcmp(key, "use_graph")) *value = h->use_graph;
   else if (!strcmp(key, "fused_planes")) *value = use_fused(h) ? 1.0 : 0.0;
   else if (!strcmp(key, "plane_lag")) *value = h->plane_lag;
@@ -664,10 +672,13 @@ int dns_tune_tiles(dns_handle* h, int steps, int* y_inverse, int* y_forward, int
   if (rc) return rc;
   if (steps < 1 || !y_inverse || !y_forward || !z) return fail(DNS_ERR_ARG, "dns_tune_tiles: bad arguments");
   if ((rc = use_device(h))) return rc;
-  int ycand[9] = {0}, zcand[9] = {0};
+  // candidates per knob (the default first): y-inverse width, y-forward width, z width,
+  // and the radix plan variant (0, 1) of each pass
+  int ycand[9] = {0}, zcand[9] = {0}, pcand[2] = {0, 1};
   const int ny = 1 + h->ops->y_tiles(ycand + 1, 8);
   const int nz = 1 + h->ops->z_tiles(zcand + 1, 8);
-  if (ny == 1 && nz == 1) {  // this grid offers the default widths only
+  const int np = h->ops->plans;
+  if (ny == 1 && nz == 1 && np == 1) {  // this grid offers the defaults only
     *y_inverse = h->ytile[0];
     *y_forward = h->ytile[1];
     *z = h->ztile;
@@ -677,20 +688,24 @@ int dns_tune_tiles(dns_handle* h, int steps, int* y_inverse, int* y_forward, int
   void* save = nullptr;
   if ((rc = dev_alloc(h, &save, bytes, "tuning copy of the state"))) return rc;
   const double t0 = h->t;
-  const int keep[3] = {h->ytile[0], h->ytile[1], h->ztile};
+  const int keep[4] = {h->ytile[0], h->ytile[1], h->ztile, h->plan};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t err = cudaMemcpyAsync(save, h->U, bytes, cudaMemcpyDeviceToDevice, h->stream);
   if (err == cudaSuccess) err = cudaEventCreate(&e0);
   if (err == cudaSuccess) err = cudaEventCreate(&e1);
   if (err != cudaSuccess) rc = cuda_fail(err, "dns_tune_tiles set-up");
+  auto apply = [&](const int* v) {
+    h->ytile[0] = v[0];
+    h->ytile[1] = v[1];
+    h->ztile = v[2];
+    h->plan = v[3];
+    h->graph_dirty = true;
+  };
   // each candidate starts from the saved state: capture and one warm-up step, then
   // three timings of `steps` steps exactly as dns_step runs them; *ms = their median,
   // *spread = their range
-  auto timed = [&](int ti, int tf, int tz, float* ms, float* spread) -> int {
-    h->ytile[0] = ti;
-    h->ytile[1] = tf;
-    h->ztile = tz;
-    h->graph_dirty = true;
+  auto timed = [&](const int* v, float* ms, float* spread) -> int {
+    apply(v);
     cudaError_t ce = cudaMemcpyAsync(h->U, save, bytes, cudaMemcpyDeviceToDevice, h->stream);
     if (ce != cudaSuccess) return cuda_fail(ce, "dns_tune_tiles copy");
     h->w_valid = false;
@@ -709,28 +724,37 @@ int dns_tune_tiles(dns_handle* h, int steps, int* y_inverse, int* y_forward, int
     *spread = t[2] - t[0];
     return DNS_OK;
   };
-  // one pass at a time, the others kept: the y-inverse width, the y-forward width,
-  // then the z width, each with the best widths found before it. The first candidate is
-  // the default width; another replaces the one kept so far only if its median beats that
-  // one's median by more than that one's spread (differences inside the timing noise keep
-  // the earlier choice).
-  int bi = keep[0], bf = keep[1], bz = keep[2];
+  // one knob at a time, the others kept: the radix plan of the x-, y-inverse, z- and
+  // y-forward passes (with the widths the handle has), the y-inverse width, the y-forward
+  // width, then the z width, each with the best values found before it. The first
+  // candidate is the default; another replaces the one kept so far only if its median
+  // beats that one's median by more than that one's spread (differences inside the
+  // timing noise keep the earlier choice).
+  int best_v[4] = {keep[0], keep[1], keep[2], 0};
+  // which < 3: a tile width; which = 3 + b: the plan bit b
   auto pick = [&](int n, const int* cand, int which) {
     float best = 0.f, best_spread = 0.f, ms = 0.f, spread = 0.f;
+    auto with = [&](int* v, int c) {
+      if (which < 3) v[which] = cand[c];
+      else v[3] = (v[3] & ~(1 << (which - 3))) | (cand[c] << (which - 3));
+    };
     for (int c = 0; c < n && !rc; ++c) {
-      const int ti = which == 0 ? cand[c] : bi, tf = which == 1 ? cand[c] : bf, tz = which == 2 ? cand[c] : bz;
-      if ((rc = timed(ti, tf, tz, &ms, &spread))) return;
+      int v[4] = {best_v[0], best_v[1], best_v[2], best_v[3]};
+      with(v, c);
+      if ((rc = timed(v, &ms, &spread))) return;
       if (c == 0 || ms < best - best_spread) {
         best = ms;
         best_spread = spread;
-        (which == 0 ? bi : which == 1 ? bf : bz) = cand[c];
+        with(best_v, c);
       }
     }
   };
+  if (np > 1)
+    for (int b : {PLAN_X, PLAN_YI, PLAN_Z, PLAN_YF}) pick(np, pcand, 3 + b);
   pick(ny, ycand, 0);
   pick(ny, ycand, 1);
   pick(nz, zcand, 2);
-  // the state and time as before; the fastest widths kept
+  // the state and time as before; the fastest values kept
   err = cudaMemcpyAsync(h->U, save, bytes, cudaMemcpyDeviceToDevice, h->stream);
   if (err == cudaSuccess) err = cudaStreamSynchronize(h->stream);
   if (e0) cudaEventDestroy(e0);
@@ -739,10 +763,7 @@ int dns_tune_tiles(dns_handle* h, int steps, int* y_inverse, int* y_forward, int
   h->bytes -= bytes;
   h->t = t0;
   h->w_valid = false;
-  h->ytile[0] = rc ? keep[0] : bi;
-  h->ytile[1] = rc ? keep[1] : bf;
-  h->ztile = rc ? keep[2] : bz;
-  h->graph_dirty = true;
+  apply(rc ? keep : best_v);
   ++h->epoch;
   if (!rc && err != cudaSuccess) rc = cuda_fail(err, "dns_tune_tiles restore");
   *y_inverse = h->ytile[0];
@@ -1165,7 +1186,8 @@ std::vector<EnsUnit> ens_units(const dns_ensemble* e) {
       std::vector<int> group;
       for (int j = i; j < n; ++j) {
         const dns_handle* g = e->m[j];
-        if (!done[j] && !g->closure && g->ops == h->ops && g->variant == h->variant && same_scheme(g->rk, h->rk)) {
+        if (!done[j] && !g->closure && g->ops == h->ops && g->variant == h->variant && g->plan == h->plan &&
+            same_scheme(g->rk, h->rk)) {
           group.push_back(j);
           done[j] = true;
         }
@@ -1356,7 +1378,7 @@ int dns_ensemble_tune(dns_ensemble* e, int* best_streams) {
   // kept), applied to every member of the class
   int rc = DNS_OK;
   std::vector<const DnsOps*> done_ops;
-  std::vector<std::array<int, 3>> done_tiles;
+  std::vector<std::array<int, 4>> done_tiles;  // y-inverse, y-forward, z widths, radix plan
   for (dns_handle* h : e->m) {
     size_t k = 0;
     while (k < done_ops.size() && done_ops[k] != h->ops) ++k;
@@ -1364,13 +1386,16 @@ int dns_ensemble_tune(dns_ensemble* e, int* best_streams) {
       int ti = 0, tf = 0, tz = 0;
       if ((rc = dns_tune_tiles(h, 5, &ti, &tf, &tz))) return rc;
       done_ops.push_back(h->ops);
-      done_tiles.push_back({ti, tf, tz});
-    } else if (h->ytile[0] != done_tiles[k][0] || h->ytile[1] != done_tiles[k][1] || h->ztile != done_tiles[k][2]) {
+      done_tiles.push_back({ti, tf, tz, h->plan});
+    } else if (h->ytile[0] != done_tiles[k][0] || h->ytile[1] != done_tiles[k][1] || h->ztile != done_tiles[k][2] ||
+               h->plan != done_tiles[k][3]) {
       h->ytile[0] = done_tiles[k][0];
       h->ytile[1] = done_tiles[k][1];
       h->ztile = done_tiles[k][2];
+      h->plan = done_tiles[k][3];
       h->graph_dirty = true;
       ++h->epoch;
+      h->w_valid = false;
     }
   }
   rc = ens_prepare_members(e);

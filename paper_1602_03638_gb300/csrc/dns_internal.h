@@ -44,6 +44,7 @@ struct PassArgs {
   float f_ks[3] = {1.f, 1.f, 1.f};
   int ytile[2] = {0, 0};  // y-pass tile widths of the stage launches (inverse, forward); 0 = default
   int ztile = 0;          // z-pass tile width of the stage launches; 0 = default
+  int plan = 0;           // radix plan variant per pass of the stage launches: bit PLAN_* set = AltPlan
   const void* in = nullptr;  // physical input (3,Nx,Ny,Nz) for set_state
   void* out = nullptr;       // physical output (3,Nx,Ny,Nz) / RHS output
   int* ctl = nullptr;  // plane-pass control block (error flag, queue head, per-plane counters)
@@ -97,7 +98,11 @@ struct DnsOps {
   int plane_ctl_words;  // ints of the plane-pass control block (0: no plane pass)
   int NY, NZ;  // points along y and z (N is the count along x)
   int TW;      // length of the twiddle table exp(-2 pi i t / TW) (a multiple of N, NY, NZ)
+  int plans;   // radix plan variants the stage launches offer (1: the default only, 2: AltPlan too)
 };
+
+// bits of PassArgs::plan: the radix plan variant of each pass of a stage
+constexpr int PLAN_X = 0, PLAN_YI = 1, PLAN_Z = 2, PLAN_YF = 3, PLAN_BITS = 4;
 
 constexpr int BATCH_MAX_N = 128;
 constexpr int BATCH_MAX_COUNT = 32;

@@ -296,6 +296,38 @@ struct SmemPlan<512, 8> : FixedPlan3<512, 16, 16, 2> {};
 template <>
 struct SmemPlan<1024, 8> : FixedPlan3<1024, 16, 16, 4> {};
 
+// Alternative radix schedule (plan variant 1, offered to the tile tuner of the small
+// grids): radix 3 first where L has the factor 3, then radix-4 passes, and one radix-8
+// pass last when the power-of-two exponent is odd (radix 2 when it is 1). More passes
+// of smaller radix than WarpPlan: more butterflies per pass (lanes busy), fewer
+// registers, one more exchange through shared memory.
+template <int L>
+struct AltPlan {
+  static constexpr int three = (L % 3 == 0) ? 1 : 0;
+  static constexpr int p2 = three ? L / 3 : L;
+  static constexpr int a = ilog2c(p2);
+  static_assert((1 << a) == p2 && (p2 % 3) != 0 && a >= 1, "FFT length must be 2^a or 3*2^a");
+  static constexpr int odd_r = (a % 2) ? (a == 1 ? 2 : 8) : 0;  // the last power-of-two radix
+  static constexpr int n4 = (a % 2) ? (a == 1 ? 0 : (a - 3) / 2) : a / 2;
+  static constexpr int npass = three + n4 + (odd_r ? 1 : 0);
+  static constexpr int radix(int p) { return (three && p == 0) ? 3 : (p - three < n4 ? 4 : odd_r); }
+  static constexpr int ns(int p) {
+    int r = 1;
+    for (int q = 0; q < p; ++q) r *= radix(q);
+    return r;
+  }
+};
+
+// The plan of variant V: 0 = the default schedule, 1 = AltPlan.
+template <int L, int CB, int V>
+struct SmemPlanV : SmemPlan<L, CB> {};
+template <int L, int CB>
+struct SmemPlanV<L, CB, 1> : AltPlan<L> {};
+template <int L, int V>
+struct LinePlanV : WarpPlan<L> {};
+template <int L>
+struct LinePlanV<L, 1> : AltPlan<L> {};
+
 template <int L>
 struct IsPow2 {
   static constexpr bool value = L > 0 && (L & (L - 1)) == 0;
@@ -344,10 +376,10 @@ struct GStore {
   __device__ __forceinline__ void store(cx<T>* q, int, cx<T> v) const { *q = CONJ ? conjg(v) : v; }
 };
 
-template <typename T, int L, int TWN, int P, class Src, class Work, class Dst>
+template <typename T, int L, int TWN, int P, int V, class Src, class Work, class Dst>
 __device__ __forceinline__ void warp_fft_pass(const Src& src, const Work& work, const Dst& dst,
                                               const cx<T>* __restrict__ tw, int lane) {
-  using PL = SmemPlan<L, (int)sizeof(cx<T>)>;
+  using PL = SmemPlanV<L, (int)sizeof(cx<T>), V>;
   constexpr int R = PL::radix(P);
   constexpr int NS = PL::ns(P);
   constexpr int NB = L / R;
@@ -423,16 +455,17 @@ __device__ __forceinline__ void warp_fft_pass(const Src& src, const Work& work, 
     }
   }
   __syncwarp();
-  if constexpr (!LAST) warp_fft_pass<T, L, TWN, P + 1>(src, work, dst, tw, lane);
+  if constexpr (!LAST) warp_fft_pass<T, L, TWN, P + 1, V>(src, work, dst, tw, lane);
 }
 
 // Forward DFT of one line of length L by one warp: reads through `src`, uses
 // the shared-memory line `work` between passes, writes through `dst` (which may
 // alias `work` or `src`: every pass reads all its values before writing).
-template <typename T, int L, int TWN, class Src, class Work, class Dst>
+// V: the radix plan variant (SmemPlanV).
+template <typename T, int L, int TWN, int V = 0, class Src, class Work, class Dst>
 __device__ __forceinline__ void warp_fft(const Src& src, const Work& work, const Dst& dst,
                                          const cx<T>* __restrict__ tw, int lane) {
-  warp_fft_pass<T, L, TWN, 0>(src, work, dst, tw, lane);
+  warp_fft_pass<T, L, TWN, 0, V>(src, work, dst, tw, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -442,15 +475,15 @@ __device__ __forceinline__ void warp_fft(const Src& src, const Work& work, const
 // g * NB + j), so short lines whose passes have fewer butterflies than lanes
 // still keep the warp busy. Same radix plan and twiddles as warp_fft.
 // ---------------------------------------------------------------------------
-template <int L>
+template <int L, int V = 0>
 struct LinesPerWarp {  // largest power of two G with G * (butterflies of pass 0) <= 32, at most 16
-  static constexpr int nb0 = L / WarpPlan<L>::radix(0);
+  static constexpr int nb0 = L / LinePlanV<L, V>::radix(0);
   static constexpr int value = nb0 >= 32 ? 1 : (nb0 >= 16 ? 2 : (nb0 >= 8 ? 4 : (nb0 >= 4 ? 8 : 16)));
 };
 
-template <typename T, int L, int TWN, int G, int LD, int P>
+template <typename T, int L, int TWN, int G, int LD, int P, int V>
 __device__ __forceinline__ void warp_fft_lines_pass(cx<T>* s0, const cx<T>* __restrict__ tw, int lane) {
-  using PL = WarpPlan<L>;
+  using PL = LinePlanV<L, V>;
   constexpr int R = PL::radix(P);
   constexpr int NS = PL::ns(P);
   constexpr int NB = L / R;
@@ -495,13 +528,13 @@ __device__ __forceinline__ void warp_fft_lines_pass(cx<T>* s0, const cx<T>* __re
     }
   }
   __syncwarp();
-  if constexpr (!LAST) warp_fft_lines_pass<T, L, TWN, G, LD, P + 1>(s0, tw, lane);
+  if constexpr (!LAST) warp_fft_lines_pass<T, L, TWN, G, LD, P + 1, V>(s0, tw, lane);
 }
 
-// Forward DFT, in place, of the G lines s0 + g (see above) by one warp.
-template <typename T, int L, int TWN, int G, int LD>
+// Forward DFT, in place, of the G lines s0 + g (see above) by one warp (V: plan variant).
+template <typename T, int L, int TWN, int G, int LD, int V = 0>
 __device__ __forceinline__ void warp_fft_lines(cx<T>* s0, const cx<T>* __restrict__ tw, int lane) {
-  warp_fft_lines_pass<T, L, TWN, G, LD, 0>(s0, tw, lane);
+  warp_fft_lines_pass<T, L, TWN, G, LD, 0, V>(s0, tw, lane);
 }
 
 // ---------------------------------------------------------------------------

@@ -175,7 +175,8 @@ struct GStoreNyquistFree {
 // NT: threads of the calling block (XP_THREADS for k_xpass; the plane pass runs the
 // stage update with 256, its warps 6 and 7 idle during the line transforms).
 // NY, NZ: points along y and z where they differ from N (rows kz * NY + ky).
-template <typename T, int N, int MODE, int NT = XP_THREADS, int NY = N, int NZ = N>
+// V: radix plan variant of the line transforms (SmemPlanV).
+template <typename T, int N, int MODE, int NT = XP_THREADS, int NY = N, int NZ = N, int V = 0>
 __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
   static_assert(NT >= XP_THREADS && NT % 32 == 0, "the x-pass needs at least one warp per line");
   // in the plane pass the RK state is a stream past the plane data kept in L2 (FP32
@@ -243,13 +244,13 @@ __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
       __syncthreads();
       if (row_kept && warp < 3) {
         const SLine<T, 1> line{s + warp * LS};
-        warp_fft<T, N, TW>(line, line, line, tw, lane);
+        warp_fft<T, N, TW, V>(line, line, line, tw, lane);
       }
       cp_async_wait<0>();
     } else {
       if (row_kept && warp < 3) {
         const SLine<T, 1> line{s + warp * LS};
-        warp_fft<T, N, TW>(GLoad<T, false>{W + warp * FS + rb}, line, line, tw, lane);
+        warp_fft<T, N, TW, V>(GLoad<T, false>{W + warp * FS + rb}, line, line, tw, lane);
       }
     }
     __syncthreads();
@@ -376,21 +377,21 @@ __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
       if constexpr (G::XPRE && !G::XWIDE) {
         if (warp < 3) {
           const SLine<T, 1> line{s + warp * LS};
-          warp_fft<T, N, TW>(line, line, GStore<T, true>{W + warp * FS + rb}, tw, lane);
+          warp_fft<T, N, TW, V>(line, line, GStore<T, true>{W + warp * FS + rb}, tw, lane);
         } else {  // omega: from its unpadded row, through a padded work line over rows 3-8
           const int c = warp - 3;
           const SLine<T, 1> work{st + 3 * N + c * LS};
-          warp_fft<T, N, TW>(SRow<T>{st + c * N}, work, GStore<T, true>{W + warp * FS + rb}, tw, lane);
+          warp_fft<T, N, TW, V>(SRow<T>{st + c * N}, work, GStore<T, true>{W + warp * FS + rb}, tw, lane);
         }
       } else {
         const SLine<T, 1> line{s + warp * LS};
-        warp_fft<T, N, TW>(line, line, GStore<T, true>{W + warp * FS + rb}, tw, lane);
+        warp_fft<T, N, TW, V>(line, line, GStore<T, true>{W + warp * FS + rb}, tw, lane);
       }
     }
   } else if constexpr (MODE == XM_FWD_STORE) {
     if (warp < 3) {
       const SLine<T, 1> line{s + warp * LS};
-      warp_fft<T, N, TW>(GLoad<T, false>{U + warp * FS + rb}, line,
+      warp_fft<T, N, TW, V>(GLoad<T, false>{U + warp * FS + rb}, line,
                         GStoreNyquistFree<T>{U + warp * FS + rb, N, ky == NY / 2}, tw, lane);
     }
   } else {
@@ -417,20 +418,20 @@ __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
     cx<T>* dst = (MODE == XM_INV_DIV) ? reinterpret_cast<cx<T>*>(a.D) : W;
     if (warp < NF) {
       const SLine<T, 1> line{s + warp * LS};
-      warp_fft<T, N, TW>(line, line, GStore<T, true>{dst + warp * FS + rb}, tw, lane);
+      warp_fft<T, N, TW, V>(line, line, GStore<T, true>{dst + warp * FS + rb}, tw, lane);
     }
   }
 }
 
-template <typename T, int N, int MODE, int NY = N, int NZ = N>
+template <typename T, int N, int MODE, int NY = N, int NZ = N, int V = 0>
 __global__ void __launch_bounds__(XP_THREADS, (Geometry<T, N, NY, NZ>::XMIN)) k_xpass(PassArgs a) {
-  xpass_body<T, N, MODE, XP_THREADS, NY, NZ>(a, blockIdx.x);
+  xpass_body<T, N, MODE, XP_THREADS, NY, NZ, V>(a, blockIdx.x);
 }
 
 // Batched form (ensembles): member blockIdx.y, its arguments in B.a[blockIdx.y].
-template <typename T, int N, int MODE>
+template <typename T, int N, int MODE, int V = 0>
 __global__ void __launch_bounds__(XP_THREADS, (Geometry<T, N>::XMIN)) k_xpass_b(const __grid_constant__ BatchArgs B) {
-  xpass_body<T, N, MODE>(B.a[blockIdx.y], blockIdx.x);
+  xpass_body<T, N, MODE, XP_THREADS, N, N, V>(B.a[blockIdx.y], blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -457,7 +458,7 @@ __device__ __forceinline__ int ywalk_row(int r) {
 
 // One y tile: TX adjacent columns starting at `base` (field, kz plane and first
 // column already applied), transformed along y in place. NT: threads of the block.
-template <typename T, int N, int INV, int PRUNE, int TXO, int NT>
+template <typename T, int N, int INV, int PRUNE, int TXO, int NT, int V = 0>
 __device__ __forceinline__ void ypass_tile(cx<T>* __restrict__ base, const cx<T>* __restrict__ tw, int kmax3) {
   using Y = YCfg<T, N, INV, TXO>;
   constexpr int TX = Y::TX;
@@ -478,8 +479,8 @@ __device__ __forceinline__ void ypass_tile(cx<T>* __restrict__ base, const cx<T>
 #pragma unroll 1
   for (int c = warp; c < TX; c += NT / 32) {  // warps loop over the columns
     const SLine<T, LD> line{s + c};
-    if constexpr (INV) warp_fft<T, N, N>(SLineConj<T, LD>{s + c}, line, line, tw, lane);
-    else warp_fft<T, N, N>(line, line, line, tw, lane);
+    if constexpr (INV) warp_fft<T, N, N, V>(SLineConj<T, LD>{s + c}, line, line, tw, lane);
+    else warp_fft<T, N, N, V>(line, line, line, tw, lane);
   }
   __syncthreads();
 #pragma unroll 8
@@ -493,7 +494,7 @@ __device__ __forceinline__ void ypass_tile(cx<T>* __restrict__ base, const cx<T>
 
 // NY, NZ: points along y and z where they differ from N (N: the x extent, the
 // row stride of the tile's columns).
-template <typename T, int N, int INV, int PRUNE, int TXO = 0, int NY = N, int NZ = N>
+template <typename T, int N, int INV, int PRUNE, int TXO = 0, int NY = N, int NZ = N, int V = 0>
 __global__ void __launch_bounds__(YCfg<T, N, INV, TXO, NY>::THREADS, (YCfg<T, N, INV, TXO, NY>::MINB))
     k_ypass(cx<T>* __restrict__ F, const cx<T>* __restrict__ tw, int kmax3) {
   using G = Geometry<T, N, NY, NZ>;
@@ -518,8 +519,8 @@ __global__ void __launch_bounds__(YCfg<T, N, INV, TXO, NY>::THREADS, (YCfg<T, N,
 #pragma unroll 1
   for (int c = warp; c < TX; c += NT / 32) {
     const SLine<T, LD> line{s + c};
-    if constexpr (INV) warp_fft<T, NY, G::TW>(SLineConj<T, LD>{s + c}, line, line, tw, lane);
-    else warp_fft<T, NY, G::TW>(line, line, line, tw, lane);
+    if constexpr (INV) warp_fft<T, NY, G::TW, V>(SLineConj<T, LD>{s + c}, line, line, tw, lane);
+    else warp_fft<T, NY, G::TW, V>(line, line, line, tw, lane);
   }
   __syncthreads();
 #pragma unroll 8
@@ -533,7 +534,7 @@ __global__ void __launch_bounds__(YCfg<T, N, INV, TXO, NY>::THREADS, (YCfg<T, N,
 
 // Batched form on the members' work arrays (ensembles): blockIdx.z = member *
 // fields + field; otherwise the same steps as k_ypass (TXO: a tuned tile width).
-template <typename T, int N, int INV, int PRUNE, int TXO = 0>
+template <typename T, int N, int INV, int PRUNE, int TXO = 0, int V = 0>
 __global__ void __launch_bounds__(YCfg<T, N, INV, TXO>::THREADS, (YCfg<T, N, INV, TXO>::MINB))
     k_ypass_b(const __grid_constant__ BatchArgs B, int fields) {
   using G = Geometry<T, N>;
@@ -541,7 +542,7 @@ __global__ void __launch_bounds__(YCfg<T, N, INV, TXO>::THREADS, (YCfg<T, N, INV
   const PassArgs& a = B.a[blockIdx.z / fields];
   cx<T>* base = reinterpret_cast<cx<T>*>(a.W) + (blockIdx.z % fields) * G::FS + (size_t)blockIdx.y * N * N +
                 blockIdx.x * Y::TX;
-  ypass_tile<T, N, INV, PRUNE, TXO, Y::THREADS>(base, reinterpret_cast<const cx<T>*>(a.tw), a.kmax3);
+  ypass_tile<T, N, INV, PRUNE, TXO, Y::THREADS, V>(base, reinterpret_cast<const cx<T>*>(a.tw), a.kmax3);
 }
 
 // ---------------------------------------------------------------------------
@@ -553,7 +554,7 @@ __global__ void __launch_bounds__(YCfg<T, N, INV, TXO>::THREADS, (YCfg<T, N, INV
 // ---------------------------------------------------------------------------
 // NY, NZ: points along y and z where they differ from N (lines of NZ points at the
 // NX x NY positions; physical arrays (3, N, NY, NZ)).
-template <typename T, int N, int MODE, int TXO = 0, int NY = N, int NZ = N>
+template <typename T, int N, int MODE, int TXO = 0, int NY = N, int NZ = N, int V = 0>
 __device__ __forceinline__ void zpass_body(const PassArgs a, const int bx, const int by) {
   using G = Geometry<T, N, NY, NZ>;
   constexpr int M = G::M;
@@ -607,9 +608,9 @@ __device__ __forceinline__ void zpass_body(const PassArgs a, const int bx, const
       }
     }
     __syncthreads();
-    constexpr int GL = LinesPerWarp<M>::value <= TX ? LinesPerWarp<M>::value : TX;  // lines per warp
+    constexpr int GL = LinesPerWarp<M, V>::value <= TX ? LinesPerWarp<M, V>::value : TX;  // lines per warp
 #pragma unroll 1
-    for (int l = warp * GL; l < NL; l += (ZP_THREADS / 32) * GL) warp_fft_lines<T, M, TW, GL, LD>(s + l, tw, lane);
+    for (int l = warp * GL; l < NL; l += (ZP_THREADS / 32) * GL) warp_fft_lines<T, M, TW, GL, LD, V>(s + l, tw, lane);
     __syncthreads();
     // now conj(s) = x_{2n} + i x_{2n+1} (physical values, unnormalised c2r)
   }
@@ -629,9 +630,9 @@ __device__ __forceinline__ void zpass_body(const PassArgs a, const int bx, const
   }
 
   if constexpr (MODE == ZM_CROSS || MODE == ZM_LOAD) {
-    constexpr int GL = LinesPerWarp<M>::value <= TX ? LinesPerWarp<M>::value : TX;
+    constexpr int GL = LinesPerWarp<M, V>::value <= TX ? LinesPerWarp<M, V>::value : TX;
 #pragma unroll 1
-    for (int l = warp * GL; l < 3 * TX; l += (ZP_THREADS / 32) * GL) warp_fft_lines<T, M, TW, GL, LD>(s + l, tw, lane);
+    for (int l = warp * GL; l < 3 * TX; l += (ZP_THREADS / 32) * GL) warp_fft_lines<T, M, TW, GL, LD, V>(s + l, tw, lane);
     __syncthreads();
     // r2c post-processing: X_k = 1/2 [(Z_k + conj Z_{M-k}) - i e^{-2 pi i k/N} (Z_k - conj Z_{M-k})]
     cx<T>* dst = reinterpret_cast<cx<T>*>(MODE == ZM_CROSS ? a.W : a.U);
@@ -673,15 +674,15 @@ __device__ __forceinline__ void zpass_body(const PassArgs a, const int bx, const
   }
 }
 
-template <typename T, int N, int MODE, int TXO = 0, int NY = N, int NZ = N>
+template <typename T, int N, int MODE, int TXO = 0, int NY = N, int NZ = N, int V = 0>
 __global__ void __launch_bounds__(ZP_THREADS, (Geometry<T, N, NY, NZ>::ZMIN)) k_zpass(PassArgs a) {
-  zpass_body<T, N, MODE, TXO, NY, NZ>(a, blockIdx.x, blockIdx.y);
+  zpass_body<T, N, MODE, TXO, NY, NZ, V>(a, blockIdx.x, blockIdx.y);
 }
 
 // Batched form (ensembles): member blockIdx.z (TXO: a tuned tile width).
-template <typename T, int N, int MODE, int TXO = 0>
+template <typename T, int N, int MODE, int TXO = 0, int V = 0>
 __global__ void __launch_bounds__(ZP_THREADS, (Geometry<T, N>::ZMIN)) k_zpass_b(const __grid_constant__ BatchArgs B) {
-  zpass_body<T, N, MODE, TXO>(B.a[blockIdx.z], blockIdx.x, blockIdx.y);
+  zpass_body<T, N, MODE, TXO, N, N, V>(B.a[blockIdx.z], blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -1962,15 +1963,35 @@ struct SolverImpl {
   static constexpr bool ytile_ok(int t) {
     return ISO && N <= BATCH_MAX_N && t >= 4 && t <= 32 && pow2_part(N) % t == 0 && t * (int)sizeof(cx<T>) <= 256;
   }
+  // radix plan variants of the stage's line transforms offered to the tuner (SmemPlanV /
+  // LinePlanV: 0 the default schedule, 1 AltPlan); the ensemble grids only. PassArgs::plan
+  // holds one bit per pass: PLAN_X (x-stage and x inverse), PLAN_YI (y-inverse),
+  // PLAN_Z (z-pass), PLAN_YF (y-forward).
+  static constexpr int PLANS = (ISO && N <= BATCH_MAX_N) ? 2 : 1;
+  static int bit(int plan, int b) { return (plan >> b) & 1; }
+  // f(std::integral_constant<int, V>) with the variant V = plan (0 where not offered)
+  template <class F>
+  static void with_plan(int plan, F&& f) {
+    if constexpr (PLANS > 1) {
+      if (plan == 1) return f(std::integral_constant<int, 1>{});
+    }
+    f(std::integral_constant<int, 0>{});
+  }
+
+  template <int TXO, int V>
+  static void tile_attr_v(cudaError_t& e) {
+    if (e == cudaSuccess) e = smem_attr(k_ypass<T, N, 1, 0, TXO, N, N, V>, YCfg<T, N, 1, TXO>::SMEM);
+    if (e == cudaSuccess) e = smem_attr(k_ypass<T, N, 0, 1, TXO, N, N, V>, YCfg<T, N, 0, TXO>::SMEM);
+    if constexpr (!ZCross<T, N>::enabled) {
+      if (e == cudaSuccess) e = smem_attr(k_ypass_b<T, N, 1, 0, TXO, V>, YCfg<T, N, 1, TXO>::SMEM);
+      if (e == cudaSuccess) e = smem_attr(k_ypass_b<T, N, 0, 1, TXO, V>, YCfg<T, N, 0, TXO>::SMEM);
+    }
+  }
   template <int TXO>
   static void tile_attr(cudaError_t& e) {
     if constexpr (ytile_ok(TXO)) {
-      if (e == cudaSuccess) e = smem_attr(k_ypass<T, N, 1, 0, TXO>, YCfg<T, N, 1, TXO>::SMEM);
-      if (e == cudaSuccess) e = smem_attr(k_ypass<T, N, 0, 1, TXO>, YCfg<T, N, 0, TXO>::SMEM);
-      if constexpr (!ZCross<T, N>::enabled) {
-        if (e == cudaSuccess) e = smem_attr(k_ypass_b<T, N, 1, 0, TXO>, YCfg<T, N, 1, TXO>::SMEM);
-        if (e == cudaSuccess) e = smem_attr(k_ypass_b<T, N, 0, 1, TXO>, YCfg<T, N, 0, TXO>::SMEM);
-      }
+      tile_attr_v<TXO, 0>(e);
+      if constexpr (PLANS > 1) tile_attr_v<TXO, 1>(e);
     }
   }
   static int y_tiles(int* tiles, int max) {
@@ -1989,6 +2010,10 @@ struct SolverImpl {
     if constexpr (ztile_ok(TXO)) {
       if (e == cudaSuccess) e = smem_attr(k_zpass<T, N, ZM_CROSS, TXO>, G::zbytes(TXO));
       if (e == cudaSuccess) e = smem_attr(k_zpass_b<T, N, ZM_CROSS, TXO>, G::zbytes(TXO));
+      if constexpr (PLANS > 1) {
+        if (e == cudaSuccess) e = smem_attr(k_zpass<T, N, ZM_CROSS, TXO, N, N, 1>, G::zbytes(TXO));
+        if (e == cudaSuccess) e = smem_attr(k_zpass_b<T, N, ZM_CROSS, TXO, 1>, G::zbytes(TXO));
+      }
     }
   }
   static int z_tiles(int* tiles, int max) {
@@ -1997,26 +2022,31 @@ struct SolverImpl {
       if (ztile_ok(t) && n < max) tiles[n++] = t;
     return n;
   }
-  template <int TXO>
+  template <int TXO, int V = 0>
   static void z_go(const PassArgs& a, cudaStream_t st) {
     constexpr int TX = TXO > 0 ? TXO : G::ZTX;
-    k_zpass<T, N, ZM_CROSS, TXO, NY, NZ><<<dim3(N / TX, NY), ZP_THREADS, G::zbytes(TX), st>>>(a);
+    k_zpass<T, N, ZM_CROSS, TXO, NY, NZ, V><<<dim3(N / TX, NY), ZP_THREADS, G::zbytes(TX), st>>>(a);
   }
-  template <int INV, int PRUNE, int TXO>
+  template <int INV, int PRUNE, int TXO, int V = 0>
   static void y_go(cx<T>* F, const cx<T>* tw, int kmax3, int planes, int fields, cudaStream_t st) {
     using Y = YCfg<T, N, INV, TXO, NY>;
-    k_ypass<T, N, INV, PRUNE, TXO, NY, NZ><<<dim3(N / Y::TX, planes, fields), Y::THREADS, Y::SMEM, st>>>(F, tw, kmax3);
+    k_ypass<T, N, INV, PRUNE, TXO, NY, NZ, V><<<dim3(N / Y::TX, planes, fields), Y::THREADS, Y::SMEM, st>>>(F, tw, kmax3);
   }
-  // the stage's y-pass with tile width `tile` (0, or a width not offered: the default)
+  // the stage's y-pass with tile width `tile` (0, or a width not offered: the default) and
+  // radix plan variant `plan`
   template <int INV, int PRUNE>
-  static void y_stage(int tile, cx<T>* F, const cx<T>* tw, int kmax3, int planes, int fields, cudaStream_t st) {
-    if constexpr (ISO && N <= BATCH_MAX_N) {
-      if constexpr (ytile_ok(4)) if (tile == 4) return y_go<INV, PRUNE, 4>(F, tw, kmax3, planes, fields, st);
-      if constexpr (ytile_ok(8)) if (tile == 8) return y_go<INV, PRUNE, 8>(F, tw, kmax3, planes, fields, st);
-      if constexpr (ytile_ok(16)) if (tile == 16) return y_go<INV, PRUNE, 16>(F, tw, kmax3, planes, fields, st);
-      if constexpr (ytile_ok(32)) if (tile == 32) return y_go<INV, PRUNE, 32>(F, tw, kmax3, planes, fields, st);
-    }
-    y_go<INV, PRUNE, 0>(F, tw, kmax3, planes, fields, st);
+  static void y_stage(int tile, int plan, cx<T>* F, const cx<T>* tw, int kmax3, int planes, int fields,
+                      cudaStream_t st) {
+    with_plan(plan, [&](auto v) {
+      constexpr int V = decltype(v)::value;
+      if constexpr (ISO && N <= BATCH_MAX_N) {
+        if constexpr (ytile_ok(4)) if (tile == 4) return y_go<INV, PRUNE, 4, V>(F, tw, kmax3, planes, fields, st);
+        if constexpr (ytile_ok(8)) if (tile == 8) return y_go<INV, PRUNE, 8, V>(F, tw, kmax3, planes, fields, st);
+        if constexpr (ytile_ok(16)) if (tile == 16) return y_go<INV, PRUNE, 16, V>(F, tw, kmax3, planes, fields, st);
+        if constexpr (ytile_ok(32)) if (tile == 32) return y_go<INV, PRUNE, 32, V>(F, tw, kmax3, planes, fields, st);
+      }
+      y_go<INV, PRUNE, 0, V>(F, tw, kmax3, planes, fields, st);
+    });
   }
 
   static cudaError_t prepare() {
@@ -2042,6 +2072,15 @@ struct SolverImpl {
     DNS_ATTR((k_ypass<T, N, 0, 1, 0, NY, NZ>), (YCfg<T, N, 0, 0, NY>::SMEM));
     DNS_ATTR((k_ypass<T, N, 0, 0, 0, NY, NZ>), (YCfg<T, N, 0, 0, NY>::SMEM));
     DNS_ATTR((k_zpass<T, N, ZM_CROSS, 0, NY, NZ>), G::ZSMEM);
+    if constexpr (PLANS > 1) {
+      DNS_ATTR((k_xpass<T, N, XM_INV_CURL, N, N, 1>), G::XSMEM);
+      DNS_ATTR((k_xpass<T, N, XM_STAGE, N, N, 1>), G::XSMEM_ST);
+      DNS_ATTR((k_xpass<T, N, XM_STAGE2N, N, N, 1>), G::XSMEM_ST);
+      DNS_ATTR((k_xpass<T, N, XM_RHS, N, N, 1>), G::XSMEM_ST);
+      DNS_ATTR((k_ypass<T, N, 1, 0, 0, N, N, 1>), (YCfg<T, N, 1, 0>::SMEM));
+      DNS_ATTR((k_ypass<T, N, 0, 1, 0, N, N, 1>), (YCfg<T, N, 0, 0>::SMEM));
+      DNS_ATTR((k_zpass<T, N, ZM_CROSS, 0, N, N, 1>), G::ZSMEM);
+    }
     if constexpr (ISO && ZCross<T, N>::enabled) DNS_ATTR((k_zcross<T, N>), G::ZSMEM);
     if constexpr (ISO && N == 512) DNS_ATTR((k_zcross16<T, N>), G::ZSMEM);
     if constexpr (ISO && N == 512 && sizeof(T) == 4) DNS_ATTR((k_zcross16p<T, N>), Z16P<T>::SMEM);
@@ -2058,6 +2097,13 @@ struct SolverImpl {
       DNS_ATTR((k_ypass_b<T, N, 0, 1>), (YCfg<T, N, 0>::SMEM));
       DNS_ATTR((k_xpass_b<T, N, XM_STAGE>), G::XSMEM_ST);
       DNS_ATTR((k_xpass_b<T, N, XM_STAGE2N>), G::XSMEM_ST);
+      if constexpr (PLANS > 1) {
+        DNS_ATTR((k_ypass_b<T, N, 1, 0, 0, 1>), (YCfg<T, N, 1>::SMEM));
+        DNS_ATTR((k_zpass_b<T, N, ZM_CROSS, 0, 1>), G::ZSMEM);
+        DNS_ATTR((k_ypass_b<T, N, 0, 1, 0, 1>), (YCfg<T, N, 0>::SMEM));
+        DNS_ATTR((k_xpass_b<T, N, XM_STAGE, 1>), G::XSMEM_ST);
+        DNS_ATTR((k_xpass_b<T, N, XM_STAGE2N, 1>), G::XSMEM_ST);
+      }
     }
 #undef DNS_ATTR
     return e;
@@ -2079,11 +2125,14 @@ struct SolverImpl {
     else if constexpr (ZCross<T, N>::enabled)
       k_zcross<T, N><<<dim3(N / G::ZTX, N), 32 * ZCrossWarps<T, N>::value, G::ZSMEM, st>>>(a);
     else {
-      if constexpr (ztile_ok(4)) if (a.ztile == 4) return z_go<4>(a, st);
-      if constexpr (ztile_ok(8)) if (a.ztile == 8) return z_go<8>(a, st);
-      if constexpr (ztile_ok(16)) if (a.ztile == 16) return z_go<16>(a, st);
-      if constexpr (ztile_ok(32)) if (a.ztile == 32) return z_go<32>(a, st);
-      z_go<0>(a, st);
+      with_plan(bit(a.plan, PLAN_Z), [&](auto v) {
+        constexpr int V = decltype(v)::value;
+        if constexpr (ztile_ok(4)) if (a.ztile == 4) return z_go<4, V>(a, st);
+        if constexpr (ztile_ok(8)) if (a.ztile == 8) return z_go<8, V>(a, st);
+        if constexpr (ztile_ok(16)) if (a.ztile == 16) return z_go<16, V>(a, st);
+        if constexpr (ztile_ok(32)) if (a.ztile == 32) return z_go<32, V>(a, st);
+        z_go<0, V>(a, st);
+      });
     }
   }
 
@@ -2107,24 +2156,29 @@ struct SolverImpl {
   static cudaError_t x_inverse_curl(const PassArgs& a0, int from_stage, cudaStream_t st) {
     PassArgs a = a0;
     if (from_stage) a.U = a.US;
-    k_xpass<T, N, XM_INV_CURL, NY, NZ><<<ROWS, XP_THREADS, G::XSMEM, st>>>(f32args(a));
+    with_plan(bit(a.plan, PLAN_X), [&](auto v) {
+      k_xpass<T, N, XM_INV_CURL, NY, NZ, decltype(v)::value><<<ROWS, XP_THREADS, G::XSMEM, st>>>(f32args(a));
+    });
     return cudaGetLastError();
   }
 
   static void rhs_front(const PassArgs& a, cudaStream_t st) {
     cx<T>* W = reinterpret_cast<cx<T>*>(a.W);
     const cx<T>* tw = reinterpret_cast<const cx<T>*>(a.tw);
-    y_stage<1, 0>(a.ytile[0], W, tw, k3y(a), M, 6, st);
+    y_stage<1, 0>(a.ytile[0], bit(a.plan, PLAN_YI), W, tw, k3y(a), M, 6, st);
     z_cross(a, st);
-    y_stage<0, 1>(a.ytile[1], W, tw, k3y(a), kc_of(k3z(a)), 3, st);
+    y_stage<0, 1>(a.ytile[1], bit(a.plan, PLAN_YF), W, tw, k3y(a), kc_of(k3z(a)), 3, st);
   }
 
   // the x-stage launch of a stage, in the form of the stage's scheme
   static void x_stage(const PassArgs& a, cudaStream_t st) {
-    if (a.lsrk)
-      k_xpass<T, N, XM_STAGE2N, NY, NZ><<<ROWS, XP_THREADS, xsmem_stage(a.stage, a.last), st>>>(f32args(a));
-    else
-      k_xpass<T, N, XM_STAGE, NY, NZ><<<ROWS, XP_THREADS, xsmem_stage(a.stage, a.last), st>>>(f32args(a));
+    with_plan(bit(a.plan, PLAN_X), [&](auto v) {
+      constexpr int V = decltype(v)::value;
+      if (a.lsrk)
+        k_xpass<T, N, XM_STAGE2N, NY, NZ, V><<<ROWS, XP_THREADS, xsmem_stage(a.stage, a.last), st>>>(f32args(a));
+      else
+        k_xpass<T, N, XM_STAGE, NY, NZ, V><<<ROWS, XP_THREADS, xsmem_stage(a.stage, a.last), st>>>(f32args(a));
+    });
   }
 
   static cudaError_t rk_stage(const PassArgs& a, cudaStream_t st) {
@@ -2137,46 +2191,50 @@ struct SolverImpl {
     cx<T>* W = reinterpret_cast<cx<T>*>(a.W);
     const cx<T>* tw = reinterpret_cast<const cx<T>*>(a.tw);
     switch (part) {
-      case 0: y_stage<1, 0>(a.ytile[0], W, tw, k3y(a), M, 6, st); break;
+      case 0: y_stage<1, 0>(a.ytile[0], bit(a.plan, PLAN_YI), W, tw, k3y(a), M, 6, st); break;
       case 1: z_cross(a, st); break;
-      case 2: y_stage<0, 1>(a.ytile[1], W, tw, k3y(a), kc_of(k3z(a)), 3, st); break;
+      case 2: y_stage<0, 1>(a.ytile[1], bit(a.plan, PLAN_YF), W, tw, k3y(a), kc_of(k3z(a)), 3, st); break;
       default: x_stage(a, st); break;
     }
     return cudaGetLastError();
   }
 
-  // batched passes with tile width TXO (0: default)
-  template <int INV, int PRUNE, int TXO>
+  // batched passes with tile width TXO (0: default) and plan variant V
+  template <int INV, int PRUNE, int TXO, int V>
   static void yb_go(const BatchArgs& B, int count, int planes, int fields, cudaStream_t st) {
     using Y = YCfg<T, N, INV, TXO>;
-    k_ypass_b<T, N, INV, PRUNE, TXO><<<dim3(N / Y::TX, planes, fields * count), Y::THREADS, Y::SMEM, st>>>(B, fields);
+    k_ypass_b<T, N, INV, PRUNE, TXO, V><<<dim3(N / Y::TX, planes, fields * count), Y::THREADS, Y::SMEM, st>>>(B, fields);
   }
-  template <int INV, int PRUNE>
+  template <int INV, int PRUNE, int V>
   static void yb_stage(int tile, const BatchArgs& B, int count, int planes, int fields, cudaStream_t st) {
     if constexpr (ISO && N <= BATCH_MAX_N) {
-      if constexpr (ytile_ok(4)) if (tile == 4) return yb_go<INV, PRUNE, 4>(B, count, planes, fields, st);
-      if constexpr (ytile_ok(8)) if (tile == 8) return yb_go<INV, PRUNE, 8>(B, count, planes, fields, st);
-      if constexpr (ytile_ok(16)) if (tile == 16) return yb_go<INV, PRUNE, 16>(B, count, planes, fields, st);
-      if constexpr (ytile_ok(32)) if (tile == 32) return yb_go<INV, PRUNE, 32>(B, count, planes, fields, st);
+      if constexpr (ytile_ok(4)) if (tile == 4) return yb_go<INV, PRUNE, 4, V>(B, count, planes, fields, st);
+      if constexpr (ytile_ok(8)) if (tile == 8) return yb_go<INV, PRUNE, 8, V>(B, count, planes, fields, st);
+      if constexpr (ytile_ok(16)) if (tile == 16) return yb_go<INV, PRUNE, 16, V>(B, count, planes, fields, st);
+      if constexpr (ytile_ok(32)) if (tile == 32) return yb_go<INV, PRUNE, 32, V>(B, count, planes, fields, st);
     }
-    yb_go<INV, PRUNE, 0>(B, count, planes, fields, st);
+    yb_go<INV, PRUNE, 0, V>(B, count, planes, fields, st);
   }
-  template <int TXO>
+  template <int TXO, int V>
   static void zb_go(const BatchArgs& B, int count, cudaStream_t st) {
     constexpr int TX = TXO > 0 ? TXO : G::ZTX;
-    k_zpass_b<T, N, ZM_CROSS, TXO><<<dim3(N / TX, N, count), ZP_THREADS, G::zbytes(TX), st>>>(B);
+    k_zpass_b<T, N, ZM_CROSS, TXO, V><<<dim3(N / TX, N, count), ZP_THREADS, G::zbytes(TX), st>>>(B);
   }
+  template <int V>
   static void zb_stage(int tile, const BatchArgs& B, int count, cudaStream_t st) {
-    if constexpr (ztile_ok(4)) if (tile == 4) return zb_go<4>(B, count, st);
-    if constexpr (ztile_ok(8)) if (tile == 8) return zb_go<8>(B, count, st);
-    if constexpr (ztile_ok(16)) if (tile == 16) return zb_go<16>(B, count, st);
-    if constexpr (ztile_ok(32)) if (tile == 32) return zb_go<32>(B, count, st);
-    zb_go<0>(B, count, st);
+    if constexpr (ztile_ok(4)) if (tile == 4) return zb_go<4, V>(B, count, st);
+    if constexpr (ztile_ok(8)) if (tile == 8) return zb_go<8, V>(B, count, st);
+    if constexpr (ztile_ok(16)) if (tile == 16) return zb_go<16, V>(B, count, st);
+    if constexpr (ztile_ok(32)) if (tile == 32) return zb_go<32, V>(B, count, st);
+    zb_go<0, V>(B, count, st);
   }
 
+  // one batched stage; the members share one radix plan (the ensemble groups them by it)
   static cudaError_t rk_stage_batch(const PassArgs* A, int count, int kmax3, cudaStream_t st) {
     if constexpr (BATCHED && N != 512 && N != 1024) {
       if (count < 1 || count > BATCH_MAX_COUNT) return cudaErrorInvalidValue;
+      for (int i = 1; i < count; ++i)
+        if (A[i].plan != A[0].plan) return cudaErrorInvalidValue;
       BatchArgs B;
       for (int i = 0; i < count; ++i) B.a[i] = f32args(A[i]);
       // the members' tile widths where they agree (a size class tuned together), else the defaults
@@ -2186,13 +2244,18 @@ struct SolverImpl {
         if (A[i].ytile[1] != yf) yf = 0;
         if (A[i].ztile != zt) zt = 0;
       }
-      yb_stage<1, 0>(yi, B, count, M, 6, st);
-      zb_stage(zt, B, count, st);
-      yb_stage<0, 1>(yf, B, count, kc_of(kmax3), 3, st);
-      if (A[0].lsrk)
-        k_xpass_b<T, N, XM_STAGE2N><<<dim3(M * N, count), XP_THREADS, xsmem_stage(A[0].stage, A[0].last), st>>>(B);
-      else
-        k_xpass_b<T, N, XM_STAGE><<<dim3(M * N, count), XP_THREADS, xsmem_stage(A[0].stage, A[0].last), st>>>(B);
+      const int plan = A[0].plan;
+      with_plan(bit(plan, PLAN_YI), [&](auto v) { yb_stage<1, 0, decltype(v)::value>(yi, B, count, M, 6, st); });
+      with_plan(bit(plan, PLAN_Z), [&](auto v) { zb_stage<decltype(v)::value>(zt, B, count, st); });
+      with_plan(bit(plan, PLAN_YF),
+                [&](auto v) { yb_stage<0, 1, decltype(v)::value>(yf, B, count, kc_of(kmax3), 3, st); });
+      with_plan(bit(plan, PLAN_X), [&](auto v) {
+        constexpr int V = decltype(v)::value;
+        if (A[0].lsrk)
+          k_xpass_b<T, N, XM_STAGE2N, V><<<dim3(M * N, count), XP_THREADS, xsmem_stage(A[0].stage, A[0].last), st>>>(B);
+        else
+          k_xpass_b<T, N, XM_STAGE, V><<<dim3(M * N, count), XP_THREADS, xsmem_stage(A[0].stage, A[0].last), st>>>(B);
+      });
       return cudaGetLastError();
     } else {
       return cudaErrorNotSupported;
@@ -2270,7 +2333,9 @@ struct SolverImpl {
     rhs_front(a, st);
     PassArgs b = a;
     b.stage = 0;
-    k_xpass<T, N, XM_RHS, NY, NZ><<<ROWS, XP_THREADS, xsmem_stage(0, 3), st>>>(f32args(b));
+    with_plan(bit(b.plan, PLAN_X), [&](auto v) {
+      k_xpass<T, N, XM_RHS, NY, NZ, decltype(v)::value><<<ROWS, XP_THREADS, xsmem_stage(0, 3), st>>>(f32args(b));
+    });
     return cudaGetLastError();
   }
 
@@ -2310,7 +2375,7 @@ struct SolverImpl {
                              &diag,     BATCHED ? &rk_stage_batch : nullptr, &y_tiles, &z_tiles,
                              PLANE ? &rk_stage_fused : nullptr, &prime_fused,
                              PLANE ? &rk_stage_fused_part : nullptr, PLANE ? &plane_wait_test : nullptr,
-                             PLANE ? PlaneCfg<T, N>::ctl_words() : 0, NY, NZ, G::TW};
+                             PLANE ? PlaneCfg<T, N>::ctl_words() : 0, NY, NZ, G::TW, PLANS};
     return &o;
   }
 };

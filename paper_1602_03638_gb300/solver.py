@@ -164,9 +164,9 @@ class Solver:
         _lib.check(_lib.lib().dns_set_rk_tableau(self._h, int(form), len(a), av, bv), "dns_set_rk_tableau")
 
     def tune_tiles(self, steps: int = 5) -> tuple:
-        """Time dns_step with each y- and z-pass tile width the grid offers; keep the
-        fastest (y_inverse, y_forward, z) widths (0 = default). The state and time are
-        left unchanged."""
+        """Time dns_step with each radix plan and each y- and z-pass tile width the grid
+        offers; keep the fastest plan (option "fft_plan") and (y_inverse, y_forward, z)
+        widths (0 = default), returned. The state and time are left unchanged."""
         ti, tf, tz = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _lib.check(_lib.lib().dns_tune_tiles(self._h, int(steps), ctypes.byref(ti), ctypes.byref(tf), ctypes.byref(tz)),
                    "dns_tune_tiles")
@@ -258,15 +258,17 @@ class Ensemble:
         _lib.check(_lib.lib().dns_ensemble_step(self._e, int(n)), "dns_ensemble_step")
 
     def tune(self) -> dict:
-        """Pick the y- and z-pass tile widths per grid size and the schedule (batching,
-        branch count) by timing; advances every member (see include/dns.h)."""
+        """Pick the radix plan and the y- and z-pass tile widths per grid size and the
+        schedule (batching, branch count) by timing; advances every member (see
+        include/dns.h)."""
         k = ctypes.c_int()
         _lib.check(_lib.lib().dns_ensemble_tune(self._e, ctypes.byref(k)), "dns_ensemble_tune")
         tiles = {}
         for m in self.members:
             tiles.setdefault(m.N, {"y_inverse": int(m.get_option("y_tile_inverse")),
                                    "y_forward": int(m.get_option("y_tile_forward")),
-                                   "z": int(m.get_option("z_tile"))})
+                                   "z": int(m.get_option("z_tile")),
+                                   "plan": int(m.get_option("fft_plan"))})
         return {"batching": self.batching, "streams": k.value, "tiles": tiles}
 
     def set_batching(self, max_batch: int):

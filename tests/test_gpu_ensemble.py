@@ -31,8 +31,9 @@ def _ics(Ns, dtype):
     return [inputs.isotropic_spectral(N, seed=100 + i, k0=2.0 + i % 4).numpy().astype(CPLX[dtype]) for i, N in enumerate(Ns)]
 
 
-def _alone(N, nu, dt, dtype, uh, steps):
+def _alone(N, nu, dt, dtype, uh, steps, plan=0):
     with Solver(N, nu, dt, dtype) as s:
+        s.set_option("fft_plan", plan)
         s.set_state_spectral(uh)
         s.step(steps)
         return s.get_state_spectral()
@@ -105,10 +106,11 @@ def test_ensemble_tune_advances_and_keeps_identity():
         assert pick["batching"] > 0 or 1 <= pick["streams"] <= len(Ns)
         taken = int(round(ens.members[0].diagnostics()["t"] / 0.005))
         assert taken >= 2 and taken % 2 == 0
+        plans = [int(m.get_option("fft_plan")) for m in ens.members]  # chosen by the tuner
         ens.step(2)
         got = [m.get_state_spectral() for m in ens.members]
     for i, N in enumerate(Ns):
-        assert np.array_equal(got[i], _alone(N, 0.01, 0.005, "f32", ics[i], taken + 2))
+        assert np.array_equal(got[i], _alone(N, 0.01, 0.005, "f32", ics[i], taken + 2, plans[i]))
 
 
 def test_ensemble_argument_errors():
