@@ -189,20 +189,42 @@ int dns_get_option(const dns_handle* h, const char* key, double* value);
  * arrays as the built-in schemes. Errors: DNS_ERR_ARG. */
 int dns_set_rk_tableau(dns_handle* h, int form, int stages, const double* a, const double* b);
 
-/* Schedule tuner for the small grids: times dns_step with both radix plans of each
- * pass ("fft_plan" bits) and every tile width the grid offers for the y-inverse, the
- * y-forward and the z-pass (defaults included), one knob at a time (the plan bits first)
+/* Schedule tuner: times dns_step with the plane-pass schedule off and on ("fused_planes",
+ * where compiled), both radix plans of each pass ("fft_plan" bits, N <= 128) and every
+ * tile width the grid offers for the y-inverse, the y-forward and the z-pass (N <= 128;
+ * defaults included), one knob at a time (the schedule, then the plan bits, then the widths)
  * with the best values found before it, three timings of `steps` graph replays each
  * after a capture and a warm-up step; a candidate replaces the one kept so far
  * (starting from the default) only if its median time beats that one's median by
  * more than that one's spread (max - min); the kept widths are written to
- * *y_inverse, *y_forward, *z (0 = default) and the kept plan is the handle's
- * "fft_plan". Every candidate starts from the same state, and the state and time
+ * *y_inverse, *y_forward, *z (0 = default), the kept plan and schedule are the handle's
+ * "fft_plan" and "fused_planes". Every candidate starts from the same state, and the state and time
  * are restored at the end; the results of later steps do not depend on the widths
  * (the plan changes their rounding only). Allocates and frees one state copy (3
  * fields). Synchronises. Errors: DNS_ERR_ARG (steps < 1, NULL outputs),
  * DNS_ERR_OOM, DNS_ERR_CUDA. */
 int dns_tune_tiles(dns_handle* h, int steps, int* y_inverse, int* y_forward, int* z);
+
+/* Tune cache (no counterpart in the paper; the tuners' choices kept across runs):
+ * with a path set, dns_tune_tiles first looks for a stored choice for the handle's
+ * device (its name), grid counts and precision and applies it without timing (the
+ * state is untouched); otherwise it tunes and appends its choice. dns_ensemble_tune
+ * does the same for its schedule, keyed by device, precision and the members' sizes
+ * with their counts (a stored schedule is applied without advancing the members;
+ * the size classes' plans and widths come from the tiles entries). The file is plain
+ * text, one entry per line, the last matching line wins:
+ *   tiles <device> <Nx> <Ny> <Nz> <f32|f64> <y_inverse> <y_forward> <z> <fft_plan> <fused_planes>
+ *   ensemble <device> <f32|f64> <N:count,...> <max_batch> <streams>
+ * with blanks in the device name written as '_'; a stored value the grid does not
+ * offer makes the tuner time again. Process-wide; NULL or "" turns it off (the
+ * default). Errors: DNS_ERR_ARG if the file cannot be opened for appending. */
+int dns_set_tune_cache(const char* path);
+
+/* The stored tiles entry of the tune cache for (device, Nx, Ny, Nz, dtype): returns 1
+ * and writes the widths, the plan mask and the schedule when found, 0 when not (or no
+ * cache is set), DNS_ERR_ARG for a NULL argument. Host only; needs no device. */
+int dns_tune_cache_lookup(const char* device, int Nx, int Ny, int Nz, int dtype, int* y_inverse, int* y_forward,
+                          int* z, int* plan, int* fused_planes);
 
 /* The tile widths a grid offers the tuner besides the default: which = 0 the
  * y-passes ("y_tile_inverse", "y_tile_forward"), 1 the z-pass ("z_tile"), for

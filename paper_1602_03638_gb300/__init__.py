@@ -5,6 +5,6 @@ include/dns.h); ``Solver`` is a thin marshalling layer over it. Nothing here
 computes the method on the CPU: without the built library every call raises.
 """
 
-from .solver import Ensemble, Solver  # noqa: F401
+from .solver import Ensemble, Solver, set_tune_cache, tune_cache_lookup  # noqa: F401
 
-__all__ = ["Solver", "Ensemble"]
+__all__ = ["Solver", "Ensemble", "set_tune_cache", "tune_cache_lookup"]

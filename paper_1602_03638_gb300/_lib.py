@@ -49,6 +49,9 @@ SIGNATURES = {
     "dns_set_option": (_I, [_P, ctypes.c_char_p, _D]),
     "dns_get_option": (_I, [_P, ctypes.c_char_p, ctypes.POINTER(_D)]),
     "dns_tune_tiles": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "dns_set_tune_cache": (_I, [ctypes.c_char_p]),
+    "dns_tune_cache_lookup": (_I, [ctypes.c_char_p, _I, _I, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
+                                   ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "dns_set_rk_tableau": (_I, [_P, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "dns_tile_widths": (_I, [_I, _I, _I, ctypes.POINTER(_I), _I]),
     "dns_set_state": (_I, [_P, _P, _I]),

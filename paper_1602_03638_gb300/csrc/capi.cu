@@ -9,7 +9,10 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -667,18 +670,140 @@ int dns_set_rk_tableau(dns_handle* h, int form, int stages, const double* a, con
   return DNS_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// ---- tune cache: the tuners' choices kept in a text file across runs ----
+// One entry per line, later lines win:
+//   tiles <device> <Nx> <Ny> <Nz> <f32|f64> <y_inverse> <y_forward> <z> <plan> <fused_planes>
+//   ensemble <device> <f32|f64> <N:count,...> <max_batch> <streams>
+std::mutex g_tc_mu;
+std::string g_tc_path;
+
+std::string tc_device(int dev) {
+  cudaDeviceProp p;
+  if (cudaGetDeviceProperties(&p, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return "unknown";
+  }
+  std::string n = p.name;
+  for (char& c : n)
+    if (c == ' ' || c == '\t') c = '_';
+  return n.empty() ? std::string("unknown") : n;
+}
+
+// values of the last line whose leading tokens equal `key`, or false
+bool tc_find(const std::vector<std::string>& key, std::vector<long>& vals, size_t nvals) {
+  std::lock_guard<std::mutex> lk(g_tc_mu);
+  if (g_tc_path.empty()) return false;
+  FILE* f = fopen(g_tc_path.c_str(), "r");
+  if (!f) return false;
+  bool found = false;
+  char line[1024];
+  while (fgets(line, sizeof line, f)) {
+    std::vector<std::string> tok;
+    for (char* t = strtok(line, " \t\r\n"); t; t = strtok(nullptr, " \t\r\n")) tok.push_back(t);
+    if (tok.size() != key.size() + nvals || !std::equal(key.begin(), key.end(), tok.begin())) continue;
+    std::vector<long> v;
+    bool ok = true;
+    for (size_t i = key.size(); i < tok.size() && ok; ++i) {
+      char* end = nullptr;
+      v.push_back(strtol(tok[i].c_str(), &end, 10));
+      ok = end && *end == '\0';
+    }
+    if (ok) {
+      vals = v;
+      found = true;
+    }
+  }
+  fclose(f);
+  return found;
+}
+
+void tc_put(const std::vector<std::string>& key, const std::vector<long>& vals) {
+  std::lock_guard<std::mutex> lk(g_tc_mu);
+  if (g_tc_path.empty()) return;
+  FILE* f = fopen(g_tc_path.c_str(), "a");
+  if (!f) return;
+  for (const std::string& k : key) fprintf(f, "%s ", k.c_str());
+  for (size_t i = 0; i < vals.size(); ++i) fprintf(f, i + 1 < vals.size() ? "%ld " : "%ld\n", vals[i]);
+  fclose(f);
+}
+
+std::vector<std::string> tc_tiles_key(const std::string& device, int Nx, int Ny, int Nz, int dtype) {
+  return {"tiles", device, std::to_string(Nx), std::to_string(Ny), std::to_string(Nz), dtype ? "f64" : "f32"};
+}
+
+bool offered(int v, const int* cand, int n) {
+  for (int i = 0; i < n; ++i)
+    if (cand[i] == v) return true;
+  return false;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dns_set_tune_cache(const char* path) {
+  std::lock_guard<std::mutex> lk(g_tc_mu);
+  if (!path || !*path) {
+    g_tc_path.clear();
+    return DNS_OK;
+  }
+  FILE* f = fopen(path, "a");
+  if (!f) return fail(DNS_ERR_ARG, "dns_set_tune_cache: cannot open '%s' for appending", path);
+  fclose(f);
+  g_tc_path = path;
+  return DNS_OK;
+}
+
+int dns_tune_cache_lookup(const char* device, int Nx, int Ny, int Nz, int dtype, int* y_inverse, int* y_forward,
+                          int* z, int* plan, int* fused_planes) {
+  if (!device || !y_inverse || !y_forward || !z || !plan || !fused_planes)
+    return fail(DNS_ERR_ARG, "dns_tune_cache_lookup: NULL argument");
+  std::vector<long> v;
+  if (!tc_find(tc_tiles_key(device, Nx, Ny, Nz, dtype), v, 5)) return 0;
+  *y_inverse = (int)v[0];
+  *y_forward = (int)v[1];
+  *z = (int)v[2];
+  *plan = (int)v[3];
+  *fused_planes = (int)v[4];
+  return 1;
+}
+
 int dns_tune_tiles(dns_handle* h, int steps, int* y_inverse, int* y_forward, int* z) {
   int rc = check_handle(h);
   if (rc) return rc;
   if (steps < 1 || !y_inverse || !y_forward || !z) return fail(DNS_ERR_ARG, "dns_tune_tiles: bad arguments");
   if ((rc = use_device(h))) return rc;
   // candidates per knob (the default first): y-inverse width, y-forward width, z width,
-  // and the radix plan variant (0, 1) of each pass
-  int ycand[9] = {0}, zcand[9] = {0}, pcand[2] = {0, 1};
+  // the radix plan variant (0, 1) of each pass, and the schedule (four passes, plane pass)
+  int ycand[9] = {0}, zcand[9] = {0}, pcand[2] = {0, 1}, fcand[2] = {0, 1};
   const int ny = 1 + h->ops->y_tiles(ycand + 1, 8);
   const int nz = 1 + h->ops->z_tiles(zcand + 1, 8);
   const int np = h->ops->plans;
-  if (ny == 1 && nz == 1 && np == 1) {  // this grid offers the defaults only
+  const int nf = (h->ops->rk_stage_fused && h->ctl) ? 2 : 1;
+  if (ny == 1 && nz == 1 && np == 1 && nf == 1) {  // this grid offers the defaults only
+    *y_inverse = h->ytile[0];
+    *y_forward = h->ytile[1];
+    *z = h->ztile;
+    return DNS_OK;
+  }
+  // a choice stored in the tune cache for this device and grid is applied without timing
+  const std::vector<std::string> tkey = tc_tiles_key(tc_device(h->device), h->N, h->Ny, h->Nz, h->dtype);
+  std::vector<long> cached;
+  if (tc_find(tkey, cached, 5) && offered((int)cached[0], ycand, ny) && offered((int)cached[1], ycand, ny) &&
+      offered((int)cached[2], zcand, nz) && cached[3] >= 0 && cached[3] < (np > 1 ? 1 << PLAN_BITS : 1) &&
+      cached[4] >= 0 && cached[4] < nf) {
+    h->ytile[0] = (int)cached[0];
+    h->ytile[1] = (int)cached[1];
+    h->ztile = (int)cached[2];
+    h->plan = (int)cached[3];
+    h->fused = (int)cached[4];
+    h->graph_dirty = true;
+    ++h->epoch;
+    h->w_valid = false;
     *y_inverse = h->ytile[0];
     *y_forward = h->ytile[1];
     *z = h->ztile;
@@ -688,7 +813,7 @@ int dns_tune_tiles(dns_handle* h, int steps, int* y_inverse, int* y_forward, int
   void* save = nullptr;
   if ((rc = dev_alloc(h, &save, bytes, "tuning copy of the state"))) return rc;
   const double t0 = h->t;
-  const int keep[4] = {h->ytile[0], h->ytile[1], h->ztile, h->plan};
+  const int keep[5] = {h->ytile[0], h->ytile[1], h->ztile, h->plan, h->fused};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t err = cudaMemcpyAsync(save, h->U, bytes, cudaMemcpyDeviceToDevice, h->stream);
   if (err == cudaSuccess) err = cudaEventCreate(&e0);
@@ -699,6 +824,7 @@ int dns_tune_tiles(dns_handle* h, int steps, int* y_inverse, int* y_forward, int
     h->ytile[1] = v[1];
     h->ztile = v[2];
     h->plan = v[3];
+    h->fused = v[4];
     h->graph_dirty = true;
   };
   // each candidate starts from the saved state: capture and one warm-up step, then
@@ -724,22 +850,24 @@ int dns_tune_tiles(dns_handle* h, int steps, int* y_inverse, int* y_forward, int
     *spread = t[2] - t[0];
     return DNS_OK;
   };
-  // one knob at a time, the others kept: the radix plan of the x-, y-inverse, z- and
-  // y-forward passes (with the widths the handle has), the y-inverse width, the y-forward
-  // width, then the z width, each with the best values found before it. The first
-  // candidate is the default; another replaces the one kept so far only if its median
-  // beats that one's median by more than that one's spread (differences inside the
-  // timing noise keep the earlier choice).
-  int best_v[4] = {keep[0], keep[1], keep[2], 0};
-  // which < 3: a tile width; which = 3 + b: the plan bit b
+  // one knob at a time, the others kept: the schedule (four passes or the plane pass),
+  // the radix plan of the x-, y-inverse, z- and y-forward passes (with the widths the
+  // handle has), the y-inverse width, the y-forward width, then the z width, each with
+  // the best values found before it. The first candidate is the default; another
+  // replaces the one kept so far only if its median beats that one's median by more
+  // than that one's spread (differences inside the timing noise keep the earlier choice).
+  int best_v[5] = {keep[0], keep[1], keep[2], 0, 0};
+  // which < 3: a tile width; which = 3 + b: the plan bit b; which = FUSED: the schedule
+  constexpr int FUSED = 3 + PLAN_BITS;
   auto pick = [&](int n, const int* cand, int which) {
     float best = 0.f, best_spread = 0.f, ms = 0.f, spread = 0.f;
     auto with = [&](int* v, int c) {
       if (which < 3) v[which] = cand[c];
+      else if (which == FUSED) v[4] = cand[c];
       else v[3] = (v[3] & ~(1 << (which - 3))) | (cand[c] << (which - 3));
     };
     for (int c = 0; c < n && !rc; ++c) {
-      int v[4] = {best_v[0], best_v[1], best_v[2], best_v[3]};
+      int v[5] = {best_v[0], best_v[1], best_v[2], best_v[3], best_v[4]};
       with(v, c);
       if ((rc = timed(v, &ms, &spread))) return;
       if (c == 0 || ms < best - best_spread) {
@@ -749,6 +877,7 @@ int dns_tune_tiles(dns_handle* h, int steps, int* y_inverse, int* y_forward, int
       }
     }
   };
+  if (nf > 1) pick(nf, fcand, FUSED);
   if (np > 1)
     for (int b : {PLAN_X, PLAN_YI, PLAN_Z, PLAN_YF}) pick(np, pcand, 3 + b);
   pick(ny, ycand, 0);
@@ -766,6 +895,7 @@ int dns_tune_tiles(dns_handle* h, int steps, int* y_inverse, int* y_forward, int
   apply(rc ? keep : best_v);
   ++h->epoch;
   if (!rc && err != cudaSuccess) rc = cuda_fail(err, "dns_tune_tiles restore");
+  if (!rc) tc_put(tkey, {best_v[0], best_v[1], best_v[2], best_v[3], best_v[4]});
   *y_inverse = h->ytile[0];
   *y_forward = h->ytile[1];
   *z = h->ztile;
@@ -1401,6 +1531,20 @@ int dns_ensemble_tune(dns_ensemble* e, int* best_streams) {
   rc = ens_prepare_members(e);
   if (rc) return rc;
   const int n = (int)e->m.size();
+  // the schedule stored in the tune cache for this device, precision and member sizes
+  std::map<int, int> census;
+  for (dns_handle* h : e->m) ++census[h->N];
+  std::string sizes;
+  for (const auto& kv : census) sizes += (sizes.empty() ? "" : ",") + std::to_string(kv.first) + ":" + std::to_string(kv.second);
+  const std::vector<std::string> ekey = {"ensemble", tc_device(e->m[0]->device), e->m[0]->dtype ? "f64" : "f32", sizes};
+  std::vector<long> cached;
+  if (tc_find(ekey, cached, 2) && cached[0] >= 0 && cached[1] >= 0 && cached[1] <= n) {
+    e->batch = (int)cached[0];
+    e->streams = (int)cached[1];
+    e->dirty = true;
+    if (best_streams) *best_streams = e->streams;
+    return DNS_OK;
+  }
   // candidate schedules: batched launches (whole groups, then smaller batches,
   // one graph branch per unit) and per-member launches over 1 .. n branches
   struct Cand {
@@ -1442,6 +1586,7 @@ int dns_ensemble_tune(dns_ensemble* e, int* best_streams) {
   e->batch = pick.batch;
   e->streams = pick.streams;
   e->dirty = true;
+  tc_put(ekey, {pick.batch, pick.streams});
   if (best_streams) *best_streams = pick.streams;
   return DNS_OK;
 }

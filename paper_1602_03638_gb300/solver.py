@@ -46,6 +46,25 @@ def _ptr(arr, shape, real_dtype_bytes, complex_):
 INTEGRATORS = {"rk4": 0, "euler": 1, "heun": 2, "midpoint": 3, "williamson3": 4, "ck45": 5}
 
 
+def set_tune_cache(path) -> None:
+    """Keep the tuners' choices in a text file across runs (dns_set_tune_cache); None turns it off."""
+    _lib.check(_lib.lib().dns_set_tune_cache(None if path is None else str(path).encode()), "dns_set_tune_cache")
+
+
+def tune_cache_lookup(device: str, shape, dtype: str):
+    """The stored tiles entry for (device, (Nx, Ny, Nz), dtype), or None:
+    {"y_inverse", "y_forward", "z", "plan", "fused_planes"}."""
+    nx, ny, nz = _shape(shape)
+    v = [ctypes.c_int() for _ in range(5)]
+    rc = _lib.lib().dns_tune_cache_lookup(device.encode(), nx, ny, nz, {"f32": 0, "f64": 1}[dtype],
+                                          *[ctypes.byref(x) for x in v])
+    if rc < 0:
+        _lib.check(rc, "dns_tune_cache_lookup")
+    if rc == 0:
+        return None
+    return dict(zip(("y_inverse", "y_forward", "z", "plan", "fused_planes"), (x.value for x in v)))
+
+
 def _shape(N) -> tuple:
     """(Nx, Ny, Nz) from one point count or three."""
     if np.ndim(N) == 0:
@@ -164,9 +183,10 @@ class Solver:
         _lib.check(_lib.lib().dns_set_rk_tableau(self._h, int(form), len(a), av, bv), "dns_set_rk_tableau")
 
     def tune_tiles(self, steps: int = 5) -> tuple:
-        """Time dns_step with each radix plan and each y- and z-pass tile width the grid
-        offers; keep the fastest plan (option "fft_plan") and (y_inverse, y_forward, z)
-        widths (0 = default), returned. The state and time are left unchanged."""
+        """Time dns_step with each schedule, radix plan and y- and z-pass tile width the grid
+        offers; keep the fastest schedule and plan (options "fused_planes", "fft_plan") and
+        (y_inverse, y_forward, z) widths (0 = default), returned. The state and time are
+        left unchanged."""
         ti, tf, tz = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _lib.check(_lib.lib().dns_tune_tiles(self._h, int(steps), ctypes.byref(ti), ctypes.byref(tf), ctypes.byref(tz)),
                    "dns_tune_tiles")

@@ -94,3 +94,36 @@ def test_supported_sizes_match_the_instances():
     assert sizes == [8, 12, 16, 24, 32, 48, 64, 96, 128, 256, 512, 1024]
     with open(os.path.join(HEADER_DIR, "dns.h")) as f:
         assert "8, 12, 16, 24, 32, 48, 64, 96, 128, 256, 512, 1024" in f.read()
+
+
+def test_tune_cache_file_lookup(tmp_path, L):
+    """The tune cache's text format (dns_set_tune_cache): later entries win, malformed and
+    foreign lines are ignored, and an unwritable path is refused. Host only."""
+    from paper_1602_03638_gb300 import set_tune_cache, tune_cache_lookup
+
+    path = tmp_path / "tune.txt"
+    path.write_text(
+        "tiles GB300 32 32 32 f32 8 4 16 5 0\n"
+        "tiles GB300 32 32 32 f32 16 4 8 9 0\n"     # later line wins
+        "tiles GB300 48 48 48 f64 0 0 4 x 0\n"      # malformed value: ignored
+        "tiles GB300 256 256 256 f32 0 0 0 0 1\n"
+        "tiles Other 32 32 32 f32 4 4 4 1 0\n"      # another device
+        "ensemble GB300 f32 32:2,48:1 0 4\n"
+        "garbage\n")
+    try:
+        set_tune_cache(path)
+        assert tune_cache_lookup("GB300", 32, "f32") == {"y_inverse": 16, "y_forward": 4, "z": 8, "plan": 9,
+                                                         "fused_planes": 0}
+        assert tune_cache_lookup("GB300", 256, "f32")["fused_planes"] == 1
+        assert tune_cache_lookup("GB300", (32, 32, 32), "f64") is None
+        assert tune_cache_lookup("GB300", 48, "f64") is None
+        assert tune_cache_lookup("Other", 32, "f32")["plan"] == 1
+        set_tune_cache(None)
+        assert tune_cache_lookup("GB300", 32, "f32") is None  # cache off
+        with pytest.raises(_lib.DnsError):
+            set_tune_cache(tmp_path / "no_such_dir" / "tune.txt")
+    finally:
+        set_tune_cache(None)
+    a = ctypes.c_int()
+    assert L.dns_tune_cache_lookup(None, 32, 32, 32, 0, ctypes.byref(a), ctypes.byref(a), ctypes.byref(a),
+                                   ctypes.byref(a), ctypes.byref(a)) == _lib.DNS_ERR_ARG

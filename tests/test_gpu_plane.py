@@ -107,3 +107,18 @@ def test_bounded_waits_give_up_and_the_handle_recovers():
         ref = r.get_state_spectral()
     np.testing.assert_array_equal(got, ref)
     assert np.isfinite(d["energy"])
+
+
+def test_tuner_times_the_plane_schedule_and_keeps_the_state():
+    N = 256
+    uh = inputs.isotropic_spectral(N, seed=77, k0=N / 8.0, device="cuda").to(torch.complex64)
+    with Solver(N, 0.004, 2e-3, "f32") as s:
+        s.set_state_spectral(uh)
+        assert s.tune_tiles(1) == (0, 0, 0)  # no widths or plans at this size: the schedule only
+        fused = int(s.get_option("fused_planes"))
+        assert fused in (0, 1)
+        assert torch.equal(s.get_state_spectral(torch.empty_like(uh)), uh) and s.diagnostics()["t"] == 0.0
+        s.step(2)
+        got = s.get_state_spectral(torch.empty_like(uh))
+    ref, _ = _run(N, "f32", 1 - fused, uh, 2)  # the two schedules agree to the last bit
+    assert np.array_equal(got.cpu().numpy(), ref)

@@ -139,3 +139,37 @@ def test_ensemble_members_on_other_plans_equal_solo_runs(batching):
     for i, N in enumerate(Ns):
         solo = _run(N, dtype, ics[i], plans[i], steps=5, nu=nu, dt=dt)
         assert np.array_equal(got[i], solo), f"member {i} (N={N}, plan {plans[i]})"
+
+
+def test_tune_cache_applies_stored_choices_without_timing(tmp_path):
+    from paper_1602_03638_gb300 import set_tune_cache
+
+    path = tmp_path / "tune.txt"
+    set_tune_cache(path)
+    try:
+        N, dtype = 32, "f32"
+        uh = _iso(N, 11, dtype)
+        picks = []
+        for _ in range(2):
+            with Solver(N, 0.01, 0.004, dtype) as s:
+                s.set_state_spectral(uh)
+                picks.append((s.tune_tiles(2), s.get_option("fft_plan")))
+                assert np.array_equal(s.get_state_spectral(), uh) and s.diagnostics()["t"] == 0.0
+        assert picks[0] == picks[1]
+        lines = path.read_text().splitlines()
+        assert len(lines) == 1 and lines[0].split()[0] == "tiles"  # the second tune read, not timed
+        Ns = [16, 24, 16]
+        ics = [_iso(n, 30 + i, dtype) for i, n in enumerate(Ns)]
+        scheds = []
+        for k in range(2):
+            with Ensemble(Ns, [0.01] * 3, [0.004] * 3, dtype) as ens:
+                for m, u in zip(ens.members, ics):
+                    m.set_state_spectral(u)
+                scheds.append(ens.tune())
+                t = [m.diagnostics()["t"] for m in ens.members]
+                assert (min(t) > 0.0) if k == 0 else (max(t) == 0.0)  # a stored schedule takes no steps
+        assert scheds[0] == scheds[1]
+        kinds = [ln.split()[0] for ln in path.read_text().splitlines()]
+        assert kinds.count("ensemble") == 1 and kinds.count("tiles") == 3
+    finally:
+        set_tune_cache(None)
