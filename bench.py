@@ -482,7 +482,7 @@ def run_cufft_comparison(torch, N=N_MAIN, steps=3, warm=2):
 def run_closure_share(torch, N=64, steps=50):
     """Device time of the coarse 64^3 FP32 step with the closure inside the step graph, against
     the same step without it, and of the network forward alone on the N^3 features (CUDA
-    events): the kernel-time share of the wmma network in the modelled step."""
+    events): the kernel-time share of the network (tcgen05 inference) in the modelled step."""
     import numpy as np
 
     from paper_1602_03638_gb300 import Solver, inputs, sgs

@@ -439,7 +439,9 @@ int dns_mlp_train_step(dns_mlp* net, const float* X, const float* T, int P, doub
  * steps are seen by the next step); net = NULL detaches. FP32 handles of cubic
  * grids on the 2 pi box only (DNS_ERR_UNSUPPORTED otherwise); not together with
  * dns_set_forcing (DNS_ERR_ARG). Allocates its scratch (10 + 6 floats per grid
- * point and 12 spectral fields) on the first attach. */
+ * point and 21 spectral fields) and two side streams on the first attach: the three
+ * gradient transforms and the two stress transforms are independent and run
+ * concurrently (forked from and joined back into the handle's stream). */
 int dns_set_closure(dns_handle* h, dns_mlp* net, double delta);
 
 /* Test hook for allocation-failure handling: the n-th device allocation made

@@ -251,9 +251,12 @@ struct dns_handle {
   double closure_delta = 0.0;
   void* CX = nullptr;
   void* CT = nullptr;
-  void* CS = nullptr;
-  void* CW = nullptr;
+  void* CS = nullptr;  // 9 spectral fields: the gradients of u_0, u_1, u_2, then 6 stress fields
+  void* CW = nullptr;  // 9 work fields of the three gradient transforms
   void* FC = nullptr;
+  // side streams and fork/join events of the closure's independent transforms
+  cudaStream_t cl_side[2] = {nullptr, nullptr};
+  cudaEvent_t cl_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   void* tw = nullptr;
   double* diag = nullptr;
   int* ctl = nullptr;  // plane-pass control block (ops->plane_ctl_words ints)
@@ -293,6 +296,10 @@ void release(dns_handle* h) {
   void* bufs[] = {h->U, h->U1, h->US, h->W, h->D, h->F, h->tw, h->diag, h->ctl, h->CX, h->CT, h->CS, h->CW, h->FC};
   for (void* b : bufs)
     if (b) cudaFree(b);
+  for (cudaEvent_t ev : h->cl_ev)
+    if (ev) cudaEventDestroy(ev);
+  for (cudaStream_t cs : h->cl_side)
+    if (cs) cudaStreamDestroy(cs);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->own_stream) cudaStreamDestroy(h->own_stream);
 }
@@ -366,27 +373,40 @@ void set_stage(const dns_handle* h, int s, PassArgs& a) {
 // The closure force of the current state into FC (dns_set_closure): velocity
 // gradients i k_j u_hat_i -> 9 inverse transforms -> features; the network -> the 6
 // stress components -> 2 x 3 forward transforms -> f_i = -i k_j tau_hat_ij. FP32
-// handles on the 2 pi box; everything on the stream, no host synchronisation.
+// handles on the 2 pi box; everything on the stream, no host synchronisation. The
+// three gradient transforms and the two stress transforms are independent: they run
+// on the stream and two side streams (fork and join through events, also inside a
+// captured graph), each with its own scratch, so that their short launches overlap.
 cudaError_t closure_eval(dns_handle* h, cudaStream_t st) {
   const int N = h->N;
-  const size_t P = (size_t)N * N * N, cb = h->ops->elem_bytes;
+  const size_t P = (size_t)N * N * N, cb = h->ops->elem_bytes, fb = h->fs * cb;
   PassArgs a = base_args(h);
-  cudaError_t e = cudaSuccess;
+  cudaStream_t sc[3] = {st, h->cl_side[0], h->cl_side[1]};
+  cudaError_t e = cudaEventRecord(h->cl_ev[0], st);
+  for (int c = 1; c < 3 && e == cudaSuccess; ++c) e = cudaStreamWaitEvent(sc[c], h->cl_ev[0], 0);
   for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
-    e = closure_gradient(h->U, N, c, h->CS, h->dtype, st);
     PassArgs g = a;
-    g.U = h->CS;
-    g.W = h->CW;
+    g.U = (char*)h->CS + 3 * c * fb;
+    g.W = (char*)h->CW + 3 * c * fb;
     g.out = (float*)h->CX + 3 * c * P;
-    if (e == cudaSuccess) e = h->ops->inverse3d(g, st);
+    e = closure_gradient(h->U, N, c, g.U, h->dtype, sc[c]);
+    if (e == cudaSuccess) e = h->ops->inverse3d(g, sc[c]);
+  }
+  for (int c = 1; c < 3 && e == cudaSuccess; ++c) {
+    e = cudaEventRecord(h->cl_ev[c], sc[c]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->cl_ev[c], 0);
   }
   if (e == cudaSuccess) e = mlp_forward_async(h->closure, (const float*)h->CX, (float*)h->CT, (int)P, st);
-  for (int r = 0; r < 6 && e == cudaSuccess; r += 3) {
+  if (e == cudaSuccess) e = cudaEventRecord(h->cl_ev[3], st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(sc[1], h->cl_ev[3], 0);
+  for (int r = 0; r < 2 && e == cudaSuccess; ++r) {
     PassArgs f = a;
-    f.in = (const float*)h->CT + r * P;
-    f.U = (char*)h->CS + r * h->fs * cb;
-    e = h->ops->forward3d(f, st);
+    f.in = (const float*)h->CT + 3 * r * P;
+    f.U = (char*)h->CS + 3 * r * fb;
+    e = h->ops->forward3d(f, sc[r]);
   }
+  if (e == cudaSuccess) e = cudaEventRecord(h->cl_ev[4], sc[1]);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->cl_ev[4], 0);
   if (e == cudaSuccess) e = closure_force(h->CS, N, h->FC, h->dtype, st);
   return e;
 }
@@ -1148,9 +1168,13 @@ int dns_set_closure(dns_handle* h, dns_mlp* net, double delta) {
   if (!h->CX) {
     if ((rc = dev_alloc(h, &h->CX, 10 * P * sizeof(float), "closure features"))) return rc;
     if ((rc = dev_alloc(h, &h->CT, 6 * P * sizeof(float), "closure stress"))) return rc;
-    if ((rc = dev_alloc(h, &h->CS, 6 * h->fs * cb, "closure spectral fields"))) return rc;
-    if ((rc = dev_alloc(h, &h->CW, 3 * h->fs * cb, "closure work fields"))) return rc;
+    if ((rc = dev_alloc(h, &h->CS, 9 * h->fs * cb, "closure spectral fields"))) return rc;
+    if ((rc = dev_alloc(h, &h->CW, 9 * h->fs * cb, "closure work fields"))) return rc;
     if ((rc = dev_alloc(h, &h->FC, 3 * h->fs * cb, "closure force"))) return rc;
+    for (cudaStream_t& cs : h->cl_side)
+      DNS_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "dns_set_closure streams");
+    for (cudaEvent_t& ev : h->cl_ev)
+      DNS_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "dns_set_closure events");
   }
   DNS_CUDA(fill_f32((float*)h->CX + 9 * P, P, (float)delta, h->stream), "dns_set_closure");
   h->closure = net;
