@@ -572,18 +572,23 @@ __device__ __forceinline__ void zpass_body(const PassArgs a, const int bx, const
 
   if constexpr (MODE == ZM_LOAD) {
     // physical lines (x0 + x, y, :) of the 3 components, packed in pairs
+    // (the whole tile in flight at once by cp.async, no register staging)
     const cx<T>* in = reinterpret_cast<const cx<T>*>(a.in);
     for (int e = threadIdx.x; e < 3 * TX * M; e += ZP_THREADS) {
       const int n = e % M, x = (e / M) % TX, c = e / (M * TX);
-      s[padp(n) * LD + c * TX + x] = in[((size_t)(c * N + x0 + x) * NY + y) * M + n];
+      cp_async<sizeof(cx<T>)>(s + padp(n) * LD + c * TX + x, in + ((size_t)(c * N + x0 + x) * NY + y) * M + n);
     }
+    cp_async_commit();
+    cp_async_wait<0>();
     __syncthreads();
   } else {
     const cx<T>* src = reinterpret_cast<const cx<T>*>(MODE == ZM_MAXABS ? a.D : a.W);
     for (int e = threadIdx.x; e < NF * TX * M; e += ZP_THREADS) {
       const int x = e % TX, k = (e / TX) % M, f = e / (TX * M);
-      s[padp(k) * LD + f * TX + x] = src[f * FS + ((size_t)k * NY + y) * N + x0 + x];
+      cp_async<sizeof(cx<T>)>(s + padp(k) * LD + f * TX + x, src + f * FS + ((size_t)k * NY + y) * N + x0 + x);
     }
+    cp_async_commit();
+    cp_async_wait<0>();
     __syncthreads();
     // c2r pre-processing: Z'_k = (X_k + conj X_{M-k}) + i e^{+2 pi i k/N} (X_k - conj X_{M-k}),
     // stored conjugated so that a forward DFT gives the inverse one.
