@@ -145,7 +145,9 @@ int dns_set_stream(dns_handle* h, void* stream);
  *                      then radix-4 passes (one radix-8 pass for odd powers of two).
  *                      The same transforms with another rounding order: results agree
  *                      to round-off, not bit for bit; dns_tune_tiles picks the bits by
- *                      timing. 0 (default) .. 15; only 0 on the other grids.
+ *                      timing. 0 .. 15; only 0 on the other grids. A new handle starts with
+ *                      the mask measured fastest per grid size and precision on GB300
+ *                      (dns_get_option reads it).
  *   "use_graph"        1: dns_step replays a captured CUDA graph (default)
  *   "fused_planes"     0 (default) or 1 where compiled (N >= 256): 1 runs each RK
  *                      stage as two launches, the z-pass and one persistent plane pass that

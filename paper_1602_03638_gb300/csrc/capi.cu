@@ -498,6 +498,7 @@ int dns_create3(int Nx, int Ny, int Nz, double nu, double dt, int dtype, dns_han
   h->N = N;
   h->Ny = Ny;
   h->Nz = Nz;
+  h->plan = ops->default_plan;
   h->dtype = dtype;
   h->nu = nu;
   h->dt = dt;
@@ -799,7 +800,7 @@ int dns_tune_tiles(dns_handle* h, int steps, int* y_inverse, int* y_forward, int
   if ((rc = use_device(h))) return rc;
   // candidates per knob (the default first): y-inverse width, y-forward width, z width,
   // the radix plan variant (0, 1) of each pass, and the schedule (four passes, plane pass)
-  int ycand[9] = {0}, zcand[9] = {0}, pcand[2] = {0, 1}, fcand[2] = {0, 1};
+  int ycand[9] = {0}, zcand[9] = {0}, fcand[2] = {0, 1};
   const int ny = 1 + h->ops->y_tiles(ycand + 1, 8);
   const int nz = 1 + h->ops->z_tiles(zcand + 1, 8);
   const int np = h->ops->plans;
@@ -876,7 +877,7 @@ int dns_tune_tiles(dns_handle* h, int steps, int* y_inverse, int* y_forward, int
   // the best values found before it. The first candidate is the default; another
   // replaces the one kept so far only if its median beats that one's median by more
   // than that one's spread (differences inside the timing noise keep the earlier choice).
-  int best_v[5] = {keep[0], keep[1], keep[2], 0, 0};
+  int best_v[5] = {keep[0], keep[1], keep[2], h->ops->default_plan, 0};
   // which < 3: a tile width; which = 3 + b: the plan bit b; which = FUSED: the schedule
   constexpr int FUSED = 3 + PLAN_BITS;
   auto pick = [&](int n, const int* cand, int which) {
@@ -899,7 +900,11 @@ int dns_tune_tiles(dns_handle* h, int steps, int* y_inverse, int* y_forward, int
   };
   if (nf > 1) pick(nf, fcand, FUSED);
   if (np > 1)
-    for (int b : {PLAN_X, PLAN_YI, PLAN_Z, PLAN_YF}) pick(np, pcand, 3 + b);
+    for (int b : {PLAN_X, PLAN_YI, PLAN_Z, PLAN_YF}) {
+      const int d = (h->ops->default_plan >> b) & 1;  // the default's bit first
+      const int bits[2] = {d, 1 - d};
+      pick(np, bits, 3 + b);
+    }
   pick(ny, ycand, 0);
   pick(ny, ycand, 1);
   pick(nz, zcand, 2);

@@ -99,6 +99,7 @@ struct DnsOps {
   int NY, NZ;  // points along y and z (N is the count along x)
   int TW;      // length of the twiddle table exp(-2 pi i t / TW) (a multiple of N, NY, NZ)
   int plans;   // radix plan variants the stage launches offer (1: the default only, 2: AltPlan too)
+  int default_plan;  // the plan mask a new handle starts with
 };
 
 // bits of PassArgs::plan: the radix plan variant of each pass of a stage

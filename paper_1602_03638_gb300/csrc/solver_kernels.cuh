@@ -1973,6 +1973,25 @@ struct SolverImpl {
   // holds one bit per pass: PLAN_X (x-stage and x inverse), PLAN_YI (y-inverse),
   // PLAN_Z (z-pass), PLAN_YF (y-forward).
   static constexpr int PLANS = (ISO && N <= BATCH_MAX_N) ? 2 : 1;
+  // The handle's initial plan mask: AltPlan in the passes where it measured faster on
+  // GB300 (per-pass CUDA-event times of both schedules, 100 graph-replayed steps; FP64
+  // passes whose default has a radix-16 pass or radix-8 passes only run about twice as
+  // fast with radix 4). dns_tune_tiles re-measures on the machine at hand.
+  static constexpr int default_plan() {
+    if constexpr (PLANS == 1) {
+      return 0;
+    } else if constexpr (sizeof(T) == 8) {
+      constexpr int XYY = (1 << PLAN_X) | (1 << PLAN_YI) | (1 << PLAN_YF);
+      return (N == 16 || N == 48 || N == 64 || N == 128) ? XYY : 0;
+    } else {
+      switch (N) {
+        case 48: return (1 << PLAN_X) | (1 << PLAN_YF);
+        case 64: return (1 << PLAN_X) | (1 << PLAN_YI);
+        case 128: return (1 << PLAN_X) | (1 << PLAN_YI) | (1 << PLAN_YF);
+        default: return 0;
+      }
+    }
+  }
   static int bit(int plan, int b) { return (plan >> b) & 1; }
   // f(std::integral_constant<int, V>) with the variant V = plan (0 where not offered)
   template <class F>
@@ -2380,7 +2399,7 @@ struct SolverImpl {
                              &diag,     BATCHED ? &rk_stage_batch : nullptr, &y_tiles, &z_tiles,
                              PLANE ? &rk_stage_fused : nullptr, &prime_fused,
                              PLANE ? &rk_stage_fused_part : nullptr, PLANE ? &plane_wait_test : nullptr,
-                             PLANE ? PlaneCfg<T, N>::ctl_words() : 0, NY, NZ, G::TW, PLANS};
+                             PLANE ? PlaneCfg<T, N>::ctl_words() : 0, NY, NZ, G::TW, PLANS, default_plan()};
     return &o;
   }
 };

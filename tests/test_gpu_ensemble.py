@@ -31,9 +31,10 @@ def _ics(Ns, dtype):
     return [inputs.isotropic_spectral(N, seed=100 + i, k0=2.0 + i % 4).numpy().astype(CPLX[dtype]) for i, N in enumerate(Ns)]
 
 
-def _alone(N, nu, dt, dtype, uh, steps, plan=0):
+def _alone(N, nu, dt, dtype, uh, steps, plan=None):
     with Solver(N, nu, dt, dtype) as s:
-        s.set_option("fft_plan", plan)
+        if plan is not None:  # else the handle's default plan, as the members'
+            s.set_option("fft_plan", plan)
         s.set_state_spectral(uh)
         s.step(steps)
         return s.get_state_spectral()

@@ -173,3 +173,14 @@ def test_tune_cache_applies_stored_choices_without_timing(tmp_path):
         assert kinds.count("ensemble") == 1 and kinds.count("tiles") == 3
     finally:
         set_tune_cache(None)
+
+
+def test_new_handles_start_with_the_measured_default_masks():
+    # the masks measured fastest on GB300 (dns_get_option reads them); one plan above 128
+    expect = {(16, "f64"): 11, (64, "f64"): 11, (32, "f64"): 0, (96, "f64"): 0, (128, "f32"): 11,
+              (48, "f32"): 9, (64, "f32"): 3, (96, "f32"): 0, (24, "f32"): 0, (256, "f32"): 0}
+    for (N, dtype), mask in expect.items():
+        with Solver(N, 0.01, 0.004, dtype) as s:
+            assert s.get_option("fft_plan") == mask, (N, dtype)
+    with Solver((32, 16, 24), 0.01, 0.004, "f32") as s:
+        assert s.get_option("fft_plan") == 0
