@@ -633,7 +633,7 @@ def run_ours(args):
                           # the 3-pass model (x, y and z transforms each a separate HBM sweep, 204 cv
                           # per step): what the plane blocking of the 132-cv model would buy
                           "frac_of_measured_3pass_model": 204.0 * cvb / (ms_step * 1e-3) / 1e9 / peak,
-                          # DRAM bytes this build's four passes move per step (ncu, profiles/)
+                          # DRAM bytes the four passes move per step (ncu, profiles/)
                           "dram_bytes_per_step_measured": step_traffic(N, dtype)},
         "kernels": kernels,
         "clocks": clocks,

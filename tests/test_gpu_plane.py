@@ -5,7 +5,7 @@ Sec. 3.2 with the transposes replaced by changes of pass direction).
 
 The plane pass runs the same per-column and per-line arithmetic as the four-pass schedule, so
 after the same steps from the same state the two states agree to the last bit (checked), and
-both agree with the FP64 oracle (the benchmark spec tolerances). The bounded waits are exercised by
+both agree with the FP64 oracle (FP64 1e-12, FP32 1e-5 relative L2). The bounded waits are exercised by
 a debug hook whose waits cannot be met: they give up after 1 s, the host reads
 DNS_ERR_TIMEOUT, and the handle keeps working.
 """

@@ -314,7 +314,7 @@ def test_in_step_closure_rhs_matches_reference():
 
 def test_trained_closure_beats_the_unmodelled_coarse_run():
     """A-posteriori: 256^3 DNS (this solver) -> box-filtered 32^3 data -> network trained on the
-    GPU -> coarse 32^3 runs with and without the closure, judged against the filtered DNS."""
+    GPU -> coarse 32^3 runs with and without the closure, compared against the filtered DNS."""
     sgs = _sgs()
     r = sgs.closure_experiment(Nf=256, Nc=32, nu=2e-3, dt_f=2e-3, dt_c=5e-3, t_dev=0.4, t_run=0.8,
                                iters=400, batch=32768, seed=0)
