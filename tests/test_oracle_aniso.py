@@ -152,3 +152,12 @@ def test_random_field_is_divergence_free_and_in_each_directions_box():
     assert np.abs(np.sum(g.K * uh, axis=0)).max() < 1e-12 * np.abs(uh).max()
     assert np.all(uh[:, ~g.mask] == 0)
     assert abs(sn.energy(uh) - 1.0) < 1e-12
+
+
+def test_zero_nyquist_clears_each_directions_own_nyquist_plane():
+    uh = np.ones((3, 6, 4, 5), dtype=np.complex128)  # (Nx, Ny, Nz) = (6, 4, 8)
+    z = sn.zero_nyquist(uh)
+    K = sn.wavenumbers((6, 4, 8))
+    nyq = (np.abs(K[0]) == 3) | (np.abs(K[1]) == 2) | (K[2] == 4)
+    assert np.all(z[:, nyq] == 0) and np.all(z[:, ~nyq] == 1)
+    assert int(nyq.sum()) == 6 * 4 * 5 - 5 * 3 * 4  # kept: 5 kx x 3 ky x 4 kz
