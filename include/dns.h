@@ -92,7 +92,7 @@ int dns_create(int N, double nu, double dt, int dtype, dns_handle** out);
  * "dealias_variant" 1), the inverse transform normalised by 1/(Nx Ny Nz).
  * Array shapes and errors as for dns_create; Nx = Ny = Nz is the same as
  * dns_create(Nx, ...). The other counts run the generic passes: the options
- * "fused_planes", "y_tile_*" and "z_tile" offer only their defaults, and
+ * "fused_planes", "fft_plan", "y_tile_*" and "z_tile" offer only their defaults, and
  * dns_set_closure and ensembles take cubic grids only. dns_get_option reads
  * the counts back as "Nx", "Ny", "Nz" (on any handle).
  * Errors: DNS_ERR_ARG (the shape is not compiled, see the list above), as for
