@@ -872,36 +872,12 @@ __global__ void __launch_bounds__(32 * ZCrossWarps<T, N>::value, (ZCrossWarps<T,
 }
 
 // ---------------------------------------------------------------------------
-// z-pass of the right-hand side for N = 512 (lines of M = 256 values): each
+// Half-warp 256-point FFT of the N = 512 z-pass (lines of M = 256 values): each
 // line belongs to one half-warp, lane h holding positions h + 16 m (m < 16),
 // and the 256-point DFT is two radix-16 passes with a single shared-memory
 // exchange whose stores (17 h + r) and loads (h + 17 m) are free of bank
-// conflicts. Tile loads, the cross product and the stores walk
-// kz = 32 g + ZTX kq + c (kq = lane / ZTX), conflict-free per half-warp.
+// conflicts.
 // ---------------------------------------------------------------------------
-// Per-lane twiddles of the half-warp 256-point FFT and of the real-transform
-// pre/post-processing, computed once per block (FP32 form): p2[r] =
-// exp(-2 pi i h r / 256) for the second radix-16 pass and pre[m] =
-// exp(-2 pi i (h + 16 m) / 512). The FP64 form reads the table where used.
-template <typename T>
-struct HwTw {
-  cx<T> p2[16];
-  cx<T> pre[16];
-  __device__ __forceinline__ void init(const cx<T>* __restrict__ tw, int h) {
-    if constexpr (sizeof(T) == 4) {
-      twiddle_powers<16>(ldro(tw + 2 * h), p2);
-      const cx<T> tl = ldro(tw + h);
-      pre[0] = tl;
-#pragma unroll
-      for (int m = 1; m < 16; ++m) pre[m] = cmul(tl, ldro(tw + 16 * m));
-    }
-  }
-  __device__ __forceinline__ cx<T> wk(const cx<T>* __restrict__ tw, int h, int m) const {
-    if constexpr (sizeof(T) == 4) return pre[m];
-    else return ldro(tw + h + 16 * m);
-  }
-};
-
 // Leaner per-lane twiddles for the FP32 pipelined z-pass: the second-pass powers
 // p2[r] as in HwTw, and exp(-2 pi i (h + 16 m) / 512) formed on use as
 // tl * exp(-2 pi i m / 32) with the second factor a compile-time constant.
@@ -957,127 +933,6 @@ __device__ __forceinline__ void hw_fft256(cx<T> (&v)[16], cx<T>* ln, const HT& h
     for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], ldro(tw + h * r * C));
   }
   dft16(v);
-}
-
-// Warps per k_zcross16 block: 6 ZTX c2r and 3 ZTX r2c half-warp lines give
-// 4 and 2 line pairs per warp.
-template <typename T, int N>
-struct Z16Warps {
-  static constexpr int value = (3 * Geometry<T, N>::ZTX) / 4;
-};
-
-template <typename T, int N>
-__global__ void __launch_bounds__(32 * Z16Warps<T, N>::value, 2) k_zcross16(PassArgs a) {
-  using G = Geometry<T, N>;
-  constexpr int M = G::M, TX = G::ZTX, LD = G::ZLD;
-  constexpr int NW = Z16Warps<T, N>::value;
-  constexpr int ITEMS = (M / 32) * TX;  // walk items per field
-  constexpr size_t FS = G::FS;
-  static_assert(M == 256, "k_zcross16 is the N = 512 z-pass");
-  static_assert(TX == 4 || TX == 8 || TX == 16, "walk needs ZTX in {4, 8, 16}");
-  extern __shared__ unsigned char smraw[];
-  cx<T>* s = reinterpret_cast<cx<T>*>(smraw);
-  const cx<T>* tw = reinterpret_cast<const cx<T>*>(a.tw);
-  cx<T>* W = reinterpret_cast<cx<T>*>(a.W);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int h = lane & 15, half = lane >> 4;
-  const int x0 = blockIdx.x * TX, y = blockIdx.y;
-  int kc = (a.kmax3 + 2) / 3;
-  if (kc > M) kc = M;
-  const int tx = lane % TX, kq = lane / TX;
-  const cx<T>* gl = W + ((size_t)(TX * kq) * N + y) * N + x0 + tx;
-  cx<T>* sl = s + padp(TX * kq) * LD + tx;
-
-  // tile load: loads batched ahead of the shared-memory stores
-  static_assert((6 * ITEMS) % NW == 0, "z tile load split");
-  constexpr int PER_WARP = 6 * ITEMS / NW, BATCH = 8;
-  static_assert(PER_WARP % BATCH == 0, "z tile load batches");
-#pragma unroll 1
-  for (int i0 = 0; i0 < PER_WARP; i0 += BATCH) {
-    cx<T> t[BATCH];
-#pragma unroll
-    for (int u = 0; u < BATCH; ++u) {
-      const int it = w + (i0 + u) * NW;
-      const int f = it / ITEMS, r = it % ITEMS, g = r / TX, c = r % TX;
-      t[u] = gl[f * FS + (size_t)(32 * g + c) * N * N];
-    }
-#pragma unroll
-    for (int u = 0; u < BATCH; ++u) {
-      const int it = w + (i0 + u) * NW;
-      const int f = it / ITEMS, r = it % ITEMS, g = r / TX, c = r % TX;
-      sl[(34 * g + c) * LD + f * TX] = t[u];
-    }
-  }
-  HwTw<T> ht;
-  ht.init(tw, h);
-  __syncthreads();
-
-  cx<T> v[16];
-  // c2r of the 6 TX lines, two per warp at a time; physical pairs back in place
-#pragma unroll 1
-  for (int l = 2 * w + half; l < 6 * TX; l += 2 * NW) {
-    cx<T>* ln = s + l;
-    const cx<T>* pa = ln + h * LD;
-#pragma unroll
-    for (int m = 0; m < 16; ++m) {
-      const cx<T> xk = pa[17 * m * LD];
-      const cx<T> xm = (h == 0 && m == 0) ? mk((T)0, (T)0) : ln[padp(M - h - 16 * m) * LD];
-      cx<T> z;
-      if (h == 0 && m == 0) {
-        z = mk(xk.x, xk.x);  // Im X_0 ignored, X_M = 0
-      } else {
-        const cx<T> wk = ht.wk(tw, h, m);
-        const cx<T> A = xk + conjg(xm), B = xk - conjg(xm);
-        z = A + mul_pi(cmul(conjg(wk), B));
-      }
-      v[m] = conjg(z);
-    }
-    __syncwarp();
-    hw_fft256<T, N, LD>(v, ln, ht, tw, h);
-    cx<T>* pw = ln + h * LD;
-#pragma unroll
-    for (int m = 0; m < 16; ++m) pw[17 * m * LD] = conjg(v[m]);
-  }
-  __syncthreads();
-  // u x omega at every point, into the u lines
-  for (int it = w; it < ITEMS; it += NW) {
-    const int g = it / TX, c = it % TX;
-    cx<T>* p = sl + (34 * g + c) * LD;
-    const cx<T> u0 = p[0 * TX], u1 = p[1 * TX], u2 = p[2 * TX];
-    const cx<T> w0 = p[3 * TX], w1v = p[4 * TX], w2 = p[5 * TX];
-    p[0 * TX] = mk(u1.x * w2.x - u2.x * w1v.x, u1.y * w2.y - u2.y * w1v.y);
-    p[1 * TX] = mk(u2.x * w0.x - u0.x * w2.x, u2.y * w0.y - u0.y * w2.y);
-    p[2 * TX] = mk(u0.x * w1v.x - u1.x * w0.x, u0.y * w1v.y - u1.y * w0.y);
-  }
-  __syncthreads();
-  // r2c of the 3 TX product lines; X_k (k < kc) back into the line
-#pragma unroll 1
-  for (int l = 2 * w + half; l < 3 * TX; l += 2 * NW) {
-    cx<T>* ln = s + l;
-    const cx<T>* pa = ln + h * LD;
-#pragma unroll
-    for (int m = 0; m < 16; ++m) v[m] = pa[17 * m * LD];
-    __syncwarp();
-    hw_fft256<T, N, LD>(v, ln, ht, tw, h);
-    cx<T>* po = ln + h * LD;
-    const int partner = (16 - h) & 15;
-#pragma unroll
-    for (int m = 0; m < 16; ++m) {
-      cx<T> zo;
-      zo.x = __shfl_sync(0xffffffffu, v[15 - m].x, partner, 16);
-      zo.y = __shfl_sync(0xffffffffu, v[15 - m].y, partner, 16);
-      if (h == 0) zo = v[(16 - m) & 15];
-      const cx<T> wk = ht.wk(tw, h, m);
-      const cx<T> A = v[m] + conjg(zo), B = v[m] - conjg(zo);
-      if (h + 16 * m < kc) po[17 * m * LD] = scal(A + mul_mi(cmul(wk, B)), (T)0.5);
-    }
-  }
-  __syncthreads();
-  cx<T>* gd = W + ((size_t)(TX * kq) * N + y) * N + x0 + tx;
-  for (int it = w; it < 3 * ITEMS; it += NW) {
-    const int f = it / ITEMS, r = it % ITEMS, g = r / TX, c = r % TX;
-    if (32 * g + TX * kq + c < kc) gd[f * FS + (size_t)(32 * g + c) * N * N] = sl[(34 * g + c) * LD + f * TX];
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -2106,7 +1961,6 @@ struct SolverImpl {
       DNS_ATTR((k_zpass<T, N, ZM_CROSS, 0, N, N, 1>), G::ZSMEM);
     }
     if constexpr (ISO && ZCross<T, N>::enabled) DNS_ATTR((k_zcross<T, N>), G::ZSMEM);
-    if constexpr (ISO && N == 512) DNS_ATTR((k_zcross16<T, N>), G::ZSMEM);
     if constexpr (ISO && N == 512 && sizeof(T) == 4) DNS_ATTR((k_zcross16p<T, N>), Z16P<T>::SMEM);
     if constexpr (ISO && N == 1024 && sizeof(T) == 4) DNS_ATTR((k_zcross32p<T, N>), Z32P<T>::SMEM);
     if constexpr (ISO && N == 256 && sizeof(T) == 4) DNS_ATTR((k_zcross8q<T, N>), Z8Q<T>::SMEM);
@@ -2140,8 +1994,8 @@ struct SolverImpl {
       z_go<0>(a, st);
     else if constexpr (N == 512 && sizeof(T) == 4)
       k_zcross16p<T, N><<<num_sms(), 32 * Z16P<T>::NW, Z16P<T>::SMEM, st>>>(a);
-    else if constexpr (N == 512)
-      k_zcross16<T, N><<<dim3(N / G::ZTX, N), 32 * Z16Warps<T, N>::value, G::ZSMEM, st>>>(a);
+    else if constexpr (N == 512)  // FP64: the generic z-pass, measured faster than a half-warp
+      z_go<0>(a, st);             // radix-16 kernel (38.2 against 41.2 ms per launch)
     else if constexpr (N == 1024 && sizeof(T) == 4)
       k_zcross32p<T, N><<<num_sms(), 32 * Z32P<T>::NW, Z32P<T>::SMEM, st>>>(a);
     else if constexpr (N == 256 && sizeof(T) == 4)
