@@ -224,6 +224,35 @@ class Solver:
         _lib.check(_lib.lib().dns_rhs(self._h, p, dev), "dns_rhs")
         return out
 
+    def set_forcing(self, fhat=None):
+        """A force (3, Nx, Ny, Nz/2+1) complex, paper order, added to the nonlinear term of every
+        stage before the mask and the projection (dns_set_forcing); None removes it."""
+        if fhat is None:
+            _lib.check(_lib.lib().dns_set_forcing(self._h, None, 0), "dns_set_forcing")
+            return
+        p, dev = _ptr(fhat, self.spec_shape, self._rb, True)
+        _lib.check(_lib.lib().dns_set_forcing(self._h, p, dev), "dns_set_forcing")
+
+    def transform_r2c(self, phys, out):
+        """The solver's forward 3D transform of 3 device fields (dns_transform_r2c): phys
+        (3, Nx, Ny, Nz) real -> out (3, Nx, Ny, Nz/2+1) complex, unnormalised, Nyquist zeroed."""
+        p, dev = _ptr(phys, self.phys_shape, self._rb, False)
+        q, dev2 = _ptr(out, self.spec_shape, self._rb, True)
+        if not (dev and dev2):
+            raise ValueError("transform_r2c takes device arrays")
+        _lib.check(_lib.lib().dns_transform_r2c(self._h, p, q), "dns_transform_r2c")
+        return out
+
+    def transform_c2r(self, spec, out):
+        """The solver's inverse 3D transform of 3 device fields (dns_transform_c2r), with the
+        1/(Nx Ny Nz) factor."""
+        p, dev = _ptr(spec, self.spec_shape, self._rb, True)
+        q, dev2 = _ptr(out, self.phys_shape, self._rb, False)
+        if not (dev and dev2):
+            raise ValueError("transform_c2r takes device arrays")
+        _lib.check(_lib.lib().dns_transform_c2r(self._h, p, q), "dns_transform_c2r")
+        return out
+
     def diagnostics(self, check_finite: bool = True) -> dict:
         d = _lib.dns_diag()
         rc = _lib.lib().dns_diagnostics(self._h, ctypes.byref(d))

@@ -257,3 +257,40 @@ def test_rk4_run_on_1024x512x256_keeps_the_energy_budget():
     dEdt = (d[2]["energy"] - d[0]["energy"]) / (d[2]["t"] - d[0]["t"])
     assert abs(-dEdt - d[1]["dissipation"]) < 1e-3 * d[1]["dissipation"]
     assert max(x["max_div"] for x in d) < 1e-4
+
+
+@pytest.mark.parametrize("dtype,bound", [("f64", 1e-12), ("f32", 1e-5)])
+def test_forced_rhs_on_other_counts_matches_oracle(dtype, bound):
+    from oracle import sgs_mlp
+
+    shape, nu = (24, 48, 16), 0.01
+    uh = _field(shape, 13, dtype)
+    rng = np.random.default_rng(3)
+    fh = sn.to_spectral(rng.standard_normal((3,) + shape)).astype(CPLX[dtype]) * 1e-3
+    with Solver(shape, nu, 1e-3, dtype) as s:
+        s.set_state_spectral(uh)
+        s.set_forcing(fh)
+        got = s.rhs()
+        s.set_forcing(None)
+        unforced = s.rhs()
+    g = sn.Grid(shape)
+    ref = sgs_mlp.rhs_forced(uh.astype(np.complex128), g, nu, fh.astype(np.complex128))
+    assert rel_l2(got, ref) <= bound
+    assert rel_l2(unforced, sn.rhs(uh.astype(np.complex128), g, nu)) <= bound
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_device_transforms_on_other_counts(dtype):
+    shape = (32, 16, 24)
+    rng = np.random.default_rng(9)
+    u = rng.standard_normal((3,) + shape)
+    rdt = torch.float32 if dtype == "f32" else torch.float64
+    cdt = torch.complex64 if dtype == "f32" else torch.complex128
+    tol = 1e-6 if dtype == "f32" else 1e-13
+    with Solver(shape, 0.01, 1e-3, dtype) as s:
+        ud = torch.from_numpy(u).to(rdt).cuda()
+        spec = s.transform_r2c(ud, torch.empty((3, 32, 16, 13), dtype=cdt, device="cuda"))
+        ref = sn.to_spectral(u)
+        assert rel_l2(spec.cpu().numpy(), ref) <= tol
+        back = s.transform_c2r(spec, torch.empty_like(ud))
+        assert rel_l2(back.cpu().numpy(), sn.inverse(ref)) <= tol
