@@ -550,9 +550,10 @@ def combine_replicas(ms_local, steps, points, dist=None, device="cpu"):
     return ms_max, world * points * steps / (ms_max * 1e-3)
 
 
-def step_traffic(N, dtype):
-    """DRAM bytes per RK4 step from the per-launch ncu traffic (4 launches of each kernel), or None."""
-    parts = [ncu_traffic(k, N, dtype) for k in ("z_pass", "plane_pass")]
+def step_traffic(N, dtype, classes):
+    """DRAM bytes per RK4 step from the per-launch ncu traffic of the schedule's kernel classes
+    (each launched once per stage, 4 stages), or None."""
+    parts = [ncu_traffic(k, N, dtype) for k in classes]
     return None if any(p is None for p in parts) else 4.0 * sum(parts)
 
 
@@ -633,8 +634,8 @@ def run_ours(args):
                           # the 3-pass model (x, y and z transforms each a separate HBM sweep, 204 cv
                           # per step): what the plane blocking of the 132-cv model would buy
                           "frac_of_measured_3pass_model": 204.0 * cvb / (ms_step * 1e-3) / 1e9 / peak,
-                          # DRAM bytes the four passes move per step (ncu, profiles/)
-                          "dram_bytes_per_step_measured": step_traffic(N, dtype)},
+                          # DRAM bytes the schedule's passes move per step (ncu, profiles/)
+                          "dram_bytes_per_step_measured": step_traffic(N, dtype, list(prof))},
         "kernels": kernels,
         "clocks": clocks,
     }
