@@ -1533,11 +1533,11 @@ int dns_ensemble_step(dns_ensemble* e, int n) {
 
 int dns_ensemble_tune(dns_ensemble* e, int* best_streams) {
   if (!e) return fail(DNS_ERR_ARG, "dns_ensemble_tune: ensemble is NULL");
-  // y- and z-pass tile widths per size class: tuned on one member (its state is
-  // kept), applied to every member of the class
+  // schedule, radix plans and y- and z-pass tile widths per size class: tuned on one
+  // member (its state is kept), applied to every member of the class
   int rc = DNS_OK;
   std::vector<const DnsOps*> done_ops;
-  std::vector<std::array<int, 4>> done_tiles;  // y-inverse, y-forward, z widths, radix plan
+  std::vector<std::array<int, 5>> done_tiles;  // y-inverse, y-forward, z widths, radix plan, schedule
   for (dns_handle* h : e->m) {
     size_t k = 0;
     while (k < done_ops.size() && done_ops[k] != h->ops) ++k;
@@ -1545,13 +1545,14 @@ int dns_ensemble_tune(dns_ensemble* e, int* best_streams) {
       int ti = 0, tf = 0, tz = 0;
       if ((rc = dns_tune_tiles(h, 5, &ti, &tf, &tz))) return rc;
       done_ops.push_back(h->ops);
-      done_tiles.push_back({ti, tf, tz, h->plan});
+      done_tiles.push_back({ti, tf, tz, h->plan, h->fused});
     } else if (h->ytile[0] != done_tiles[k][0] || h->ytile[1] != done_tiles[k][1] || h->ztile != done_tiles[k][2] ||
-               h->plan != done_tiles[k][3]) {
+               h->plan != done_tiles[k][3] || h->fused != done_tiles[k][4]) {
       h->ytile[0] = done_tiles[k][0];
       h->ytile[1] = done_tiles[k][1];
       h->ztile = done_tiles[k][2];
       h->plan = done_tiles[k][3];
+      h->fused = done_tiles[k][4];
       h->graph_dirty = true;
       ++h->epoch;
       h->w_valid = false;
