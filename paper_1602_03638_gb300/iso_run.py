@@ -6,6 +6,9 @@ diagnostics every `every` steps and, at the end, the relative L2 distance betwee
 final spectral states (the error of the FP32 form against the FP64 form).
 
     python -m paper_1602_03638_gb300.iso_run --N 1024 --steps 200 --every 20 > iso1024.json
+    python -m paper_1602_03638_gb300.iso_run --shape 1024,512,256 --steps 200 > box.json
+
+(--shape: a compiled grid with other point counts per direction, Nx,Ny,Nz.)
 
 The two runs are sequential (the FP64 state of a 1024^3 run holds 137 GB of device memory);
 the FP64 final state is kept on the device for the comparison.
@@ -61,7 +64,7 @@ def _run_one(N, nu, dt, steps, every, dtype, seed, k0):
 
 
 def rel_l2(a: torch.Tensor, b: torch.Tensor, slab: int = 64) -> float:
-    """||a - b|| / ||b|| over complex spectral arrays (3, N, N, N/2+1), in FP64, by slabs of kx."""
+    """||a - b|| / ||b|| over complex spectral arrays (3, Nx, Ny, Nz/2+1), in FP64, by slabs of kx."""
     num = den = 0.0
     for c in range(a.shape[0]):
         for i in range(0, a.shape[1], slab):
@@ -72,9 +75,11 @@ def rel_l2(a: torch.Tensor, b: torch.Tensor, slab: int = 64) -> float:
     return (num / den) ** 0.5
 
 
-def run(N: int = 1024, steps: int = 200, every: int = 20, nu: float = 1e-3, dt: float = 5e-4, seed: int = 0,
+def run(N=1024, steps: int = 200, every: int = 20, nu: float = 1e-3, dt: float = 5e-4, seed: int = 0,
         k0: float = 4.0, forms=("f64", "f32")) -> dict:
-    out = {"N": N, "nu": nu, "dt": dt, "steps": steps, "seed": seed, "k0": k0, "runs": {}}
+    """N: one point count or (Nx, Ny, Nz)."""
+    out = {"N": N if isinstance(N, int) else list(N), "nu": nu, "dt": dt, "steps": steps, "seed": seed, "k0": k0,
+           "runs": {}}
     finals = {}
     for dtype in forms:
         r, final = _run_one(N, nu, dt, steps, every, dtype, seed, k0)
@@ -94,6 +99,7 @@ def run(N: int = 1024, steps: int = 200, every: int = 20, nu: float = 1e-3, dt: 
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--N", type=int, default=1024)
+    ap.add_argument("--shape", default=None, help="Nx,Ny,Nz of a compiled grid with other counts per direction")
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--every", type=int, default=20)
     ap.add_argument("--nu", type=float, default=1e-3)
@@ -102,7 +108,8 @@ def main(argv=None) -> int:
     ap.add_argument("--k0", type=float, default=4.0)
     ap.add_argument("--forms", default="f64,f32")
     a = ap.parse_args(argv)
-    json.dump(run(a.N, a.steps, a.every, a.nu, a.dt, a.seed, a.k0, tuple(a.forms.split(","))), sys.stdout)
+    N = tuple(int(v) for v in a.shape.split(",")) if a.shape else a.N
+    json.dump(run(N, a.steps, a.every, a.nu, a.dt, a.seed, a.k0, tuple(a.forms.split(","))), sys.stdout)
     print()
     return 0
 
