@@ -58,10 +58,12 @@ CPU_N, CPU_STEPS = 128, 8
 PAPER_TG512_PTS_STEPS_PER_S = 6.2e7  # Sec. 4 verification run, 2048 Shaheen cores (context)
 
 
-def pass_bytes(N, real_bytes, stages=4):
+def pass_bytes(N, real_bytes, stages=4, rows=False):
     """Algorithmic bytes per launch of each kernel class (mean over the RK4 stages).
     N: one point count, or (Nx, Ny, Nz) for a grid with other counts per direction (then
     FV = Nx Ny (Nz/2), kc = (Nz+2)//3 planes and the rows |ky| < Ny/3 of Ny).
+    rows: the state vanishes on every row (kz, ky) outside the 2/3 box (the solver's row
+    flag), so the passes skip those rows (below).
 
     Counted from the 2/3 mask: a field-volume FV = N^2 (N/2) complex values (the stored half
     spectrum; the kz = N/2 plane is identically zero); kc = (N+2)//3 planes kz < N/3 and
@@ -74,6 +76,11 @@ def pass_bytes(N, real_bytes, stages=4):
                  R 3 (kc/M) FV (products) + RK state + W 6 FV (u and omega, y-inverted)
     RK state per stage: stage 0 reads u (3) and writes u1, us (6); a middle stage reads us,
     u1, u (9) and writes u1, us (6); the last reads us, u1 (6) and writes u (3).
+    With rows (a fraction zk yk of the rows kept):
+      y_inverse  R 6 zk yk FV (kept rows of the planes kz < N/3) + W 6 zk FV (those planes)
+      z_pass     R 6 zk FV + W 3 zk FV
+      y_forward  as above
+      x_stage    (R 3 + RK state + W 6) zk yk FV (kept rows only)
     """
     nx, ny, nz = (N,) * 3 if isinstance(N, int) else tuple(N)
     M = nz // 2
@@ -93,8 +100,25 @@ def pass_bytes(N, real_bytes, stages=4):
             r, w = 6, 3
         rk.append(r + w)
     rk_mean = sum(rk) / len(rk)
+    if rows:
+        return {"y_inverse": 6.0 * zk * (yk + 1.0) * fv, "z_pass": 9.0 * zk * fv,
+                "y_forward": (3.0 * zk + 3.0 * zk * yk) * fv, "x_stage": (3.0 + rk_mean + 6.0) * zk * yk * fv}
     return {"y_inverse": 12.0 * fv, "z_pass": (6.0 + 3.0 * zk) * fv, "y_forward": (3.0 * zk + 3.0 * zk * yk) * fv,
             "x_stage": (3.0 * zk * yk + rk_mean + 6.0) * fv, "plane_pass": (3.0 * zk + rk_mean + 6.0) * fv}
+
+
+def truncated_step_cv(N):
+    """The 2-pass step model (STEP_CV) for a state that vanishes outside the 2/3 box, in cv:
+    per stage the xy inverse reads the state's box modes (3 b3) and writes the planes kz < N/3
+    (6 zk), the z-pass reads those (6 zk) and writes the products there (3 zk), the xy forward
+    reads them (3 zk), the viscous term reads the box modes (3 b3); the RK traffic (36 cv) only
+    touches the box modes (b3 = the box's share of the half spectrum)."""
+    M = N // 2
+    kc = (N + 2) // 3
+    zk = kc / (M + 1)
+    yk = (2 * kc - 1) / N
+    b3 = zk * yk * yk
+    return 4.0 * (6.0 * b3 + 18.0 * zk) + 36.0 * b3
 
 
 def cv_bytes(N, real_bytes):
@@ -193,7 +217,7 @@ def oracle_sample(N, steps, nu, dt):
     from oracle import spectral_ns as sn
     from paper_1602_03638_gb300 import inputs
 
-    uh = sn.to_spectral(inputs.taylor_green(N))
+    uh = inputs.taylor_green_spectral(N).numpy()
     g = sn.Grid(N)
     t0 = time.perf_counter()
     for _ in range(steps):
@@ -209,7 +233,7 @@ def run_reference(args):
     from paper_1602_03638_gb300 import inputs
 
     N = CPU_N
-    uh = sn.to_spectral(inputs.taylor_green(N))
+    uh = inputs.taylor_green_spectral(N).numpy()
     g = sn.Grid(N)
     for _ in range(args.warmup):
         uh = sn.rk4_step(uh, g, NU, DT)
@@ -258,13 +282,11 @@ def time_steps(torch, s, st, steps):
 
 
 def run_form(torch, Solver, inputs, N, dtype, warm, steps):
-    td = torch.float32 if dtype == "f32" else torch.float64
+    cdt = torch.complex64 if dtype == "f32" else torch.complex128
     with Solver(N, NU, DT, dtype) as s:
         st = torch.cuda.current_stream()
         s.set_stream(st)
-        u = inputs.taylor_green_torch(N, device="cuda", dtype=td)
-        s.set_state(u)
-        del u
+        s.set_state_spectral(inputs.taylor_green_spectral(N, device="cuda", dtype=cdt))
         for _ in range(warm):
             s.step(1)
         torch.cuda.synchronize()
@@ -272,7 +294,8 @@ def run_form(torch, Solver, inputs, N, dtype, warm, steps):
     rb = 4 if dtype == "f32" else 8
     model_ms = STEP_CV * cv_bytes(N, rb) / (measured_peaks()[0] * 1e9) * 1e3
     out = {"N": N, "dtype": dtype, "ms_per_step": ms, "value": N ** 3 / (ms * 1e-3), "steps": steps,
-           "hbm_roofline_frac_of_measured": model_ms / ms}
+           "hbm_roofline_frac_of_measured": model_ms / ms,
+           "truncated_state_roofline_frac_of_measured": model_ms * truncated_step_cv(N) / STEP_CV / ms}
     if dtype == "f64":
         # FP64 arithmetic bound: ~270 N^3 log2 N flops per RK4 step (36 scalar 3D transforms,
         # radix-2 count) against the FP64 FMA rate measured on this GPU (dns_measure_fp64_peak)
@@ -309,9 +332,7 @@ def run_plane_schedule(torch, Solver, inputs, N=N_MAIN, warm=3, steps=10):
         s.set_option("fused_planes", 1)
         st = torch.cuda.current_stream()
         s.set_stream(st)
-        u = inputs.taylor_green_torch(N, device="cuda", dtype=torch.float32)
-        s.set_state(u)
-        del u
+        s.set_state_spectral(inputs.taylor_green_spectral(N, device="cuda", dtype=torch.complex64))
         for _ in range(warm):
             s.step(1)
         torch.cuda.synchronize()
@@ -347,7 +368,7 @@ def run_grids(torch, Solver, inputs, shape=(1024, 512, 256), warm=3, steps=10):
                     "hbm_roofline_frac_of_measured": STEP_CV * cv_bytes(shape, rb) / (peak * 1e9) / (ms * 1e-3)}
             if dtype == "f32":
                 prof = s.profile_steps(n)
-                kb = pass_bytes(shape, rb)
+                kb = pass_bytes(shape, rb, rows=s.get_option("rows_vanish") == 1.0)
                 form["kernels"] = {k: {"ms_per_launch": t / c, "launches": c,
                                        "achieved_gbs": kb[k] / (t / c * 1e-3) / 1e9,
                                        "frac_of_peak": kb[k] / (t / c * 1e-3) / 1e9 / peak}
@@ -366,9 +387,7 @@ def run_integrators(torch, Solver, inputs, N=512, warm=3, steps=10):
         with Solver(N, NU, DT, "f32", integrator=scheme) as s:
             st = torch.cuda.current_stream()
             s.set_stream(st)
-            u = inputs.taylor_green_torch(N, device="cuda", dtype=torch.float32)
-            s.set_state(u)
-            del u
+            s.set_state_spectral(inputs.taylor_green_spectral(N, device="cuda", dtype=torch.complex64))
             for _ in range(warm):
                 s.step(1)
             torch.cuda.synchronize()
@@ -584,9 +603,12 @@ def run_ours(args):
         s.set_option("fused_planes", 1 if args.schedule == "plane" else 0)
     st = torch.cuda.current_stream()
     s.set_stream(st)
-    u = inputs.taylor_green_torch(N, device="cuda", dtype=torch.float32)
-    s.set_state(u)
-    del u
+    # the Taylor-Green vortex from its exact Fourier coefficients: the state vanishes outside
+    # the 2/3 box, so the passes skip those rows (set from FP32 mesh values, the forward
+    # transform would leave rounding residue there and the full transforms would run)
+    s.set_state_spectral(inputs.taylor_green_spectral(N, device="cuda", dtype=torch.complex64))
+    rows = s.get_option("rows_vanish") == 1.0 and s.get_option("prune_rows") == 1.0 and \
+        s.get_option("fused_planes") == 0.0
     for _ in range(args.warmup):
         s.step(1)
     torch.cuda.synchronize()
@@ -605,11 +627,24 @@ def run_ours(args):
     dom = max(prof, key=lambda k: prof[k][0])
     dom_ms = prof[dom][0] / prof[dom][1]
     cvb = cv_bytes(N, 4)
-    kb = pass_bytes(N, 4)
+    kb = pass_bytes(N, 4, rows=rows)
     achieved = kb[dom] / (dom_ms * 1e-3) / 1e9
     kernels = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1], "share": v[0] / sum(x[0] for x in prof.values()),
                    "algorithmic_bytes_per_launch": kb[k],
                    "algorithmic_GBps": kb[k] / (v[0] / v[1] * 1e-3) / 1e9} for k, v in prof.items()}
+    full = None
+    if rows and not args.no_extras:
+        # the same workload with the full transforms (option prune_rows = 0): same results
+        s.set_option("prune_rows", 0)
+        s.step(2)
+        torch.cuda.synchronize()
+        fms = time_steps(torch, s, st, args.steps) / args.steps
+        fprof = s.profile_steps(max(1, args.steps // 2))
+        fkb = pass_bytes(N, 4)
+        full = {"ms_per_step": fms, "value": N ** 3 / (fms * 1e-3),
+                "step_roofline_frac_of_measured": STEP_CV * cvb / (fms * 1e-3) / 1e9 / peak,
+                "kernels": {k: {"ms_per_launch": v[0] / v[1], "algorithmic_bytes_per_launch": fkb[k],
+                                "algorithmic_GBps": fkb[k] / (v[0] / v[1] * 1e-3) / 1e9} for k, v in fprof.items()}}
     s.close()
 
     if rank != 0:
@@ -622,7 +657,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": value / PAPER_TG512_PTS_STEPS_PER_S, "dtype": "f32",
-        "data": "synthetic (Taylor-Green initial condition on device)", "config": main_config(world, N),
+        "data": "synthetic (Taylor-Green initial condition from its exact Fourier coefficients, on device)",
+        "config": main_config(world, N),
         "gpu_launches": 4 * len(prof) * args.steps,  # kernels per RK4 stage x 4 stages x steps
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind,
@@ -634,33 +670,43 @@ def run_ours(args):
                           # the 3-pass model (x, y and z transforms each a separate HBM sweep, 204 cv
                           # per step): what the plane blocking of the 132-cv model would buy
                           "frac_of_measured_3pass_model": 204.0 * cvb / (ms_step * 1e-3) / 1e9 / peak,
+                          # the same 2-pass model for a state that vanishes outside the 2/3 box
+                          # (the one this workload has): the minimum the pruned passes could reach
+                          "truncated_state_model_bytes_per_step": truncated_step_cv(N) * cvb,
+                          "frac_of_measured_truncated_state_model":
+                              truncated_step_cv(N) * cvb / (ms_step * 1e-3) / 1e9 / peak,
+                          "rows_pruned": rows,
                           # DRAM bytes the schedule's passes move per step (ncu, profiles/)
                           "dram_bytes_per_step_measured": step_traffic(N, dtype, list(prof))},
         "kernels": kernels,
         "clocks": clocks,
     }
+    if full is not None:
+        line["full_transforms"] = full
 
     if not args.no_extras:
         # end to end through the public API with pinned host buffers
         with Solver(N, NU, DT, dtype) as s2:
-            host_u = torch.from_numpy(inputs.taylor_green(N, dtype=np.float32)).pin_memory()
-            out_u = torch.empty_like(host_u).pin_memory()
-            s2.set_state(host_u)
+            host_uh = inputs.taylor_green_spectral(N, dtype=torch.complex64).pin_memory()
+            out_u = torch.empty((3, N, N, N), dtype=torch.float32).pin_memory()
+            s2.set_state_spectral(host_uh)
             s2.step(1)
             s2.diagnostics()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            s2.set_state(host_u)
+            s2.set_state_spectral(host_uh)
             for _ in range(args.steps):
                 s2.step(1)
                 d = s2.diagnostics()
             s2.get_state(out_u)
             e2e_s = time.perf_counter() - t0
-            ph = 3 * N ** 3 * 4
+            sh, ph = host_uh.numel() * 8, 3 * N ** 3 * 4
             line["e2e"] = {"value": N ** 3 * args.steps / e2e_s, "unit": UNIT,
-                           "h2d_bytes_per_step": ph / args.steps,
+                           "h2d_bytes_per_step": sh / args.steps,
                            "d2h_bytes_per_step": (ph + args.steps * 5 * 8) / args.steps,
-                           "final_energy": d["energy"]}
+                           "final_energy": d["energy"],
+                           "what": "upload of the spectral state (pinned), K steps with a diagnostics read-back "
+                                   "each, download of the physical state (pinned)"}
         # precision forms
         forms = [run_form(torch, Solver, inputs, 512, "f64", 2, 3), run_form(torch, Solver, inputs, 1024, "f32", 2, 3),
                  run_form(torch, Solver, inputs, 1024, "f64", 1, 2),
@@ -670,7 +716,8 @@ def run_ours(args):
         errs = {}
         for dt_ in ("f32", "f64"):
             with Solver(CPU_N, NU, DT, dt_) as s3:
-                s3.set_state(inputs.taylor_green(CPU_N, dtype=np.float32 if dt_ == "f32" else np.float64))
+                s3.set_state_spectral(inputs.taylor_green_spectral(CPU_N).numpy().astype(
+                    np.complex64 if dt_ == "f32" else np.complex128))
                 s3.step(CPU_STEPS)
                 got = s3.get_state_spectral()
             errs[dt_] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))

@@ -55,6 +55,23 @@ __global__ void k_diag_final(double* partials, int nblocks) {
   }
 }
 
+// *flag = 1 if a row (kz, ky) of the state U (3 fields of M x Ny rows of Nx values, internal
+// layout) outside the 2/3 box (3 kz >= k3z or 3 |ky| >= k3y) holds a nonzero value (NaN
+// counts as nonzero, -0 as zero); *flag is left unchanged otherwise (cleared by the caller).
+template <typename T>
+__global__ void k_rows_outside(const cx<T>* __restrict__ U, int Nx, int Ny, int M, int k3y, int k3z, int* flag) {
+  const size_t rows = (size_t)3 * M * Ny;
+  for (size_t r = blockIdx.x; r < rows; r += gridDim.x) {
+    const int ky = (int)(r % Ny), kz = (int)((r / Ny) % M);
+    const int kf = ky < Ny / 2 ? ky : ky - Ny;
+    if (3 * kz < k3z && 3 * (kf < 0 ? -kf : kf) < k3y) continue;  // inside: the same for the whole block
+    const cx<T>* p = U + r * Nx;
+    int nz = 0;
+    for (int j = threadIdx.x; j < Nx; j += blockDim.x) nz |= (p[j].x != (T)0) | (p[j].y != (T)0);
+    if (__syncthreads_or(nz) && threadIdx.x == 0) atomicOr(flag, 1);
+  }
+}
+
 // Paper order P[c][kx][ky][kz'] (kz' <= Nz/2)  <->  internal O[c][kz][ky][kx] (kz < Nz/2).
 // grid = (ceil(Nx/32), ceil(kzcount/32), 3*Ny), block = (32, 8)
 template <typename T>
@@ -263,6 +280,7 @@ struct dns_handle {
   size_t bytes = 0;
   size_t fs = 0;  // complex values per field
   bool w_valid = false;
+  int prune_rows = 1;  // option "prune_rows": skip the rows outside the 2/3 box where the state vanishes
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   bool graph_dirty = true;
@@ -304,6 +322,9 @@ void release(dns_handle* h) {
   if (h->own_stream) cudaStreamDestroy(h->own_stream);
 }
 
+// The row flag (PassArgs::rows) in the diagnostics block past the results and max|div|.
+int* row_flag(const dns_handle* h) { return reinterpret_cast<int*>(h->diag + DIAG_BLOCKS * 4 + 6); }
+
 PassArgs base_args(const dns_handle* h) {
   PassArgs a;
   a.U = h->U;
@@ -326,7 +347,25 @@ PassArgs base_args(const dns_handle* h) {
   a.plane_lag = h->plane_lag;
   a.partials = h->diag;
   a.maxbits = reinterpret_cast<unsigned long long*>(h->diag + DIAG_BLOCKS * 4 + 4);
+  // the row flag: the four-pass stages only (the plane pass reads every row)
+  const bool plane = h->fused && h->ops->rk_stage_fused && h->ctl;
+  if (h->prune_rows && !plane) a.rows = row_flag(h);
   return a;
+}
+
+// Sets the row flag from the state now in U (on the handle's stream): 0 if U vanishes on
+// every row (kz, ky) outside the handle's 2/3 box, else 1.
+cudaError_t check_rows(dns_handle* h) {
+  int* flag = row_flag(h);
+  cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), h->stream);
+  if (e != cudaSuccess) return e;
+  const int k3y = h->Ny + 2 * h->variant, k3z = h->Nz + 2 * h->variant;
+  const int M = h->Nz / 2, blocks = 1024;
+  if (h->dtype == DNS_F32)
+    k_rows_outside<float><<<blocks, 256, 0, h->stream>>>((const cx<float>*)h->U, h->N, h->Ny, M, k3y, k3z, flag);
+  else
+    k_rows_outside<double><<<blocks, 256, 0, h->stream>>>((const cx<double>*)h->U, h->N, h->Ny, M, k3y, k3z, flag);
+  return cudaGetLastError();
 }
 
 int rk_stages(const dns_handle* h) { return h->rk.stages; }
@@ -542,6 +581,7 @@ int dns_create3(int Nx, int Ny, int Nz, double nu, double dt, int dtype, dns_han
       ce = cudaMemcpy(h->tw, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice);
     }
     if (ce == cudaSuccess) ce = cudaMemset(h->U, 0, 3 * h->fs * cb);
+    if (ce == cudaSuccess) ce = cudaMemset(row_flag(h), 0, sizeof(int));  // the zero state vanishes everywhere
     if (ce != cudaSuccess) rc = cuda_fail(ce, "dns_create initialisation");
   }
   if (rc != DNS_OK) {
@@ -578,6 +618,11 @@ int dns_set_option(dns_handle* h, const char* key, double value) {
   if (!strcmp(key, "dealias_variant")) {
     if (value != 0.0 && value != 1.0) return fail(DNS_ERR_ARG, "dealias_variant must be 0 or 1");
     h->variant = (int)value;
+    if ((rc = use_device(h))) return rc;
+    DNS_CUDA(check_rows(h), "dealias_variant row check");  // the box changed
+  } else if (!strcmp(key, "prune_rows")) {
+    if (value != 0.0 && value != 1.0) return fail(DNS_ERR_ARG, "prune_rows must be 0 or 1");
+    h->prune_rows = (int)value;
   } else if (!strcmp(key, "integrator")) {
     if (!(value >= 0.0 && value < RK_BUILTIN) || value != std::floor(value))
       return fail(DNS_ERR_ARG,
@@ -658,7 +703,14 @@ int dns_get_option(const dns_handle* h, const char* key, double* value) {
   else if (!strcmp(key, "Nx")) *value = h->N;
   else if (!strcmp(key, "Ny")) *value = h->Ny;
   else if (!strcmp(key, "Nz")) *value = h->Nz;
-  else return fail(DNS_ERR_ARG, "dns_get_option: unknown key '%s'", key);
+  else if (!strcmp(key, "prune_rows")) *value = h->prune_rows;
+  else if (!strcmp(key, "rows_vanish")) {  // the row flag (synchronises the handle's stream)
+    int f = 1;
+    if ((rc = use_device(h))) return rc;
+    DNS_CUDA(cudaMemcpyAsync(&f, row_flag(h), sizeof(int), cudaMemcpyDeviceToHost, h->stream), "rows_vanish");
+    DNS_CUDA(cudaStreamSynchronize(h->stream), "rows_vanish");
+    *value = f == 0 ? 1.0 : 0.0;
+  } else return fail(DNS_ERR_ARG, "dns_get_option: unknown key '%s'", key);
   return DNS_OK;
 }
 
@@ -948,6 +1000,7 @@ int dns_set_state(dns_handle* h, const void* u, int on_device) {
     a.in = h->W;
   }
   DNS_CUDA(h->ops->forward3d(a, h->stream), "dns_set_state transform");
+  DNS_CUDA(check_rows(h), "dns_set_state row check");
   h->w_valid = false;
   h->t = 0.0;
   return DNS_OK;
@@ -967,6 +1020,7 @@ int dns_set_state_spectral(dns_handle* h, const void* uhat, int on_device) {
     src = h->W;
   }
   DNS_CUDA(launch_transpose(h, src, h->U, true), "dns_set_state_spectral transpose");
+  DNS_CUDA(check_rows(h), "dns_set_state_spectral row check");
   h->w_valid = false;
   h->t = 0.0;
   return DNS_OK;

@@ -45,6 +45,13 @@ struct PassArgs {
   int ytile[2] = {0, 0};  // y-pass tile widths of the stage launches (inverse, forward); 0 = default
   int ztile = 0;          // z-pass tile width of the stage launches; 0 = default
   int plan = 0;           // radix plan variant per pass of the stage launches: bit PLAN_* set = AltPlan
+  // Row flag of the state (nullptr: not used). *rows == 0 when the state vanishes on every
+  // row (kz, ky) outside the 2/3 box; the RK stage keeps those rows zero (no nonlinear term
+  // there, the viscous term is proportional to u_hat), so the stage's passes skip them: the
+  // x-stage and x inverse leave their rows unwritten, the y-inverse transforms only the
+  // planes kz < kc and reads the rows outside the box as zeros, the z-pass reads only
+  // kz < kc. The results are those of the full transforms (the skipped terms are zeros).
+  const int* rows = nullptr;
   const void* in = nullptr;  // physical input (3,Nx,Ny,Nz) for set_state
   void* out = nullptr;       // physical output (3,Nx,Ny,Nz) / RHS output
   int* ctl = nullptr;  // plane-pass control block (error flag, queue head, per-plane counters)

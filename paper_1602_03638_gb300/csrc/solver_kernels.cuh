@@ -115,6 +115,8 @@ __device__ __forceinline__ T par(double d, float f) {
   else return d;
 }
 __device__ __forceinline__ bool kept(int k, int kmax3) { return 3 * (k < 0 ? -k : k) < kmax3; }
+// The state vanishes on every row (kz, ky) outside the 2/3 box (PassArgs::rows).
+__device__ __forceinline__ bool rows_vanish(const int* rows) { return rows != nullptr && __ldg(rows) == 0; }
 
 // XM_STAGE2N: the stage update of Williamson's 2N low-storage form (a mode of its
 // own, so that the two-register stage update compiles without its branch)
@@ -204,12 +206,17 @@ __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
   // wavenumbers of the row and of column j: integer index times 2 pi / L (1 on the 2 pi box)
   const T ksx = par<T>(a.ks[0], a.f_ks[0]);
   const T kzv = (T)kz * par<T>(a.ks[2], a.f_ks[2]), kyv = (T)kfreq(ky, NY) * par<T>(a.ks[1], a.f_ks[1]);
+  // rows outside the 2/3 box carry no nonlinear term (each direction's cut-off from its
+  // own point count); where the state vanishes on them, the stage leaves them zero and
+  // neither the update nor the x inverse has anything to do there
+  const int k3y = NY == N ? a.kmax3 : a.kmax3y, k3z = NZ == N ? a.kmax3 : a.kmax3z;
+  const bool row_kept = (3 * kz < k3z) && kept(kfreq(ky, NY), k3y);
+  if constexpr (STAGE || MODE == XM_INV_CURL) {
+    if (!row_kept && rows_vanish(a.rows)) return;
+  }
 
   if constexpr (STAGE || MODE == XM_RHS) {
-    // rows outside the 2/3 box carry no nonlinear term: skip their transform
-    // (each direction's cut-off from its own point count)
-    const int k3y = NY == N ? a.kmax3 : a.kmax3y, k3z = NZ == N ? a.kmax3 : a.kmax3z;
-    const bool row_kept = (3 * kz < k3z) && kept(kfreq(ky, NY), k3y);
+    // rows outside the box: skip their forward transform
     const T nu = par<T>(a.nu, a.f_nu), cA = par<T>(a.cA, a.f_cA), cB = par<T>(a.cB, a.f_cB);
     const int stage = a.stage, last = a.last;
     // Williamson 2N stages keep the stage state in U (updated in place) and dU in U1
@@ -456,10 +463,30 @@ __device__ __forceinline__ int ywalk_row(int r) {
   }
 }
 
+// Fill of a y tile (TX columns of L rows, row stride `stride` in global memory) whose rows
+// outside the 2/3 box are zeros: the kept rows |ky| <= R (R = (kmax3 - 1) / 3, rows 0 .. R
+// and L - R .. L - 1) by cp.async, the rows R + 1 .. L - R - 1 between them as zeros.
+template <typename T, int L, int TX, int LD, int NT>
+__device__ __forceinline__ void ytile_fill_kept(cx<T>* s, const cx<T>* __restrict__ base, int stride, int kmax3) {
+  int R = (kmax3 - 1) / 3;
+  if (R > L / 2 - 1) R = L / 2 - 1;
+  const int lo = R + 1, gap = L - 2 * R - 1;  // kept rows [0, lo) and [lo + gap, L)
+  for (int e = threadIdx.x; e < TX * (L - gap); e += NT) {
+    const int x = e % TX, r = e / TX, y = r < lo ? r : r + gap;
+    cp_async<sizeof(cx<T>)>(s + padp(y) * LD + x, base + (size_t)y * stride + x);
+  }
+  for (int e = threadIdx.x; e < TX * gap; e += NT) {
+    const int x = e % TX, y = lo + e / TX;
+    s[padp(y) * LD + x] = mk((T)0, (T)0);
+  }
+}
+
 // One y tile: TX adjacent columns starting at `base` (field, kz plane and first
 // column already applied), transformed along y in place. NT: threads of the block.
+// vanish (inverse only): the rows with |ky| >= N/3 are zeros, not read.
 template <typename T, int N, int INV, int PRUNE, int TXO, int NT, int V = 0>
-__device__ __forceinline__ void ypass_tile(cx<T>* __restrict__ base, const cx<T>* __restrict__ tw, int kmax3) {
+__device__ __forceinline__ void ypass_tile(cx<T>* __restrict__ base, const cx<T>* __restrict__ tw, int kmax3,
+                                           bool vanish = false) {
   using Y = YCfg<T, N, INV, TXO>;
   constexpr int TX = Y::TX;
   constexpr int LD = Y::LD;
@@ -468,10 +495,14 @@ __device__ __forceinline__ void ypass_tile(cx<T>* __restrict__ base, const cx<T>
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // the whole tile in flight at once (cp.async, no register staging); the
   // inverse's conjugation is applied when the first pass reads it
+  if (INV && vanish) {
+    ytile_fill_kept<T, N, TX, LD, NT>(s, base, N, kmax3);
+  } else {
 #pragma unroll 8
-  for (int e = threadIdx.x; e < TX * N; e += NT) {
-    const int x = e % TX, y = ywalk_row<T, TX, N>(e / TX);
-    cp_async<sizeof(cx<T>)>(s + padp(y) * LD + x, base + (size_t)y * N + x);
+    for (int e = threadIdx.x; e < TX * N; e += NT) {
+      const int x = e % TX, y = ywalk_row<T, TX, N>(e / TX);
+      cp_async<sizeof(cx<T>)>(s + padp(y) * LD + x, base + (size_t)y * N + x);
+    }
   }
   cp_async_commit();
   cp_async_wait<0>();
@@ -494,9 +525,12 @@ __device__ __forceinline__ void ypass_tile(cx<T>* __restrict__ base, const cx<T>
 
 // NY, NZ: points along y and z where they differ from N (N: the x extent, the
 // row stride of the tile's columns).
+// rows, kcz (inverse of a stage): where the state vanishes outside the 2/3 box
+// (rows_vanish), the planes kz >= kcz are left alone (zeros that the z-pass does not
+// read) and the rows with |ky| >= NY/3 (kmax3) are read as zeros.
 template <typename T, int N, int INV, int PRUNE, int TXO = 0, int NY = N, int NZ = N, int V = 0>
 __global__ void __launch_bounds__(YCfg<T, N, INV, TXO, NY>::THREADS, (YCfg<T, N, INV, TXO, NY>::MINB))
-    k_ypass(cx<T>* __restrict__ F, const cx<T>* __restrict__ tw, int kmax3) {
+    k_ypass(cx<T>* __restrict__ F, const cx<T>* __restrict__ tw, int kmax3, const int* rows, int kcz) {
   using G = Geometry<T, N, NY, NZ>;
   using Y = YCfg<T, N, INV, TXO, NY>;
   constexpr int TX = Y::TX;
@@ -505,13 +539,19 @@ __global__ void __launch_bounds__(YCfg<T, N, INV, TXO, NY>::THREADS, (YCfg<T, N,
   extern __shared__ unsigned char smraw[];
   cx<T>* s = reinterpret_cast<cx<T>*>(smraw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool vanish = INV && rows_vanish(rows);
+  if (vanish && (int)blockIdx.y >= kcz) return;
   cx<T>* base = F + blockIdx.z * G::FS + (size_t)blockIdx.y * NY * N + blockIdx.x * TX;
   // the whole tile in flight at once (cp.async, no register staging); the
   // inverse's conjugation is applied when the first pass reads it
+  if (vanish) {
+    ytile_fill_kept<T, NY, TX, LD, NT>(s, base, N, kmax3);
+  } else {
 #pragma unroll 8
-  for (int e = threadIdx.x; e < TX * NY; e += NT) {
-    const int x = e % TX, y = ywalk_row<T, TX, NY>(e / TX);
-    cp_async<sizeof(cx<T>)>(s + padp(y) * LD + x, base + (size_t)y * N + x);
+    for (int e = threadIdx.x; e < TX * NY; e += NT) {
+      const int x = e % TX, y = ywalk_row<T, TX, NY>(e / TX);
+      cp_async<sizeof(cx<T>)>(s + padp(y) * LD + x, base + (size_t)y * N + x);
+    }
   }
   cp_async_commit();
   cp_async_wait<0>();
@@ -540,9 +580,11 @@ __global__ void __launch_bounds__(YCfg<T, N, INV, TXO>::THREADS, (YCfg<T, N, INV
   using G = Geometry<T, N>;
   using Y = YCfg<T, N, INV, TXO>;
   const PassArgs& a = B.a[blockIdx.z / fields];
+  const bool vanish = INV && rows_vanish(a.rows);  // the member's planes kz >= kc are not transformed
+  if (vanish && 3 * (int)blockIdx.y >= a.kmax3) return;
   cx<T>* base = reinterpret_cast<cx<T>*>(a.W) + (blockIdx.z % fields) * G::FS + (size_t)blockIdx.y * N * N +
                 blockIdx.x * Y::TX;
-  ypass_tile<T, N, INV, PRUNE, TXO, Y::THREADS, V>(base, reinterpret_cast<const cx<T>*>(a.tw), a.kmax3);
+  ypass_tile<T, N, INV, PRUNE, TXO, Y::THREADS, V>(base, reinterpret_cast<const cx<T>*>(a.tw), a.kmax3, vanish);
 }
 
 // ---------------------------------------------------------------------------
@@ -583,9 +625,29 @@ __device__ __forceinline__ void zpass_body(const PassArgs a, const int bx, const
     __syncthreads();
   } else {
     const cx<T>* src = reinterpret_cast<const cx<T>*>(MODE == ZM_MAXABS ? a.D : a.W);
-    for (int e = threadIdx.x; e < NF * TX * M; e += ZP_THREADS) {
-      const int x = e % TX, k = (e / TX) % M, f = e / (TX * M);
-      cp_async<sizeof(cx<T>)>(s + padp(k) * LD + f * TX + x, src + f * FS + ((size_t)k * NY + y) * N + x0 + x);
+    // a stage whose state vanishes outside the 2/3 box: the planes kz >= kc hold zeros
+    // (the y-inverse left them alone) and are filled with zeros instead of read
+    int klim = M;
+    if constexpr (MODE == ZM_CROSS) {
+      if (rows_vanish(a.rows)) {
+        klim = ((NZ == N ? a.kmax3 : a.kmax3z) + 2) / 3;
+        if (klim > M) klim = M;
+      }
+    }
+    if (klim < M) {
+      for (int e = threadIdx.x; e < NF * TX * klim; e += ZP_THREADS) {
+        const int x = e % TX, k = (e / TX) % klim, f = e / (TX * klim);
+        cp_async<sizeof(cx<T>)>(s + padp(k) * LD + f * TX + x, src + f * FS + ((size_t)k * NY + y) * N + x0 + x);
+      }
+      for (int e = threadIdx.x; e < NF * TX * (M - klim); e += ZP_THREADS) {
+        const int x = e % TX, k = klim + (e / TX) % (M - klim), f = e / (TX * (M - klim));
+        s[padp(k) * LD + f * TX + x] = mk((T)0, (T)0);
+      }
+    } else {
+      for (int e = threadIdx.x; e < NF * TX * M; e += ZP_THREADS) {
+        const int x = e % TX, k = (e / TX) % M, f = e / (TX * M);
+        cp_async<sizeof(cx<T>)>(s + padp(k) * LD + f * TX + x, src + f * FS + ((size_t)k * NY + y) * N + x0 + x);
+      }
     }
     cp_async_commit();
     cp_async_wait<0>();
@@ -823,9 +885,17 @@ __global__ void __launch_bounds__(32 * ZCrossWarps<T, N>::value, (ZCrossWarps<T,
   const cx<T>* gl = W + ((size_t)(ZW::S * kq) * N + y) * N + x0 + tx;
   cx<T>* sl = s + (ZW::S * kq) * LD + tx;
 
-  for (int it = w; it < 6 * ZW::ITEMS; it += NW) {
-    const int f = it / ZW::ITEMS, r = it % ZW::ITEMS, g = r / ZW::S, c = r % ZW::S;
-    sl[(17 * g + c) * LD + f * TX] = gl[f * FS + (size_t)(16 * g + c) * N * N];
+  if (rows_vanish(a.rows)) {  // planes kz >= kc of a state that vanishes outside the 2/3 box: zeros
+    for (int it = w; it < 6 * ZW::ITEMS; it += NW) {
+      const int f = it / ZW::ITEMS, r = it % ZW::ITEMS, g = r / ZW::S, c = r % ZW::S;
+      sl[(17 * g + c) * LD + f * TX] =
+          16 * g + ZW::S * kq + c < kc ? gl[f * FS + (size_t)(16 * g + c) * N * N] : mk((T)0, (T)0);
+    }
+  } else {
+    for (int it = w; it < 6 * ZW::ITEMS; it += NW) {
+      const int f = it / ZW::ITEMS, r = it % ZW::ITEMS, g = r / ZW::S, c = r % ZW::S;
+      sl[(17 * g + c) * LD + f * TX] = gl[f * FS + (size_t)(16 * g + c) * N * N];
+    }
   }
   ZTw<T, N> zt;
   zt.load(tw, lane);
@@ -982,11 +1052,22 @@ __global__ void __launch_bounds__(32 * Z16P<T>::NW, 1) k_zcross16p(PassArgs a) {
   // base plus j times a constant stride.
   static_assert(TX == 16 && ITEMS == 128 && 3 * ITEMS == 16 * NW, "z tile chunking");
   auto fetch = [&](int t, int f0) {
+    // a stage whose state vanishes outside the 2/3 box: the planes kz >= kc hold zeros (the
+    // y-inverse left them alone) and are filled with zeros instead of read
     const int f = f0 + w / 8, g = w % 8;
     const cx<T>* gl = W + lane_g + (size_t)(t / XT) * N + (t % XT) * TX + (size_t)f * FS + (size_t)(32 * g) * N * N;
     cx<T>* sd = sl + 34 * g * LD + f * TX;
+    if (rows_vanish(a.rows)) {
+      const int nv = kc - (32 * g + TX * kq);  // rows of this lane's chunk below kc
 #pragma unroll
-    for (int j = 0; j < 16; ++j) cp_async<sizeof(cx<T>)>(sd + j * LD, gl + (size_t)j * N * N);
+      for (int j = 0; j < 16; ++j) {
+        if (j < nv) cp_async<sizeof(cx<T>)>(sd + j * LD, gl + (size_t)j * N * N);
+        else sd[j * LD] = mk((T)0, (T)0);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) cp_async<sizeof(cx<T>)>(sd + j * LD, gl + (size_t)j * N * N);
+    }
   };
   // c2r of the TX lines of fields f0 .. f0+2, two lines per warp at a time
   HwTwL ht;
@@ -1243,12 +1324,24 @@ __global__ void __launch_bounds__(32 * Z32P<T>::NW, 1) k_zcross32p(PassArgs a) {
   // compile-time offsets
   static_assert(TX == 8 && ITEMS == 128 && 3 * ITEMS == 32 * NW, "z tile chunking");
   auto fetch = [&](int t, int f0) {
+    // planes kz >= kc of a stage whose state vanishes outside the 2/3 box: zeros, not read
     const int f = f0 + w / 4, q = w % 4;
     const cx<T>* gl = W + lane_g + (size_t)(t / XT) * N + (t % XT) * TX + (size_t)f * FS + (size_t)(128 * q) * N * N;
     cx<T>* sd = sl + 136 * q * LD + f * TX;
+    if (rows_vanish(a.rows)) {
+      const int nv = kc - (128 * q + TX * kq);  // this lane's rows below kc: 32 (j / 8) + j % 8 < nv
 #pragma unroll
-    for (int j = 0; j < 32; ++j)
-      cp_async<sizeof(cx<T>)>(sd + (34 * (j / 8) + j % 8) * LD, gl + (size_t)(32 * (j / 8) + j % 8) * N * N);
+      for (int j = 0; j < 32; ++j) {
+        if (32 * (j / 8) + j % 8 < nv)
+          cp_async<sizeof(cx<T>)>(sd + (34 * (j / 8) + j % 8) * LD, gl + (size_t)(32 * (j / 8) + j % 8) * N * N);
+        else
+          sd[(34 * (j / 8) + j % 8) * LD] = mk((T)0, (T)0);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        cp_async<sizeof(cx<T>)>(sd + (34 * (j / 8) + j % 8) * LD, gl + (size_t)(32 * (j / 8) + j % 8) * N * N);
+    }
   };
   HwTw32 ht;
   ht.init(tw, h);
@@ -1449,9 +1542,20 @@ __global__ void __launch_bounds__(32 * Z8Q<T>::NW, 2) k_zcross8q(PassArgs a) {
     const int f = w / 2, q = w % 2;
     const cx<T>* gf = gl + (size_t)f * FS + (size_t)(64 * q) * PL;
     cx<T>* sd = sl + 68 * q * LD + f * TX;
+    if (rows_vanish(a.rows)) {  // planes kz >= kc of a state that vanishes outside the 2/3 box: zeros
+      const int nv = kc - (64 * q + TX * kq);
 #pragma unroll
-    for (int j = 0; j < 32; ++j)
-      cp_async<sizeof(cx<T>)>(sd + (34 * (j / 16) + j % 16) * LD, gf + (size_t)(32 * (j / 16) + j % 16) * PL);
+      for (int j = 0; j < 32; ++j) {
+        if (32 * (j / 16) + j % 16 < nv)
+          cp_async<sizeof(cx<T>)>(sd + (34 * (j / 16) + j % 16) * LD, gf + (size_t)(32 * (j / 16) + j % 16) * PL);
+        else
+          sd[(34 * (j / 16) + j % 16) * LD] = mk((T)0, (T)0);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        cp_async<sizeof(cx<T>)>(sd + (34 * (j / 16) + j % 16) * LD, gf + (size_t)(32 * (j / 16) + j % 16) * PL);
+    }
   }
   cp_async_commit();
   HwTwL qt;  // w = exp(-2 pi i h / 128), tl = exp(-2 pi i h / 256)
@@ -1906,25 +2010,32 @@ struct SolverImpl {
     constexpr int TX = TXO > 0 ? TXO : G::ZTX;
     k_zpass<T, N, ZM_CROSS, TXO, NY, NZ, V><<<dim3(N / TX, NY), ZP_THREADS, G::zbytes(TX), st>>>(a);
   }
+  // rows, kcz: the row flag of a stage's y-inverse and its plane limit (k_ypass)
   template <int INV, int PRUNE, int TXO, int V = 0>
-  static void y_go(cx<T>* F, const cx<T>* tw, int kmax3, int planes, int fields, cudaStream_t st) {
+  static void y_go(cx<T>* F, const cx<T>* tw, int kmax3, int planes, int fields, cudaStream_t st,
+                   const int* rows = nullptr, int kcz = 0) {
     using Y = YCfg<T, N, INV, TXO, NY>;
-    k_ypass<T, N, INV, PRUNE, TXO, NY, NZ, V><<<dim3(N / Y::TX, planes, fields), Y::THREADS, Y::SMEM, st>>>(F, tw, kmax3);
+    k_ypass<T, N, INV, PRUNE, TXO, NY, NZ, V>
+        <<<dim3(N / Y::TX, planes, fields), Y::THREADS, Y::SMEM, st>>>(F, tw, kmax3, rows, kcz);
   }
   // the stage's y-pass with tile width `tile` (0, or a width not offered: the default) and
   // radix plan variant `plan`
   template <int INV, int PRUNE>
   static void y_stage(int tile, int plan, cx<T>* F, const cx<T>* tw, int kmax3, int planes, int fields,
-                      cudaStream_t st) {
+                      cudaStream_t st, const int* rows = nullptr, int kcz = 0) {
     with_plan(plan, [&](auto v) {
       constexpr int V = decltype(v)::value;
       if constexpr (ISO && N <= BATCH_MAX_N) {
-        if constexpr (ytile_ok(4)) if (tile == 4) return y_go<INV, PRUNE, 4, V>(F, tw, kmax3, planes, fields, st);
-        if constexpr (ytile_ok(8)) if (tile == 8) return y_go<INV, PRUNE, 8, V>(F, tw, kmax3, planes, fields, st);
-        if constexpr (ytile_ok(16)) if (tile == 16) return y_go<INV, PRUNE, 16, V>(F, tw, kmax3, planes, fields, st);
-        if constexpr (ytile_ok(32)) if (tile == 32) return y_go<INV, PRUNE, 32, V>(F, tw, kmax3, planes, fields, st);
+        if constexpr (ytile_ok(4))
+          if (tile == 4) return y_go<INV, PRUNE, 4, V>(F, tw, kmax3, planes, fields, st, rows, kcz);
+        if constexpr (ytile_ok(8))
+          if (tile == 8) return y_go<INV, PRUNE, 8, V>(F, tw, kmax3, planes, fields, st, rows, kcz);
+        if constexpr (ytile_ok(16))
+          if (tile == 16) return y_go<INV, PRUNE, 16, V>(F, tw, kmax3, planes, fields, st, rows, kcz);
+        if constexpr (ytile_ok(32))
+          if (tile == 32) return y_go<INV, PRUNE, 32, V>(F, tw, kmax3, planes, fields, st, rows, kcz);
       }
-      y_go<INV, PRUNE, 0, V>(F, tw, kmax3, planes, fields, st);
+      y_go<INV, PRUNE, 0, V>(F, tw, kmax3, planes, fields, st, rows, kcz);
     });
   }
 
@@ -2040,10 +2151,16 @@ struct SolverImpl {
     return cudaGetLastError();
   }
 
+  // the stage's y-inverse of the 6 fields (with the row flag: planes kz < kc only)
+  static void y_inverse(const PassArgs& a, cudaStream_t st) {
+    y_stage<1, 0>(a.ytile[0], bit(a.plan, PLAN_YI), reinterpret_cast<cx<T>*>(a.W),
+                  reinterpret_cast<const cx<T>*>(a.tw), k3y(a), M, 6, st, a.rows, kc_of(k3z(a)));
+  }
+
   static void rhs_front(const PassArgs& a, cudaStream_t st) {
     cx<T>* W = reinterpret_cast<cx<T>*>(a.W);
     const cx<T>* tw = reinterpret_cast<const cx<T>*>(a.tw);
-    y_stage<1, 0>(a.ytile[0], bit(a.plan, PLAN_YI), W, tw, k3y(a), M, 6, st);
+    y_inverse(a, st);
     z_cross(a, st);
     y_stage<0, 1>(a.ytile[1], bit(a.plan, PLAN_YF), W, tw, k3y(a), kc_of(k3z(a)), 3, st);
   }
@@ -2069,7 +2186,7 @@ struct SolverImpl {
     cx<T>* W = reinterpret_cast<cx<T>*>(a.W);
     const cx<T>* tw = reinterpret_cast<const cx<T>*>(a.tw);
     switch (part) {
-      case 0: y_stage<1, 0>(a.ytile[0], bit(a.plan, PLAN_YI), W, tw, k3y(a), M, 6, st); break;
+      case 0: y_inverse(a, st); break;
       case 1: z_cross(a, st); break;
       case 2: y_stage<0, 1>(a.ytile[1], bit(a.plan, PLAN_YF), W, tw, k3y(a), kc_of(k3z(a)), 3, st); break;
       default: x_stage(a, st); break;
@@ -2221,7 +2338,7 @@ struct SolverImpl {
     using Y = YCfg<T, N, 0, 0, NY>;
     k_zpass<T, N, ZM_LOAD, 0, NY, NZ><<<dim3(N / G::ZTX, NY), ZP_THREADS, G::ZSMEM, st>>>(a);
     k_ypass<T, N, 0, 0, 0, NY, NZ><<<dim3(N / Y::TX, M, 3), Y::THREADS, Y::SMEM, st>>>(
-        reinterpret_cast<cx<T>*>(a.U), reinterpret_cast<const cx<T>*>(a.tw), k3y(a));
+        reinterpret_cast<cx<T>*>(a.U), reinterpret_cast<const cx<T>*>(a.tw), k3y(a), nullptr, 0);
     k_xpass<T, N, XM_FWD_STORE, NY, NZ><<<ROWS, XP_THREADS, G::XSMEM, st>>>(f32args(a));
     return cudaGetLastError();
   }
@@ -2230,7 +2347,7 @@ struct SolverImpl {
     using Y = YCfg<T, N, 1, 0, NY>;
     k_xpass<T, N, XM_INV_PLAIN, NY, NZ><<<ROWS, XP_THREADS, G::XSMEM, st>>>(f32args(a));
     k_ypass<T, N, 1, 0, 0, NY, NZ><<<dim3(N / Y::TX, M, 3), Y::THREADS, Y::SMEM, st>>>(
-        reinterpret_cast<cx<T>*>(a.W), reinterpret_cast<const cx<T>*>(a.tw), k3y(a));
+        reinterpret_cast<cx<T>*>(a.W), reinterpret_cast<const cx<T>*>(a.tw), k3y(a), nullptr, 0);
     k_zpass<T, N, ZM_STORE, 0, NY, NZ><<<dim3(N / G::ZTX, NY), ZP_THREADS, G::ZSMEM, st>>>(a);
     return cudaGetLastError();
   }
@@ -2241,7 +2358,7 @@ struct SolverImpl {
     k_diag_final<<<1, 32, 0, st>>>(a.partials, DIAG_BLOCKS);
     k_xpass<T, N, XM_INV_DIV, NY, NZ><<<ROWS, XP_THREADS, G::XSMEM, st>>>(f32args(a));
     k_ypass<T, N, 1, 0, 0, NY, NZ><<<dim3(N / Y::TX, M, 1), Y::THREADS, Y::SMEM, st>>>(
-        reinterpret_cast<cx<T>*>(a.D), reinterpret_cast<const cx<T>*>(a.tw), k3y(a));
+        reinterpret_cast<cx<T>*>(a.D), reinterpret_cast<const cx<T>*>(a.tw), k3y(a), nullptr, 0);
     cudaMemsetAsync(a.maxbits, 0, sizeof(unsigned long long), st);
     k_zpass<T, N, ZM_MAXABS, 0, NY, NZ><<<dim3(N / G::ZTX, NY), ZP_THREADS, G::ZSMEM, st>>>(a);
     return cudaGetLastError();

@@ -4,7 +4,8 @@ This module holds no arithmetic of the solver itself (no transforms, no
 right-hand side, no time stepping): it only builds velocity fields.
 
 * Taylor-Green vortex, u = (sin x cos y cos z, -cos x sin y cos z, 0)
-  (the initial condition of the Appendix script and of Sec. 4 "Verification").
+  (the initial condition of the Appendix script and of Sec. 4 "Verification"), on the
+  mesh or as its exact Fourier coefficients.
 * ABC (Arnold-Beltrami-Childress) flow with |k| = 1, for which omega = u.
 * Decaying-isotropic random field in spectral form (Rogallo-style random
   phases): divergence-free, Hermitian in the kz = 0 plane, no Nyquist modes,
@@ -36,6 +37,21 @@ def taylor_green(N: int, dtype=np.float64) -> np.ndarray:
     u[0] = (sx[:, None, None] * cx[None, :, None] * cx[None, None, :]).astype(dtype)
     u[1] = (-cx[:, None, None] * sx[None, :, None] * cx[None, None, :]).astype(dtype)
     return u
+
+
+def taylor_green_spectral(N: int, device="cpu", dtype=torch.complex128) -> torch.Tensor:
+    """Taylor-Green velocity in the half spectrum (3, N, N, N/2+1), paper order, written out
+    exactly: sin x cos y cos z has the Fourier coefficient s_x / (8i) at k = (s_x, s_y, s_z),
+    s_i = +-1, and -cos x sin y cos z the coefficient -s_y / (8i); the unnormalised forward
+    transform multiplies them by N^3. Only kz = +1 is stored (kz = -1 is its conjugate) and
+    every other mode is exactly zero."""
+    uh = torch.zeros((3, N, N, N // 2 + 1), device=device, dtype=dtype)
+    c = float(N) ** 3 / 8.0
+    for sx in (1, -1):
+        for sy in (1, -1):
+            uh[0, sx % N, sy % N, 1] = -1j * c * sx
+            uh[1, sx % N, sy % N, 1] = 1j * c * sy
+    return uh
 
 
 def taylor_green_torch(N: int, device="cpu", dtype=torch.float32) -> torch.Tensor:
