@@ -21,7 +21,6 @@ Printed on rank 0 as one JSON line, with
                 precision against the FP64 CPU oracle at 128^3
   ensemble      128 members of mixed sizes: one graph launch per step versus
                 sequential per-member launches
-  plane_schedule  the same workload with the plane-pass schedule (fused_planes = 1)
   cufft_comparison  the same step composed from torch.fft (cuFFT) and torch
                 elementwise calls (a library comparison, not the product path)
   closure       learned subgrid closure (512^3 DNS -> 64^3): training cost,
@@ -72,8 +71,6 @@ def pass_bytes(N, real_bytes, stages=4, rows=False):
       z_pass     R 6 FV + W 3 (kc/M) FV (products kz < N/3)
       y_forward  R 3 (kc/M) FV + W 3 (kc/M)(2kc-1)/N FV (rows |ky| < N/3)
       x_stage    R 3 (kc/M)(2kc-1)/N FV (N_hat rows) + RK state + W 6 FV (u, omega)
-      plane_pass (y-forward, x-stage and y-inverse in one launch, planes handed over in L2)
-                 R 3 (kc/M) FV (products) + RK state + W 6 FV (u and omega, y-inverted)
     RK state per stage: stage 0 reads u (3) and writes u1, us (6); a middle stage reads us,
     u1, u (9) and writes u1, us (6); the last reads us, u1 (6) and writes u (3).
     With rows (a fraction zk yk of the rows kept):
@@ -104,7 +101,7 @@ def pass_bytes(N, real_bytes, stages=4, rows=False):
         return {"y_inverse": 6.0 * zk * (yk + 1.0) * fv, "z_pass": 9.0 * zk * fv,
                 "y_forward": (3.0 * zk + 3.0 * zk * yk) * fv, "x_stage": (3.0 + rk_mean + 6.0) * zk * yk * fv}
     return {"y_inverse": 12.0 * fv, "z_pass": (6.0 + 3.0 * zk) * fv, "y_forward": (3.0 * zk + 3.0 * zk * yk) * fv,
-            "x_stage": (3.0 * zk * yk + rk_mean + 6.0) * fv, "plane_pass": (3.0 * zk + rk_mean + 6.0) * fv}
+            "x_stage": (3.0 * zk * yk + rk_mean + 6.0) * fv}
 
 
 def truncated_step_cv(N):
@@ -321,27 +318,6 @@ def fp64_peak_tflops():
         _lib.check(_lib.lib().dns_measure_fp64_peak(ctypes.byref(v)), "dns_measure_fp64_peak")
         _FP64_PEAK = float(v.value)
     return _FP64_PEAK
-
-
-def run_plane_schedule(torch, Solver, inputs, N=N_MAIN, warm=3, steps=10):
-    """Taylor-Green N^3 FP32 with the plane-pass schedule (option fused_planes = 1): each stage
-    as the z-pass plus one persistent launch doing the y-forward, x-stage and y-inverse plane by
-    plane with the plane data handed over in L2. Same results as the default schedule (bitwise);
-    step time and per-kernel split for comparison."""
-    with Solver(N, NU, DT, "f32") as s:
-        s.set_option("fused_planes", 1)
-        st = torch.cuda.current_stream()
-        s.set_stream(st)
-        s.set_state_spectral(inputs.taylor_green_spectral(N, device="cuda", dtype=torch.complex64))
-        for _ in range(warm):
-            s.step(1)
-        torch.cuda.synchronize()
-        ms = time_steps(torch, s, st, steps) / steps
-        prof = s.profile_steps(steps)
-    kb = pass_bytes(N, 4)
-    return {"N": N, "dtype": "f32", "ms_per_step": ms, "value": N ** 3 / (ms * 1e-3),
-            "kernels": {k: {"ms_per_launch": v[0] / v[1], "algorithmic_bytes_per_launch": kb[k],
-                            "algorithmic_GBps": kb[k] / (v[0] / v[1] * 1e-3) / 1e9} for k, v in prof.items()}}
 
 
 def run_grids(torch, Solver, inputs, shape=(1024, 512, 256), warm=3, steps=10):
@@ -599,16 +575,13 @@ def run_ours(args):
     N, dtype = args.N, "f32"
     peak, peak_kind = measured_peaks()
     s = Solver(N, NU, DT, dtype)
-    if args.schedule != "auto":
-        s.set_option("fused_planes", 1 if args.schedule == "plane" else 0)
     st = torch.cuda.current_stream()
     s.set_stream(st)
     # the Taylor-Green vortex from its exact Fourier coefficients: the state vanishes outside
     # the 2/3 box, so the passes skip those rows (set from FP32 mesh values, the forward
     # transform would leave rounding residue there and the full transforms would run)
     s.set_state_spectral(inputs.taylor_green_spectral(N, device="cuda", dtype=torch.complex64))
-    rows = s.get_option("rows_vanish") == 1.0 and s.get_option("prune_rows") == 1.0 and \
-        s.get_option("fused_planes") == 0.0
+    rows = s.get_option("rows_vanish") == 1.0 and s.get_option("prune_rows") == 1.0
     for _ in range(args.warmup):
         s.step(1)
     torch.cuda.synchronize()
@@ -724,7 +697,6 @@ def run_ours(args):
         line["forms"] = forms
         line["integrators"] = run_integrators(torch, Solver, inputs)
         line["grids"] = run_grids(torch, Solver, inputs)
-        line["plane_schedule"] = run_plane_schedule(torch, Solver, inputs)
         line["ensemble"] = run_ensemble(torch, np)
         line["cufft_comparison"] = run_cufft_comparison(torch)
         line["closure"] = run_closure()
@@ -750,9 +722,6 @@ def main():
     ap.add_argument("--N", type=int, default=N_MAIN, help="grid size of the timed workload (profiling runs only)")
     ap.add_argument("--closure-only", action="store_true",
                     help="print only the in-graph closure timing at 64^3 (run_closure_share) and exit")
-    ap.add_argument("--schedule", choices=["auto", "plane", "four"], default="auto",
-                    help="stage schedule of the timed solver: plane pass where compiled (auto), or the four-pass "
-                         "schedule (profiling comparisons only)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -60,7 +60,7 @@ typedef enum {
   DNS_ERR_OOM = -2,         /* device allocation failed */
   DNS_ERR_CUDA = -3,        /* a CUDA call or kernel failed */
   DNS_ERR_NONFINITE = -4,   /* the state holds NaN or Inf */
-  DNS_ERR_TIMEOUT = -5,     /* a bounded device wait of the plane pass gave up (1 s) */
+  DNS_ERR_TIMEOUT = -5,     /* a bounded device wait gave up (1 s): the tensor-core MLP kernels */
   DNS_ERR_UNSUPPORTED = -6  /* no usable sm_103 device, or N not instantiated */
 } dns_status;
 
@@ -92,7 +92,7 @@ int dns_create(int N, double nu, double dt, int dtype, dns_handle** out);
  * "dealias_variant" 1), the inverse transform normalised by 1/(Nx Ny Nz).
  * Array shapes and errors as for dns_create; Nx = Ny = Nz is the same as
  * dns_create(Nx, ...). The other counts run the generic passes: the options
- * "fused_planes", "fft_plan", "y_tile_*" and "z_tile" offer only their defaults, and
+ * "fft_plan", "y_tile_*" and "z_tile" offer only their defaults, and
  * dns_set_closure and ensembles take cubic grids only. dns_get_option reads
  * the counts back as "Nx", "Ny", "Nz" (on any handle).
  * Errors: DNS_ERR_ARG (the shape is not compiled, see the list above), as for
@@ -149,31 +149,31 @@ int dns_set_stream(dns_handle* h, void* stream);
  *                      the mask measured fastest per grid size and precision on GB300
  *                      (dns_get_option reads it).
  *   "use_graph"        1: dns_step replays a captured CUDA graph (default)
- *   "fused_planes"     0 (default) or 1 where compiled (N >= 256): 1 runs each RK
- *                      stage as two launches, the z-pass and one persistent plane pass that
- *                      walks the kz planes and does the y-forward, x-stage and
- *                      y-inverse of each plane while its data is in L2 (the three
- *                      are local to a kz plane; Sec. 3.2 transposes become changes
- *                      of pass direction). 0: four launches per stage (y-inverse,
- *                      z-pass, y-forward, x-stage). Same arithmetic, bit-identical
- *                      results. The plane pass moves fewer DRAM bytes but, on
- *                      GB300, runs slower than the four passes at 256^3 - 1024^3.
- *                      The plane pass orders its work items through per-plane
- *                      counters in device memory; a wait that gives up after 1 s
- *                      (never in a correct run) makes the next synchronising call
- *                      (dns_get_state*, dns_diagnostics, dns_profile_steps) return
- *                      DNS_ERR_TIMEOUT.
- *   "plane_lag"        0 (default: chosen from the launch's block count) or 1 .. 8:
- *                      queue steps between a plane's y-forward and x-stage work and
- *                      between its x-stage and y-inverse work in the plane pass.
- *                      A schedule knob only: results do not depend on it.
+ *   "prune_rows"       1 (default): where the state vanishes on every row (kz, ky)
+ *                      outside the 2/3 box (checked on the device, and read back, by
+ *                      dns_set_state, dns_set_state_spectral and a change of
+ *                      "dealias_variant", which therefore synchronise the stream), the
+ *                      stage's passes skip those rows: the RK stage keeps them zero
+ *                      (no nonlinear term there, a viscous term proportional to u_hat;
+ *                      Eq. NSfinal), so their transforms are transforms of zeros. The
+ *                      x-stage and the x inverse leave them alone, the y-inverse
+ *                      transforms only the planes kz < Nz/3 and reads the other rows as
+ *                      zeros, the z-pass reads only kz < Nz/3; where the state also
+ *                      vanishes at |kx| >= Nx/3, the x-stage reads and writes its rows at
+ *                      the kept columns only. The results equal the full transforms bit
+ *                      for bit (exact zeros of either sign); the RK registers and work
+ *                      fields of the skipped rows are left unwritten. 0: the full
+ *                      transforms whatever the state.
  *   "nu", "dt"         change the viscosity / time step
  *   "time"             set the simulated time reported by dns_diagnostics
  * Errors: DNS_ERR_ARG for an unknown key or a value out of range. */
 int dns_set_option(dns_handle* h, const char* key, double value);
 
 /* The current value of an option of dns_set_option ("time" included), or of the
- * read-only grid counts "Nx", "Ny", "Nz", in *value.
+ * read-only keys, in *value: the grid counts "Nx", "Ny", "Nz"; "rows_vanish" 1 if the
+ * state vanishes on every row (kz, ky) outside the 2/3 box, else 0, and "box_vanish" 1 if
+ * it vanishes at every mode outside the box (what "prune_rows" uses, as checked by the
+ * last dns_set_state* or change of "dealias_variant").
  * Errors: DNS_ERR_ARG for an unknown key or a NULL pointer. */
 int dns_get_option(const dns_handle* h, const char* key, double* value);
 
@@ -191,16 +191,15 @@ int dns_get_option(const dns_handle* h, const char* key, double* value);
  * arrays as the built-in schemes. Errors: DNS_ERR_ARG. */
 int dns_set_rk_tableau(dns_handle* h, int form, int stages, const double* a, const double* b);
 
-/* Schedule tuner: times dns_step with the plane-pass schedule off and on ("fused_planes",
- * where compiled), both radix plans of each pass ("fft_plan" bits, N <= 128) and every
- * tile width the grid offers for the y-inverse, the y-forward and the z-pass (N <= 128;
- * defaults included), one knob at a time (the schedule, then the plan bits, then the widths)
+/* Schedule tuner: times dns_step with both radix plans of each pass ("fft_plan" bits,
+ * N <= 128) and every tile width the grid offers for the y-inverse, the y-forward and the
+ * z-pass (N <= 128; defaults included), one knob at a time (the plan bits, then the widths)
  * with the best values found before it, three timings of `steps` graph replays each
  * after a capture and a warm-up step; a candidate replaces the one kept so far
  * (starting from the default) only if its median time beats that one's median by
  * more than that one's spread (max - min); the kept widths are written to
- * *y_inverse, *y_forward, *z (0 = default), the kept plan and schedule are the handle's
- * "fft_plan" and "fused_planes". Every candidate starts from the same state, and the state and time
+ * *y_inverse, *y_forward, *z (0 = default), the kept plan is the handle's "fft_plan".
+ * Every candidate starts from the same state, and the state and time
  * are restored at the end; the results of later steps do not depend on the widths
  * (the plan changes their rounding only). Allocates and frees one state copy (3
  * fields). Synchronises. Errors: DNS_ERR_ARG (steps < 1, NULL outputs),
@@ -215,7 +214,7 @@ int dns_tune_tiles(dns_handle* h, int steps, int* y_inverse, int* y_forward, int
  * with their counts (a stored schedule is applied without advancing the members;
  * the size classes' plans and widths come from the tiles entries). The file is plain
  * text, one entry per line, the last matching line wins:
- *   tiles <device> <Nx> <Ny> <Nz> <f32|f64> <y_inverse> <y_forward> <z> <fft_plan> <fused_planes>
+ *   tiles <device> <Nx> <Ny> <Nz> <f32|f64> <y_inverse> <y_forward> <z> <fft_plan>
  *   ensemble <device> <f32|f64> <N:count,...> <max_batch> <streams>
  * with blanks in the device name written as '_'; a stored value the grid does not
  * offer makes the tuner time again. Process-wide; NULL or "" turns it off (the
@@ -223,10 +222,10 @@ int dns_tune_tiles(dns_handle* h, int steps, int* y_inverse, int* y_forward, int
 int dns_set_tune_cache(const char* path);
 
 /* The stored tiles entry of the tune cache for (device, Nx, Ny, Nz, dtype): returns 1
- * and writes the widths, the plan mask and the schedule when found, 0 when not (or no
- * cache is set), DNS_ERR_ARG for a NULL argument. Host only; needs no device. */
+ * and writes the widths and the plan mask when found, 0 when not (or no cache is set),
+ * DNS_ERR_ARG for a NULL argument. Host only; needs no device. */
 int dns_tune_cache_lookup(const char* device, int Nx, int Ny, int Nz, int dtype, int* y_inverse, int* y_forward,
-                          int* z, int* plan, int* fused_planes);
+                          int* z, int* plan);
 
 /* The tile widths a grid offers the tuner besides the default: which = 0 the
  * y-passes ("y_tile_inverse", "y_tile_forward"), 1 the z-pass ("z_tile"), for
@@ -237,11 +236,13 @@ int dns_tile_widths(int N, int dtype, int which, int* widths, int max);
 
 /* State from a physical velocity field u (3,N,N,N): u_hat = F(u) with the
  * Nyquist modes zeroed (Eq. iffteq forward transform; no projection).
- * Resets the time to 0. */
+ * Resets the time to 0. Checks where the state vanishes (option "prune_rows") and
+ * synchronises the stream. */
 int dns_set_state(dns_handle* h, const void* u, int on_device);
 
 /* State from spectral coefficients (3,N,N,N/2+1), complex, paper order;
- * Nyquist modes are zeroed. Resets the time to 0. */
+ * Nyquist modes are zeroed. Resets the time to 0. Checks where the state vanishes
+ * (option "prune_rows") and synchronises the stream. */
 int dns_set_state_spectral(dns_handle* h, const void* uhat, int on_device);
 
 /* Enqueues n >= 0 steps of Eq. NSfinal with the handle's integrator (default
@@ -268,11 +269,9 @@ int dns_diagnostics(dns_handle* h, dns_diag* out);
 /* Measurement aid: advances n >= 1 steps exactly like dns_step but
  * launches the kernels one by one (no graph) with a CUDA event after each,
  * and returns per kernel class the summed device time in ms[c] and the
- * launch count in launches[c]. Four-pass schedule: c = 0 y-inverse, 1 z-pass
- * (c2r, u x omega, r2c), 2 y-forward, 3 x-stage (forward x, mask, projection,
- * viscous term, stage update, next inverse x). Plane-pass schedule (option
- * "fused_planes"): c = 0 z-pass, 1 plane pass (y-forward, x-stage, y-inverse),
- * classes 2 and 3 zero. nclass must be >= 4. Synchronises. */
+ * launch count in launches[c]: c = 0 y-inverse, 1 z-pass (c2r, u x omega, r2c),
+ * 2 y-forward, 3 x-stage (forward x, mask, projection, viscous term, stage update,
+ * next inverse x). nclass must be >= 4. Synchronises. */
 int dns_profile_steps(dns_handle* h, int n, double* ms, int* launches, int nclass);
 
 /* Measured FP64 FMA throughput of the current device in TFLOP/s (2 flops per
@@ -451,15 +450,6 @@ int dns_set_closure(dns_handle* h, dns_mlp* net, double delta);
  * the device; n = 0 disables the hook. */
 int dns_debug_fail_alloc_after(int n);
 
-/* Test hook for the bounded waits of the plane pass (no counterpart in the
- * paper): runs one plane pass of stage 0 whose work queue starts past the
- * y-forward and x-stage items its first y-inverse items wait for, so those
- * waits give up after 1 s; every block then stops. Returns DNS_ERR_TIMEOUT
- * (the expected outcome: the error flag was read back and cleared),
- * DNS_ERR_ARG if the waits did not give up, DNS_ERR_UNSUPPORTED for a grid
- * without a plane pass. The state u_hat is untouched (stage 0 does not write
- * it); the work fields are re-primed by the next step. Synchronises. */
-int dns_debug_plane_wait_timeout(dns_handle* h);
 
 #ifdef __cplusplus
 }

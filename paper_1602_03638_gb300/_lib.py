@@ -51,7 +51,7 @@ SIGNATURES = {
     "dns_tune_tiles": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "dns_set_tune_cache": (_I, [ctypes.c_char_p]),
     "dns_tune_cache_lookup": (_I, [ctypes.c_char_p, _I, _I, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
-                                   ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+                                   ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "dns_set_rk_tableau": (_I, [_P, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "dns_tile_widths": (_I, [_I, _I, _I, ctypes.POINTER(_I), _I]),
     "dns_set_state": (_I, [_P, _P, _I]),
@@ -65,7 +65,6 @@ SIGNATURES = {
     "dns_device_bytes": (ctypes.c_size_t, [_P]),
     "dns_last_error": (ctypes.c_char_p, [_P]),
     "dns_debug_fail_alloc_after": (_I, [_I]),
-    "dns_debug_plane_wait_timeout": (_I, [_P]),
     "dns_spectral_sums_noalloc": (_I, [_P, _I, _I, _D, _P, _P]),
     "dns_ensemble_create": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_D), _I, ctypes.POINTER(_P)]),
     "dns_ensemble_destroy": (_I, [_P]),

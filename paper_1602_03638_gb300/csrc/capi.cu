@@ -55,20 +55,25 @@ __global__ void k_diag_final(double* partials, int nblocks) {
   }
 }
 
-// *flag = 1 if a row (kz, ky) of the state U (3 fields of M x Ny rows of Nx values, internal
-// layout) outside the 2/3 box (3 kz >= k3z or 3 |ky| >= k3y) holds a nonzero value (NaN
-// counts as nonzero, -0 as zero); *flag is left unchanged otherwise (cleared by the caller).
+// The row flag of the state U (3 fields of M x Ny rows of Nx values, internal layout):
+// bit 0 is set if a row (kz, ky) outside the 2/3 box (3 kz >= k3z or 3 |ky| >= k3y) holds a
+// nonzero value, bit 1 if a row inside it does at a column with 3 |kx| >= k3x (NaN counts as
+// nonzero, -0 as zero); the bits are only set here (the caller clears the flag).
 template <typename T>
-__global__ void k_rows_outside(const cx<T>* __restrict__ U, int Nx, int Ny, int M, int k3y, int k3z, int* flag) {
+__global__ void k_rows_outside(const cx<T>* __restrict__ U, int Nx, int Ny, int M, int k3x, int k3y, int k3z,
+                               int* flag) {
   const size_t rows = (size_t)3 * M * Ny;
   for (size_t r = blockIdx.x; r < rows; r += gridDim.x) {
     const int ky = (int)(r % Ny), kz = (int)((r / Ny) % M);
     const int kf = ky < Ny / 2 ? ky : ky - Ny;
-    if (3 * kz < k3z && 3 * (kf < 0 ? -kf : kf) < k3y) continue;  // inside: the same for the whole block
+    const bool inside = 3 * kz < k3z && 3 * (kf < 0 ? -kf : kf) < k3y;  // the same for the whole block
     const cx<T>* p = U + r * Nx;
     int nz = 0;
-    for (int j = threadIdx.x; j < Nx; j += blockDim.x) nz |= (p[j].x != (T)0) | (p[j].y != (T)0);
-    if (__syncthreads_or(nz) && threadIdx.x == 0) atomicOr(flag, 1);
+    for (int j = threadIdx.x; j < Nx; j += blockDim.x) {
+      const int kx = j < Nx / 2 ? j : j - Nx;
+      if (!inside || 3 * (kx < 0 ? -kx : kx) >= k3x) nz |= (p[j].x != (T)0) | (p[j].y != (T)0);
+    }
+    if (__syncthreads_or(nz) && threadIdx.x == 0) atomicOr(flag, inside ? 2 : 1);
   }
 }
 
@@ -248,8 +253,6 @@ struct dns_handle {
   int ztile = 0;          // z-pass tile width of the stage; 0 = default
   int plan = 0;  // radix plan variant per pass of the stage's line transforms (option "fft_plan", bits PLAN_*)
   int use_graph = 1;
-  int fused = 0;  // plane-pass schedule (option "fused_planes"; measured slower than the four passes)
-  int plane_lag = 0;  // option "plane_lag" (0: automatic)
   double nu = 0.0, dt = 0.0, t = 0.0;
   const DnsOps* ops = nullptr;
   int device = 0;
@@ -276,11 +279,11 @@ struct dns_handle {
   cudaEvent_t cl_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   void* tw = nullptr;
   double* diag = nullptr;
-  int* ctl = nullptr;  // plane-pass control block (ops->plane_ctl_words ints)
   size_t bytes = 0;
   size_t fs = 0;  // complex values per field
   bool w_valid = false;
   int prune_rows = 1;  // option "prune_rows": skip the rows outside the 2/3 box where the state vanishes
+  int support = PRUNE_BOX;  // where the state vanishes (PRUNE_*), from the last check (the zero state: everywhere)
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   bool graph_dirty = true;
@@ -311,7 +314,7 @@ int dev_alloc(dns_handle* h, void** p, size_t bytes, const char* what) {
 void release(dns_handle* h) {
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->graph) cudaGraphDestroy(h->graph);
-  void* bufs[] = {h->U, h->U1, h->US, h->W, h->D, h->F, h->tw, h->diag, h->ctl, h->CX, h->CT, h->CS, h->CW, h->FC};
+  void* bufs[] = {h->U, h->U1, h->US, h->W, h->D, h->F, h->tw, h->diag, h->CX, h->CT, h->CS, h->CW, h->FC};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (cudaEvent_t ev : h->cl_ev)
@@ -322,7 +325,7 @@ void release(dns_handle* h) {
   if (h->own_stream) cudaStreamDestroy(h->own_stream);
 }
 
-// The row flag (PassArgs::rows) in the diagnostics block past the results and max|div|.
+// Scratch word of the row check (check_rows) in the diagnostics block, past the results and max|div|.
 int* row_flag(const dns_handle* h) { return reinterpret_cast<int*>(h->diag + DIAG_BLOCKS * 4 + 6); }
 
 PassArgs base_args(const dns_handle* h) {
@@ -343,52 +346,47 @@ PassArgs base_args(const dns_handle* h) {
   a.ytile[1] = h->ytile[1];
   a.ztile = h->ztile;
   a.plan = h->plan;
-  a.ctl = h->ctl;
-  a.plane_lag = h->plane_lag;
   a.partials = h->diag;
   a.maxbits = reinterpret_cast<unsigned long long*>(h->diag + DIAG_BLOCKS * 4 + 4);
-  // the row flag: the four-pass stages only (the plane pass reads every row)
-  const bool plane = h->fused && h->ops->rk_stage_fused && h->ctl;
-  if (h->prune_rows && !plane) a.rows = row_flag(h);
+  if (h->prune_rows) a.prune = h->support;
   return a;
 }
 
-// Sets the row flag from the state now in U (on the handle's stream): 0 if U vanishes on
-// every row (kz, ky) outside the handle's 2/3 box, else 1.
+// Where the state now in U vanishes (h->support, PRUNE_*): the row flag, bit 0 unless U
+// vanishes on every row (kz, ky) outside the handle's 2/3 box, bit 1 unless it also vanishes
+// at the columns |kx| >= N/3 of the rows inside, computed on the handle's stream and read
+// back (synchronises). A change re-captures the step graph.
 cudaError_t check_rows(dns_handle* h) {
   int* flag = row_flag(h);
   cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), h->stream);
   if (e != cudaSuccess) return e;
-  const int k3y = h->Ny + 2 * h->variant, k3z = h->Nz + 2 * h->variant;
+  const int k3x = h->N + 2 * h->variant, k3y = h->Ny + 2 * h->variant, k3z = h->Nz + 2 * h->variant;
   const int M = h->Nz / 2, blocks = 1024;
   if (h->dtype == DNS_F32)
-    k_rows_outside<float><<<blocks, 256, 0, h->stream>>>((const cx<float>*)h->U, h->N, h->Ny, M, k3y, k3z, flag);
+    k_rows_outside<float><<<blocks, 256, 0, h->stream>>>((const cx<float>*)h->U, h->N, h->Ny, M, k3x, k3y, k3z, flag);
   else
-    k_rows_outside<double><<<blocks, 256, 0, h->stream>>>((const cx<double>*)h->U, h->N, h->Ny, M, k3y, k3z, flag);
-  return cudaGetLastError();
+    k_rows_outside<double><<<blocks, 256, 0, h->stream>>>((const cx<double>*)h->U, h->N, h->Ny, M, k3x, k3y, k3z,
+                                                          flag);
+  int f = 3;
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&f, flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return e;
+  const int support = (f & 1) ? PRUNE_NONE : ((f & 2) ? PRUNE_ROWS : PRUNE_BOX);
+  if (support != h->support) {
+    h->support = support;
+    h->graph_dirty = true;
+    ++h->epoch;
+  }
+  return cudaSuccess;
 }
 
 int rk_stages(const dns_handle* h) { return h->rk.stages; }
 
-bool use_fused(const dns_handle* h) { return h->fused && h->ops->rk_stage_fused && h->ctl; }
-
-// Brings W into the form the stage launches expect: the x-inverse of u and omega
-// (four-pass schedule) or their x- and y-inverse (plane-pass schedule).
+// Brings W into the form the stage launches expect: the x-inverse of u and omega.
 cudaError_t prime_work(dns_handle* h, cudaStream_t st) {
   PassArgs a = base_args(h);
-  return use_fused(h) ? h->ops->prime_fused(a, 0, st) : h->ops->x_inverse_curl(a, 0, st);
-}
-
-// Reports (and clears) a plane-pass wait that gave up; the stream is synchronised.
-int check_plane_error(dns_handle* h, const char* where) {
-  if (!h->ctl) return DNS_OK;
-  int err = 0;
-  DNS_CUDA(cudaMemcpyAsync(&err, h->ctl, sizeof(int), cudaMemcpyDeviceToHost, h->stream), where);
-  DNS_CUDA(cudaStreamSynchronize(h->stream), where);
-  if (!err) return DNS_OK;
-  DNS_CUDA(cudaMemsetAsync(h->ctl, 0, sizeof(int), h->stream), where);
-  h->w_valid = false;
-  return fail(DNS_ERR_TIMEOUT, "%s: a plane-pass wait gave up after 1 s; the state is not valid", where);
+  return h->ops->x_inverse_curl(a, 0, st);
 }
 
 // stage s of the handle's scheme: its coefficients times dt and the index of the last stage
@@ -456,10 +454,9 @@ cudaError_t enqueue_step(dns_handle* h, cudaStream_t st) {
     if (e != cudaSuccess) return e;
   }
   PassArgs a = base_args(h);
-  const bool fused = use_fused(h);
   for (int s = 0; s < rk_stages(h); ++s) {
     set_stage(h, s, a);
-    cudaError_t e = fused ? h->ops->rk_stage_fused(a, st) : h->ops->rk_stage(a, st);
+    cudaError_t e = h->ops->rk_stage(a, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -563,13 +560,6 @@ int dns_create3(int Nx, int Ny, int Nz, double nu, double dt, int dtype, dns_han
   const int TW = ops->TW;  // exp(-2 pi i t / TW): N on a cubic grid, else a common multiple of the counts
   if (rc == DNS_OK) rc = dev_alloc(h, &h->tw, (size_t)TW * cb, "twiddles");
   if (rc == DNS_OK) rc = dev_alloc(h, (void**)&h->diag, (DIAG_BLOCKS * 4 + 8) * sizeof(double), "diagnostics");
-  if (rc == DNS_OK && ops->plane_ctl_words > 0) {
-    rc = dev_alloc(h, (void**)&h->ctl, (size_t)ops->plane_ctl_words * sizeof(int), "plane-pass control block");
-    if (rc == DNS_OK) {
-      ce = cudaMemset(h->ctl, 0, (size_t)ops->plane_ctl_words * sizeof(int));
-      if (ce != cudaSuccess) rc = cuda_fail(ce, "dns_create control block");
-    }
-  }
   if (rc == DNS_OK) {
     std::vector<double> t64(2 * TW);
     for (int t = 0; t < TW; ++t) twiddle(t, TW, &t64[2 * t], &t64[2 * t + 1]);
@@ -581,7 +571,6 @@ int dns_create3(int Nx, int Ny, int Nz, double nu, double dt, int dtype, dns_han
       ce = cudaMemcpy(h->tw, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice);
     }
     if (ce == cudaSuccess) ce = cudaMemset(h->U, 0, 3 * h->fs * cb);
-    if (ce == cudaSuccess) ce = cudaMemset(row_flag(h), 0, sizeof(int));  // the zero state vanishes everywhere
     if (ce != cudaSuccess) rc = cuda_fail(ce, "dns_create initialisation");
   }
   if (rc != DNS_OK) {
@@ -655,15 +644,6 @@ int dns_set_option(dns_handle* h, const char* key, double value) {
   } else if (!strcmp(key, "use_graph")) {
     if (value != 0.0 && value != 1.0) return fail(DNS_ERR_ARG, "use_graph must be 0 or 1");
     h->use_graph = (int)value;
-  } else if (!strcmp(key, "fused_planes")) {
-    if (value != 0.0 && value != 1.0) return fail(DNS_ERR_ARG, "fused_planes must be 0 or 1");
-    if (value == 1.0 && !h->ops->rk_stage_fused)
-      return fail(DNS_ERR_ARG, "fused_planes: N = %d has no plane-pass schedule", h->N);
-    h->fused = (int)value;
-  } else if (!strcmp(key, "plane_lag")) {
-    if (!(value >= 0.0 && value <= 8.0) || value != std::floor(value))
-      return fail(DNS_ERR_ARG, "plane_lag must be an integer in 0 .. 8");
-    h->plane_lag = (int)value;
   } else if (!strcmp(key, "nu")) {
     if (!(value >= 0.0) || !std::isfinite(value)) return fail(DNS_ERR_ARG, "nu must be finite and >= 0");
     h->nu = value;
@@ -695,8 +675,6 @@ int dns_get_option(const dns_handle* h, const char* key, double* value) {
   else if (!strcmp(key, "z_tile")) *value = h->ztile;
   else if (!strcmp(key, "fft_plan")) *value = h->plan;
   else if (!strcmp(key, "use_graph")) *value = h->use_graph;
-  else if (!strcmp(key, "fused_planes")) *value = use_fused(h) ? 1.0 : 0.0;
-  else if (!strcmp(key, "plane_lag")) *value = h->plane_lag;
   else if (!strcmp(key, "nu")) *value = h->nu;
   else if (!strcmp(key, "dt")) *value = h->dt;
   else if (!strcmp(key, "time")) *value = h->t;
@@ -704,13 +682,8 @@ int dns_get_option(const dns_handle* h, const char* key, double* value) {
   else if (!strcmp(key, "Ny")) *value = h->Ny;
   else if (!strcmp(key, "Nz")) *value = h->Nz;
   else if (!strcmp(key, "prune_rows")) *value = h->prune_rows;
-  else if (!strcmp(key, "rows_vanish")) {  // the row flag (synchronises the handle's stream)
-    int f = 1;
-    if ((rc = use_device(h))) return rc;
-    DNS_CUDA(cudaMemcpyAsync(&f, row_flag(h), sizeof(int), cudaMemcpyDeviceToHost, h->stream), "rows_vanish");
-    DNS_CUDA(cudaStreamSynchronize(h->stream), "rows_vanish");
-    *value = f == 0 ? 1.0 : 0.0;
-  } else return fail(DNS_ERR_ARG, "dns_get_option: unknown key '%s'", key);
+  else if (!strcmp(key, "rows_vanish")) *value = h->support >= PRUNE_ROWS ? 1.0 : 0.0;
+  else if (!strcmp(key, "box_vanish")) *value = h->support == PRUNE_BOX ? 1.0 : 0.0; else return fail(DNS_ERR_ARG, "dns_get_option: unknown key '%s'", key);
   return DNS_OK;
 }
 
@@ -749,7 +722,7 @@ namespace {
 
 // ---- tune cache: the tuners' choices kept in a text file across runs ----
 // One entry per line, later lines win:
-//   tiles <device> <Nx> <Ny> <Nz> <f32|f64> <y_inverse> <y_forward> <z> <plan> <fused_planes>
+//   tiles <device> <Nx> <Ny> <Nz> <f32|f64> <y_inverse> <y_forward> <z> <plan>
 //   ensemble <device> <f32|f64> <N:count,...> <max_batch> <streams>
 std::mutex g_tc_mu;
 std::string g_tc_path;
@@ -832,16 +805,15 @@ int dns_set_tune_cache(const char* path) {
 }
 
 int dns_tune_cache_lookup(const char* device, int Nx, int Ny, int Nz, int dtype, int* y_inverse, int* y_forward,
-                          int* z, int* plan, int* fused_planes) {
-  if (!device || !y_inverse || !y_forward || !z || !plan || !fused_planes)
+                          int* z, int* plan) {
+  if (!device || !y_inverse || !y_forward || !z || !plan)
     return fail(DNS_ERR_ARG, "dns_tune_cache_lookup: NULL argument");
   std::vector<long> v;
-  if (!tc_find(tc_tiles_key(device, Nx, Ny, Nz, dtype), v, 5)) return 0;
+  if (!tc_find(tc_tiles_key(device, Nx, Ny, Nz, dtype), v, 4)) return 0;
   *y_inverse = (int)v[0];
   *y_forward = (int)v[1];
   *z = (int)v[2];
   *plan = (int)v[3];
-  *fused_planes = (int)v[4];
   return 1;
 }
 
@@ -851,13 +823,12 @@ int dns_tune_tiles(dns_handle* h, int steps, int* y_inverse, int* y_forward, int
   if (steps < 1 || !y_inverse || !y_forward || !z) return fail(DNS_ERR_ARG, "dns_tune_tiles: bad arguments");
   if ((rc = use_device(h))) return rc;
   // candidates per knob (the default first): y-inverse width, y-forward width, z width,
-  // the radix plan variant (0, 1) of each pass, and the schedule (four passes, plane pass)
-  int ycand[9] = {0}, zcand[9] = {0}, fcand[2] = {0, 1};
+  // and the radix plan variant (0, 1) of each pass
+  int ycand[9] = {0}, zcand[9] = {0};
   const int ny = 1 + h->ops->y_tiles(ycand + 1, 8);
   const int nz = 1 + h->ops->z_tiles(zcand + 1, 8);
   const int np = h->ops->plans;
-  const int nf = (h->ops->rk_stage_fused && h->ctl) ? 2 : 1;
-  if (ny == 1 && nz == 1 && np == 1 && nf == 1) {  // this grid offers the defaults only
+  if (ny == 1 && nz == 1 && np == 1) {  // this grid offers the defaults only
     *y_inverse = h->ytile[0];
     *y_forward = h->ytile[1];
     *z = h->ztile;
@@ -866,14 +837,12 @@ int dns_tune_tiles(dns_handle* h, int steps, int* y_inverse, int* y_forward, int
   // a choice stored in the tune cache for this device and grid is applied without timing
   const std::vector<std::string> tkey = tc_tiles_key(tc_device(h->device), h->N, h->Ny, h->Nz, h->dtype);
   std::vector<long> cached;
-  if (tc_find(tkey, cached, 5) && offered((int)cached[0], ycand, ny) && offered((int)cached[1], ycand, ny) &&
-      offered((int)cached[2], zcand, nz) && cached[3] >= 0 && cached[3] < (np > 1 ? 1 << PLAN_BITS : 1) &&
-      cached[4] >= 0 && cached[4] < nf) {
+  if (tc_find(tkey, cached, 4) && offered((int)cached[0], ycand, ny) && offered((int)cached[1], ycand, ny) &&
+      offered((int)cached[2], zcand, nz) && cached[3] >= 0 && cached[3] < (np > 1 ? 1 << PLAN_BITS : 1)) {
     h->ytile[0] = (int)cached[0];
     h->ytile[1] = (int)cached[1];
     h->ztile = (int)cached[2];
     h->plan = (int)cached[3];
-    h->fused = (int)cached[4];
     h->graph_dirty = true;
     ++h->epoch;
     h->w_valid = false;
@@ -886,7 +855,7 @@ int dns_tune_tiles(dns_handle* h, int steps, int* y_inverse, int* y_forward, int
   void* save = nullptr;
   if ((rc = dev_alloc(h, &save, bytes, "tuning copy of the state"))) return rc;
   const double t0 = h->t;
-  const int keep[5] = {h->ytile[0], h->ytile[1], h->ztile, h->plan, h->fused};
+  const int keep[4] = {h->ytile[0], h->ytile[1], h->ztile, h->plan};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t err = cudaMemcpyAsync(save, h->U, bytes, cudaMemcpyDeviceToDevice, h->stream);
   if (err == cudaSuccess) err = cudaEventCreate(&e0);
@@ -897,7 +866,6 @@ int dns_tune_tiles(dns_handle* h, int steps, int* y_inverse, int* y_forward, int
     h->ytile[1] = v[1];
     h->ztile = v[2];
     h->plan = v[3];
-    h->fused = v[4];
     h->graph_dirty = true;
   };
   // each candidate starts from the saved state: capture and one warm-up step, then
@@ -923,24 +891,22 @@ int dns_tune_tiles(dns_handle* h, int steps, int* y_inverse, int* y_forward, int
     *spread = t[2] - t[0];
     return DNS_OK;
   };
-  // one knob at a time, the others kept: the schedule (four passes or the plane pass),
-  // the radix plan of the x-, y-inverse, z- and y-forward passes (with the widths the
-  // handle has), the y-inverse width, the y-forward width, then the z width, each with
+  // one knob at a time, the others kept: the radix plan of the x-, y-inverse, z- and
+  // y-forward passes (with the widths the handle has), the y-inverse width, the
+  // y-forward width, then the z width, each with
   // the best values found before it. The first candidate is the default; another
   // replaces the one kept so far only if its median beats that one's median by more
   // than that one's spread (differences inside the timing noise keep the earlier choice).
-  int best_v[5] = {keep[0], keep[1], keep[2], h->ops->default_plan, 0};
-  // which < 3: a tile width; which = 3 + b: the plan bit b; which = FUSED: the schedule
-  constexpr int FUSED = 3 + PLAN_BITS;
+  int best_v[4] = {keep[0], keep[1], keep[2], h->ops->default_plan};
+  // which < 3: a tile width; which = 3 + b: the plan bit b
   auto pick = [&](int n, const int* cand, int which) {
     float best = 0.f, best_spread = 0.f, ms = 0.f, spread = 0.f;
     auto with = [&](int* v, int c) {
       if (which < 3) v[which] = cand[c];
-      else if (which == FUSED) v[4] = cand[c];
       else v[3] = (v[3] & ~(1 << (which - 3))) | (cand[c] << (which - 3));
     };
     for (int c = 0; c < n && !rc; ++c) {
-      int v[5] = {best_v[0], best_v[1], best_v[2], best_v[3], best_v[4]};
+      int v[4] = {best_v[0], best_v[1], best_v[2], best_v[3]};
       with(v, c);
       if ((rc = timed(v, &ms, &spread))) return;
       if (c == 0 || ms < best - best_spread) {
@@ -950,7 +916,6 @@ int dns_tune_tiles(dns_handle* h, int steps, int* y_inverse, int* y_forward, int
       }
     }
   };
-  if (nf > 1) pick(nf, fcand, FUSED);
   if (np > 1)
     for (int b : {PLAN_X, PLAN_YI, PLAN_Z, PLAN_YF}) {
       const int d = (h->ops->default_plan >> b) & 1;  // the default's bit first
@@ -972,7 +937,7 @@ int dns_tune_tiles(dns_handle* h, int steps, int* y_inverse, int* y_forward, int
   apply(rc ? keep : best_v);
   ++h->epoch;
   if (!rc && err != cudaSuccess) rc = cuda_fail(err, "dns_tune_tiles restore");
-  if (!rc) tc_put(tkey, {best_v[0], best_v[1], best_v[2], best_v[3], best_v[4]});
+  if (!rc) tc_put(tkey, {best_v[0], best_v[1], best_v[2], best_v[3]});
   *y_inverse = h->ytile[0];
   *y_forward = h->ytile[1];
   *z = h->ztile;
@@ -1072,7 +1037,7 @@ int dns_get_state(dns_handle* h, void* u, int on_device) {
     DNS_CUDA(cudaMemcpyAsync(u, dst, phys_bytes(h), cudaMemcpyDeviceToHost, h->stream), "dns_get_state copy");
   DNS_CUDA(cudaStreamSynchronize(h->stream), "dns_get_state");
   h->w_valid = false;
-  return check_plane_error(h, "dns_get_state");
+  return DNS_OK;
 }
 
 int dns_get_state_spectral(dns_handle* h, void* uhat, int on_device) {
@@ -1090,7 +1055,7 @@ int dns_get_state_spectral(dns_handle* h, void* uhat, int on_device) {
     h->w_valid = false;
   }
   DNS_CUDA(cudaStreamSynchronize(h->stream), "dns_get_state_spectral");
-  return check_plane_error(h, "dns_get_state_spectral");
+  return DNS_OK;
 }
 
 int dns_rhs(dns_handle* h, void* duhat, int on_device) {
@@ -1123,7 +1088,6 @@ int dns_diagnostics(dns_handle* h, dns_diag* out) {
   DNS_CUDA(cudaMemcpyAsync(r, h->diag + DIAG_BLOCKS * 4, sizeof(r), cudaMemcpyDeviceToHost, h->stream),
            "dns_diagnostics copy");
   DNS_CUDA(cudaStreamSynchronize(h->stream), "dns_diagnostics");
-  if ((rc = check_plane_error(h, "dns_diagnostics"))) return rc;
   const double n3 = (double)h->N * (double)h->Ny * (double)h->Nz;
   const double n6 = n3 * n3;
   unsigned long long bits;
@@ -1252,8 +1216,7 @@ int dns_profile_steps(dns_handle* h, int n, double* ms, int* launches, int nclas
     DNS_CUDA(prime_work(h, h->stream), "dns_profile_steps initial transform");
     h->w_valid = true;
   }
-  const bool fused = use_fused(h);
-  const int parts = fused ? 2 : 4;  // plane-pass schedule: z-pass, plane pass
+  const int parts = 4;
   const int nk = parts * rk_stages(h) * n;
   std::vector<cudaEvent_t> ev(nk + 1);
   for (auto& e : ev) DNS_CUDA(cudaEventCreate(&e), "cudaEventCreate");
@@ -1264,7 +1227,7 @@ int dns_profile_steps(dns_handle* h, int n, double* ms, int* launches, int nclas
     for (int s = 0; s < rk_stages(h) && err == cudaSuccess; ++s) {
       set_stage(h, s, a);
       for (int p = 0; p < parts && err == cudaSuccess; ++p) {
-        err = fused ? h->ops->rk_stage_fused_part(a, p, h->stream) : h->ops->rk_stage_part(a, p, h->stream);
+        err = h->ops->rk_stage_part(a, p, h->stream);
         if (err == cudaSuccess) err = cudaEventRecord(ev[++k], h->stream);
       }
     }
@@ -1283,7 +1246,7 @@ int dns_profile_steps(dns_handle* h, int n, double* ms, int* launches, int nclas
   for (auto& e : ev) cudaEventDestroy(e);
   if (err != cudaSuccess) return cuda_fail(err, "dns_profile_steps");
   h->t += n * h->dt;
-  return check_plane_error(h, "dns_profile_steps");
+  return DNS_OK;
 }
 
 size_t dns_device_bytes(const dns_handle* h) { return h ? h->bytes : 0; }
@@ -1291,21 +1254,6 @@ size_t dns_device_bytes(const dns_handle* h) { return h ? h->bytes : 0; }
 const char* dns_last_error(const dns_handle* h) {
   (void)h;
   return g_err.c_str();
-}
-
-int dns_debug_plane_wait_timeout(dns_handle* h) {
-  int rc = check_handle(h);
-  if (rc) return rc;
-  if (!h->ops->plane_wait_test || !h->ctl)
-    return fail(DNS_ERR_UNSUPPORTED, "dns_debug_plane_wait_timeout: N = %d has no plane pass", h->N);
-  if ((rc = use_device(h))) return rc;
-  PassArgs a = base_args(h);
-  set_stage(h, 0, a);
-  h->w_valid = false;  // W is left partly transformed; the next step re-primes it
-  DNS_CUDA(h->ops->plane_wait_test(a, h->stream), "dns_debug_plane_wait_timeout");
-  rc = check_plane_error(h, "dns_debug_plane_wait_timeout");
-  if (rc == DNS_OK) return fail(DNS_ERR_ARG, "dns_debug_plane_wait_timeout: the waits did not give up");
-  return rc;
 }
 
 int dns_measure_fp64_peak(double* tflops) {
@@ -1591,7 +1539,7 @@ int dns_ensemble_tune(dns_ensemble* e, int* best_streams) {
   // member (its state is kept), applied to every member of the class
   int rc = DNS_OK;
   std::vector<const DnsOps*> done_ops;
-  std::vector<std::array<int, 5>> done_tiles;  // y-inverse, y-forward, z widths, radix plan, schedule
+  std::vector<std::array<int, 4>> done_tiles;  // y-inverse, y-forward, z widths, radix plan
   for (dns_handle* h : e->m) {
     size_t k = 0;
     while (k < done_ops.size() && done_ops[k] != h->ops) ++k;
@@ -1599,14 +1547,13 @@ int dns_ensemble_tune(dns_ensemble* e, int* best_streams) {
       int ti = 0, tf = 0, tz = 0;
       if ((rc = dns_tune_tiles(h, 5, &ti, &tf, &tz))) return rc;
       done_ops.push_back(h->ops);
-      done_tiles.push_back({ti, tf, tz, h->plan, h->fused});
+      done_tiles.push_back({ti, tf, tz, h->plan});
     } else if (h->ytile[0] != done_tiles[k][0] || h->ytile[1] != done_tiles[k][1] || h->ztile != done_tiles[k][2] ||
-               h->plan != done_tiles[k][3] || h->fused != done_tiles[k][4]) {
+               h->plan != done_tiles[k][3]) {
       h->ytile[0] = done_tiles[k][0];
       h->ytile[1] = done_tiles[k][1];
       h->ztile = done_tiles[k][2];
       h->plan = done_tiles[k][3];
-      h->fused = done_tiles[k][4];
       h->graph_dirty = true;
       ++h->epoch;
       h->w_valid = false;

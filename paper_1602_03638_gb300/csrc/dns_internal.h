@@ -45,17 +45,17 @@ struct PassArgs {
   int ytile[2] = {0, 0};  // y-pass tile widths of the stage launches (inverse, forward); 0 = default
   int ztile = 0;          // z-pass tile width of the stage launches; 0 = default
   int plan = 0;           // radix plan variant per pass of the stage launches: bit PLAN_* set = AltPlan
-  // Row flag of the state (nullptr: not used). *rows == 0 when the state vanishes on every
-  // row (kz, ky) outside the 2/3 box; the RK stage keeps those rows zero (no nonlinear term
-  // there, the viscous term is proportional to u_hat), so the stage's passes skip them: the
-  // x-stage and x inverse leave their rows unwritten, the y-inverse transforms only the
-  // planes kz < kc and reads the rows outside the box as zeros, the z-pass reads only
-  // kz < kc. The results are those of the full transforms (the skipped terms are zeros).
-  const int* rows = nullptr;
+  // Support of the state (PRUNE_*): PRUNE_ROWS when it vanishes on every row (kz, ky)
+  // outside the 2/3 box, PRUNE_BOX when it also vanishes at |kx| >= N/3 on the rows inside.
+  // The RK stage keeps such zeros (no nonlinear term there, the viscous term is
+  // proportional to u_hat), so the stage's passes skip them: the x-stage and x inverse
+  // leave the rows outside unwritten (and with PRUNE_BOX read and write the kept columns
+  // only), the y-inverse transforms only the planes kz < kc and reads the rows outside the
+  // box as zeros, the z-pass reads only kz < kc. The results are those of the full
+  // transforms (the skipped terms are zeros).
+  int prune = 0;
   const void* in = nullptr;  // physical input (3,Nx,Ny,Nz) for set_state
   void* out = nullptr;       // physical output (3,Nx,Ny,Nz) / RHS output
-  int* ctl = nullptr;  // plane-pass control block (error flag, queue head, per-plane counters)
-  int plane_lag = 0;   // plane-pass lag in queue steps (0: chosen from the block count)
   double* partials = nullptr;          // diagnostics block partials
   unsigned long long* maxbits = nullptr;  // diagnostics max|div| (bits of a double)
 };
@@ -91,23 +91,14 @@ struct DnsOps {
   int (*y_tiles)(int* tiles, int max);
   // the same for the z-pass
   int (*z_tiles)(int* tiles, int max);
-  // Plane-pass schedule (nullptr where not compiled): the stage as two launches,
-  // z-pass then one persistent plane pass (y-forward, x-stage, y-inverse walked by
-  // kz plane); W then holds the x- and y-inverse of u and omega between stages.
-  // prime_fused brings W into that form from the state (x inverse, then y inverse).
-  cudaError_t (*rk_stage_fused)(const PassArgs& a, cudaStream_t s);
-  cudaError_t (*prime_fused)(const PassArgs& a, int from_stage, cudaStream_t s);
-  // part 0: z-pass (with the control-block reset), part 1: plane pass
-  cudaError_t (*rk_stage_fused_part)(const PassArgs& a, int part, cudaStream_t s);
-  // one plane pass whose queue starts at its first y-inverse item of plane 0, so
-  // that its waits cannot be met (test of the bounded waits)
-  cudaError_t (*plane_wait_test)(const PassArgs& a, cudaStream_t s);
-  int plane_ctl_words;  // ints of the plane-pass control block (0: no plane pass)
   int NY, NZ;  // points along y and z (N is the count along x)
   int TW;      // length of the twiddle table exp(-2 pi i t / TW) (a multiple of N, NY, NZ)
   int plans;   // radix plan variants the stage launches offer (1: the default only, 2: AltPlan too)
   int default_plan;  // the plan mask a new handle starts with
 };
+
+// values of PassArgs::prune
+constexpr int PRUNE_NONE = 0, PRUNE_ROWS = 1, PRUNE_BOX = 2;
 
 // bits of PassArgs::plan: the radix plan variant of each pass of a stage
 constexpr int PLAN_X = 0, PLAN_YI = 1, PLAN_Z = 2, PLAN_YF = 3, PLAN_BITS = 4;

@@ -115,8 +115,10 @@ __device__ __forceinline__ T par(double d, float f) {
   else return d;
 }
 __device__ __forceinline__ bool kept(int k, int kmax3) { return 3 * (k < 0 ? -k : k) < kmax3; }
-// The state vanishes on every row (kz, ky) outside the 2/3 box (PassArgs::rows).
-__device__ __forceinline__ bool rows_vanish(const int* rows) { return rows != nullptr && __ldg(rows) == 0; }
+// The support of the stage's state (PassArgs::prune): rows_vanish, it vanishes on every
+// row (kz, ky) outside the 2/3 box; box_vanish, at every mode outside the box.
+__device__ __forceinline__ bool rows_vanish(const PassArgs& a) { return a.prune >= PRUNE_ROWS; }
+__device__ __forceinline__ bool box_vanish(const PassArgs& a) { return a.prune == PRUNE_BOX; }
 
 // XM_STAGE2N: the stage update of Williamson's 2N low-storage form (a mode of its
 // own, so that the two-register stage update compiles without its branch)
@@ -145,17 +147,10 @@ __device__ __forceinline__ void put_curl_lines(cx<T>* s, int pos, int LS, cx<T> 
   p[5 * LS] = conjg(w2);
 }
 
-// Global store of one complex value; with HINT, marked evict-first in L2 (the
-// RK state the plane pass streams past the plane data it keeps in L2).
-template <bool HINT, typename T>
-__device__ __forceinline__ void st_state(cx<T>* p, cx<T> v, unsigned long long pol) {
-  if constexpr (!HINT) {
-    *p = v;
-  } else if constexpr (sizeof(T) == 4) {
-    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(v.x), "f"(v.y), "l"(pol) : "memory");
-  } else {
-    asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(p), "d"(v.x), "d"(v.y), "l"(pol) : "memory");
-  }
+// Global store of one complex value of the RK state.
+template <typename T>
+__device__ __forceinline__ void st_state(cx<T>* p, cx<T> v) {
+  *p = v;
 }
 
 // Global store of a forward-transformed state row with the Nyquist modes zeroed.
@@ -174,19 +169,12 @@ struct GStoreNyquistFree {
 // ---------------------------------------------------------------------------
 // x-pass: one block owns one row (kz, ky) of length N; warp f transforms line f.
 // ---------------------------------------------------------------------------
-// NT: threads of the calling block (XP_THREADS for k_xpass; the plane pass runs the
-// stage update with 256, its warps 6 and 7 idle during the line transforms).
 // NY, NZ: points along y and z where they differ from N (rows kz * NY + ky).
 // V: radix plan variant of the line transforms (SmemPlanV).
-template <typename T, int N, int MODE, int NT = XP_THREADS, int NY = N, int NZ = N, int V = 0>
+template <typename T, int N, int MODE, int NY = N, int NZ = N, int V = 0>
 __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
-  static_assert(NT >= XP_THREADS && NT % 32 == 0, "the x-pass needs at least one warp per line");
-  // in the plane pass the RK state is a stream past the plane data kept in L2 (FP32
-  // instances only: the hinted FP64 512^3 plane pass raised an illegal-instruction
-  // fault whose cause was not found, so FP64 keeps plain accesses)
+  constexpr int NT = XP_THREADS;  // one warp per line of u and omega
   constexpr bool STAGE = MODE == XM_STAGE || MODE == XM_STAGE2N;  // a stage update (either form)
-  constexpr bool HINT = NT != XP_THREADS && STAGE && sizeof(T) == 4;
-  const unsigned long long pol = HINT ? l2_evict_first_policy() : 0ull;
   using G = Geometry<T, N, NY, NZ>;
   constexpr int LS = G::XLS;
   constexpr size_t FS = G::FS;
@@ -212,7 +200,7 @@ __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
   const int k3y = NY == N ? a.kmax3 : a.kmax3y, k3z = NZ == N ? a.kmax3 : a.kmax3z;
   const bool row_kept = (3 * kz < k3z) && kept(kfreq(ky, NY), k3y);
   if constexpr (STAGE || MODE == XM_INV_CURL) {
-    if (!row_kept && rows_vanish(a.rows)) return;
+    if (!row_kept && rows_vanish(a)) return;
   }
 
   if constexpr (STAGE || MODE == XM_RHS) {
@@ -227,6 +215,10 @@ __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
     // last of the two-register form)
     const bool need1 = STAGE && stage > 0, need0 = STAGE && stage > 0 && stage < last && !lsrk;
     cx<T>* const st = s + G::XST;  // XPRE: rows [Sst 0..2][U1 0..2][U 0..2], N values each
+    // a state that vanishes at every mode outside the box (box_vanish) keeps vanishing at
+    // the columns |kx| >= N/3 of this row too: its rows are read and written at the kept
+    // columns only, the others give u = omega = 0
+    const bool xbox = STAGE && box_vanish(a);
     if constexpr (G::XPRE) {
       if (row_kept) {
         for (int e = threadIdx.x; e < 3 * N; e += NT) {
@@ -239,8 +231,10 @@ __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
       auto fetch_rows = [&](const cx<T>* src, cx<T>* dst) {
         for (int e = threadIdx.x; e < 3 * N / PK; e += NT) {
           const int f = (e * PK) / N, j = (e * PK) % N;
-          if constexpr (HINT) cp_async16_hint(dst + f * N + j, src + f * FS + rb + j, pol);
-          else cp_async<16>(dst + f * N + j, src + f * FS + rb + j);
+          // the columns outside the box are one contiguous range: a copy none of whose
+          // columns is kept has both ends outside
+          if (xbox && !kept(kfreq(j, N), a.kmax3) && !kept(kfreq(j + PK - 1, N), a.kmax3)) continue;
+          cp_async<16>(dst + f * N + j, src + f * FS + rb + j);
         }
       };
       fetch_rows(Sst, st);
@@ -290,7 +284,9 @@ __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
         // P = (k . N_hat) / |k|^2   (Eq. mod_pressure without the factor i)
         const cx<T> p = mk((kx * n0.x + kyv * n1.x + kzv * n2.x) * ik2, (kx * n0.y + kyv * n1.y + kzv * n2.y) * ik2);
         const size_t gi = rb + j;
-        const cx<T> u0 = ld_s(0, j), u1 = ld_s(1, j), u2 = ld_s(2, j);
+        const bool xin = !xbox || kept(kxi, a.kmax3);
+        const cx<T> zero = mk((T)0, (T)0);
+        const cx<T> u0 = xin ? ld_s(0, j) : zero, u1 = xin ? ld_s(1, j) : zero, u2 = xin ? ld_s(2, j) : zero;
         const T nk2 = nu * k2;
         // dU = N_hat - k P - nu |k|^2 u_hat   (Eq. NSfinal)
         const cx<T> d0 = mk(n0.x - kx * p.x - nk2 * u0.x, n0.y - kx * p.y - nk2 * u0.y);
@@ -302,8 +298,10 @@ __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
           out[FS + gi] = d1;
           out[2 * FS + gi] = d2;
         } else {
-          cx<T> v0, v1, v2;
-          if constexpr (lsrk) {  // 2N stage: dU <- A_s dU + dt RHS, u <- u + B_s dU
+          cx<T> v0 = zero, v1 = zero, v2 = zero;
+          if (!xin) {
+            // outside the box: the state stays zero there and is not written
+          } else if constexpr (lsrk) {  // 2N stage: dU <- A_s dU + dt RHS, u <- u + B_s dU
             const T cC = par<T>(a.cC, a.f_cC);
             cx<T> e0 = scal(d0, cC), e1 = scal(d1, cC), e2 = scal(d2, cC);
             if (stage > 0) {
@@ -312,51 +310,51 @@ __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
               e2 = e2 + scal(ld_1(2, j), cA);
             }
             if (stage < last) {
-              st_state<HINT>(U1 + gi, e0, pol);
-              st_state<HINT>(U1 + FS + gi, e1, pol);
-              st_state<HINT>(U1 + 2 * FS + gi, e2, pol);
+              st_state(U1 + gi, e0);
+              st_state(U1 + FS + gi, e1);
+              st_state(U1 + 2 * FS + gi, e2);
             }
             v0 = u0 + scal(e0, cB);
             v1 = u1 + scal(e1, cB);
             v2 = u2 + scal(e2, cB);
-            st_state<HINT>(U + gi, v0, pol);
-            st_state<HINT>(U + FS + gi, v1, pol);
-            st_state<HINT>(U + 2 * FS + gi, v2, pol);
+            st_state(U + gi, v0);
+            st_state(U + FS + gi, v1);
+            st_state(U + 2 * FS + gi, v2);
           } else if (stage == 0 && last == 0) {  // one-stage step (forward Euler): u += a_0 dt dU
             v0 = u0 + scal(d0, cA);
             v1 = u1 + scal(d1, cA);
             v2 = u2 + scal(d2, cA);
-            st_state<HINT>(U + gi, v0, pol);
-            st_state<HINT>(U + FS + gi, v1, pol);
-            st_state<HINT>(U + 2 * FS + gi, v2, pol);
+            st_state(U + gi, v0);
+            st_state(U + FS + gi, v1);
+            st_state(U + 2 * FS + gi, v2);
           } else if (stage == 0) {
-            st_state<HINT>(U1 + gi, u0 + scal(d0, cA), pol);
-            st_state<HINT>(U1 + FS + gi, u1 + scal(d1, cA), pol);
-            st_state<HINT>(U1 + 2 * FS + gi, u2 + scal(d2, cA), pol);
+            st_state(U1 + gi, u0 + scal(d0, cA));
+            st_state(U1 + FS + gi, u1 + scal(d1, cA));
+            st_state(U1 + 2 * FS + gi, u2 + scal(d2, cA));
             v0 = u0 + scal(d0, cB);
             v1 = u1 + scal(d1, cB);
             v2 = u2 + scal(d2, cB);
-            st_state<HINT>(US + gi, v0, pol);
-            st_state<HINT>(US + FS + gi, v1, pol);
-            st_state<HINT>(US + 2 * FS + gi, v2, pol);
+            st_state(US + gi, v0);
+            st_state(US + FS + gi, v1);
+            st_state(US + 2 * FS + gi, v2);
           } else if (stage < last) {
             const cx<T> b0 = ld_0(0, j), b1 = ld_0(1, j), b2 = ld_0(2, j);
-            st_state<HINT>(U1 + gi, ld_1(0, j) + scal(d0, cA), pol);
-            st_state<HINT>(U1 + FS + gi, ld_1(1, j) + scal(d1, cA), pol);
-            st_state<HINT>(U1 + 2 * FS + gi, ld_1(2, j) + scal(d2, cA), pol);
+            st_state(U1 + gi, ld_1(0, j) + scal(d0, cA));
+            st_state(U1 + FS + gi, ld_1(1, j) + scal(d1, cA));
+            st_state(U1 + 2 * FS + gi, ld_1(2, j) + scal(d2, cA));
             v0 = b0 + scal(d0, cB);
             v1 = b1 + scal(d1, cB);
             v2 = b2 + scal(d2, cB);
-            st_state<HINT>(US + gi, v0, pol);
-            st_state<HINT>(US + FS + gi, v1, pol);
-            st_state<HINT>(US + 2 * FS + gi, v2, pol);
+            st_state(US + gi, v0);
+            st_state(US + FS + gi, v1);
+            st_state(US + 2 * FS + gi, v2);
           } else {
             v0 = ld_1(0, j) + scal(d0, cA);
             v1 = ld_1(1, j) + scal(d1, cA);
             v2 = ld_1(2, j) + scal(d2, cA);
-            st_state<HINT>(U + gi, v0, pol);
-            st_state<HINT>(U + FS + gi, v1, pol);
-            st_state<HINT>(U + 2 * FS + gi, v2, pol);
+            st_state(U + gi, v0);
+            st_state(U + FS + gi, v1);
+            st_state(U + 2 * FS + gi, v2);
           }
           if constexpr (G::XPRE && !G::XWIDE) {
             // u into lines 0-2 (padded, where this thread read N_hat), omega into
@@ -380,7 +378,6 @@ __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
       columns(std::true_type{});
     if constexpr (STAGE) {
       __syncthreads();
-      if (NT > XP_THREADS && warp >= 6) return;  // one warp per line of u and omega
       if constexpr (G::XPRE && !G::XWIDE) {
         if (warp < 3) {
           const SLine<T, 1> line{s + warp * LS};
@@ -405,10 +402,13 @@ __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
     // inverse x transform of u and omega (XM_INV_CURL), of u alone
     // (XM_INV_PLAIN) or of i k . u (XM_INV_DIV), all scaled by 1/N^3
     constexpr int NF = (MODE == XM_INV_CURL) ? 6 : (MODE == XM_INV_PLAIN ? 3 : 1);
+    const bool xbox = MODE == XM_INV_CURL && box_vanish(a);  // columns |kx| >= N/3 hold zeros
     for (int j = threadIdx.x; j < N; j += NT) {
       const size_t gi = rb + j;
       const int pj = padp(j);
-      const cx<T> u0 = U[gi], u1 = U[FS + gi], u2 = U[2 * FS + gi];
+      const bool xin = !xbox || kept(kfreq(j, N), a.kmax3);
+      const cx<T> zero = mk((T)0, (T)0);
+      const cx<T> u0 = xin ? U[gi] : zero, u1 = xin ? U[FS + gi] : zero, u2 = xin ? U[2 * FS + gi] : zero;
       const T kx = (T)kfreq(j, N) * ksx;
       if constexpr (MODE == XM_INV_CURL) {
         put_curl_lines<T>(s, pj, LS, u0, u1, u2, kx, kyv, kzv, sc);
@@ -432,13 +432,13 @@ __device__ __forceinline__ void xpass_body(const PassArgs a, const int bx) {
 
 template <typename T, int N, int MODE, int NY = N, int NZ = N, int V = 0>
 __global__ void __launch_bounds__(XP_THREADS, (Geometry<T, N, NY, NZ>::XMIN)) k_xpass(PassArgs a) {
-  xpass_body<T, N, MODE, XP_THREADS, NY, NZ, V>(a, blockIdx.x);
+  xpass_body<T, N, MODE, NY, NZ, V>(a, blockIdx.x);
 }
 
 // Batched form (ensembles): member blockIdx.y, its arguments in B.a[blockIdx.y].
 template <typename T, int N, int MODE, int V = 0>
 __global__ void __launch_bounds__(XP_THREADS, (Geometry<T, N>::XMIN)) k_xpass_b(const __grid_constant__ BatchArgs B) {
-  xpass_body<T, N, MODE, XP_THREADS, N, N, V>(B.a[blockIdx.y], blockIdx.x);
+  xpass_body<T, N, MODE, N, N, V>(B.a[blockIdx.y], blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -465,16 +465,27 @@ __device__ __forceinline__ int ywalk_row(int r) {
 
 // Fill of a y tile (TX columns of L rows, row stride `stride` in global memory) whose rows
 // outside the 2/3 box are zeros: the kept rows |ky| <= R (R = (kmax3 - 1) / 3, rows 0 .. R
-// and L - R .. L - 1) by cp.async, the rows R + 1 .. L - R - 1 between them as zeros.
+// and L - R .. L - 1) by cp.async (in the bank-friendly walk order where it permutes the
+// rows), the rows R + 1 .. L - R - 1 between them as zeros.
 template <typename T, int L, int TX, int LD, int NT>
-__device__ __forceinline__ void ytile_fill_kept(cx<T>* s, const cx<T>* __restrict__ base, int stride, int kmax3) {
+__device__ __noinline__ void ytile_fill_kept(cx<T>* s, const cx<T>* __restrict__ base, int stride, int kmax3) {
   int R = (kmax3 - 1) / 3;
   if (R > L / 2 - 1) R = L / 2 - 1;
   const int lo = R + 1, gap = L - 2 * R - 1;  // kept rows [0, lo) and [lo + gap, L)
-  for (int e = threadIdx.x; e < TX * (L - gap); e += NT) {
-    const int x = e % TX, r = e / TX, y = r < lo ? r : r + gap;
-    cp_async<sizeof(cx<T>)>(s + padp(y) * LD + x, base + (size_t)y * stride + x);
+  if constexpr (sizeof(cx<T>) == 8 && TX == 8 && L % 16 == 0) {
+#pragma unroll 8
+    for (int e = threadIdx.x; e < TX * L; e += NT) {
+      const int x = e % TX, y = ywalk_row<T, TX, L>(e / TX);
+      if (y < lo || y >= lo + gap) cp_async<sizeof(cx<T>)>(s + padp(y) * LD + x, base + (size_t)y * stride + x);
+    }
+  } else {
+#pragma unroll 8
+    for (int e = threadIdx.x; e < TX * (L - gap); e += NT) {
+      const int x = e % TX, r = e / TX, y = r < lo ? r : r + gap;
+      cp_async<sizeof(cx<T>)>(s + padp(y) * LD + x, base + (size_t)y * stride + x);
+    }
   }
+#pragma unroll 4
   for (int e = threadIdx.x; e < TX * gap; e += NT) {
     const int x = e % TX, y = lo + e / TX;
     s[padp(y) * LD + x] = mk((T)0, (T)0);
@@ -525,12 +536,12 @@ __device__ __forceinline__ void ypass_tile(cx<T>* __restrict__ base, const cx<T>
 
 // NY, NZ: points along y and z where they differ from N (N: the x extent, the
 // row stride of the tile's columns).
-// rows, kcz (inverse of a stage): where the state vanishes outside the 2/3 box
-// (rows_vanish), the planes kz >= kcz are left alone (zeros that the z-pass does not
-// read) and the rows with |ky| >= NY/3 (kmax3) are read as zeros.
-template <typename T, int N, int INV, int PRUNE, int TXO = 0, int NY = N, int NZ = N, int V = 0>
+// PR (inverse of a stage whose state vanishes outside the 2/3 box): the grid covers the
+// planes kz < kc only (the others hold zeros that the z-pass does not read) and the rows
+// with |ky| >= NY/3 (kmax3) are read as zeros.
+template <typename T, int N, int INV, int PRUNE, int TXO = 0, int NY = N, int NZ = N, int V = 0, int PR = 0>
 __global__ void __launch_bounds__(YCfg<T, N, INV, TXO, NY>::THREADS, (YCfg<T, N, INV, TXO, NY>::MINB))
-    k_ypass(cx<T>* __restrict__ F, const cx<T>* __restrict__ tw, int kmax3, const int* rows, int kcz) {
+    k_ypass(cx<T>* __restrict__ F, const cx<T>* __restrict__ tw, int kmax3) {
   using G = Geometry<T, N, NY, NZ>;
   using Y = YCfg<T, N, INV, TXO, NY>;
   constexpr int TX = Y::TX;
@@ -539,12 +550,10 @@ __global__ void __launch_bounds__(YCfg<T, N, INV, TXO, NY>::THREADS, (YCfg<T, N,
   extern __shared__ unsigned char smraw[];
   cx<T>* s = reinterpret_cast<cx<T>*>(smraw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const bool vanish = INV && rows_vanish(rows);
-  if (vanish && (int)blockIdx.y >= kcz) return;
   cx<T>* base = F + blockIdx.z * G::FS + (size_t)blockIdx.y * NY * N + blockIdx.x * TX;
   // the whole tile in flight at once (cp.async, no register staging); the
   // inverse's conjugation is applied when the first pass reads it
-  if (vanish) {
+  if constexpr (INV && PR) {
     ytile_fill_kept<T, NY, TX, LD, NT>(s, base, N, kmax3);
   } else {
 #pragma unroll 8
@@ -580,7 +589,7 @@ __global__ void __launch_bounds__(YCfg<T, N, INV, TXO>::THREADS, (YCfg<T, N, INV
   using G = Geometry<T, N>;
   using Y = YCfg<T, N, INV, TXO>;
   const PassArgs& a = B.a[blockIdx.z / fields];
-  const bool vanish = INV && rows_vanish(a.rows);  // the member's planes kz >= kc are not transformed
+  const bool vanish = INV && rows_vanish(a);  // the member's planes kz >= kc are not transformed
   if (vanish && 3 * (int)blockIdx.y >= a.kmax3) return;
   cx<T>* base = reinterpret_cast<cx<T>*>(a.W) + (blockIdx.z % fields) * G::FS + (size_t)blockIdx.y * N * N +
                 blockIdx.x * Y::TX;
@@ -629,7 +638,7 @@ __device__ __forceinline__ void zpass_body(const PassArgs a, const int bx, const
     // (the y-inverse left them alone) and are filled with zeros instead of read
     int klim = M;
     if constexpr (MODE == ZM_CROSS) {
-      if (rows_vanish(a.rows)) {
+      if (rows_vanish(a)) {
         klim = ((NZ == N ? a.kmax3 : a.kmax3z) + 2) / 3;
         if (klim > M) klim = M;
       }
@@ -885,7 +894,7 @@ __global__ void __launch_bounds__(32 * ZCrossWarps<T, N>::value, (ZCrossWarps<T,
   const cx<T>* gl = W + ((size_t)(ZW::S * kq) * N + y) * N + x0 + tx;
   cx<T>* sl = s + (ZW::S * kq) * LD + tx;
 
-  if (rows_vanish(a.rows)) {  // planes kz >= kc of a state that vanishes outside the 2/3 box: zeros
+  if (rows_vanish(a)) {  // planes kz >= kc of a state that vanishes outside the 2/3 box: zeros
     for (int it = w; it < 6 * ZW::ITEMS; it += NW) {
       const int f = it / ZW::ITEMS, r = it % ZW::ITEMS, g = r / ZW::S, c = r % ZW::S;
       sl[(17 * g + c) * LD + f * TX] =
@@ -1057,7 +1066,7 @@ __global__ void __launch_bounds__(32 * Z16P<T>::NW, 1) k_zcross16p(PassArgs a) {
     const int f = f0 + w / 8, g = w % 8;
     const cx<T>* gl = W + lane_g + (size_t)(t / XT) * N + (t % XT) * TX + (size_t)f * FS + (size_t)(32 * g) * N * N;
     cx<T>* sd = sl + 34 * g * LD + f * TX;
-    if (rows_vanish(a.rows)) {
+    if (rows_vanish(a)) {
       const int nv = kc - (32 * g + TX * kq);  // rows of this lane's chunk below kc
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
@@ -1328,7 +1337,7 @@ __global__ void __launch_bounds__(32 * Z32P<T>::NW, 1) k_zcross32p(PassArgs a) {
     const int f = f0 + w / 4, q = w % 4;
     const cx<T>* gl = W + lane_g + (size_t)(t / XT) * N + (t % XT) * TX + (size_t)f * FS + (size_t)(128 * q) * N * N;
     cx<T>* sd = sl + 136 * q * LD + f * TX;
-    if (rows_vanish(a.rows)) {
+    if (rows_vanish(a)) {
       const int nv = kc - (128 * q + TX * kq);  // this lane's rows below kc: 32 (j / 8) + j % 8 < nv
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
@@ -1542,7 +1551,7 @@ __global__ void __launch_bounds__(32 * Z8Q<T>::NW, 2) k_zcross8q(PassArgs a) {
     const int f = w / 2, q = w % 2;
     const cx<T>* gf = gl + (size_t)f * FS + (size_t)(64 * q) * PL;
     cx<T>* sd = sl + 68 * q * LD + f * TX;
-    if (rows_vanish(a.rows)) {  // planes kz >= kc of a state that vanishes outside the 2/3 box: zeros
+    if (rows_vanish(a)) {  // planes kz >= kc of a state that vanishes outside the 2/3 box: zeros
       const int nv = kc - (64 * q + TX * kq);
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
@@ -1697,194 +1706,6 @@ __global__ void __launch_bounds__(DG_THREADS) k_diag(PassArgs a) {
 __global__ void k_diag_final(double* partials, int nblocks);
 
 // ---------------------------------------------------------------------------
-// Plane pass: the y-forward, x-stage and y-inverse of one RK stage in ONE
-// persistent launch, walked in kz-plane order so that each plane's data passes
-// from one step to the next through L2 instead of HBM. The three steps of a
-// stage are local to a kz plane (they transform along y and x only): the y
-// forward of plane p feeds the x-stage rows of plane p, whose u and omega feed
-// the y inverse of plane p. Only the z-pass, a separate launch, couples planes
-// (the change of pass direction that replaces the paper's slab transposes,
-// Sec. 3.2).
-//
-// Work is taken in chunks (CYF y-forward tiles, CX x-stage rows or CYI y-inverse
-// tiles of one plane) from one atomic counter, in a fixed order of steps q:
-//   step q = [Yf(q) if q < kc] [X(q - L) if L <= q < M + L] [Yi(q - 2L) if q >= 2L]
-// so that a plane's x-stage rows come L steps after its y-forward tiles and its
-// y-inverse tiles L steps after its rows (L, the lag, is chosen by the host so
-// that L steps span more chunks than there are blocks: the producers are done
-// when their consumers are taken). X(p) waits until every Yf(p) chunk is
-// released, Yi(p) until every X(p) chunk is; each warp releases its own stores
-// (red.release after __syncwarp), so a chunk counts PLANE_THREADS / 32 releases.
-// Every chunk a chunk waits for comes earlier in the order and was taken by a
-// block that is running (or holds it as its prefetched next chunk while it
-// finishes an earlier one), so the earliest unfinished chunk always progresses:
-// no residency assumption is needed. A wait still gives up after PLANE_WAIT_NS
-// (an error flag that the host reports as DNS_ERR_TIMEOUT and a stop flag that
-// ends every block's loop).
-// ---------------------------------------------------------------------------
-constexpr int PLANE_THREADS = 256;
-constexpr int PLANE_WARPS = PLANE_THREADS / 32;
-// control block: [0] error (sticky; cleared by the host when reported), [1] queue
-// head, [2] stop flag, [3] unused, then the per-plane counters yf_done[M], x_done[M].
-// Words 1.. are zeroed before every launch.
-constexpr int PLANE_CTL_ERR = 0, PLANE_CTL_HEAD = 1, PLANE_CTL_STOP = 2, PLANE_CTL_WORDS = 4;
-constexpr unsigned long long PLANE_WAIT_NS = 1000000000ull;  // 1 s
-
-template <typename T, int N>
-struct PlaneCfg {
-  using YI = YCfg<T, N, 1>;
-  using YF = YCfg<T, N, 0>;
-  static constexpr int NTI = N / YI::TX;  // y-inverse tiles per field and plane
-  static constexpr int NTF = N / YF::TX;  // y-forward tiles per field and plane
-  static constexpr int CX = 4, CYF = 2, CYI = 2;  // rows / tiles per chunk
-  static constexpr int NYF = 3 * NTF / CYF;  // y-forward chunks per plane
-  static constexpr int NX = N / CX;          // x-stage chunks per plane
-  static constexpr int NYI = 6 * NTI / CYI;  // y-inverse chunks per plane
-  static constexpr bool enabled = N >= 256;
-  static_assert(!enabled || (3 * NTF % CYF == 0 && N % CX == 0 && 6 * NTI % CYI == 0), "plane-pass chunks");
-  static constexpr int MINB = (sizeof(T) == 4 && N <= 512) ? 3 : 2;
-  static constexpr size_t SMEM_Y = YI::SMEM > YF::SMEM ? YI::SMEM : YF::SMEM;
-  static constexpr int ctl_words() { return PLANE_CTL_WORDS + N; }  // 2 counters per plane, M = N/2 planes
-  // the lag: L steps hold at least 1.5x as many chunks as the launch has blocks
-  static int lag(int blocks) {
-    const int per_step = NYF + NX + NYI;
-    int L = (3 * blocks + 2 * per_step - 1) / (2 * per_step);
-    return L < 1 ? 1 : (L > 8 ? 8 : L);
-  }
-};
-
-__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void red_release_gpu(int* p, int v) {
-  asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Waits until *cnt >= target; false if the pass was stopped or the wait gave up.
-static __device__ __noinline__ bool plane_wait(const int* cnt, int target, int* ctl) {
-  const unsigned long long t0 = global_ns();
-  for (;;) {
-    __nanosleep(64);
-    if (ld_acquire_gpu(cnt) >= target) return true;
-    if (ld_acquire_gpu(ctl + PLANE_CTL_STOP)) return false;
-    if (global_ns() - t0 > PLANE_WAIT_NS) {
-      atomicExch(ctl + PLANE_CTL_ERR, 1);
-      atomicExch(ctl + PLANE_CTL_STOP, 1);
-      return false;
-    }
-  }
-}
-
-template <typename T, int N>
-__device__ __forceinline__ int plane_step_chunks(int q, int kc, int L) {
-  using P = PlaneCfg<T, N>;
-  constexpr int M = N / 2;
-  return (q < kc ? P::NYF : 0) + (q >= L && q < M + L ? P::NX : 0) + (q >= 2 * L ? P::NYI : 0);
-}
-
-template <typename T, int N>
-__global__ void __launch_bounds__(PLANE_THREADS, (PlaneCfg<T, N>::MINB))
-    k_plane(PassArgs a, int* __restrict__ ctl, int L) {
-  using G = Geometry<T, N>;
-  using P = PlaneCfg<T, N>;
-  constexpr int M = N / 2;
-  __shared__ int s_kind, s_plane, s_chunk;
-  int kc = (a.kmax3 + 2) / 3;
-  if (kc > M) kc = M;
-  int* yf_done = ctl + PLANE_CTL_WORDS;
-  int* x_done = yf_done + M;
-  const int total = P::NYF * kc + P::NX * M + P::NYI * M;
-  cx<T>* W = reinterpret_cast<cx<T>*>(a.W);
-  const cx<T>* tw = reinterpret_cast<const cx<T>*>(a.tw);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // thread 0: the prefetched next chunk, and the cursor of the queue (step q
-  // holds chunks [qbeg, qbeg + plane_step_chunks(q)))
-  int nxt = 0, q = 0, qbeg = 0;
-  if (threadIdx.x == 0) nxt = atomicAdd(ctl + PLANE_CTL_HEAD, 1);
-  for (;;) {
-    if (threadIdx.x == 0) {
-      int kind = -1, plane = 0, chunk = 0;
-      const int item = nxt;
-      if (item < total) {
-        int n = plane_step_chunks<T, N>(q, kc, L);
-        while (item >= qbeg + n) {
-          qbeg += n;
-          ++q;
-          n = plane_step_chunks<T, N>(q, kc, L);
-        }
-        const int r = item - qbeg;
-        const int nyf = q < kc ? P::NYF : 0;
-        const int nx = (q >= L && q < M + L) ? P::NX : 0;
-        const int* dep = nullptr;
-        int target = 0;
-        if (r < nyf) {
-          kind = 0;
-          plane = q;
-          chunk = r;
-        } else if (r < nyf + nx) {
-          kind = 1;
-          plane = q - L;
-          chunk = r - nyf;
-          if (plane < kc) {
-            dep = yf_done + plane;
-            target = P::NYF * PLANE_WARPS;
-          }
-        } else {
-          kind = 2;
-          plane = q - 2 * L;
-          chunk = r - nyf - nx;
-          dep = x_done + plane;
-          target = P::NX * PLANE_WARPS;
-        }
-        if (dep && ld_acquire_gpu(dep) < target && !plane_wait(dep, target, ctl)) kind = -1;
-        if (kind >= 0) nxt = atomicAdd(ctl + PLANE_CTL_HEAD, 1);  // used by the next iteration
-      }
-      s_kind = kind;
-      s_plane = plane;
-      s_chunk = chunk;
-    }
-    __syncthreads();  // publishes the chunk; the previous chunk's shared memory is free
-    const int kind = s_kind, plane = s_plane, chunk = s_chunk;
-    if (kind < 0) break;
-    if (kind == 0) {
-#pragma unroll 1
-      for (int k = 0; k < P::CYF; ++k) {
-        if (k) __syncthreads();
-        const int t = chunk * P::CYF + k;
-        cx<T>* base = W + (t / P::NTF) * G::FS + (size_t)plane * N * N + (t % P::NTF) * P::YF::TX;
-        ypass_tile<T, N, 0, 1, 0, PLANE_THREADS>(base, tw, a.kmax3);
-      }
-    } else if (kind == 1) {
-#pragma unroll 1
-      for (int k = 0; k < P::CX; ++k) {
-        if (k) __syncthreads();
-        if (a.lsrk) xpass_body<T, N, XM_STAGE2N, PLANE_THREADS>(a, plane * N + chunk * P::CX + k);
-        else xpass_body<T, N, XM_STAGE, PLANE_THREADS>(a, plane * N + chunk * P::CX + k);
-      }
-    } else {
-#pragma unroll 1
-      for (int k = 0; k < P::CYI; ++k) {
-        if (k) __syncthreads();
-        const int t = chunk * P::CYI + k;
-        cx<T>* base = W + (t / P::NTI) * G::FS + (size_t)plane * N * N + (t % P::NTI) * P::YI::TX;
-        ypass_tile<T, N, 1, 0, 0, PLANE_THREADS>(base, tw, a.kmax3);
-      }
-    }
-    if (kind < 2) {  // each warp releases its own stores of the chunk
-      __syncwarp();
-      if (lane == 0) red_release_gpu(kind == 0 ? yf_done + plane : x_done + plane, 1);
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
 // Host launchers for one (T, N).
 // ---------------------------------------------------------------------------
 // Number of SMs of the current device (persistent kernels launch one block each).
@@ -1901,8 +1722,8 @@ inline int num_sms() {
 }
 
 // NY, NZ: points along y and z where they differ from N (a non-cubic grid runs the
-// generic passes only: no tuned tile widths, specialised z-passes, batched
-// ensembles or plane pass).
+// generic passes only: no tuned tile widths, specialised z-passes or batched
+// ensembles).
 template <typename T, int N, int NY = N, int NZ = N>
 struct SolverImpl {
   using G = Geometry<T, N, NY, NZ>;
@@ -1910,7 +1731,6 @@ struct SolverImpl {
   static constexpr bool ISO = NY == N && NZ == N;
   static constexpr int ROWS = M * NY;  // x-pass rows (kz, ky)
   static constexpr bool BATCHED = ISO && N <= BATCH_MAX_N && !ZCross<T, N>::enabled;
-  static constexpr bool PLANE = ISO && PlaneCfg<T, N>::enabled;
   // non-cubic grids with 256-point FP32 z-lines use the quarter-warp z-pass of 256^3
   static constexpr bool Z8_BOX = !ISO && NZ == 256 && sizeof(T) == 4 && N % 16 == 0;
   // each direction's 2/3 cut-off (3|k_i| < kmax3 of that direction)
@@ -1964,6 +1784,7 @@ struct SolverImpl {
   template <int TXO, int V>
   static void tile_attr_v(cudaError_t& e) {
     if (e == cudaSuccess) e = smem_attr(k_ypass<T, N, 1, 0, TXO, N, N, V>, YCfg<T, N, 1, TXO>::SMEM);
+    if (e == cudaSuccess) e = smem_attr(k_ypass<T, N, 1, 0, TXO, N, N, V, 1>, YCfg<T, N, 1, TXO>::SMEM);
     if (e == cudaSuccess) e = smem_attr(k_ypass<T, N, 0, 1, TXO, N, N, V>, YCfg<T, N, 0, TXO>::SMEM);
     if constexpr (!ZCross<T, N>::enabled) {
       if (e == cudaSuccess) e = smem_attr(k_ypass_b<T, N, 1, 0, TXO, V>, YCfg<T, N, 1, TXO>::SMEM);
@@ -2010,32 +1831,33 @@ struct SolverImpl {
     constexpr int TX = TXO > 0 ? TXO : G::ZTX;
     k_zpass<T, N, ZM_CROSS, TXO, NY, NZ, V><<<dim3(N / TX, NY), ZP_THREADS, G::zbytes(TX), st>>>(a);
   }
-  // rows, kcz: the row flag of a stage's y-inverse and its plane limit (k_ypass)
-  template <int INV, int PRUNE, int TXO, int V = 0>
-  static void y_go(cx<T>* F, const cx<T>* tw, int kmax3, int planes, int fields, cudaStream_t st,
-                   const int* rows = nullptr, int kcz = 0) {
+  // PR: the y-inverse of a stage whose state vanishes outside the 2/3 box (k_ypass)
+  template <int INV, int PRUNE, int TXO, int V = 0, int PR = 0>
+  static void y_go(cx<T>* F, const cx<T>* tw, int kmax3, int planes, int fields, cudaStream_t st) {
     using Y = YCfg<T, N, INV, TXO, NY>;
-    k_ypass<T, N, INV, PRUNE, TXO, NY, NZ, V>
-        <<<dim3(N / Y::TX, planes, fields), Y::THREADS, Y::SMEM, st>>>(F, tw, kmax3, rows, kcz);
+    k_ypass<T, N, INV, PRUNE, TXO, NY, NZ, V, PR><<<dim3(N / Y::TX, planes, fields), Y::THREADS, Y::SMEM, st>>>(F, tw, kmax3);
   }
   // the stage's y-pass with tile width `tile` (0, or a width not offered: the default) and
-  // radix plan variant `plan`
+  // radix plan variant `plan`; pr (inverse only): the pruned form PR = 1
   template <int INV, int PRUNE>
   static void y_stage(int tile, int plan, cx<T>* F, const cx<T>* tw, int kmax3, int planes, int fields,
-                      cudaStream_t st, const int* rows = nullptr, int kcz = 0) {
+                      cudaStream_t st, bool pr = false) {
     with_plan(plan, [&](auto v) {
       constexpr int V = decltype(v)::value;
+      auto go = [&](auto t) {
+        constexpr int TXO = decltype(t)::value;
+        if constexpr (INV) {
+          if (pr) return y_go<INV, PRUNE, TXO, V, 1>(F, tw, kmax3, planes, fields, st);
+        }
+        y_go<INV, PRUNE, TXO, V, 0>(F, tw, kmax3, planes, fields, st);
+      };
       if constexpr (ISO && N <= BATCH_MAX_N) {
-        if constexpr (ytile_ok(4))
-          if (tile == 4) return y_go<INV, PRUNE, 4, V>(F, tw, kmax3, planes, fields, st, rows, kcz);
-        if constexpr (ytile_ok(8))
-          if (tile == 8) return y_go<INV, PRUNE, 8, V>(F, tw, kmax3, planes, fields, st, rows, kcz);
-        if constexpr (ytile_ok(16))
-          if (tile == 16) return y_go<INV, PRUNE, 16, V>(F, tw, kmax3, planes, fields, st, rows, kcz);
-        if constexpr (ytile_ok(32))
-          if (tile == 32) return y_go<INV, PRUNE, 32, V>(F, tw, kmax3, planes, fields, st, rows, kcz);
+        if constexpr (ytile_ok(4)) if (tile == 4) return go(std::integral_constant<int, 4>{});
+        if constexpr (ytile_ok(8)) if (tile == 8) return go(std::integral_constant<int, 8>{});
+        if constexpr (ytile_ok(16)) if (tile == 16) return go(std::integral_constant<int, 16>{});
+        if constexpr (ytile_ok(32)) if (tile == 32) return go(std::integral_constant<int, 32>{});
       }
-      y_go<INV, PRUNE, 0, V>(F, tw, kmax3, planes, fields, st, rows, kcz);
+      go(std::integral_constant<int, 0>{});
     });
   }
 
@@ -2059,6 +1881,7 @@ struct SolverImpl {
     DNS_ATTR((k_xpass<T, N, XM_INV_PLAIN, NY, NZ>), G::XSMEM);
     DNS_ATTR((k_xpass<T, N, XM_INV_DIV, NY, NZ>), G::XSMEM);
     DNS_ATTR((k_ypass<T, N, 1, 0, 0, NY, NZ>), (YCfg<T, N, 1, 0, NY>::SMEM));
+    DNS_ATTR((k_ypass<T, N, 1, 0, 0, NY, NZ, 0, 1>), (YCfg<T, N, 1, 0, NY>::SMEM));
     DNS_ATTR((k_ypass<T, N, 0, 1, 0, NY, NZ>), (YCfg<T, N, 0, 0, NY>::SMEM));
     DNS_ATTR((k_ypass<T, N, 0, 0, 0, NY, NZ>), (YCfg<T, N, 0, 0, NY>::SMEM));
     DNS_ATTR((k_zpass<T, N, ZM_CROSS, 0, NY, NZ>), G::ZSMEM);
@@ -2068,6 +1891,7 @@ struct SolverImpl {
       DNS_ATTR((k_xpass<T, N, XM_STAGE2N, N, N, 1>), G::XSMEM_ST);
       DNS_ATTR((k_xpass<T, N, XM_RHS, N, N, 1>), G::XSMEM_ST);
       DNS_ATTR((k_ypass<T, N, 1, 0, 0, N, N, 1>), (YCfg<T, N, 1, 0>::SMEM));
+      DNS_ATTR((k_ypass<T, N, 1, 0, 0, N, N, 1, 1>), (YCfg<T, N, 1, 0>::SMEM));
       DNS_ATTR((k_ypass<T, N, 0, 1, 0, N, N, 1>), (YCfg<T, N, 0, 0>::SMEM));
       DNS_ATTR((k_zpass<T, N, ZM_CROSS, 0, N, N, 1>), G::ZSMEM);
     }
@@ -2076,7 +1900,6 @@ struct SolverImpl {
     if constexpr (ISO && N == 1024 && sizeof(T) == 4) DNS_ATTR((k_zcross32p<T, N>), Z32P<T>::SMEM);
     if constexpr (ISO && N == 256 && sizeof(T) == 4) DNS_ATTR((k_zcross8q<T, N>), Z8Q<T>::SMEM);
     if constexpr (Z8_BOX) DNS_ATTR((k_zcross8q<T, N, NY, NZ>), Z8Q<T>::SMEM);
-    if constexpr (PLANE) DNS_ATTR((k_plane<T, N>), (plane_smem(1, 3)));
     DNS_ATTR((k_zpass<T, N, ZM_STORE, 0, NY, NZ>), G::ZSMEM);
     DNS_ATTR((k_zpass<T, N, ZM_LOAD, 0, NY, NZ>), G::ZSMEM);
     DNS_ATTR((k_zpass<T, N, ZM_MAXABS, 0, NY, NZ>), G::ZSMEM);
@@ -2151,10 +1974,11 @@ struct SolverImpl {
     return cudaGetLastError();
   }
 
-  // the stage's y-inverse of the 6 fields (with the row flag: planes kz < kc only)
+  // the stage's y-inverse of the 6 fields (a pruned state: the planes kz < kc only)
   static void y_inverse(const PassArgs& a, cudaStream_t st) {
+    const bool pr = a.prune >= PRUNE_ROWS;
     y_stage<1, 0>(a.ytile[0], bit(a.plan, PLAN_YI), reinterpret_cast<cx<T>*>(a.W),
-                  reinterpret_cast<const cx<T>*>(a.tw), k3y(a), M, 6, st, a.rows, kc_of(k3z(a)));
+                  reinterpret_cast<const cx<T>*>(a.tw), k3y(a), pr ? kc_of(k3z(a)) : M, 6, st, pr);
   }
 
   static void rhs_front(const PassArgs& a, cudaStream_t st) {
@@ -2257,71 +2081,6 @@ struct SolverImpl {
     }
   }
 
-  // ---- plane-pass schedule
-  using PC = PlaneCfg<T, N>;
-  static size_t plane_smem(int stage, int last) {
-    const size_t x = xsmem_stage(stage, last);
-    return x > PC::SMEM_Y ? x : PC::SMEM_Y;
-  }
-  static cudaError_t plane_reset(const PassArgs& a, cudaStream_t st) {
-    return cudaMemsetAsync(a.ctl + 1, 0, (size_t)(PC::ctl_words() - 1) * sizeof(int), st);
-  }
-  static void plane_launch(const PassArgs& a, cudaStream_t st) {
-    const int blocks = num_sms() * PC::MINB;
-    const int L = a.plane_lag > 0 ? a.plane_lag : PC::lag(blocks);
-    k_plane<T, N><<<blocks, PLANE_THREADS, plane_smem(a.stage, a.last), st>>>(f32args(a), a.ctl, L);
-  }
-  static cudaError_t rk_stage_fused(const PassArgs& a, cudaStream_t st) {
-    if constexpr (PLANE) {
-      cudaError_t e = plane_reset(a, st);
-      if (e != cudaSuccess) return e;
-      z_cross(a, st);
-      plane_launch(a, st);
-      return cudaGetLastError();
-    } else {
-      return cudaErrorNotSupported;
-    }
-  }
-  static cudaError_t rk_stage_fused_part(const PassArgs& a, int part, cudaStream_t st) {
-    if constexpr (PLANE) {
-      if (part == 0) {
-        cudaError_t e = plane_reset(a, st);
-        if (e != cudaSuccess) return e;
-        z_cross(a, st);
-      } else {
-        plane_launch(a, st);
-      }
-      return cudaGetLastError();
-    } else {
-      return cudaErrorNotSupported;
-    }
-  }
-  static cudaError_t prime_fused(const PassArgs& a, int from_stage, cudaStream_t st) {
-    cudaError_t e = x_inverse_curl(a, from_stage, st);
-    if (e != cudaSuccess) return e;
-    y_go<1, 0, 0>(reinterpret_cast<cx<T>*>(a.W), reinterpret_cast<const cx<T>*>(a.tw), k3y(a), M, 6, st);
-    return cudaGetLastError();
-  }
-  static cudaError_t plane_wait_test(const PassArgs& a, cudaStream_t st) {
-    if constexpr (PLANE) {
-      int kc = (a.kmax3 + 2) / 3;
-      if (kc > M) kc = M;
-      // the chunks of steps 0 .. 2L-1 and step 2L's y-forward and x-stage chunks
-      const int L = a.plane_lag > 0 ? a.plane_lag : PC::lag(num_sms() * PC::MINB);
-      int first_yi = 0;  // no step before 2L holds y-inverse chunks
-      for (int q = 0; q <= 2 * L; ++q) first_yi += (q < kc ? PC::NYF : 0) + (q >= L && q < M + L ? PC::NX : 0);
-      cudaError_t e = plane_reset(a, st);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(a.ctl + PLANE_CTL_HEAD, &first_yi, sizeof(int), cudaMemcpyHostToDevice, st);
-      if (e != cudaSuccess) return e;
-      plane_launch(a, st);
-      e = cudaGetLastError();
-      if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // first_yi lives on this stack
-      return e;
-    } else {
-      return cudaErrorNotSupported;
-    }
-  }
-
   static cudaError_t rhs(const PassArgs& a, cudaStream_t st) {
     cudaError_t e = x_inverse_curl(a, 0, st);
     if (e != cudaSuccess) return e;
@@ -2338,7 +2097,7 @@ struct SolverImpl {
     using Y = YCfg<T, N, 0, 0, NY>;
     k_zpass<T, N, ZM_LOAD, 0, NY, NZ><<<dim3(N / G::ZTX, NY), ZP_THREADS, G::ZSMEM, st>>>(a);
     k_ypass<T, N, 0, 0, 0, NY, NZ><<<dim3(N / Y::TX, M, 3), Y::THREADS, Y::SMEM, st>>>(
-        reinterpret_cast<cx<T>*>(a.U), reinterpret_cast<const cx<T>*>(a.tw), k3y(a), nullptr, 0);
+        reinterpret_cast<cx<T>*>(a.U), reinterpret_cast<const cx<T>*>(a.tw), k3y(a));
     k_xpass<T, N, XM_FWD_STORE, NY, NZ><<<ROWS, XP_THREADS, G::XSMEM, st>>>(f32args(a));
     return cudaGetLastError();
   }
@@ -2347,7 +2106,7 @@ struct SolverImpl {
     using Y = YCfg<T, N, 1, 0, NY>;
     k_xpass<T, N, XM_INV_PLAIN, NY, NZ><<<ROWS, XP_THREADS, G::XSMEM, st>>>(f32args(a));
     k_ypass<T, N, 1, 0, 0, NY, NZ><<<dim3(N / Y::TX, M, 3), Y::THREADS, Y::SMEM, st>>>(
-        reinterpret_cast<cx<T>*>(a.W), reinterpret_cast<const cx<T>*>(a.tw), k3y(a), nullptr, 0);
+        reinterpret_cast<cx<T>*>(a.W), reinterpret_cast<const cx<T>*>(a.tw), k3y(a));
     k_zpass<T, N, ZM_STORE, 0, NY, NZ><<<dim3(N / G::ZTX, NY), ZP_THREADS, G::ZSMEM, st>>>(a);
     return cudaGetLastError();
   }
@@ -2358,7 +2117,7 @@ struct SolverImpl {
     k_diag_final<<<1, 32, 0, st>>>(a.partials, DIAG_BLOCKS);
     k_xpass<T, N, XM_INV_DIV, NY, NZ><<<ROWS, XP_THREADS, G::XSMEM, st>>>(f32args(a));
     k_ypass<T, N, 1, 0, 0, NY, NZ><<<dim3(N / Y::TX, M, 1), Y::THREADS, Y::SMEM, st>>>(
-        reinterpret_cast<cx<T>*>(a.D), reinterpret_cast<const cx<T>*>(a.tw), k3y(a), nullptr, 0);
+        reinterpret_cast<cx<T>*>(a.D), reinterpret_cast<const cx<T>*>(a.tw), k3y(a));
     cudaMemsetAsync(a.maxbits, 0, sizeof(unsigned long long), st);
     k_zpass<T, N, ZM_MAXABS, 0, NY, NZ><<<dim3(N / G::ZTX, NY), ZP_THREADS, G::ZSMEM, st>>>(a);
     return cudaGetLastError();
@@ -2368,9 +2127,7 @@ struct SolverImpl {
     static const DnsOps o = {N,         sizeof(T) == 4 ? 0 : 1, sizeof(cx<T>), &prepare,   &x_inverse_curl,
                              &rk_stage, &rk_stage_part,        &rhs,          &forward3d, &inverse3d,
                              &diag,     BATCHED ? &rk_stage_batch : nullptr, &y_tiles, &z_tiles,
-                             PLANE ? &rk_stage_fused : nullptr, &prime_fused,
-                             PLANE ? &rk_stage_fused_part : nullptr, PLANE ? &plane_wait_test : nullptr,
-                             PLANE ? PlaneCfg<T, N>::ctl_words() : 0, NY, NZ, G::TW, PLANS, default_plan()};
+                             NY,        NZ,                    G::TW,         PLANS,      default_plan()};
     return &o;
   }
 };

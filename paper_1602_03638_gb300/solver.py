@@ -53,16 +53,16 @@ def set_tune_cache(path) -> None:
 
 def tune_cache_lookup(device: str, shape, dtype: str):
     """The stored tiles entry for (device, (Nx, Ny, Nz), dtype), or None:
-    {"y_inverse", "y_forward", "z", "plan", "fused_planes"}."""
+    {"y_inverse", "y_forward", "z", "plan"}."""
     nx, ny, nz = _shape(shape)
-    v = [ctypes.c_int() for _ in range(5)]
+    v = [ctypes.c_int() for _ in range(4)]
     rc = _lib.lib().dns_tune_cache_lookup(device.encode(), nx, ny, nz, {"f32": 0, "f64": 1}[dtype],
                                           *[ctypes.byref(x) for x in v])
     if rc < 0:
         _lib.check(rc, "dns_tune_cache_lookup")
     if rc == 0:
         return None
-    return dict(zip(("y_inverse", "y_forward", "z", "plan", "fused_planes"), (x.value for x in v)))
+    return dict(zip(("y_inverse", "y_forward", "z", "plan"), (x.value for x in v)))
 
 
 def _shape(N) -> tuple:
@@ -183,10 +183,9 @@ class Solver:
         _lib.check(_lib.lib().dns_set_rk_tableau(self._h, int(form), len(a), av, bv), "dns_set_rk_tableau")
 
     def tune_tiles(self, steps: int = 5) -> tuple:
-        """Time dns_step with each schedule, radix plan and y- and z-pass tile width the grid
-        offers; keep the fastest schedule and plan (options "fused_planes", "fft_plan") and
-        (y_inverse, y_forward, z) widths (0 = default), returned. The state and time are
-        left unchanged."""
+        """Time dns_step with each radix plan and y- and z-pass tile width the grid offers;
+        keep the fastest plan (option "fft_plan") and (y_inverse, y_forward, z) widths
+        (0 = default), returned. The state and time are left unchanged."""
         ti, tf, tz = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _lib.check(_lib.lib().dns_tune_tiles(self._h, int(steps), ctypes.byref(ti), ctypes.byref(tf), ctypes.byref(tz)),
                    "dns_tune_tiles")
@@ -261,20 +260,13 @@ class Solver:
         return {k: getattr(d, k) for k, _ in d._fields_}
 
     KERNEL_CLASSES = ("y_inverse", "z_pass", "y_forward", "x_stage")
-    PLANE_CLASSES = ("z_pass", "plane_pass")
 
     def profile_steps(self, n: int) -> dict:
-        """Advance n steps eagerly; per kernel class (total ms, launches). The classes are
-        those of the handle's schedule: four passes, or z-pass and plane pass."""
+        """Advance n steps eagerly; per kernel class (total ms, launches)."""
         ms = (ctypes.c_double * 4)()
         ln = (ctypes.c_int * 4)()
         _lib.check(_lib.lib().dns_profile_steps(self._h, int(n), ms, ln, 4), "dns_profile_steps")
-        names = self.PLANE_CLASSES if self.get_option("fused_planes") else self.KERNEL_CLASSES
-        return {k: (ms[i], ln[i]) for i, k in enumerate(names)}
-
-    def plane_wait_timeout_test(self) -> int:
-        """Runs dns_debug_plane_wait_timeout; returns its status code (DNS_ERR_TIMEOUT expected)."""
-        return int(_lib.lib().dns_debug_plane_wait_timeout(self._h))
+        return {k: (ms[i], ln[i]) for i, k in enumerate(self.KERNEL_CLASSES)}
 
     def device_bytes(self) -> int:
         return int(_lib.lib().dns_device_bytes(self._h))

@@ -103,18 +103,19 @@ def test_tune_cache_file_lookup(tmp_path, L):
 
     path = tmp_path / "tune.txt"
     path.write_text(
-        "tiles GB300 32 32 32 f32 8 4 16 5 0\n"
-        "tiles GB300 32 32 32 f32 16 4 8 9 0\n"     # later line wins
-        "tiles GB300 48 48 48 f64 0 0 4 x 0\n"      # malformed value: ignored
-        "tiles GB300 256 256 256 f32 0 0 0 0 1\n"
-        "tiles Other 32 32 32 f32 4 4 4 1 0\n"      # another device
+        "tiles GB300 32 32 32 f32 8 4 16 5\n"
+        "tiles GB300 32 32 32 f32 16 4 8 9\n"     # later line wins
+        "tiles GB300 48 48 48 f64 0 0 4 x\n"      # malformed value: ignored
+        "tiles GB300 256 256 256 f32 0 0 0 0\n"
+        "tiles GB300 64 64 64 f32 4 4\n"          # too few values: ignored
+        "tiles Other 32 32 32 f32 4 4 4 1\n"      # another device
         "ensemble GB300 f32 32:2,48:1 0 4\n"
         "garbage\n")
     try:
         set_tune_cache(path)
-        assert tune_cache_lookup("GB300", 32, "f32") == {"y_inverse": 16, "y_forward": 4, "z": 8, "plan": 9,
-                                                         "fused_planes": 0}
-        assert tune_cache_lookup("GB300", 256, "f32")["fused_planes"] == 1
+        assert tune_cache_lookup("GB300", 32, "f32") == {"y_inverse": 16, "y_forward": 4, "z": 8, "plan": 9}
+        assert tune_cache_lookup("GB300", 256, "f32") == {"y_inverse": 0, "y_forward": 0, "z": 0, "plan": 0}
+        assert tune_cache_lookup("GB300", 64, "f32") is None
         assert tune_cache_lookup("GB300", (32, 32, 32), "f64") is None
         assert tune_cache_lookup("GB300", 48, "f64") is None
         assert tune_cache_lookup("Other", 32, "f32")["plan"] == 1
@@ -126,4 +127,4 @@ def test_tune_cache_file_lookup(tmp_path, L):
         set_tune_cache(None)
     a = ctypes.c_int()
     assert L.dns_tune_cache_lookup(None, 32, 32, 32, 0, ctypes.byref(a), ctypes.byref(a), ctypes.byref(a),
-                                   ctypes.byref(a), ctypes.byref(a)) == _lib.DNS_ERR_ARG
+                                   ctypes.byref(a)) == _lib.DNS_ERR_ARG

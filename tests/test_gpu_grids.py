@@ -156,7 +156,7 @@ def test_unsupported_counts_and_cubic_only_features_are_refused():
         Solver((32, 16, 48), 0.01, 1e-3, "f32")
     with Solver((32, 16, 24), 0.01, 1e-3, "f32") as s:
         with pytest.raises(RuntimeError):
-            s.set_option("fused_planes", 1)
+            s.set_option("fft_plan", 1)
         with pytest.raises(RuntimeError):
             s.set_option("y_tile_inverse", 8)
     # equal counts give the cubic solver

@@ -7,7 +7,9 @@ the right-hand side of Eq. NSfinal is -nu |k|^2 u_hat. A state that vanishes on 
 the transforms of those rows are transforms of zeros. The solver checks the state on the
 device whenever it is set (or the dealias rule changes) and then skips those rows: the
 x-stage and the x inverse leave them alone, the y-inverse transforms only the planes
-kz < N/3 and reads the other rows as zeros, the z-pass reads only kz < N/3. Skipping zeros
+kz < N/3 and reads the other rows as zeros, the z-pass reads only kz < N/3; where the state
+also vanishes at |kx| >= N/3 (flag "box_vanish"), the x-stage reads and writes its rows at the
+kept columns only. Skipping zeros
 changes no nonzero sum, so the pruned steps must equal the full ones (prune_rows = 0) bit
 for bit (exact zeros of either sign compare equal) on every z-pass kernel, integrator,
 dealias rule and schedule; a state with modes outside the box must take the full path.
@@ -63,11 +65,12 @@ def test_flag_follows_the_state():
     N = 48
     with Solver(N, 0.01, 0.004, "f32") as s:
         assert s.get_option("rows_vanish") == 1.0  # a new handle holds the zero state
+        assert s.get_option("box_vanish") == 1.0
         assert s.get_option("prune_rows") == 1.0
         s.set_state_spectral(_iso(N, 1, "f32"))
-        assert s.get_option("rows_vanish") == 1.0
+        assert s.get_option("rows_vanish") == 1.0 and s.get_option("box_vanish") == 1.0
         s.set_state_spectral(_full_spectrum(N, 2, "f32"))
-        assert s.get_option("rows_vanish") == 0.0
+        assert s.get_option("rows_vanish") == 0.0 and s.get_option("box_vanish") == 0.0
         # one mode at ky = N/3: outside the box of 3|k| < N, inside the one of 3|k| < N + 2
         uh = np.zeros((3, N, N, N // 2 + 1), np.complex64)
         uh[0, 1, N // 3, 1] = 1.0
@@ -85,7 +88,11 @@ def test_flag_follows_the_state():
         uh[:] = 0
         uh[1, N // 3, 1, 1] = 1.0
         s.set_state_spectral(uh)
-        assert s.get_option("rows_vanish") == 1.0
+        assert s.get_option("rows_vanish") == 1.0 and s.get_option("box_vanish") == 0.0
+        uh[1, N // 3, 1, 1] = 0.0
+        uh[1, N // 3 - 1, 1, 1] = 1.0
+        s.set_state_spectral(uh)
+        assert s.get_option("box_vanish") == 1.0
         uh[:] = 0
         uh[2, 3, N // 2 - 1, 2] = np.nan  # NaN counts as nonzero
         s.set_state_spectral(uh)
@@ -146,6 +153,28 @@ def test_pruned_taylor_green_matches_oracle():
         got, vanish = _run(N, dtype, uh.astype(CPLX[dtype]), steps, 1, nu=nu, dt=dt)
         assert vanish == 1.0
         assert rel_l2(got, ref) <= bound, dtype
+
+
+@pytest.mark.parametrize("N,dtype", [(48, "f32"), (96, "f64"), (512, "f32")])
+def test_columns_outside_the_box_in_kept_rows(N, dtype):
+    # modes at |kx| >= N/3 on rows inside the box: the rows are pruned, the columns are not
+    rng = np.random.default_rng(N)
+    uh = inputs.isotropic_spectral(N, seed=11, k0=max(2.0, N / 8.0), device="cuda", dtype=TCPLX[dtype])
+    for kx in (N // 3 + 1, N - N // 3 - 1, N // 2 - 1):
+        uh[0, kx, 3, 2] = complex(rng.standard_normal(), rng.standard_normal())
+        uh[2, kx, N - 2, 1] = complex(rng.standard_normal(), rng.standard_normal())
+    out = []
+    for prune in (1, 0):
+        with Solver(N, 0.01, 0.004, dtype) as s:
+            s.set_option("prune_rows", prune)
+            s.set_state_spectral(uh)
+            assert s.get_option("rows_vanish") == 1.0 and s.get_option("box_vanish") == 0.0
+            s.step(3)
+            o = torch.empty_like(uh)
+            s.get_state_spectral(o)
+            torch.cuda.synchronize()
+            out.append(o)
+    assert torch.equal(out[0], out[1])
 
 
 def test_out_of_box_state_takes_the_full_path():
@@ -227,21 +256,25 @@ def test_new_state_after_pruned_steps_reads_no_stale_rows():
     assert np.array_equal(outs[0], outs[1])
 
 
-def test_plane_schedule_and_tuner_with_the_flag():
-    N = 256
-    uh = inputs.isotropic_spectral(N, seed=9, k0=8.0, device="cuda", dtype=torch.complex64)
-    outs = []
-    for prune, fused in ((1, 0), (1, 1), (0, 0)):
-        with Solver(N, 0.002, 0.002, "f32") as s:
-            s.set_option("prune_rows", prune)
-            s.set_option("fused_planes", fused)
-            s.set_state_spectral(uh)
-            s.step(2)
-            o = torch.empty_like(uh)
-            s.get_state_spectral(o)
-            torch.cuda.synchronize()
-            outs.append(o)
-    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+def test_tuner_with_the_flag():
+    # the tuner times pruned steps from a saved state and restores it: the flag still holds
+    N = 48
+    uh = _iso(N, 9, "f32")
+    with Solver(N, 0.01, 0.004, "f32") as s:
+        s.set_state_spectral(uh)
+        tiles = s.tune_tiles(2)
+        plan = s.get_option("fft_plan")
+        assert s.get_option("rows_vanish") == 1.0 and np.array_equal(s.get_state_spectral(), uh)
+        s.step(4)
+        got = s.get_state_spectral()
+    with Solver(N, 0.01, 0.004, "f32") as s:
+        s.set_option("prune_rows", 0)
+        s.set_option("fft_plan", plan)
+        for k, v in zip(("y_tile_inverse", "y_tile_forward", "z_tile"), tiles):
+            s.set_option(k, v)
+        s.set_state_spectral(uh)
+        s.step(4)
+        assert np.array_equal(s.get_state_spectral(), got)
 
 
 @pytest.mark.parametrize("batching", [0, 1 << 30])

@@ -173,87 +173,3 @@ def test_offered_tile_widths_divide_the_grid_and_fit(N, cb):
         assert N % t == 0
         # tile rows padp(k) (k < N/2) of 6 fields x t columns inside the allocation
         assert padp(N // 2 - 1) * odd_ld(6 * t) + 6 * t - 1 < padded_len(N // 2) * odd_ld(6 * t)
-
-
-# ---------------------------------------------------------------- plane pass work queue
-
-CX, CYF, CYI = 4, 2, 2  # rows / tiles per chunk of k_plane
-
-
-def plane_cfg(N, cb):
-    """Chunks per plane of k_plane: (y-forward, x-stage, y-inverse)."""
-    nti, ntf = N // ycfg(N, cb, 1)[0], N // ycfg(N, cb, 0)[0]
-    assert (3 * ntf) % CYF == 0 and N % CX == 0 and (6 * nti) % CYI == 0
-    return 3 * ntf // CYF, N // CX, 6 * nti // CYI
-
-
-def plane_step_chunks(q, kc, M, L, nyf, nx, nyi):
-    return (nyf if q < kc else 0) + (nx if L <= q < M + L else 0) + (nyi if q >= 2 * L else 0)
-
-
-def plane_decode(item, kc, M, L, cfg, cursor):
-    """The thread-0 decode of k_plane: chunk -> (kind, plane, chunk, (dependency, chunks needed))."""
-    nyf, nx, nyi = cfg
-    q, qbeg = cursor
-    n = plane_step_chunks(q, kc, M, L, *cfg)
-    while item >= qbeg + n:
-        qbeg += n
-        q += 1
-        n = plane_step_chunks(q, kc, M, L, *cfg)
-    cursor[:] = [q, qbeg]
-    r = item - qbeg
-    a = nyf if q < kc else 0
-    b = nx if L <= q < M + L else 0
-    if r < a:
-        return 0, q, r, None
-    if r < a + b:
-        p = q - L
-        return 1, p, r - a, (("yf", p), nyf) if p < kc else None
-    return 2, q - 2 * L, r - a - b, (("x", q - 2 * L), nx)
-
-
-def plane_lag(blocks, cfg):
-    per_step = sum(cfg)
-    return min(8, max(1, (3 * blocks + 2 * per_step - 1) // (2 * per_step)))
-
-
-@pytest.mark.parametrize("L", [1, 2, 3, 5])
-@pytest.mark.parametrize("variant", [0, 1])
-@pytest.mark.parametrize("cb", [8, 16])
-@pytest.mark.parametrize("N", [256, 512, 1024])
-def test_plane_queue_is_a_bijection_whose_waits_point_backwards(N, cb, variant, L):
-    M = N // 2
-    kc = min(M, (N + 2 * variant + 2) // 3)
-    cfg = plane_cfg(N, cb)
-    nyf, nx, nyi = cfg
-    total = nyf * kc + nx * M + nyi * M
-    seen = set()
-    done = {}  # counter -> chunks released so far, in queue order
-    cursor = [0, 0]
-    for item in range(total):
-        kind, plane, chunk, wait = plane_decode(item, kc, M, L, cfg, cursor)
-        assert 0 <= plane < (kc if kind == 0 else M)
-        assert 0 <= chunk < cfg[kind]
-        assert (kind, plane, chunk) not in seen
-        seen.add((kind, plane, chunk))
-        if wait is not None:
-            # everything the chunk waits for lies earlier in the order (taken by a running block)
-            assert done.get(wait[0], 0) == wait[1], (item, kind, plane)
-        if kind < 2:
-            key = ("yf" if kind == 0 else "x", plane)
-            done[key] = done.get(key, 0) + 1
-    assert len(seen) == total
-    # chunks cover every tile / row exactly once
-    assert nyf * CYF == 3 * (N // ycfg(N, cb, 0)[0]) and nx * CX == N and nyi * CYI == 6 * (N // ycfg(N, cb, 1)[0])
-    # the wait test's start chunk is the first y-inverse chunk of plane 0
-    first_yi = sum((nyf if q < kc else 0) + (nx if L <= q < M + L else 0) for q in range(2 * L + 1))
-    assert plane_decode(first_yi, kc, M, L, cfg, [0, 0])[:3] == (2, 0, 0)
-    assert plane_decode(first_yi - 1, kc, M, L, cfg, [0, 0])[0] != 2
-
-
-@pytest.mark.parametrize("cb,N,blocks", [(8, 256, 456), (8, 512, 456), (8, 1024, 304), (16, 512, 304), (16, 256, 304)])
-def test_plane_lag_spans_more_chunks_than_blocks(cb, N, blocks):
-    cfg = plane_cfg(N, cb)
-    L = plane_lag(blocks, cfg)
-    assert 1 <= L <= 8
-    assert L == 8 or L * sum(cfg) >= 1.5 * blocks
