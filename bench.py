@@ -256,7 +256,7 @@ def run_reference(args):
 def main_config(world, N=N_MAIN):
     return {"workload": f"taylor_green_{N}_f32", "model": "pseudo-spectral NS, RK4, 2/3 dealiasing", "N": N,
             "nu": NU, "dt": DT, "global_batch": world, "seq_len": None, "parallelism": f"replicas{world}",
-            "l2": "no flush needed: every pass streams 1.6-3.2 GB, > 129 MB L2"}
+            "l2": "no flush needed: every pass moves 1.8-5 GB, > 129 MB L2"}
 
 
 def reference_config(world, N):
@@ -284,22 +284,31 @@ def run_form(torch, Solver, inputs, N, dtype, warm, steps):
         st = torch.cuda.current_stream()
         s.set_stream(st)
         s.set_state_spectral(inputs.taylor_green_spectral(N, device="cuda", dtype=cdt))
+        pruned = s.get_option("rows_vanish") == 1.0 and s.get_option("prune_rows") == 1.0
         for _ in range(warm):
             s.step(1)
         torch.cuda.synchronize()
         ms = time_steps(torch, s, st, steps) / steps
     rb = 4 if dtype == "f32" else 8
     model_ms = STEP_CV * cv_bytes(N, rb) / (measured_peaks()[0] * 1e9) * 1e3
-    out = {"N": N, "dtype": dtype, "ms_per_step": ms, "value": N ** 3 / (ms * 1e-3), "steps": steps,
+    out = {"N": N, "dtype": dtype, "ms_per_step": ms, "value": N ** 3 / (ms * 1e-3), "steps": steps, "rows_pruned": pruned,
            "hbm_roofline_frac_of_measured": model_ms / ms,
            "truncated_state_roofline_frac_of_measured": model_ms * truncated_step_cv(N) / STEP_CV / ms}
     if dtype == "f64":
         # FP64 arithmetic bound: ~270 N^3 log2 N flops per RK4 step (36 scalar 3D transforms,
-        # radix-2 count) against the FP64 FMA rate measured on this GPU (dns_measure_fp64_peak)
-        flops = 270.0 * N ** 3 * math.log2(N)
+        # radix-2 count, a third per direction) against the FP64 FMA rate measured on this GPU
+        # (dns_measure_fp64_peak). Where the state vanishes outside the 2/3 box the passes
+        # transform only the lines that are not identically zero: per stage the 6 inverse and
+        # 3 forward transforms keep all z-lines, the y-lines of the planes kz < N/3 (zk) and
+        # the x-lines of the rows inside the box (zk yk): a factor (1 + zk + zk yk) / 3.
+        flops_full = 270.0 * N ** 3 * math.log2(N)
+        kc = (N + 2) // 3
+        zk, yk = kc / (N // 2), (2 * kc - 1) / N
+        flops = flops_full * ((1.0 + zk + zk * yk) / 3.0 if pruned else 1.0)
         peak = fp64_peak_tflops() * 1e12
         out["roofline"] = {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": peak / 1e12,
                            "unit": "TFLOP/s", "frac": flops / (ms * 1e-3) / peak, "flops_per_step": flops,
+                           "flops_per_step_full_transforms": flops_full, "rows_pruned": pruned,
                            "peak_kind": "measured (dependent-FMA probe, CUDA events)"}
     return out
 
