@@ -57,12 +57,13 @@ CPU_N, CPU_STEPS = 128, 8
 PAPER_TG512_PTS_STEPS_PER_S = 6.2e7  # Sec. 4 verification run, 2048 Shaheen cores (context)
 
 
-def pass_bytes(N, real_bytes, stages=4, rows=False):
+def pass_bytes(N, real_bytes, stages=4, rows=False, box=False):
     """Algorithmic bytes per launch of each kernel class (mean over the RK4 stages).
     N: one point count, or (Nx, Ny, Nz) for a grid with other counts per direction (then
     FV = Nx Ny (Nz/2), kc = (Nz+2)//3 planes and the rows |ky| < Ny/3 of Ny).
     rows: the state vanishes on every row (kz, ky) outside the 2/3 box (the solver's row
-    flag), so the passes skip those rows (below).
+    flag), so the passes skip those rows (below); box: it also vanishes at |kx| >= N/3, so
+    the x-stage reads and writes the RK state at the kept columns (a fraction yk) only.
 
     Counted from the 2/3 mask: a field-volume FV = N^2 (N/2) complex values (the stored half
     spectrum; the kz = N/2 plane is identically zero); kc = (N+2)//3 planes kz < N/3 and
@@ -77,7 +78,7 @@ def pass_bytes(N, real_bytes, stages=4, rows=False):
       y_inverse  R 6 zk yk FV (kept rows of the planes kz < N/3) + W 6 zk FV (those planes)
       z_pass     R 6 zk FV + W 3 zk FV
       y_forward  as above
-      x_stage    (R 3 + RK state + W 6) zk yk FV (kept rows only)
+      x_stage    (R 3 + RK state + W 6) zk yk FV (kept rows only; with box the RK state x yk)
     """
     nx, ny, nz = (N,) * 3 if isinstance(N, int) else tuple(N)
     M = nz // 2
@@ -98,8 +99,9 @@ def pass_bytes(N, real_bytes, stages=4, rows=False):
         rk.append(r + w)
     rk_mean = sum(rk) / len(rk)
     if rows:
+        xk = (2 * ((nx + 2) // 3) - 1) / nx if box else 1.0
         return {"y_inverse": 6.0 * zk * (yk + 1.0) * fv, "z_pass": 9.0 * zk * fv,
-                "y_forward": (3.0 * zk + 3.0 * zk * yk) * fv, "x_stage": (3.0 + rk_mean + 6.0) * zk * yk * fv}
+                "y_forward": (3.0 * zk + 3.0 * zk * yk) * fv, "x_stage": (3.0 + rk_mean * xk + 6.0) * zk * yk * fv}
     return {"y_inverse": 12.0 * fv, "z_pass": (6.0 + 3.0 * zk) * fv, "y_forward": (3.0 * zk + 3.0 * zk * yk) * fv,
             "x_stage": (3.0 * zk * yk + rk_mean + 6.0) * fv}
 
@@ -353,7 +355,8 @@ def run_grids(torch, Solver, inputs, shape=(1024, 512, 256), warm=3, steps=10):
                     "hbm_roofline_frac_of_measured": STEP_CV * cv_bytes(shape, rb) / (peak * 1e9) / (ms * 1e-3)}
             if dtype == "f32":
                 prof = s.profile_steps(n)
-                kb = pass_bytes(shape, rb, rows=s.get_option("rows_vanish") == 1.0)
+                kb = pass_bytes(shape, rb, rows=s.get_option("rows_vanish") == 1.0,
+                                box=s.get_option("box_vanish") == 1.0)
                 form["kernels"] = {k: {"ms_per_launch": t / c, "launches": c,
                                        "achieved_gbs": kb[k] / (t / c * 1e-3) / 1e9,
                                        "frac_of_peak": kb[k] / (t / c * 1e-3) / 1e9 / peak}
@@ -591,6 +594,7 @@ def run_ours(args):
     # transform would leave rounding residue there and the full transforms would run)
     s.set_state_spectral(inputs.taylor_green_spectral(N, device="cuda", dtype=torch.complex64))
     rows = s.get_option("rows_vanish") == 1.0 and s.get_option("prune_rows") == 1.0
+    box = rows and s.get_option("box_vanish") == 1.0
     for _ in range(args.warmup):
         s.step(1)
     torch.cuda.synchronize()
@@ -609,7 +613,7 @@ def run_ours(args):
     dom = max(prof, key=lambda k: prof[k][0])
     dom_ms = prof[dom][0] / prof[dom][1]
     cvb = cv_bytes(N, 4)
-    kb = pass_bytes(N, 4, rows=rows)
+    kb = pass_bytes(N, 4, rows=rows, box=box)
     achieved = kb[dom] / (dom_ms * 1e-3) / 1e9
     kernels = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1], "share": v[0] / sum(x[0] for x in prof.values()),
                    "algorithmic_bytes_per_launch": kb[k],
