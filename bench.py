@@ -654,8 +654,13 @@ def run_ours(args):
                           "frac_of_measured": step_bytes / (ms_step * 1e-3) / 1e9 / peak,
                           "frac_of_spec_8TBps": step_bytes / (ms_step * 1e-3) / 1e9 / SPEC_HBM_GBS,
                           # the 3-pass model (x, y and z transforms each a separate HBM sweep, 204 cv
-                          # per step): what the plane blocking of the 132-cv model would buy
-                          "frac_of_measured_3pass_model": 204.0 * cvb / (ms_step * 1e-3) / 1e9 / peak,
+                          # per step): what the plane blocking of the 132-cv model would buy (like the
+                          # 132-cv model it counts the full transforms, which a pruned step skips)
+                          "frac_of_measured_3pass_model":
+                              None if rows else 204.0 * cvb / (ms_step * 1e-3) / 1e9 / peak,
+                          "models": "model_bytes_per_step (132 cv) and the 3-pass model count the full "
+                                    "transforms; with rows_pruned the passes skip the lines a truncated state "
+                                    "leaves zero, whose own 2-pass minimum is the truncated-state model",
                           # the same 2-pass model for a state that vanishes outside the 2/3 box
                           # (the one this workload has): the minimum the pruned passes could reach
                           "truncated_state_model_bytes_per_step": truncated_step_cv(N) * cvb,
