@@ -173,3 +173,36 @@ def test_offered_tile_widths_divide_the_grid_and_fit(N, cb):
         assert N % t == 0
         # tile rows padp(k) (k < N/2) of 6 fields x t columns inside the allocation
         assert padp(N // 2 - 1) * odd_ld(6 * t) + 6 * t - 1 < padded_len(N // 2) * odd_ld(6 * t)
+
+
+# ---------------------------------------------------------------- x-stage rows of a pruned state
+
+def _kept_rows_map(NY, M, k3y, k3z):
+    """The block -> row map of the x-stage launch over the rows inside the 2/3 box
+    (xpass_body with compact = true, xpass_kept_ky, x_rows)."""
+    R = min((k3y - 1) // 3, NY // 2 - 1)
+    kcz = min(M, (k3z + 2) // 3)
+    w = 2 * R + 1
+    rows = []
+    for bx in range(kcz * w):
+        t = bx % w
+        rows.append((bx // w) * NY + (t if t <= R else NY - w + t))
+    return rows
+
+
+@pytest.mark.parametrize("shape", [(n, n, n) for n in (8, 12, 16, 24, 32, 48, 64, 96, 128, 256, 512, 1024)]
+                         + [(32, 16, 24), (24, 48, 16), (1024, 512, 256)])
+@pytest.mark.parametrize("variant", [0, 1])
+def test_pruned_x_stage_rows_are_exactly_the_kept_rows(shape, variant):
+    nx, ny, nz = shape
+    M = nz // 2
+    k3y, k3z = ny + 2 * variant, nz + 2 * variant
+    rows = _kept_rows_map(ny, M, k3y, k3z)
+    kept = []
+    for kz in range(M):
+        for ky in range(ny):
+            kf = ky if ky < ny // 2 else ky - ny
+            if 3 * kz < k3z and 3 * abs(kf) < k3y:
+                kept.append(kz * ny + ky)
+    assert sorted(rows) == kept  # a bijection onto the kept rows, in row order per plane
+    assert all(0 <= r < M * ny for r in rows)
