@@ -662,14 +662,13 @@ __device__ __forceinline__ void zpass_body(const PassArgs a, const int bx, const
         if (klim > M) klim = M;
       }
     }
-    if (klim < M) {
-      for (int e = threadIdx.x; e < NF * TX * klim; e += ZP_THREADS) {
-        const int x = e % TX, k = (e / TX) % klim, f = e / (TX * klim);
-        cp_async<sizeof(cx<T>)>(s + padp(k) * LD + f * TX + x, src + f * FS + ((size_t)k * NY + y) * N + x0 + x);
-      }
-      for (int e = threadIdx.x; e < NF * TX * (M - klim); e += ZP_THREADS) {
-        const int x = e % TX, k = klim + (e / TX) % (M - klim), f = e / (TX * (M - klim));
-        s[padp(k) * LD + f * TX + x] = mk((T)0, (T)0);
+    if (klim < M) {  // the walk of the full fill (compile-time divisors), planes past klim as zeros
+      for (int e = threadIdx.x; e < NF * TX * M; e += ZP_THREADS) {
+        const int x = e % TX, k = (e / TX) % M, f = e / (TX * M);
+        if (k < klim)
+          cp_async<sizeof(cx<T>)>(s + padp(k) * LD + f * TX + x, src + f * FS + ((size_t)k * NY + y) * N + x0 + x);
+        else
+          s[padp(k) * LD + f * TX + x] = mk((T)0, (T)0);
       }
     } else {
       for (int e = threadIdx.x; e < NF * TX * M; e += ZP_THREADS) {
