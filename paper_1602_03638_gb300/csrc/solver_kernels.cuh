@@ -735,14 +735,27 @@ __device__ __forceinline__ void zpass_body(const PassArgs a, const int bx, const
       kc = ((NZ == N ? a.kmax3 : a.kmax3z) + 2) / 3;
       if (kc > M) kc = M;
     }
-    for (int e = threadIdx.x; e < 3 * TX * kc; e += ZP_THREADS) {
-      const int x = e % TX, k = (e / TX) % kc, c = e / (TX * kc);
-      const int l = c * TX + x;
-      const cx<T> zk = s[padp(k) * LD + l], zm = s[padp((M - k) % M) * LD + l];
-      const cx<T> wk = ldro(tw + k * TS);
-      const cx<T> A = zk + conjg(zm), B = zk - conjg(zm);
-      dst[c * FS + ((size_t)k * NY + y) * N + x0 + x] = scal(A + mul_mi(cmul(wk, B)), (T)0.5);
-    }
+    // the walk over (product, k < kc, x) with kc a compile-time constant where it is the
+    // default rule's (or M), so that its divisions are multiplications
+    auto post = [&](auto kcc) {
+      constexpr int KC = decltype(kcc)::value;  // 0: kc known at run time only
+      const int kk = KC > 0 ? KC : kc;
+      for (int e = threadIdx.x; e < 3 * TX * kk; e += ZP_THREADS) {
+        const int x = e % TX, k = (e / TX) % kk, c = e / (TX * kk);
+        const int l = c * TX + x;
+        const cx<T> zk = s[padp(k) * LD + l], zm = s[padp((M - k) % M) * LD + l];
+        const cx<T> wk = ldro(tw + k * TS);
+        const cx<T> A = zk + conjg(zm), B = zk - conjg(zm);
+        dst[c * FS + ((size_t)k * NY + y) * N + x0 + x] = scal(A + mul_mi(cmul(wk, B)), (T)0.5);
+      }
+    };
+    constexpr int KC0 = (NZ + 2) / 3 < M ? (NZ + 2) / 3 : M;  // kc of the rule 3|k| < NZ
+    if (kc == M)
+      post(std::integral_constant<int, M>{});
+    else if (kc == KC0)
+      post(std::integral_constant<int, KC0>{});
+    else
+      post(std::integral_constant<int, 0>{});
   } else if constexpr (MODE == ZM_STORE) {
     cx<T>* out = reinterpret_cast<cx<T>*>(a.out);
     for (int e = threadIdx.x; e < 3 * TX * M; e += ZP_THREADS) {
